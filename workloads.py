@@ -1,0 +1,149 @@
+"""Seeded synthetic canonical (CP) tensors for RHOSVD.
+
+This module only *generates inputs*: factor matrices U^(l) (n_l x R, column-major,
+FP64) and weights xi (length R) of a d=3 canonical tensor
+A = sum_k xi_k u1_k (x) u2_k (x) u3_k (paper Sec. 2.1, eq. can_A3).  It holds none
+of the RHOSVD arithmetic; both the CPU oracle (``oracle/``) and the CUDA library
+consume what it returns.
+
+Grid (paper Sec. 3 "centers of discretization intervals", Sec. 4.1 mesh h=2b/n):
+cell centres x_i = -b + (i - 1/2) h, h = 2b/n, i = 1..n.  Factor columns are the
+Gaussians sampled at those points (collocation).
+
+Random numbers come from numpy's PCG64 generator seeded with the stated seed;
+every draw below is listed in the order it is made, so a workload is fully fixed
+by (recipe, seed).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class CP:
+    """A d=3 canonical tensor: U[l] is (n_l, R) Fortran-ordered float64, xi is (R,)."""
+
+    U: list
+    xi: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return [u.shape[0] for u in self.U]
+
+    @property
+    def R(self):
+        return int(self.xi.shape[0])
+
+
+def grid(n: int, b: float) -> np.ndarray:
+    """Cell-centre grid on [-b, b] with h = 2b/n."""
+    h = 2.0 * b / n
+    return -b + (np.arange(n, dtype=np.float64) + 0.5) * h
+
+
+def gaussian_columns(x: np.ndarray, centres: np.ndarray, expo: np.ndarray) -> np.ndarray:
+    """Column k = exp(-expo_k (x - centre_k)^2) sampled on x; (n, R) Fortran order."""
+    d = x[:, None] - centres[None, :]
+    return np.asfortranarray(np.exp(-expo[None, :] * d * d))
+
+
+def gaussian_sum(n: int, R: int, seed: int, b: float = 10.0, centre_box: float = 5.0,
+                 a_range=(0.5, 20.0), c_range=(0.1, 1.0)) -> CP:
+    """Sum of R isotropic Gaussians c_k exp(-a_k |x - x_k|^2) on an n^3 grid.
+
+    Draw order with PCG64(seed): centres (R,3) uniform in [-centre_box, centre_box],
+    then log a_k uniform in [log a_lo, log a_hi], then c_k uniform in c_range.
+    The 3D Gaussian separates: u_k^(l)(i) = exp(-a_k (x_i - x_{k,l})^2), xi_k = c_k.
+    """
+    g = np.random.default_rng(seed)
+    centres = g.uniform(-centre_box, centre_box, size=(R, 3))
+    a = np.exp(g.uniform(math.log(a_range[0]), math.log(a_range[1]), size=R))
+    c = g.uniform(c_range[0], c_range[1], size=R)
+    x = grid(n, b)
+    U = [gaussian_columns(x, centres[:, l].copy(), a) for l in range(3)]
+    return CP(U=U, xi=c.astype(np.float64),
+              meta=dict(kind="gaussian_sum", n=n, R=R, seed=seed, b=b,
+                        centres=centres, a=a))
+
+
+def newton_sinc_nodes(h: float = 0.4, k_lo: int = -19, k_hi: int = 0):
+    """Quadrature nodes/weights for 1/z = (2/sqrt(pi)) int_0^inf exp(-z^2 t^2) dt.
+
+    With t = e^u the integrand becomes (2/sqrt(pi)) e^u exp(-z^2 e^{2u}); the step-h
+    trapezoid (sinc) rule gives t_k = e^{k h}, p_k = (2/sqrt(pi)) h e^{k h}
+    (paper Sec. 4.1, eqs. laplace, sinc_Newt, Laplace_Newton).  The long-range part
+    keeps t_k <= 1, i.e. k <= 0 (eq. RS_repres).
+    """
+    k = np.arange(k_lo, k_hi + 1, dtype=np.float64)
+    t = np.exp(k * h)
+    p = (2.0 / math.sqrt(math.pi)) * h * np.exp(k * h)
+    return t, p
+
+
+def newton_long_range_sum(n: int = 2048, N: int = 1000, seed: int = 0, b: float = 10.0,
+                          centre_box: float = 8.0, h: float = 0.4, k_lo: int = -19,
+                          k_hi: int = 0) -> CP:
+    """Collective long-range Newton potential of N unit charges.
+
+    Each centre x_j carries the long-range Gaussians of the sinc-quadrature Newton
+    kernel: p_k exp(-t_k^2 |x - x_j|^2), k = k_lo..k_hi (t_k <= 1).  R = N (k_hi-k_lo+1).
+    Draw order with PCG64(seed): centres (N,3) uniform in [-centre_box, centre_box].
+    Term index nu = j * M + (k - k_lo), M = k_hi - k_lo + 1.
+    """
+    g = np.random.default_rng(seed)
+    centres = g.uniform(-centre_box, centre_box, size=(N, 3))
+    t, p = newton_sinc_nodes(h, k_lo, k_hi)
+    M = t.shape[0]
+    x = grid(n, b)
+    expo = np.tile(t * t, N)
+    U = []
+    for l in range(3):
+        cen = np.repeat(centres[:, l], M)
+        U.append(gaussian_columns(x, cen, expo))
+    xi = np.tile(p, N).astype(np.float64)
+    return CP(U=U, xi=xi, meta=dict(kind="newton_long_range", n=n, N=N, seed=seed, b=b,
+                                    h=h, k_lo=k_lo, k_hi=k_hi, centres=centres))
+
+
+def batched_gaussian_sums(count: int = 512, seed0: int = 0, n_choices=(128, 256, 512, 1024),
+                          R_range=(100, 8000)):
+    """Shapes and seeds of the batched workload: member i uses seed seed0+i.
+
+    Draw order with PCG64(seed0 + 10**6): n_i uniform over n_choices, then
+    R_i = round(exp(uniform(log R_lo, log R_hi))).  Returns a list of (n, R, seed).
+    """
+    g = np.random.default_rng(seed0 + 10**6)
+    ns = g.choice(np.asarray(n_choices), size=count)
+    Rs = np.rint(np.exp(g.uniform(math.log(R_range[0]), math.log(R_range[1]), size=count)))
+    return [(int(ns[i]), int(Rs[i]), seed0 + i) for i in range(count)]
+
+
+# Named workloads (sizes, distributions and thresholds).
+CONFIGS = {
+    "gauss_n128_R200": dict(n=128, R=200, seed=0, eps=1e-6),
+    "hadamard_n1024_R64x64": dict(n=1024, Ra=64, Rb=64, seeds=(0, 1), eps=1e-7),
+    "newton_lr_n2048_N1000": dict(n=2048, N=1000, seed=0, eps=1e-6),
+}
+
+
+def hartree_like_factors(n: int = 1024, Ra: int = 64, Rb: int = 64, seeds=(0, 1)):
+    """The two rank-64 Gaussian sums whose Hadamard product is the rank-4096 input."""
+    return gaussian_sum(n, Ra, seeds[0]), gaussian_sum(n, Rb, seeds[1])
+
+
+def random_cp(n, R, seed, signed=True, dist="normal") -> CP:
+    """Unstructured random CP tensor (tests): factors N(0,1) or U[0,1), weights N(0,1)."""
+    g = np.random.default_rng(seed)
+    ns = [n] * 3 if np.isscalar(n) else list(n)
+    U = []
+    for l in range(3):
+        if dist == "normal":
+            U.append(np.asfortranarray(g.standard_normal((ns[l], R))))
+        else:
+            U.append(np.asfortranarray(g.random((ns[l], R))))
+    xi = g.standard_normal(R) if signed else g.random(R) + 0.1
+    return CP(U=U, xi=xi.astype(np.float64), meta=dict(kind="random", seed=seed))
