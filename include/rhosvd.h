@@ -1,0 +1,145 @@
+/*
+ * rhosvd.h -- C ABI of the GB300 (sm_103a) RHOSVD library.
+ *
+ * Reduced HOSVD canonical-to-Tucker (C2T) rank reduction of a d = 3 canonical tensor
+ *   A = sum_{nu=1}^R xi_nu u_nu^(1) (x) u_nu^(2) (x) u_nu^(3)          (Sec. 2.1, eq. can_A3)
+ * into the orthogonal Tucker tensor
+ *   A0 = beta x_1 Z^(1) x_2 Z^(2) x_3 Z^(3),                            (Def. 2.2, eq. RHOSVD)
+ * where Z^(l) (n_l x r_l) spans the dominant left singular subspace of the normalised side
+ * matrix U^(l) (eq. SVD_Ul, eq. svdr) and the core is the Khatri-Rao contraction
+ *   beta(i,j,m) = sum_nu xi_nu V^(1)(i,nu) V^(2)(j,nu) V^(3)(m,nu),  V^(l) = Z^(l)T U^(l)
+ * (Prop. 2.2).  Plus the canonical Hadamard product and sum whose rank growth RHOSVD cuts
+ * back (Sec. 3 eq. rho_ten; Lemma 4.2; Sec. 4.3).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named in a struct are DEVICE pointers unless stated otherwise; the caller
+ *     owns every buffer (inputs, outputs, workspace).  Inputs are never written.
+ *   - Matrices are column-major; U^(l) is n_l x R with leading dimension ld_l >= n_l.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *     Host-side argument errors are returned immediately; results and device-side
+ *     status land in `rhosvd_info` (device memory) and are valid after a stream sync.
+ *   - The library never aborts, never throws, never prints and never allocates memory in
+ *     rhosvd_c2t / rhosvd_cp_hadamard / rhosvd_cp_sum.
+ *   - Return value: RHOSVD_OK or a negative RHOSVD_ERR_* code.
+ */
+#ifndef RHOSVD_H
+#define RHOSVD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RHOSVD_OK 0
+#define RHOSVD_ERR_INVALID_ARG (-1)     /* bad sizes, NULL pointers, unsupported options    */
+#define RHOSVD_ERR_RANK_OVERFLOW (-2)   /* device: some r_l > r_max (needed rank in info)   */
+#define RHOSVD_ERR_NOT_CONVERGED (-3)   /* device: a small factorisation broke down          */
+#define RHOSVD_ERR_NONFINITE (-4)       /* device: Inf/NaN in factors or weights             */
+#define RHOSVD_ERR_SKETCH (-5)          /* device: sketch residual alone exceeds eps         */
+#define RHOSVD_ERR_CUDA (-6)            /* a CUDA launch/runtime call failed                 */
+#define RHOSVD_ERR_WORKSPACE (-7)       /* workspace NULL or smaller than required          */
+
+#define RHOSVD_PLAIN_FP64 0             /* every step in FP64 on the CUDA cores              */
+
+#define RHOSVD_K_MAX 256                /* largest subspace width k handled on the device    */
+
+/* A d = 3 canonical tensor (Sec. 2.1, eq. can_A3).  Factor columns need not be
+ * normalised: the library normalises them and folds the norms into the weights. */
+typedef struct rhosvd_cp {
+    int n[3];               /* mode sizes n_l >= 1                                        */
+    int R;                  /* canonical rank R >= 0                                      */
+    const double* U[3];     /* U^(l): n_l x R, column-major, leading dimension ld[l]      */
+    int ld[3];              /* ld[l] >= n[l]                                              */
+    const double* xi;       /* weights xi_nu, length R (may be signed)                    */
+} rhosvd_cp;
+
+typedef struct rhosvd_opts {
+    double eps;             /* relative Frobenius threshold per mode: r_l is the smallest r
+                               with sum_{k>r} sigma_{l,k}^2 <= eps^2 sum_k sigma_{l,k}^2
+                               (the epsilon-threshold of Thm. 2.3)                        */
+    int ranks[3];           /* > 0: fixed r_l = min(ranks[l], rank bound); 0: use eps     */
+    int r_max;              /* capacity of the outputs; 1 <= r_max <= RHOSVD_K_MAX        */
+    int oversample;         /* sketch columns beyond r_max (k = r_max + oversample)       */
+    int precision;          /* RHOSVD_PLAIN_FP64                                          */
+    unsigned long long seed;/* seed of the counter-based sketch generator                 */
+} rhosvd_opts;
+
+/* Device-written result record (one per call).  Valid after the stream is synchronised. */
+typedef struct rhosvd_info {
+    int status;             /* RHOSVD_OK or a device-side RHOSVD_ERR_* code              */
+    int r[3];               /* Tucker ranks r_l actually stored                           */
+    int r_needed[3];        /* rank the eps rule asked for (== r unless RANK_OVERFLOW)     */
+    int k[3];               /* width of the orthonormal basis Q^(l) (subspace searched)   */
+    int kept;               /* canonical terms kept after dropping zero terms             */
+    int direct[3];          /* 1 if mode l used the exact n_l x n_l Gram (no sketch)       */
+    double xi_norm;         /* ||xi'|| of the normalised weights (Thm. 2.3)              */
+    double total[3];        /* ||U^(l) normalised||_F^2                                   */
+    double resid[3];        /* energy of U^(l) outside span(Q^(l)) (sketch residual)      */
+    double tail[3];         /* (sum_{k>r_l} sigma_{l,k}^2)^{1/2}, incl. the residual      */
+} rhosvd_info;
+
+/* Outputs of rhosvd_c2t (all device memory, caller-allocated). */
+typedef struct rhosvd_tucker {
+    double* Z[3];           /* Z^(l): n_l x r_max, ld n_l; columns >= r_l are zero         */
+    double* beta;           /* capacity r_max^3; the r1 x r2 x r3 core packed densely,
+                               beta[i + r1 (j + r2 m)]                                    */
+    double* sigma[3];       /* capacity RHOSVD_K_MAX each: sigma_{l,1..k_l}, descending,
+                               zero beyond k_l                                            */
+    double* V[3];           /* optional (NULL = not returned): r_max x R, ld r_max; rows
+                               < r_l hold V^(l) = Z^(l)T U^(l)_normalised = D_{l,0} V_0^T,
+                               the mixed Tucker-canonical core factors (Prop. 2.2)        */
+    double* xi_out;         /* optional (NULL = not returned): the R normalised weights   */
+    rhosvd_info* info;      /* required                                                  */
+} rhosvd_tucker;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int rhosvd_version(void);
+
+/* Message for a status code (static storage). */
+const char* rhosvd_strerror(int code);
+
+/* Bytes of device workspace rhosvd_c2t needs for this tensor and these options, or 0 if
+ * the arguments are invalid.  Depends only on sizes and options. */
+size_t rhosvd_c2t_workspace_size(const rhosvd_cp* cp, const rhosvd_opts* opts);
+
+/* Width of the subspace searched in mode l (k_l before rank revealing); -1 on bad args. */
+int rhosvd_subspace_width(const rhosvd_cp* cp, const rhosvd_opts* opts, int mode);
+
+/*
+ * RHOSVD canonical-to-Tucker transform (Def. 2.2, Prop. 2.2, Thm. 2.3).
+ * Steps, all on the device: normalise the canonical vectors (Sec. 2.1); per mode find an
+ * orthonormal basis Q of the range of U^(l) (the exact identity when n_l <= k, else a
+ * randomised range sketch U^(l) Omega with Rademacher Omega); project B = Q^T U^(l);
+ * eigen-decompose B B^T to get the singular values and left singular vectors inside
+ * span(Q) (eq. SVD_Ul restricted to Q); choose r_l by the eps rule; write
+ * Z^(l) = Q W_r, V^(l) = W_r^T B and the Khatri-Rao core beta.
+ * workspace: device memory of at least rhosvd_c2t_workspace_size() bytes, 256-byte aligned.
+ * Errors: RHOSVD_ERR_INVALID_ARG, RHOSVD_ERR_WORKSPACE, RHOSVD_ERR_CUDA (returned);
+ *         RANK_OVERFLOW, NOT_CONVERGED, NONFINITE, SKETCH (in info->status).
+ */
+int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rhosvd_tucker* out,
+               void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Hadamard (entrywise) product of two canonical tensors with equal mode sizes
+ * (Sec. 3 eq. rho_ten; Lemma 4.2): term nu = i + Ra * j of the result has columns
+ * u^(l)_nu = a^(l)_i .* b^(l)_j and weight xa_i * xb_j; rank Ra * Rb.
+ * U_out[l]: n_l x (Ra Rb), leading dimension ld_out[l] >= n_l; xi_out: Ra Rb values.
+ * Output buffers must not overlap the inputs.
+ */
+int rhosvd_cp_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, double* const U_out[3],
+                       const int ld_out[3], double* xi_out, void* stream);
+
+/*
+ * Linear combination alpha A + beta B as one canonical tensor of rank Ra + Rb (Sec. 4.3:
+ * sums are formed by grouping the terms): columns [A | B], weights [alpha xa | beta xb].
+ */
+int rhosvd_cp_sum(double alpha, const rhosvd_cp* a, double beta, const rhosvd_cp* b,
+                  double* const U_out[3], const int ld_out[3], double* xi_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RHOSVD_H */

@@ -98,7 +98,7 @@ def householder_r(A):
     return Rf
 
 
-def jacobi_left(A, max_sweeps=60):
+def jacobi_left(A, max_sweeps=100):
     """One-sided Jacobi: (sigma descending, Z) with A = Z diag(sigma) V^T."""
     A = _f64(A).copy(order="F")
     m, n = A.shape
@@ -110,7 +110,7 @@ def jacobi_left(A, max_sweeps=60):
     return sig, Z
 
 
-def side_svd(Un, max_sweeps=60):
+def side_svd(Un, max_sweeps=100):
     """(sigma, Z) of a side matrix (n x R), q = min(n, R) values/vectors."""
     Un = _f64(Un)
     n, R = Un.shape
@@ -143,7 +143,7 @@ def normalize(U, xi):
     return Un, xin, norms.reshape(3, R), keep
 
 
-def c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=None, max_sweeps=60):
+def c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=None, max_sweeps=100):
     """The whole RHOSVD.  Returns a dict with Z (list of n_l x r_l), beta (r1,r2,r3 array,
     index [i,j,m]), sigma (list), V (list of r_l x R), xin, ranks, kept, xi_norm, tails."""
     U = [_f64(u) for u in U]

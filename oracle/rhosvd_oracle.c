@@ -136,13 +136,19 @@ int orc_householder_r(int m, int n, double* A, int lda, double* Rout)
  * sigma_i = ||a_i|| and z_i = a_i / sigma_i.  For the pair (p,q) with
  * alpha = a_p.a_p, beta = a_q.a_q, gamma = a_p.a_q the rotation angle zeroes gamma:
  * zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
- * c = 1/sqrt(1+t^2), s = c t.  A pair counts as orthogonal when |gamma| <= tol sqrt(alpha beta).
+ * c = 1/sqrt(1+t^2), s = c t.  A pair counts as orthogonal when |gamma| <= tol sqrt(alpha beta),
+ * tol = m u.  A column whose norm is <= m u ||A||_F is numerically zero (its singular value is
+ * below what FP64 resolves in A) and is not rotated; without this rule rotations among such
+ * noise-level columns never settle.
  * Output: sigma (n values, descending) and Z (m x n, column i <-> sigma_i; zero column
  * for sigma_i = 0).  A is overwritten.  Returns sweeps used, or ORC_ERR_NOTCONV.
  */
 int orc_jacobi_left(int m, int n, double* A, double* sigma, double* Z, int max_sweeps)
 {
     const double tol = (double)m * DBL_EPSILON;
+    double fro2 = 0.0;
+    for (size_t e = 0; e < (size_t)m * n; ++e) fro2 += A[e] * A[e];
+    const double negligible = tol * tol * fro2;
     int sweep = 0, converged = 0;
     for (sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
         long rotations = 0;
@@ -156,7 +162,7 @@ int orc_jacobi_left(int m, int n, double* A, double* sigma, double* Z, int max_s
                     beta += aq[i] * aq[i];
                     gamma += ap[i] * aq[i];
                 }
-                if (alpha == 0.0 || beta == 0.0 || gamma == 0.0) continue;
+                if (alpha <= negligible || beta <= negligible || gamma == 0.0) continue;
                 if (fabs(gamma) <= tol * sqrt(alpha) * sqrt(beta)) continue;
                 double zeta = (beta - alpha) / (2.0 * gamma);
                 double t;

@@ -1,0 +1,301 @@
+"""Python binding of the RHOSVD CUDA library (``include/rhosvd.h``).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.  PyTorch
+provides device memory and the current stream.  The functions carry the C names:
+
+    rhosvd_version, rhosvd_strerror, rhosvd_c2t_workspace_size, rhosvd_subspace_width,
+    rhosvd_c2t, rhosvd_cp_hadamard, rhosvd_cp_sum
+
+Factor matrices are column-major: a factor U^(l) is a float64 CUDA tensor of shape
+(n_l, R) with stride (1, ld), e.g. ``torch.empty(R, n).t()``.  If the library cannot be
+loaded (not built, no CUDA), every entry point raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+RHOSVD_OK = 0
+RHOSVD_ERR_INVALID_ARG = -1
+RHOSVD_ERR_RANK_OVERFLOW = -2
+RHOSVD_ERR_NOT_CONVERGED = -3
+RHOSVD_ERR_NONFINITE = -4
+RHOSVD_ERR_SKETCH = -5
+RHOSVD_ERR_CUDA = -6
+RHOSVD_ERR_WORKSPACE = -7
+RHOSVD_PLAIN_FP64 = 0
+RHOSVD_K_MAX = 256
+
+_c = ctypes
+
+
+class rhosvd_cp(_c.Structure):
+    _fields_ = [("n", _c.c_int * 3), ("R", _c.c_int), ("U", _c.c_void_p * 3), ("ld", _c.c_int * 3),
+                ("xi", _c.c_void_p)]
+
+
+class rhosvd_opts(_c.Structure):
+    _fields_ = [("eps", _c.c_double), ("ranks", _c.c_int * 3), ("r_max", _c.c_int), ("oversample", _c.c_int),
+                ("precision", _c.c_int), ("seed", _c.c_ulonglong)]
+
+
+class rhosvd_info(_c.Structure):
+    _fields_ = [("status", _c.c_int), ("r", _c.c_int * 3), ("r_needed", _c.c_int * 3), ("k", _c.c_int * 3),
+                ("kept", _c.c_int), ("direct", _c.c_int * 3), ("xi_norm", _c.c_double),
+                ("total", _c.c_double * 3), ("resid", _c.c_double * 3), ("tail", _c.c_double * 3)]
+
+
+class rhosvd_tucker(_c.Structure):
+    _fields_ = [("Z", _c.c_void_p * 3), ("beta", _c.c_void_p), ("sigma", _c.c_void_p * 3), ("V", _c.c_void_p * 3),
+                ("xi_out", _c.c_void_p), ("info", _c.c_void_p)]
+
+
+class RhosvdError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__(f"{where}: {rhosvd_strerror(code)} ({code})")
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "_build", "librhosvd.so")
+
+
+def load(build_if_missing: bool = False):
+    """Load librhosvd.so (raises if it is missing or cannot be loaded)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"RHOSVD CUDA library not built ({path}); run __graft_entry__.build()")
+            from . import build_lib
+            build_lib.build()
+        L = _c.CDLL(path)
+        L.rhosvd_version.restype = _c.c_int
+        L.rhosvd_strerror.restype = _c.c_char_p
+        L.rhosvd_strerror.argtypes = [_c.c_int]
+        L.rhosvd_c2t_workspace_size.restype = _c.c_size_t
+        L.rhosvd_c2t_workspace_size.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts)]
+        L.rhosvd_subspace_width.restype = _c.c_int
+        L.rhosvd_subspace_width.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts), _c.c_int]
+        L.rhosvd_c2t.restype = _c.c_int
+        L.rhosvd_c2t.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts), _c.POINTER(rhosvd_tucker),
+                                 _c.c_void_p, _c.c_size_t, _c.c_void_p]
+        L.rhosvd_cp_hadamard.restype = _c.c_int
+        L.rhosvd_cp_hadamard.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_cp), _c.c_void_p * 3,
+                                         _c.c_int * 3, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_cp_sum.restype = _c.c_int
+        L.rhosvd_cp_sum.argtypes = [_c.c_double, _c.POINTER(rhosvd_cp), _c.c_double, _c.POINTER(rhosvd_cp),
+                                    _c.c_void_p * 3, _c.c_int * 3, _c.c_void_p, _c.c_void_p]
+        _lib = L
+        return L
+
+
+# ------------------------------------------------------------------ marshalling helpers
+
+def _torch():
+    import torch
+    return torch
+
+
+def _check_factor(U, l):
+    torch = _torch()
+    if not isinstance(U, torch.Tensor) or U.dtype != torch.float64 or U.dim() != 2 or not U.is_cuda:
+        raise TypeError(f"factor {l} must be a 2-D float64 CUDA tensor")
+    n, R = U.shape
+    if R > 1 and n > 0 and U.stride(0) != 1:
+        raise ValueError(f"factor {l} must be column-major (stride (1, ld)); got stride {tuple(U.stride())}")
+    ld = U.stride(1) if R > 1 else max(n, 1)
+    return n, R, max(ld, n)
+
+
+def make_cp(U, xi) -> rhosvd_cp:
+    cp = rhosvd_cp()
+    R = None
+    for l in range(3):
+        n, Rl, ld = _check_factor(U[l], l)
+        if R is None:
+            R = Rl
+        elif Rl != R:
+            raise ValueError("factors disagree on the rank R")
+        cp.n[l] = n
+        cp.ld[l] = ld
+        cp.U[l] = U[l].data_ptr()
+    if xi.dtype != _torch().float64 or not xi.is_cuda or xi.numel() != R or not xi.is_contiguous():
+        raise ValueError("xi must be a contiguous float64 CUDA tensor of length R")
+    cp.R = R
+    cp.xi = xi.data_ptr()
+    return cp
+
+
+def make_opts(eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0,
+              precision=RHOSVD_PLAIN_FP64) -> rhosvd_opts:
+    o = rhosvd_opts()
+    o.eps = float(eps)
+    for l in range(3):
+        o.ranks[l] = int(ranks[l])
+    o.r_max = int(r_max)
+    o.oversample = int(oversample)
+    o.precision = int(precision)
+    o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    return o
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _c.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------ C entry points
+
+def rhosvd_version() -> int:
+    return int(load().rhosvd_version())
+
+
+def rhosvd_strerror(code: int) -> str:
+    try:
+        return load().rhosvd_strerror(int(code)).decode()
+    except Exception:                                  # library unavailable
+        return f"status {code}"
+
+
+def rhosvd_c2t_workspace_size(cp: rhosvd_cp, opts: rhosvd_opts) -> int:
+    return int(load().rhosvd_c2t_workspace_size(_c.byref(cp), _c.byref(opts)))
+
+
+def rhosvd_subspace_width(cp: rhosvd_cp, opts: rhosvd_opts, mode: int) -> int:
+    return int(load().rhosvd_subspace_width(_c.byref(cp), _c.byref(opts), int(mode)))
+
+
+@dataclass
+class TuckerResult:
+    """Device outputs of one rhosvd_c2t call (see rhosvd_tucker in include/rhosvd.h)."""
+    Z: list
+    beta: object
+    sigma: object
+    V: list
+    xi_out: object
+    info_buf: object
+    r_max: int
+
+    def info(self) -> rhosvd_info:
+        """Synchronise the current stream and read the device-written info record."""
+        torch = _torch()
+        torch.cuda.current_stream().synchronize()
+        raw = bytes(self.info_buf.cpu().numpy().tobytes())
+        return rhosvd_info.from_buffer_copy(raw)
+
+    def tucker(self):
+        """(ranks, beta (r1,r2,r3) float64 CUDA view, [Z_l (n_l, r_l)])."""
+        inf = self.info()
+        r = [inf.r[l] for l in range(3)]
+        cnt = r[0] * r[1] * r[2]
+        beta = self.beta[:cnt].reshape(r[2], r[1], r[0]).permute(2, 1, 0)
+        Z = [self.Z[l][:, : r[l]] for l in range(3)]
+        return r, beta, Z
+
+
+def alloc_tucker(n, R, r_max, device="cuda", with_V=False, with_xi=False) -> TuckerResult:
+    torch = _torch()
+    Z = [torch.empty(r_max, n[l], dtype=torch.float64, device=device).t() for l in range(3)]
+    beta = torch.empty(r_max ** 3, dtype=torch.float64, device=device)
+    sigma = torch.empty(3, RHOSVD_K_MAX, dtype=torch.float64, device=device)
+    V = [torch.empty(max(R, 1), r_max, dtype=torch.float64, device=device).t() for _ in range(3)] if with_V else None
+    xi_out = torch.empty(max(R, 1), dtype=torch.float64, device=device) if with_xi else None
+    info = torch.zeros(_c.sizeof(rhosvd_info), dtype=torch.uint8, device=device)
+    return TuckerResult(Z=Z, beta=beta, sigma=sigma, V=V, xi_out=xi_out, info_buf=info, r_max=r_max)
+
+
+def tucker_struct(res: TuckerResult) -> rhosvd_tucker:
+    t = rhosvd_tucker()
+    for l in range(3):
+        t.Z[l] = res.Z[l].data_ptr()
+        t.sigma[l] = res.sigma[l].data_ptr()
+        t.V[l] = res.V[l].data_ptr() if res.V is not None else None
+    t.beta = res.beta.data_ptr()
+    t.xi_out = res.xi_out.data_ptr() if res.xi_out is not None else None
+    t.info = res.info_buf.data_ptr()
+    return t
+
+
+def rhosvd_c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0, out=None,
+               workspace=None, stream=None, with_V=False, with_xi=False) -> TuckerResult:
+    """RHOSVD canonical-to-Tucker transform of the CP tensor (U[0], U[1], U[2], xi)."""
+    torch = _torch()
+    L = load()
+    cp = make_cp(U, xi)
+    opts = make_opts(eps, ranks, r_max, oversample, seed)
+    need = int(L.rhosvd_c2t_workspace_size(_c.byref(cp), _c.byref(opts)))
+    if need == 0:
+        raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_c2t_workspace_size")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=U[0].device)
+    if out is None:
+        out = alloc_tucker([cp.n[l] for l in range(3)], cp.R, r_max, U[0].device, with_V, with_xi)
+    t = tucker_struct(out)
+    rc = L.rhosvd_c2t(_c.byref(cp), _c.byref(opts), _c.byref(t), _c.c_void_p(workspace.data_ptr()),
+                      _c.c_size_t(workspace.numel()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_c2t")
+    return out
+
+
+def _out_arrays(U_out):
+    ptrs = (_c.c_void_p * 3)(*[u.data_ptr() for u in U_out])
+    lds = (_c.c_int * 3)(*[max(u.stride(1) if u.shape[1] > 1 else u.shape[0], u.shape[0]) for u in U_out])
+    return ptrs, lds
+
+
+def rhosvd_cp_hadamard(Ua, xa, Ub, xb, U_out=None, xi_out=None, stream=None):
+    """Hadamard product of two CP tensors; returns (U_out list, xi_out)."""
+    torch = _torch()
+    L = load()
+    a, b = make_cp(Ua, xa), make_cp(Ub, xb)
+    R = a.R * b.R
+    dev = Ua[0].device
+    if U_out is None:
+        U_out = [torch.empty(R, a.n[l], dtype=torch.float64, device=dev).t() for l in range(3)]
+    if xi_out is None:
+        xi_out = torch.empty(R, dtype=torch.float64, device=dev)
+    ptrs, lds = _out_arrays(U_out)
+    rc = L.rhosvd_cp_hadamard(_c.byref(a), _c.byref(b), ptrs, lds, _c.c_void_p(xi_out.data_ptr()),
+                              _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_cp_hadamard")
+    return U_out, xi_out
+
+
+def rhosvd_cp_sum(alpha, Ua, xa, beta, Ub, xb, U_out=None, xi_out=None, stream=None):
+    """alpha A + beta B as one CP tensor; returns (U_out list, xi_out)."""
+    torch = _torch()
+    L = load()
+    a, b = make_cp(Ua, xa), make_cp(Ub, xb)
+    R = a.R + b.R
+    dev = Ua[0].device
+    if U_out is None:
+        U_out = [torch.empty(R, a.n[l], dtype=torch.float64, device=dev).t() for l in range(3)]
+    if xi_out is None:
+        xi_out = torch.empty(R, dtype=torch.float64, device=dev)
+    ptrs, lds = _out_arrays(U_out)
+    rc = L.rhosvd_cp_sum(_c.c_double(alpha), _c.byref(a), _c.c_double(beta), _c.byref(b), ptrs, lds,
+                         _c.c_void_p(xi_out.data_ptr()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_cp_sum")
+    return U_out, xi_out
+
+
+def to_device_factor(U_np, device="cuda"):
+    """Column-major float64 CUDA copy of a numpy (n, R) array."""
+    torch = _torch()
+    import numpy as np
+    a = np.asarray(U_np, dtype=np.float64)
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to(device).t()

@@ -1,0 +1,484 @@
+// api.cu -- C ABI of the RHOSVD library: argument checks, workspace plan and the stream-
+// ordered launch sequence of the canonical-to-Tucker transform (Def. 2.2, Prop. 2.2).
+// Every rank decision is taken on the device; the host never synchronises inside a call.
+#include "internal.cuh"
+#include <string.h>
+
+using namespace rh;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+// Workspace plan: sizes and byte offsets, a pure function of sizes and options.
+struct Plan {
+    int n[3], R, rmax, kin[3], direct[3];
+    int KW;               // max k_l over modes
+    int NQ;               // max n_l over modes
+    int ks_sketch, ks_gram, ks_bbt;
+    size_t o_state, o_norms, o_inv, o_xin, o_bufA, o_bufB, o_G, o_L, o_perm, o_B, o_vec, o_W, o_V, o_part;
+    size_t total;
+};
+
+int choose_split(int tiles, int K)
+{
+    int ks = (2 * 148 + tiles - 1) / (tiles > 0 ? tiles : 1);
+    int kmax = (K + 255) / 256;
+    if (ks > kmax) ks = kmax;
+    if (ks > 32) ks = 32;
+    if (ks < 1) ks = 1;
+    return ks;
+}
+
+int tiles_of(int M, int N) { return ((M + 63) / 64) * ((N + 63) / 64); }
+
+int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
+{
+    if (!cp || !o) return RHOSVD_ERR_INVALID_ARG;
+    if (cp->R < 0) return RHOSVD_ERR_INVALID_ARG;
+    if (o->r_max < 1 || o->r_max > KMAX || o->oversample < 0) return RHOSVD_ERR_INVALID_ARG;
+    if (o->precision != RHOSVD_PLAIN_FP64) return RHOSVD_ERR_INVALID_ARG;
+    if (!(o->eps >= 0.0)) return RHOSVD_ERR_INVALID_ARG;
+    memset(p, 0, sizeof(*p));
+    p->R = cp->R;
+    p->rmax = o->r_max;
+    int kcap = o->r_max + o->oversample;
+    if (kcap > KMAX) kcap = KMAX;
+    p->KW = 1;
+    p->NQ = 1;
+    for (int l = 0; l < 3; ++l) {
+        if (cp->n[l] < 1 || cp->ld[l] < cp->n[l] || o->ranks[l] < 0) return RHOSVD_ERR_INVALID_ARG;
+        p->n[l] = cp->n[l];
+        if (cp->n[l] <= kcap) {
+            p->direct[l] = 1;
+            p->kin[l] = cp->n[l];
+        } else {
+            p->direct[l] = 0;
+            int k = kcap;
+            if (cp->R > 0 && k > cp->R) k = cp->R;
+            if (k < 1) k = 1;
+            p->kin[l] = k;
+        }
+        if (p->kin[l] > p->KW) p->KW = p->kin[l];
+        if (cp->n[l] > p->NQ) p->NQ = cp->n[l];
+    }
+    const int R = cp->R > 0 ? cp->R : 1;
+    const long long NK = (long long)p->NQ * p->KW, KK = (long long)p->KW * p->KW;
+    // split-K factors of the launches that use the partial buffer
+    int t_sk = 0, t_g = 0;
+    for (int l = 0; l < 3; ++l) {
+        t_sk += tiles_of(p->n[l], p->kin[l]);
+        t_g += tiles_of(p->kin[l], p->kin[l]);
+    }
+    p->ks_sketch = choose_split(t_sk, R);
+    p->ks_gram = choose_split(t_g, p->NQ);
+    p->ks_bbt = choose_split(t_g, R);
+    long long part = 0;
+    part = (long long)p->ks_sketch * 3 * NK;
+    long long pg = (long long)p->ks_gram * 3 * KK, pb = (long long)p->ks_bbt * 3 * KK;
+    if (pg > part) part = pg;
+    if (pb > part) part = pb;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o2 = off; off += up(bytes); return o2; };
+    p->o_state = take(sizeof(DevState));
+    p->o_norms = take(sizeof(double) * 3 * R);
+    p->o_inv = take(sizeof(double) * 3 * R);
+    p->o_xin = take(sizeof(double) * R);
+    p->o_bufA = take(sizeof(double) * 3 * NK);
+    p->o_bufB = take(sizeof(double) * 3 * NK);
+    p->o_G = take(sizeof(double) * 3 * KK);
+    p->o_L = take(sizeof(double) * 3 * KK);
+    p->o_perm = take(sizeof(int) * 3 * p->KW);
+    p->o_B = take(sizeof(double) * 3 * (size_t)p->KW * R);
+    p->o_vec = take(sizeof(double) * 6 * 3 * p->KW);
+    p->o_W = take(sizeof(double) * 3 * (size_t)p->KW * p->rmax);
+    p->o_V = take(sizeof(double) * 3 * (size_t)p->rmax * R);
+    p->o_part = take(sizeof(double) * (size_t)part);
+    p->total = off;
+    return RHOSVD_OK;
+}
+
+GemmProblem blank_problem()
+{
+    GemmProblem g;
+    memset(&g, 0, sizeof(g));
+    return g;
+}
+
+}  // namespace
+
+extern "C" int rhosvd_version(void) { return 100; }
+
+extern "C" const char* rhosvd_strerror(int code)
+{
+    switch (code) {
+    case RHOSVD_OK: return "success";
+    case RHOSVD_ERR_INVALID_ARG: return "invalid argument";
+    case RHOSVD_ERR_RANK_OVERFLOW: return "a Tucker rank exceeds r_max (needed rank in info->r_needed)";
+    case RHOSVD_ERR_NOT_CONVERGED: return "a small factorisation broke down";
+    case RHOSVD_ERR_NONFINITE: return "non-finite value in the factors or weights";
+    case RHOSVD_ERR_SKETCH: return "the range sketch missed more energy than eps allows (raise oversample or r_max)";
+    case RHOSVD_ERR_CUDA: return "CUDA runtime or launch error";
+    case RHOSVD_ERR_WORKSPACE: return "workspace missing or too small";
+    default: return "unknown status";
+    }
+}
+
+extern "C" size_t rhosvd_c2t_workspace_size(const rhosvd_cp* cp, const rhosvd_opts* opts)
+{
+    Plan p;
+    if (make_plan(cp, opts, &p) != RHOSVD_OK) return 0;
+    return p.total;
+}
+
+extern "C" int rhosvd_subspace_width(const rhosvd_cp* cp, const rhosvd_opts* opts, int mode)
+{
+    Plan p;
+    if (mode < 0 || mode > 2 || make_plan(cp, opts, &p) != RHOSVD_OK) return -1;
+    return p.kin[mode];
+}
+
+extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rhosvd_tucker* out,
+                          void* workspace, size_t workspace_bytes, void* stream)
+{
+    Plan p;
+    int rc = make_plan(cp, opts, &p);
+    if (rc) return rc;
+    if (!out || !out->info || !out->beta) return RHOSVD_ERR_INVALID_ARG;
+    for (int l = 0; l < 3; ++l) {
+        if (!out->Z[l] || !out->sigma[l]) return RHOSVD_ERR_INVALID_ARG;
+        if (cp->R > 0 && !cp->U[l]) return RHOSVD_ERR_INVALID_ARG;
+    }
+    if (cp->R > 0 && !cp->xi) return RHOSVD_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < p.total || ((uintptr_t)workspace % ALIGN) != 0)
+        return RHOSVD_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    DevState* S = (DevState*)(ws + p.o_state);
+    double* norms = (double*)(ws + p.o_norms);
+    double* inv = (double*)(ws + p.o_inv);
+    double* xin = (double*)(ws + p.o_xin);
+    double* bufA = (double*)(ws + p.o_bufA);
+    double* bufB = (double*)(ws + p.o_bufB);
+    double* G = (double*)(ws + p.o_G);
+    double* L = (double*)(ws + p.o_L);
+    int* perm = (int*)(ws + p.o_perm);
+    double* Bm = (double*)(ws + p.o_B);
+    double* vec = (double*)(ws + p.o_vec);
+    double* W = (double*)(ws + p.o_W);
+    double* Vw = (double*)(ws + p.o_V);
+    double* part = (double*)(ws + p.o_part);
+    const int R = cp->R, KW = p.KW, rmax = p.rmax;
+    const long long NK = (long long)p.NQ * KW, KK = (long long)KW * KW;
+    const int vs = KW;
+    double* vd = vec;
+    double* ve = vec + 3 * vs;
+    double* vtau = vec + 6 * vs;
+    double* vD = vec + 9 * vs;
+    double* vL = vec + 12 * vs;
+    double* vmu = vec + 15 * vs;
+    double* V[3];
+    for (int l = 0; l < 3; ++l) V[l] = out->V[l] ? out->V[l] : Vw + (size_t)l * rmax * (R > 0 ? R : 1);
+
+    // ---- reset outputs and state
+    if (cudaMemsetAsync(out->info, 0, sizeof(rhosvd_info), st) != cudaSuccess) return RHOSVD_ERR_CUDA;
+    if (cudaMemsetAsync(S, 0, sizeof(DevState), st) != cudaSuccess) return RHOSVD_ERR_CUDA;
+    for (int l = 0; l < 3; ++l) {
+        if (cudaMemsetAsync(out->Z[l], 0, sizeof(double) * (size_t)p.n[l] * rmax, st) != cudaSuccess)
+            return RHOSVD_ERR_CUDA;
+        if (cudaMemsetAsync(out->sigma[l], 0, sizeof(double) * KMAX, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
+    }
+    if ((rc = launch_init_state(S, p.kin[0], p.kin[1], p.kin[2], p.direct[0] ? p.n[0] : 0,
+                                p.direct[1] ? p.n[1] : 0, p.direct[2] ? p.n[2] : 0, st)))
+        return rc;
+
+    // ---- a1: column norms, normalised weights (Sec. 2.1)
+    NormArgs na;
+    for (int l = 0; l < 3; ++l) { na.U[l] = cp->U[l]; na.ld[l] = cp->ld[l]; na.n[l] = p.n[l]; }
+    na.R = R;
+    na.norms = norms;
+    if ((rc = launch_colnorms(na, st))) return rc;
+    if ((rc = launch_terms(norms, cp->xi, R, inv, xin, out->xi_out, out->info, S->total, st))) return rc;
+
+    ModeMap all = {{0, 1, 2}};
+    ModeMap sk;
+    int nsk = 0;
+    for (int l = 0; l < 3; ++l)
+        if (!p.direct[l]) sk.m[nsk++] = l;
+    double* Qfin[3];
+    int ldq[3];
+    for (int l = 0; l < 3; ++l) {
+        ldq[l] = p.n[l];
+        if (p.direct[l]) {
+            Qfin[l] = bufA + l * NK;
+            if ((rc = launch_identity(Qfin[l], p.n[l], p.n[l], st))) return rc;
+        } else {
+            Qfin[l] = bufB + l * NK;
+        }
+    }
+
+    if (nsk > 0 && R > 0) {
+        // ---- a2: range sketch Y = U diag(1/||u||) Omega (Rademacher), Y in bufA
+        GemmBatch gb;
+        memset(&gb, 0, sizeof(gb));
+        gb.nbatch = nsk;
+        gb.ksplit = p.ks_sketch;
+        gb.bkind = B_SKETCH;
+        for (int b = 0; b < nsk; ++b) {
+            const int l = sk.m[b];
+            GemmProblem g = blank_problem();
+            g.A = Mat{cp->U[l], 1, cp->ld[l]};
+            g.C = bufA + l * NK;
+            g.crs = 1;
+            g.ccs = p.n[l];
+            g.M = p.n[l];
+            g.N = p.kin[l];
+            g.K = R;
+            g.bscale = inv + (size_t)l * R;
+            g.seed = opts->seed;
+            g.mode = l;
+            gb.p[b] = g;
+        }
+        if ((rc = launch_gemm_splitk(gb, part, st))) return rc;
+
+        // ---- a3: CholeskyQR with pivoting, three passes: Y -> Q1 (bufB) -> Q2 (bufA) -> Q (bufB)
+        const double tols[3] = {1e-15, 1e-11, 0.0};
+        const int pivots[3] = {1, 1, 0};
+        for (int pass = 0; pass < 3; ++pass) {
+            double* X = (pass == 1) ? bufB : bufA;
+            double* Y = (pass == 1) ? bufA : bufB;
+            GemmBatch g2;
+            memset(&g2, 0, sizeof(g2));
+            g2.nbatch = nsk;
+            g2.ksplit = p.ks_gram;
+            g2.bkind = B_PLAIN;
+            for (int b = 0; b < nsk; ++b) {
+                const int l = sk.m[b];
+                GemmProblem g = blank_problem();
+                double* Xl = X + l * NK;
+                g.A = Mat{Xl, (long long)p.n[l], 1};      // A(i,x) = X(x,i)
+                g.B = Mat{Xl, 1, (long long)p.n[l]};      // B(x,j) = X(x,j)
+                g.C = G + l * KK;
+                g.crs = 1;
+                g.ccs = KW;
+                g.M = p.kin[l];
+                g.N = p.kin[l];
+                g.K = p.n[l];
+                if (pass > 0) { g.dM = &S->m[l]; g.dN = &S->m[l]; }
+                g2.p[b] = g;
+            }
+            if ((rc = launch_gemm_splitk(g2, part, st))) return rc;
+            const int* dk = (pass == 0) ? S->kin : S->m;
+            if ((rc = launch_chol(sk, G, KK, KW, dk, L, KK, KW, perm, KW, S->m, S->piv_fail, pivots[pass],
+                                  tols[pass], nsk, st)))
+                return rc;
+            TrsmArgs ta;
+            memset(&ta, 0, sizeof(ta));
+            for (int l = 0; l < 3; ++l) {
+                ta.X[l] = X + l * NK;
+                ta.ldx[l] = p.n[l];
+                ta.Q[l] = Y + l * NK;
+                ta.ldq[l] = p.n[l];
+                ta.n[l] = p.n[l];
+            }
+            ta.L = L;
+            ta.lstride = KK;
+            ta.ldl = KW;
+            ta.perm = perm;
+            ta.pstride = KW;
+            ta.dm = S->m;
+            if ((rc = launch_trsm(sk, ta, p.NQ, nsk, st))) return rc;
+        }
+    }
+
+    if (R > 0) {
+        // ---- a4: projection B = Q^T U diag(1/||u||)  (m_l x R, ld KW)
+        GemmBatch gb;
+        memset(&gb, 0, sizeof(gb));
+        gb.nbatch = 3;
+        gb.ksplit = 1;
+        gb.bkind = B_PLAIN;
+        for (int l = 0; l < 3; ++l) {
+            GemmProblem g = blank_problem();
+            g.A = Mat{Qfin[l], (long long)ldq[l], 1};
+            g.B = Mat{cp->U[l], 1, cp->ld[l]};
+            g.C = Bm + (size_t)l * KW * R;
+            g.crs = 1;
+            g.ccs = KW;
+            g.M = p.kin[l];
+            g.dM = &S->m[l];
+            g.N = R;
+            g.K = p.n[l];
+            g.colscale = inv + (size_t)l * R;
+            gb.p[l] = g;
+        }
+        if ((rc = launch_gemm(gb, st))) return rc;
+
+        // ---- a5: M = B B^T (m_l x m_l), trace, tridiagonal form, eigenvalues
+        GemmBatch gm;
+        memset(&gm, 0, sizeof(gm));
+        gm.nbatch = 3;
+        gm.ksplit = p.ks_bbt;
+        gm.bkind = B_PLAIN;
+        for (int l = 0; l < 3; ++l) {
+            GemmProblem g = blank_problem();
+            double* Bl = Bm + (size_t)l * KW * R;
+            g.A = Mat{Bl, 1, KW};
+            g.B = Mat{Bl, KW, 1};
+            g.C = G + l * KK;
+            g.crs = 1;
+            g.ccs = KW;
+            g.M = p.kin[l];
+            g.N = p.kin[l];
+            g.K = R;
+            g.dM = &S->m[l];
+            g.dN = &S->m[l];
+            gm.p[l] = g;
+        }
+        if ((rc = launch_gemm_splitk(gm, part, st))) return rc;
+    }
+    if (R == 0 && cudaMemsetAsync(G, 0, sizeof(double) * 3 * KK, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
+    if ((rc = launch_trace(all, G, KK, KW, S->m, S->trace, 3, st))) return rc;
+    if ((rc = launch_tridiag(all, G, KK, KW, S->m, vd, ve, vtau, vs, 3, st))) return rc;
+    if ((rc = launch_eigvals(all, vd, ve, vs, S->m, vD, vL, vmu, S, 3, st))) return rc;
+
+    // ---- a6: eps-rank (Thm. 2.3), sigma, then eigenvectors of the kept eigenvalues
+    RankArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.mu = vmu;
+    ra.vstride = vs;
+    ra.dk = S->m;
+    ra.trace = S->trace;
+    ra.total = S->total;
+    ra.eps = opts->eps;
+    ra.r_max = rmax;
+    ra.info = out->info;
+    ra.st = S;
+    for (int l = 0; l < 3; ++l) {
+        ra.ranks[l] = opts->ranks[l];
+        ra.sigma[l] = out->sigma[l];
+        ra.direct[l] = p.direct[l];
+    }
+    if ((rc = launch_rank(ra, st))) return rc;
+    if ((rc = launch_eigvecs(all, vD, vL, vmu, vs, S->m, S, W, (long long)KW * rmax, KW, rmax, 3, st))) return rc;
+    if ((rc = launch_backtransform(all, G, KK, KW, vtau, vs, S->m, S, W, (long long)KW * rmax, KW, rmax, 3, st)))
+        return rc;
+
+    if (R > 0) {
+        // ---- Z = Q W_r (n_l x r_l) and V = W_r^T B (r_l x R, ld r_max)
+        GemmBatch gz;
+        memset(&gz, 0, sizeof(gz));
+        gz.nbatch = 3;
+        gz.ksplit = 1;
+        gz.bkind = B_PLAIN;
+        GemmBatch gv = gz;
+        for (int l = 0; l < 3; ++l) {
+            GemmProblem g = blank_problem();
+            double* Wl = W + (size_t)l * KW * rmax;
+            g.A = Mat{Qfin[l], 1, (long long)ldq[l]};
+            g.B = Mat{Wl, 1, KW};
+            g.C = out->Z[l];
+            g.crs = 1;
+            g.ccs = p.n[l];
+            g.M = p.n[l];
+            g.N = rmax;
+            g.dN = &S->r[l];
+            g.K = p.kin[l];
+            g.dK = &S->m[l];
+            gz.p[l] = g;
+            GemmProblem h = blank_problem();
+            h.A = Mat{Wl, KW, 1};
+            h.B = Mat{Bm + (size_t)l * KW * R, 1, KW};
+            h.C = V[l];
+            h.crs = 1;
+            h.ccs = rmax;
+            h.M = rmax;
+            h.dM = &S->r[l];
+            h.N = R;
+            h.K = p.kin[l];
+            h.dK = &S->m[l];
+            gv.p[l] = h;
+        }
+        if ((rc = launch_gemm(gz, st))) return rc;
+        if ((rc = launch_gemm(gv, st))) return rc;
+
+        // ---- a7: core beta = V1 diag(xi') (V3 (.) V2)^T (Prop. 2.2), packed r1 x r2 x r3
+        GemmBatch gc;
+        memset(&gc, 0, sizeof(gc));
+        gc.nbatch = 1;
+        gc.ksplit = 1;
+        gc.bkind = B_KR;
+        GemmProblem g = blank_problem();
+        g.A = Mat{V[0], 1, rmax};
+        g.C = out->beta;
+        g.crs = 1;
+        g.ccs = -1;           // = r1, decided on the device
+        g.M = rmax;
+        g.dM = &S->r[0];
+        g.N = rmax * rmax;
+        g.N_from_r2r3 = 1;
+        g.dNa = &S->r[1];
+        g.dNb = &S->r[2];
+        g.K = R;
+        g.V2 = V[1];
+        g.V3 = V[2];
+        g.xi = xin;
+        g.ldv = rmax;
+        gc.p[0] = g;
+        if ((rc = launch_gemm(gc, st))) return rc;
+    }
+    return RHOSVD_OK;
+}
+
+extern "C" int rhosvd_cp_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, double* const U_out[3],
+                                  const int ld_out[3], double* xi_out, void* stream)
+{
+    if (!a || !b || !U_out || !ld_out || !xi_out) return RHOSVD_ERR_INVALID_ARG;
+    if (a->R < 0 || b->R < 0) return RHOSVD_ERR_INVALID_ARG;
+    if ((long long)a->R * b->R > 0x7fffffffLL) return RHOSVD_ERR_INVALID_ARG;
+    HadArgs h;
+    for (int l = 0; l < 3; ++l) {
+        if (a->n[l] != b->n[l] || a->n[l] < 1 || a->ld[l] < a->n[l] || b->ld[l] < b->n[l] ||
+            ld_out[l] < a->n[l] || !U_out[l])
+            return RHOSVD_ERR_INVALID_ARG;
+        if ((a->R > 0 && !a->U[l]) || (b->R > 0 && !b->U[l])) return RHOSVD_ERR_INVALID_ARG;
+        h.A[l] = a->U[l]; h.lda[l] = a->ld[l];
+        h.B[l] = b->U[l]; h.ldb[l] = b->ld[l];
+        h.C[l] = U_out[l]; h.ldc[l] = ld_out[l];
+        h.n[l] = a->n[l];
+    }
+    h.Ra = a->R;
+    h.Rb = b->R;
+    h.xa = a->xi;
+    h.xb = b->xi;
+    h.xc = xi_out;
+    return launch_hadamard(h, (cudaStream_t)stream);
+}
+
+extern "C" int rhosvd_cp_sum(double alpha, const rhosvd_cp* a, double beta, const rhosvd_cp* b,
+                             double* const U_out[3], const int ld_out[3], double* xi_out, void* stream)
+{
+    if (!a || !b || !U_out || !ld_out || !xi_out) return RHOSVD_ERR_INVALID_ARG;
+    if (a->R < 0 || b->R < 0) return RHOSVD_ERR_INVALID_ARG;
+    SumArgs s;
+    for (int l = 0; l < 3; ++l) {
+        if (a->n[l] != b->n[l] || a->n[l] < 1 || a->ld[l] < a->n[l] || b->ld[l] < b->n[l] ||
+            ld_out[l] < a->n[l] || !U_out[l])
+            return RHOSVD_ERR_INVALID_ARG;
+        if ((a->R > 0 && !a->U[l]) || (b->R > 0 && !b->U[l])) return RHOSVD_ERR_INVALID_ARG;
+        s.A[l] = a->U[l]; s.lda[l] = a->ld[l];
+        s.B[l] = b->U[l]; s.ldb[l] = b->ld[l];
+        s.C[l] = U_out[l]; s.ldc[l] = ld_out[l];
+        s.n[l] = a->n[l];
+    }
+    s.Ra = a->R;
+    s.Rb = b->R;
+    s.xa = a->xi;
+    s.xb = b->xi;
+    s.xc = xi_out;
+    s.alpha = alpha;
+    s.beta = beta;
+    return launch_cpsum(s, (cudaStream_t)stream);
+}

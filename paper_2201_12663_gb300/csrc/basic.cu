@@ -1,0 +1,210 @@
+// basic.cu -- streaming kernels: column norms and term normalisation (Sec. 2.1, eq. can_A3),
+// canonical Hadamard product and sum (Sec. 3 eq. rho_ten, Lemma 4.2, Sec. 4.3), identity
+// basis for the direct mode.
+#include "internal.cuh"
+
+namespace rh {
+
+// One warp per column: ||u|| = m * sqrt(sum (u_i 2^-e)^2) with m = 2^e >= max|u_i|, so the
+// scaling is exact and squares neither underflow nor overflow.  grid: (ceil(R/8), 3).
+
+__global__ void k_colnorms(NormArgs a)
+{
+    const int l = blockIdx.y;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= a.R) return;
+    const double* u = a.U[l] + (long long)warp * a.ld[l];
+    const int n = a.n[l];
+    double mx = 0.0;
+    for (int i = lane; i < n; i += 32) mx = fmax(mx, fabs(u[i]));
+    mx = warp_max(mx);
+    double nrm;
+    if (mx == 0.0) {
+        nrm = 0.0;
+    } else if (!isfinite(mx)) {
+        nrm = mx;                     // Inf (NaN propagates through fmax only if all NaN)
+    } else {
+        int ex;
+        frexp(mx, &ex);               // mx = f 2^ex, f in [0.5, 1)
+        const double sc = ldexp(1.0, -ex);
+        double s = 0.0;
+        bool bad = false;
+        for (int i = lane; i < n; i += 32) {
+            const double x = u[i];
+            if (x != x) bad = true;
+            const double t = x * sc;
+            s = fma(t, t, s);
+        }
+        s = warp_sum(s);
+        bad = __any_sync(0xffffffffu, bad);
+        nrm = bad ? NAN : ldexp(sqrt(s), ex);
+    }
+    if (lane == 0) a.norms[(long long)l * a.R + warp] = nrm;
+}
+
+// Per term: keep iff all three norms are finite and nonzero; inv_l = 1/||u_l||, weight
+// xi' = xi prod_l ||u_l|| (0 for a dropped term).  Non-finite data sets NONFINITE.
+__global__ void k_terms(const double* norms, const double* xi, int R, double* inv, double* xin,
+                        double* xi_user, rhosvd_info* info)
+{
+    for (int nu = blockIdx.x * blockDim.x + threadIdx.x; nu < R; nu += gridDim.x * blockDim.x) {
+        const double d0 = norms[nu], d1 = norms[R + nu], d2 = norms[2 * R + nu];
+        const double x = xi[nu];
+        const bool fin = isfinite(d0) && isfinite(d1) && isfinite(d2) && isfinite(x);
+        if (!fin) set_status(info, RHOSVD_ERR_NONFINITE);
+        const bool keep = fin && d0 > 0.0 && d1 > 0.0 && d2 > 0.0;
+        inv[nu] = keep ? 1.0 / d0 : 0.0;
+        inv[R + nu] = keep ? 1.0 / d1 : 0.0;
+        inv[2 * R + nu] = keep ? 1.0 / d2 : 0.0;
+        const double w = keep ? x * d0 * d1 * d2 : 0.0;
+        xin[nu] = w;
+        if (xi_user) xi_user[nu] = w;
+    }
+}
+
+// Deterministic single-block sums: kept terms, ||xi'||^2 and ||U_l normalised||_F^2.
+__global__ void k_term_totals(const double* norms, const double* inv, const double* xin, int R,
+                              double* total, rhosvd_info* info)
+{
+    __shared__ double red[32];
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, x2 = 0.0, cnt = 0.0;
+    for (int nu = threadIdx.x; nu < R; nu += blockDim.x) {
+        const double a0 = norms[nu] * inv[nu], a1 = norms[R + nu] * inv[R + nu],
+                     a2 = norms[2 * R + nu] * inv[2 * R + nu];
+        t0 += a0 * a0;
+        t1 += a1 * a1;
+        t2 += a2 * a2;
+        x2 += xin[nu] * xin[nu];
+        cnt += (inv[nu] != 0.0) ? 1.0 : 0.0;
+    }
+    t0 = block_sum(t0, red);
+    t1 = block_sum(t1, red);
+    t2 = block_sum(t2, red);
+    x2 = block_sum(x2, red);
+    cnt = block_sum(cnt, red);
+    if (threadIdx.x == 0) {
+        total[0] = t0;
+        total[1] = t1;
+        total[2] = t2;
+        info->kept = (int)cnt;
+        info->xi_norm = sqrt(x2);
+    }
+}
+
+// Identity basis Q = I_n (n x n, ld n) for the direct mode of each listed mode.
+__global__ void k_identity(double* Q, int n, int ld)
+{
+    const long long total = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        Q[(long long)j * ld + i] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+
+// ---------------------------------------------------------------- rank growth operations
+
+// C(:, i + Ra j) = A(:, i) .* B(:, j); grid (column blocks, 3 modes); one warp per column.
+__global__ void k_hadamard(HadArgs a)
+{
+    const int l = blockIdx.y;
+    const long long R = (long long)a.Ra * a.Rb;
+    const int lane = threadIdx.x & 31;
+    const int n = a.n[l];
+    for (long long nu = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; nu < R;
+         nu += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int i = (int)(nu % a.Ra), j = (int)(nu / a.Ra);
+        const double* ca = a.A[l] + (long long)i * a.lda[l];
+        const double* cb = a.B[l] + (long long)j * a.ldb[l];
+        double* cc = a.C[l] + nu * a.ldc[l];
+        for (int x = lane; x < n; x += 32) cc[x] = ca[x] * cb[x];
+        if (l == 0 && lane == 0) a.xc[nu] = a.xa[i] * a.xb[j];
+    }
+}
+
+
+__global__ void k_cpsum(SumArgs a)
+{
+    const int l = blockIdx.y;
+    const int R = a.Ra + a.Rb;
+    const int lane = threadIdx.x & 31;
+    const int n = a.n[l];
+    for (long long nu = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; nu < R;
+         nu += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const bool fromA = nu < a.Ra;
+        const double* src = fromA ? a.A[l] + nu * a.lda[l] : a.B[l] + (nu - a.Ra) * a.ldb[l];
+        double* dst = a.C[l] + nu * a.ldc[l];
+        for (int x = lane; x < n; x += 32) dst[x] = src[x];
+        if (l == 0 && lane == 0) a.xc[nu] = fromA ? a.alpha * a.xa[nu] : a.beta * a.xb[nu - a.Ra];
+    }
+}
+
+
+__global__ void k_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2)
+{
+    s->kin[0] = k0; s->kin[1] = k1; s->kin[2] = k2;
+    s->m[0] = m0; s->m[1] = m1; s->m[2] = m2;
+}
+
+int launch_colnorms(const NormArgs& a, cudaStream_t st)
+{
+    if (a.R <= 0) return 0;
+    dim3 grid((a.R + 7) / 8, 3);
+    k_colnorms<<<grid, 256, 0, st>>>(a);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_terms(const double* norms, const double* xi, int R, double* inv, double* xin, double* xi_user,
+                 rhosvd_info* info, double* total, cudaStream_t st)
+{
+    if (R > 0) {
+        k_terms<<<(R + 255) / 256, 256, 0, st>>>(norms, xi, R, inv, xin, xi_user, info);
+        RH_CHECK_LAUNCH();
+    }
+    k_term_totals<<<1, 1024, 0, st>>>(norms, inv, xin, R, total, info);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_identity(double* Q, int n, int ld, cudaStream_t st)
+{
+    k_identity<<<(n * n + 255) / 256, 256, 0, st>>>(Q, n, ld);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, cudaStream_t st)
+{
+    k_init_state<<<1, 1, 0, st>>>(s, k0, k1, k2, m0, m1, m2);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_hadamard(const HadArgs& a, cudaStream_t st)
+{
+    const long long R = (long long)a.Ra * a.Rb;
+    if (R <= 0) return 0;
+    long long blocks = (R + 7) / 8;
+    if (blocks > 4096) blocks = 4096;
+    dim3 grid((unsigned)blocks, 3);
+    k_hadamard<<<grid, 256, 0, st>>>(a);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_cpsum(const SumArgs& a, cudaStream_t st)
+{
+    const long long R = (long long)a.Ra + a.Rb;
+    if (R <= 0) return 0;
+    long long blocks = (R + 7) / 8;
+    if (blocks > 4096) blocks = 4096;
+    dim3 grid((unsigned)blocks, 3);
+    k_cpsum<<<grid, 256, 0, st>>>(a);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+}  // namespace rh

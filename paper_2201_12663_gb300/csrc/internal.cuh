@@ -1,0 +1,231 @@
+// internal.cuh -- shared definitions of the RHOSVD CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "../../include/rhosvd.h"
+
+namespace rh {
+
+constexpr int KMAX = RHOSVD_K_MAX;
+
+// Per-call device state written and read by the kernels of one rhosvd_c2t call.
+struct DevState {
+    int kin[3];         // sketch width k_l (or n_l in the direct mode)
+    int m[3];           // width of the orthonormal basis Q^(l) after rank revealing
+    int r[3];           // Tucker ranks (mirror of info->r)
+    int piv_fail[3];    // small factorisation break-down flags
+    int pad[4];
+    double shift[3];    // shift used for the LDL^T representation of the tridiagonal
+    double trace[3];    // trace(B B^T) = ||B||_F^2
+    double total[3];    // ||U^(l) normalised||_F^2
+};
+
+// Counter-based sign generator for the Rademacher sketch: bit (c & 63) of
+// splitmix64(seed ^ (mode << 56) ^ (nu * 4 + (c >> 6))).  splitmix64 is Vigna's public
+// 64-bit finaliser: add 0x9E3779B97F4A7C15, then two xor-shift-multiply rounds.
+__host__ __device__ inline uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__host__ __device__ inline double rademacher(uint64_t seed, int mode, long long nu, int c)
+{
+    uint64_t h = splitmix64(seed ^ ((uint64_t)mode << 56) ^ ((uint64_t)nu * 4ull + (uint64_t)(c >> 6)));
+    return ((h >> (c & 63)) & 1ull) ? 1.0 : -1.0;
+}
+
+__device__ inline double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ inline double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum; `red` must hold blockDim.x/32 doubles.  All threads get the result.
+__device__ inline double block_sum(double v, double* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    return t;
+}
+
+__device__ inline double block_max(double v, double* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t = fmax(t, red[w]);
+    return t;
+}
+
+// Record the first device-side error in the info record.
+__device__ inline void set_status(rhosvd_info* info, int code)
+{
+    atomicCAS(&info->status, 0, code);
+}
+
+// ---------------------------------------------------------------- generic FP64 GEMM
+// C(i,j) (M x N) = sum_k A(i,k) B(k,j), one problem per "batch" (the three modes).
+// Element (i,k) of a plain operand lives at p[i*rs + k*cs].
+struct Mat {
+    const double* p;
+    long long rs, cs;
+};
+
+enum BKind { B_PLAIN = 0, B_SKETCH = 1, B_KR = 2 };
+
+struct GemmProblem {
+    Mat A, B;                  // B unused for generated kinds
+    double* C;                 // output, element (i,j) at C[i*crs + j*ccs]
+    long long crs, ccs;
+    long long split_stride;    // offset between split-K partial outputs
+    const double* colscale;    // nullable: C(:,j) *= colscale[j] in the epilogue
+    const double* rowscale;    // nullable: C(i,:) *= rowscale[i]
+    const int* dM;             // nullable device dims (ranks decided on the device)
+    const int* dN;
+    const int* dK;
+    int M, N, K;               // host upper bounds (grid) / values when d* is NULL
+    int N_from_r2r3;           // core: N = r2 * r3 taken from dNa, dNb
+    const int* dNa;
+    const int* dNb;
+    // generated-B parameters
+    const double* bscale;      // sketch: 1/||u_nu|| per row nu of B
+    uint64_t seed;
+    int mode;
+    const double* V2;          // KR: B(nu, j + r2 m) = xi_nu V2(j,nu) V3(m,nu)
+    const double* V3;
+    const double* xi;
+    int ldv;
+};
+
+struct GemmBatch {
+    GemmProblem p[3];
+    int nbatch;
+    int ksplit;
+    int bkind;
+};
+
+
+// Maps blockIdx (0..nb-1) to the mode it works on, so a launch can cover any subset of modes.
+struct ModeMap {
+    int m[3];
+};
+
+// ---------------------------------------------------------------- kernel arguments
+struct NormArgs {
+    const double* U[3];
+    int ld[3];
+    int n[3];
+    int R;
+    double* norms;      // 3 x R
+};
+
+struct HadArgs {
+    const double* A[3];
+    int lda[3];
+    const double* B[3];
+    int ldb[3];
+    double* C[3];
+    int ldc[3];
+    int n[3];
+    int Ra, Rb;
+    const double* xa;
+    const double* xb;
+    double* xc;
+};
+
+struct SumArgs {
+    const double* A[3];
+    int lda[3];
+    const double* B[3];
+    int ldb[3];
+    double* C[3];
+    int ldc[3];
+    int n[3];
+    int Ra, Rb;
+    const double* xa;
+    const double* xb;
+    double* xc;
+    double alpha, beta;
+};
+
+struct TrsmArgs {
+    const double* X[3];
+    int ldx[3];
+    double* Q[3];
+    int ldq[3];
+    int n[3];
+    const double* L;
+    long long lstride;
+    int ldl;
+    const int* perm;
+    int pstride;
+    const int* dm;
+};
+
+struct RankArgs {
+    const double* mu;
+    int vstride;
+    const int* dk;
+    const double* trace;     // per mode
+    const double* total;     // per mode
+    double eps;
+    int ranks[3];
+    int r_max;
+    double* sigma[3];        // user outputs (KMAX each)
+    rhosvd_info* info;
+    DevState* st;
+    int direct[3];
+};
+
+// ---------------------------------------------------------------- launchers (return 0 or RHOSVD_ERR_CUDA)
+int launch_gemm(GemmBatch& gb, cudaStream_t st);
+int launch_gemm_splitk(GemmBatch gb, double* part, cudaStream_t st);
+int launch_colnorms(const NormArgs& a, cudaStream_t st);
+int launch_terms(const double* norms, const double* xi, int R, double* inv, double* xin, double* xi_user,
+                 rhosvd_info* info, double* total, cudaStream_t st);
+int launch_identity(double* Q, int n, int ld, cudaStream_t st);
+int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, cudaStream_t st);
+int launch_hadamard(const HadArgs& a, cudaStream_t st);
+int launch_cpsum(const SumArgs& a, cudaStream_t st);
+int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, double* L, long long lstride,
+                int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot, double tol, int nb,
+                cudaStream_t st);
+int launch_trsm(ModeMap mm, const TrsmArgs& a, int nmax, int nb, cudaStream_t st);
+int launch_trace(ModeMap mm, const double* A, long long astride, int lda, const int* dk, double* trace, int nb,
+                 cudaStream_t st);
+int launch_tridiag(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e, double* tau,
+                   int vstride, int nb, cudaStream_t st);
+int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D, double* Lo,
+                   double* mu, DevState* s, int nb, cudaStream_t st);
+int launch_rank(const RankArgs& a, cudaStream_t st);
+int launch_eigvecs(ModeMap mm, const double* D, const double* Lo, const double* mu, int vstride, const int* dk,
+                   const DevState* s, double* W, long long wstride, int ldw, int rmax, int nb, cudaStream_t st);
+int launch_backtransform(ModeMap mm, const double* A, long long astride, int lda, const double* tau, int vstride,
+                         const int* dk, const DevState* s, double* W, long long wstride, int ldw, int rmax,
+                         int nb, cudaStream_t st);
+
+}  // namespace rh
+
+#define RH_CHECK_LAUNCH()                                   \
+    do {                                                    \
+        cudaError_t e_ = cudaGetLastError();                \
+        if (e_ != cudaSuccess) return RHOSVD_ERR_CUDA;      \
+    } while (0)

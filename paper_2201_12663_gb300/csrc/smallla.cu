@@ -1,0 +1,496 @@
+// smallla.cu -- small dense FP64 linear algebra on k x k (k <= RHOSVD_K_MAX) matrices,
+// one thread block per mode:
+//   * left-looking Cholesky with optional diagonal pivoting and a relative stopping
+//     tolerance (rank revealing for the PSD Gram Y^T Y) and the row-wise triangular solve
+//     that turns Y into an orthonormal basis (CholeskyQR with pivoting, three passes);
+//   * Householder reduction of the symmetric M = B B^T to tridiagonal form;
+//   * eigenvalues of the tridiagonal from an LDL^T representation of T + s I by bisection
+//     on the differential stationary qd negative count (relative accuracy for the graded,
+//     positive spectra a Gram of a normalised side matrix has);
+//   * eigenvectors of the wanted (largest r) eigenvalues by twisted factorisation
+//     (stationary + progressive qd, twist at min |gamma|), then the Householder
+//     back-transformation.
+// These give the singular values sigma_k = sqrt(lambda_k(B B^T)) and left singular
+// vectors of the side matrix restricted to span(Q) (eq. SVD_Ul, eq. svdr).
+#include "internal.cuh"
+#include <float.h>
+
+namespace rh {
+
+// ------------------------------------------------------------------ pivoted Cholesky
+// G: k x k symmetric (full storage, leading dimension ldg), batch stride gstride.
+// dims: *dk (device) or hk.  L (leading dimension ldl) receives L(i, t) for original row i
+// and step t; perm[t] the pivot of step t.  Stops at the first step whose largest remaining
+// Schur diagonal is <= tol * (largest initial diagonal); the number of steps taken is
+// written to *dm_out.  With pivot == 0 the order is the identity and a non-positive
+// pivot sets *fail.
+__global__ void k_chol_piv(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int hk,
+                           double* L, long long lstride, int ldl, int* perm, int pstride,
+                           int* dm_out, int* fail, int pivot, double tol)
+{
+    const int b = mm.m[blockIdx.x];
+    const int k = dk ? dk[b] : hk;
+    G += b * gstride;
+    L += b * lstride;
+    perm += b * pstride;
+    __shared__ double dsh[KMAX];
+    __shared__ int done[KMAX];
+    __shared__ double red[32];
+    __shared__ int redi[32];
+    __shared__ int s_p;
+    __shared__ double s_piv;
+    const int i = threadIdx.x;
+    double d0max;
+    if (i < k) { dsh[i] = G[(long long)i * ldg + i]; done[i] = 0; }
+    __syncthreads();
+    {
+        double v = (i < k) ? dsh[i] : 0.0;
+        d0max = block_max(v, red);
+    }
+    int m = k;
+    for (int t = 0; t < k; ++t) {
+        // pivot selection (first index of the largest remaining diagonal)
+        if (pivot) {
+            double v = (i < k && !done[i]) ? dsh[i] : -1.0;
+            int idx = i;
+            for (int o = 16; o > 0; o >>= 1) {
+                double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+                if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
+            }
+            __syncthreads();
+            if ((i & 31) == 0) { red[i >> 5] = v; redi[i >> 5] = idx; }
+            __syncthreads();
+            if (i == 0) {
+                double bv = -1.0; int bi = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                    if (red[w] > bv || (red[w] == bv && redi[w] < bi)) { bv = red[w]; bi = redi[w]; }
+                s_p = bi;
+                s_piv = bv;
+            }
+        } else if (i == 0) {
+            s_p = t;
+            s_piv = dsh[t];
+        }
+        __syncthreads();
+        const int p = s_p;
+        const double dp = s_piv;
+        if (!(dp > tol * d0max) || !(dp > 0.0)) {
+            if (!pivot && i == 0 && fail) fail[b] = 1;
+            m = t;
+            break;
+        }
+        const double piv = sqrt(dp);
+        if (i == 0) { perm[t] = p; done[p] = 1; }
+        __syncthreads();
+        if (i < k && !done[i]) {
+            double sacc = G[(long long)p * ldg + i];
+            for (int s = 0; s < t; ++s) sacc -= L[(long long)s * ldl + i] * L[(long long)s * ldl + p];
+            const double lit = sacc / piv;
+            L[(long long)t * ldl + i] = lit;
+            dsh[i] -= lit * lit;
+        }
+        if (i == p) L[(long long)t * ldl + p] = piv;
+        __syncthreads();
+    }
+    if (i == 0) dm_out[b] = m;
+}
+
+// ------------------------------------------------------------------ row triangular solve
+// Q(:, t) = (X(:, perm[t]) - sum_{s<t} Q(:, s) L(perm[t], s)) / L(perm[t], t), t < m.
+// One thread per row of X (n rows); blockIdx.y = mode.  X and Q are n x . column-major.
+
+__global__ void k_trsm_rows(ModeMap mm, TrsmArgs a)
+{
+    const int b = mm.m[blockIdx.y];
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= a.n[b]) return;
+    const int m = a.dm[b];
+    const double* L = a.L + b * a.lstride;
+    const int* perm = a.perm + b * a.pstride;
+    const double* X = a.X[b];
+    double* Q = a.Q[b];
+    const int ldx = a.ldx[b], ldq = a.ldq[b], ldl = a.ldl;
+    double q[KMAX];
+    for (int t = 0; t < m; ++t) {
+        const int p = perm[t];
+        double s0 = X[(long long)p * ldx + row], s1 = 0.0;
+        int s = 0;
+        for (; s + 1 < t; s += 2) {
+            s0 -= q[s] * L[(long long)s * ldl + p];
+            s1 -= q[s + 1] * L[(long long)(s + 1) * ldl + p];
+        }
+        if (s < t) s0 -= q[s] * L[(long long)s * ldl + p];
+        const double v = (s0 + s1) / L[(long long)t * ldl + p];
+        q[t] = v;
+        Q[(long long)t * ldq + row] = v;
+    }
+}
+
+// ------------------------------------------------------------------ tridiagonalisation
+// A: k x k symmetric (full storage, leading dimension lda, batch stride astride), in place.
+// Reflector j (j = 0..k-3): x = A(j+1:k, j), alpha = -sign(x_0)||x||, v = x - alpha e_1,
+// tau = 2 / v^T v; the trailing block gets A <- H A H via p = tau A v, w = p - (tau/2)(p^T v) v,
+// A <- A - v w^T - w v^T.  Output: d (diagonal), e (sub-diagonal), tau, and v stored in
+// A(j+1:k, j).
+__global__ void k_tridiag(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e,
+                          double* tau, int vstride)
+{
+    const int b = mm.m[blockIdx.x];
+    const int k = dk[b];
+    A += b * astride;
+    d += b * vstride;
+    e += b * vstride;
+    tau += b * vstride;
+    __shared__ double v[KMAX], w[KMAX];
+    __shared__ double red[32];
+    const int i = threadIdx.x;
+    for (int j = 0; j + 2 < k; ++j) {
+        const int len = k - j - 1;                 // rows j+1..k-1
+        const int gi = j + 1 + i;
+        double xi = (i < len) ? A[(long long)j * lda + gi] : 0.0;
+        const double x0 = A[(long long)j * lda + j + 1];
+        double tailsq = block_sum((i >= 1 && i < len) ? xi * xi : 0.0, red);
+        double t_j, alpha;
+        if (tailsq == 0.0) {
+            t_j = 0.0;
+            alpha = x0;
+            if (i < len) v[i] = 0.0;
+        } else {
+            const double xn = sqrt(x0 * x0 + tailsq);
+            alpha = (x0 >= 0.0) ? -xn : xn;
+            const double v0 = x0 - alpha;
+            const double vtv = v0 * v0 + tailsq;
+            t_j = 2.0 / vtv;
+            if (i < len) v[i] = (i == 0) ? v0 : xi;
+        }
+        __syncthreads();
+        if (i == 0) { tau[j] = t_j; e[j] = alpha; d[j] = A[(long long)j * lda + j]; }
+        if (t_j != 0.0) {
+            // p = tau * A22 v (row i of the trailing block)
+            double pi = 0.0;
+            if (i < len) {
+                for (int c = 0; c < len; ++c) pi += A[(long long)(j + 1 + c) * lda + gi] * v[c];
+                pi *= t_j;
+            }
+            const double ptv = block_sum((i < len) ? pi * v[i] : 0.0, red);
+            const double Kc = 0.5 * t_j * ptv;
+            if (i < len) w[i] = pi - Kc * v[i];
+            __syncthreads();
+            if (i < len) {
+                const double vi = v[i], wi = w[i];
+                for (int c = 0; c < len; ++c) {
+                    double* a = &A[(long long)(j + 1 + c) * lda + gi];
+                    *a -= vi * w[c] + wi * v[c];
+                }
+            }
+        }
+        __syncthreads();
+        if (i < len) A[(long long)j * lda + gi] = v[i];   // keep the reflector
+        __syncthreads();
+    }
+    if (i == 0) {
+        if (k >= 2) {
+            d[k - 2] = A[(long long)(k - 2) * lda + (k - 2)];
+            d[k - 1] = A[(long long)(k - 1) * lda + (k - 1)];
+            e[k - 2] = A[(long long)(k - 2) * lda + (k - 1)];
+            tau[k - 2] = 0.0;
+        } else if (k == 1) {
+            d[0] = A[0];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ eigenvalues
+// Negative count of L D L^T - sigma I by the differential stationary qd transform.
+__device__ inline int negcount(const double* D, const double* Lo, int k, double sigma)
+{
+    int c = 0;
+    double t = -sigma;
+    for (int i = 0; i + 1 < k; ++i) {
+        double dp = D[i] + t;
+        if (dp < 0.0) ++c;
+        if (dp == 0.0) dp = -DBL_MIN;
+        t = t * (D[i] * Lo[i] * Lo[i]) / dp - sigma;
+        if (!isfinite(t)) t = -sigma;   // overflow after a near-zero pivot: restart the tail
+    }
+    if (D[k - 1] + t < 0.0) ++c;
+    return c;
+}
+
+// LDL^T = T + s I with s > 0 doubled until every pivot is positive; then bisection for every
+// eigenvalue mu_a (ascending) of L D L^T.  Writes D, Lo, mu and the shift s.
+__global__ void k_eigvals(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D,
+                          double* Lo, double* mu, DevState* st)
+{
+    const int b = mm.m[blockIdx.x];
+    const int k = dk[b];
+    d += b * vstride;
+    e += b * vstride;
+    D += b * vstride;
+    Lo += b * vstride;
+    mu += b * vstride;
+    __shared__ double s_hi;
+    __shared__ double Dsh[KMAX], Lsh[KMAX];
+    if (threadIdx.x == 0) {
+        double tnorm = 0.0;
+        for (int i = 0; i < k; ++i) {
+            double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
+            tnorm = fmax(tnorm, r);
+        }
+        double s = fmax(4.0 * k * DBL_EPSILON * tnorm, DBL_MIN);
+        bool ok = false;
+        for (int tries = 0; tries < 60 && !ok; ++tries) {
+            ok = true;
+            double Dc = d[0] + s;
+            for (int i = 0; i < k; ++i) {
+                if (!(Dc > 0.0)) { ok = false; break; }
+                Dsh[i] = Dc;
+                if (i + 1 < k) {
+                    const double l = e[i] / Dc;
+                    Lsh[i] = l;
+                    Dc = d[i + 1] + s - l * e[i];
+                }
+            }
+            if (!ok) s *= 4.0;
+        }
+        if (!ok) st->piv_fail[b] = 1;
+        double hi = 0.0;
+        for (int i = 0; i < k; ++i) {
+            double r = d[i] + s + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
+            hi = fmax(hi, r);
+        }
+        s_hi = hi * (1.0 + 8.0 * DBL_EPSILON) + DBL_MIN;
+        st->shift[b] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) { D[i] = Dsh[i]; Lo[i] = (i + 1 < k) ? Lsh[i] : 0.0; }
+    for (int a = threadIdx.x; a < k; a += blockDim.x) {
+        double lo = 0.0, hi = s_hi;
+        for (int it = 0; it < 400; ++it) {
+            if (hi - lo <= 2.0 * DBL_EPSILON * hi) break;
+            double mid = (lo > 0.0 && hi > 2.0 * lo) ? sqrt(lo) * sqrt(hi) : 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (negcount(Dsh, Lsh, k, mid) <= a) lo = mid; else hi = mid;
+        }
+        mu[a] = 0.5 * (lo + hi);
+    }
+}
+
+// ------------------------------------------------------------------ rank rule
+// Per mode: lambda_j = max(mu_{k-1-j} - s, 0) (descending), rho^2 = max(total - trace, 0).
+// r = min r with rho^2 + sum_{j >= r} lambda_j <= eps^2 total (or the fixed rank).
+
+__global__ void k_rank_select(RankArgs a)
+{
+    const int b = threadIdx.x;
+    if (b >= 3) return;
+    const int k = a.dk[b];
+    const double* mu = a.mu + b * a.vstride;
+    const double s = a.st->shift[b];
+    const double total = a.total[b];
+    const double rho2 = fmax(total - a.trace[b], 0.0);
+    if (a.st->piv_fail[b]) set_status(a.info, RHOSVD_ERR_NOT_CONVERGED);
+    // tails from the smallest eigenvalue upward
+    const double thr = a.eps * a.eps * total;
+    double tail = rho2;
+    int r = k;
+    if (a.ranks[b] > 0) {
+        r = min(a.ranks[b], k);
+        for (int j = k - 1; j >= r; --j) tail += fmax(mu[k - 1 - j] - s, 0.0);
+    } else {
+        while (r > 0) {
+            const double lam = fmax(mu[k - 1 - (r - 1)] - s, 0.0);
+            if (tail + lam <= thr) { tail += lam; --r; } else break;
+        }
+        if (tail > thr && total > 0.0) set_status(a.info, RHOSVD_ERR_SKETCH);
+    }
+    if (total == 0.0) { r = 0; tail = 0.0; }
+    int rn = r;
+    if (r > a.r_max) { set_status(a.info, RHOSVD_ERR_RANK_OVERFLOW); r = a.r_max; }
+    a.st->r[b] = r;
+    a.info->r[b] = r;
+    a.info->r_needed[b] = rn;
+    a.info->k[b] = k;
+    a.info->total[b] = total;
+    a.info->resid[b] = rho2;
+    a.info->tail[b] = sqrt(tail);
+    a.info->direct[b] = a.direct[b];
+    for (int j = 0; j < KMAX; ++j)
+        a.sigma[b][j] = (j < k) ? sqrt(fmax(mu[k - 1 - j] - s, 0.0)) : 0.0;
+}
+
+// ------------------------------------------------------------------ eigenvectors
+// Eigenvector of L D L^T for the eigenvalue mu (twisted factorisation):
+// stationary qd  L D L^T - mu I = L+ D+ L+^T (top down, s_i), progressive qd
+// L D L^T - mu I = U- D- U-^T (bottom up, p_i), gamma_r = s_r + p_r + mu, twist at
+// argmin |gamma_r|; z_r = 1, z_i = -L+_i z_{i+1} above, z_{i+1} = -U-_i z_i below.
+__global__ void k_eigvecs(ModeMap mm, const double* D, const double* Lo, const double* mu, int vstride, const int* dk,
+                          const DevState* st, double* W, long long wstride, int ldw)
+{
+    const int b = mm.m[blockIdx.y];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;   // descending index
+    const int k = dk[b];
+    const int r = st->r[b];
+    if (j >= r || j >= k) return;
+    D += b * vstride;
+    Lo += b * vstride;
+    mu += b * vstride;
+    W += b * wstride;
+    const double lam = mu[k - 1 - j];
+    double Lp[KMAX], Um[KMAX], sv[KMAX], pv[KMAX];
+    // stationary
+    double sc = -lam;
+    for (int i = 0; i + 1 < k; ++i) {
+        sv[i] = sc;
+        double dp = D[i] + sc;
+        if (dp == 0.0) dp = DBL_MIN;
+        const double lp = D[i] * Lo[i] / dp;
+        Lp[i] = lp;
+        sc = lp * Lo[i] * sc - lam;
+    }
+    sv[k - 1] = sc;
+    // progressive
+    double pc = D[k - 1] - lam;
+    pv[k - 1] = pc;
+    for (int i = k - 2; i >= 0; --i) {
+        double dm = D[i] * Lo[i] * Lo[i] + pc;
+        if (dm == 0.0) dm = DBL_MIN;
+        const double t = D[i] / dm;
+        Um[i] = Lo[i] * t;
+        pc = pc * t - lam;
+        pv[i] = pc;
+    }
+    int tw = 0;
+    double gbest = INFINITY;
+    for (int i = 0; i < k; ++i) {
+        const double g = fabs(sv[i] + pv[i] + lam);
+        if (g < gbest) { gbest = g; tw = i; }
+    }
+    double* z = W + (long long)j * ldw;
+    z[tw] = 1.0;
+    double nrm2 = 1.0;
+    double zc = 1.0;
+    for (int i = tw - 1; i >= 0; --i) {
+        zc = -Lp[i] * zc;
+        z[i] = zc;
+        nrm2 += zc * zc;
+    }
+    zc = 1.0;
+    for (int i = tw; i + 1 < k; ++i) {
+        zc = -Um[i] * zc;
+        z[i + 1] = zc;
+        nrm2 += zc * zc;
+    }
+    const double inv = 1.0 / sqrt(nrm2);
+    for (int i = 0; i < k; ++i) z[i] *= inv;
+}
+
+// ------------------------------------------------------------------ back-transformation
+// y <- H_0 H_1 ... H_{k-3} y for each of the r columns (one warp per column); H_j uses the
+// reflector stored in A(j+1:k, j) and tau[j].
+__global__ void k_backtransform(ModeMap mm, const double* A, long long astride, int lda, const double* tau, int vstride,
+                                const int* dk, const DevState* st, double* W, long long wstride, int ldw)
+{
+    const int b = mm.m[blockIdx.y];
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int k = dk[b];
+    const int r = st->r[b];
+    if (warp >= r) return;
+    A += b * astride;
+    tau += b * vstride;
+    double* y = W + b * wstride + (long long)warp * ldw;
+    for (int j = k - 3; j >= 0; --j) {
+        const double t = tau[j];
+        if (t == 0.0) continue;
+        const double* vcol = A + (long long)j * lda;
+        double dot = 0.0;
+        for (int i = j + 1 + lane; i < k; i += 32) dot += vcol[i] * y[i];
+        dot = warp_sum(dot) * t;
+        for (int i = j + 1 + lane; i < k; i += 32) y[i] -= dot * vcol[i];
+        __syncwarp();
+    }
+}
+
+// trace of each mode's k x k matrix (before it is overwritten)
+__global__ void k_trace(ModeMap mm, const double* A, long long astride, int lda, const int* dk, double* trace)
+{
+    const int b = mm.m[blockIdx.x];
+    const int k = dk[b];
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) s += A[b * astride + (long long)i * lda + i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) trace[b] = s;
+}
+
+
+int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, double* L, long long lstride,
+                int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot, double tol, int nb,
+                cudaStream_t st)
+{
+    k_chol_piv<<<nb, KMAX, 0, st>>>(mm, G, gstride, ldg, dk, 0, L, lstride, ldl, perm, pstride, dm_out, fail, pivot, tol);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_trsm(ModeMap mm, const TrsmArgs& a, int nmax, int nb, cudaStream_t st)
+{
+    dim3 grid((nmax + 31) / 32, nb);
+    k_trsm_rows<<<grid, 32, 0, st>>>(mm, a);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_trace(ModeMap mm, const double* A, long long astride, int lda, const int* dk, double* trace, int nb,
+                 cudaStream_t st)
+{
+    k_trace<<<nb, 256, 0, st>>>(mm, A, astride, lda, dk, trace);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_tridiag(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e, double* tau,
+                   int vstride, int nb, cudaStream_t st)
+{
+    k_tridiag<<<nb, KMAX, 0, st>>>(mm, A, astride, lda, dk, d, e, tau, vstride);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D, double* Lo,
+                   double* mu, DevState* s, int nb, cudaStream_t st)
+{
+    k_eigvals<<<nb, KMAX, 0, st>>>(mm, d, e, vstride, dk, D, Lo, mu, s);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_rank(const RankArgs& a, cudaStream_t st)
+{
+    k_rank_select<<<1, 32, 0, st>>>(a);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_eigvecs(ModeMap mm, const double* D, const double* Lo, const double* mu, int vstride, const int* dk,
+                   const DevState* s, double* W, long long wstride, int ldw, int rmax, int nb, cudaStream_t st)
+{
+    dim3 grid((rmax + 63) / 64, nb);
+    k_eigvecs<<<grid, 64, 0, st>>>(mm, D, Lo, mu, vstride, dk, s, W, wstride, ldw);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_backtransform(ModeMap mm, const double* A, long long astride, int lda, const double* tau, int vstride,
+                         const int* dk, const DevState* s, double* W, long long wstride, int ldw, int rmax,
+                         int nb, cudaStream_t st)
+{
+    dim3 grid((rmax + 3) / 4, nb);
+    k_backtransform<<<grid, 128, 0, st>>>(mm, A, astride, lda, tau, vstride, dk, s, W, wstride, ldw);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+}  // namespace rh

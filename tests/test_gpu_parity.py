@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU FP64 oracle on the same
+seeded inputs.
+
+Tolerances (plain FP64 path), derived from the arithmetic:
+  * Tucker tensors: relative Frobenius difference <= 1e-6 (the plain-form bar).
+  * ranks: equal; a difference of one is accepted only at a threshold tie, i.e. when the
+    oracle's tail at the GPU rank lies within 1e-3 relative of eps^2 * total.
+  * singular values: the GPU takes them from the eigenvalues of the Gram B B^T, whose
+    absolute error is O(k u ||B||^2), so |sigma_g^2 - sigma_o^2| <= 1e-12 sigma_1^2.
+  * CP Hadamard product and sum: bit-exact (one rounding per entry on both sides).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests import tensor_utils as tu
+
+pytestmark = pytest.mark.gpu
+
+
+def to_dev(P, cp_or_U, xi=None):
+    import torch
+    U = cp_or_U.U if xi is None else cp_or_U
+    x = cp_or_U.xi if xi is None else xi
+    return [P.to_device_factor(u) for u in U], torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run_gpu(P, U, xi, eps, r_max, oversample=32, ranks=(0, 0, 0), seed=1234):
+    Ud, xd = to_dev(P, U, xi)
+    res = P.rhosvd_c2t(Ud, xd, eps=eps, ranks=ranks, r_max=r_max, oversample=oversample, seed=seed,
+                       with_V=True, with_xi=True)
+    info = res.info()
+    r = [info.r[l] for l in range(3)]
+    beta = res.beta[: r[0] * r[1] * r[2]].cpu().numpy().reshape((r[0], r[1], r[2]), order="F")
+    Z = [res.Z[l][:, : r[l]].cpu().numpy() for l in range(3)]
+    sig = res.sigma.cpu().numpy()
+    V = [res.V[l][: r[l], :].cpu().numpy() for l in range(3)]
+    return dict(info=info, ranks=r, beta=beta, Z=Z, sigma=sig, V=V, xin=res.xi_out.cpu().numpy())
+
+
+def oracle_tail(sig, r):
+    return float(np.sum(sig[r:] ** 2))
+
+
+def assert_rank_parity(g, o, eps):
+    for l in range(3):
+        rg, ro = g["ranks"][l], o["ranks"][l]
+        if rg == ro:
+            continue
+        s = o["sigma"][l]
+        thr = eps * eps * np.sum(s ** 2)
+        assert abs(rg - ro) == 1, (l, rg, ro)
+        lo = min(rg, ro)
+        # tie: removing sigma_{lo+1} moves the tail across the threshold within 1e-3
+        assert abs(oracle_tail(s, lo + 1) - thr) <= 1e-3 * thr or abs(oracle_tail(s, lo) - thr) <= 1e-3 * thr, \
+            (l, rg, ro)
+
+
+def assert_sigma_parity(g, o):
+    for l in range(3):
+        so = o["sigma"][l]
+        k = g["info"].k[l]
+        q = min(len(so), k, g["ranks"][l] + 2)
+        sg = g["sigma"][l][:q]
+        s1 = so[0] if len(so) else 0.0
+        assert np.all(np.abs(sg ** 2 - so[:q] ** 2) <= 1e-12 * s1 * s1 + 1e-14 * so[:q] ** 2), l
+
+
+def assert_tucker_parity(g, o, tol=1e-6):
+    if min(o["ranks"]) == 0:
+        assert np.linalg.norm(g["beta"]) == 0.0
+        return
+    d = tu.tucker_rel_diff(g["beta"], g["Z"], o["beta"], o["Z"])
+    assert d <= tol, d
+    for l in range(3):
+        Zg = g["Z"][l]
+        assert np.allclose(Zg.T @ Zg, np.eye(Zg.shape[1]), atol=1e-10), l
+    return d
+
+
+def check_case(P, U, xi, eps, r_max, oversample=32, ranks=(0, 0, 0)):
+    o = oracle.c2t(U, xi, eps=eps, ranks=ranks)
+    g = run_gpu(P, U, xi, eps, r_max, oversample, ranks)
+    assert g["info"].status == 0, P.rhosvd_strerror(g["info"].status)
+    assert g["info"].kept == o["kept"]
+    assert math.isclose(g["info"].xi_norm, o["xi_norm"], rel_tol=1e-13)
+    assert np.allclose(g["xin"], o["xin"], rtol=1e-14, atol=0)
+    if all(r == 0 for r in ranks):
+        assert_rank_parity(g, o, eps)
+    if g["ranks"] == o["ranks"]:
+        assert_sigma_parity(g, o)
+        d = assert_tucker_parity(g, o)
+        # the mixed Tucker-canonical factors V = Z^T U_normalised (Prop. 2.2)
+        return g, o, d
+    return g, o, None
+
+
+# ---------------------------------------------------------------- configurations
+
+def test_gauss_n128_R200_direct(rhosvd_cuda):
+    cp = workloads.gaussian_sum(128, 200, 0)
+    g, o, d = check_case(rhosvd_cuda, cp.U, cp.xi, 1e-6, r_max=128)
+    assert g["info"].direct[0] == 1
+    assert g["ranks"] == o["ranks"] and d < 1e-9
+
+
+def test_gauss_sketch_ragged(rhosvd_cuda):
+    """n = 300 > k = 128 forces the range sketch; 300 and 700 are not multiples of the tiles."""
+    cp = workloads.gaussian_sum(300, 700, 3)
+    g, o, d = check_case(rhosvd_cuda, cp.U, cp.xi, 1e-6, r_max=128, oversample=32)
+    assert g["info"].direct[0] == 0
+    assert g["info"].resid[0] <= 1e-12 * g["info"].total[0]
+    assert d is not None
+
+
+def test_hadamard_then_reduce(rhosvd_cuda):
+    P = rhosvd_cuda
+    import torch
+    A = workloads.gaussian_sum(256, 24, 0)
+    B = workloads.gaussian_sum(256, 20, 1)
+    Ua, xa = to_dev(P, A)
+    Ub, xb = to_dev(P, B)
+    Uc, xc = P.rhosvd_cp_hadamard(Ua, xa, Ub, xb)
+    torch.cuda.synchronize()
+    Uo, xo = oracle.cp_hadamard(A.U, A.xi, B.U, B.xi)
+    for l in range(3):
+        assert np.array_equal(Uc[l].cpu().numpy(), Uo[l])
+    assert np.array_equal(xc.cpu().numpy(), xo)
+    check_case(P, Uo, xo, 1e-7, r_max=160, oversample=32)
+
+
+def test_cp_sum_bit_exact(rhosvd_cuda):
+    P = rhosvd_cuda
+    import torch
+    A = workloads.gaussian_sum(96, 30, 5)
+    B = workloads.random_cp(96, 17, 6)
+    Ua, xa = to_dev(P, A)
+    Ub, xb = to_dev(P, B)
+    Uc, xc = P.rhosvd_cp_sum(0.75, Ua, xa, -1.5, Ub, xb)
+    torch.cuda.synchronize()
+    Uo, xo = oracle.cp_sum(0.75, A.U, A.xi, -1.5, B.U, B.xi)
+    for l in range(3):
+        assert np.array_equal(Uc[l].cpu().numpy(), Uo[l])
+    assert np.array_equal(xc.cpu().numpy(), xo)
+
+
+def test_newton_long_range_small(rhosvd_cuda):
+    cp = workloads.newton_long_range_sum(n=320, N=40, seed=0)
+    check_case(rhosvd_cuda, cp.U, cp.xi, 1e-6, r_max=64, oversample=32)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_rank_one(rhosvd_cuda):
+    g0 = np.random.default_rng(11)
+    U = [g0.standard_normal((n, 1)) for n in (70, 300, 5)]
+    g, o, d = check_case(rhosvd_cuda, U, np.array([2.5]), 1e-12, r_max=8)
+    assert g["ranks"] == [1, 1, 1] and d < 1e-14
+
+
+def test_fewer_terms_than_grid(rhosvd_cuda):
+    cp = workloads.gaussian_sum(300, 20, 8)
+    g, o, d = check_case(rhosvd_cuda, cp.U, cp.xi, 1e-10, r_max=32, oversample=16)
+    assert g["info"].k[0] <= 20
+
+
+def test_fixed_ranks(rhosvd_cuda):
+    cp = workloads.gaussian_sum(200, 300, 9)
+    g, o, d = check_case(rhosvd_cuda, cp.U, cp.xi, 1e-6, r_max=64, oversample=32, ranks=(5, 12, 30))
+    assert g["ranks"] == [5, 12, 30]
+
+
+def test_zero_terms_dropped(rhosvd_cuda):
+    cp = workloads.gaussian_sum(150, 120, 10)
+    U = [u.copy() for u in cp.U]
+    U[1][:, 7] = 0.0
+    U[2][:, 50] = 0.0
+    U[0][:, 90] *= 2.0 ** -1000
+    g, o, d = check_case(rhosvd_cuda, U, cp.xi, 1e-6, r_max=150)
+    assert g["info"].kept == 118
+
+
+def test_empty_and_eps_one(rhosvd_cuda):
+    P = rhosvd_cuda
+    cp = workloads.gaussian_sum(64, 40, 12)
+    g = run_gpu(P, cp.U, cp.xi, 1.0, r_max=16)
+    assert g["info"].status == 0 and g["ranks"] == [0, 0, 0]
+    U0 = [np.zeros((64, 40)) for _ in range(3)]
+    g = run_gpu(P, U0, cp.xi, 1e-6, r_max=16)
+    assert g["info"].kept == 0 and g["ranks"] == [0, 0, 0]
+
+
+def test_rank_overflow_reports_needed_rank(rhosvd_cuda):
+    P = rhosvd_cuda
+    cp = workloads.gaussian_sum(128, 200, 0)
+    o = oracle.c2t(cp.U, cp.xi, eps=1e-6)
+    g = run_gpu(P, cp.U, cp.xi, 1e-6, r_max=16, oversample=240)
+    assert g["info"].status == P.RHOSVD_ERR_RANK_OVERFLOW
+    assert [g["info"].r_needed[l] for l in range(3)] == o["ranks"]
+    assert g["ranks"] == [16, 16, 16]
+
+
+def test_nonfinite_input_flagged(rhosvd_cuda):
+    P = rhosvd_cuda
+    cp = workloads.gaussian_sum(64, 30, 13)
+    U = [u.copy() for u in cp.U]
+    U[2][3, 4] = np.nan
+    g = run_gpu(P, U, cp.xi, 1e-6, r_max=32)
+    assert g["info"].status == P.RHOSVD_ERR_NONFINITE
+
+
+def test_seed_independence_of_the_result(rhosvd_cuda):
+    """The sketch is random; the Tucker tensor is not (up to the parity tolerance)."""
+    P = rhosvd_cuda
+    cp = workloads.gaussian_sum(400, 500, 14)
+    a = run_gpu(P, cp.U, cp.xi, 1e-6, r_max=128, seed=1)
+    b = run_gpu(P, cp.U, cp.xi, 1e-6, r_max=128, seed=2)
+    assert a["ranks"] == b["ranks"]
+    assert tu.tucker_rel_diff(a["beta"], a["Z"], b["beta"], b["Z"]) < 1e-6

@@ -42,6 +42,18 @@ def test_jacobi_matches_lapack(m, n, grade):
     assert np.allclose(np.linalg.norm(Z[:, :q].T @ A, axis=1), sig[:q], rtol=1e-11, atol=1e-14 * sig[0])
 
 
+def test_jacobi_rank_deficient_resolvable_part():
+    """Numerically zero columns (norm <= m u ||A||_F) are left alone; the resolvable singular
+    values still match LAPACK and the rest stay at the noise level."""
+    g = np.random.default_rng(17)
+    A = (g.standard_normal((100, 15)) * np.logspace(0, -6, 15)) @ g.standard_normal((15, 40))
+    sig, Z = oracle.jacobi_left(A)
+    s_ref = np.linalg.svd(A, compute_uv=False)
+    assert np.allclose(sig[:15], s_ref[:15], rtol=1e-10)
+    assert np.all(sig[15:] <= 1e-13 * sig[0])
+    assert np.allclose(Z[:, :15].T @ Z[:, :15], np.eye(15), atol=1e-11)
+
+
 def test_householder_r_factor():
     g = np.random.default_rng(7)
     A = g.standard_normal((50, 20))
