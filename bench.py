@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""RHOSVD reductions/s on GB300.
+
+Workload ("hadamard_n1024_R64x64"): two seeded rank-64 Gaussian sums on a 1024^3 grid
+(centres U[-5,5]^3, exponents log-uniform [0.5,20], weights U[0.1,1], seeds 0 and 1);
+one step = their canonical Hadamard product (rank 4096) followed by the RHOSVD
+canonical-to-Tucker reduction at eps = 1e-7, i.e. one pass of the whole hot path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is reductions/s with inputs resident in HBM; `e2e`
+is the same metric through the C ABI with the step's inputs copied from pinned host memory
+and the Tucker result read back inside the timed region.  The inputs (3 MB) are smaller
+than L2, so L2 is flushed (a 256 MB write) before every timed step, outside the events.
+With --impl reference the CPU oracle is timed instead, on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="hadamard_n1024_R64x64", n=1024, Ra=64, Rb=64, seeds=[0, 1], eps=1e-7,
+                r_max=160, oversample=32, grid="[-10,10]^3 cell centres", precision="plain_fp64")
+METRIC = "RHOSVD reductions/s at stated rel. err: mixed/learned vs FP64 plain, 1×GB300"
+UNIT = "reductions/s"
+FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (CUDA-core and tensor) rate
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks sampling
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(budget_s=25.0):
+    """Time the plain C oracle on a bounded sample of the workload and extrapolate one
+    reduction: the full Hadamard product and normalisation, the side-matrix SVD of one mode
+    (Householder R + one-sided Jacobi, the dominant step), its projection, and the core
+    contraction over a slice of the terms; three modes and the full term count scale it."""
+    import numpy as np
+    import oracle
+    import workloads
+    A, B = workloads.hartree_like_factors(WORKLOAD["n"], WORKLOAD["Ra"], WORKLOAD["Rb"], WORKLOAD["seeds"])
+    t0 = time.perf_counter()
+    Uc, xc = oracle.cp_hadamard(A.U, A.xi, B.U, B.xi)
+    Un, xin, _, _ = oracle.normalize(Uc, xc)
+    t_prep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sig, Z = oracle.side_svd(Un[0])
+    t_svd = time.perf_counter() - t0
+    r = oracle.eps_rank(sig, WORKLOAD["eps"])
+    R = xc.shape[0]
+    t0 = time.perf_counter()
+    Z0 = np.asfortranarray(Z[:, :r])
+    V = np.zeros(r * R)
+    lib = oracle.lib()
+    lib.orc_project(Un[0].shape[0], R, r, oracle._dp(Z0), oracle._dp(np.asfortranarray(Un[0])), oracle._dp(V))
+    t_proj = time.perf_counter() - t0
+    # core over a slice of the terms (the loops are linear in R)
+    Rs = max(16, R // 64)
+    Vs = np.asfortranarray(V.reshape((r, R), order="F")[:, :Rs])
+    beta = np.zeros(r ** 3)
+    rr = np.array([r, r, r], dtype=np.int32)
+    t0 = time.perf_counter()
+    lib.orc_core(Rs, oracle._ip(rr), oracle._dp(Vs), oracle._dp(Vs), oracle._dp(Vs),
+                 oracle._dp(np.ascontiguousarray(xin[:Rs])), oracle._dp(beta))
+    t_core = (time.perf_counter() - t0) * (R / Rs)
+    t_red = t_prep + 3 * (t_svd + t_proj) + t_core
+    sample = (f"Hadamard product + normalisation (full), side-matrix SVD + projection of mode 1 "
+              f"(full, x3 modes), core over {Rs}/{R} terms (x{R / Rs:.0f}); measured "
+              f"{t_prep + t_svd + t_proj + t_core * Rs / R:.1f} s, extrapolated {t_red:.1f} s/reduction")
+    return {"value": 1.0 / t_red, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds_per_reduction": t_red, "rank_mode1": r}
+
+
+def nproc():
+    try:
+        return os.cpu_count()
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # each timed sample is one full-size oracle measurement (~40 s of CPU work); at most three
+    # are timed so that the run ends within a few minutes (no warm-up is needed on the CPU)
+    t_steps = []
+    cb = None
+    for i in range(min(args.steps, 3)):
+        cb = oracle_sample()
+        t_steps.append(cb["seconds_per_reduction"])
+    ms = 1000.0 * statistics.mean(t_steps)
+    value = 1000.0 / ms
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**WORKLOAD, "l2": "n/a (CPU)"}, "cpu_baseline": cpu, "samples_timed": len(t_steps),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def algorithmic_flops(stage, info, n, R):
+    """FP64 flops of one launch of a stage (all three modes), from the ranks it saw."""
+    r = [info.r[l] for l in range(3)]
+    k = [info.k[l] for l in range(3)]
+    if stage == "core":
+        return 2.0 * r[0] * r[1] * r[2] * R
+    if stage == "sketch":
+        return sum(2.0 * n * (WORKLOAD["r_max"] + WORKLOAD["oversample"]) * R for _ in range(3))
+    if stage == "project":
+        return sum(2.0 * k[l] * n * R for l in range(3))
+    if stage == "residual":
+        return sum(2.0 * n * min(k[l], r[l] + 16) * R + 3.0 * n * R for l in range(3))
+    if stage == "gram_bbt":
+        return sum(2.0 * k[l] * k[l] * R for l in range(3))
+    if stage == "v_hi":
+        return sum(2.0 * min(k[l], r[l] + 16) * k[l] * R for l in range(3))
+    return None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2201_12663_gb300 as P
+    import workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.load()
+
+    A, B = workloads.hartree_like_factors(WORKLOAD["n"], WORKLOAD["Ra"], WORKLOAD["Rb"], WORKLOAD["seeds"])
+    n, Ra, Rb = WORKLOAD["n"], WORKLOAD["Ra"], WORKLOAD["Rb"]
+    R = Ra * Rb
+    import numpy as np
+    # pinned host inputs (column-major factor storage = (R, n) row-major)
+    hA = [torch.from_numpy(np.ascontiguousarray(u.T)).pin_memory() for u in A.U]
+    hB = [torch.from_numpy(np.ascontiguousarray(u.T)).pin_memory() for u in B.U]
+    hxa = torch.from_numpy(A.xi.copy()).pin_memory()
+    hxb = torch.from_numpy(B.xi.copy()).pin_memory()
+    dA = [h.to(dev) for h in hA]
+    dB = [h.to(dev) for h in hB]
+    xa, xb = hxa.to(dev), hxb.to(dev)
+    Ua = [t.t() for t in dA]
+    Ub = [t.t() for t in dB]
+    Uc = [torch.empty(R, n, dtype=torch.float64, device=dev).t() for _ in range(3)]
+    xc = torch.empty(R, dtype=torch.float64, device=dev)
+    opts = dict(eps=WORKLOAD["eps"], r_max=WORKLOAD["r_max"], oversample=WORKLOAD["oversample"], seed=12345)
+    cp = P.make_cp(Uc, xc)
+    ws = torch.empty(P.rhosvd_c2t_workspace_size(cp, P.make_opts(**opts)), dtype=torch.uint8, device=dev)
+    out = P.alloc_tucker([n, n, n], R, WORKLOAD["r_max"], dev)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)   # 256 MB > L2
+
+    def step():
+        P.rhosvd_cp_hadamard(Ua, xa, Ub, xb, U_out=Uc, xi_out=xc)
+        P.rhosvd_c2t(Uc, xc, out=out, workspace=ws, **opts)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    info = out.info()
+    assert info.status == 0, P.rhosvd_strerror(info.status)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing (per-step events, L2 flushed between steps)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    P.rhosvd_profile_read()
+    P.rhosvd_profile_enable(True)
+    l0 = P.rhosvd_launch_count()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record()
+        step()
+        ends[i].record()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = P.rhosvd_launch_count() - l0
+    P.rhosvd_profile_enable(False)
+    prof = P.rhosvd_profile_read()
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    ms_per_step = tot.item() / args.steps
+    value = world * 1000.0 / ms_per_step
+    info = out.info()
+
+    # ---- end to end through the C ABI: H2D inputs, hot path, D2H result, per step
+    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    h2d = sum(h.numel() * 8 for h in hA + hB) + (hxa.numel() + hxb.numel()) * 8
+    hinfo = torch.empty(out.info_buf.numel(), dtype=torch.uint8).pin_memory()
+    hZ = [torch.empty(WORKLOAD["r_max"], n, dtype=torch.float64).pin_memory() for _ in range(3)]
+    hsig = torch.empty(3, P.RHOSVD_K_MAX, dtype=torch.float64).pin_memory()
+    hbeta = torch.empty(WORKLOAD["r_max"] ** 3, dtype=torch.float64).pin_memory()
+    d2h = 0
+    barrier()
+    for i in range(args.steps):
+        flush.zero_()
+        e_s[i].record()
+        for l in range(3):
+            dA[l].copy_(hA[l], non_blocking=True)
+            dB[l].copy_(hB[l], non_blocking=True)
+        xa.copy_(hxa, non_blocking=True)
+        xb.copy_(hxb, non_blocking=True)
+        step()
+        hinfo.copy_(out.info_buf, non_blocking=True)
+        for l in range(3):
+            hZ[l].copy_(out.Z[l].t(), non_blocking=True)
+        hsig.copy_(out.sigma, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        inf = P.rhosvd_info.from_buffer_copy(bytes(hinfo.numpy().tobytes()))
+        cnt = inf.r[0] * inf.r[1] * inf.r[2]
+        hbeta[:cnt].copy_(out.beta[:cnt], non_blocking=True)
+        e_e[i].record()
+        d2h = hinfo.numel() + sum(z.numel() * 8 for z in hZ) + hsig.numel() * 8 + cnt * 8
+    barrier()
+    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / args.steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * 1000.0 / te.item()
+
+    # ---- roofline of the dominant stage (largest share of the timed region)
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    shares = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()} if prof else {}
+    if dom:
+        name, (cnt, ms_tot) = dom
+        avg_ms = ms_tot / cnt
+        fl = algorithmic_flops(name, info, n, R)
+        if fl is not None:
+            ach = fl / (avg_ms * 1e-3) / 1e12
+            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "GB300 nominal FP64 rate (1.25 TFLOP/s); MEASURED_PEAKS.json has no FP64 entry",
+                    "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": fl}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**WORKLOAD, "l2": "flushed (256 MB write) before every timed step",
+                       "ranks": [info.r[l] for l in range(3)], "k": [info.k[l] for l in range(3)],
+                       "tails": [info.tail[l] for l in range(3)]},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "stage_shares": shares,
+            "stage_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+            "clocks": clocks, "wall_s_timed": t_wall, "parallelism": f"replicas{world}"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample()
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"]["host_cores_available"] = nproc()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -70,13 +70,15 @@ typedef struct rhosvd_info {
     int status;             /* RHOSVD_OK or a device-side RHOSVD_ERR_* code              */
     int r[3];               /* Tucker ranks r_l actually stored                           */
     int r_needed[3];        /* rank the eps rule asked for (== r unless RANK_OVERFLOW)     */
-    int k[3];               /* width of the orthonormal basis Q^(l) (subspace searched)   */
+    int k[3];               /* width of the orthonormal basis Q^(l) after rank revealing   */
     int kept;               /* canonical terms kept after dropping zero terms             */
     int direct[3];          /* 1 if mode l used the exact n_l x n_l Gram (no sketch)       */
     double xi_norm;         /* ||xi'|| of the normalised weights (Thm. 2.3)              */
     double total[3];        /* ||U^(l) normalised||_F^2                                   */
-    double resid[3];        /* energy of U^(l) outside span(Q^(l)) (sketch residual)      */
-    double tail[3];         /* (sum_{k>r_l} sigma_{l,k}^2)^{1/2}, incl. the residual      */
+    double resid[3];        /* ||U - Z_hi V_hi||_F^2: energy outside the leading directions
+                               computed as rank candidates (<= eps^2 total unless SKETCH)  */
+    double tail[3];         /* tau_l = ||U^(l) - Z^(l) V^(l)||_F measured directly, the
+                               per-mode truncation error of Thm. 2.3                       */
 } rhosvd_info;
 
 /* Outputs of rhosvd_c2t (all device memory, caller-allocated). */
@@ -137,6 +139,23 @@ int rhosvd_cp_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, double* const U_o
  */
 int rhosvd_cp_sum(double alpha, const rhosvd_cp* a, double beta, const rhosvd_cp* b,
                   double* const U_out[3], const int ld_out[3], double* xi_out, void* stream);
+
+/* ---------------------------------------------------------------- tracing (no paper
+ * counterpart: observability of the library itself) */
+
+/* Number of CUDA kernel launches the library has made since it was loaded (all threads). */
+long long rhosvd_launch_count(void);
+
+/* Turn per-stage timing on (1) or off (0); returns the previous setting.  When on, every
+ * stage of rhosvd_c2t / rhosvd_cp_hadamard / rhosvd_cp_sum is bracketed by two CUDA events
+ * recorded on the call's stream (the events come from a pool the library creates on first
+ * use; at most 4096 stages are kept between reads). */
+int rhosvd_profile_enable(int on);
+
+/* Wait for the recorded events, then write one line "stage count total_ms" per stage into
+ * buf (host memory, len bytes, NUL-terminated when it fits) and clear the records.
+ * Returns the number of bytes written, or RHOSVD_ERR_CUDA. */
+int rhosvd_profile_read(char* buf, int len);
 
 #ifdef __cplusplus
 }

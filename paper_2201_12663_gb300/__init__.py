@@ -95,6 +95,11 @@ def load(build_if_missing: bool = False):
         L.rhosvd_cp_sum.restype = _c.c_int
         L.rhosvd_cp_sum.argtypes = [_c.c_double, _c.POINTER(rhosvd_cp), _c.c_double, _c.POINTER(rhosvd_cp),
                                     _c.c_void_p * 3, _c.c_int * 3, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_launch_count.restype = _c.c_longlong
+        L.rhosvd_profile_enable.restype = _c.c_int
+        L.rhosvd_profile_enable.argtypes = [_c.c_int]
+        L.rhosvd_profile_read.restype = _c.c_int
+        L.rhosvd_profile_read.argtypes = [_c.c_char_p, _c.c_int]
         _lib = L
         return L
 
@@ -166,6 +171,27 @@ def rhosvd_strerror(code: int) -> str:
         return load().rhosvd_strerror(int(code)).decode()
     except Exception:                                  # library unavailable
         return f"status {code}"
+
+
+def rhosvd_launch_count() -> int:
+    return int(load().rhosvd_launch_count())
+
+
+def rhosvd_profile_enable(on: bool) -> bool:
+    return bool(load().rhosvd_profile_enable(1 if on else 0))
+
+
+def rhosvd_profile_read() -> dict:
+    """{stage: (count, total_ms)} accumulated since the last read (synchronises events)."""
+    buf = _c.create_string_buffer(1 << 16)
+    n = load().rhosvd_profile_read(buf, len(buf))
+    if n < 0:
+        raise RhosvdError(n, "rhosvd_profile_read")
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
 
 
 def rhosvd_c2t_workspace_size(cp: rhosvd_cp, opts: rhosvd_opts) -> int:

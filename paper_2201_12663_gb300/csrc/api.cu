@@ -2,9 +2,106 @@
 // ordered launch sequence of the canonical-to-Tucker transform (Def. 2.2, Prop. 2.2).
 // Every rank decision is taken on the device; the host never synchronises inside a call.
 #include "internal.cuh"
+#include <atomic>
+#include <mutex>
+#include <stdio.h>
 #include <string.h>
 
 using namespace rh;
+
+// ---------------------------------------------------------------- tracing
+// Optional per-stage timing with CUDA events recorded on the call's stream (off by default),
+// and a count of kernel launches made by the library.
+namespace {
+std::atomic<long long> g_launches{0};
+std::mutex g_prof_mu;
+int g_prof_on = 0;
+constexpr int PROF_MAX = 4096;
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+ProfRec g_prof[PROF_MAX];
+int g_prof_n = 0;
+cudaEvent_t g_pool[2 * PROF_MAX];
+int g_pool_n = 0, g_pool_used = 0;
+struct ProfAcc {
+    const char* name;
+    double ms;
+    long long count;
+};
+ProfAcc g_acc[64];
+int g_acc_n = 0;
+
+cudaEvent_t pool_event()
+{
+    if (g_pool_used < g_pool_n) return g_pool[g_pool_used++];
+    if (g_pool_n >= 2 * PROF_MAX) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g_pool[g_pool_n++] = e;
+    g_pool_used = g_pool_n;
+    return e;
+}
+
+int prof_begin(const char* name, cudaStream_t st)
+{
+    if (!g_prof_on) return -1;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_n >= PROF_MAX) return -1;
+    cudaEvent_t a = pool_event(), b = pool_event();
+    if (!a || !b) return -1;
+    g_prof[g_prof_n] = ProfRec{name, a, b};
+    cudaEventRecord(a, st);
+    return g_prof_n++;
+}
+
+void prof_end(int id, cudaStream_t st)
+{
+    if (id >= 0) cudaEventRecord(g_prof[id].b, st);
+}
+}  // namespace
+
+void rh::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+#define STAGE(name, call)                     \
+    do {                                      \
+        const int pid_ = prof_begin(name, st); \
+        rc = (call);                          \
+        prof_end(pid_, st);                   \
+        if (rc) return rc;                    \
+    } while (0)
+
+extern "C" long long rhosvd_launch_count(void) { return g_launches.load(); }
+
+extern "C" int rhosvd_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    const int prev = g_prof_on;
+    g_prof_on = on ? 1 : 0;
+    return prev;
+}
+
+extern "C" int rhosvd_profile_read(char* buf, int len)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int i = 0; i < g_prof_n; ++i) {
+        if (cudaEventSynchronize(g_prof[i].b) != cudaSuccess) return RHOSVD_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g_prof[i].a, g_prof[i].b) != cudaSuccess) return RHOSVD_ERR_CUDA;
+        int j = 0;
+        while (j < g_acc_n && strcmp(g_acc[j].name, g_prof[i].name) != 0) ++j;
+        if (j == g_acc_n && g_acc_n < 64) g_acc[g_acc_n++] = ProfAcc{g_prof[i].name, 0.0, 0};
+        if (j < 64) { g_acc[j].ms += ms; g_acc[j].count += 1; }
+    }
+    g_prof_n = 0;
+    g_pool_used = 0;
+    int w = 0;
+    for (int j = 0; j < g_acc_n && buf && w < len; ++j)
+        w += snprintf(buf + w, (size_t)(len - w), "%s %lld %.6f\n", g_acc[j].name, g_acc[j].count, g_acc[j].ms);
+    g_acc_n = 0;
+    return w;
+}
 
 namespace {
 
@@ -18,7 +115,9 @@ struct Plan {
     int KW;               // max k_l over modes
     int NQ;               // max n_l over modes
     int ks_sketch, ks_gram, ks_bbt;
-    size_t o_state, o_norms, o_inv, o_xin, o_bufA, o_bufB, o_G, o_L, o_perm, o_B, o_vec, o_W, o_V, o_part;
+    size_t o_state, o_norms, o_keep, o_nn2, o_Un, o_xin, o_bufA, o_bufB, o_G, o_L, o_perm, o_B, o_vec, o_W, o_V, o_Z, o_rp,
+        o_part;
+    long long rp_stride;   // residual partials per mode (tiles of the residual GEMM)
     size_t total;
 };
 
@@ -84,7 +183,9 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
     auto take = [&](size_t bytes) { size_t o2 = off; off += up(bytes); return o2; };
     p->o_state = take(sizeof(DevState));
     p->o_norms = take(sizeof(double) * 3 * R);
-    p->o_inv = take(sizeof(double) * 3 * R);
+    p->o_keep = take(sizeof(double) * R);
+    p->o_nn2 = take(sizeof(double) * 3 * R);
+    p->o_Un = take(sizeof(double) * 3 * (size_t)p->NQ * R);
     p->o_xin = take(sizeof(double) * R);
     p->o_bufA = take(sizeof(double) * 3 * NK);
     p->o_bufB = take(sizeof(double) * 3 * NK);
@@ -93,8 +194,11 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
     p->o_perm = take(sizeof(int) * 3 * p->KW);
     p->o_B = take(sizeof(double) * 3 * (size_t)p->KW * R);
     p->o_vec = take(sizeof(double) * 6 * 3 * p->KW);
-    p->o_W = take(sizeof(double) * 3 * (size_t)p->KW * p->rmax);
-    p->o_V = take(sizeof(double) * 3 * (size_t)p->rmax * R);
+    p->o_W = take(sizeof(double) * 3 * KK);
+    p->o_V = take(sizeof(double) * 3 * (size_t)p->KW * R);
+    p->o_Z = take(sizeof(double) * 3 * NK);
+    p->rp_stride = (long long)((p->NQ + 63) / 64) * ((R + 63) / 64);
+    p->o_rp = take(sizeof(double) * 3 * (size_t)p->rp_stride);
     p->o_part = take(sizeof(double) * (size_t)part);
     p->total = off;
     return RHOSVD_OK;
@@ -158,7 +262,9 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     char* ws = (char*)workspace;
     DevState* S = (DevState*)(ws + p.o_state);
     double* norms = (double*)(ws + p.o_norms);
-    double* inv = (double*)(ws + p.o_inv);
+    double* keepf = (double*)(ws + p.o_keep);
+    double* nn2 = (double*)(ws + p.o_nn2);
+    double* Un = (double*)(ws + p.o_Un);
     double* xin = (double*)(ws + p.o_xin);
     double* bufA = (double*)(ws + p.o_bufA);
     double* bufB = (double*)(ws + p.o_bufB);
@@ -169,6 +275,8 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     double* vec = (double*)(ws + p.o_vec);
     double* W = (double*)(ws + p.o_W);
     double* Vw = (double*)(ws + p.o_V);
+    double* Zw = (double*)(ws + p.o_Z);
+    double* rpart = (double*)(ws + p.o_rp);
     double* part = (double*)(ws + p.o_part);
     const int R = cp->R, KW = p.KW, rmax = p.rmax;
     const long long NK = (long long)p.NQ * KW, KK = (long long)KW * KW;
@@ -179,8 +287,8 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     double* vD = vec + 9 * vs;
     double* vL = vec + 12 * vs;
     double* vmu = vec + 15 * vs;
-    double* V[3];
-    for (int l = 0; l < 3; ++l) V[l] = out->V[l] ? out->V[l] : Vw + (size_t)l * rmax * (R > 0 ? R : 1);
+    const long long VS = (long long)KW * (R > 0 ? R : 1);
+    const long long US = (long long)p.NQ * (R > 0 ? R : 1);   // normalised side matrix per mode
 
     // ---- reset outputs and state
     if (cudaMemsetAsync(out->info, 0, sizeof(rhosvd_info), st) != cudaSuccess) return RHOSVD_ERR_CUDA;
@@ -190,17 +298,16 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             return RHOSVD_ERR_CUDA;
         if (cudaMemsetAsync(out->sigma[l], 0, sizeof(double) * KMAX, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
     }
-    if ((rc = launch_init_state(S, p.kin[0], p.kin[1], p.kin[2], p.direct[0] ? p.n[0] : 0,
-                                p.direct[1] ? p.n[1] : 0, p.direct[2] ? p.n[2] : 0, st)))
-        return rc;
+    STAGE("init_state", launch_init_state(S, p.kin[0], p.kin[1], p.kin[2], p.direct[0] ? p.n[0] : 0,
+                                p.direct[1] ? p.n[1] : 0, p.direct[2] ? p.n[2] : 0, st));
 
     // ---- a1: column norms, normalised weights (Sec. 2.1)
     NormArgs na;
     for (int l = 0; l < 3; ++l) { na.U[l] = cp->U[l]; na.ld[l] = cp->ld[l]; na.n[l] = p.n[l]; }
     na.R = R;
     na.norms = norms;
-    if ((rc = launch_colnorms(na, st))) return rc;
-    if ((rc = launch_terms(norms, cp->xi, R, inv, xin, out->xi_out, out->info, S->total, st))) return rc;
+    STAGE("colnorms", launch_colnorms(na, st));
+    STAGE("normalize", launch_terms(na, cp->xi, keepf, xin, out->xi_out, out->info, Un, US, nn2, S->total, st));
 
     ModeMap all = {{0, 1, 2}};
     ModeMap sk;
@@ -213,7 +320,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
         ldq[l] = p.n[l];
         if (p.direct[l]) {
             Qfin[l] = bufA + l * NK;
-            if ((rc = launch_identity(Qfin[l], p.n[l], p.n[l], st))) return rc;
+            STAGE("identity", launch_identity(Qfin[l], p.n[l], p.n[l], st));
         } else {
             Qfin[l] = bufB + l * NK;
         }
@@ -229,19 +336,18 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
         for (int b = 0; b < nsk; ++b) {
             const int l = sk.m[b];
             GemmProblem g = blank_problem();
-            g.A = Mat{cp->U[l], 1, cp->ld[l]};
+            g.A = Mat{Un + l * US, 1, (long long)p.n[l]};
             g.C = bufA + l * NK;
             g.crs = 1;
             g.ccs = p.n[l];
             g.M = p.n[l];
             g.N = p.kin[l];
             g.K = R;
-            g.bscale = inv + (size_t)l * R;
             g.seed = opts->seed;
             g.mode = l;
             gb.p[b] = g;
         }
-        if ((rc = launch_gemm_splitk(gb, part, st))) return rc;
+        STAGE("sketch", launch_gemm_splitk(gb, part, st));
 
         // ---- a3: CholeskyQR with pivoting, three passes: Y -> Q1 (bufB) -> Q2 (bufA) -> Q (bufB)
         const double tols[3] = {1e-15, 1e-11, 0.0};
@@ -269,11 +375,10 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 if (pass > 0) { g.dM = &S->m[l]; g.dN = &S->m[l]; }
                 g2.p[b] = g;
             }
-            if ((rc = launch_gemm_splitk(g2, part, st))) return rc;
+            STAGE("cholqr_gram", launch_gemm_splitk(g2, part, st));
             const int* dk = (pass == 0) ? S->kin : S->m;
-            if ((rc = launch_chol(sk, G, KK, KW, dk, L, KK, KW, perm, KW, S->m, S->piv_fail, pivots[pass],
-                                  tols[pass], nsk, st)))
-                return rc;
+            STAGE("cholqr_chol", launch_chol(sk, G, KK, KW, dk, L, KK, KW, perm, KW, S->m, S->piv_fail, pivots[pass],
+                                  tols[pass], nsk, st));
             TrsmArgs ta;
             memset(&ta, 0, sizeof(ta));
             for (int l = 0; l < 3; ++l) {
@@ -289,7 +394,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             ta.perm = perm;
             ta.pstride = KW;
             ta.dm = S->m;
-            if ((rc = launch_trsm(sk, ta, p.NQ, nsk, st))) return rc;
+            STAGE("cholqr_trsm", launch_trsm(sk, ta, p.NQ, nsk, st));
         }
     }
 
@@ -303,7 +408,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
         for (int l = 0; l < 3; ++l) {
             GemmProblem g = blank_problem();
             g.A = Mat{Qfin[l], (long long)ldq[l], 1};
-            g.B = Mat{cp->U[l], 1, cp->ld[l]};
+            g.B = Mat{Un + l * US, 1, (long long)p.n[l]};
             g.C = Bm + (size_t)l * KW * R;
             g.crs = 1;
             g.ccs = KW;
@@ -311,10 +416,9 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             g.dM = &S->m[l];
             g.N = R;
             g.K = p.n[l];
-            g.colscale = inv + (size_t)l * R;
             gb.p[l] = g;
         }
-        if ((rc = launch_gemm(gb, st))) return rc;
+        STAGE("project", launch_gemm(gb, st));
 
         // ---- a5: M = B B^T (m_l x m_l), trace, tridiagonal form, eigenvalues
         GemmBatch gm;
@@ -337,14 +441,15 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             g.dN = &S->m[l];
             gm.p[l] = g;
         }
-        if ((rc = launch_gemm_splitk(gm, part, st))) return rc;
+        STAGE("gram_bbt", launch_gemm_splitk(gm, part, st));
     }
     if (R == 0 && cudaMemsetAsync(G, 0, sizeof(double) * 3 * KK, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
-    if ((rc = launch_trace(all, G, KK, KW, S->m, S->trace, 3, st))) return rc;
-    if ((rc = launch_tridiag(all, G, KK, KW, S->m, vd, ve, vtau, vs, 3, st))) return rc;
-    if ((rc = launch_eigvals(all, vd, ve, vs, S->m, vD, vL, vmu, S, 3, st))) return rc;
+    STAGE("trace", launch_trace(all, G, KK, KW, S->m, S->trace, 3, st));
+    STAGE("tridiag", launch_tridiag(all, G, KK, KW, S->m, vd, ve, vtau, vs, 3, st));
+    STAGE("eigvals", launch_eigvals(all, vd, ve, vs, S->m, vD, vL, vmu, S, 3, st));
 
-    // ---- a6: eps-rank (Thm. 2.3), sigma, then eigenvectors of the kept eigenvalues
+    // ---- a6: provisional rank from the eigenvalues, then eigenvectors of the rhi leading
+    //          eigenvalues (rank candidates 0..rhi) and their Householder back-transformation
     RankArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.mu = vmu;
@@ -356,53 +461,102 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     ra.r_max = rmax;
     ra.info = out->info;
     ra.st = S;
+    ra.kept = &out->info->kept;
+    ra.margin = 16;
     for (int l = 0; l < 3; ++l) {
         ra.ranks[l] = opts->ranks[l];
         ra.sigma[l] = out->sigma[l];
         ra.direct[l] = p.direct[l];
     }
-    if ((rc = launch_rank(ra, st))) return rc;
-    if ((rc = launch_eigvecs(all, vD, vL, vmu, vs, S->m, S, W, (long long)KW * rmax, KW, rmax, 3, st))) return rc;
-    if ((rc = launch_backtransform(all, G, KK, KW, vtau, vs, S->m, S, W, (long long)KW * rmax, KW, rmax, 3, st)))
-        return rc;
+    STAGE("rank_provisional", launch_rank(ra, st));
+    STAGE("eigvecs", launch_eigvecs(all, vD, vL, vmu, vs, S->m, S, W, KK, KW, KW, 3, st));
+    STAGE("backtransform", launch_backtransform(all, G, KK, KW, vtau, vs, S->m, S, W, KK, KW, KW, 3, st));
 
     if (R > 0) {
-        // ---- Z = Q W_r (n_l x r_l) and V = W_r^T B (r_l x R, ld r_max)
+        // ---- Z_hi = Q W (n_l x rhi, ld n_l) and V_hi = W^T B (rhi x R, ld KW)
         GemmBatch gz;
         memset(&gz, 0, sizeof(gz));
         gz.nbatch = 3;
         gz.ksplit = 1;
         gz.bkind = B_PLAIN;
-        GemmBatch gv = gz;
+        GemmBatch gv = gz, gr = gz;
         for (int l = 0; l < 3; ++l) {
+            double* Wl = W + l * KK;
             GemmProblem g = blank_problem();
-            double* Wl = W + (size_t)l * KW * rmax;
             g.A = Mat{Qfin[l], 1, (long long)ldq[l]};
             g.B = Mat{Wl, 1, KW};
-            g.C = out->Z[l];
+            g.C = Zw + l * NK;
             g.crs = 1;
             g.ccs = p.n[l];
             g.M = p.n[l];
-            g.N = rmax;
-            g.dN = &S->r[l];
+            g.N = p.kin[l];
+            g.dN = &S->rhi[l];
             g.K = p.kin[l];
             g.dK = &S->m[l];
             gz.p[l] = g;
             GemmProblem h = blank_problem();
             h.A = Mat{Wl, KW, 1};
             h.B = Mat{Bm + (size_t)l * KW * R, 1, KW};
-            h.C = V[l];
+            h.C = Vw + l * VS;
             h.crs = 1;
-            h.ccs = rmax;
-            h.M = rmax;
-            h.dM = &S->r[l];
+            h.ccs = KW;
+            h.M = p.kin[l];
+            h.dM = &S->rhi[l];
             h.N = R;
             h.K = p.kin[l];
             h.dK = &S->m[l];
             gv.p[l] = h;
+            // residual energy ||U_normalised - Z_hi V_hi||_F^2 (no output matrix)
+            GemmProblem e = blank_problem();
+            e.A = Mat{Zw + l * NK, 1, (long long)p.n[l]};
+            e.B = Mat{Vw + l * VS, 1, KW};
+            e.M = p.n[l];
+            e.N = R;
+            e.K = p.kin[l];
+            e.dK = &S->rhi[l];
+            e.rref = Un + l * US;
+            e.rref_ld = p.n[l];
+            e.rpart = rpart + l * p.rp_stride;
+            gr.p[l] = e;
         }
-        if ((rc = launch_gemm(gz, st))) return rc;
-        if ((rc = launch_gemm(gv, st))) return rc;
+        STAGE("z_hi", launch_gemm(gz, st));
+        STAGE("v_hi", launch_gemm(gv, st));
+        STAGE("residual", launch_gemm(gr, st));
+    } else if (cudaMemsetAsync(rpart, 0, sizeof(double) * 3 * p.rp_stride, st) != cudaSuccess) {
+        return RHOSVD_ERR_CUDA;
+    }
+
+    // ---- final eps-rank (Thm. 2.3) from the residual and the Ritz energies
+    FinalArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.V = Vw;
+    fa.vstride = VS;
+    fa.ldv = KW;
+    fa.R = R;
+    fa.eps = opts->eps;
+    fa.r_max = rmax;
+    fa.info = out->info;
+    fa.st = S;
+    fa.rpart = rpart;
+    fa.rpstride = p.rp_stride;
+    for (int l = 0; l < 3; ++l) {
+        fa.ranks[l] = opts->ranks[l];
+        fa.ntiles[l] = (int)p.rp_stride;
+    }
+    STAGE("rank_final", launch_rank_final(fa, st));
+
+    if (R > 0) {
+        // ---- outputs: Z = Z_hi(:, :r), optional V = V_hi(:r, :)
+        double* zd[3] = {out->Z[0], out->Z[1], out->Z[2]};
+        int zld[3] = {p.n[0], p.n[1], p.n[2]};
+        STAGE("copy_out", launch_copy2d(Zw, NK, zld, zd, zld, nullptr, p.n, S->r, nullptr, st));
+        if (out->V[0] && out->V[1] && out->V[2]) {
+            double* vd2[3] = {out->V[0], out->V[1], out->V[2]};
+            int vld[3] = {rmax, rmax, rmax};
+            int RR[3] = {R, R, R};
+            int vls[3] = {KW, KW, KW};
+            STAGE("copy_out", launch_copy2d(Vw, VS, vls, vd2, vld, S->r, nullptr, nullptr, RR, st));
+        }
 
         // ---- a7: core beta = V1 diag(xi') (V3 (.) V2)^T (Prop. 2.2), packed r1 x r2 x r3
         GemmBatch gc;
@@ -411,7 +565,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
         gc.ksplit = 1;
         gc.bkind = B_KR;
         GemmProblem g = blank_problem();
-        g.A = Mat{V[0], 1, rmax};
+        g.A = Mat{Vw, 1, KW};
         g.C = out->beta;
         g.crs = 1;
         g.ccs = -1;           // = r1, decided on the device
@@ -422,12 +576,12 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
         g.dNa = &S->r[1];
         g.dNb = &S->r[2];
         g.K = R;
-        g.V2 = V[1];
-        g.V3 = V[2];
+        g.V2 = Vw + VS;
+        g.V3 = Vw + 2 * VS;
         g.xi = xin;
-        g.ldv = rmax;
+        g.ldv = KW;
         gc.p[0] = g;
-        if ((rc = launch_gemm(gc, st))) return rc;
+        STAGE("core", launch_gemm(gc, st));
     }
     return RHOSVD_OK;
 }
@@ -454,7 +608,10 @@ extern "C" int rhosvd_cp_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, double
     h.xa = a->xi;
     h.xb = b->xi;
     h.xc = xi_out;
-    return launch_hadamard(h, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = 0;
+    STAGE("hadamard", launch_hadamard(h, st));
+    return RHOSVD_OK;
 }
 
 extern "C" int rhosvd_cp_sum(double alpha, const rhosvd_cp* a, double beta, const rhosvd_cp* b,
@@ -480,5 +637,8 @@ extern "C" int rhosvd_cp_sum(double alpha, const rhosvd_cp* a, double beta, cons
     s.xc = xi_out;
     s.alpha = alpha;
     s.beta = beta;
-    return launch_cpsum(s, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = 0;
+    STAGE("cp_sum", launch_cpsum(s, st));
+    return RHOSVD_OK;
 }

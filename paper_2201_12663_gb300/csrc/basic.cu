@@ -27,13 +27,16 @@ __global__ void k_colnorms(NormArgs a)
     } else {
         int ex;
         frexp(mx, &ex);               // mx = f 2^ex, f in [0.5, 1)
-        const double sc = ldexp(1.0, -ex);
+        // scale by 2^-ex in two exact power-of-two steps (2^-ex alone can overflow when the
+        // column is subnormal)
+        const int e1 = -ex / 2, e2 = -ex - e1;
+        const double sc1 = ldexp(1.0, e1), sc2 = ldexp(1.0, e2);
         double s = 0.0;
         bool bad = false;
         for (int i = lane; i < n; i += 32) {
             const double x = u[i];
             if (x != x) bad = true;
-            const double t = x * sc;
+            const double t = (x * sc1) * sc2;
             s = fma(t, t, s);
         }
         s = warp_sum(s);
@@ -43,9 +46,9 @@ __global__ void k_colnorms(NormArgs a)
     if (lane == 0) a.norms[(long long)l * a.R + warp] = nrm;
 }
 
-// Per term: keep iff all three norms are finite and nonzero; inv_l = 1/||u_l||, weight
+// Per term: keep iff all three norms are finite and nonzero (keep[nu] = 1 or 0), weight
 // xi' = xi prod_l ||u_l|| (0 for a dropped term).  Non-finite data sets NONFINITE.
-__global__ void k_terms(const double* norms, const double* xi, int R, double* inv, double* xin,
+__global__ void k_terms(const double* norms, const double* xi, int R, double* keepf, double* xin,
                         double* xi_user, rhosvd_info* info)
 {
     for (int nu = blockIdx.x * blockDim.x + threadIdx.x; nu < R; nu += gridDim.x * blockDim.x) {
@@ -54,29 +57,49 @@ __global__ void k_terms(const double* norms, const double* xi, int R, double* in
         const bool fin = isfinite(d0) && isfinite(d1) && isfinite(d2) && isfinite(x);
         if (!fin) set_status(info, RHOSVD_ERR_NONFINITE);
         const bool keep = fin && d0 > 0.0 && d1 > 0.0 && d2 > 0.0;
-        inv[nu] = keep ? 1.0 / d0 : 0.0;
-        inv[R + nu] = keep ? 1.0 / d1 : 0.0;
-        inv[2 * R + nu] = keep ? 1.0 / d2 : 0.0;
+        keepf[nu] = keep ? 1.0 : 0.0;
         const double w = keep ? x * d0 * d1 * d2 : 0.0;
         xin[nu] = w;
         if (xi_user) xi_user[nu] = w;
     }
 }
 
+// Normalised copy of the side matrices (Sec. 2.1): Un(:, nu) = u_nu / ||u_nu|| for kept
+// terms (correctly rounded division), zero columns for dropped terms; nn2 = ||Un(:, nu)||^2
+// as stored.  One warp per column, grid (ceil(R/8), 3).
+__global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long long ustride, double* nn2)
+{
+    const int l = blockIdx.y;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= a.R) return;
+    const int n = a.n[l];
+    const double* u = a.U[l] + (long long)warp * a.ld[l];
+    double* dst = Un + l * ustride + (long long)warp * n;
+    const bool keep = keepf[warp] != 0.0;
+    const double d = a.norms[(long long)l * a.R + warp];
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) {
+        const double v = keep ? u[i] / d : 0.0;
+        dst[i] = v;
+        s = fma(v, v, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) nn2[(long long)l * a.R + warp] = s;
+}
+
 // Deterministic single-block sums: kept terms, ||xi'||^2 and ||U_l normalised||_F^2.
-__global__ void k_term_totals(const double* norms, const double* inv, const double* xin, int R,
+__global__ void k_term_totals(const double* nn2, const double* keepf, const double* xin, int R,
                               double* total, rhosvd_info* info)
 {
     __shared__ double red[32];
     double t0 = 0.0, t1 = 0.0, t2 = 0.0, x2 = 0.0, cnt = 0.0;
     for (int nu = threadIdx.x; nu < R; nu += blockDim.x) {
-        const double a0 = norms[nu] * inv[nu], a1 = norms[R + nu] * inv[R + nu],
-                     a2 = norms[2 * R + nu] * inv[2 * R + nu];
-        t0 += a0 * a0;
-        t1 += a1 * a1;
-        t2 += a2 * a2;
+        t0 += nn2[nu];
+        t1 += nn2[R + nu];
+        t2 += nn2[2 * R + nu];
         x2 += xin[nu] * xin[nu];
-        cnt += (inv[nu] != 0.0) ? 1.0 : 0.0;
+        cnt += keepf[nu];
     }
     t0 = block_sum(t0, red);
     t1 = block_sum(t1, red);
@@ -157,14 +180,18 @@ int launch_colnorms(const NormArgs& a, cudaStream_t st)
     return 0;
 }
 
-int launch_terms(const double* norms, const double* xi, int R, double* inv, double* xin, double* xi_user,
-                 rhosvd_info* info, double* total, cudaStream_t st)
+int launch_terms(const NormArgs& na, const double* xi, double* keepf, double* xin, double* xi_user,
+                 rhosvd_info* info, double* Un, long long ustride, double* nn2, double* total, cudaStream_t st)
 {
+    const int R = na.R;
     if (R > 0) {
-        k_terms<<<(R + 255) / 256, 256, 0, st>>>(norms, xi, R, inv, xin, xi_user, info);
+        k_terms<<<(R + 255) / 256, 256, 0, st>>>(na.norms, xi, R, keepf, xin, xi_user, info);
+        RH_CHECK_LAUNCH();
+        dim3 grid((R + 7) / 8, 3);
+        k_normalize<<<grid, 256, 0, st>>>(na, keepf, Un, ustride, nn2);
         RH_CHECK_LAUNCH();
     }
-    k_term_totals<<<1, 1024, 0, st>>>(norms, inv, xin, R, total, info);
+    k_term_totals<<<1, 1024, 0, st>>>(nn2, keepf, xin, R, total, info);
     RH_CHECK_LAUNCH();
     return 0;
 }

@@ -23,7 +23,10 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(GemmBatch gb)
     if (P.N_from_r2r3) N = (*P.dNa) * (*P.dNb);
     const int K = dim_or(P.dK, P.K);
     const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
-    if (i0 >= M || j0 >= N) return;
+    if (i0 >= M || j0 >= N) {
+        if (P.rpart && threadIdx.x == 0) P.rpart[blockIdx.x + gridDim.x * blockIdx.y] = 0.0;
+        return;
+    }
     int kc = (K + gb.ksplit - 1) / gb.ksplit;
     kc = (kc + BK - 1) / BK * BK;
     const int kbeg = s * kc, kend = min(K, kbeg + kc);
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(GemmBatch gb)
                 if (KIND == B_PLAIN) {
                     v = P.B.p[(long long)gk * P.B.rs + (long long)gj * P.B.cs];
                 } else if (KIND == B_SKETCH) {
-                    const double sc = P.bscale[gk];
+                    const double sc = P.bscale ? P.bscale[gk] : 1.0;
                     v = (sc == 0.0) ? 0.0 : sc * rademacher(P.seed, P.mode, gk, gj);
                 } else {
                     const int jm = gj / r2, jj2 = gj - jm * r2;
@@ -88,6 +91,26 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(GemmBatch gb)
                 for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], bb[y], acc[x][y]);
         }
         __syncthreads();
+    }
+    if (P.rpart) {
+        // residual energy of this tile: sum (ref(i,j) rscale[j] - C(i,j))^2
+        double e2 = 0.0;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int gi = i0 + ty + 16 * x;
+            if (gi >= M) continue;
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const int gj = j0 + tx + 16 * y;
+                if (gj >= N) continue;
+                const double v = P.rref[(long long)gi + P.rref_ld * gj] * (P.rscale ? P.rscale[gj] : 1.0) - acc[x][y];
+                e2 = fma(v, v, e2);
+            }
+        }
+        double* red = &As[0][0];
+        e2 = block_sum(e2, red);
+        if (t == 0) P.rpart[blockIdx.x + gridDim.x * blockIdx.y] = e2;
+        return;
     }
     long long ccs = P.ccs;
     if (P.ccs < 0) ccs = M;  // core: column stride = r1 decided on the device

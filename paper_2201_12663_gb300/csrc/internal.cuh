@@ -15,10 +15,13 @@ struct DevState {
     int m[3];           // width of the orthonormal basis Q^(l) after rank revealing
     int r[3];           // Tucker ranks (mirror of info->r)
     int piv_fail[3];    // small factorisation break-down flags
-    int pad[4];
+    int rhi[3];         // number of leading eigenvectors computed (rank candidates 0..rhi)
+    int r0[3];          // provisional rank from the eigenvalues
+    int pad[2];
     double shift[3];    // shift used for the LDL^T representation of the tridiagonal
     double trace[3];    // trace(B B^T) = ||B||_F^2
     double total[3];    // ||U^(l) normalised||_F^2
+    double rho2[3];     // ||U - Z_hi V_hi||_F^2, energy outside the rhi leading directions
 };
 
 // Counter-based sign generator for the Rademacher sketch: bit (c & 63) of
@@ -106,13 +109,19 @@ struct GemmProblem {
     const int* dNa;
     const int* dNb;
     // generated-B parameters
-    const double* bscale;      // sketch: 1/||u_nu|| per row nu of B
+    const double* bscale;      // sketch: optional scale per row nu of B (null = 1)
     uint64_t seed;
     int mode;
     const double* V2;          // KR: B(nu, j + r2 m) = xi_nu V2(j,nu) V3(m,nu)
     const double* V3;
     const double* xi;
     int ldv;
+    // residual-energy epilogue: instead of storing C, accumulate
+    // sum (ref(i,j) * rscale[j] - C(i,j))^2 per thread block into rpart[tile]
+    const double* rref;
+    long long rref_ld;
+    const double* rscale;      // null = 1
+    double* rpart;
 };
 
 struct GemmBatch {
@@ -193,14 +202,31 @@ struct RankArgs {
     rhosvd_info* info;
     DevState* st;
     int direct[3];
+    const int* kept;         // info->kept
+    int margin;              // extra candidate directions beyond the provisional rank
+};
+
+struct FinalArgs {
+    const double* V;         // rhi x R per mode, ld ldv
+    long long vstride;
+    int ldv;
+    int R;
+    double eps;
+    int ranks[3];
+    int r_max;
+    rhosvd_info* info;
+    DevState* st;
+    const double* rpart;     // residual partials per mode
+    int ntiles[3];
+    long long rpstride;
 };
 
 // ---------------------------------------------------------------- launchers (return 0 or RHOSVD_ERR_CUDA)
 int launch_gemm(GemmBatch& gb, cudaStream_t st);
 int launch_gemm_splitk(GemmBatch gb, double* part, cudaStream_t st);
 int launch_colnorms(const NormArgs& a, cudaStream_t st);
-int launch_terms(const double* norms, const double* xi, int R, double* inv, double* xin, double* xi_user,
-                 rhosvd_info* info, double* total, cudaStream_t st);
+int launch_terms(const NormArgs& na, const double* xi, double* keepf, double* xin, double* xi_user,
+                 rhosvd_info* info, double* Un, long long ustride, double* nn2, double* total, cudaStream_t st);
 int launch_identity(double* Q, int n, int ld, cudaStream_t st);
 int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, cudaStream_t st);
 int launch_hadamard(const HadArgs& a, cudaStream_t st);
@@ -216,6 +242,9 @@ int launch_tridiag(ModeMap mm, double* A, long long astride, int lda, const int*
 int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D, double* Lo,
                    double* mu, DevState* s, int nb, cudaStream_t st);
 int launch_rank(const RankArgs& a, cudaStream_t st);
+int launch_rank_final(const FinalArgs& a, cudaStream_t st);
+int launch_copy2d(const double* src, long long sstride, const int lds[3], double* const dst[3], const int ldd[3],
+                  const int* drows, const int hrows[3], const int* dcols, const int hcols[3], cudaStream_t st);
 int launch_eigvecs(ModeMap mm, const double* D, const double* Lo, const double* mu, int vstride, const int* dk,
                    const DevState* s, double* W, long long wstride, int ldw, int rmax, int nb, cudaStream_t st);
 int launch_backtransform(ModeMap mm, const double* A, long long astride, int lda, const double* tau, int vstride,
@@ -224,8 +253,13 @@ int launch_backtransform(ModeMap mm, const double* A, long long astride, int lda
 
 }  // namespace rh
 
+namespace rh {
+void count_launch();   // library-wide kernel launch counter (rhosvd_launch_count)
+}
+
 #define RH_CHECK_LAUNCH()                                   \
     do {                                                    \
+        rh::count_launch();                                 \
         cudaError_t e_ = cudaGetLastError();                \
         if (e_ != cudaSuccess) return RHOSVD_ERR_CUDA;      \
     } while (0)

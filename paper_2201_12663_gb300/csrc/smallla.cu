@@ -278,9 +278,10 @@ __global__ void k_eigvals(ModeMap mm, const double* d, const double* e, int vstr
 }
 
 // ------------------------------------------------------------------ rank rule
-// Per mode: lambda_j = max(mu_{k-1-j} - s, 0) (descending), rho^2 = max(total - trace, 0).
-// r = min r with rho^2 + sum_{j >= r} lambda_j <= eps^2 total (or the fixed rank).
-
+// Provisional rank from the eigenvalues lambda_j = max(mu_{k-1-j} - s, 0) (descending) of
+// B B^T, q = min(k, kept) of them (a side matrix has at most `kept` nonzero singular values):
+// r0 = min r with sum_{j >= r} lambda_j <= eps^2 total.  The final rule (k_rank_final) then
+// checks rank candidates 0..rhi, rhi = min(q, r0 + margin), with energies computed directly.
 __global__ void k_rank_select(RankArgs a)
 {
     const int b = threadIdx.x;
@@ -289,35 +290,111 @@ __global__ void k_rank_select(RankArgs a)
     const double* mu = a.mu + b * a.vstride;
     const double s = a.st->shift[b];
     const double total = a.total[b];
-    const double rho2 = fmax(total - a.trace[b], 0.0);
+    const int q = min(k, *a.kept);
     if (a.st->piv_fail[b]) set_status(a.info, RHOSVD_ERR_NOT_CONVERGED);
-    // tails from the smallest eigenvalue upward
-    const double thr = a.eps * a.eps * total;
-    double tail = rho2;
-    int r = k;
-    if (a.ranks[b] > 0) {
-        r = min(a.ranks[b], k);
-        for (int j = k - 1; j >= r; --j) tail += fmax(mu[k - 1 - j] - s, 0.0);
+    int r0;
+    if (total == 0.0 || q == 0 || (a.ranks[b] == 0 && a.eps >= 1.0)) {
+        r0 = 0;
+    } else if (a.ranks[b] > 0) {
+        r0 = min(a.ranks[b], q);
     } else {
-        while (r > 0) {
-            const double lam = fmax(mu[k - 1 - (r - 1)] - s, 0.0);
-            if (tail + lam <= thr) { tail += lam; --r; } else break;
+        const double thr = a.eps * a.eps * total;
+        double tail = 0.0;
+        r0 = q;
+        while (r0 > 0) {
+            const double lam = fmax(mu[k - 1 - (r0 - 1)] - s, 0.0);
+            if (tail + lam <= thr) { tail += lam; --r0; } else break;
         }
-        if (tail > thr && total > 0.0) set_status(a.info, RHOSVD_ERR_SKETCH);
     }
-    if (total == 0.0) { r = 0; tail = 0.0; }
-    int rn = r;
-    if (r > a.r_max) { set_status(a.info, RHOSVD_ERR_RANK_OVERFLOW); r = a.r_max; }
-    a.st->r[b] = r;
-    a.info->r[b] = r;
-    a.info->r_needed[b] = rn;
+    int rhi = (a.ranks[b] > 0 || r0 == 0) ? r0 : min(q, r0 + a.margin);
+    if (a.ranks[b] == 0 && a.eps >= 1.0) rhi = 0;
+    a.st->r0[b] = r0;
+    a.st->rhi[b] = rhi;
     a.info->k[b] = k;
     a.info->total[b] = total;
-    a.info->resid[b] = rho2;
-    a.info->tail[b] = sqrt(tail);
     a.info->direct[b] = a.direct[b];
     for (int j = 0; j < KMAX; ++j)
-        a.sigma[b][j] = (j < k) ? sqrt(fmax(mu[k - 1 - j] - s, 0.0)) : 0.0;
+        a.sigma[b][j] = (j < q) ? sqrt(fmax(mu[k - 1 - j] - s, 0.0)) : 0.0;
+}
+
+// Final eps-rank from directly computed energies (no cancellation):
+//   rho^2 = ||U - Z_hi V_hi||_F^2 (residual GEMM partials), c_j = ||V_hi(j,:)||^2,
+//   tail(r) = rho^2 + sum_{r <= j < rhi} c_j,  r = min r with tail(r) <= eps^2 total.
+// One block per mode.
+__global__ void k_rank_final(FinalArgs a)
+{
+    const int b = blockIdx.x;
+    const int rhi = a.st->rhi[b];
+    __shared__ double c[KMAX];
+    __shared__ double red[32];
+    const double* part = a.rpart + b * a.rpstride;
+    double s = 0.0;
+    for (int t = threadIdx.x; t < a.ntiles[b]; t += blockDim.x) s += part[t];
+    const double rho2 = block_sum(s, red);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double* V = a.V + b * a.vstride;
+    for (int j = w; j < rhi; j += nw) {
+        double e = 0.0;
+        for (int nu = lane; nu < a.R; nu += 32) {
+            const double v = V[(long long)nu * a.ldv + j];
+            e = fma(v, v, e);
+        }
+        e = warp_sum(e);
+        if (lane == 0) c[j] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double total = a.st->total[b];
+    const double thr = a.eps * a.eps * total;
+    int r;
+    if (a.ranks[b] > 0 || total == 0.0 || (a.ranks[b] == 0 && a.eps >= 1.0)) {
+        r = rhi;
+    } else {
+        double tail = rho2;
+        r = rhi;
+        if (tail > thr) {
+            set_status(a.info, RHOSVD_ERR_SKETCH);
+        } else {
+            while (r > 0 && tail + c[r - 1] <= thr) { tail += c[r - 1]; --r; }
+        }
+    }
+    const int rn = r;
+    if (r > a.r_max) { set_status(a.info, RHOSVD_ERR_RANK_OVERFLOW); r = a.r_max; }
+    double tail = rho2;
+    for (int j = r; j < rhi; ++j) tail += c[j];
+    a.st->r[b] = r;
+    a.st->rho2[b] = rho2;
+    a.info->r[b] = r;
+    a.info->r_needed[b] = rn;
+    a.info->resid[b] = rho2;
+    a.info->tail[b] = sqrt(tail);
+}
+
+// dst_b(i, j) = src_b(i, j) for i < rows_b, j < cols_b (rows/cols from the device or host).
+struct CopyArgs {
+    const double* src;
+    long long sstride;
+    int lds[3];
+    double* dst[3];
+    int ldd[3];
+    const int* drows;    // per mode or null
+    int hrows[3];
+    const int* dcols;    // per mode or null
+    int hcols[3];
+};
+
+__global__ void k_copy2d(CopyArgs a)
+{
+    const int b = blockIdx.y;
+    const int rows = a.drows ? a.drows[b] : a.hrows[b];
+    const int cols = a.dcols ? a.dcols[b] : a.hcols[b];
+    const long long total = (long long)rows * cols;
+    const double* src = a.src + b * a.sstride;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        a.dst[b][(long long)j * a.ldd[b] + i] = src[(long long)j * a.lds[b] + i];
+    }
 }
 
 // ------------------------------------------------------------------ eigenvectors
@@ -331,7 +408,7 @@ __global__ void k_eigvecs(ModeMap mm, const double* D, const double* Lo, const d
     const int b = mm.m[blockIdx.y];
     const int j = blockIdx.x * blockDim.x + threadIdx.x;   // descending index
     const int k = dk[b];
-    const int r = st->r[b];
+    const int r = st->rhi[b];
     if (j >= r || j >= k) return;
     D += b * vstride;
     Lo += b * vstride;
@@ -396,7 +473,7 @@ __global__ void k_backtransform(ModeMap mm, const double* A, long long astride, 
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int k = dk[b];
-    const int r = st->r[b];
+    const int r = st->rhi[b];
     if (warp >= r) return;
     A += b * astride;
     tau += b * vstride;
@@ -470,6 +547,34 @@ int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, co
 int launch_rank(const RankArgs& a, cudaStream_t st)
 {
     k_rank_select<<<1, 32, 0, st>>>(a);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_rank_final(const FinalArgs& a, cudaStream_t st)
+{
+    k_rank_final<<<3, 256, 0, st>>>(a);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_copy2d(const double* src, long long sstride, const int lds[3], double* const dst[3], const int ldd[3],
+                  const int* drows, const int hrows[3], const int* dcols, const int hcols[3], cudaStream_t st)
+{
+    CopyArgs a;
+    a.src = src;
+    a.sstride = sstride;
+    for (int l = 0; l < 3; ++l) {
+        a.lds[l] = lds[l];
+        a.dst[l] = dst[l];
+        a.ldd[l] = ldd[l];
+        a.hrows[l] = hrows ? hrows[l] : 0;
+        a.hcols[l] = hcols ? hcols[l] : 0;
+    }
+    a.drows = drows;
+    a.dcols = dcols;
+    dim3 grid(256, 3);
+    k_copy2d<<<grid, 256, 0, st>>>(a);
     RH_CHECK_LAUNCH();
     return 0;
 }
