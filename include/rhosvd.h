@@ -39,6 +39,7 @@ extern "C" {
 #define RHOSVD_ERR_SKETCH (-5)          /* device: sketch residual alone exceeds eps         */
 #define RHOSVD_ERR_CUDA (-6)            /* a CUDA launch/runtime call failed                 */
 #define RHOSVD_ERR_WORKSPACE (-7)       /* workspace NULL or smaller than required          */
+#define RHOSVD_ERR_SCRATCH_LIMIT (-8)   /* rhosvd_c2t_noalloc: problem exceeds the static scratch */
 
 #define RHOSVD_PLAIN_FP64 0             /* every step in FP64 on the CUDA cores              */
 
@@ -139,6 +140,30 @@ int rhosvd_cp_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, double* const U_o
  */
 int rhosvd_cp_sum(double alpha, const rhosvd_cp* a, double beta, const rhosvd_cp* b,
                   double* const U_out[3], const int ld_out[3], double* xi_out, void* stream);
+
+/* ---------------------------------------------------------------- allocation-free variant
+ * (the paper has no counterpart: this serves callers of the library, not the method)
+ *
+ * rhosvd_c2t needs a device workspace from the caller.  Callers that cannot allocate device
+ * memory -- code inside a host application that owns all device allocations, code that must
+ * not risk the device-wide synchronisation cudaMalloc/cudaFree may bring, code with no
+ * allocator at hand -- call rhosvd_c2t_noalloc instead: the same reduction, same arguments
+ * minus the workspace, with scratch space taken from one static device array of
+ * RHOSVD_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until exit.
+ *   - Problems with rhosvd_c2t_workspace_size() > RHOSVD_NOALLOC_SCRATCH_BYTES are rejected
+ *     with RHOSVD_ERR_SCRATCH_LIMIT; invalid arguments give RHOSVD_ERR_INVALID_ARG.
+ *   - The first call on a device looks the array's address up (once per device); make that
+ *     first call before any stream capture starts.
+ *   - All calls on a device share the array and it keeps the previous call's contents (the
+ *     reduction clears what it needs itself).  Calls that overlap on the GPU race on it:
+ *     serialise them.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine.  (Tracing, if switched
+ *     on with rhosvd_profile_enable, creates CUDA event objects on first use.)
+ * Inputs and outputs are as for rhosvd_c2t; the caller still provides the output buffers. */
+#define RHOSVD_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+int rhosvd_c2t_noalloc(const rhosvd_cp* cp, const rhosvd_opts* opts, const rhosvd_tucker* out,
+                       void* stream);
 
 /* ---------------------------------------------------------------- tracing (no paper
  * counterpart: observability of the library itself) */

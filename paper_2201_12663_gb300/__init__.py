@@ -29,6 +29,8 @@ RHOSVD_ERR_NONFINITE = -4
 RHOSVD_ERR_SKETCH = -5
 RHOSVD_ERR_CUDA = -6
 RHOSVD_ERR_WORKSPACE = -7
+RHOSVD_ERR_SCRATCH_LIMIT = -8
+RHOSVD_NOALLOC_SCRATCH_BYTES = 64 << 20
 RHOSVD_PLAIN_FP64 = 0
 RHOSVD_K_MAX = 256
 
@@ -95,6 +97,9 @@ def load(build_if_missing: bool = False):
         L.rhosvd_cp_sum.restype = _c.c_int
         L.rhosvd_cp_sum.argtypes = [_c.c_double, _c.POINTER(rhosvd_cp), _c.c_double, _c.POINTER(rhosvd_cp),
                                     _c.c_void_p * 3, _c.c_int * 3, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_c2t_noalloc.restype = _c.c_int
+        L.rhosvd_c2t_noalloc.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts), _c.POINTER(rhosvd_tucker),
+                                         _c.c_void_p]
         L.rhosvd_launch_count.restype = _c.c_longlong
         L.rhosvd_profile_enable.restype = _c.c_int
         L.rhosvd_profile_enable.argtypes = [_c.c_int]
@@ -272,6 +277,21 @@ def rhosvd_c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0
                       _c.c_size_t(workspace.numel()), _stream_handle(stream))
     if rc != RHOSVD_OK:
         raise RhosvdError(rc, "rhosvd_c2t")
+    return out
+
+
+def rhosvd_c2t_noalloc(U, xi, out, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0,
+                       stream=None) -> TuckerResult:
+    """rhosvd_c2t without a workspace argument, for callers that cannot allocate device memory:
+    the library uses its own static scratch array (RHOSVD_NOALLOC_SCRATCH_BYTES).  `out` must
+    be provided (see alloc_tucker); this function allocates nothing."""
+    L = load()
+    cp = make_cp(U, xi)
+    opts = make_opts(eps, ranks, r_max, oversample, seed)
+    t = tucker_struct(out)
+    rc = L.rhosvd_c2t_noalloc(_c.byref(cp), _c.byref(opts), _c.byref(t), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_c2t_noalloc")
     return out
 
 

@@ -226,6 +226,8 @@ extern "C" const char* rhosvd_strerror(int code)
     case RHOSVD_ERR_SKETCH: return "the range sketch missed more energy than eps allows (raise oversample or r_max)";
     case RHOSVD_ERR_CUDA: return "CUDA runtime or launch error";
     case RHOSVD_ERR_WORKSPACE: return "workspace missing or too small";
+    case RHOSVD_ERR_SCRATCH_LIMIT:
+        return "problem needs more scratch than the static buffer of rhosvd_c2t_noalloc holds (use rhosvd_c2t)";
     default: return "unknown status";
     }
 }
