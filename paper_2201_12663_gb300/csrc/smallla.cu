@@ -218,63 +218,78 @@ __device__ inline int negcount(const double* D, const double* Lo, int k, double 
     return c;
 }
 
-// LDL^T = T + s I with s > 0 doubled until every pivot is positive; then bisection for every
-// eigenvalue mu_a (ascending) of L D L^T.  Writes D, Lo, mu and the shift s.
-__global__ void k_eigvals(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D,
-                          double* Lo, double* mu, DevState* st)
+// LDL^T = T + s I with s > 0 multiplied by 4 until every pivot is positive (one thread per
+// mode).  Writes D, Lo, the shift s and an upper bound of the spectrum of L D L^T.
+__global__ void k_ldl(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D,
+                      double* Lo, DevState* st)
 {
     const int b = mm.m[blockIdx.x];
+    if (threadIdx.x != 0) return;
     const int k = dk[b];
     d += b * vstride;
     e += b * vstride;
     D += b * vstride;
     Lo += b * vstride;
-    mu += b * vstride;
-    __shared__ double s_hi;
-    __shared__ double Dsh[KMAX], Lsh[KMAX];
-    if (threadIdx.x == 0) {
-        double tnorm = 0.0;
+    double tnorm = 0.0;
+    for (int i = 0; i < k; ++i) {
+        double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
+        tnorm = fmax(tnorm, r);
+    }
+    double s = fmax(4.0 * k * DBL_EPSILON * tnorm, DBL_MIN);
+    bool ok = false;
+    for (int tries = 0; tries < 60 && !ok; ++tries) {
+        ok = true;
+        double Dc = d[0] + s;
         for (int i = 0; i < k; ++i) {
-            double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
-            tnorm = fmax(tnorm, r);
-        }
-        double s = fmax(4.0 * k * DBL_EPSILON * tnorm, DBL_MIN);
-        bool ok = false;
-        for (int tries = 0; tries < 60 && !ok; ++tries) {
-            ok = true;
-            double Dc = d[0] + s;
-            for (int i = 0; i < k; ++i) {
-                if (!(Dc > 0.0)) { ok = false; break; }
-                Dsh[i] = Dc;
-                if (i + 1 < k) {
-                    const double l = e[i] / Dc;
-                    Lsh[i] = l;
-                    Dc = d[i + 1] + s - l * e[i];
-                }
+            if (!(Dc > 0.0)) { ok = false; break; }
+            D[i] = Dc;
+            if (i + 1 < k) {
+                const double l = e[i] / Dc;
+                Lo[i] = l;
+                Dc = d[i + 1] + s - l * e[i];
+            } else {
+                Lo[i] = 0.0;
             }
-            if (!ok) s *= 4.0;
         }
-        if (!ok) st->piv_fail[b] = 1;
-        double hi = 0.0;
-        for (int i = 0; i < k; ++i) {
-            double r = d[i] + s + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
-            hi = fmax(hi, r);
-        }
-        s_hi = hi * (1.0 + 8.0 * DBL_EPSILON) + DBL_MIN;
-        st->shift[b] = s;
+        if (!ok) s *= 4.0;
+    }
+    if (!ok) st->piv_fail[b] = 1;
+    double hi = 0.0;
+    for (int i = 0; i < k; ++i) {
+        double r = d[i] + s + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
+        hi = fmax(hi, r);
+    }
+    st->shift[b] = s;
+    st->specmax[b] = hi * (1.0 + 8.0 * DBL_EPSILON) + DBL_MIN;
+}
+
+// Bisection for eigenvalue a (ascending) of L D L^T: one thread per eigenvalue, spread over
+// many small blocks so that the long dependent chains of FP64 divisions run on many SMs.
+// grid: (ceil(KMAX / EIG_PER_BLOCK), nmodes), block: 32 threads, EIG_PER_BLOCK of them busy.
+constexpr int EIG_PER_BLOCK = 4;
+
+__global__ void k_bisect(ModeMap mm, const double* Dg, const double* Lg, int vstride, const int* dk,
+                         double* mu, const DevState* st)
+{
+    const int b = mm.m[blockIdx.y];
+    const int k = dk[b];
+    const int a = blockIdx.x * EIG_PER_BLOCK + threadIdx.x;
+    __shared__ double Dsh[KMAX], Lsh[KMAX];
+    if (blockIdx.x * EIG_PER_BLOCK >= k) return;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        Dsh[i] = Dg[b * vstride + i];
+        Lsh[i] = Lg[b * vstride + i];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < k; i += blockDim.x) { D[i] = Dsh[i]; Lo[i] = (i + 1 < k) ? Lsh[i] : 0.0; }
-    for (int a = threadIdx.x; a < k; a += blockDim.x) {
-        double lo = 0.0, hi = s_hi;
-        for (int it = 0; it < 400; ++it) {
-            if (hi - lo <= 2.0 * DBL_EPSILON * hi) break;
-            double mid = (lo > 0.0 && hi > 2.0 * lo) ? sqrt(lo) * sqrt(hi) : 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi) break;
-            if (negcount(Dsh, Lsh, k, mid) <= a) lo = mid; else hi = mid;
-        }
-        mu[a] = 0.5 * (lo + hi);
+    if (threadIdx.x >= EIG_PER_BLOCK || a >= k) return;
+    double lo = 0.0, hi = st->specmax[b];
+    for (int it = 0; it < 400; ++it) {
+        if (hi - lo <= 2.0 * DBL_EPSILON * hi) break;
+        double mid = (lo > 0.0 && hi > 2.0 * lo) ? sqrt(lo) * sqrt(hi) : 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (negcount(Dsh, Lsh, k, mid) <= a) lo = mid; else hi = mid;
     }
+    mu[b * vstride + a] = 0.5 * (lo + hi);
 }
 
 // ------------------------------------------------------------------ rank rule
@@ -539,7 +554,10 @@ int launch_tridiag(ModeMap mm, double* A, long long astride, int lda, const int*
 int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D, double* Lo,
                    double* mu, DevState* s, int nb, cudaStream_t st)
 {
-    k_eigvals<<<nb, KMAX, 0, st>>>(mm, d, e, vstride, dk, D, Lo, mu, s);
+    k_ldl<<<nb, 32, 0, st>>>(mm, d, e, vstride, dk, D, Lo, s);
+    RH_CHECK_LAUNCH();
+    dim3 grid((KMAX + EIG_PER_BLOCK - 1) / EIG_PER_BLOCK, nb);
+    k_bisect<<<grid, 32, 0, st>>>(mm, D, Lo, vstride, dk, mu, s);
     RH_CHECK_LAUNCH();
     return 0;
 }
