@@ -32,7 +32,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(workload="hadamard_n1024_R64x64", n=1024, Ra=64, Rb=64, seeds=[0, 1], eps=1e-7,
-                r_max=160, oversample=32, grid="[-10,10]^3 cell centres", precision="plain_fp64")
+                r_max=160, oversample=32, grid="[-10,10]^3 cell centres")
+PRECISIONS = {"mixed": 1, "plain": 0}
+# tensor-core digit-plane products per FP64-class product in the mixed form (6-digit operands:
+# pairs with s + t <= 7; the sketch has a +-1 operand: 6; the core uses 4 digits: 10)
+MIXED_PAIRS = {"sketch": 6, "project": 21, "v_hi": 21, "residual": 21,
+               "core": 10}
 METRIC = "RHOSVD reductions/s at stated rel. err: mixed/learned vs FP64 plain, 1×GB300"
 UNIT = "reductions/s"
 FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (CUDA-core and tensor) rate
@@ -169,7 +174,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {**WORKLOAD, "l2": "n/a (CPU)"}, "cpu_baseline": cpu, "samples_timed": len(t_steps),
+            "config": {**WORKLOAD, "precision": "oracle fp64", "l2": "n/a (CPU)"}, "cpu_baseline": cpu,
+            "samples_timed": len(t_steps),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -192,10 +198,26 @@ def algorithmic_flops(stage, info, n, R):
         return sum(2.0 * k[l] * k[l] * R for l in range(3))
     if stage == "v_hi":
         return sum(2.0 * min(k[l], r[l] + 16) * k[l] * R for l in range(3))
+    if stage == "cholqr_gram":
+        kk = WORKLOAD["r_max"] + WORKLOAD["oversample"]
+        return 3 * sum(2.0 * kk * kk * n for _ in range(3))
     return None
 
 
+def tucker_rel_diff_torch(beta_a, Z_a, beta_b, Z_b):
+    """||T_a - T_b|| / ||T_b|| for orthonormal Tucker factors, via a common basis per mode
+    (measurement aid for the bench line; torch linear algebra, not the product path)."""
+    import torch
+    ca, cb = beta_a, beta_b
+    for l in range(3):
+        Pm, _ = torch.linalg.qr(torch.cat([Z_a[l], Z_b[l]], dim=1))
+        ca = torch.movedim(torch.tensordot(Pm.T @ Z_a[l], ca, dims=([1], [l])), 0, l)
+        cb = torch.movedim(torch.tensordot(Pm.T @ Z_b[l], cb, dims=([1], [l])), 0, l)
+    return (torch.linalg.norm(ca - cb) / torch.linalg.norm(cb)).item()
+
+
 def run_ours(args):
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -214,7 +236,6 @@ def run_ours(args):
     A, B = workloads.hartree_like_factors(WORKLOAD["n"], WORKLOAD["Ra"], WORKLOAD["Rb"], WORKLOAD["seeds"])
     n, Ra, Rb = WORKLOAD["n"], WORKLOAD["Ra"], WORKLOAD["Rb"]
     R = Ra * Rb
-    import numpy as np
     # pinned host inputs (column-major factor storage = (R, n) row-major)
     hA = [torch.from_numpy(np.ascontiguousarray(u.T)).pin_memory() for u in A.U]
     hB = [torch.from_numpy(np.ascontiguousarray(u.T)).pin_memory() for u in B.U]
@@ -227,54 +248,76 @@ def run_ours(args):
     Ub = [t.t() for t in dB]
     Uc = [torch.empty(R, n, dtype=torch.float64, device=dev).t() for _ in range(3)]
     xc = torch.empty(R, dtype=torch.float64, device=dev)
-    opts = dict(eps=WORKLOAD["eps"], r_max=WORKLOAD["r_max"], oversample=WORKLOAD["oversample"], seed=12345)
-    cp = P.make_cp(Uc, xc)
-    ws = torch.empty(P.rhosvd_c2t_workspace_size(cp, P.make_opts(**opts)), dtype=torch.uint8, device=dev)
-    out = P.alloc_tucker([n, n, n], R, WORKLOAD["r_max"], dev)
     flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)   # 256 MB > L2
-
-    def step():
-        P.rhosvd_cp_hadamard(Ua, xa, Ub, xb, U_out=Uc, xi_out=xc)
-        P.rhosvd_c2t(Uc, xc, out=out, workspace=ws, **opts)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    info = out.info()
-    assert info.status == 0, P.rhosvd_strerror(info.status)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- device-resident timing (per-step events, L2 flushed between steps)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    def make_form(prec):
+        opts = dict(eps=WORKLOAD["eps"], r_max=WORKLOAD["r_max"], oversample=WORKLOAD["oversample"], seed=12345,
+                    precision=PRECISIONS[prec])
+        cp = P.make_cp(Uc, xc)
+        ws = torch.empty(P.rhosvd_c2t_workspace_size(cp, P.make_opts(**opts)), dtype=torch.uint8, device=dev)
+        out = P.alloc_tucker([n, n, n], R, WORKLOAD["r_max"], dev)
+
+        def step():
+            P.rhosvd_cp_hadamard(Ua, xa, Ub, xb, U_out=Uc, xi_out=xc)
+            P.rhosvd_c2t(Uc, xc, out=out, workspace=ws, **opts)
+        return step, out, ws
+
+    def time_form(step, out, steps, profile):
+        for _ in range(max(args.warmup, 3)):
+            step()
+        info = out.info()
+        if info.status != 0:
+            raise RuntimeError(P.rhosvd_strerror(info.status))
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        barrier()
+        P.rhosvd_profile_read()
+        P.rhosvd_profile_enable(profile)
+        l0 = P.rhosvd_launch_count()
+        for i in range(steps):
+            flush.zero_()
+            starts[i].record()
+            step()
+            ends[i].record()
+        barrier()
+        launches = P.rhosvd_launch_count() - l0
+        P.rhosvd_profile_enable(False)
+        prof = P.rhosvd_profile_read()
+        tot = torch.tensor([sum(s.elapsed_time(e) for s, e in zip(starts, ends))], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+        return tot.item() / steps, prof, launches, out.info()
+
+    main_prec = args.precision
+    other = "plain" if main_prec == "mixed" else "mixed"
+    step, out, ws = make_form(main_prec)
     sampler = ClockSampler(local)
     barrier()
     sampler.start()
-    P.rhosvd_profile_read()
-    P.rhosvd_profile_enable(True)
-    l0 = P.rhosvd_launch_count()
     t_wall = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        starts[i].record()
-        step()
-        ends[i].record()
-    barrier()
+    ms_per_step, prof, launches, info = time_form(step, out, args.steps, True)
     t_wall = time.perf_counter() - t_wall
-    launches = P.rhosvd_launch_count() - l0
-    P.rhosvd_profile_enable(False)
-    prof = P.rhosvd_profile_read()
     clocks = sampler.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    tot = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    ms_per_step = tot.item() / args.steps
     value = world * 1000.0 / ms_per_step
-    info = out.info()
+
+    # the other form, same run, same inputs (comparison; not the headline)
+    step2, out2, ws2 = make_form(other)
+    ms2, prof2, _, info2 = time_form(step2, out2, max(3, args.steps // 2), False)
+
+    # agreement of the two forms (Tucker tensors), computed on the device with torch
+    def tucker_of(res):
+        inf = res.info()
+        r = [inf.r[l] for l in range(3)]
+        beta = res.beta[: r[0] * r[1] * r[2]].reshape(r[2], r[1], r[0]).permute(2, 1, 0)
+        return beta, [res.Z[l][:, : r[l]] for l in range(3)], r
+    bm, Zm, rm = tucker_of(out)
+    bp, Zp, rp = tucker_of(out2)
+    agree = tucker_rel_diff_torch(bm, Zm, bp, Zp)     # common basis per mode: ranks may differ
 
     # ---- end to end through the C ABI: H2D inputs, hot path, D2H result, per step
     e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -306,32 +349,55 @@ def run_ours(args):
         e_e[i].record()
         d2h = hinfo.numel() + sum(z.numel() * 8 for z in hZ) + hsig.numel() * 8 + cnt * 8
     barrier()
-    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / args.steps
+    e2e_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(e_s, e_e)) / args.steps
     te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = world * 1000.0 / te.item()
 
     # ---- roofline of the dominant stage (largest share of the timed region)
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    total_ms = sum(v[1] for v in prof.values()) if prof else 0.0
+    shares = {k: round(v[1] / total_ms, 4) for k, v in prof.items()} if prof else {}
     roof = None
-    shares = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()} if prof else {}
-    if dom:
-        name, (cnt, ms_tot) = dom
+    if prof:
+        name, (cnt, ms_tot) = max(prof.items(), key=lambda kv: kv[1][1])
         avg_ms = ms_tot / cnt
         fl = algorithmic_flops(name, info, n, R)
-        if fl is not None:
+        pk = peaks()
+        if fl is not None and main_prec == "mixed" and name in MIXED_PAIRS:
             ach = fl / (avg_ms * 1e-3) / 1e12
-            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "GB300 nominal FP64 rate (1.25 TFLOP/s); MEASURED_PEAKS.json has no FP64 entry",
+            bf16 = pk.get("bf16_tflops", 1912.0)
+            roof = {"bound": "tensor", "kernel": name, "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+                    "frac": ach / bf16, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
+                    "tensor_pipe_frac": ach * MIXED_PAIRS[name] / bf16,
+                    "note": f"achieved counts FP64-class flops 2MNK; the tensor pipe executes "
+                            f"{MIXED_PAIRS[name]} BF16 digit-plane products per FP64 product",
                     "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": fl}
+        elif fl is not None:
+            ach = fl / (avg_ms * 1e-3) / 1e12
+            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "GB300 nominal FP64 rate 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 entry)",
+                    "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": fl}
+        else:
+            roof = {"bound": "alu", "kernel": name, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None,
+                    "note": "dominant stage is a single-block FP64 factorisation (latency bound); no flop model",
+                    "avg_launch_ms": avg_ms}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {**WORKLOAD, "l2": "flushed (256 MB write) before every timed step",
+            "vs_baseline": None, "dtype": "f64 (mixed: bf16 digit planes, fp32 accumulate)" if main_prec == "mixed"
+            else "f64", "data": "synthetic",
+            "config": {**WORKLOAD, "precision": main_prec,
+                       "l2": "flushed (256 MB write) before every timed step",
                        "ranks": [info.r[l] for l in range(3)], "k": [info.k[l] for l in range(3)],
                        "tails": [info.tail[l] for l in range(3)]},
+            "error": {"vs": f"{other} GPU form, same sketch", "tucker_rel_diff": agree,
+                      "ranks_other": [info2.r[l] for l in range(3)]},
+            f"{other}_form": {"value": world * 1000.0 / ms2, "ms_per_step": ms2,
+                              "stage_ms_per_step": {k: v[1] / max(3, args.steps // 2) for k, v in prof2.items()}},
+            "speedup_vs_other_form": ms2 / ms_per_step,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "stage_shares": shares,
             "stage_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
@@ -354,6 +420,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["mixed", "plain"], default="mixed")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

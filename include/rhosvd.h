@@ -40,8 +40,15 @@ extern "C" {
 #define RHOSVD_ERR_CUDA (-6)            /* a CUDA launch/runtime call failed                 */
 #define RHOSVD_ERR_WORKSPACE (-7)       /* workspace NULL or smaller than required          */
 #define RHOSVD_ERR_SCRATCH_LIMIT (-8)   /* rhosvd_c2t_noalloc: problem exceeds the static scratch */
+#define RHOSVD_ERR_TIMEOUT (-9)         /* device: a bounded wait inside a kernel gave up      */
 
 #define RHOSVD_PLAIN_FP64 0             /* every step in FP64 on the CUDA cores              */
+#define RHOSVD_MIXED 1                  /* the large contractions (range sketch, projection, Ritz
+                                           vectors, residual, core) on the tcgen05 tensor cores
+                                           with exact 8-bit BF16 digit planes and FP32 accumulation
+                                           read back into double-float (about 2^-40 of sum|a||b|);
+                                           the Grams (they square the condition number) and the
+                                           small factorisations stay FP64                      */
 
 #define RHOSVD_K_MAX 256                /* largest subspace width k handled on the device    */
 
@@ -62,7 +69,7 @@ typedef struct rhosvd_opts {
     int ranks[3];           /* > 0: fixed r_l = min(ranks[l], rank bound); 0: use eps     */
     int r_max;              /* capacity of the outputs; 1 <= r_max <= RHOSVD_K_MAX        */
     int oversample;         /* sketch columns beyond r_max (k = r_max + oversample)       */
-    int precision;          /* RHOSVD_PLAIN_FP64                                          */
+    int precision;          /* RHOSVD_PLAIN_FP64 or RHOSVD_MIXED                          */
     unsigned long long seed;/* seed of the counter-based sketch generator                 */
 } rhosvd_opts;
 

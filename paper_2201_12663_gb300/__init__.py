@@ -32,6 +32,8 @@ RHOSVD_ERR_WORKSPACE = -7
 RHOSVD_ERR_SCRATCH_LIMIT = -8
 RHOSVD_NOALLOC_SCRATCH_BYTES = 64 << 20
 RHOSVD_PLAIN_FP64 = 0
+RHOSVD_MIXED = 1
+RHOSVD_ERR_TIMEOUT = -9
 RHOSVD_K_MAX = 256
 
 _c = ctypes
@@ -259,12 +261,13 @@ def tucker_struct(res: TuckerResult) -> rhosvd_tucker:
 
 
 def rhosvd_c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0, out=None,
-               workspace=None, stream=None, with_V=False, with_xi=False) -> TuckerResult:
+               workspace=None, stream=None, with_V=False, with_xi=False,
+               precision=RHOSVD_PLAIN_FP64) -> TuckerResult:
     """RHOSVD canonical-to-Tucker transform of the CP tensor (U[0], U[1], U[2], xi)."""
     torch = _torch()
     L = load()
     cp = make_cp(U, xi)
-    opts = make_opts(eps, ranks, r_max, oversample, seed)
+    opts = make_opts(eps, ranks, r_max, oversample, seed, precision)
     need = int(L.rhosvd_c2t_workspace_size(_c.byref(cp), _c.byref(opts)))
     if need == 0:
         raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_c2t_workspace_size")

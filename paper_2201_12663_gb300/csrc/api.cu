@@ -2,6 +2,7 @@
 // ordered launch sequence of the canonical-to-Tucker transform (Def. 2.2, Prop. 2.2).
 // Every rank decision is taken on the device; the host never synchronises inside a call.
 #include "internal.cuh"
+#include "ozgemm.cuh"
 #include <atomic>
 #include <mutex>
 #include <stdio.h>
@@ -117,6 +118,12 @@ struct Plan {
     int ks_sketch, ks_gram, ks_bbt;
     size_t o_state, o_norms, o_keep, o_nn2, o_Un, o_xin, o_bufA, o_bufB, o_G, o_L, o_perm, o_B, o_vec, o_W, o_V, o_Z, o_rp,
         o_part;
+    // mixed-precision form: digit planes and helpers
+    int mixed;
+    int ldR, ldn, ldk;            // plane row lengths (multiples of 8) for K = R, n, k
+    size_t o_pU1, o_pU2, o_pP1, o_pP2, o_eU1, o_eU2, o_eP1, o_eP2, o_Vt;
+    long long EX;         // per-mode stride of the per-row exponent arrays
+    long long sU1, sU2, sP1, sP2; // per-mode plane-set sizes (elements)
     long long rp_stride;   // residual partials per mode (tiles of the residual GEMM)
     size_t total;
 };
@@ -138,7 +145,7 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
     if (!cp || !o) return RHOSVD_ERR_INVALID_ARG;
     if (cp->R < 0) return RHOSVD_ERR_INVALID_ARG;
     if (o->r_max < 1 || o->r_max > KMAX || o->oversample < 0) return RHOSVD_ERR_INVALID_ARG;
-    if (o->precision != RHOSVD_PLAIN_FP64) return RHOSVD_ERR_INVALID_ARG;
+    if (o->precision != RHOSVD_PLAIN_FP64 && o->precision != RHOSVD_MIXED) return RHOSVD_ERR_INVALID_ARG;
     if (!(o->eps >= 0.0)) return RHOSVD_ERR_INVALID_ARG;
     memset(p, 0, sizeof(*p));
     p->R = cp->R;
@@ -200,6 +207,33 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
     p->rp_stride = (long long)((p->NQ + 63) / 64) * ((R + 63) / 64);
     p->o_rp = take(sizeof(double) * 3 * (size_t)p->rp_stride);
     p->o_part = take(sizeof(double) * (size_t)part);
+    p->mixed = (o->precision == RHOSVD_MIXED);
+    if (p->mixed) {
+        auto up8 = [](long long x) { return (int)((x + 7) / 8 * 8); };
+        p->ldR = up8(R);
+        p->ldn = up8(p->NQ);
+        p->ldk = up8(p->KW);
+        p->sU1 = 6LL * p->NQ * p->ldR;
+        p->sU2 = 6LL * R * p->ldn;
+        long long a1 = (long long)R * p->ldk, a2 = (long long)p->KW * p->ldR;
+        p->sP1 = 6LL * (a1 > a2 ? a1 : a2);
+        long long b1 = (long long)p->KW * p->ldn, b2 = (long long)p->KW * p->ldk, b3 = (long long)p->NQ * p->ldk;
+        long long bm = b1 > b2 ? b1 : b2;
+        bm = bm > b3 ? bm : b3;
+        bm = bm > a2 ? bm : a2;
+        p->sP2 = 6LL * bm;
+        p->o_pU1 = take(sizeof(uint16_t) * 3 * (size_t)p->sU1);
+        p->o_pU2 = take(sizeof(uint16_t) * 3 * (size_t)p->sU2);
+        p->o_pP1 = take(sizeof(uint16_t) * 3 * (size_t)p->sP1);
+        p->o_pP2 = take(sizeof(uint16_t) * 3 * (size_t)p->sP2);
+        long long ex = p->NQ > R ? p->NQ : R;
+        p->EX = ex > p->KW ? ex : p->KW;
+        p->o_eU1 = take(3 * (size_t)p->EX);
+        p->o_eU2 = take(3 * (size_t)p->EX);
+        p->o_eP1 = take(3 * (size_t)p->EX);
+        p->o_eP2 = take(3 * (size_t)p->EX);
+        p->o_Vt = take(sizeof(double) * 3 * (size_t)R * p->KW);
+    }
     p->total = off;
     return RHOSVD_OK;
 }
@@ -226,6 +260,7 @@ extern "C" const char* rhosvd_strerror(int code)
     case RHOSVD_ERR_SKETCH: return "the range sketch missed more energy than eps allows (raise oversample or r_max)";
     case RHOSVD_ERR_CUDA: return "CUDA runtime or launch error";
     case RHOSVD_ERR_WORKSPACE: return "workspace missing or too small";
+    case RHOSVD_ERR_TIMEOUT: return "a bounded wait inside a kernel gave up";
     case RHOSVD_ERR_SCRATCH_LIMIT:
         return "problem needs more scratch than the static buffer of rhosvd_c2t_noalloc holds (use rhosvd_c2t)";
     default: return "unknown status";
@@ -291,6 +326,19 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     double* vmu = vec + 15 * vs;
     const long long VS = (long long)KW * (R > 0 ? R : 1);
     const long long US = (long long)p.NQ * (R > 0 ? R : 1);   // normalised side matrix per mode
+    const bool mixed = p.mixed != 0;
+    uint16_t* pU1 = mixed ? (uint16_t*)(ws + p.o_pU1) : nullptr;     // U planes, rows x, k = nu
+    uint16_t* pU2 = mixed ? (uint16_t*)(ws + p.o_pU2) : nullptr;     // U planes, rows nu, k = x
+    uint16_t* pP1 = mixed ? (uint16_t*)(ws + p.o_pP1) : nullptr;
+    uint16_t* pP2 = mixed ? (uint16_t*)(ws + p.o_pP2) : nullptr;
+    // per-row exponents of the digit planes (one array per plane buffer, stride EX per mode)
+    signed char* eU1 = mixed ? (signed char*)(ws + p.o_eU1) : nullptr;
+    signed char* eU2 = mixed ? (signed char*)(ws + p.o_eU2) : nullptr;
+    signed char* eP1 = mixed ? (signed char*)(ws + p.o_eP1) : nullptr;
+    signed char* eP2 = mixed ? (signed char*)(ws + p.o_eP2) : nullptr;
+    const long long EX = mixed ? p.EX : 0;
+    double* Vt = mixed ? (double*)(ws + p.o_Vt) : nullptr;
+    int* ozerr = &out->info->status;
 
     // ---- reset outputs and state
     if (cudaMemsetAsync(out->info, 0, sizeof(rhosvd_info), st) != cudaSuccess) return RHOSVD_ERR_CUDA;
@@ -328,6 +376,44 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
         }
     }
 
+    if (mixed && R > 0) {
+        // digit planes of the normalised side matrices: rows nu (k = x) for the projection, and
+        // rows x (k = nu) for the range sketch, each row with its own exponent
+        OzSliceArgs sa;
+        memset(&sa, 0, sizeof(sa));
+        sa.S = 6;
+        for (int l = 0; l < 3; ++l) {
+            sa.X[l] = Un + l * US;
+            sa.rs[l] = p.n[l];
+            sa.cs[l] = 1;
+            sa.rows[l] = R;
+            sa.K[l] = p.n[l];
+            sa.planes[l] = pU2 + l * p.sU2;
+            sa.pstride[l] = (long long)R * p.ldn;
+            sa.ld[l] = p.ldn;
+            sa.exps[l] = eU2 + l * EX;
+        }
+        STAGE("slice_u", launch_oz_slice(sa, 3, st));
+        if (nsk > 0) {
+            OzSliceArgs sb;
+            memset(&sb, 0, sizeof(sb));
+            sb.S = 6;
+            for (int b = 0; b < nsk; ++b) {
+                const int l = sk.m[b];
+                sb.X[b] = Un + l * US;
+                sb.rs[b] = 1;
+                sb.cs[b] = p.n[l];
+                sb.rows[b] = p.n[l];
+                sb.K[b] = R;
+                sb.planes[b] = pU1 + l * p.sU1;
+                sb.pstride[b] = (long long)p.n[l] * p.ldR;
+                sb.ld[b] = p.ldR;
+                sb.exps[b] = eU1 + l * EX;
+            }
+            STAGE("slice_u", launch_oz_slice(sb, nsk, st));
+        }
+    }
+
     if (nsk > 0 && R > 0) {
         // ---- a2: range sketch Y = U diag(1/||u||) Omega (Rademacher), Y in bufA
         GemmBatch gb;
@@ -349,7 +435,28 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             g.mode = l;
             gb.p[b] = g;
         }
-        STAGE("sketch", launch_gemm_splitk(gb, part, st));
+        if (mixed) {
+            OzBatch ob;
+            memset(&ob, 0, sizeof(ob));
+            ob.nbatch = nsk;
+            ob.err = ozerr;
+            for (int b = 0; b < nsk; ++b) {
+                const int l = sk.m[b];
+                OzProblem& q = ob.p[b];
+                q.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, eU1 + l * EX, 0};
+                q.M = p.n[l];
+                q.N = p.kin[l];
+                q.K = R;
+                q.C = bufA + l * NK;
+                q.crs = 1;
+                q.ccs = p.n[l];
+                q.seed = opts->seed;
+                q.mode = l;
+            }
+            STAGE("sketch", launch_ozgemm(ob, OZ_SKETCH, st));
+        } else {
+            STAGE("sketch", launch_gemm_splitk(gb, part, st));
+        }
 
         // ---- a3: CholeskyQR with pivoting, three passes: Y -> Q1 (bufB) -> Q2 (bufA) -> Q (bufB)
         const double tols[3] = {1e-15, 1e-11, 0.0};
@@ -377,6 +484,8 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 if (pass > 0) { g.dM = &S->m[l]; g.dN = &S->m[l]; }
                 g2.p[b] = g;
             }
+            // Grams stay FP64: they square the condition number, and the directions at the eps
+            // boundary sit ~1e-13 below the largest ones
             STAGE("cholqr_gram", launch_gemm_splitk(g2, part, st));
             const int* dk = (pass == 0) ? S->kin : S->m;
             STAGE("cholqr_chol", launch_chol(sk, G, KK, KW, dk, L, KK, KW, perm, KW, S->m, S->piv_fail, pivots[pass],
@@ -420,7 +529,41 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             g.K = p.n[l];
             gb.p[l] = g;
         }
-        STAGE("project", launch_gemm(gb, st));
+        if (mixed) {
+            OzSliceArgs sq;
+            memset(&sq, 0, sizeof(sq));
+            sq.S = 6;
+            OzBatch ob;
+            memset(&ob, 0, sizeof(ob));
+            ob.nbatch = 3;
+            ob.err = ozerr;
+            for (int l = 0; l < 3; ++l) {
+                sq.X[l] = Qfin[l];
+                sq.rs[l] = ldq[l];
+                sq.cs[l] = 1;
+                sq.rows[l] = p.kin[l];
+                sq.drows[l] = &S->m[l];
+                sq.K[l] = p.n[l];
+                sq.planes[l] = pP2 + l * p.sP2;
+                sq.pstride[l] = (long long)p.kin[l] * p.ldn;
+                sq.ld[l] = p.ldn;
+                sq.exps[l] = eP2 + l * EX;
+                OzProblem& q = ob.p[l];
+                q.A = OzPlanes{pU2 + l * p.sU2, (long long)R * p.ldn, p.ldn, eU2 + l * EX, 0};
+                q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.kin[l] * p.ldn, p.ldn, eP2 + l * EX, 0};
+                q.M = R;
+                q.N = p.kin[l];
+                q.dN = &S->m[l];
+                q.K = p.n[l];
+                q.C = Bm + (size_t)l * KW * R;
+                q.crs = KW;
+                q.ccs = 1;
+            }
+            STAGE("project_slice", launch_oz_slice(sq, 3, st));
+            STAGE("project", launch_ozgemm(ob, OZ_F64_STORE, st));
+        } else {
+            STAGE("project", launch_gemm(gb, st));
+        }
 
         // ---- a5: M = B B^T (m_l x m_l), trace, tridiagonal form, eigenvalues
         GemmBatch gm;
@@ -443,7 +586,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             g.dN = &S->m[l];
             gm.p[l] = g;
         }
-        STAGE("gram_bbt", launch_gemm_splitk(gm, part, st));
+        STAGE("gram_bbt", launch_gemm_splitk(gm, part, st));   // FP64 in both forms (see above)
     }
     if (R == 0 && cudaMemsetAsync(G, 0, sizeof(double) * 3 * KK, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
     STAGE("trace", launch_trace(all, G, KK, KW, S->m, S->trace, 3, st));
@@ -522,8 +665,99 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             gr.p[l] = e;
         }
         STAGE("z_hi", launch_gemm(gz, st));
-        STAGE("v_hi", launch_gemm(gv, st));
-        STAGE("residual", launch_gemm(gr, st));
+        if (mixed) {
+            // V_hi (rhi x R, ld KW) = W^T B: rows nu of B (k = i) times rows j of W (k = i)
+            OzSliceArgs s1, s2;
+            memset(&s1, 0, sizeof(s1));
+            memset(&s2, 0, sizeof(s2));
+            s1.S = s2.S = 6;
+            OzBatch ob;
+            memset(&ob, 0, sizeof(ob));
+            ob.nbatch = 3;
+            ob.err = ozerr;
+            for (int l = 0; l < 3; ++l) {
+                s1.X[l] = Bm + (size_t)l * KW * R;
+                s1.rs[l] = KW;
+                s1.cs[l] = 1;
+                s1.rows[l] = R;
+                s1.K[l] = p.kin[l];
+                s1.dK[l] = &S->m[l];
+                s1.planes[l] = pP1 + l * p.sP1;
+                s1.pstride[l] = (long long)R * p.ldk;
+                s1.ld[l] = p.ldk;
+                s2.X[l] = W + l * KK;
+                s2.rs[l] = KW;
+                s2.cs[l] = 1;
+                s2.rows[l] = p.kin[l];
+                s2.drows[l] = &S->rhi[l];
+                s2.K[l] = p.kin[l];
+                s2.dK[l] = &S->m[l];
+                s2.planes[l] = pP2 + l * p.sP2;
+                s2.pstride[l] = (long long)p.kin[l] * p.ldk;
+                s2.ld[l] = p.ldk;
+                s1.exps[l] = eP1 + l * EX;
+                s2.exps[l] = eP2 + l * EX;
+                OzProblem& q = ob.p[l];
+                q.A = OzPlanes{pP1 + l * p.sP1, (long long)R * p.ldk, p.ldk, eP1 + l * EX, 0};
+                q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.kin[l] * p.ldk, p.ldk, eP2 + l * EX, 0};
+                q.M = R;
+                q.N = p.kin[l];
+                q.dN = &S->rhi[l];
+                q.K = p.kin[l];
+                q.dK = &S->m[l];
+                q.C = Vw + l * VS;
+                q.crs = KW;
+                q.ccs = 1;
+            }
+            STAGE("v_slice", launch_oz_slice(s1, 3, st));
+            STAGE("v_slice", launch_oz_slice(s2, 3, st));
+            STAGE("v_hi", launch_ozgemm(ob, OZ_F64_STORE, st));
+            // residual energy ||U - Z_hi V_hi||^2: rows nu of V_hi (k = j) times rows x of Z_hi
+            OzBatch orb;
+            memset(&orb, 0, sizeof(orb));
+            orb.nbatch = 3;
+            orb.err = ozerr;
+            for (int l = 0; l < 3; ++l) {
+                s1.X[l] = Vw + l * VS;
+                s1.rs[l] = KW;
+                s1.cs[l] = 1;
+                s1.rows[l] = R;
+                s1.K[l] = p.kin[l];
+                s1.dK[l] = &S->rhi[l];
+                s1.planes[l] = pP1 + l * p.sP1;
+                s1.pstride[l] = (long long)R * p.ldk;
+                s1.ld[l] = p.ldk;
+                s2.X[l] = Zw + l * NK;
+                s2.rs[l] = 1;
+                s2.cs[l] = p.n[l];
+                s2.rows[l] = p.n[l];
+                s2.drows[l] = nullptr;
+                s2.K[l] = p.kin[l];
+                s2.dK[l] = &S->rhi[l];
+                s2.planes[l] = pP2 + l * p.sP2;
+                s2.pstride[l] = (long long)p.n[l] * p.ldk;
+                s2.ld[l] = p.ldk;
+                s1.exps[l] = eP1 + l * EX;
+                s2.exps[l] = eP2 + l * EX;
+                OzProblem& q = orb.p[l];
+                q.A = OzPlanes{pP1 + l * p.sP1, (long long)R * p.ldk, p.ldk, eP1 + l * EX, 0};
+                q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.n[l] * p.ldk, p.ldk, eP2 + l * EX, 0};
+                q.M = R;
+                q.N = p.n[l];
+                q.K = p.kin[l];
+                q.dK = &S->rhi[l];
+                q.ref = Un + l * US;
+                q.ref_rs = p.n[l];
+                q.ref_cs = 1;
+                q.rpart = rpart + l * p.rp_stride;
+            }
+            STAGE("resid_slice", launch_oz_slice(s1, 3, st));
+            STAGE("resid_slice", launch_oz_slice(s2, 3, st));
+            STAGE("residual", launch_ozgemm(orb, OZ_F64_RESID, st));
+        } else {
+            STAGE("v_hi", launch_gemm(gv, st));
+            STAGE("residual", launch_gemm(gr, st));
+        }
     } else if (cudaMemsetAsync(rpart, 0, sizeof(double) * 3 * p.rp_stride, st) != cudaSuccess) {
         return RHOSVD_ERR_CUDA;
     }
@@ -543,7 +777,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     fa.rpstride = p.rp_stride;
     for (int l = 0; l < 3; ++l) {
         fa.ranks[l] = opts->ranks[l];
-        fa.ntiles[l] = (int)p.rp_stride;
+        fa.ntiles[l] = mixed ? ((R + OZ_BM - 1) / OZ_BM) * ((p.NQ + OZ_NT6 - 1) / OZ_NT6) : (int)p.rp_stride;
     }
     STAGE("rank_final", launch_rank_final(fa, st));
 
@@ -583,7 +817,48 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
         g.xi = xin;
         g.ldv = KW;
         gc.p[0] = g;
-        STAGE("core", launch_gemm(gc, st));
+        if (mixed) {
+            // V^(2), V^(3) with nu-contiguous rows for the generated Khatri-Rao operand, and the
+            // digit planes of diag(xi') V^(1) (rows i, k = nu, per-row exponents)
+            const long long VTS = (long long)R * KW;
+            STAGE("core_prep", launch_transpose_v(Vw, VS, KW, Vt, VTS, R, R, S->r, 1, 2, st));
+            const int rcap = rmax < KW ? rmax : KW;   // a rank never exceeds the basis width
+            OzSliceArgs s1;
+            memset(&s1, 0, sizeof(s1));
+            s1.S = 4;
+            s1.X[0] = Vw;
+            s1.rs[0] = 1;
+            s1.cs[0] = KW;
+            s1.rows[0] = rcap;
+            s1.drows[0] = &S->r[0];
+            s1.K[0] = R;
+            s1.kscale[0] = xin;
+            s1.planes[0] = pP2;
+            s1.pstride[0] = (long long)rcap * p.ldR;
+            s1.ld[0] = p.ldR;
+            s1.exps[0] = eP2;
+            STAGE("core_prep", launch_oz_slice(s1, 1, st));
+            OzBatch ob;
+            memset(&ob, 0, sizeof(ob));
+            ob.nbatch = 1;
+            ob.err = ozerr;
+            OzProblem& q = ob.p[0];
+            q.kr = OzKR{Vt + VTS, Vt + 2 * VTS, R};
+            q.M = rcap * rcap;
+            q.M_from_r2r3 = 1;
+            q.dNa = &S->r[1];
+            q.dNb = &S->r[2];
+            q.B = OzPlanes{pP2, (long long)rcap * p.ldR, p.ldR, eP2, 0};
+            q.N = rcap;
+            q.dN = &S->r[0];
+            q.K = R;
+            q.C = out->beta;
+            q.crs = -1;
+            q.ccs = 1;
+            STAGE("core", launch_ozgemm(ob, OZ_CORE, st));
+        } else {
+            STAGE("core", launch_gemm(gc, st));
+        }
     }
     return RHOSVD_OK;
 }

@@ -165,6 +165,31 @@ __global__ void k_cpsum(SumArgs a)
 }
 
 
+// dst_l(nu, j) = src_l(j, nu): V^(l) (rows j < r_l, ld lds) to nu-contiguous rows (ld ldd = R).
+__global__ void k_transpose_v(const double* src, long long sstride, int lds, double* dst, long long dstride, int ldd,
+                              int R, const int* dr, int mode0)
+{
+    const int l = mode0 + blockIdx.y;
+    const int r = dr[l];
+    const double* S = src + l * sstride;
+    double* D = dst + l * dstride;
+    const long long total = (long long)R * r;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int nu = (int)(e % R), j = (int)(e / R);
+        D[(long long)j * ldd + nu] = S[(long long)nu * lds + j];
+    }
+}
+
+int launch_transpose_v(const double* src, long long sstride, int lds, double* dst, long long dstride, int ldd, int R,
+                       const int* dr, int mode0, int nmodes, cudaStream_t st)
+{
+    dim3 grid(512, nmodes);
+    k_transpose_v<<<grid, 256, 0, st>>>(src, sstride, lds, dst, dstride, ldd, R, dr, mode0);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
 __global__ void k_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2)
 {
     s->kin[0] = k0; s->kin[1] = k1; s->kin[2] = k2;

@@ -229,6 +229,8 @@ int launch_colnorms(const NormArgs& a, cudaStream_t st);
 int launch_terms(const NormArgs& na, const double* xi, double* keepf, double* xin, double* xi_user,
                  rhosvd_info* info, double* Un, long long ustride, double* nn2, double* total, cudaStream_t st);
 int launch_identity(double* Q, int n, int ld, cudaStream_t st);
+int launch_transpose_v(const double* src, long long sstride, int lds, double* dst, long long dstride, int ldd, int R,
+                       const int* dr, int mode0, int nmodes, cudaStream_t st);
 int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, cudaStream_t st);
 int launch_hadamard(const HadArgs& a, cudaStream_t st);
 int launch_cpsum(const SumArgs& a, cudaStream_t st);

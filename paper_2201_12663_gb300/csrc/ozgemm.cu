@@ -1,0 +1,435 @@
+// ozgemm.cu -- tcgen05 kernels of the sliced FP64-class GEMM (see ozgemm.cuh for the arithmetic).
+//
+// CTA tile 128 x NT, K pipelined in stages of 32 through two shared-memory buffers.  Operand
+// planes sit in shared memory in the canonical K-major layout without swizzle (8-row x 16-byte
+// core matrices, LBO = 128 B along K, SBO = 512 B along M/N).  One thread issues the
+// tcgen05.mma instructions (kind::f16, BF16 in, FP32 accumulate) for every digit pair (s, t)
+// with s + t <= GMAX into TMEM accumulators, one per group g = s + t.  A group of np pairs is
+// exact while np * 2^16 * (its K since the last readback) < 2^24, so it is read back into
+// double-float registers every 8 / np stages (rounded down to a power of two).  With fewer
+// accumulators than groups, the last one takes the remaining (smallest) groups; it is inexact
+// but read back at the shortest cadence, so its FP32 partial sums never span more than a few
+// stages (the tensor cores' FP32 accumulation drops the bits of each product below the
+// accumulator's last place: over a long K with operands of one sign that error would grow with
+// K).  16 warps: warp w reads TMEM lanes 32 (w % 4) .. +31 and a quarter of the columns.
+// Every wait on an mbarrier is bounded; on expiry the kernel flags `err` and still frees TMEM.
+#include "ozgemm.cuh"
+
+namespace rh {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle, LBO 128 B, SBO 512 B, sm_100 version 1.
+__device__ __forceinline__ uint64_t oz_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((512u >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t oz_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void oz_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void oz_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+}
+
+// Bounded wait for the completion of the phase with the given parity.  Returns false on expiry.
+__device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (long it = 0; it < (1L << 24) && !done; ++it) {
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float* v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// (hi, lo) += x in double-float: exact two-sum, then renormalise so that |lo| stays below half
+// an ulp of hi and its own roundings stay at 2^-48 of the sum
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
+{
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    const float l = lo + err;
+    hi = s + l;
+    lo = l - (hi - s);
+}
+
+// number of digit pairs (s, t), 1 <= s <= SA, 1 <= t <= SB, in group g = s + t
+__host__ __device__ constexpr int oz_npairs(int SA, int SB, int g)
+{
+    int c = 0;
+    for (int s = 1; s <= SA; ++s)
+        if (g - s >= 1 && g - s <= SB) ++c;
+    return c;
+}
+
+// readback cadence (stages of 32 K) of an exact group of np pairs: np * 2^16 * 32 c <= 2^24
+__host__ __device__ constexpr int oz_cad(int np) { return np <= 1 ? 8 : (np == 2 ? 4 : (np <= 4 ? 2 : 1)); }
+
+// cadence of accumulator a when accumulators 0 .. NE-1 hold the exact groups g = a + 2 and
+// accumulator NE (if any) the rest, which is read back at the shortest exact cadence
+__host__ __device__ constexpr int oz_acc_cad(int SA, int SB, int NE, int a)
+{
+    if (a < NE) return oz_cad(oz_npairs(SA, SB, a + 2));
+    int m = 8;
+    for (int e = 0; e < NE; ++e) m = oz_cad(oz_npairs(SA, SB, e + 2)) < m ? oz_cad(oz_npairs(SA, SB, e + 2)) : m;
+    return m;
+}
+
+__host__ __device__ constexpr bool oz_exact_ok(int SA, int SB, int NE)
+{
+    for (int e = 0; e < NE; ++e)
+        if (oz_npairs(SA, SB, e + 2) > 8) return false;
+    return true;
+}
+
+// byte offset of (row r, 16-byte chunk c of the 32-wide K stage) in a plane tile
+__device__ __forceinline__ uint32_t oz_off(int r, int c) { return (uint32_t)((r >> 3) * 512 + c * 128 + (r & 7) * 16); }
+
+__device__ __forceinline__ int oz_dim(const int* d, int h) { return d ? *d : h; }
+
+}  // namespace
+
+template <int SA, int SB, int GMAX, int ASRC, int BSRC, int EPI, int NT, int NACC>
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
+{
+    constexpr int A_PLANE = OZ_BM * OZ_BK * 2;
+    constexpr int B_PLANE = NT * OZ_BK * 2;
+    constexpr int STAGE = SA * A_PLANE + SB * B_PLANE;
+    constexpr int NQ = NT / 4;                  // columns per thread in the epilogue
+    constexpr int NG = GMAX - 1;                // groups g = 2 .. GMAX
+    constexpr int NE = NACC >= NG ? NG : NACC - 1;   // exact accumulators
+    constexpr int NU = NACC >= NG ? NG : NACC;       // accumulators in use
+    constexpr int MINCAD = oz_acc_cad(SA, SB, NE, NU - 1) < oz_acc_cad(SA, SB, NE, 0)
+                               ? oz_acc_cad(SA, SB, NE, NU - 1) : oz_acc_cad(SA, SB, NE, 0);
+    static_assert(NT % 32 == 0 && NT >= 32 && NU * NT <= 512, "tile: 8-column TMEM loads per thread quarter");
+    static_assert(GMAX >= 2 && GMAX <= SA + SB && NACC >= 2, "groups");
+    static_assert(oz_exact_ok(SA, SB, NE), "an exact group needs at most 8 pairs");
+    const OzProblem& P = batch.p[blockIdx.z];
+    int M = P.M_from_r2r3 ? (*P.dNa) * (*P.dNb) : oz_dim(P.dM, P.M);
+    const int N = oz_dim(P.dN, P.N);
+    const int K = oz_dim(P.dK, P.K);
+    const int i0 = blockIdx.x * OZ_BM, j0 = blockIdx.y * NT;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (i0 >= M || j0 >= N) {
+        if (EPI == OZ_EPI_RESID && tid == 0) P.rpart[blockIdx.x + gridDim.x * blockIdx.y] = 0.0;
+        return;
+    }
+    extern __shared__ __align__(1024) unsigned char oz_smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ double red[32];
+    __shared__ int s_fail;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    // accumulator a < NACC - 1 holds group g = a + 2 exactly; accumulator NACC - 1 the rest
+
+    const int r2 = ASRC == OZ_A_KR ? *P.dNa : 1;
+    const int nkt = (K + OZ_BK - 1) / OZ_BK;
+
+    // ---- producer: fill stage buffer `buf` with K slice kt of every plane
+    auto produce = [&](int kt, int buf) {
+        unsigned char* sA = oz_smem + buf * STAGE;
+        unsigned char* sB = sA + SA * A_PLANE;
+        const int k0 = kt * OZ_BK;
+        // A: 128 rows x 4 chunks of 8
+        for (int e = tid; e < OZ_BM * 4; e += OZ_THREADS) {
+            const int r = e >> 2, c = e & 3;
+            const int gi = i0 + r, gk = k0 + c * 8;
+            if (ASRC == OZ_A_PLANES) {
+#pragma unroll
+                for (int s = 0; s < SA; ++s) {
+                    uint4 v = make_uint4(0, 0, 0, 0);
+                    if (gi < M && gk < K)
+                        v = *reinterpret_cast<const uint4*>(P.A.base + s * P.A.pstride + (long long)gi * P.A.ld + gk);
+                    *reinterpret_cast<uint4*>(sA + s * A_PLANE + oz_off(r, c)) = v;
+                }
+            } else {
+                uint16_t d[8][SA];
+                const int jj = gi % r2, mm = gi / r2;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    double x = 0.0;
+                    if (gi < M && gk + q < K)
+                        x = P.kr.V2t[(long long)jj * P.kr.ldt + gk + q] * P.kr.V3t[(long long)mm * P.kr.ldt + gk + q];
+                    oz_digits(x, 0, SA, d[q]);
+                }
+#pragma unroll
+                for (int s = 0; s < SA; ++s) {
+                    uint4 v;
+                    v.x = (uint32_t)d[0][s] | ((uint32_t)d[1][s] << 16);
+                    v.y = (uint32_t)d[2][s] | ((uint32_t)d[3][s] << 16);
+                    v.z = (uint32_t)d[4][s] | ((uint32_t)d[5][s] << 16);
+                    v.w = (uint32_t)d[6][s] | ((uint32_t)d[7][s] << 16);
+                    *reinterpret_cast<uint4*>(sA + s * A_PLANE + oz_off(r, c)) = v;
+                }
+            }
+        }
+        // B: NT rows x 4 chunks of 8
+        for (int e = tid; e < NT * 4; e += OZ_THREADS) {
+            const int r = e >> 2, c = e & 3;
+            const int gj = j0 + r, gk = k0 + c * 8;
+            if (BSRC == OZ_B_PLANES) {
+#pragma unroll
+                for (int t = 0; t < SB; ++t) {
+                    uint4 v = make_uint4(0, 0, 0, 0);
+                    if (gj < N && gk < K)
+                        v = *reinterpret_cast<const uint4*>(P.B.base + t * P.B.pstride + (long long)gj * P.B.ld + gk);
+                    *reinterpret_cast<uint4*>(sB + t * B_PLANE + oz_off(r, c)) = v;
+                }
+            } else {
+                uint16_t d[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    d[q] = 0;
+                    if (gj < N && gk + q < K)
+                        d[q] = rademacher(P.seed, P.mode, gk + q, gj) > 0.0 ? (uint16_t)0x3F80 : (uint16_t)0xBF80;
+                }
+                uint4 v;
+                v.x = (uint32_t)d[0] | ((uint32_t)d[1] << 16);
+                v.y = (uint32_t)d[2] | ((uint32_t)d[3] << 16);
+                v.z = (uint32_t)d[4] | ((uint32_t)d[5] << 16);
+                v.w = (uint32_t)d[6] | ((uint32_t)d[7] << 16);
+                *reinterpret_cast<uint4*>(sB + oz_off(r, c)) = v;
+            }
+        }
+    };
+
+    // epilogue registers: rows 32 (warp % 4) + lane, columns (warp / 4) NQ .. + NQ
+    const int q4 = warp & 3, cg = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+    float hi[NQ], lo[NQ];
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
+    auto readback = [&](uint32_t tacc) {
+#pragma unroll
+        for (int c = 0; c < NQ; c += 8) {
+            float v[8];
+            tmem_ld8(tacc + lane_base + cg * NQ + c, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) two_sum_acc(hi[c + j], lo[c + j], v[j]);
+        }
+    };
+
+    bool ok = true;
+    if (nkt > 0) produce(0, 0);
+    constexpr uint32_t IDESC = oz_idesc(NT);
+    for (int kt = 0; kt < nkt; ++kt) {
+        const int buf = kt & 1;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t aBase = smem_u32(oz_smem + buf * STAGE);
+            const uint32_t bBase = aBase + SA * A_PLANE;
+            bool started[NU];
+#pragma unroll
+            for (int a = 0; a < NU; ++a) started[a] = false;
+#pragma unroll
+            for (int s = 1; s <= SA; ++s) {
+#pragma unroll
+                for (int t = 1; t <= SB; ++t) {
+                    if (s + t > GMAX) continue;
+                    const int a = (s + t - 2) < NE ? (s + t - 2) : NE;
+                    const int cad = oz_acc_cad(SA, SB, NE, a);
+                    // the first MMA of a group after its readback overwrites the accumulator
+                    const uint32_t acc = ((kt % cad) != 0 || started[a]) ? 1u : 0u;
+                    started[a] = true;
+                    const uint32_t tacc = tmem + (uint32_t)(a * NT);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t da = oz_desc(aBase + (s - 1) * A_PLANE + kk * 256);
+                        const uint64_t db = oz_desc(bBase + (t - 1) * B_PLANE + kk * 256);
+                        oz_mma(tacc, da, db, IDESC, kk > 0 ? 1u : acc);
+                    }
+                }
+            }
+            oz_commit(&mbar[buf]);
+        }
+        // produce the next stage into the other buffer once the MMAs that read it are done
+        if (kt + 1 < nkt) {
+            if (kt >= 1) ok = oz_wait(&mbar[buf ^ 1], (uint32_t)(((kt - 1) >> 1) & 1)) && ok;
+            produce(kt + 1, buf ^ 1);
+        }
+        const bool last = (kt + 1 == nkt);
+        if (last || (kt % MINCAD) == MINCAD - 1) {      // every cadence is a multiple of MINCAD
+            ok = oz_wait(&mbar[buf], (uint32_t)((kt >> 1) & 1)) && ok;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int a = NU - 1; a >= 0; --a) {
+                const int cad = oz_acc_cad(SA, SB, NE, a);
+                if (last || (kt % cad) == cad - 1) readback(tmem + (uint32_t)(a * NT));
+            }
+        }
+    }
+    if (!ok) s_fail = 1;
+    const int row = i0 + q4 * 32 + lane;
+    const int ea = (ASRC == OZ_A_PLANES && P.A.exps && row < M) ? (int)P.A.exps[row] : (ASRC == OZ_A_PLANES ? P.A.exp0 : 0);
+    double e2 = 0.0;
+    const long long ccs = P.ccs < 0 ? (long long)M : P.ccs;
+    const long long crs = P.crs < 0 ? (long long)N : P.crs;
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+        const int col = j0 + cg * NQ + c;
+        if (row >= M || col >= N) continue;
+        const int eb = BSRC == OZ_B_PLANES ? (P.B.exps ? (int)P.B.exps[col] : P.B.exp0) : 8;
+        double v = (double)hi[c] + (double)lo[c];
+        v = ldexp(v, ea + eb - 16);
+        if (EPI == OZ_EPI_STORE) {
+            P.C[(long long)row * crs + (long long)col * ccs] = v;
+        } else {
+            const double d = P.ref[(long long)row * P.ref_rs + (long long)col * P.ref_cs] - v;
+            e2 = fma(d, d, e2);
+        }
+    }
+    if (EPI == OZ_EPI_RESID) {
+        e2 = block_sum(e2, red);
+        if (tid == 0) P.rpart[blockIdx.x + gridDim.x * blockIdx.y] = e2;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && s_fail && batch.err) atomicCAS(batch.err, 0, RHOSVD_ERR_TIMEOUT);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------- digit-plane slicer
+// One warp per operand row: optional exponent pass, then S planes written along k.
+__global__ void k_oz_slice(OzSliceArgs a)
+{
+    const int b = blockIdx.y;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int rows = a.drows[b] ? *a.drows[b] : a.rows[b];
+    if (warp >= a.rows[b]) return;
+    const int K = a.dK[b] ? *a.dK[b] : a.K[b];
+    const int ld = a.ld[b];
+    uint16_t* P = a.planes[b];
+    const long long ps = a.pstride[b];
+    const double* X = a.X[b];
+    const double* ks = a.kscale[b];
+    const bool live = warp < rows;
+    int E = a.exp0;
+    if (a.exps[b]) {
+        double mx = 0.0;
+        if (live)
+            for (int k = lane; k < K; k += 32) {
+                double x = X[(long long)warp * a.rs[b] + (long long)k * a.cs[b]];
+                if (ks) x *= ks[k];
+                mx = fmax(mx, fabs(x));
+            }
+        mx = warp_max(mx);
+        if (mx > 0.0) {
+            int ex;
+            frexp(mx, &ex);          // mx < 2^ex
+            E = ex;
+        } else {
+            E = -126;
+        }
+        if (E < -126) E = -126;
+        if (E > 127) E = 127;
+        if (lane == 0) a.exps[b][warp] = (signed char)E;
+    }
+    for (int k = lane; k < ld; k += 32) {
+        double x = 0.0;
+        if (live && k < K) {
+            x = X[(long long)warp * a.rs[b] + (long long)k * a.cs[b]];
+            if (ks) x *= ks[k];
+        }
+        uint16_t d[8];
+        oz_digits(x, E, a.S, d);
+        for (int s = 0; s < a.S; ++s) P[s * ps + (long long)warp * ld + k] = d[s];
+    }
+}
+
+int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st)
+{
+    int rmax = 0;
+    for (int b = 0; b < nb; ++b) rmax = max(rmax, a.rows[b]);
+    if (rmax <= 0) return 0;
+    dim3 grid((rmax + 7) / 8, nb);
+    k_oz_slice<<<grid, 256, 0, st>>>(a);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+template <int SA, int SB, int GMAX, int ASRC, int BSRC, int EPI, int NT, int NACC>
+static int run_oz(const OzBatch& b, cudaStream_t st)
+{
+    int Mh = 0, Nh = 0;
+    for (int i = 0; i < b.nbatch; ++i) {
+        Mh = max(Mh, b.p[i].M);
+        Nh = max(Nh, b.p[i].N);
+    }
+    if (Mh <= 0 || Nh <= 0) return 0;
+    constexpr int STAGE = SA * OZ_BM * OZ_BK * 2 + SB * NT * OZ_BK * 2;
+    constexpr int SMEM = 2 * STAGE;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_ozgemm<SA, SB, GMAX, ASRC, BSRC, EPI, NT, NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMEM) != cudaSuccess)
+            return RHOSVD_ERR_CUDA;
+        attr = true;
+    }
+    dim3 grid((Mh + OZ_BM - 1) / OZ_BM, (Nh + NT - 1) / NT, b.nbatch);
+    k_ozgemm<SA, SB, GMAX, ASRC, BSRC, EPI, NT, NACC><<<grid, OZ_THREADS, SMEM, st>>>(b);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+int launch_ozgemm(const OzBatch& b, OzKind kind, cudaStream_t st)
+{
+    switch (kind) {
+    case OZ_F64_STORE: return run_oz<6, 6, 8, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_STORE, OZ_NT6, 7>(b, st);
+    case OZ_F64_RESID: return run_oz<6, 6, 8, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_RESID, OZ_NT6, 7>(b, st);
+    case OZ_SKETCH: return run_oz<6, 1, 7, OZ_A_PLANES, OZ_B_SIGN, OZ_EPI_STORE, 96, 5>(b, st);
+    case OZ_CORE: return run_oz<4, 4, 5, OZ_A_KR, OZ_B_PLANES, OZ_EPI_STORE, 160, 3>(b, st);
+    }
+    return RHOSVD_ERR_INVALID_ARG;
+}
+
+}  // namespace rh

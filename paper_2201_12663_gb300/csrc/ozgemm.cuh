@@ -1,0 +1,134 @@
+// ozgemm.cuh -- FP64-class GEMM on the tcgen05 tensor cores by exact 8-bit slicing (used by
+// the mixed-precision form of the RHOSVD path).
+//
+// A real value x with |x| < 2^E is written as x = 2^E * sum_{s=1..S} d_s 2^(-8s), the d_s in
+// [0, 256] the base-256 digits of |x| 2^(8S-E) (the last one rounded) carrying the sign of x.
+// Every digit is exact in BF16, every product of two digits exact in FP32 (below 2^16), and a
+// sum of such products stays exact while it fits 24 bits.  The product of two operands is
+// x y = 2^(Ea+Eb) sum_{s,t} d_s d'_t 2^(-8(s+t)); the kernel forms the groups g = s + t up to
+// GMAX, each in its own TMEM accumulator, and reads every group back into double-float
+// registers before its FP32 sum could round.  For FP64 operands S = 6 and GMAX = 8: all seven
+// groups are exact, the error is the rounding of the last digits (|x - x^| <= 2^(E-49)) and
+// the dropped pairs s + t >= 9 (below 2^(Ea+Eb-54) per term), i.e. about 2^-48 of the
+// scaled sum 2^(Ea+Eb) K.  Each operand row gets its own exponent E (from its largest entry), so
+// the leading digit carries the row's leading bits.  The core contraction uses S = 4, GMAX = 5
+// with the groups s + t >= 4 in one inexact accumulator (about 2^-31).
+#pragma once
+#include "internal.cuh"
+#include <cuda_bf16.h>
+
+namespace rh {
+
+constexpr int OZ_BM = 128;      // rows of a CTA tile (TMEM lanes)
+constexpr int OZ_BK = 32;       // K per pipeline stage
+constexpr int OZ_THREADS = 512; // 16 warps
+constexpr int OZ_NT6 = 64;      // tile width of the S = 6 products (seven 64-column accumulators)
+
+// Operand given as digit planes in global memory: plane p, operand row i, k at
+// base[p * pstride + i * ld + k] (bf16 bit patterns), ld a multiple of 8.
+struct OzPlanes {
+    const uint16_t* base;
+    long long pstride;
+    int ld;
+    const signed char* exps;   // per operand row exponent E_i (nullable = all `exp0`)
+    int exp0;
+};
+
+// Generated Khatri-Rao operand for the core: row (j + r2 m), k = nu:
+// V2t[nu + ldt j] * V3t[nu + ldt m] (FP64, |.| <= 1), exponent 0.
+struct OzKR {
+    const double* V2t;
+    const double* V3t;
+    int ldt;
+};
+
+struct OzProblem {
+    OzPlanes A, B;
+    OzKR kr;
+    int M, N, K;                 // host values / upper bounds
+    const int* dM;
+    const int* dN;
+    const int* dK;
+    int N_from_r2r3;             // core: N = dNa * dNb... (rows of the generated A are r2 r3)
+    const int* dNa;
+    const int* dNb;
+    int M_from_r2r3;             // core: M = r2 * r3 from dNa, dNb
+    int krs_from_dNa;            // r2 for the KR row decomposition taken from *dNa
+    // output (EPI_STORE): C(i, j) at C[i * crs + j * ccs]; ccs < 0 means ccs = M, crs < 0 means
+    // crs = N (sizes decided on the device)
+    double* C;
+    long long crs, ccs;
+    // residual energy (EPI_RESID): sum over the tile of (ref(j, i) - C(i, j))^2, ref element
+    // (row j of the reference = operand column j, column i) at ref[i * ref_rs + j * ref_cs]
+    const double* ref;
+    long long ref_rs, ref_cs;
+    double* rpart;
+    uint64_t seed;               // Rademacher B: element (k, j) = sign(seed, mode, k, j)
+    int mode;
+};
+
+struct OzBatch {
+    OzProblem p[3];
+    int nbatch;
+    int* err;                    // status word: RHOSVD_ERR_TIMEOUT if a bounded wait gave up
+};
+
+enum OzASrc { OZ_A_PLANES = 0, OZ_A_KR = 1 };
+enum OzBSrc { OZ_B_PLANES = 0, OZ_B_SIGN = 1 };
+enum OzEpi { OZ_EPI_STORE = 0, OZ_EPI_RESID = 1 };
+
+// digit planes of one FP64 value for exponent E (|x| < 2^E): writes S bf16 bit patterns
+__device__ __forceinline__ void oz_digits(double x, int E, int S, uint16_t* out)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+    int e;
+    if (ef == 0) { e = -1022; } else { m |= 0x10000000000000ull; e = ef - 1023; }
+    // |x| = m 2^(e-52); F = round(|x| 2^(8S - E)) = round(m 2^(e - 52 + 8S - E))
+    const int sh = 52 - (e + 8 * S - E);
+    unsigned long long F;
+    if (m == 0 || sh >= 64) {
+        F = 0;
+    } else if (sh <= 0) {
+        F = 1ull << (8 * S);     // |x| >= 2^E does not occur for a valid exponent; saturate
+    } else {
+        F = (m + (1ull << (sh - 1))) >> sh;
+    }
+    const bool neg = (bits >> 63) != 0;
+    for (int s = 1; s <= S; ++s) {
+        const int d = (int)((F >> (8 * (S - s))) & (s == 1 ? 0x1FFull : 0xFFull));
+        float v = ldexpf((float)d, -8 * (s - 1));
+        if (neg) v = -v;
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        out[s - 1] = *reinterpret_cast<const uint16_t*>(&b);
+    }
+}
+
+// Digit planes of an operand: operand row i < rows, k < K reads X[i * rs + k * cs] (times
+// kscale[k] if given); planes[p * pstride + i * ld + k], zero for k in [K, ld).  With `exps`,
+// a per-row exponent E_i (|x| < 2^E_i) is computed and stored, else every row uses exp0.
+// One problem per mode b < nb with its own pointers (arrays of 3).
+struct OzSliceArgs {
+    const double* X[3];
+    long long rs[3], cs[3];
+    int rows[3];                 // host upper bound
+    const int* drows[3];         // nullable device row count
+    int K[3];
+    const int* dK[3];
+    const double* kscale[3];
+    uint16_t* planes[3];
+    long long pstride[3];
+    int ld[3];
+    signed char* exps[3];
+    int S;
+    int exp0;
+};
+int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st);
+
+// the four instantiations: FP64-class product (S = 6, all groups exact) storing C or reducing
+// the residual energy; range sketch against Rademacher signs; Khatri-Rao core (S = 4)
+enum OzKind { OZ_F64_STORE = 0, OZ_F64_RESID = 1, OZ_SKETCH = 2, OZ_CORE = 3 };
+int launch_ozgemm(const OzBatch& b, OzKind kind, cudaStream_t st);
+
+}  // namespace rh

@@ -33,10 +33,10 @@ def to_dev(P, cp_or_U, xi=None):
     return [P.to_device_factor(u) for u in U], torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def run_gpu(P, U, xi, eps, r_max, oversample=32, ranks=(0, 0, 0), seed=1234):
+def run_gpu(P, U, xi, eps, r_max, oversample=32, ranks=(0, 0, 0), seed=1234, precision=0):
     Ud, xd = to_dev(P, U, xi)
     res = P.rhosvd_c2t(Ud, xd, eps=eps, ranks=ranks, r_max=r_max, oversample=oversample, seed=seed,
-                       with_V=True, with_xi=True)
+                       with_V=True, with_xi=True, precision=precision)
     info = res.info()
     r = [info.r[l] for l in range(3)]
     beta = res.beta[: r[0] * r[1] * r[2]].cpu().numpy().reshape((r[0], r[1], r[2]), order="F")
@@ -99,9 +99,9 @@ def assert_tucker_parity(g, o, tol=1e-6):
     return d
 
 
-def check_case(P, U, xi, eps, r_max, oversample=32, ranks=(0, 0, 0)):
+def check_case(P, U, xi, eps, r_max, oversample=32, ranks=(0, 0, 0), precision=0):
     o = oracle.c2t(U, xi, eps=eps, ranks=ranks)
-    g = run_gpu(P, U, xi, eps, r_max, oversample, ranks)
+    g = run_gpu(P, U, xi, eps, r_max, oversample, ranks, precision=precision)
     assert g["info"].status == 0, P.rhosvd_strerror(g["info"].status)
     assert g["info"].kept == o["kept"]
     assert math.isclose(g["info"].xi_norm, o["xi_norm"], rel_tol=1e-13)
