@@ -202,19 +202,41 @@ __global__ void k_tridiag(ModeMap mm, double* A, long long astride, int lda, con
 }
 
 // ------------------------------------------------------------------ eigenvalues
-// Negative count of L D L^T - sigma I by the differential stationary qd transform.
-__device__ inline int negcount(const double* D, const double* Lo, int k, double sigma)
+// Number of eigenvalues of L D L^T below x: the signs of the pivots D+_i of the stationary qd
+// transform L D L^T - x I = L+ D+ L+^T (t_0 = -x, D+_i = D_i + t_i, t_{i+1} = t_i W_i / D+_i - x,
+// W_i = D_i L_i^2).  Written without division: t_i = N_i / Q_i with Q_0 = 1, N_0 = -x gives
+// P_i = D_i Q_i + N_i = D+_i Q_i, Q_{i+1} = P_i, N_{i+1} = N_i W_i - x P_i, and D+_i < 0 exactly
+// when P_i and Q_i differ in sign.  Three FP64 operations a step; the sign test and the
+// exponent watch run on the integer pipe.  N and Q are rescaled by a power of two (exact) when
+// their larger exponent leaves [-400, 400]; both vanishing restarts the recurrence as after a
+// split.  A zero pivot needs no special case: Q = 0 makes the next t infinite and the form
+// continues with its limit.
+__device__ __forceinline__ int negcount(const double* D, const double* W, int k, double x)
 {
+    double Q = 1.0, N = -x;
+    int hq = __double2hiint(Q);
     int c = 0;
-    double t = -sigma;
-    for (int i = 0; i + 1 < k; ++i) {
-        double dp = D[i] + t;
-        if (dp < 0.0) ++c;
-        if (dp == 0.0) dp = -DBL_MIN;
-        t = t * (D[i] * Lo[i] * Lo[i]) / dp - sigma;
-        if (!isfinite(t)) t = -sigma;   // overflow after a near-zero pivot: restart the tail
+    for (int i = 0; i < k; ++i) {
+        const double P = fma(D[i], Q, N);
+        const int hp = __double2hiint(P);
+        c += (int)((unsigned)(hp ^ hq) >> 31);
+        N = fma(-x, P, N * W[i]);
+        Q = P;
+        hq = hp;
+        const int ep = (hp >> 20) & 0x7FF, en = (__double2hiint(N) >> 20) & 0x7FF;
+        const int em = ep > en ? ep : en;
+        if (em > 1023 + 400 || em < 1023 - 400) {
+            if (em == 0) {
+                Q = 1.0;
+                N = -x;
+            } else {
+                const double sc = __hiloint2double((2046 - em) << 20, 0);   // 2^(1023 - em)
+                Q *= sc;
+                N *= sc;
+            }
+            hq = __double2hiint(Q);
+        }
     }
-    if (D[k - 1] + t < 0.0) ++c;
     return c;
 }
 
@@ -263,33 +285,51 @@ __global__ void k_ldl(ModeMap mm, const double* d, const double* e, int vstride,
     st->specmax[b] = hi * (1.0 + 8.0 * DBL_EPSILON) + DBL_MIN;
 }
 
-// Bisection for eigenvalue a (ascending) of L D L^T: one thread per eigenvalue, spread over
-// many small blocks so that the long dependent chains of FP64 divisions run on many SMs.
-// grid: (ceil(KMAX / EIG_PER_BLOCK), nmodes), block: 32 threads, EIG_PER_BLOCK of them busy.
-constexpr int EIG_PER_BLOCK = 4;
+// Eigenvalue a (ascending) of L D L^T by multisection: one warp per eigenvalue, each lane
+// counts at one of 32 points inside the current bracket, and the bracket shrinks to the two
+// neighbouring points around the eigenvalue (33-fold per round).  Points are spaced
+// geometrically while hi > 4 lo (relative accuracy across the whole spectrum), linearly after.
+// The bracket starts at [s/2, specmax]: T + s I has no eigenvalue below s (1 - k u ||T|| / s).
+// About 12 rounds reach hi - lo <= 2 u hi.
+// grid: (ceil(KMAX / EIG_WARPS), nmodes), block: 32 EIG_WARPS threads.
+constexpr int EIG_WARPS = 4;
 
 __global__ void k_bisect(ModeMap mm, const double* Dg, const double* Lg, int vstride, const int* dk,
                          double* mu, const DevState* st)
 {
     const int b = mm.m[blockIdx.y];
     const int k = dk[b];
-    const int a = blockIdx.x * EIG_PER_BLOCK + threadIdx.x;
-    __shared__ double Dsh[KMAX], Lsh[KMAX];
-    if (blockIdx.x * EIG_PER_BLOCK >= k) return;
+    __shared__ double Dsh[KMAX], Wsh[KMAX];
+    if (blockIdx.x * EIG_WARPS >= k) return;
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        Dsh[i] = Dg[b * vstride + i];
-        Lsh[i] = Lg[b * vstride + i];
+        const double d = Dg[b * vstride + i];
+        const double l = (i + 1 < k) ? Lg[b * vstride + i] : 0.0;
+        Dsh[i] = d;
+        Wsh[i] = d * l * l;
     }
     __syncthreads();
-    if (threadIdx.x >= EIG_PER_BLOCK || a >= k) return;
-    double lo = 0.0, hi = st->specmax[b];
-    for (int it = 0; it < 400; ++it) {
+    const int lane = threadIdx.x & 31;
+    const int a = blockIdx.x * EIG_WARPS + (threadIdx.x >> 5);
+    if (a >= k) return;
+    double lo = 0.5 * st->shift[b], hi = st->specmax[b];
+    const int j = lane + 1;
+    for (int round = 0; round < 64; ++round) {
         if (hi - lo <= 2.0 * DBL_EPSILON * hi) break;
-        double mid = (lo > 0.0 && hi > 2.0 * lo) ? sqrt(lo) * sqrt(hi) : 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (negcount(Dsh, Lsh, k, mid) <= a) lo = mid; else hi = mid;
+        double x = fma(hi - lo, (double)j * (1.0 / 33.0), lo);
+        if (hi > 4.0 * lo) {
+            const float lr = log2f((float)(hi / lo));
+            const double g = lo * (double)exp2f(lr * (float)j * (1.0f / 33.0f));
+            if (g > lo && g < hi) x = g;
+        }
+        const bool below = negcount(Dsh, Wsh, k, x) <= a;     // lambda_a >= x
+        const unsigned m = __ballot_sync(0xffffffffu, below);
+        const int f = (~m) ? __ffs(~m) - 1 : 32;               // first point above lambda_a
+        const double xl = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+        const double xh = __shfl_sync(0xffffffffu, x, f < 32 ? f : 31);
+        if (f > 0) lo = xl;
+        if (f < 32) hi = xh;
     }
-    mu[b * vstride + a] = 0.5 * (lo + hi);
+    if (lane == 0) mu[b * vstride + a] = 0.5 * (lo + hi);
 }
 
 // ------------------------------------------------------------------ rank rule
@@ -556,8 +596,8 @@ int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, co
 {
     k_ldl<<<nb, 32, 0, st>>>(mm, d, e, vstride, dk, D, Lo, s);
     RH_CHECK_LAUNCH();
-    dim3 grid((KMAX + EIG_PER_BLOCK - 1) / EIG_PER_BLOCK, nb);
-    k_bisect<<<grid, 32, 0, st>>>(mm, D, Lo, vstride, dk, mu, s);
+    dim3 grid((KMAX + EIG_WARPS - 1) / EIG_WARPS, nb);
+    k_bisect<<<grid, 32 * EIG_WARPS, 0, st>>>(mm, D, Lo, vstride, dk, mu, s);
     RH_CHECK_LAUNCH();
     return 0;
 }
