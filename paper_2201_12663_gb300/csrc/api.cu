@@ -215,8 +215,9 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
         p->ldk = up8(p->KW);
         p->sU1 = 6LL * p->NQ * p->ldR;
         p->sU2 = 6LL * R * p->ldn;
-        long long a1 = (long long)R * p->ldk, a2 = (long long)p->KW * p->ldR;
-        p->sP1 = 6LL * (a1 > a2 ? a1 : a2);
+        long long a1 = (long long)R * p->ldk, a2 = (long long)p->KW * p->ldR, a3 = (long long)p->KW * p->ldk;
+        a1 = a1 > a2 ? a1 : a2;
+        p->sP1 = 6LL * (a1 > a3 ? a1 : a3);
         long long b1 = (long long)p->KW * p->ldn, b2 = (long long)p->KW * p->ldk, b3 = (long long)p->NQ * p->ldk;
         long long bm = b1 > b2 ? b1 : b2;
         bm = bm > b3 ? bm : b3;
@@ -488,24 +489,82 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             // boundary sit ~1e-13 below the largest ones
             STAGE("cholqr_gram", launch_gemm_splitk(g2, part, st));
             const int* dk = (pass == 0) ? S->kin : S->m;
-            STAGE("cholqr_chol", launch_chol(sk, G, KK, KW, dk, L, KK, KW, perm, KW, S->m, S->piv_fail, pivots[pass],
-                                  tols[pass], nsk, st));
-            TrsmArgs ta;
-            memset(&ta, 0, sizeof(ta));
-            for (int l = 0; l < 3; ++l) {
-                ta.X[l] = X + l * NK;
-                ta.ldx[l] = p.n[l];
-                ta.Q[l] = Y + l * NK;
-                ta.ldq[l] = p.n[l];
-                ta.n[l] = p.n[l];
+            STAGE("cholqr_chol", launch_chol(sk, G, KK, KW, dk, S->kx, L, KK, KW, perm, KW, S->m, S->piv_fail,
+                                             pivots[pass], tols[pass], nsk, KW, st));
+            // Y = X P Lt^{-T}: the triangular inverse scattered into W (the Gram's buffer), then
+            // one GEMM over the kx columns of X
+            double* Wq = G;
+            STAGE("cholqr_trinv", launch_trinv(sk, L, KK, KW, perm, KW, S->kx, S->m, Wq, KK, KW, nsk, st));
+            if (mixed) {
+                OzSliceArgs sx, sw;
+                memset(&sx, 0, sizeof(sx));
+                memset(&sw, 0, sizeof(sw));
+                sx.S = sw.S = 6;
+                OzBatch ob;
+                memset(&ob, 0, sizeof(ob));
+                ob.nbatch = nsk;
+                ob.err = ozerr;
+                for (int b = 0; b < nsk; ++b) {
+                    const int l = sk.m[b];
+                    sx.X[b] = X + l * NK;                 // rows x, k = column c of X
+                    sx.rs[b] = 1;
+                    sx.cs[b] = p.n[l];
+                    sx.rows[b] = p.n[l];
+                    sx.K[b] = p.kin[l];
+                    sx.dK[b] = &S->kx[l];
+                    sx.planes[b] = pP2 + l * p.sP2;
+                    sx.pstride[b] = (long long)p.n[l] * p.ldk;
+                    sx.ld[b] = p.ldk;
+                    sx.exps[b] = eP2 + l * EX;
+                    sw.X[b] = Wq + l * KK;                // rows t (columns of W), k = c
+                    sw.rs[b] = KW;
+                    sw.cs[b] = 1;
+                    sw.rows[b] = p.kin[l];
+                    sw.drows[b] = &S->m[l];
+                    sw.K[b] = p.kin[l];
+                    sw.dK[b] = &S->kx[l];
+                    sw.planes[b] = pP1 + l * p.sP1;
+                    sw.pstride[b] = (long long)p.kin[l] * p.ldk;
+                    sw.ld[b] = p.ldk;
+                    sw.exps[b] = eP1 + l * EX;
+                    OzProblem& q = ob.p[b];
+                    q.A = OzPlanes{sx.planes[b], sx.pstride[b], p.ldk, sx.exps[b], 0};
+                    q.B = OzPlanes{sw.planes[b], sw.pstride[b], p.ldk, sw.exps[b], 0};
+                    q.M = p.n[l];
+                    q.N = p.kin[l];
+                    q.dN = &S->m[l];
+                    q.K = p.kin[l];
+                    q.dK = &S->kx[l];
+                    q.C = Y + l * NK;
+                    q.crs = 1;
+                    q.ccs = p.n[l];
+                }
+                STAGE("cholqr_apply", launch_oz_slice(sx, nsk, st));
+                STAGE("cholqr_apply", launch_oz_slice(sw, nsk, st));
+                STAGE("cholqr_apply", launch_ozgemm(ob, OZ_F64_STORE, st));
+            } else {
+                GemmBatch gq;
+                memset(&gq, 0, sizeof(gq));
+                gq.nbatch = nsk;
+                gq.ksplit = 1;
+                gq.bkind = B_PLAIN;
+                for (int b = 0; b < nsk; ++b) {
+                    const int l = sk.m[b];
+                    GemmProblem g = blank_problem();
+                    g.A = Mat{X + l * NK, 1, (long long)p.n[l]};      // A(x, c) = X(x, c)
+                    g.B = Mat{Wq + l * KK, 1, (long long)KW};         // B(c, t) = W(c, t)
+                    g.C = Y + l * NK;
+                    g.crs = 1;
+                    g.ccs = p.n[l];
+                    g.M = p.n[l];
+                    g.N = p.kin[l];
+                    g.dN = &S->m[l];
+                    g.K = p.kin[l];
+                    g.dK = &S->kx[l];
+                    gq.p[b] = g;
+                }
+                STAGE("cholqr_apply", launch_gemm(gq, st));
             }
-            ta.L = L;
-            ta.lstride = KK;
-            ta.ldl = KW;
-            ta.perm = perm;
-            ta.pstride = KW;
-            ta.dm = S->m;
-            STAGE("cholqr_trsm", launch_trsm(sk, ta, p.NQ, nsk, st));
         }
     }
 
@@ -590,7 +649,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     }
     if (R == 0 && cudaMemsetAsync(G, 0, sizeof(double) * 3 * KK, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
     STAGE("trace", launch_trace(all, G, KK, KW, S->m, S->trace, 3, st));
-    STAGE("tridiag", launch_tridiag(all, G, KK, KW, S->m, vd, ve, vtau, vs, 3, st));
+    STAGE("tridiag", launch_tridiag(all, G, KK, KW, S->m, vd, ve, vtau, vs, 3, KW, st));
     STAGE("eigvals", launch_eigvals(all, vd, ve, vs, S->m, vD, vL, vmu, S, 3, st));
 
     // ---- a6: provisional rank from the eigenvalues, then eigenvectors of the rhi leading

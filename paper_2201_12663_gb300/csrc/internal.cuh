@@ -17,7 +17,8 @@ struct DevState {
     int piv_fail[3];    // small factorisation break-down flags
     int rhi[3];         // number of leading eigenvectors computed (rank candidates 0..rhi)
     int r0[3];          // provisional rank from the eigenvalues
-    int pad[2];
+    int kx[3];          // columns of the current CholeskyQR input
+    int pad[1];
     double shift[3];    // shift used for the LDL^T representation of the tridiagonal
     double trace[3];    // trace(B B^T) = ||B||_F^2
     double total[3];    // ||U^(l) normalised||_F^2
@@ -176,19 +177,6 @@ struct SumArgs {
     double alpha, beta;
 };
 
-struct TrsmArgs {
-    const double* X[3];
-    int ldx[3];
-    double* Q[3];
-    int ldq[3];
-    int n[3];
-    const double* L;
-    long long lstride;
-    int ldl;
-    const int* perm;
-    int pstride;
-    const int* dm;
-};
 
 struct RankArgs {
     const double* mu;
@@ -234,14 +222,15 @@ int launch_transpose_v(const double* src, long long sstride, int lds, double* ds
 int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, cudaStream_t st);
 int launch_hadamard(const HadArgs& a, cudaStream_t st);
 int launch_cpsum(const SumArgs& a, cudaStream_t st);
-int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, double* L, long long lstride,
-                int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot, double tol, int nb,
-                cudaStream_t st);
-int launch_trsm(ModeMap mm, const TrsmArgs& a, int nmax, int nb, cudaStream_t st);
+int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int* kx_out, double* L,
+                long long lstride, int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot, double tol, int nb,
+                int kbound, cudaStream_t st);
+int launch_trinv(ModeMap mm, const double* L, long long lstride, int ldl, const int* perm, int pstride,
+                 const int* dkx, const int* dm, double* W, long long wstride, int ldw, int nb, cudaStream_t st);
 int launch_trace(ModeMap mm, const double* A, long long astride, int lda, const int* dk, double* trace, int nb,
                  cudaStream_t st);
 int launch_tridiag(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e, double* tau,
-                   int vstride, int nb, cudaStream_t st);
+                   int vstride, int nb, int kbound, cudaStream_t st);
 int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D, double* Lo,
                    double* mu, DevState* s, int nb, cudaStream_t st);
 int launch_rank(const RankArgs& a, cudaStream_t st);

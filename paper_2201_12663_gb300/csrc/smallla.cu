@@ -14,18 +14,20 @@
 // vectors of the side matrix restricted to span(Q) (eq. SVD_Ul, eq. svdr).
 #include "internal.cuh"
 #include <float.h>
+#include <limits.h>
 
 namespace rh {
 
 // ------------------------------------------------------------------ pivoted Cholesky
-// G: k x k symmetric (full storage, leading dimension ldg), batch stride gstride.
-// dims: *dk (device) or hk.  L (leading dimension ldl) receives L(i, t) for original row i
-// and step t; perm[t] the pivot of step t.  Stops at the first step whose largest remaining
-// Schur diagonal is <= tol * (largest initial diagonal); the number of steps taken is
-// written to *dm_out.  With pivot == 0 the order is the identity and a non-positive
-// pivot sets *fail.
+// Pivoted Cholesky P^T G P = Lt Lt^T (left-looking, one block per mode).  Rows are kept in
+// pivot order: slot t holds the row chosen at step t, the active rows sit packed in slots
+// (t, k), and choosing a pivot swaps it into slot t (its computed part of Lt moves with it).
+// So Lt is stored directly (Lt(i, s) at L[s * ldl + i]), each step's active rows fill whole
+// warps, and perm[t] is the original index of slot t -- for every slot, also those left
+// after a rank stop (their rows are not factorised).  Stops at the first pivot <= tol *
+// max(diag G) (the numerical rank m); without pivoting that raises `fail`.  kx_out[b] = k.
 __global__ void k_chol_piv(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int hk,
-                           double* L, long long lstride, int ldl, int* perm, int pstride,
+                           int* kx_out, double* L, long long lstride, int ldl, int* perm, int pstride,
                            int* dm_out, int* fail, int pivot, double tol)
 {
     const int b = mm.m[blockIdx.x];
@@ -34,96 +36,306 @@ __global__ void k_chol_piv(ModeMap mm, const double* G, long long gstride, int l
     L += b * lstride;
     perm += b * pstride;
     __shared__ double dsh[KMAX];
-    __shared__ int done[KMAX];
+    __shared__ int orig[KMAX];
     __shared__ double red[32];
     __shared__ int redi[32];
-    __shared__ int s_p;
+    __shared__ int s_q;
     __shared__ double s_piv;
     const int i = threadIdx.x;
-    double d0max;
-    if (i < k) { dsh[i] = G[(long long)i * ldg + i]; done[i] = 0; }
+    if (i < k) { dsh[i] = G[(long long)i * ldg + i]; orig[i] = i; }
     __syncthreads();
-    {
-        double v = (i < k) ? dsh[i] : 0.0;
-        d0max = block_max(v, red);
-    }
+    const double d0max = block_max((i < k) ? dsh[i] : 0.0, red);
     int m = k;
     for (int t = 0; t < k; ++t) {
-        // pivot selection (first index of the largest remaining diagonal)
+        // pivot: first slot of the largest remaining diagonal
         if (pivot) {
-            double v = (i < k && !done[i]) ? dsh[i] : -1.0;
+            double v = (i >= t && i < k) ? dsh[i] : -DBL_MAX;   // below any active diagonal
             int idx = i;
             for (int o = 16; o > 0; o >>= 1) {
-                double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-                int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+                const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
                 if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
             }
             __syncthreads();
             if ((i & 31) == 0) { red[i >> 5] = v; redi[i >> 5] = idx; }
             __syncthreads();
             if (i == 0) {
-                double bv = -1.0; int bi = 0;
+                double bv = -DBL_MAX;
+                int bi = t;
                 for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
                     if (red[w] > bv || (red[w] == bv && redi[w] < bi)) { bv = red[w]; bi = redi[w]; }
-                s_p = bi;
+                s_q = bi;
                 s_piv = bv;
             }
         } else if (i == 0) {
-            s_p = t;
+            s_q = t;
             s_piv = dsh[t];
         }
         __syncthreads();
-        const int p = s_p;
+        const int q = s_q;
         const double dp = s_piv;
         if (!(dp > tol * d0max) || !(dp > 0.0)) {
             if (!pivot && i == 0 && fail) fail[b] = 1;
             m = t;
             break;
         }
-        const double piv = sqrt(dp);
-        if (i == 0) { perm[t] = p; done[p] = 1; }
-        __syncthreads();
-        if (i < k && !done[i]) {
-            double sacc = G[(long long)p * ldg + i];
-            for (int s = 0; s < t; ++s) sacc -= L[(long long)s * ldl + i] * L[(long long)s * ldl + p];
-            const double lit = sacc / piv;
-            L[(long long)t * ldl + i] = lit;
-            dsh[i] -= lit * lit;
+        if (q != t) {           // move the pivot row into slot t
+            for (int c = i; c < t; c += blockDim.x) {
+                const double x = L[(long long)c * ldl + t];
+                L[(long long)c * ldl + t] = L[(long long)c * ldl + q];
+                L[(long long)c * ldl + q] = x;
+            }
+            if (i == 0) {
+                const int o = orig[t];
+                orig[t] = orig[q];
+                orig[q] = o;
+                dsh[q] = dsh[t];
+                dsh[t] = dp;
+            }
         }
-        if (i == p) L[(long long)t * ldl + p] = piv;
+        __syncthreads();
+        const double piv = sqrt(dp);
+        const double rp = 1.0 / piv;
+        if (i == 0) L[(long long)t * ldl + t] = piv;
+        const int row = t + 1 + i;
+        if (row < k) {
+            const double* Lr = L + row;
+            const double* Lt = L + t;
+            double a0 = G[(long long)orig[t] * ldg + orig[row]], a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int c = 0;
+            for (; c + 3 < t; c += 4) {
+                a0 = fma(-Lr[(long long)c * ldl], Lt[(long long)c * ldl], a0);
+                a1 = fma(-Lr[(long long)(c + 1) * ldl], Lt[(long long)(c + 1) * ldl], a1);
+                a2 = fma(-Lr[(long long)(c + 2) * ldl], Lt[(long long)(c + 2) * ldl], a2);
+                a3 = fma(-Lr[(long long)(c + 3) * ldl], Lt[(long long)(c + 3) * ldl], a3);
+            }
+            for (; c < t; ++c) a0 = fma(-Lr[(long long)c * ldl], Lt[(long long)c * ldl], a0);
+            const double lit = ((a0 + a1) + (a2 + a3)) * rp;
+            L[(long long)t * ldl + row] = lit;
+            dsh[row] -= lit * lit;
+        }
         __syncthreads();
     }
-    if (i == 0) dm_out[b] = m;
+    for (int t = i; t < k; t += blockDim.x) perm[t] = orig[t];
+    if (i == 0) {
+        dm_out[b] = m;
+        kx_out[b] = k;
+    }
 }
 
-// ------------------------------------------------------------------ row triangular solve
-// Q(:, t) = (X(:, perm[t]) - sum_{s<t} Q(:, s) L(perm[t], s)) / L(perm[t], t), t < m.
-// One thread per row of X (n rows); blockIdx.y = mode.  X and Q are n x . column-major.
+// ---- shared-memory forms (k up to SM_PACK_K): the factor lives in shared memory as a packed
+// lower triangle, column c (rows c .. k-1) at pk_off(c, k) + row - c, and every step spreads
+// its dot products over row groups of 32 x column chunks so that all 16 warps issue FP64 work
+// (on this part the FP64 pipe, not memory, is the limit).
+constexpr int SM_THREADS = 512;
+constexpr int SM_PACK_K = 224;          // 224 * 225 / 2 doubles = 197 KB
 
-__global__ void k_trsm_rows(ModeMap mm, TrsmArgs a)
+__device__ __forceinline__ int pk_off(int c, int k) { return c * k - ((c * (c - 1)) >> 1); }
+
+// Row-group x column-chunk split of a step with nr rows and nc terms a row: tasks (rg, ch),
+// rg < ceil(nr / 32), ch < nch; warp w takes tasks w, w + 16, ...
+struct SplitRC {
+    int rg, nch, clen;
+    __device__ SplitRC(int nr, int nc)
+    {
+        rg = (nr + 31) >> 5;
+        nch = rg >= 16 ? 1 : 16 / rg;
+        clen = (nc + nch - 1) / nch;
+        if (clen == 0) clen = 1;
+    }
+};
+
+// Same factorisation as k_chol_piv, with Lt in shared memory (dynamic, k(k+1)/2 doubles).
+__global__ void __launch_bounds__(SM_THREADS) k_chol_smem(ModeMap mm, const double* G, long long gstride, int ldg,
+                                                         const int* dk, int* kx_out, double* L, long long lstride,
+                                                         int ldl, int* perm, int pstride, int* dm_out, int* fail,
+                                                         int pivot, double tol)
+{
+    const int b = mm.m[blockIdx.x];
+    const int k = dk[b];
+    G += b * gstride;
+    L += b * lstride;
+    perm += b * pstride;
+    extern __shared__ double Ls[];
+    __shared__ double dsh[KMAX];
+    __shared__ int orig[KMAX];
+    __shared__ double part[SM_THREADS];
+    __shared__ double red[33];
+    __shared__ int redi[32];
+    __shared__ long long redl[32];
+    __shared__ int s_q;
+    __shared__ double s_piv;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < k) { dsh[tid] = G[(long long)tid * ldg + tid]; orig[tid] = tid; }
+    __syncthreads();
+    double d0max = 0.0;
+    {
+        double v = tid < k ? dsh[tid] : 0.0;
+        v = warp_max(v);
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        for (int w = 0; w < SM_THREADS / 32; ++w) d0max = fmax(d0max, red[w]);
+        __syncthreads();
+    }
+    // Scalar FP64 work (the stop test, sqrt, reciprocal) is done once by thread 0 and shared:
+    // FP64 is a slow pipe here, and 16 warps repeating it would cost more than the dot products.
+    // The pivot search compares bit patterns on the integer pipe (a non-negative double orders
+    // like its bits; a negative Schur diagonal maps to -1, a finished slot to LLONG_MIN, so that
+    // with every remaining diagonal negative the search still lands on an active slot and the
+    // stop test ends the factorisation).
+    __shared__ double s_rp;
+    __shared__ int s_stop;
+    int m = k;
+    for (int t = 0; t < k; ++t) {
+        if (pivot) {
+            long long key = LLONG_MIN;         // finished or absent slots lose to every active one
+            if (tid >= t && tid < k) {
+                const long long bits = __double_as_longlong(dsh[tid]);
+                key = bits >= 0 ? bits : -1;    // a negative diagonal ranks below all others
+            }
+            int idx = tid;
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+                if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+            }
+            if (lane == 0) { redl[warp] = key; redi[warp] = idx; }
+            __syncthreads();
+            if (tid == 0) {
+                long long bk = LLONG_MIN;
+                int bi = t;
+                for (int w = 0; w < SM_THREADS / 32; ++w)
+                    if (redl[w] > bk || (redl[w] == bk && redi[w] < bi)) { bk = redl[w]; bi = redi[w]; }
+                s_q = bi;
+            }
+        } else if (tid == 0) {
+            s_q = t;
+        }
+        if (tid == 0) {
+            const double dp = dsh[s_q];
+            const bool stop = !(dp > tol * d0max) || !(dp > 0.0);
+            s_stop = stop;
+            s_piv = dp;
+            if (!stop) {
+                const double piv = sqrt(dp);
+                s_rp = 1.0 / piv;
+                Ls[pk_off(t, k)] = piv;
+            }
+        }
+        __syncthreads();
+        const int q = s_q;
+        const double dp = s_piv;
+        if (s_stop) {
+            if (!pivot && tid == 0 && fail) fail[b] = 1;
+            m = t;
+            break;
+        }
+        if (q != t) {
+            for (int c = tid; c < t; c += SM_THREADS) {
+                const int o = pk_off(c, k) - c;
+                const double x = Ls[o + t];
+                Ls[o + t] = Ls[o + q];
+                Ls[o + q] = x;
+            }
+            if (tid == 0) {
+                const int o = orig[t];
+                orig[t] = orig[q];
+                orig[q] = o;
+                dsh[q] = dsh[t];
+                dsh[t] = dp;
+            }
+        }
+        __syncthreads();
+        const int nr = k - t - 1;
+        const SplitRC sp(nr, t);
+        for (int task = warp; task < sp.rg * sp.nch; task += SM_THREADS / 32) {
+            const int rg = task / sp.nch, ch = task - rg * sp.nch;
+            const int r = t + 1 + rg * 32 + lane;
+            double a0 = 0.0, a1 = 0.0;
+            if (r < k) {
+                const int cb = ch * sp.clen, ce = min(t, cb + sp.clen);
+                int c = cb;
+                for (; c + 1 < ce; c += 2) {
+                    const int o0 = pk_off(c, k) - c, o1 = pk_off(c + 1, k) - c - 1;
+                    a0 = fma(Ls[o0 + r], Ls[o0 + t], a0);
+                    a1 = fma(Ls[o1 + r], Ls[o1 + t], a1);
+                }
+                if (c < ce) {
+                    const int o0 = pk_off(c, k) - c;
+                    a0 = fma(Ls[o0 + r], Ls[o0 + t], a0);
+                }
+            }
+            part[task * 32 + lane] = a0 + a1;
+        }
+        __syncthreads();
+        const double rp = s_rp;
+        const int ot = pk_off(t, k) - t;
+        if (tid < nr) {
+            const int r = t + 1 + tid;
+            double sacc = G[(long long)orig[t] * ldg + orig[r]];
+            const int rg = tid >> 5;
+            for (int ch = 0; ch < sp.nch; ++ch) sacc -= part[(rg * sp.nch + ch) * 32 + lane];
+            const double lit = sacc * rp;
+            Ls[ot + r] = lit;
+            dsh[r] -= lit * lit;
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < k; t += SM_THREADS) perm[t] = orig[t];
+    for (int c = warp; c < m; c += SM_THREADS / 32) {
+        const int o = pk_off(c, k) - c;
+        for (int r = c + lane; r < m; r += 32) L[(long long)c * ldl + r] = Ls[o + r];
+    }
+    if (tid == 0) {
+        dm_out[b] = m;
+        kx_out[b] = k;
+    }
+}
+
+// ------------------------------------------------------------------ triangular inverse
+// Lt^{-1} of the m x m factor of k_chol_piv, scattered into W (kx x m, ld ldw) so that
+// Q = X W = X P Lt^{-T} (the CholeskyQR factor) is one GEMM: W(perm[j], t) = Lt^{-1}(t, j) for
+// t >= j, 0 for t < j; rows perm[j], m <= j < kx (columns of X left out) are zero.
+// Column j of Lt^{-1} by forward substitution with column axpys: one warp per column, lane l
+// holding entries l, l + 32, ...  grid: (ceil(KMAX / 4), nmodes), block 128.
+__global__ void k_trinv(ModeMap mm, const double* L, long long lstride, int ldl, const int* perm, int pstride,
+                        const int* dkx, const int* dm, double* W, long long wstride, int ldw)
 {
     const int b = mm.m[blockIdx.y];
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= a.n[b]) return;
-    const int m = a.dm[b];
-    const double* L = a.L + b * a.lstride;
-    const int* perm = a.perm + b * a.pstride;
-    const double* X = a.X[b];
-    double* Q = a.Q[b];
-    const int ldx = a.ldx[b], ldq = a.ldq[b], ldl = a.ldl;
-    double q[KMAX];
-    for (int t = 0; t < m; ++t) {
-        const int p = perm[t];
-        double s0 = X[(long long)p * ldx + row], s1 = 0.0;
-        int s = 0;
-        for (; s + 1 < t; s += 2) {
-            s0 -= q[s] * L[(long long)s * ldl + p];
-            s1 -= q[s + 1] * L[(long long)(s + 1) * ldl + p];
+    const int m = dm[b], kx = dkx[b];
+    L += b * lstride;
+    perm += b * pstride;
+    W += b * wstride;
+    __shared__ double rdiag[KMAX];
+    for (int s = threadIdx.x; s < m; s += blockDim.x) rdiag[s] = 1.0 / L[(long long)s * ldl + s];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (j >= kx) return;
+    double* Wr = W + perm[j];
+    if (j >= m) {
+        for (int t = lane; t < m; t += 32) Wr[(long long)t * ldw] = 0.0;
+        return;
+    }
+    for (int t = lane; t < j; t += 32) Wr[(long long)t * ldw] = 0.0;
+    constexpr int NR = KMAX / 32;
+    double x[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) x[r] = (r * 32 + lane == j) ? 1.0 : 0.0;
+    for (int s = j; s < m; ++s) {
+        const int rs = s >> 5;
+        double xs = 0.0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (r == rs) xs = __shfl_sync(0xffffffffu, x[r], s & 31);
+        xs *= rdiag[s];
+        if (lane == 0) Wr[(long long)s * ldw] = xs;
+        const double* Lc = L + (long long)s * ldl;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int i = r * 32 + lane;
+            if (r >= rs && i > s && i < m) x[r] = fma(-Lc[i], xs, x[r]);
         }
-        if (s < t) s0 -= q[s] * L[(long long)s * ldl + p];
-        const double v = (s0 + s1) / L[(long long)t * ldl + p];
-        q[t] = v;
-        Q[(long long)t * ldq + row] = v;
     }
 }
 
@@ -197,6 +409,123 @@ __global__ void k_tridiag(ModeMap mm, double* A, long long astride, int lda, con
             tau[k - 2] = 0.0;
         } else if (k == 1) {
             d[0] = A[0];
+        }
+    }
+}
+
+// Same reduction as k_tridiag with the trailing block in shared memory (packed lower
+// triangle): p = A22 v by row groups x column chunks, the rank-2 update on the lower triangle
+// only (column c by a warp, rows i >= c by its lanes).
+__global__ void __launch_bounds__(SM_THREADS) k_tridiag_smem(ModeMap mm, double* A, long long astride, int lda,
+                                                            const int* dk, double* d, double* e, double* tau,
+                                                            int vstride)
+{
+    const int b = mm.m[blockIdx.x];
+    const int k = dk[b];
+    A += b * astride;
+    d += b * vstride;
+    e += b * vstride;
+    tau += b * vstride;
+    extern __shared__ double S[];
+    __shared__ double v[KMAX], w[KMAX];
+    __shared__ double part[SM_THREADS];
+    __shared__ double red[33];
+    __shared__ double sc[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int c = warp; c < k; c += SM_THREADS / 32) {
+        const int o = pk_off(c, k) - c;
+        for (int i = c + lane; i < k; i += 32) S[o + i] = A[(long long)c * lda + i];
+    }
+    __syncthreads();
+    for (int j = 0; j + 2 < k; ++j) {
+        const int len = k - j - 1, c0 = j + 1;
+        const int oj = pk_off(j, k) - j;
+        const double x0 = S[oj + c0];
+        const double xi = (tid >= 1 && tid < len) ? S[oj + c0 + tid] : 0.0;
+        // tail norm, then alpha and tau by thread 0 (one FP64 sqrt and division, shared)
+        double ts = xi * xi;
+        const int nwa = (len + 31) >> 5;
+        if (warp < nwa) ts = warp_sum(ts);
+        if (lane == 0 && warp < nwa) red[warp] = ts;
+        __syncthreads();
+        if (warp == 0) {
+            double t2 = lane < nwa ? red[lane] : 0.0;
+            t2 = warp_sum(t2);
+            if (lane == 0) {
+                double tj = 0.0, al = x0;
+                if (t2 != 0.0) {
+                    const double xn = sqrt(x0 * x0 + t2);
+                    al = (x0 >= 0.0) ? -xn : xn;
+                    const double v0 = x0 - al;
+                    tj = 2.0 / (v0 * v0 + t2);
+                }
+                sc[0] = tj;
+                sc[1] = al;
+            }
+        }
+        __syncthreads();
+        const double t_j = sc[0], alpha = sc[1];
+        if (tid < len) {
+            const double vi = (t_j == 0.0) ? 0.0 : (tid == 0 ? x0 - alpha : xi);
+            v[tid] = vi;
+            A[(long long)j * lda + c0 + tid] = vi;       // the reflector, for the back-transformation
+        }
+        if (tid == 0) { tau[j] = t_j; e[j] = alpha; d[j] = S[oj + j]; }
+        __syncthreads();
+        if (t_j != 0.0) {
+            const SplitRC sp(len, len);
+            for (int task = warp; task < sp.rg * sp.nch; task += SM_THREADS / 32) {
+                const int rg = task / sp.nch, ch = task - rg * sp.nch;
+                const int i = rg * 32 + lane;
+                double acc = 0.0;
+                if (i < len) {
+                    const int gi = c0 + i;
+                    const int cb = ch * sp.clen, ce = min(len, cb + sp.clen);
+                    const int oi = pk_off(gi, k) - gi;
+                    for (int c = cb; c < ce; ++c) {
+                        const int gc = c0 + c;
+                        const int idx = gi >= gc ? pk_off(gc, k) - gc + gi : oi + gc;
+                        acc = fma(S[idx], v[c], acc);
+                    }
+                }
+                part[task * 32 + lane] = acc;
+            }
+            __syncthreads();
+            double pi = 0.0;
+            if (tid < len) {
+                const int rg = tid >> 5;
+                for (int ch = 0; ch < sp.nch; ++ch) pi += part[(rg * sp.nch + ch) * 32 + lane];
+                pi *= t_j;
+            }
+            double pv = tid < len ? pi * v[tid] : 0.0;
+            if (warp < nwa) pv = warp_sum(pv);
+            if (lane == 0 && warp < nwa) red[warp] = pv;
+            __syncthreads();
+            if (warp == 0) {
+                double t2 = lane < nwa ? red[lane] : 0.0;
+                t2 = warp_sum(t2);
+                if (lane == 0) sc[0] = 0.5 * t_j * t2;
+            }
+            __syncthreads();
+            const double Kc = sc[0];
+            if (tid < len) w[tid] = pi - Kc * v[tid];
+            __syncthreads();
+            for (int c = warp; c < len; c += SM_THREADS / 32) {
+                const double vc = v[c], wc = w[c];
+                double* Sc = S + pk_off(c0 + c, k) - (c0 + c) + c0;    // row i (relative) at Sc[i]
+                for (int i = c + lane; i < len; i += 32) Sc[i] = fma(-v[i], wc, fma(-w[i], vc, Sc[i]));
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (k >= 2) {
+            d[k - 2] = S[pk_off(k - 2, k)];
+            d[k - 1] = S[pk_off(k - 1, k)];
+            e[k - 2] = S[pk_off(k - 2, k) + 1];
+            tau[k - 2] = 0.0;
+        } else if (k == 1) {
+            d[0] = S[0];
         }
     }
 }
@@ -558,19 +887,34 @@ __global__ void k_trace(ModeMap mm, const double* A, long long astride, int lda,
 }
 
 
-int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, double* L, long long lstride,
-                int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot, double tol, int nb,
-                cudaStream_t st)
+int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int* kx_out, double* L,
+                long long lstride, int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot, double tol, int nb,
+                int kbound, cudaStream_t st)
 {
-    k_chol_piv<<<nb, KMAX, 0, st>>>(mm, G, gstride, ldg, dk, 0, L, lstride, ldl, perm, pstride, dm_out, fail, pivot, tol);
+    if (kbound <= SM_PACK_K) {
+        const size_t smem = sizeof(double) * (size_t)kbound * (kbound + 1) / 2;
+        static bool attr = false;
+        if (!attr) {
+            if (cudaFuncSetAttribute(k_chol_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(double) * SM_PACK_K * (SM_PACK_K + 1) / 2)) != cudaSuccess)
+                return RHOSVD_ERR_CUDA;
+            attr = true;
+        }
+        k_chol_smem<<<nb, SM_THREADS, smem, st>>>(mm, G, gstride, ldg, dk, kx_out, L, lstride, ldl, perm, pstride,
+                                                  dm_out, fail, pivot, tol);
+    } else {
+        k_chol_piv<<<nb, KMAX, 0, st>>>(mm, G, gstride, ldg, dk, 0, kx_out, L, lstride, ldl, perm, pstride, dm_out,
+                                        fail, pivot, tol);
+    }
     RH_CHECK_LAUNCH();
     return 0;
 }
 
-int launch_trsm(ModeMap mm, const TrsmArgs& a, int nmax, int nb, cudaStream_t st)
+int launch_trinv(ModeMap mm, const double* L, long long lstride, int ldl, const int* perm, int pstride,
+                 const int* dkx, const int* dm, double* W, long long wstride, int ldw, int nb, cudaStream_t st)
 {
-    dim3 grid((nmax + 31) / 32, nb);
-    k_trsm_rows<<<grid, 32, 0, st>>>(mm, a);
+    dim3 grid((KMAX + 3) / 4, nb);
+    k_trinv<<<grid, 128, 0, st>>>(mm, L, lstride, ldl, perm, pstride, dkx, dm, W, wstride, ldw);
     RH_CHECK_LAUNCH();
     return 0;
 }
@@ -584,9 +928,21 @@ int launch_trace(ModeMap mm, const double* A, long long astride, int lda, const 
 }
 
 int launch_tridiag(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e, double* tau,
-                   int vstride, int nb, cudaStream_t st)
+                   int vstride, int nb, int kbound, cudaStream_t st)
 {
-    k_tridiag<<<nb, KMAX, 0, st>>>(mm, A, astride, lda, dk, d, e, tau, vstride);
+    if (kbound <= SM_PACK_K) {
+        const size_t smem = sizeof(double) * (size_t)kbound * (kbound + 1) / 2;
+        static bool attr = false;
+        if (!attr) {
+            if (cudaFuncSetAttribute(k_tridiag_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(double) * SM_PACK_K * (SM_PACK_K + 1) / 2)) != cudaSuccess)
+                return RHOSVD_ERR_CUDA;
+            attr = true;
+        }
+        k_tridiag_smem<<<nb, SM_THREADS, smem, st>>>(mm, A, astride, lda, dk, d, e, tau, vstride);
+    } else {
+        k_tridiag<<<nb, KMAX, 0, st>>>(mm, A, astride, lda, dk, d, e, tau, vstride);
+    }
     RH_CHECK_LAUNCH();
     return 0;
 }
