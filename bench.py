@@ -206,13 +206,16 @@ def algorithmic_flops(stage, info, n, R):
 
 def tucker_rel_diff_torch(beta_a, Z_a, beta_b, Z_b):
     """||T_a - T_b|| / ||T_b|| for orthonormal Tucker factors, via a common basis per mode
-    (measurement aid for the bench line; torch linear algebra, not the product path)."""
+    (measurement aid for the bench line; torch linear algebra on the host, not the product
+    path)."""
     import torch
-    ca, cb = beta_a, beta_b
+    ca, cb = beta_a.cpu(), beta_b.cpu()
+    Za = [z.cpu() for z in Z_a]
+    Zb = [z.cpu() for z in Z_b]
     for l in range(3):
-        Pm, _ = torch.linalg.qr(torch.cat([Z_a[l], Z_b[l]], dim=1))
-        ca = torch.movedim(torch.tensordot(Pm.T @ Z_a[l], ca, dims=([1], [l])), 0, l)
-        cb = torch.movedim(torch.tensordot(Pm.T @ Z_b[l], cb, dims=([1], [l])), 0, l)
+        Pm, _ = torch.linalg.qr(torch.cat([Za[l], Zb[l]], dim=1))
+        ca = torch.movedim(torch.tensordot(Pm.T @ Za[l], ca, dims=([1], [l])), 0, l)
+        cb = torch.movedim(torch.tensordot(Pm.T @ Zb[l], cb, dims=([1], [l])), 0, l)
     return (torch.linalg.norm(ca - cb) / torch.linalg.norm(cb)).item()
 
 

@@ -116,6 +116,7 @@ struct Plan {
     int KW;               // max k_l over modes
     int NQ;               // max n_l over modes
     int ks_sketch, ks_gram, ks_bbt;
+    size_t o_cpart;
     size_t o_state, o_norms, o_keep, o_nn2, o_Un, o_xin, o_bufA, o_bufB, o_G, o_L, o_perm, o_B, o_vec, o_W, o_V, o_Z, o_rp,
         o_part;
     // mixed-precision form: digit planes and helpers
@@ -123,6 +124,8 @@ struct Plan {
     int ldR, ldn, ldk;            // plane row lengths (multiples of 8) for K = R, n, k
     size_t o_pU1, o_pU2, o_pP1, o_pP2, o_eU1, o_eU2, o_eP1, o_eP2, o_Vt;
     long long EX;         // per-mode stride of the per-row exponent arrays
+    int oz_s_sketch, oz_s_gram, oz_s_bbt;   // split-K counts of the tensor-core products
+    size_t o_ozpart;      // their partial sums
     long long sU1, sU2, sP1, sP2; // per-mode plane-set sizes (elements)
     long long rp_stride;   // residual partials per mode (tiles of the residual GEMM)
     size_t total;
@@ -206,6 +209,7 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
     p->o_Z = take(sizeof(double) * 3 * NK);
     p->rp_stride = (long long)((p->NQ + 63) / 64) * ((R + 63) / 64);
     p->o_rp = take(sizeof(double) * 3 * (size_t)p->rp_stride);
+    p->o_cpart = take(sizeof(double) * 3 * (size_t)rh::RITZ_CHUNKS * rh::KMAX);
     p->o_part = take(sizeof(double) * (size_t)part);
     p->mixed = (o->precision == RHOSVD_MIXED);
     if (p->mixed) {
@@ -234,6 +238,15 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
         p->o_eP1 = take(3 * (size_t)p->EX);
         p->o_eP2 = take(3 * (size_t)p->EX);
         p->o_Vt = take(sizeof(double) * 3 * (size_t)R * p->KW);
+        int nsk = 0;
+        for (int l = 0; l < 3; ++l) nsk += p->direct[l] ? 0 : 1;
+        p->oz_s_sketch = nsk > 0 ? rh::oz_choose_split((int)p->NQ, p->KW, R, 96, nsk) : 1;
+        p->oz_s_gram = nsk > 0 ? rh::oz_choose_split(p->KW, p->KW, (int)p->NQ, rh::OZ_NT6, nsk) : 1;
+        p->oz_s_bbt = rh::oz_choose_split(p->KW, p->KW, R, rh::OZ_NT6, 3);
+        long long zp = 3LL * p->oz_s_sketch * NK;
+        if (3LL * p->oz_s_gram * KK > zp) zp = 3LL * p->oz_s_gram * KK;
+        if (3LL * p->oz_s_bbt * KK > zp) zp = 3LL * p->oz_s_bbt * KK;
+        p->o_ozpart = take(sizeof(double) * (size_t)zp);
     }
     p->total = off;
     return RHOSVD_OK;
@@ -339,6 +352,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     signed char* eP2 = mixed ? (signed char*)(ws + p.o_eP2) : nullptr;
     const long long EX = mixed ? p.EX : 0;
     double* Vt = mixed ? (double*)(ws + p.o_Vt) : nullptr;
+    double* ozpart = mixed ? (double*)(ws + p.o_ozpart) : nullptr;
     int* ozerr = &out->info->status;
 
     // ---- reset outputs and state
@@ -440,6 +454,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             OzBatch ob;
             memset(&ob, 0, sizeof(ob));
             ob.nbatch = nsk;
+            ob.nsplit = p.oz_s_sketch;
             ob.err = ozerr;
             for (int b = 0; b < nsk; ++b) {
                 const int l = sk.m[b];
@@ -453,6 +468,8 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 q.ccs = p.n[l];
                 q.seed = opts->seed;
                 q.mode = l;
+                q.Cpart = ozpart + (size_t)l * p.oz_s_sketch * NK;
+                q.split_stride = NK;
             }
             STAGE("sketch", launch_ozgemm(ob, OZ_SKETCH, st));
         } else {
@@ -485,9 +502,46 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 if (pass > 0) { g.dM = &S->m[l]; g.dN = &S->m[l]; }
                 g2.p[b] = g;
             }
-            // Grams stay FP64: they square the condition number, and the directions at the eps
-            // boundary sit ~1e-13 below the largest ones
-            STAGE("cholqr_gram", launch_gemm_splitk(g2, part, st));
+            if (mixed) {
+                // G = X^T X on the tensor cores: rows c of the operand = columns of X (k = x);
+                // every digit group is exact, so the Gram keeps FP64-class accuracy
+                OzSliceArgs sg;
+                memset(&sg, 0, sizeof(sg));
+                sg.S = 6;
+                OzBatch ob;
+                memset(&ob, 0, sizeof(ob));
+                ob.nbatch = nsk;
+                ob.nsplit = p.oz_s_gram;
+                ob.err = ozerr;
+                for (int b = 0; b < nsk; ++b) {
+                    const int l = sk.m[b];
+                    sg.X[b] = X + l * NK;
+                    sg.rs[b] = p.n[l];
+                    sg.cs[b] = 1;
+                    sg.rows[b] = p.kin[l];
+                    sg.drows[b] = pass > 0 ? &S->m[l] : nullptr;
+                    sg.K[b] = p.n[l];
+                    sg.planes[b] = pP2 + l * p.sP2;
+                    sg.pstride[b] = (long long)p.kin[l] * p.ldn;
+                    sg.ld[b] = p.ldn;
+                    sg.exps[b] = eP2 + l * EX;
+                    OzProblem& q = ob.p[b];
+                    q.A = OzPlanes{sg.planes[b], sg.pstride[b], p.ldn, sg.exps[b], 0};
+                    q.B = q.A;
+                    q.M = q.N = p.kin[l];
+                    if (pass > 0) q.dM = q.dN = &S->m[l];
+                    q.K = p.n[l];
+                    q.C = G + l * KK;
+                    q.crs = 1;
+                    q.ccs = KW;
+                    q.Cpart = ozpart + (size_t)l * p.oz_s_gram * KK;
+                    q.split_stride = KK;
+                }
+                STAGE("cholqr_gram", launch_oz_slice(sg, nsk, st));
+                STAGE("cholqr_gram", launch_ozgemm(ob, OZ_F64_STORE, st));
+            } else {
+                STAGE("cholqr_gram", launch_gemm_splitk(g2, part, st));
+            }
             const int* dk = (pass == 0) ? S->kin : S->m;
             STAGE("cholqr_chol", launch_chol(sk, G, KK, KW, dk, S->kx, L, KK, KW, perm, KW, S->m, S->piv_fail,
                                              pivots[pass], tols[pass], nsk, KW, st));
@@ -645,7 +699,44 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             g.dN = &S->m[l];
             gm.p[l] = g;
         }
-        STAGE("gram_bbt", launch_gemm_splitk(gm, part, st));   // FP64 in both forms (see above)
+        if (mixed) {
+            // M = B B^T on the tensor cores: rows i of B (k = nu, stride KW)
+            OzSliceArgs sg;
+            memset(&sg, 0, sizeof(sg));
+            sg.S = 6;
+            OzBatch ob;
+            memset(&ob, 0, sizeof(ob));
+            ob.nbatch = 3;
+            ob.nsplit = p.oz_s_bbt;
+            ob.err = ozerr;
+            for (int l = 0; l < 3; ++l) {
+                sg.X[l] = Bm + (size_t)l * KW * R;
+                sg.rs[l] = 1;
+                sg.cs[l] = KW;
+                sg.rows[l] = p.kin[l];
+                sg.drows[l] = &S->m[l];
+                sg.K[l] = R;
+                sg.planes[l] = pP1 + l * p.sP1;
+                sg.pstride[l] = (long long)p.kin[l] * p.ldR;
+                sg.ld[l] = p.ldR;
+                sg.exps[l] = eP1 + l * EX;
+                OzProblem& q = ob.p[l];
+                q.A = OzPlanes{sg.planes[l], sg.pstride[l], p.ldR, sg.exps[l], 0};
+                q.B = q.A;
+                q.M = q.N = p.kin[l];
+                q.dM = q.dN = &S->m[l];
+                q.K = R;
+                q.C = G + l * KK;
+                q.crs = 1;
+                q.ccs = KW;
+                q.Cpart = ozpart + (size_t)l * p.oz_s_bbt * KK;
+                q.split_stride = KK;
+            }
+            STAGE("gram_bbt", launch_oz_slice(sg, 3, st));
+            STAGE("gram_bbt", launch_ozgemm(ob, OZ_F64_STORE, st));
+        } else {
+            STAGE("gram_bbt", launch_gemm_splitk(gm, part, st));
+        }
     }
     if (R == 0 && cudaMemsetAsync(G, 0, sizeof(double) * 3 * KK, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
     STAGE("trace", launch_trace(all, G, KK, KW, S->m, S->trace, 3, st));
@@ -723,7 +814,56 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             e.rpart = rpart + l * p.rp_stride;
             gr.p[l] = e;
         }
-        STAGE("z_hi", launch_gemm(gz, st));
+        if (mixed) {
+            // Z_hi = Q W on the tensor cores: rows x of Q (k = i), rows j of W^T (k = i)
+            OzSliceArgs sq, sw;
+            memset(&sq, 0, sizeof(sq));
+            memset(&sw, 0, sizeof(sw));
+            sq.S = sw.S = 6;
+            OzBatch oz;
+            memset(&oz, 0, sizeof(oz));
+            oz.nbatch = 3;
+            oz.err = ozerr;
+            for (int l = 0; l < 3; ++l) {
+                sq.X[l] = Qfin[l];
+                sq.rs[l] = 1;
+                sq.cs[l] = ldq[l];
+                sq.rows[l] = p.n[l];
+                sq.K[l] = p.kin[l];
+                sq.dK[l] = &S->m[l];
+                sq.planes[l] = pP2 + l * p.sP2;
+                sq.pstride[l] = (long long)p.n[l] * p.ldk;
+                sq.ld[l] = p.ldk;
+                sq.exps[l] = eP2 + l * EX;
+                sw.X[l] = W + l * KK;
+                sw.rs[l] = KW;
+                sw.cs[l] = 1;
+                sw.rows[l] = p.kin[l];
+                sw.drows[l] = &S->rhi[l];
+                sw.K[l] = p.kin[l];
+                sw.dK[l] = &S->m[l];
+                sw.planes[l] = pP1 + l * p.sP1;
+                sw.pstride[l] = (long long)p.kin[l] * p.ldk;
+                sw.ld[l] = p.ldk;
+                sw.exps[l] = eP1 + l * EX;
+                OzProblem& q = oz.p[l];
+                q.A = OzPlanes{sq.planes[l], sq.pstride[l], p.ldk, sq.exps[l], 0};
+                q.B = OzPlanes{sw.planes[l], sw.pstride[l], p.ldk, sw.exps[l], 0};
+                q.M = p.n[l];
+                q.N = p.kin[l];
+                q.dN = &S->rhi[l];
+                q.K = p.kin[l];
+                q.dK = &S->m[l];
+                q.C = Zw + l * NK;
+                q.crs = 1;
+                q.ccs = p.n[l];
+            }
+            STAGE("z_hi", launch_oz_slice(sq, 3, st));
+            STAGE("z_hi", launch_oz_slice(sw, 3, st));
+            STAGE("z_hi", launch_ozgemm(oz, OZ_F64_STORE, st));
+        } else {
+            STAGE("z_hi", launch_gemm(gz, st));
+        }
         if (mixed) {
             // V_hi (rhi x R, ld KW) = W^T B: rows nu of B (k = i) times rows j of W (k = i)
             OzSliceArgs s1, s2;
@@ -834,6 +974,9 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     fa.st = S;
     fa.rpart = rpart;
     fa.rpstride = p.rp_stride;
+    fa.cpart = (double*)(ws + p.o_cpart);
+    fa.nchunk = R > 0 ? (R + 63) / 64 : 1;
+    if (fa.nchunk > rh::RITZ_CHUNKS) fa.nchunk = rh::RITZ_CHUNKS;
     for (int l = 0; l < 3; ++l) {
         fa.ranks[l] = opts->ranks[l];
         fa.ntiles[l] = mixed ? ((R + OZ_BM - 1) / OZ_BM) * ((p.NQ + OZ_NT6 - 1) / OZ_NT6) : (int)p.rp_stride;

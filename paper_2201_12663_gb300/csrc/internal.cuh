@@ -208,7 +208,10 @@ struct FinalArgs {
     const double* rpart;     // residual partials per mode
     int ntiles[3];
     long long rpstride;
+    double* cpart;           // Ritz energy partials: [mode][chunk][KMAX]
+    int nchunk;              // chunks of nu (at most RITZ_CHUNKS)
 };
+constexpr int RITZ_CHUNKS = 256;
 
 // ---------------------------------------------------------------- launchers (return 0 or RHOSVD_ERR_CUDA)
 int launch_gemm(GemmBatch& gb, cudaStream_t st);

@@ -136,10 +136,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
     static_assert(NT % 32 == 0 && NT >= 32 && NU * NT <= 512, "tile: 8-column TMEM loads per thread quarter");
     static_assert(GMAX >= 2 && GMAX <= SA + SB && NACC >= 2, "groups");
     static_assert(oz_exact_ok(SA, SB, NE), "an exact group needs at most 8 pairs");
-    const OzProblem& P = batch.p[blockIdx.z];
+    const int nsplit = batch.nsplit > 1 ? batch.nsplit : 1;
+    const int split = blockIdx.z % nsplit;
+    const OzProblem& P = batch.p[blockIdx.z / nsplit];
     int M = P.M_from_r2r3 ? (*P.dNa) * (*P.dNb) : oz_dim(P.dM, P.M);
     const int N = oz_dim(P.dN, P.N);
-    const int K = oz_dim(P.dK, P.K);
+    const int Kall = oz_dim(P.dK, P.K);
+    // this CTA's K range [kbase, kbase + K): whole stages, the last split takes the rest
+    const int kspan = ((Kall + nsplit - 1) / nsplit + OZ_BK - 1) / OZ_BK * OZ_BK;
+    const int kbase = min(Kall, split * kspan);
+    const int K = min(Kall, kbase + kspan) - kbase;
+    double* const Cout = nsplit > 1 ? P.Cpart + split * P.split_stride : P.C;
     const int i0 = blockIdx.x * OZ_BM, j0 = blockIdx.y * NT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (i0 >= M || j0 >= N) {
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
     auto produce = [&](int kt, int buf) {
         unsigned char* sA = oz_smem + buf * STAGE;
         unsigned char* sB = sA + SA * A_PLANE;
-        const int k0 = kt * OZ_BK;
+        const int k0 = kbase + kt * OZ_BK;
         // A: 128 rows x 4 chunks of 8
         for (int e = tid; e < OZ_BM * 4; e += OZ_THREADS) {
             const int r = e >> 2, c = e & 3;
@@ -185,7 +192,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
 #pragma unroll
                 for (int s = 0; s < SA; ++s) {
                     uint4 v = make_uint4(0, 0, 0, 0);
-                    if (gi < M && gk < K)
+                    if (gi < M && gk < kbase + K)
                         v = *reinterpret_cast<const uint4*>(P.A.base + s * P.A.pstride + (long long)gi * P.A.ld + gk);
                     *reinterpret_cast<uint4*>(sA + s * A_PLANE + oz_off(r, c)) = v;
                 }
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     double x = 0.0;
-                    if (gi < M && gk + q < K)
+                    if (gi < M && gk + q < kbase + K)
                         x = P.kr.V2t[(long long)jj * P.kr.ldt + gk + q] * P.kr.V3t[(long long)mm * P.kr.ldt + gk + q];
                     oz_digits(x, 0, SA, d[q]);
                 }
@@ -218,7 +225,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
 #pragma unroll
                 for (int t = 0; t < SB; ++t) {
                     uint4 v = make_uint4(0, 0, 0, 0);
-                    if (gj < N && gk < K)
+                    if (gj < N && gk < kbase + K)
                         v = *reinterpret_cast<const uint4*>(P.B.base + t * P.B.pstride + (long long)gj * P.B.ld + gk);
                     *reinterpret_cast<uint4*>(sB + t * B_PLANE + oz_off(r, c)) = v;
                 }
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     d[q] = 0;
-                    if (gj < N && gk + q < K)
+                    if (gj < N && gk + q < kbase + K)
                         d[q] = rademacher(P.seed, P.mode, gk + q, gj) > 0.0 ? (uint16_t)0x3F80 : (uint16_t)0xBF80;
                 }
                 uint4 v;
@@ -322,7 +329,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
         double v = (double)hi[c] + (double)lo[c];
         v = ldexp(v, ea + eb - 16);
         if (EPI == OZ_EPI_STORE) {
-            P.C[(long long)row * crs + (long long)col * ccs] = v;
+            Cout[(long long)row * crs + (long long)col * ccs] = v;
         } else {
             const double d = P.ref[(long long)row * P.ref_rs + (long long)col * P.ref_cs] - v;
             e2 = fma(d, d, e2);
@@ -386,6 +393,34 @@ __global__ void k_oz_slice(OzSliceArgs a)
     }
 }
 
+// C(i, j) = sum over the splits of the partials, in split order.  grid (ceil(MN / 256), nb).
+__global__ void k_oz_reduce(OzBatch batch)
+{
+    const OzProblem& P = batch.p[blockIdx.y];
+    const int M = P.M_from_r2r3 ? (*P.dNa) * (*P.dNb) : oz_dim(P.dM, P.M);
+    const int N = oz_dim(P.dN, P.N);
+    const long long crs = P.crs < 0 ? (long long)N : P.crs;
+    const long long ccs = P.ccs < 0 ? (long long)M : P.ccs;
+    const long long total = (long long)M * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % M), j = (int)(e / M);
+        const long long o = i * crs + j * ccs;
+        double s = 0.0;
+        for (int sp = 0; sp < batch.nsplit; ++sp) s += P.Cpart[sp * P.split_stride + o];
+        P.C[o] = s;
+    }
+}
+
+int oz_choose_split(int M, int N, int K, int nt, int nbatch)
+{
+    const long long tiles = (long long)((M + OZ_BM - 1) / OZ_BM) * ((N + nt - 1) / nt) * (nbatch > 0 ? nbatch : 1);
+    const int stages = (K + OZ_BK - 1) / OZ_BK;
+    int s = 1;
+    while (tiles * s * 2 <= 2 * 152 && stages / (s * 2) >= 4) s *= 2;
+    return s;
+}
+
 int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st)
 {
     int rmax = 0;
@@ -415,9 +450,17 @@ static int run_oz(const OzBatch& b, cudaStream_t st)
             return RHOSVD_ERR_CUDA;
         attr = true;
     }
-    dim3 grid((Mh + OZ_BM - 1) / OZ_BM, (Nh + NT - 1) / NT, b.nbatch);
+    const int nsplit = b.nsplit > 1 ? b.nsplit : 1;
+    if (nsplit > 1 && EPI != OZ_EPI_STORE) return RHOSVD_ERR_INVALID_ARG;
+    dim3 grid((Mh + OZ_BM - 1) / OZ_BM, (Nh + NT - 1) / NT, b.nbatch * nsplit);
     k_ozgemm<SA, SB, GMAX, ASRC, BSRC, EPI, NT, NACC><<<grid, OZ_THREADS, SMEM, st>>>(b);
     RH_CHECK_LAUNCH();
+    if (nsplit > 1) {
+        const long long mn = (long long)Mh * Nh;
+        dim3 rg((unsigned)((mn + 255) / 256 < 4096 ? (mn + 255) / 256 : 4096), b.nbatch);
+        k_oz_reduce<<<rg, 256, 0, st>>>(b);
+        RH_CHECK_LAUNCH();
+    }
     return 0;
 }
 

@@ -65,11 +65,17 @@ struct OzProblem {
     double* rpart;
     uint64_t seed;               // Rademacher B: element (k, j) = sign(seed, mode, k, j)
     int mode;
+    // split-K (EPI_STORE only): with OzBatch::nsplit > 1, split s sums K range s of nsplit
+    // (multiples of 32) into Cpart + s * split_stride, laid out like C; k_oz_reduce then adds
+    // the partials into C in a fixed order
+    double* Cpart;
+    long long split_stride;
 };
 
 struct OzBatch {
     OzProblem p[3];
     int nbatch;
+    int nsplit;                  // 0 or 1: no split
     int* err;                    // status word: RHOSVD_ERR_TIMEOUT if a bounded wait gave up
 };
 
@@ -130,5 +136,8 @@ int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st);
 // the residual energy; range sketch against Rademacher signs; Khatri-Rao core (S = 4)
 enum OzKind { OZ_F64_STORE = 0, OZ_F64_RESID = 1, OZ_SKETCH = 2, OZ_CORE = 3 };
 int launch_ozgemm(const OzBatch& b, OzKind kind, cudaStream_t st);
+
+// split count for an M x N x K product: enough CTAs for two per SM, at least 4 stages each
+int oz_choose_split(int M, int N, int K, int nt, int nbatch);
 
 }  // namespace rh

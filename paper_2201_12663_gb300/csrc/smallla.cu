@@ -705,6 +705,25 @@ __global__ void k_rank_select(RankArgs a)
 //   rho^2 = ||U - Z_hi V_hi||_F^2 (residual GEMM partials), c_j = ||V_hi(j,:)||^2,
 //   tail(r) = rho^2 + sum_{r <= j < rhi} c_j,  r = min r with tail(r) <= eps^2 total.
 // One block per mode.
+// Ritz energy partials: cpart[b][ch][j] = sum over nu in chunk ch of V_hi(j, nu)^2, thread j
+// (coalesced along j).  grid (nchunk, 3), block KMAX.
+__global__ void k_ritz_partial(FinalArgs a)
+{
+    const int b = blockIdx.y, ch = blockIdx.x, j = threadIdx.x;
+    const int rhi = a.st->rhi[b];
+    const int clen = (a.R + a.nchunk - 1) / a.nchunk;
+    const int nu0 = ch * clen, nu1 = min(a.R, nu0 + clen);
+    double e = 0.0;
+    if (j < rhi) {
+        const double* V = a.V + b * a.vstride + j;
+        for (int nu = nu0; nu < nu1; ++nu) {
+            const double v = V[(long long)nu * a.ldv];
+            e = fma(v, v, e);
+        }
+    }
+    a.cpart[((long long)b * a.nchunk + ch) * KMAX + j] = e;
+}
+
 __global__ void k_rank_final(FinalArgs a)
 {
     const int b = blockIdx.x;
@@ -715,16 +734,11 @@ __global__ void k_rank_final(FinalArgs a)
     double s = 0.0;
     for (int t = threadIdx.x; t < a.ntiles[b]; t += blockDim.x) s += part[t];
     const double rho2 = block_sum(s, red);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const double* V = a.V + b * a.vstride;
-    for (int j = w; j < rhi; j += nw) {
+    for (int j = threadIdx.x; j < rhi; j += blockDim.x) {
+        const double* cp = a.cpart + (long long)b * a.nchunk * KMAX + j;
         double e = 0.0;
-        for (int nu = lane; nu < a.R; nu += 32) {
-            const double v = V[(long long)nu * a.ldv + j];
-            e = fma(v, v, e);
-        }
-        e = warp_sum(e);
-        if (lane == 0) c[j] = e;
+        for (int ch = 0; ch < a.nchunk; ++ch) e += cp[(long long)ch * KMAX];
+        c[j] = e;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -967,6 +981,8 @@ int launch_rank(const RankArgs& a, cudaStream_t st)
 
 int launch_rank_final(const FinalArgs& a, cudaStream_t st)
 {
+    k_ritz_partial<<<dim3(a.nchunk, 3), KMAX, 0, st>>>(a);
+    RH_CHECK_LAUNCH();
     k_rank_final<<<3, 256, 0, st>>>(a);
     RH_CHECK_LAUNCH();
     return 0;
