@@ -116,13 +116,13 @@ struct Plan {
     int KW;               // max k_l over modes
     int NQ;               // max n_l over modes
     int ks_sketch, ks_gram, ks_bbt;
-    size_t o_cpart;
+    size_t o_cpart, o_colmax;
     size_t o_state, o_norms, o_keep, o_nn2, o_Un, o_xin, o_bufA, o_bufB, o_G, o_L, o_perm, o_B, o_vec, o_W, o_V, o_Z, o_rp,
         o_part;
     // mixed-precision form: digit planes and helpers
     int mixed;
     int ldR, ldn, ldk;            // plane row lengths (multiples of 8) for K = R, n, k
-    size_t o_pU1, o_pU2, o_pP1, o_pP2, o_eU1, o_eU2, o_eP1, o_eP2, o_Vt;
+    size_t o_pU1, o_pU2, o_pP1, o_pP2, o_eU2, o_eP1, o_eP2, o_Vt;
     long long EX;         // per-mode stride of the per-row exponent arrays
     int oz_s_sketch, oz_s_gram, oz_s_bbt;   // split-K counts of the tensor-core products
     size_t o_ozpart;      // their partial sums
@@ -193,6 +193,7 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
     auto take = [&](size_t bytes) { size_t o2 = off; off += up(bytes); return o2; };
     p->o_state = take(sizeof(DevState));
     p->o_norms = take(sizeof(double) * 3 * R);
+    p->o_colmax = take(sizeof(double) * 3 * R);
     p->o_keep = take(sizeof(double) * R);
     p->o_nn2 = take(sizeof(double) * 3 * R);
     p->o_Un = take(sizeof(double) * 3 * (size_t)p->NQ * R);
@@ -233,7 +234,6 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
         p->o_pP2 = take(sizeof(uint16_t) * 3 * (size_t)p->sP2);
         long long ex = p->NQ > R ? p->NQ : R;
         p->EX = ex > p->KW ? ex : p->KW;
-        p->o_eU1 = take(3 * (size_t)p->EX);
         p->o_eU2 = take(3 * (size_t)p->EX);
         p->o_eP1 = take(3 * (size_t)p->EX);
         p->o_eP2 = take(3 * (size_t)p->EX);
@@ -313,6 +313,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     char* ws = (char*)workspace;
     DevState* S = (DevState*)(ws + p.o_state);
     double* norms = (double*)(ws + p.o_norms);
+    double* colmax = (double*)(ws + p.o_colmax);
     double* keepf = (double*)(ws + p.o_keep);
     double* nn2 = (double*)(ws + p.o_nn2);
     double* Un = (double*)(ws + p.o_Un);
@@ -346,7 +347,6 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     uint16_t* pP1 = mixed ? (uint16_t*)(ws + p.o_pP1) : nullptr;
     uint16_t* pP2 = mixed ? (uint16_t*)(ws + p.o_pP2) : nullptr;
     // per-row exponents of the digit planes (one array per plane buffer, stride EX per mode)
-    signed char* eU1 = mixed ? (signed char*)(ws + p.o_eU1) : nullptr;
     signed char* eU2 = mixed ? (signed char*)(ws + p.o_eU2) : nullptr;
     signed char* eP1 = mixed ? (signed char*)(ws + p.o_eP1) : nullptr;
     signed char* eP2 = mixed ? (signed char*)(ws + p.o_eP2) : nullptr;
@@ -371,8 +371,21 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
     for (int l = 0; l < 3; ++l) { na.U[l] = cp->U[l]; na.ld[l] = cp->ld[l]; na.n[l] = p.n[l]; }
     na.R = R;
     na.norms = norms;
+    na.colmax = colmax;
     STAGE("colnorms", launch_colnorms(na, st));
-    STAGE("normalize", launch_terms(na, cp->xi, keepf, xin, out->xi_out, out->info, Un, US, nn2, S->total, st));
+    // the mixed form cuts the projection operand's digit planes (rows nu, k = x, per-row
+    // exponents) while it writes the normalised columns
+    NormSlice ns;
+    memset(&ns, 0, sizeof(ns));
+    if (mixed) {
+        for (int l = 0; l < 3; ++l) {
+            ns.planes[l] = pU2 + l * p.sU2;
+            ns.pstride[l] = (long long)R * p.ldn;
+            ns.ld[l] = p.ldn;
+            ns.exps[l] = eU2 + l * EX;
+        }
+    }
+    STAGE("normalize", launch_terms(na, cp->xi, keepf, xin, out->xi_out, out->info, Un, US, nn2, S->total, ns, st));
 
     ModeMap all = {{0, 1, 2}};
     ModeMap sk;
@@ -391,42 +404,25 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
         }
     }
 
-    if (mixed && R > 0) {
-        // digit planes of the normalised side matrices: rows nu (k = x) for the projection, and
-        // rows x (k = nu) for the range sketch, each row with its own exponent
-        OzSliceArgs sa;
-        memset(&sa, 0, sizeof(sa));
-        sa.S = 6;
-        for (int l = 0; l < 3; ++l) {
-            sa.X[l] = Un + l * US;
-            sa.rs[l] = p.n[l];
-            sa.cs[l] = 1;
-            sa.rows[l] = R;
-            sa.K[l] = p.n[l];
-            sa.planes[l] = pU2 + l * p.sU2;
-            sa.pstride[l] = (long long)R * p.ldn;
-            sa.ld[l] = p.ldn;
-            sa.exps[l] = eU2 + l * EX;
+    if (mixed && R > 0 && nsk > 0) {
+        // digit planes of the range-sketch operand (rows x, k = nu): one fixed exponent (the
+        // normalised entries are below 2^1), which is all a random range sketch needs
+        SliceTArgs sb;
+        memset(&sb, 0, sizeof(sb));
+        sb.E0 = 1;
+        int nmax = 0;
+        for (int b = 0; b < nsk; ++b) {
+            const int l = sk.m[b];
+            sb.X[b] = Un + l * US;
+            sb.ldx[b] = p.n[l];
+            sb.rows[b] = p.n[l];
+            sb.K[b] = R;
+            sb.planes[b] = pU1 + l * p.sU1;
+            sb.pstride[b] = (long long)p.n[l] * p.ldR;
+            sb.ld[b] = p.ldR;
+            nmax = p.n[l] > nmax ? p.n[l] : nmax;
         }
-        STAGE("slice_u", launch_oz_slice(sa, 3, st));
-        if (nsk > 0) {
-            OzSliceArgs sb;
-            memset(&sb, 0, sizeof(sb));
-            sb.S = 6;
-            for (int b = 0; b < nsk; ++b) {
-                const int l = sk.m[b];
-                sb.X[b] = Un + l * US;
-                sb.rs[b] = 1;
-                sb.cs[b] = p.n[l];
-                sb.rows[b] = p.n[l];
-                sb.K[b] = R;
-                sb.planes[b] = pU1 + l * p.sU1;
-                sb.pstride[b] = (long long)p.n[l] * p.ldR;
-                sb.ld[b] = p.ldR;
-                sb.exps[b] = eU1 + l * EX;
-            }
-            STAGE("slice_u", launch_oz_slice(sb, nsk, st));
-        }
+        STAGE("slice_u", launch_slice_t(sb, nsk, p.ldR, nmax, st));
     }
 
     if (nsk > 0 && R > 0) {
@@ -459,7 +455,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             for (int b = 0; b < nsk; ++b) {
                 const int l = sk.m[b];
                 OzProblem& q = ob.p[b];
-                q.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, eU1 + l * EX, 0};
+                q.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1};
                 q.M = p.n[l];
                 q.N = p.kin[l];
                 q.K = R;
@@ -1023,7 +1019,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             // V^(2), V^(3) with nu-contiguous rows for the generated Khatri-Rao operand, and the
             // digit planes of diag(xi') V^(1) (rows i, k = nu, per-row exponents)
             const long long VTS = (long long)R * KW;
-            STAGE("core_prep", launch_transpose_v(Vw, VS, KW, Vt, VTS, R, R, S->r, 1, 2, st));
+            STAGE("core_prep", launch_transpose_v(Vw, VS, KW, (float2*)Vt, VTS, R, R, S->r, 1, 2, st));
             const int rcap = rmax < KW ? rmax : KW;   // a rank never exceeds the basis width
             OzSliceArgs s1;
             memset(&s1, 0, sizeof(s1));
@@ -1045,7 +1041,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             ob.nbatch = 1;
             ob.err = ozerr;
             OzProblem& q = ob.p[0];
-            q.kr = OzKR{Vt + VTS, Vt + 2 * VTS, R};
+            q.kr = OzKR{(const float2*)(Vt + VTS), (const float2*)(Vt + 2 * VTS), R};
             q.M = rcap * rcap;
             q.M_from_r2r3 = 1;
             q.dNa = &S->r[1];

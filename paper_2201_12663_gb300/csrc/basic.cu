@@ -2,12 +2,14 @@
 // canonical Hadamard product and sum (Sec. 3 eq. rho_ten, Lemma 4.2, Sec. 4.3), identity
 // basis for the direct mode.
 #include "internal.cuh"
+#include "ozgemm.cuh"
 
 namespace rh {
 
-// One warp per column: ||u|| = m * sqrt(sum (u_i 2^-e)^2) with m = 2^e >= max|u_i|, so the
-// scaling is exact and squares neither underflow nor overflow.  grid: (ceil(R/8), 3).
-
+// One warp per column: max |u_i| by an integer max over the sign-cleared bit patterns (a
+// non-negative double orders like its bits; NaN patterns sort above Inf), then
+// ||u|| = 2^ex sqrt(sum (u_i 2^-ex)^2) with max |u_i| < 2^ex, so the scaling is exact and the
+// squares neither underflow nor overflow.  Writes the norm and max |u_i|.  grid (ceil(R/8), 3).
 __global__ void k_colnorms(NormArgs a)
 {
     const int l = blockIdx.y;
@@ -16,34 +18,46 @@ __global__ void k_colnorms(NormArgs a)
     if (warp >= a.R) return;
     const double* u = a.U[l] + (long long)warp * a.ld[l];
     const int n = a.n[l];
-    double mx = 0.0;
-    for (int i = lane; i < n; i += 32) mx = fmax(mx, fabs(u[i]));
-    mx = warp_max(mx);
+    long long mb = 0;
+    for (int i = lane; i < n; i += 32) {
+        const long long b = __double_as_longlong(u[i]) & 0x7FFFFFFFFFFFFFFFll;
+        mb = b > mb ? b : mb;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long b = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = b > mb ? b : mb;
+    }
+    const double mx = __longlong_as_double(mb);
     double nrm;
-    if (mx == 0.0) {
+    if (mb == 0) {
         nrm = 0.0;
-    } else if (!isfinite(mx)) {
-        nrm = mx;                     // Inf (NaN propagates through fmax only if all NaN)
+    } else if (mb >= 0x7FF0000000000000ll) {
+        nrm = mx;                     // Inf, or NaN when a NaN is present
     } else {
         int ex;
-        frexp(mx, &ex);               // mx = f 2^ex, f in [0.5, 1)
-        // scale by 2^-ex in two exact power-of-two steps (2^-ex alone can overflow when the
-        // column is subnormal)
-        const int e1 = -ex / 2, e2 = -ex - e1;
-        const double sc1 = ldexp(1.0, e1), sc2 = ldexp(1.0, e2);
+        frexp(mx, &ex);               // mx < 2^ex
         double s = 0.0;
-        bool bad = false;
-        for (int i = lane; i < n; i += 32) {
-            const double x = u[i];
-            if (x != x) bad = true;
-            const double t = (x * sc1) * sc2;
-            s = fma(t, t, s);
+        if (ex > -1022 && ex < 1022) {
+            const double sc = __hiloint2double((1023 - ex) << 20, 0);     // 2^-ex
+            for (int i = lane; i < n; i += 32) {
+                const double t = u[i] * sc;
+                s = fma(t, t, s);
+            }
+        } else {                      // 2^-ex out of range: two exact power-of-two steps
+            const int e1 = -ex / 2, e2 = -ex - e1;
+            const double sc1 = ldexp(1.0, e1), sc2 = ldexp(1.0, e2);
+            for (int i = lane; i < n; i += 32) {
+                const double t = (u[i] * sc1) * sc2;
+                s = fma(t, t, s);
+            }
         }
         s = warp_sum(s);
-        bad = __any_sync(0xffffffffu, bad);
-        nrm = bad ? NAN : ldexp(sqrt(s), ex);
+        nrm = ldexp(sqrt(s), ex);
     }
-    if (lane == 0) a.norms[(long long)l * a.R + warp] = nrm;
+    if (lane == 0) {
+        a.norms[(long long)l * a.R + warp] = nrm;
+        a.colmax[(long long)l * a.R + warp] = mx;
+    }
 }
 
 // Per term: keep iff all three norms are finite and nonzero (keep[nu] = 1 or 0), weight
@@ -65,8 +79,13 @@ __global__ void k_terms(const double* norms, const double* xi, int R, double* ke
 }
 
 // Normalised copy of the side matrices (Sec. 2.1): Un(:, nu) = u_nu / ||u_nu|| for kept
-// terms (to about one ulp), zero columns for dropped terms; nn2 = ||Un(:, nu)||^2 as stored.  One warp per column, grid (ceil(R/8), 3).
-__global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long long ustride, double* nn2)
+// terms (to about one ulp), zero columns for dropped terms; nn2 = ||Un(:, nu)||^2 as stored.
+// u / d is u * (2^-e / f) with d = f 2^e, f in [0.5, 1) (one FP64 multiply an entry; two exact
+// power-of-two steps when 2^-e would leave the range).  With digit planes requested, column nu
+// is also cut into S = 6 planes as operand row nu (k = x) with exponent E_nu from
+// max |Un(:, nu)| = colmax * scale (the same multiply as the entries, so max < 2^E_nu holds
+// exactly).  One warp per column, grid (ceil(R/8), 3).
+__global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long long ustride, double* nn2, NormSlice ns)
 {
     const int l = blockIdx.y;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -77,25 +96,84 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
     double* dst = Un + l * ustride + (long long)warp * n;
     const bool keep = keepf[warp] != 0.0;
     const double d = a.norms[(long long)l * a.R + warp];
-    // u / d as (u * (2^e1 / f)) * 2^e2 with d = f 2^e, f in [0.5, 1), e1 + e2 = -e: no overflow
-    // for any finite d > 0 (|u| <= d), one FP64 division per column instead of per entry, and
-    // within 1.5 ulp of the quotient
-    double s1 = 0.0, s2 = 0.0;
+    double s1 = 0.0, s2 = 1.0;
     if (keep) {
         int e;
         const double f = frexp(d, &e);
-        const int e1 = -e / 2, e2 = -e - e1;
-        s1 = ldexp(1.0 / f, e1);
-        s2 = ldexp(1.0, e2);
+        if (e > -1000 && e < 1000) {
+            s1 = ldexp(1.0 / f, -e);
+        } else {
+            const int e1 = -e / 2, e2 = -e - e1;
+            s1 = ldexp(1.0 / f, e1);
+            s2 = ldexp(1.0, e2);
+        }
+    }
+    uint16_t* P = ns.planes[l];
+    int E = -126;
+    if (P) {
+        const double mx = (a.colmax[(long long)l * a.R + warp] * s1) * s2;
+        if (mx > 0.0) {
+            frexp(mx, &E);
+            E = E < -126 ? -126 : (E > 127 ? 127 : E);
+        }
+        if (lane == 0) ns.exps[l][warp] = (signed char)E;
     }
     double s = 0.0;
-    for (int i = lane; i < n; i += 32) {
-        const double v = (u[i] * s1) * s2;
-        dst[i] = v;
-        s = fma(v, v, s);
+    const int lim = P ? ns.ld[l] : n;
+    for (int i = lane; i < lim; i += 32) {
+        double v = 0.0;
+        if (i < n) {
+            v = keep ? (u[i] * s1) * s2 : 0.0;
+            dst[i] = v;
+            s = fma(v, v, s);
+        }
+        if (P) {
+            uint16_t dg[6];
+            oz_digits(v, E, 6, dg);
+            uint16_t* q = P + (long long)warp * ns.ld[l] + i;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) q[t * ns.pstride[l]] = dg[t];
+        }
     }
     s = warp_sum(s);
     if (lane == 0) nn2[(long long)l * a.R + warp] = s;
+}
+
+// Transposed digit planes with one fixed exponent E0 (|x| < 2^E0): planes[s][x ld + nu] from
+// X(x, nu) = X[x + ldx nu], zero for nu in [K, ld).  A 32 x 32 tile goes through shared memory so
+// that reads run along x and writes along nu.  grid (ceil(ld/32), ceil(rows/32), nmodes), block 32 x 8.
+__global__ void k_slice_t(SliceTArgs a)
+{
+    const int b = blockIdx.z;
+    const int nu0 = blockIdx.x * 32, x0 = blockIdx.y * 32;
+    const int rows = a.rows[b], K = a.K[b], ld = a.ld[b];
+    if (x0 >= rows || nu0 >= ld) return;
+    __shared__ double tile[32][33];
+    const double* X = a.X[b];
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int nu = nu0 + j, x = x0 + threadIdx.x;
+        tile[j][threadIdx.x] = (nu < K && x < rows) ? X[(long long)nu * a.ldx[b] + x] : 0.0;
+    }
+    __syncthreads();
+    uint16_t* P = a.planes[b];
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int x = x0 + i, nu = nu0 + threadIdx.x;
+        if (x >= rows || nu >= ld) continue;
+        uint16_t dg[6];
+        oz_digits(tile[threadIdx.x][i], a.E0, 6, dg);
+        uint16_t* q = P + (long long)x * ld + nu;
+#pragma unroll
+        for (int t = 0; t < 6; ++t) q[t * a.pstride[b]] = dg[t];
+    }
+}
+
+int launch_slice_t(const SliceTArgs& a, int nb, int ldmax, int rowsmax, cudaStream_t st)
+{
+    if (nb <= 0 || ldmax <= 0 || rowsmax <= 0) return 0;
+    dim3 grid((ldmax + 31) / 32, (rowsmax + 31) / 32, nb);
+    k_slice_t<<<grid, dim3(32, 8), 0, st>>>(a);
+    RH_CHECK_LAUNCH();
+    return 0;
 }
 
 // Deterministic single-block sums: kept terms, ||xi'||^2 and ||U_l normalised||_F^2.
@@ -176,22 +254,27 @@ __global__ void k_cpsum(SumArgs a)
 
 
 // dst_l(nu, j) = src_l(j, nu): V^(l) (rows j < r_l, ld lds) to nu-contiguous rows (ld ldd = R).
-__global__ void k_transpose_v(const double* src, long long sstride, int lds, double* dst, long long dstride, int ldd,
+// dst_l(j, nu) = src_l(nu, j) for j < r_l, nu < R, as a float pair (h, l) with h = fl32(v) and
+// l = fl32(v - h): the Khatri-Rao operand of the tensor-core core contraction forms its products
+// from these on the FP32 pipe (h h' exact by fma; about 2^-46 relative in all).
+__global__ void k_transpose_v(const double* src, long long sstride, int lds, float2* dst, long long dstride, int ldd,
                               int R, const int* dr, int mode0)
 {
     const int l = mode0 + blockIdx.y;
     const int r = dr[l];
     const double* S = src + l * sstride;
-    double* D = dst + l * dstride;
+    float2* D = dst + l * dstride;
     const long long total = (long long)R * r;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const int nu = (int)(e % R), j = (int)(e / R);
-        D[(long long)j * ldd + nu] = S[(long long)nu * lds + j];
+        const double v = S[(long long)nu * lds + j];
+        const float h = __double2float_rn(v);
+        D[(long long)j * ldd + nu] = make_float2(h, __double2float_rn(v - (double)h));
     }
 }
 
-int launch_transpose_v(const double* src, long long sstride, int lds, double* dst, long long dstride, int ldd, int R,
+int launch_transpose_v(const double* src, long long sstride, int lds, float2* dst, long long dstride, int ldd, int R,
                        const int* dr, int mode0, int nmodes, cudaStream_t st)
 {
     dim3 grid(512, nmodes);
@@ -216,14 +299,15 @@ int launch_colnorms(const NormArgs& a, cudaStream_t st)
 }
 
 int launch_terms(const NormArgs& na, const double* xi, double* keepf, double* xin, double* xi_user,
-                 rhosvd_info* info, double* Un, long long ustride, double* nn2, double* total, cudaStream_t st)
+                 rhosvd_info* info, double* Un, long long ustride, double* nn2, double* total, const NormSlice& ns,
+                 cudaStream_t st)
 {
     const int R = na.R;
     if (R > 0) {
         k_terms<<<(R + 255) / 256, 256, 0, st>>>(na.norms, xi, R, keepf, xin, xi_user, info);
         RH_CHECK_LAUNCH();
         dim3 grid((R + 7) / 8, 3);
-        k_normalize<<<grid, 256, 0, st>>>(na, keepf, Un, ustride, nn2);
+        k_normalize<<<grid, 256, 0, st>>>(na, keepf, Un, ustride, nn2, ns);
         RH_CHECK_LAUNCH();
     }
     k_term_totals<<<1, 1024, 0, st>>>(nn2, keepf, xin, R, total, info);

@@ -146,6 +146,16 @@ struct NormArgs {
     int n[3];
     int R;
     double* norms;      // 3 x R
+    double* colmax;     // 3 x R: max |u_i| of each column
+};
+
+// Digit planes of the normalised columns, cut while they are written (mixed form): column nu
+// of mode l becomes operand row nu (k = x) with its own exponent.  planes[l] null: none.
+struct NormSlice {
+    uint16_t* planes[3];
+    long long pstride[3];
+    int ld[3];
+    signed char* exps[3];
 };
 
 struct HadArgs {
@@ -213,14 +223,28 @@ struct FinalArgs {
 };
 constexpr int RITZ_CHUNKS = 256;
 
+// Transposed digit planes with a fixed exponent (the range-sketch operand: rows x, k = nu).
+struct SliceTArgs {
+    const double* X[3];
+    int ldx[3];
+    int rows[3];
+    int K[3];
+    uint16_t* planes[3];
+    long long pstride[3];
+    int ld[3];
+    int E0;
+};
+
 // ---------------------------------------------------------------- launchers (return 0 or RHOSVD_ERR_CUDA)
 int launch_gemm(GemmBatch& gb, cudaStream_t st);
 int launch_gemm_splitk(GemmBatch gb, double* part, cudaStream_t st);
 int launch_colnorms(const NormArgs& a, cudaStream_t st);
 int launch_terms(const NormArgs& na, const double* xi, double* keepf, double* xin, double* xi_user,
-                 rhosvd_info* info, double* Un, long long ustride, double* nn2, double* total, cudaStream_t st);
+                 rhosvd_info* info, double* Un, long long ustride, double* nn2, double* total, const NormSlice& ns,
+                 cudaStream_t st);
 int launch_identity(double* Q, int n, int ld, cudaStream_t st);
-int launch_transpose_v(const double* src, long long sstride, int lds, double* dst, long long dstride, int ldd, int R,
+int launch_slice_t(const SliceTArgs& a, int nb, int ldmax, int rowsmax, cudaStream_t st);
+int launch_transpose_v(const double* src, long long sstride, int lds, float2* dst, long long dstride, int ldd, int R,
                        const int* dr, int mode0, int nmodes, cudaStream_t st);
 int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, cudaStream_t st);
 int launch_hadamard(const HadArgs& a, cudaStream_t st);

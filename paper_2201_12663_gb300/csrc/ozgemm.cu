@@ -197,14 +197,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
                     *reinterpret_cast<uint4*>(sA + s * A_PLANE + oz_off(r, c)) = v;
                 }
             } else {
+                // entries V2(j, nu) V3(m, nu) from FP32 pairs on the FP32 pipe: the head product
+                // is exact with its fma error, the cross terms add the rest (about 2^-46
+                // relative, far below the 2^-8 SA digits); F = round(x 2^(8 SA)) on the integer pipe
+                static_assert(ASRC != OZ_A_KR || SA <= 4, "the pair product carries about 46 bits");
                 uint16_t d[8][SA];
                 const int jj = gi % r2, mm = gi / r2;
+                constexpr float TWO_8S = (float)(1ull << (8 * SA));
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    double x = 0.0;
-                    if (gi < M && gk + q < kbase + K)
-                        x = P.kr.V2t[(long long)jj * P.kr.ldt + gk + q] * P.kr.V3t[(long long)mm * P.kr.ldt + gk + q];
-                    oz_digits(x, 0, SA, d[q]);
+                    long long F = 0;
+                    if (gi < M && gk + q < kbase + K) {
+                        const float2 a = P.kr.V2t[(long long)jj * P.kr.ldt + gk + q];
+                        const float2 b = P.kr.V3t[(long long)mm * P.kr.ldt + gk + q];
+                        const float ph = a.x * b.x;
+                        float pe = fmaf(a.x, b.x, -ph);
+                        pe = fmaf(a.x, b.y, fmaf(a.y, b.x, pe));
+                        F = __float2ll_rn(ph * TWO_8S) + __float2ll_rn(pe * TWO_8S);
+                    }
+                    oz_digits_int(F, SA, d[q]);
                 }
 #pragma unroll
                 for (int s = 0; s < SA; ++s) {
@@ -326,8 +337,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
         const int col = j0 + cg * NQ + c;
         if (row >= M || col >= N) continue;
         const int eb = BSRC == OZ_B_PLANES ? (P.B.exps ? (int)P.B.exps[col] : P.B.exp0) : 8;
-        double v = (double)hi[c] + (double)lo[c];
-        v = ldexp(v, ea + eb - 16);
+        // 2^(ea + eb - 16) built from its exponent bits (ea + eb in [-252, 254]: always normal),
+        // so the scaling is one exact multiply instead of an ldexp call on the FP64 pipe
+        const double sc = __hiloint2double((ea + eb - 16 + 1023) << 20, 0);
+        const double v = ((double)hi[c] + (double)lo[c]) * sc;
         if (EPI == OZ_EPI_STORE) {
             Cout[(long long)row * crs + (long long)col * ccs] = v;
         } else {

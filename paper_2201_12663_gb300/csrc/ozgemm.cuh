@@ -35,10 +35,11 @@ struct OzPlanes {
 };
 
 // Generated Khatri-Rao operand for the core: row (j + r2 m), k = nu:
-// V2t[nu + ldt j] * V3t[nu + ldt m] (FP64, |.| <= 1), exponent 0.
+// V2(j, nu) V3(m, nu) (|.| <= 1, exponent 0), each factor given as an FP32 pair (h, l) at
+// V2t[nu + ldt j], V3t[nu + ldt m].
 struct OzKR {
-    const double* V2t;
-    const double* V3t;
+    const float2* V2t;
+    const float2* V3t;
     int ldt;
 };
 
@@ -83,6 +84,20 @@ enum OzASrc { OZ_A_PLANES = 0, OZ_A_KR = 1 };
 enum OzBSrc { OZ_B_PLANES = 0, OZ_B_SIGN = 1 };
 enum OzEpi { OZ_EPI_STORE = 0, OZ_EPI_RESID = 1 };
 
+// S digit planes (bf16 bit patterns) of the signed integer F = +-round(|x| 2^(8S - E))
+__device__ __forceinline__ void oz_digits_int(long long F, int S, uint16_t* out)
+{
+    const bool neg = F < 0;
+    const unsigned long long A = (unsigned long long)(neg ? -F : F);
+    for (int s = 1; s <= S; ++s) {
+        const int d = (int)((A >> (8 * (S - s))) & (s == 1 ? 0x1FFull : 0xFFull));
+        float v = ldexpf((float)d, -8 * (s - 1));
+        if (neg) v = -v;
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        out[s - 1] = *reinterpret_cast<const uint16_t*>(&b);
+    }
+}
+
 // digit planes of one FP64 value for exponent E (|x| < 2^E): writes S bf16 bit patterns
 __device__ __forceinline__ void oz_digits(double x, int E, int S, uint16_t* out)
 {
@@ -101,14 +116,8 @@ __device__ __forceinline__ void oz_digits(double x, int E, int S, uint16_t* out)
     } else {
         F = (m + (1ull << (sh - 1))) >> sh;
     }
-    const bool neg = (bits >> 63) != 0;
-    for (int s = 1; s <= S; ++s) {
-        const int d = (int)((F >> (8 * (S - s))) & (s == 1 ? 0x1FFull : 0xFFull));
-        float v = ldexpf((float)d, -8 * (s - 1));
-        if (neg) v = -v;
-        const __nv_bfloat16 b = __float2bfloat16_rn(v);
-        out[s - 1] = *reinterpret_cast<const uint16_t*>(&b);
-    }
+    const long long Fs = (long long)F;
+    oz_digits_int((bits >> 63) ? -Fs : Fs, S, out);
 }
 
 // Digit planes of an operand: operand row i < rows, k < K reads X[i * rs + k * cs] (times

@@ -668,36 +668,38 @@ __global__ void k_bisect(ModeMap mm, const double* Dg, const double* Lg, int vst
 // checks rank candidates 0..rhi, rhi = min(q, r0 + margin), with energies computed directly.
 __global__ void k_rank_select(RankArgs a)
 {
-    const int b = threadIdx.x;
+    const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;     // warp b: mode b
     if (b >= 3) return;
     const int k = a.dk[b];
     const double* mu = a.mu + b * a.vstride;
     const double s = a.st->shift[b];
-    const double total = a.total[b];
     const int q = min(k, *a.kept);
-    if (a.st->piv_fail[b]) set_status(a.info, RHOSVD_ERR_NOT_CONVERGED);
-    int r0;
-    if (total == 0.0 || q == 0 || (a.ranks[b] == 0 && a.eps >= 1.0)) {
-        r0 = 0;
-    } else if (a.ranks[b] > 0) {
-        r0 = min(a.ranks[b], q);
-    } else {
-        const double thr = a.eps * a.eps * total;
-        double tail = 0.0;
-        r0 = q;
-        while (r0 > 0) {
-            const double lam = fmax(mu[k - 1 - (r0 - 1)] - s, 0.0);
-            if (tail + lam <= thr) { tail += lam; --r0; } else break;
+    if (lane == 0) {
+        const double total = a.total[b];
+        if (a.st->piv_fail[b]) set_status(a.info, RHOSVD_ERR_NOT_CONVERGED);
+        int r0;
+        if (total == 0.0 || q == 0 || (a.ranks[b] == 0 && a.eps >= 1.0)) {
+            r0 = 0;
+        } else if (a.ranks[b] > 0) {
+            r0 = min(a.ranks[b], q);
+        } else {
+            const double thr = a.eps * a.eps * total;
+            double tail = 0.0;
+            r0 = q;
+            while (r0 > 0) {
+                const double lam = fmax(mu[k - 1 - (r0 - 1)] - s, 0.0);
+                if (tail + lam <= thr) { tail += lam; --r0; } else break;
+            }
         }
+        int rhi = (a.ranks[b] > 0 || r0 == 0) ? r0 : min(q, r0 + a.margin);
+        if (a.ranks[b] == 0 && a.eps >= 1.0) rhi = 0;
+        a.st->r0[b] = r0;
+        a.st->rhi[b] = rhi;
+        a.info->k[b] = k;
+        a.info->total[b] = total;
+        a.info->direct[b] = a.direct[b];
     }
-    int rhi = (a.ranks[b] > 0 || r0 == 0) ? r0 : min(q, r0 + a.margin);
-    if (a.ranks[b] == 0 && a.eps >= 1.0) rhi = 0;
-    a.st->r0[b] = r0;
-    a.st->rhi[b] = rhi;
-    a.info->k[b] = k;
-    a.info->total[b] = total;
-    a.info->direct[b] = a.direct[b];
-    for (int j = 0; j < KMAX; ++j)
+    for (int j = lane; j < KMAX; j += 32)         // sigma: one square root a lane
         a.sigma[b][j] = (j < q) ? sqrt(fmax(mu[k - 1 - j] - s, 0.0)) : 0.0;
 }
 
@@ -974,7 +976,7 @@ int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, co
 
 int launch_rank(const RankArgs& a, cudaStream_t st)
 {
-    k_rank_select<<<1, 32, 0, st>>>(a);
+    k_rank_select<<<1, 96, 0, st>>>(a);
     RH_CHECK_LAUNCH();
     return 0;
 }
