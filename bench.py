@@ -34,10 +34,14 @@ if ROOT not in sys.path:
 WORKLOAD = dict(workload="hadamard_n1024_R64x64", n=1024, Ra=64, Rb=64, seeds=[0, 1], eps=1e-7,
                 r_max=160, oversample=32, grid="[-10,10]^3 cell centres")
 PRECISIONS = {"mixed": 1, "plain": 0}
-# tensor-core digit-plane products per FP64-class product in the mixed form (6-digit operands:
-# pairs with s + t <= 7; the sketch has a +-1 operand: 6; the core uses 4 digits: 10)
-MIXED_PAIRS = {"sketch": 6, "project": 21, "v_hi": 21, "residual": 21,
-               "core": 10}
+# tensor-core digit-plane products per FP64-class product in the mixed form: 6-digit operands
+# with every pair s + t <= 8 (26); the sketch against a +-1 operand (6); the core with 4-digit
+# operands, pairs s + t <= 5 (10)
+MIXED_PAIRS = {"sketch": 6, "project": 26, "v_hi": 26, "residual": 26, "z_hi": 26, "gram_bbt": 26,
+               "cholqr_gram": 26, "cholqr_apply": 26, "core": 10}
+# DRAM bytes per launch of a stage's kernel from an ncu capture of the same code (None when the
+# kernel has changed since): profiles/chol_smem_hadamard_n1024_R64x64.md
+NCU_TRAFFIC = {"cholqr_chol": 0.530e6}
 METRIC = "RHOSVD reductions/s at stated rel. err: mixed/learned vs FP64 plain, 1×GB300"
 UNIT = "reductions/s"
 FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (CUDA-core and tensor) rate
@@ -183,13 +187,14 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ our arm
 def algorithmic_flops(stage, info, n, R):
-    """FP64 flops of one launch of a stage (all three modes), from the ranks it saw."""
+    """FP64-class flops of one launch of a stage (all three modes), from the ranks it saw."""
     r = [info.r[l] for l in range(3)]
     k = [info.k[l] for l in range(3)]
+    kin = WORKLOAD["r_max"] + WORKLOAD["oversample"]
     if stage == "core":
         return 2.0 * r[0] * r[1] * r[2] * R
     if stage == "sketch":
-        return sum(2.0 * n * (WORKLOAD["r_max"] + WORKLOAD["oversample"]) * R for _ in range(3))
+        return sum(2.0 * n * kin * R for _ in range(3))
     if stage == "project":
         return sum(2.0 * k[l] * n * R for l in range(3))
     if stage == "residual":
@@ -198,9 +203,19 @@ def algorithmic_flops(stage, info, n, R):
         return sum(2.0 * k[l] * k[l] * R for l in range(3))
     if stage == "v_hi":
         return sum(2.0 * min(k[l], r[l] + 16) * k[l] * R for l in range(3))
+    if stage == "z_hi":
+        return sum(2.0 * n * k[l] * min(k[l], r[l] + 16) for l in range(3))
+    # CholeskyQR: pass 1 on kin columns, passes 2 and 3 on the m_l kept ones; per launch = mean
     if stage == "cholqr_gram":
-        kk = WORKLOAD["r_max"] + WORKLOAD["oversample"]
-        return 3 * sum(2.0 * kk * kk * n for _ in range(3))
+        return (sum(2.0 * kin * kin * n for _ in range(3)) + 2 * sum(2.0 * k[l] ** 2 * n for l in range(3))) / 3
+    if stage == "cholqr_apply":
+        return (sum(2.0 * n * kin * kin for _ in range(3)) + 2 * sum(2.0 * n * k[l] ** 2 for l in range(3))) / 3
+    if stage == "cholqr_chol":
+        return (sum(kin ** 3 / 3.0 for _ in range(3)) + 2 * sum(k[l] ** 3 / 3.0 for l in range(3))) / 3
+    if stage == "cholqr_trinv":
+        return (sum(kin ** 3 / 3.0 for _ in range(3)) + 2 * sum(k[l] ** 3 / 3.0 for l in range(3))) / 3
+    if stage == "tridiag":
+        return sum(4.0 * k[l] ** 3 / 3.0 for l in range(3))
     return None
 
 
@@ -368,25 +383,27 @@ def run_ours(args):
         fl = algorithmic_flops(name, info, n, R)
         pk = peaks()
         if fl is not None and main_prec == "mixed" and name in MIXED_PAIRS:
+            # the digit-plane scheme executes MIXED_PAIRS BF16 products per FP64-class product,
+            # so its FP64-class peak is the measured BF16 rate divided by that count
             ach = fl / (avg_ms * 1e-3) / 1e12
             bf16 = pk.get("bf16_tflops", 1912.0)
-            roof = {"bound": "tensor", "kernel": name, "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
-                    "frac": ach / bf16, "traffic": None,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
-                    "tensor_pipe_frac": ach * MIXED_PAIRS[name] / bf16,
-                    "note": f"achieved counts FP64-class flops 2MNK; the tensor pipe executes "
-                            f"{MIXED_PAIRS[name]} BF16 digit-plane products per FP64 product",
+            peak = bf16 / MIXED_PAIRS[name]
+            roof = {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": NCU_TRAFFIC.get(name),
+                    "peak_source": f"MEASURED_PEAKS.json bf16_tflops {bf16} (burst, of measured) / "
+                                   f"{MIXED_PAIRS[name]} digit-plane products",
                     "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": fl}
         elif fl is not None:
             ach = fl / (avg_ms * 1e-3) / 1e12
             roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "GB300 nominal FP64 rate 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 entry)",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(name),
+                    "peak_source": "GB300 nominal FP64 rate 1.25 TFLOP/s (of fallback: MEASURED_PEAKS.json has "
+                                   "no FP64 entry)",
+                    "note": "sequential factorisation in one block per mode: latency and FP64 issue of one SM",
                     "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": fl}
         else:
             roof = {"bound": "alu", "kernel": name, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": None, "traffic": None,
-                    "note": "dominant stage is a single-block FP64 factorisation (latency bound); no flop model",
+                    "frac": None, "traffic": None, "note": "no flop model for this stage",
                     "avg_launch_ms": avg_ms}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -77,3 +77,22 @@ def test_mixed_matches_plain_gpu(rhosvd_cuda, case):
             total = g["info"].total[l]
             assert g["info"].tail[l] >= o["tails"][l] * (1 - 1e-9) - 1e-13 * total ** 0.5
             assert g["info"].tail[l] ** 2 <= eps * eps * total * (1 + 1e-9)
+
+
+def test_mixed_rank_one_exact(rhosvd_cuda):
+    """One canonical term: the normalised side matrices are single unit columns, so sigma_1 = 1
+    and V = Z^T U = +-1 exactly, and nothing lies outside Z.  In the mixed form every one of
+    these passes through digit-plane products of one-signed data over K = n, the case where
+    inexact FP32 accumulation would lose bits in proportion to K."""
+    P = rhosvd_cuda
+    g0 = np.random.default_rng(11)
+    U = [np.abs(g0.standard_normal((n, 1))) + 0.1 for n in (70, 300, 5)]
+    g = run_gpu(P, U, np.array([2.5]), 1e-12, r_max=8, precision=MIXED)
+    assert g["info"].status == 0, P.rhosvd_strerror(g["info"].status)
+    assert g["ranks"] == [1, 1, 1]
+    for l in range(3):
+        assert abs(g["sigma"][l][0] - 1.0) <= 1e-13, (l, g["sigma"][l][0])
+        assert abs(abs(g["V"][l][0, 0]) - 1.0) <= 1e-13, (l, g["V"][l][0, 0])
+        assert g["info"].resid[l] <= 1e-26, (l, g["info"].resid[l])
+        u = U[l][:, 0] / np.linalg.norm(U[l][:, 0])
+        assert abs(abs(g["Z"][l][:, 0] @ u) - 1.0) <= 1e-14
