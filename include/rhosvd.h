@@ -70,6 +70,12 @@ typedef struct rhosvd_opts {
     int r_max;              /* capacity of the outputs; 1 <= r_max <= RHOSVD_K_MAX        */
     int oversample;         /* sketch columns beyond r_max (k = r_max + oversample)       */
     int precision;          /* RHOSVD_PLAIN_FP64 or RHOSVD_MIXED                          */
+    int deflate;            /* width of the second range sketch, taken on the residual of the
+                               first basis (Y2 = (I - Q Q^T) U Omega2) and appended to it:
+                               0 = the default (16), < 0 = none, 1..64 = that width.  It
+                               finds the directions whose singular values sit near sqrt(u)
+                               of the largest, which a Gram-based orthonormalisation of a
+                               single sketch cannot resolve (needed for eps near 1e-7)   */
     unsigned long long seed;/* seed of the counter-based sketch generator                 */
 } rhosvd_opts;
 

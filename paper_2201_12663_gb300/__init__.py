@@ -46,7 +46,7 @@ class rhosvd_cp(_c.Structure):
 
 class rhosvd_opts(_c.Structure):
     _fields_ = [("eps", _c.c_double), ("ranks", _c.c_int * 3), ("r_max", _c.c_int), ("oversample", _c.c_int),
-                ("precision", _c.c_int), ("seed", _c.c_ulonglong)]
+                ("precision", _c.c_int), ("deflate", _c.c_int), ("seed", _c.c_ulonglong)]
 
 
 class rhosvd_info(_c.Structure):
@@ -149,7 +149,7 @@ def make_cp(U, xi) -> rhosvd_cp:
 
 
 def make_opts(eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0,
-              precision=RHOSVD_PLAIN_FP64) -> rhosvd_opts:
+              precision=RHOSVD_PLAIN_FP64, deflate=0) -> rhosvd_opts:
     o = rhosvd_opts()
     o.eps = float(eps)
     for l in range(3):
@@ -157,6 +157,7 @@ def make_opts(eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0,
     o.r_max = int(r_max)
     o.oversample = int(oversample)
     o.precision = int(precision)
+    o.deflate = int(deflate)
     o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     return o
 
@@ -262,12 +263,12 @@ def tucker_struct(res: TuckerResult) -> rhosvd_tucker:
 
 def rhosvd_c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0, out=None,
                workspace=None, stream=None, with_V=False, with_xi=False,
-               precision=RHOSVD_PLAIN_FP64) -> TuckerResult:
+               precision=RHOSVD_PLAIN_FP64, deflate=0) -> TuckerResult:
     """RHOSVD canonical-to-Tucker transform of the CP tensor (U[0], U[1], U[2], xi)."""
     torch = _torch()
     L = load()
     cp = make_cp(U, xi)
-    opts = make_opts(eps, ranks, r_max, oversample, seed, precision)
+    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate)
     need = int(L.rhosvd_c2t_workspace_size(_c.byref(cp), _c.byref(opts)))
     if need == 0:
         raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_c2t_workspace_size")
@@ -284,13 +285,13 @@ def rhosvd_c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0
 
 
 def rhosvd_c2t_noalloc(U, xi, out, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0,
-                       stream=None) -> TuckerResult:
+                       stream=None, precision=RHOSVD_PLAIN_FP64, deflate=0) -> TuckerResult:
     """rhosvd_c2t without a workspace argument, for callers that cannot allocate device memory:
     the library uses its own static scratch array (RHOSVD_NOALLOC_SCRATCH_BYTES).  `out` must
     be provided (see alloc_tucker); this function allocates nothing."""
     L = load()
     cp = make_cp(U, xi)
-    opts = make_opts(eps, ranks, r_max, oversample, seed)
+    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate)
     t = tucker_struct(out)
     rc = L.rhosvd_c2t_noalloc(_c.byref(cp), _c.byref(opts), _c.byref(t), _stream_handle(stream))
     if rc != RHOSVD_OK:

@@ -113,10 +113,12 @@ inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 // Workspace plan: sizes and byte offsets, a pure function of sizes and options.
 struct Plan {
     int n[3], R, rmax, kin[3], direct[3];
-    int KW;               // max k_l over modes
+    int KW;               // basis capacity: max k_l over modes + kdef
+    int kdef;             // width of the deflation sketch (0: none)
     int NQ;               // max n_l over modes
     int ks_sketch, ks_gram, ks_bbt;
-    size_t o_cpart, o_colmax;
+    size_t o_cpart, o_colmax, o_defl, o_defT;
+    int oz_s_defl;
     size_t o_state, o_norms, o_keep, o_nn2, o_Un, o_xin, o_bufA, o_bufB, o_G, o_L, o_perm, o_B, o_vec, o_W, o_V, o_Z, o_rp,
         o_part;
     // mixed-precision form: digit planes and helpers
@@ -155,6 +157,10 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
     p->rmax = o->r_max;
     int kcap = o->r_max + o->oversample;
     if (kcap > KMAX) kcap = KMAX;
+    // width of the deflation sketch; the basis may grow to kin + kdef columns
+    int kdef = o->deflate == 0 ? 16 : (o->deflate < 0 ? 0 : o->deflate);
+    if (kdef > 64) return RHOSVD_ERR_INVALID_ARG;
+    if (kcap + kdef > KMAX) kdef = KMAX - kcap;
     p->KW = 1;
     p->NQ = 1;
     for (int l = 0; l < 3; ++l) {
@@ -173,6 +179,10 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
         if (p->kin[l] > p->KW) p->KW = p->kin[l];
         if (cp->n[l] > p->NQ) p->NQ = cp->n[l];
     }
+    p->kdef = 0;
+    for (int l = 0; l < 3; ++l)
+        if (!p->direct[l] && cp->R > p->kin[l]) p->kdef = kdef;   // only a sketched mode can miss directions
+    p->KW += p->kdef;
     const int R = cp->R > 0 ? cp->R : 1;
     const long long NK = (long long)p->NQ * p->KW, KK = (long long)p->KW * p->KW;
     // split-K factors of the launches that use the partial buffer
@@ -211,6 +221,10 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
     p->rp_stride = (long long)((p->NQ + 63) / 64) * ((R + 63) / 64);
     p->o_rp = take(sizeof(double) * 3 * (size_t)p->rp_stride);
     p->o_cpart = take(sizeof(double) * 3 * (size_t)rh::RITZ_CHUNKS * rh::KMAX);
+    if (p->kdef > 0) {
+        p->o_defl = take(sizeof(double) * 3 * (size_t)NK);
+        p->o_defT = take(sizeof(double) * 3 * (size_t)rh::KMAX * p->kdef);
+    }
     p->o_part = take(sizeof(double) * (size_t)part);
     p->mixed = (o->precision == RHOSVD_MIXED);
     if (p->mixed) {
@@ -243,7 +257,9 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
         p->oz_s_sketch = nsk > 0 ? rh::oz_choose_split((int)p->NQ, p->KW, R, 96, nsk) : 1;
         p->oz_s_gram = nsk > 0 ? rh::oz_choose_split(p->KW, p->KW, (int)p->NQ, rh::OZ_NT6, nsk) : 1;
         p->oz_s_bbt = rh::oz_choose_split(p->KW, p->KW, R, rh::OZ_NT6, 3);
+        p->oz_s_defl = (nsk > 0 && p->kdef > 0) ? rh::oz_choose_split((int)p->NQ, p->kdef, R, 96, nsk) : 1;
         long long zp = 3LL * p->oz_s_sketch * NK;
+        if (3LL * p->oz_s_defl * NK > zp) zp = 3LL * p->oz_s_defl * NK;
         if (3LL * p->oz_s_gram * KK > zp) zp = 3LL * p->oz_s_gram * KK;
         if (3LL * p->oz_s_bbt * KK > zp) zp = 3LL * p->oz_s_bbt * KK;
         p->o_ozpart = take(sizeof(double) * (size_t)zp);
@@ -364,7 +380,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
         if (cudaMemsetAsync(out->sigma[l], 0, sizeof(double) * KMAX, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
     }
     STAGE("init_state", launch_init_state(S, p.kin[0], p.kin[1], p.kin[2], p.direct[0] ? p.n[0] : 0,
-                                p.direct[1] ? p.n[1] : 0, p.direct[2] ? p.n[2] : 0, st));
+                                p.direct[1] ? p.n[1] : 0, p.direct[2] ? p.n[2] : 0, p.kdef, st));
 
     // ---- a1: column norms, normalised weights (Sec. 2.1)
     NormArgs na;
@@ -472,12 +488,17 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             STAGE("sketch", launch_gemm_splitk(gb, part, st));
         }
 
-        // ---- a3: CholeskyQR with pivoting, three passes: Y -> Q1 (bufB) -> Q2 (bufA) -> Q (bufB)
+        // ---- a3: CholeskyQR with pivoting, three passes: bIn -> bTmp -> bIn -> bTmp.  kh: host
+        // column bounds; dk0: device columns of the input; dm, dkx: device basis width and input
+        // columns (outputs); d0out: the first pass's largest Gram diagonal (optional); d0ref,
+        // floor_rel: absolute pivot floor floor_rel * d0ref (optional)
+        auto cholqr3 = [&](double* bIn, double* bTmp, const int* kh, const int* dk0, int* dm, int* dkx,
+                           double* d0out, const double* d0ref, double floor_rel) -> int {
         const double tols[3] = {1e-15, 1e-11, 0.0};
         const int pivots[3] = {1, 1, 0};
         for (int pass = 0; pass < 3; ++pass) {
-            double* X = (pass == 1) ? bufB : bufA;
-            double* Y = (pass == 1) ? bufA : bufB;
+            double* X = (pass == 1) ? bTmp : bIn;
+            double* Y = (pass == 1) ? bIn : bTmp;
             GemmBatch g2;
             memset(&g2, 0, sizeof(g2));
             g2.nbatch = nsk;
@@ -492,10 +513,10 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 g.C = G + l * KK;
                 g.crs = 1;
                 g.ccs = KW;
-                g.M = p.kin[l];
-                g.N = p.kin[l];
+                g.M = kh[l];
+                g.N = kh[l];
                 g.K = p.n[l];
-                if (pass > 0) { g.dM = &S->m[l]; g.dN = &S->m[l]; }
+                if (pass > 0) { g.dM = &dm[l]; g.dN = &dm[l]; }
                 g2.p[b] = g;
             }
             if (mixed) {
@@ -514,18 +535,18 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                     sg.X[b] = X + l * NK;
                     sg.rs[b] = p.n[l];
                     sg.cs[b] = 1;
-                    sg.rows[b] = p.kin[l];
-                    sg.drows[b] = pass > 0 ? &S->m[l] : nullptr;
+                    sg.rows[b] = kh[l];
+                    sg.drows[b] = pass > 0 ? &dm[l] : nullptr;
                     sg.K[b] = p.n[l];
                     sg.planes[b] = pP2 + l * p.sP2;
-                    sg.pstride[b] = (long long)p.kin[l] * p.ldn;
+                    sg.pstride[b] = (long long)kh[l] * p.ldn;
                     sg.ld[b] = p.ldn;
                     sg.exps[b] = eP2 + l * EX;
                     OzProblem& q = ob.p[b];
                     q.A = OzPlanes{sg.planes[b], sg.pstride[b], p.ldn, sg.exps[b], 0};
                     q.B = q.A;
-                    q.M = q.N = p.kin[l];
-                    if (pass > 0) q.dM = q.dN = &S->m[l];
+                    q.M = q.N = kh[l];
+                    if (pass > 0) q.dM = q.dN = &dm[l];
                     q.K = p.n[l];
                     q.C = G + l * KK;
                     q.crs = 1;
@@ -538,13 +559,14 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             } else {
                 STAGE("cholqr_gram", launch_gemm_splitk(g2, part, st));
             }
-            const int* dk = (pass == 0) ? S->kin : S->m;
-            STAGE("cholqr_chol", launch_chol(sk, G, KK, KW, dk, S->kx, L, KK, KW, perm, KW, S->m, S->piv_fail,
-                                             pivots[pass], tols[pass], nsk, KW, st));
+            const int* dk = (pass == 0) ? dk0 : dm;
+            STAGE("cholqr_chol", launch_chol(sk, G, KK, KW, dk, dkx, L, KK, KW, perm, KW, dm, S->piv_fail,
+                                             pivots[pass], tols[pass], nsk, KW, pass == 0 ? d0out : nullptr,
+                                             d0ref, floor_rel, st));
             // Y = X P Lt^{-T}: the triangular inverse scattered into W (the Gram's buffer), then
             // one GEMM over the kx columns of X
             double* Wq = G;
-            STAGE("cholqr_trinv", launch_trinv(sk, L, KK, KW, perm, KW, S->kx, S->m, Wq, KK, KW, nsk, st));
+            STAGE("cholqr_trinv", launch_trinv(sk, L, KK, KW, perm, KW, dkx, dm, Wq, KK, KW, nsk, st));
             if (mixed) {
                 OzSliceArgs sx, sw;
                 memset(&sx, 0, sizeof(sx));
@@ -560,8 +582,8 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                     sx.rs[b] = 1;
                     sx.cs[b] = p.n[l];
                     sx.rows[b] = p.n[l];
-                    sx.K[b] = p.kin[l];
-                    sx.dK[b] = &S->kx[l];
+                    sx.K[b] = kh[l];
+                    sx.dK[b] = &dkx[l];
                     sx.planes[b] = pP2 + l * p.sP2;
                     sx.pstride[b] = (long long)p.n[l] * p.ldk;
                     sx.ld[b] = p.ldk;
@@ -569,22 +591,22 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                     sw.X[b] = Wq + l * KK;                // rows t (columns of W), k = c
                     sw.rs[b] = KW;
                     sw.cs[b] = 1;
-                    sw.rows[b] = p.kin[l];
-                    sw.drows[b] = &S->m[l];
-                    sw.K[b] = p.kin[l];
-                    sw.dK[b] = &S->kx[l];
+                    sw.rows[b] = kh[l];
+                    sw.drows[b] = &dm[l];
+                    sw.K[b] = kh[l];
+                    sw.dK[b] = &dkx[l];
                     sw.planes[b] = pP1 + l * p.sP1;
-                    sw.pstride[b] = (long long)p.kin[l] * p.ldk;
+                    sw.pstride[b] = (long long)kh[l] * p.ldk;
                     sw.ld[b] = p.ldk;
                     sw.exps[b] = eP1 + l * EX;
                     OzProblem& q = ob.p[b];
                     q.A = OzPlanes{sx.planes[b], sx.pstride[b], p.ldk, sx.exps[b], 0};
                     q.B = OzPlanes{sw.planes[b], sw.pstride[b], p.ldk, sw.exps[b], 0};
                     q.M = p.n[l];
-                    q.N = p.kin[l];
-                    q.dN = &S->m[l];
-                    q.K = p.kin[l];
-                    q.dK = &S->kx[l];
+                    q.N = kh[l];
+                    q.dN = &dm[l];
+                    q.K = kh[l];
+                    q.dK = &dkx[l];
                     q.C = Y + l * NK;
                     q.crs = 1;
                     q.ccs = p.n[l];
@@ -607,15 +629,86 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                     g.crs = 1;
                     g.ccs = p.n[l];
                     g.M = p.n[l];
-                    g.N = p.kin[l];
-                    g.dN = &S->m[l];
-                    g.K = p.kin[l];
-                    g.dK = &S->kx[l];
+                    g.N = kh[l];
+                    g.dN = &dm[l];
+                    g.K = kh[l];
+                    g.dK = &dkx[l];
                     gq.p[b] = g;
                 }
                 STAGE("cholqr_apply", launch_gemm(gq, st));
             }
         }
+        return 0;
+        };
+        {
+            const int rc = cholqr3(bufA, bufB, p.kin, S->kin, S->m, S->kx, S->gmax, nullptr, 0.0);
+            if (rc) return rc;
+        }
+        if (p.kdef > 0) {
+            // ---- deflation: a second sketch on the residual of the first basis,
+            // Y2 = (I - Q Q^T) U Omega2 (two projections), orthonormalised on its own scale and
+            // appended to Q.  A Gram of one sketch resolves directions only down to ~sqrt(u) of
+            // the largest; near eps = 1e-7 the tail energy sits there.  A pivot must also exceed
+            // 1e-26 of the first sketch's largest Gram diagonal: below that, Y2 is rounding noise.
+            double* Ydf = bufA;                              // free after the first CholeskyQR
+            double* Qdf = (double*)(ws + p.o_defl);
+            double* Tdf = (double*)(ws + p.o_defT);
+            const unsigned long long seed2 = opts->seed ^ 0x9E3779B97F4A7C15ull;
+            int kdh[3] = {p.kdef, p.kdef, p.kdef};
+            if (mixed) {
+                OzBatch ob;
+                memset(&ob, 0, sizeof(ob));
+                ob.nbatch = nsk;
+                ob.nsplit = p.oz_s_defl;
+                ob.err = ozerr;
+                for (int b = 0; b < nsk; ++b) {
+                    const int l = sk.m[b];
+                    OzProblem& q = ob.p[b];
+                    q.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1};
+                    q.M = p.n[l];
+                    q.N = p.kdef;
+                    q.K = R;
+                    q.C = Ydf + l * NK;
+                    q.crs = 1;
+                    q.ccs = p.n[l];
+                    q.seed = seed2;
+                    q.mode = l;
+                    q.Cpart = ozpart + (size_t)l * p.oz_s_defl * NK;
+                    q.split_stride = NK;
+                }
+                STAGE("deflate_sketch", launch_ozgemm(ob, OZ_SKETCH, st));
+            } else {
+                GemmBatch gd;
+                memset(&gd, 0, sizeof(gd));
+                gd.nbatch = nsk;
+                gd.ksplit = p.ks_sketch;
+                gd.bkind = B_SKETCH;
+                for (int b = 0; b < nsk; ++b) {
+                    const int l = sk.m[b];
+                    GemmProblem g = blank_problem();
+                    g.A = Mat{Un + l * US, 1, (long long)p.n[l]};
+                    g.C = Ydf + l * NK;
+                    g.crs = 1;
+                    g.ccs = p.n[l];
+                    g.M = p.n[l];
+                    g.N = p.kdef;
+                    g.K = R;
+                    g.seed = seed2;
+                    g.mode = l;
+                    gd.p[b] = g;
+                }
+                STAGE("deflate_sketch", launch_gemm_splitk(gd, part, st));
+            }
+            for (int it = 0; it < 2; ++it)
+                STAGE("deflate_project", launch_deflate(sk, bufB, Ydf, NK, p.n, S->m, p.kdef, Tdf,
+                                                        (long long)KMAX * p.kdef, nsk, p.NQ, st));
+            {
+                const int rc = cholqr3(Ydf, Qdf, kdh, S->kdef, S->mdef, S->kxdef, nullptr, S->gmax, 1e-26);
+                if (rc) return rc;
+            }
+            STAGE("deflate_append", launch_append(sk, bufB, Qdf, NK, p.n, S->m, S->mdef, nsk, p.NQ, p.kdef, st));
+        }
+
     }
 
     if (R > 0) {
@@ -1020,6 +1113,9 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             // digit planes of diag(xi') V^(1) (rows i, k = nu, per-row exponents)
             const long long VTS = (long long)R * KW;
             STAGE("core_prep", launch_transpose_v(Vw, VS, KW, (float2*)Vt, VTS, R, R, S->r, 1, 2, st));
+            // per-row exponents of V^(2), V^(3) (modes 1, 2 of eP1): the Khatri-Rao row (j, m)
+            // is cut with e2[j] + e3[m]
+            STAGE("core_prep", launch_row_exps((const float2*)Vt, VTS, R, S->r, 1, 2, R, eP1, EX, st));
             const int rcap = rmax < KW ? rmax : KW;   // a rank never exceeds the basis width
             OzSliceArgs s1;
             memset(&s1, 0, sizeof(s1));
@@ -1041,7 +1137,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             ob.nbatch = 1;
             ob.err = ozerr;
             OzProblem& q = ob.p[0];
-            q.kr = OzKR{(const float2*)(Vt + VTS), (const float2*)(Vt + 2 * VTS), R};
+            q.kr = OzKR{(const float2*)(Vt + VTS), (const float2*)(Vt + 2 * VTS), R, eP1 + EX, eP1 + 2 * EX};
             q.M = rcap * rcap;
             q.M_from_r2r3 = 1;
             q.dNa = &S->r[1];

@@ -283,10 +283,40 @@ int launch_transpose_v(const double* src, long long sstride, int lds, float2* ds
     return 0;
 }
 
-__global__ void k_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2)
+// Per-row exponents of the split factors: out_l[j] = E with max_nu |V_l(j, nu)| < 2^E for the
+// pair (h, l) at Vt_l[j ldt + nu] (|v| <= |h| (1 + 2^-23), so E comes from max |h| (1 + 2^-20)),
+// clamped to [-45, 1].  Warp per row j < r_l.  grid (ceil(KMAX / 8), nmodes), block 256.
+__global__ void k_row_exps(const float2* Vt, long long vstride, int ldt, const int* dr, int mode0, int R,
+                           signed char* out, long long ostride)
+{
+    const int l = mode0 + blockIdx.y;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (j >= dr[l]) return;
+    const float2* v = Vt + l * vstride + (long long)j * ldt;
+    float mx = 0.f;
+    for (int nu = lane; nu < R; nu += 32) mx = fmaxf(mx, fabsf(v[nu].x));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int E = -45;
+    if (mx > 0.f) {
+        frexpf(mx * (1.0f + 0x1p-20f), &E);
+        E = E < -45 ? -45 : (E > 1 ? 1 : E);
+    }
+    if (lane == 0) out[l * ostride + j] = (signed char)E;
+}
+
+int launch_row_exps(const float2* Vt, long long vstride, int ldt, const int* dr, int mode0, int nmodes, int R,
+                    signed char* out, long long ostride, cudaStream_t st)
+{
+    k_row_exps<<<dim3((KMAX + 7) / 8, nmodes), 256, 0, st>>>(Vt, vstride, ldt, dr, mode0, R, out, ostride);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+__global__ void k_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, int kdef)
 {
     s->kin[0] = k0; s->kin[1] = k1; s->kin[2] = k2;
     s->m[0] = m0; s->m[1] = m1; s->m[2] = m2;
+    s->kdef[0] = s->kdef[1] = s->kdef[2] = kdef;
 }
 
 int launch_colnorms(const NormArgs& a, cudaStream_t st)
@@ -322,9 +352,9 @@ int launch_identity(double* Q, int n, int ld, cudaStream_t st)
     return 0;
 }
 
-int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, cudaStream_t st)
+int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, int kdef, cudaStream_t st)
 {
-    k_init_state<<<1, 1, 0, st>>>(s, k0, k1, k2, m0, m1, m2);
+    k_init_state<<<1, 1, 0, st>>>(s, k0, k1, k2, m0, m1, m2, kdef);
     RH_CHECK_LAUNCH();
     return 0;
 }

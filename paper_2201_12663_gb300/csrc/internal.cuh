@@ -18,7 +18,10 @@ struct DevState {
     int rhi[3];         // number of leading eigenvectors computed (rank candidates 0..rhi)
     int r0[3];          // provisional rank from the eigenvalues
     int kx[3];          // columns of the current CholeskyQR input
-    int pad[1];
+    int kdef[3];        // width of the deflation sketch (second range sketch)
+    int mdef[3];        // deflation directions kept
+    int kxdef[3];       // columns of the deflation CholeskyQR input
+    double gmax[3];     // largest diagonal of the first sketch's Gram (scale of the sketch)
     double shift[3];    // shift used for the LDL^T representation of the tridiagonal
     double trace[3];    // trace(B B^T) = ||B||_F^2
     double total[3];    // ||U^(l) normalised||_F^2
@@ -235,6 +238,11 @@ struct SliceTArgs {
     int E0;
 };
 
+struct DeflDims {
+    int n[3];
+    const int* dm;     // device basis widths
+};
+
 // ---------------------------------------------------------------- launchers (return 0 or RHOSVD_ERR_CUDA)
 int launch_gemm(GemmBatch& gb, cudaStream_t st);
 int launch_gemm_splitk(GemmBatch gb, double* part, cudaStream_t st);
@@ -244,14 +252,23 @@ int launch_terms(const NormArgs& na, const double* xi, double* keepf, double* xi
                  cudaStream_t st);
 int launch_identity(double* Q, int n, int ld, cudaStream_t st);
 int launch_slice_t(const SliceTArgs& a, int nb, int ldmax, int rowsmax, cudaStream_t st);
+int launch_row_exps(const float2* Vt, long long vstride, int ldt, const int* dr, int mode0, int nmodes, int R,
+                    signed char* out, long long ostride, cudaStream_t st);
 int launch_transpose_v(const double* src, long long sstride, int lds, float2* dst, long long dstride, int ldd, int R,
                        const int* dr, int mode0, int nmodes, cudaStream_t st);
-int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, cudaStream_t st);
+int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, int kdef, cudaStream_t st);
 int launch_hadamard(const HadArgs& a, cudaStream_t st);
 int launch_cpsum(const SumArgs& a, cudaStream_t st);
 int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int* kx_out, double* L,
                 long long lstride, int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot, double tol, int nb,
-                int kbound, cudaStream_t st);
+                int kbound, double* d0_out, const double* d0_ref, double floor_rel, cudaStream_t st);
+// Deflation of the second range sketch against the basis Q (n x m, ld n per mode):
+// T = Q^T Y, then Y -= Q T (k2 columns of Y, ld n).
+int launch_deflate(ModeMap mm, const double* Q, double* Y, long long nk, const int n[3], const int* dm, int k2,
+                   double* T, long long tstride, int nb, int nmax, cudaStream_t st);
+// Q(:, m + j) = Q2(:, j), j < m2 (device counts), then m += m2.
+int launch_append(ModeMap mm, double* Q, const double* Q2, long long nk, const int n[3], int* dm, const int* dm2,
+                  int nb, int nmax, int k2, cudaStream_t st);
 int launch_trinv(ModeMap mm, const double* L, long long lstride, int ldl, const int* perm, int pstride,
                  const int* dkx, const int* dm, double* W, long long wstride, int ldw, int nb, cudaStream_t st);
 int launch_trace(ModeMap mm, const double* A, long long astride, int lda, const int* dk, double* trace, int nb,

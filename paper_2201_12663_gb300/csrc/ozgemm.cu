@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
                 static_assert(ASRC != OZ_A_KR || SA <= 4, "the pair product carries about 46 bits");
                 uint16_t d[8][SA];
                 const int jj = gi % r2, mm = gi / r2;
-                constexpr float TWO_8S = (float)(1ull << (8 * SA));
+                const int Er = (P.kr.e2 && gi < M) ? (int)P.kr.e2[jj] + (int)P.kr.e3[mm] : 0;
+                const float TWO_8S = __int_as_float((127 + 8 * SA - Er) << 23);     // 2^(8 SA - E)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     long long F = 0;
@@ -328,7 +329,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
     }
     if (!ok) s_fail = 1;
     const int row = i0 + q4 * 32 + lane;
-    const int ea = (ASRC == OZ_A_PLANES && P.A.exps && row < M) ? (int)P.A.exps[row] : (ASRC == OZ_A_PLANES ? P.A.exp0 : 0);
+    int ea = (ASRC == OZ_A_PLANES && P.A.exps && row < M) ? (int)P.A.exps[row] : (ASRC == OZ_A_PLANES ? P.A.exp0 : 0);
+    if (ASRC == OZ_A_KR && P.kr.e2 && row < M) ea = (int)P.kr.e2[row % r2] + (int)P.kr.e3[row / r2];
     double e2 = 0.0;
     const long long ccs = P.ccs < 0 ? (long long)M : P.ccs;
     const long long crs = P.crs < 0 ? (long long)N : P.crs;

@@ -34,13 +34,16 @@ struct OzPlanes {
     int exp0;
 };
 
-// Generated Khatri-Rao operand for the core: row (j + r2 m), k = nu:
-// V2(j, nu) V3(m, nu) (|.| <= 1, exponent 0), each factor given as an FP32 pair (h, l) at
-// V2t[nu + ldt j], V3t[nu + ldt m].
+// Generated Khatri-Rao operand for the core: row (j + r2 m), k = nu: V2(j, nu) V3(m, nu)
+// (|.| <= 1), each factor given as an FP32 pair (h, l) at V2t[nu + ldt j], V3t[nu + ldt m].
 struct OzKR {
     const float2* V2t;
     const float2* V3t;
     int ldt;
+    // per-row exponents (|V2(j, .)| < 2^e2[j], |V3(m, .)| < 2^e3[m]): row (j, m) of the operand
+    // is cut with E = e2[j] + e3[m], so small rows keep their own 32 bits (null: E = 0)
+    const signed char* e2;
+    const signed char* e3;
 };
 
 struct OzProblem {

@@ -28,7 +28,8 @@ namespace rh {
 // max(diag G) (the numerical rank m); without pivoting that raises `fail`.  kx_out[b] = k.
 __global__ void k_chol_piv(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int hk,
                            int* kx_out, double* L, long long lstride, int ldl, int* perm, int pstride,
-                           int* dm_out, int* fail, int pivot, double tol)
+                           int* dm_out, int* fail, int pivot, double tol, double* d0_out, const double* d0_ref,
+                           double floor_rel)
 {
     const int b = mm.m[blockIdx.x];
     const int k = dk ? dk[b] : hk;
@@ -45,6 +46,8 @@ __global__ void k_chol_piv(ModeMap mm, const double* G, long long gstride, int l
     if (i < k) { dsh[i] = G[(long long)i * ldg + i]; orig[i] = i; }
     __syncthreads();
     const double d0max = block_max((i < k) ? dsh[i] : 0.0, red);
+    if (d0_out && i == 0) d0_out[b] = d0max;
+    const double dfloor = d0_ref ? floor_rel * d0_ref[b] : 0.0;
     int m = k;
     for (int t = 0; t < k; ++t) {
         // pivot: first slot of the largest remaining diagonal
@@ -74,7 +77,7 @@ __global__ void k_chol_piv(ModeMap mm, const double* G, long long gstride, int l
         __syncthreads();
         const int q = s_q;
         const double dp = s_piv;
-        if (!(dp > tol * d0max) || !(dp > 0.0)) {
+        if (!(dp > tol * d0max) || !(dp > 0.0) || !(dp > dfloor)) {
             if (!pivot && i == 0 && fail) fail[b] = 1;
             m = t;
             break;
@@ -149,7 +152,8 @@ struct SplitRC {
 __global__ void __launch_bounds__(SM_THREADS) k_chol_smem(ModeMap mm, const double* G, long long gstride, int ldg,
                                                          const int* dk, int* kx_out, double* L, long long lstride,
                                                          int ldl, int* perm, int pstride, int* dm_out, int* fail,
-                                                         int pivot, double tol)
+                                                         int pivot, double tol, double* d0_out, const double* d0_ref,
+                                                         double floor_rel)
 {
     const int b = mm.m[blockIdx.x];
     const int k = dk[b];
@@ -177,6 +181,10 @@ __global__ void __launch_bounds__(SM_THREADS) k_chol_smem(ModeMap mm, const doub
         for (int w = 0; w < SM_THREADS / 32; ++w) d0max = fmax(d0max, red[w]);
         __syncthreads();
     }
+    if (d0_out && tid == 0) d0_out[b] = d0max;
+    // absolute floor (deflation sketch): a pivot must also exceed floor_rel times the first
+    // sketch's scale, so that cancellation noise never becomes a basis direction
+    const double dfloor = d0_ref ? floor_rel * d0_ref[b] : 0.0;
     // Scalar FP64 work (the stop test, sqrt, reciprocal) is done once by thread 0 and shared:
     // FP64 is a slow pipe here, and 16 warps repeating it would cost more than the dot products.
     // The pivot search compares bit patterns on the integer pipe (a non-negative double orders
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(SM_THREADS) k_chol_smem(ModeMap mm, const doub
         }
         if (tid == 0) {
             const double dp = dsh[s_q];
-            const bool stop = !(dp > tol * d0max) || !(dp > 0.0);
+            const bool stop = !(dp > tol * d0max) || !(dp > 0.0) || !(dp > dfloor);
             s_stop = stop;
             s_piv = dp;
             if (!stop) {
@@ -337,6 +345,94 @@ __global__ void k_trinv(ModeMap mm, const double* L, long long lstride, int ldl,
             if (r >= rs && i > s && i < m) x[r] = fma(-Lc[i], xs, x[r]);
         }
     }
+}
+
+// ------------------------------------------------------------------ deflation sketch
+// T(j, c) = sum_x Q(x, j) Y(x, c) for j < m, c < k2: block (c, mode), warp per j, lanes over x.
+__global__ void k_deflate_proj(ModeMap mm, const double* Q, const double* Y, long long nk, DeflDims d, double* T,
+                               long long tstride)
+{
+    const int b = mm.m[blockIdx.y];
+    const int c = blockIdx.x;
+    const int n = d.n[b], m = d.dm[b];
+    const double* y = Y + b * nk + (long long)c * n;
+    const double* q = Q + b * nk;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = warp; j < m; j += nw) {
+        const double* qj = q + (long long)j * n;
+        double s = 0.0;
+        for (int x = lane; x < n; x += 32) s = fma(qj[x], y[x], s);
+        s = warp_sum(s);
+        if (lane == 0) T[b * tstride + (long long)c * KMAX + j] = s;
+    }
+}
+
+// Y(x, c) -= sum_{j < m} Q(x, j) T(j, c): thread per (x, c).  grid (ceil(n/256), k2, modes).
+__global__ void k_deflate_sub(ModeMap mm, const double* Q, double* Y, long long nk, DeflDims d, const double* T,
+                              long long tstride)
+{
+    const int b = mm.m[blockIdx.z];
+    const int c = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = d.n[b], m = d.dm[b];
+    if (x >= n) return;
+    const double* q = Q + b * nk + x;
+    const double* t = T + b * tstride + (long long)c * KMAX;
+    double s0 = 0.0, s1 = 0.0;
+    int j = 0;
+    for (; j + 1 < m; j += 2) {
+        s0 = fma(q[(long long)j * n], t[j], s0);
+        s1 = fma(q[(long long)(j + 1) * n], t[j + 1], s1);
+    }
+    if (j < m) s0 = fma(q[(long long)j * n], t[j], s0);
+    Y[b * nk + (long long)c * n + x] -= s0 + s1;
+}
+
+int launch_deflate(ModeMap mm, const double* Q, double* Y, long long nk, const int n[3], const int* dm, int k2,
+                   double* T, long long tstride, int nb, int nmax, cudaStream_t st)
+{
+    if (nb <= 0 || k2 <= 0) return 0;
+    DeflDims d;
+    for (int l = 0; l < 3; ++l) d.n[l] = n[l];
+    d.dm = dm;
+    k_deflate_proj<<<dim3(k2, nb), 256, 0, st>>>(mm, Q, Y, nk, d, T, tstride);
+    RH_CHECK_LAUNCH();
+    k_deflate_sub<<<dim3((nmax + 255) / 256, k2, nb), 256, 0, st>>>(mm, Q, Y, nk, d, T, tstride);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+// Q(:, m + j) = Q2(:, j) for j < m2.  grid (ceil(n/256), k2, modes).
+__global__ void k_append(ModeMap mm, double* Q, const double* Q2, long long nk, DeflDims d, const int* dm2)
+{
+    const int b = mm.m[blockIdx.z];
+    const int j = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = d.n[b], m = d.dm[b];
+    if (j >= dm2[b] || x >= n) return;
+    Q[b * nk + (long long)(m + j) * n + x] = Q2[b * nk + (long long)j * n + x];
+}
+
+__global__ void k_append_count(ModeMap mm, int* dm, const int* dm2, int nb)
+{
+    if (threadIdx.x < nb) {
+        const int b = mm.m[threadIdx.x];
+        dm[b] += dm2[b];
+    }
+}
+
+int launch_append(ModeMap mm, double* Q, const double* Q2, long long nk, const int n[3], int* dm, const int* dm2,
+                  int nb, int nmax, int k2, cudaStream_t st)
+{
+    if (nb <= 0 || k2 <= 0) return 0;
+    DeflDims d;
+    for (int l = 0; l < 3; ++l) d.n[l] = n[l];
+    d.dm = dm;
+    k_append<<<dim3((nmax + 255) / 256, k2, nb), 256, 0, st>>>(mm, Q, Q2, nk, d, dm2);
+    RH_CHECK_LAUNCH();
+    k_append_count<<<1, 32, 0, st>>>(mm, dm, dm2, nb);
+    RH_CHECK_LAUNCH();
+    return 0;
 }
 
 // ------------------------------------------------------------------ tridiagonalisation
@@ -905,7 +1001,7 @@ __global__ void k_trace(ModeMap mm, const double* A, long long astride, int lda,
 
 int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int* kx_out, double* L,
                 long long lstride, int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot, double tol, int nb,
-                int kbound, cudaStream_t st)
+                int kbound, double* d0_out, const double* d0_ref, double floor_rel, cudaStream_t st)
 {
     if (kbound <= SM_PACK_K) {
         const size_t smem = sizeof(double) * (size_t)kbound * (kbound + 1) / 2;
@@ -917,10 +1013,10 @@ int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const i
             attr = true;
         }
         k_chol_smem<<<nb, SM_THREADS, smem, st>>>(mm, G, gstride, ldg, dk, kx_out, L, lstride, ldl, perm, pstride,
-                                                  dm_out, fail, pivot, tol);
+                                                  dm_out, fail, pivot, tol, d0_out, d0_ref, floor_rel);
     } else {
         k_chol_piv<<<nb, KMAX, 0, st>>>(mm, G, gstride, ldg, dk, 0, kx_out, L, lstride, ldl, perm, pstride, dm_out,
-                                        fail, pivot, tol);
+                                        fail, pivot, tol, d0_out, d0_ref, floor_rel);
     }
     RH_CHECK_LAUNCH();
     return 0;
