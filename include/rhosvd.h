@@ -178,6 +178,33 @@ int rhosvd_cp_sum(double alpha, const rhosvd_cp* a, double beta, const rhosvd_cp
 int rhosvd_c2t_noalloc(const rhosvd_cp* cp, const rhosvd_opts* opts, const rhosvd_tucker* out,
                        void* stream);
 
+/* ---------------------------------------------------------------- batched form (no paper
+ * counterpart: many independent reductions, e.g. the Hartree-like products of many pairs)
+ *
+ * rhosvd_c2t_batched reduces `count` independent canonical tensors cps[i] with options
+ * opts[i] into outs[i] (each as rhosvd_c2t would; results are identical to one rhosvd_c2t
+ * call per tensor).  The tensors may have any n and R.  The library schedules them onto
+ * `lanes` concurrent stream lanes (longest-processing-time first on the cost 3 (n1+n2+n3) R,
+ * plus a fixed term for the sequential small factorisations); it captures the whole launch
+ * sequence into one CUDA graph, caches the executable graph under the call's arguments (the
+ * pointer values included), and launches it on `stream`.  A repeated call with the same
+ * arguments is one graph launch.
+ *   - lanes > 0: that many lanes (at most 32).  lanes <= 0: the library picks the count, by
+ *     timing the candidates 4, 8, 16, 32 once on the first call for a batch shape (that first
+ *     call synchronises the device), and remembers the fastest for that shape.
+ *   - workspace: caller-owned device memory of rhosvd_c2t_batched_workspace_size(count, cps,
+ *     opts, lanes) bytes, 256-byte aligned: one slot per lane, sized for the largest tensor.
+ *   - Returns host-side argument errors like rhosvd_c2t; device-side conditions are in each
+ *     outs[i].info.  Not reentrant across threads (one internal lock).
+ *   - rhosvd_batch_latency_enable(1) makes later batched calls record, after each tensor, its
+ *     completion time since the batch started; rhosvd_batch_latency_read(ms, count) waits for
+ *     the last batch and writes those times (ms) in tensor order. */
+size_t rhosvd_c2t_batched_workspace_size(int count, const rhosvd_cp* cps, const rhosvd_opts* opts, int lanes);
+int rhosvd_c2t_batched(int count, const rhosvd_cp* cps, const rhosvd_opts* opts, const rhosvd_tucker* outs,
+                       void* workspace, size_t workspace_bytes, int lanes, void* stream);
+int rhosvd_batch_latency_enable(int on);
+int rhosvd_batch_latency_read(float* ms, int count);
+
 /* ---------------------------------------------------------------- tracing (no paper
  * counterpart: observability of the library itself) */
 

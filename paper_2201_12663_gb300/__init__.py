@@ -102,6 +102,16 @@ def load(build_if_missing: bool = False):
         L.rhosvd_c2t_noalloc.restype = _c.c_int
         L.rhosvd_c2t_noalloc.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts), _c.POINTER(rhosvd_tucker),
                                          _c.c_void_p]
+        L.rhosvd_c2t_batched_workspace_size.restype = _c.c_size_t
+        L.rhosvd_c2t_batched_workspace_size.argtypes = [_c.c_int, _c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts),
+                                                        _c.c_int]
+        L.rhosvd_c2t_batched.restype = _c.c_int
+        L.rhosvd_c2t_batched.argtypes = [_c.c_int, _c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts),
+                                         _c.POINTER(rhosvd_tucker), _c.c_void_p, _c.c_size_t, _c.c_int, _c.c_void_p]
+        L.rhosvd_batch_latency_enable.restype = _c.c_int
+        L.rhosvd_batch_latency_enable.argtypes = [_c.c_int]
+        L.rhosvd_batch_latency_read.restype = _c.c_int
+        L.rhosvd_batch_latency_read.argtypes = [_c.POINTER(_c.c_float), _c.c_int]
         L.rhosvd_launch_count.restype = _c.c_longlong
         L.rhosvd_profile_enable.restype = _c.c_int
         L.rhosvd_profile_enable.argtypes = [_c.c_int]
@@ -349,3 +359,55 @@ def to_device_factor(U_np, device="cuda"):
     import numpy as np
     a = np.asarray(U_np, dtype=np.float64)
     return torch.from_numpy(np.ascontiguousarray(a.T)).to(device).t()
+
+
+class BatchedCall:
+    """Marshalled arguments of one rhosvd_c2t_batched call (arrays of rhosvd_cp, rhosvd_opts and
+    rhosvd_tucker plus the workspace).  Keep it and call run() again to repeat the same batch:
+    the library then replays its cached graph."""
+
+    def __init__(self, tensors, outs, lanes=0, device="cuda", **opt_kw):
+        torch = _torch()
+        L = load()
+        self.count = len(tensors)
+        self.cps = (rhosvd_cp * self.count)(*[make_cp(U, xi) for U, xi in tensors])
+        self.opts = (rhosvd_opts * self.count)(*[make_opts(**opt_kw) for _ in range(self.count)])
+        self.outs = outs
+        self.tk = (rhosvd_tucker * self.count)(*[tucker_struct(o) for o in outs])
+        self.lanes = int(lanes)
+        need = int(L.rhosvd_c2t_batched_workspace_size(self.count, self.cps, self.opts, self.lanes))
+        if need == 0:
+            raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_c2t_batched_workspace_size")
+        self.workspace = torch.empty(need, dtype=torch.uint8, device=device)
+        self._keep = tensors          # the factors must outlive the cached graph's use of them
+
+    def run(self, stream=None):
+        L = load()
+        rc = L.rhosvd_c2t_batched(self.count, self.cps, self.opts, self.tk, _c.c_void_p(self.workspace.data_ptr()),
+                                  _c.c_size_t(self.workspace.numel()), self.lanes, _stream_handle(stream))
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_c2t_batched")
+        return self.outs
+
+
+def rhosvd_c2t_batched(tensors, r_max=64, lanes=0, stream=None, with_V=False, with_xi=False, **opt_kw):
+    """Reduce a list of canonical tensors [(U, xi), ...] in one batched call; returns the list of
+    TuckerResult (one per tensor, as rhosvd_c2t would give) and the BatchedCall for repeats."""
+    outs = [alloc_tucker([U[l].shape[0] for l in range(3)], U[0].shape[1], r_max, U[0].device, with_V, with_xi)
+            for U, _ in tensors]
+    call = BatchedCall(tensors, outs, lanes=lanes, device=tensors[0][0][0].device, r_max=r_max, **opt_kw)
+    call.run(stream)
+    return outs, call
+
+
+def rhosvd_batch_latency_enable(on=True) -> int:
+    return int(load().rhosvd_batch_latency_enable(1 if on else 0))
+
+
+def rhosvd_batch_latency_read(count):
+    """Completion time (ms since the batch started) of each tensor of the last batched call."""
+    buf = (_c.c_float * count)()
+    rc = load().rhosvd_batch_latency_read(buf, count)
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_batch_latency_read")
+    return [float(x) for x in buf]

@@ -348,17 +348,20 @@ __global__ void k_trinv(ModeMap mm, const double* L, long long lstride, int ldl,
 }
 
 // ------------------------------------------------------------------ deflation sketch
-// T(j, c) = sum_x Q(x, j) Y(x, c) for j < m, c < k2: block (c, mode), warp per j, lanes over x.
+// T(j, c) = sum_x Q(x, j) Y(x, c) for j < m, c < k2: block (c, group of 8 j, mode), warp per
+// j, lanes over x.
 __global__ void k_deflate_proj(ModeMap mm, const double* Q, const double* Y, long long nk, DeflDims d, double* T,
                                long long tstride)
 {
-    const int b = mm.m[blockIdx.y];
+    const int b = mm.m[blockIdx.z];
     const int c = blockIdx.x;
     const int n = d.n[b], m = d.dm[b];
     const double* y = Y + b * nk + (long long)c * n;
     const double* q = Q + b * nk;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int j = warp; j < m; j += nw) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        const int j = blockIdx.y * 8 + warp;
+        if (j >= m) return;
         const double* qj = q + (long long)j * n;
         double s = 0.0;
         for (int x = lane; x < n; x += 32) s = fma(qj[x], y[x], s);
@@ -395,7 +398,7 @@ int launch_deflate(ModeMap mm, const double* Q, double* Y, long long nk, const i
     DeflDims d;
     for (int l = 0; l < 3; ++l) d.n[l] = n[l];
     d.dm = dm;
-    k_deflate_proj<<<dim3(k2, nb), 256, 0, st>>>(mm, Q, Y, nk, d, T, tstride);
+    k_deflate_proj<<<dim3(k2, KMAX / 8, nb), 256, 0, st>>>(mm, Q, Y, nk, d, T, tstride);
     RH_CHECK_LAUNCH();
     k_deflate_sub<<<dim3((nmax + 255) / 256, k2, nb), 256, 0, st>>>(mm, Q, Y, nk, d, T, tstride);
     RH_CHECK_LAUNCH();

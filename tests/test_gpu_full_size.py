@@ -11,7 +11,8 @@ on sampled entries computed one by one on the CPU:
   * beta(i, j, m) = sum_nu xi'_nu V1(i, nu) V2(j, nu) V3(m, nu) for sampled (i, j, m), from the
     library's own V and xi' (Prop. 2.2), so the Khatri-Rao contraction is checked at full size;
   * the two forms agree on the Tucker tensor.
-Tolerances as in test_gpu_parity.py; the mixed core carries about 2^-31 of sum |terms|."""
+Tolerances as in test_gpu_parity.py; the mixed core's bound is derived from its digit
+rounding relative to the operands' row maxima (see the core check)."""
 import json
 import math
 import os
@@ -113,8 +114,9 @@ def test_full_size_factors_and_core(rhosvd_cuda, factors, precision):
     # core entries from the library's own V and xi'.  Plain: FP64 rounding of the sum.  Mixed:
     # the core's operands a = xi' V1(i, .) and b = V2(j, .) V3(m, .) are cut into 4 base-256
     # digits relative to their row maxima (a row of b uses max|V2(j, .)| max|V3(m, .)|), so each
-    # term is off by at most 2^-33 (max|a| |b_nu| + |a_nu| max|b|); 2^-31 leaves room for the
-    # pair products and the inexact lowest groups.
+    # term is off by at most 2^-33 (max|a| |b_nu| + |a_nu| max|b|) from the digit rounding.  The
+    # groups s + t = 4, 5 are summed in FP32 over runs of 128 K between readbacks (inexact, the
+    # tensor cores truncate); 2^-28 leaves a factor 32 for them and the pair products.
     V1, V2, V3 = g["V"]
     xin = g["xin"]
     r = g["ranks"]
@@ -128,7 +130,7 @@ def test_full_size_factors_and_core(rhosvd_cuda, factors, precision):
         else:
             amax = np.abs(a).max()
             bmax = np.abs(V2[j]).max() * np.abs(V3[m]).max()
-            tol = 2.0 ** -31 * (amax * np.abs(bb).sum() + bmax * np.abs(a).sum())
+            tol = 2.0 ** -28 * (amax * np.abs(bb).sum() + bmax * np.abs(a).sum())
         assert abs(g["beta"][i, j, m] - terms.sum()) <= tol, (i, j, m)
 
 
