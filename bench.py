@@ -234,6 +234,77 @@ def tucker_rel_diff_torch(beta_a, Z_a, beta_b, Z_b):
     return (torch.linalg.norm(ca - cb) / torch.linalg.norm(cb)).item()
 
 
+BATCH = dict(workload="batched_gaussian_sums_512", count=512, n_choices=[128, 256, 512, 1024],
+             R_range=[100, 8000], eps=1e-6, r_max=160, oversample=32, seed=7)
+
+
+def batched_leg(P, dev, steps, warmup, precision):
+    """The batched workload: 512 Gaussian sums of uneven n and R at eps = 1e-6 (factor columns
+    evaluated on the device from workloads.gaussian_sum_params), reduced by one batched call
+    (stream lanes, one cached CUDA graph) and by a per-tensor launch loop for comparison."""
+    import torch
+    import workloads
+    members = workloads.batched_gaussian_sums(BATCH["count"], n_choices=tuple(BATCH["n_choices"]),
+                                              R_range=tuple(BATCH["R_range"]))
+    tensors = []
+    for n, R, seed in members:
+        x, ce, a, c = workloads.gaussian_sum_params(n, R, seed)
+        xt = torch.from_numpy(x).to(dev)
+        at = torch.from_numpy(a).to(dev)
+        U = []
+        for l in range(3):
+            d = xt[:, None] - torch.from_numpy(ce[:, l].copy()).to(dev)[None, :]
+            U.append(torch.exp(-at[None, :] * d * d).t().contiguous().t())     # column-major n x R
+        tensors.append((U, torch.from_numpy(c).to(dev)))
+    opts = dict(eps=BATCH["eps"], r_max=BATCH["r_max"], oversample=BATCH["oversample"], seed=BATCH["seed"],
+                precision=PRECISIONS[precision])
+    outs = [P.alloc_tucker([U[l].shape[0] for l in range(3)], U[0].shape[1], BATCH["r_max"], dev)
+            for U, _ in tensors]
+    call = P.BatchedCall(tensors, outs, lanes=0, device=dev, **opts)
+    t0 = time.perf_counter()
+    call.run()                                  # autotunes the lane count, builds the graph
+    torch.cuda.synchronize()
+    t_first = time.perf_counter() - t0
+    statuses = [o.info().status for o in outs]
+    for _ in range(max(warmup, 1)):
+        call.run()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        starts[i].record()
+        call.run()
+        ends[i].record()
+    torch.cuda.synchronize()
+    ms_batch = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
+    prev = P.rhosvd_batch_latency_enable(True)
+    call.run()
+    torch.cuda.synchronize()
+    lat = sorted(P.rhosvd_batch_latency_read(len(tensors)))
+    P.rhosvd_batch_latency_enable(bool(prev))
+    # per-tensor launch loop on one stream, one workspace
+    need = max(P.rhosvd_c2t_workspace_size(P.make_cp(U, xi), P.make_opts(**opts)) for U, xi in tensors)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    for (U, xi), o in zip(tensors[:8], outs[:8]):
+        P.rhosvd_c2t(U, xi, out=o, workspace=ws, **opts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for (U, xi), o in zip(tensors, outs):
+        P.rhosvd_c2t(U, xi, out=o, workspace=ws, **opts)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1)
+    ok = sum(1 for s_ in statuses if s_ == 0)
+    return {**BATCH, "precision": precision, "tensors_per_s": len(tensors) * 1000.0 / ms_batch,
+            "ms_per_batch": ms_batch, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(0.99 * (len(lat) - 1))],
+            "latency": "completion time since the batch started, per tensor",
+            "loop_tensors_per_s": len(tensors) * 1000.0 / ms_loop, "loop_ms": ms_loop,
+            "speedup_vs_loop": ms_loop / ms_batch, "status_ok": ok, "first_call_s": t_first,
+            "input_gb": sum(3 * U[0].shape[0] * U[0].shape[1] * 8 for U, _ in tensors) / 1e9,
+            "l2": "inputs (about 10 GB) larger than L2"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -422,6 +493,8 @@ def run_ours(args):
             "gpu_launches": launches, "roofline": roof, "stage_shares": shares,
             "stage_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
             "clocks": clocks, "wall_s_timed": t_wall, "parallelism": f"replicas{world}"}
+    if not args.no_batched:
+        line["batched"] = batched_leg(P, dev, args.steps, args.warmup, main_prec)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample()
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -440,6 +513,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--precision", choices=["mixed", "plain"], default="mixed")
     args = ap.parse_args()
     if args.warmup < 3:

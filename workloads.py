@@ -70,6 +70,19 @@ def gaussian_sum(n: int, R: int, seed: int, b: float = 10.0, centre_box: float =
                         centres=centres, a=a))
 
 
+def gaussian_sum_params(n: int, R: int, seed: int, b: float = 10.0, centre_box: float = 5.0,
+                        a_range=(0.5, 20.0), c_range=(0.1, 1.0)):
+    """The random parameters of gaussian_sum(n, R, seed) in the same draw order, without the
+    factor columns: (grid x, centres (R,3), exponents a (R,), weights c (R,)).  The columns
+    are u_k^(l)(i) = exp(-a_k (x_i - centres[k, l])^2); large batches evaluate them on the
+    device."""
+    g = np.random.default_rng(seed)
+    centres = g.uniform(-centre_box, centre_box, size=(R, 3))
+    a = np.exp(g.uniform(math.log(a_range[0]), math.log(a_range[1]), size=R))
+    c = g.uniform(c_range[0], c_range[1], size=R)
+    return grid(n, b), centres, a, c
+
+
 def newton_sinc_nodes(h: float = 0.4, k_lo: int = -19, k_hi: int = 0):
     """Quadrature nodes/weights for 1/z = (2/sqrt(pi)) int_0^inf exp(-z^2 t^2) dt.
 
