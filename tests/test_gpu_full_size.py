@@ -139,3 +139,56 @@ def test_full_size_forms_agree(rhosvd_cuda, factors):
     b = run_full(rhosvd_cuda, factors, 1)
     assert a["ranks"] == b["ranks"]
     assert tu.tucker_rel_diff(b["beta"], b["Z"], a["beta"], a["Z"]) < 1e-7
+
+
+# ---------------------------------------------------------------- range-separated collective potential
+# Long-range Newton Gaussians of N = 1000 unit charges (20 a charge): n = 2048, R = 20000, eps = 1e-6.
+
+NEWTON_GOLD = os.path.join(os.path.dirname(__file__), "golden", "newton_n2048_N1000_eps1e-6.json")
+NEWTON_OPTS = dict(eps=1e-6, r_max=64, oversample=32, seed=2024)
+
+
+@pytest.fixture(scope="module")
+def newton():
+    cp = workloads.newton_long_range_sum(n=2048, N=1000, seed=0)
+    with open(NEWTON_GOLD) as f:
+        return cp, json.load(f)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_newton(rhosvd_cuda, newton, precision):
+    P = rhosvd_cuda
+    import torch
+    cp, gold = newton
+    Ud = [P.to_device_factor(u) for u in cp.U]
+    xd = torch.from_numpy(cp.xi).cuda()
+    res = P.rhosvd_c2t(Ud, xd, with_V=True, with_xi=True, precision=precision, **NEWTON_OPTS)
+    info = res.info()
+    assert info.status == 0, P.rhosvd_strerror(info.status)
+    assert info.kept == gold["kept"]
+    assert math.isclose(info.xi_norm, gold["xi_norm"], rel_tol=1e-12)
+    r = [info.r[l] for l in range(3)]
+    eps = NEWTON_OPTS["eps"]
+    sig = res.sigma.cpu().numpy()
+    for l in range(3):
+        so = np.array(gold["sigma"][l])
+        total = gold["total"][l]
+        thr = eps * eps * total
+        if r[l] != gold["ranks"][l]:
+            lo = min(r[l], gold["ranks"][l])
+            t1, t0 = np.sum(so[lo + 1:] ** 2), np.sum(so[lo:] ** 2)
+            assert abs(r[l] - gold["ranks"][l]) == 1 and (abs(t1 - thr) <= 1e-3 * thr or abs(t0 - thr) <= 1e-3 * thr)
+        else:
+            assert info.tail[l] >= gold["tails"][l] * (1 - 1e-9) - 1e-13 * math.sqrt(total)
+        k = info.k[l]
+        q = min(len(so), k, r[l] + 2)
+        tol = 6 * U64 * (2048 * k + k * (k + 1)) * so[0] ** 2
+        assert np.all(np.abs(sig[l][:q] ** 2 - so[:q] ** 2) <= tol + 1e-14 * so[:q] ** 2), l
+        assert info.tail[l] ** 2 <= thr * (1 + 1e-9)
+        Z = res.Z[l][:, : r[l]].cpu().numpy()
+        assert np.abs(Z.T @ Z - np.eye(r[l])).max() <= 1e-12
+        V = res.V[l][: r[l], :].cpu().numpy()
+        for nu in np.random.default_rng(3 + l).choice(cp.U[l].shape[1], size=32, replace=False):
+            u = cp.U[l][:, nu] / np.linalg.norm(cp.U[l][:, nu])
+            assert np.abs(V[:, nu] - Z.T @ u).max() <= 1e-12, (l, nu)
+
