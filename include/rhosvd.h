@@ -205,6 +205,60 @@ int rhosvd_c2t_batched(int count, const rhosvd_cp* cps, const rhosvd_opts* opts,
 int rhosvd_batch_latency_enable(int on);
 int rhosvd_batch_latency_read(float* ms, int count);
 
+/* ---------------------------------------------------------------- learned subspace proposal
+ * (no paper counterpart: a learned start for the range finder of the side-matrix SVD, eq.
+ * SVD_Ul; the plain method stays its fallback and measures the error either way)
+ *
+ * rhosvd_c2t_start is rhosvd_c2t with the random range sketch replaced by a caller's start
+ * basis Q0^(l) (n_l x k0, column-major, leading dimension ld[l] >= n_l, device): iters = 0 takes
+ * Y = Q0 (no pass over U), iters = 1 one subspace iteration Y = U~ (U~^T Q0) (it scales each
+ * direction by its sigma^2, so directions far below the largest fade from a Gram-based basis:
+ * for a start that is already accurate use 0).  The rest is unchanged, the second (deflation)
+ * sketch included, and so is the acceptance test: the measured energy outside the basis must
+ * stay within eps^2 ||U~||^2 (energy captured >= 1 - eps^2), otherwise info.status is
+ * RHOSVD_ERR_SKETCH and the caller falls back to rhosvd_c2t.  Modes with n_l <= r_max +
+ * oversample keep the exact identity basis.  Workspace: rhosvd_c2t_start_workspace_size. */
+size_t rhosvd_c2t_start_workspace_size(const rhosvd_cp* cp, const rhosvd_opts* opts, int k0);
+int rhosvd_c2t_start(const rhosvd_cp* cp, const rhosvd_opts* opts, const double* const Q0[3], const int ld[3],
+                     int k0, int iters, const rhosvd_tucker* out, void* workspace, size_t workspace_bytes,
+                     void* stream);
+
+/* The proposal network: 128 -> 512 -> 512 -> 512 -> 2048 with GELU (erf form) after the hidden
+ * layers; FP32 master weights, BF16 copies for the GEMMs (tcgen05 tensor cores, FP32
+ * accumulation); Adam (0.9, 0.999, 1e-8).  Input per mode: the 128 features of rhosvd_features.
+ * Output per mode: 2048 = 64 x 32 values, C(i, j) at [i + 64 j], the coefficients of 32 vectors
+ * over the Chebyshev polynomials T_0..T_63 of the grid (rhosvd_chebyshev); the proposal is
+ * Q0 = T C.  Training loss per sample: ||C C^T - G||_F^2 averaged over the batch, with G (64 x 64
+ * at [i + 64 i']) the target projector T^T Z Z^T T of the plain method's leading basis Z.
+ * All device pointers are FP32 unless stated; batches are multiples of 8, at most batch_max.
+ * The handle owns the weights (device memory); calls on one handle are serialised. */
+int rhosvd_mlp_create(int batch_max, unsigned long long seed, void** handle);
+int rhosvd_mlp_destroy(void* handle);
+int rhosvd_mlp_forward(void* handle, const float* X, int B, float* Y, void* stream);
+int rhosvd_mlp_gradients(void* handle, const float* X, const float* G, int B, float* loss, void* stream);
+int rhosvd_mlp_train_step(void* handle, const float* X, const float* G, int B, float lr, float* loss, void* stream);
+long long rhosvd_mlp_num_params(void);
+/* host <-> device copy of all parameters (W0, b0, W1, b1, ...; W row-major out x in):
+ * get = 1 reads (which = 0: the weights, 1: the gradients of the last rhosvd_mlp_gradients),
+ * get = 0 writes the weights.  Synchronises the device. */
+int rhosvd_mlp_params(void* handle, float* host, int get, int which);
+/* Features of one Gaussian sum sum_k c_k exp(-a_k |x - x_k|^2) (device, FP64): per mode l,
+ * out[128 l + 0..63] = c-weighted histogram (unit sum, 64 bins) of the centre coordinate x_{k,l}
+ * over [-cbox, cbox], out[128 l + 64..127] = of log a_k over [la, lb] (values outside the range
+ * fall into the end bins).  centres: R x 3 row-major; loga, c: length R; out: 3 x 128 FP32. */
+int rhosvd_features(const double* centres, const double* loga, const double* c, int R, double cbox, double la,
+                    double lb, float* out, void* stream);
+/* Q_T (n x 64, column-major, device FP64, n >= 64): the Chebyshev polynomials T_j(x_i / b) on the
+ * grid x_i = -b + (i + 1/2) 2b/n, orthonormalised in order (Gram-Schmidt twice per column): the
+ * discrete orthogonal polynomials of the grid, the coordinates of the proposal. */
+int rhosvd_chebyshev(int n, double b, double* T, void* stream);
+/* Training target of one mode: G (64 x 64, FP32, G[i + 64 i']) = P P^T with P = Q_T^T Z, Z the
+ * plain method's leading basis (n x r, column-major, ld ldz, r <= 64), all device memory. */
+int rhosvd_proj_target(int n, const double* Q, const double* Z, int ldz, int r, float* G, void* stream);
+/* The proposal of one mode: Q0 (n x 32, column-major, ld n, FP64) = Q_T C with C(i, j) = Y[i + 64 j]
+ * the network's output for that mode (FP32). */
+int rhosvd_proposal_basis(int n, const double* QT, const float* Y, double* Q0, void* stream);
+
 /* ---------------------------------------------------------------- tracing (no paper
  * counterpart: observability of the library itself) */
 

@@ -112,6 +112,36 @@ def load(build_if_missing: bool = False):
         L.rhosvd_batch_latency_enable.argtypes = [_c.c_int]
         L.rhosvd_batch_latency_read.restype = _c.c_int
         L.rhosvd_batch_latency_read.argtypes = [_c.POINTER(_c.c_float), _c.c_int]
+        L.rhosvd_c2t_start_workspace_size.restype = _c.c_size_t
+        L.rhosvd_c2t_start_workspace_size.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts), _c.c_int]
+        L.rhosvd_c2t_start.restype = _c.c_int
+        L.rhosvd_c2t_start.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts), _c.c_void_p * 3, _c.c_int * 3,
+                                       _c.c_int, _c.c_int, _c.POINTER(rhosvd_tucker), _c.c_void_p, _c.c_size_t,
+                                       _c.c_void_p]
+        L.rhosvd_mlp_create.restype = _c.c_int
+        L.rhosvd_mlp_create.argtypes = [_c.c_int, _c.c_ulonglong, _c.POINTER(_c.c_void_p)]
+        L.rhosvd_mlp_destroy.restype = _c.c_int
+        L.rhosvd_mlp_destroy.argtypes = [_c.c_void_p]
+        L.rhosvd_mlp_forward.restype = _c.c_int
+        L.rhosvd_mlp_forward.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_mlp_gradients.restype = _c.c_int
+        L.rhosvd_mlp_gradients.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_mlp_train_step.restype = _c.c_int
+        L.rhosvd_mlp_train_step.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_float, _c.c_void_p,
+                                            _c.c_void_p]
+        L.rhosvd_mlp_num_params.restype = _c.c_longlong
+        L.rhosvd_mlp_params.restype = _c.c_int
+        L.rhosvd_mlp_params.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int]
+        L.rhosvd_features.restype = _c.c_int
+        L.rhosvd_features.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_double, _c.c_double,
+                                      _c.c_double, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_chebyshev.restype = _c.c_int
+        L.rhosvd_chebyshev.argtypes = [_c.c_int, _c.c_double, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_proj_target.restype = _c.c_int
+        L.rhosvd_proj_target.argtypes = [_c.c_int, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p,
+                                         _c.c_void_p]
+        L.rhosvd_proposal_basis.restype = _c.c_int
+        L.rhosvd_proposal_basis.argtypes = [_c.c_int, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p]
         L.rhosvd_launch_count.restype = _c.c_longlong
         L.rhosvd_profile_enable.restype = _c.c_int
         L.rhosvd_profile_enable.argtypes = [_c.c_int]
@@ -411,3 +441,154 @@ def rhosvd_batch_latency_read(count):
     if rc != RHOSVD_OK:
         raise RhosvdError(rc, "rhosvd_batch_latency_read")
     return [float(x) for x in buf]
+
+
+# ------------------------------------------------------------------ learned subspace proposal
+
+def rhosvd_c2t_start(U, xi, Q0, iters=1, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0, out=None,
+                     workspace=None, stream=None, with_V=False, with_xi=False, precision=RHOSVD_PLAIN_FP64,
+                     deflate=0) -> TuckerResult:
+    """rhosvd_c2t with the range sketch replaced by the start basis Q0 (list of three n_l x k0
+    column-major float64 CUDA tensors): iters 0 uses Q0 itself, iters 1 one subspace iteration."""
+    torch = _torch()
+    L = load()
+    cp = make_cp(U, xi)
+    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate)
+    k0 = int(Q0[0].shape[1])
+    q = (_c.c_void_p * 3)()
+    ld = (_c.c_int * 3)()
+    for l in range(3):
+        if Q0[l].dtype != torch.float64 or Q0[l].shape[1] != k0 or Q0[l].stride(0) != 1:
+            raise ValueError("Q0 must be column-major float64 n_l x k0")
+        q[l] = Q0[l].data_ptr()
+        ld[l] = max(Q0[l].stride(1), Q0[l].shape[0])
+    need = int(L.rhosvd_c2t_start_workspace_size(_c.byref(cp), _c.byref(opts), k0))
+    if need == 0:
+        raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_c2t_start_workspace_size")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=U[0].device)
+    if out is None:
+        out = alloc_tucker([cp.n[l] for l in range(3)], cp.R, r_max, U[0].device, with_V, with_xi)
+    t = tucker_struct(out)
+    rc = L.rhosvd_c2t_start(_c.byref(cp), _c.byref(opts), q, ld, k0, int(iters), _c.byref(t),
+                            _c.c_void_p(workspace.data_ptr()), _c.c_size_t(workspace.numel()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_c2t_start")
+    return out
+
+
+class Mlp:
+    """The proposal network (device weights owned by the library handle)."""
+
+    IN, OUT = 128, 2048
+
+    def __init__(self, batch_max=256, seed=0):
+        L = load()
+        h = _c.c_void_p()
+        rc = L.rhosvd_mlp_create(int(batch_max), int(seed) & 0xFFFFFFFFFFFFFFFF, _c.byref(h))
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_mlp_create")
+        self.h = h
+        self.batch_max = int(batch_max)
+
+    def close(self):
+        if self.h:
+            load().rhosvd_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, X, stream=None):
+        torch = _torch()
+        B = X.shape[0]
+        Y = torch.empty(B, self.OUT, dtype=torch.float32, device=X.device)
+        rc = load().rhosvd_mlp_forward(self.h, _c.c_void_p(X.data_ptr()), B, _c.c_void_p(Y.data_ptr()),
+                                       _stream_handle(stream))
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_mlp_forward")
+        return Y
+
+    def gradients(self, X, G, stream=None):
+        torch = _torch()
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        rc = load().rhosvd_mlp_gradients(self.h, _c.c_void_p(X.data_ptr()), _c.c_void_p(G.data_ptr()), X.shape[0],
+                                         _c.c_void_p(loss.data_ptr()), _stream_handle(stream))
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_mlp_gradients")
+        return loss
+
+    def train_step(self, X, G, lr, stream=None):
+        torch = _torch()
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        rc = load().rhosvd_mlp_train_step(self.h, _c.c_void_p(X.data_ptr()), _c.c_void_p(G.data_ptr()), X.shape[0],
+                                          _c.c_float(lr), _c.c_void_p(loss.data_ptr()), _stream_handle(stream))
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_mlp_train_step")
+        return loss
+
+    def params(self, which=0):
+        """All parameters (which=0) or the last gradients (which=1) as one float32 numpy vector."""
+        import numpy as np
+        buf = np.empty(int(load().rhosvd_mlp_num_params()), dtype=np.float32)
+        rc = load().rhosvd_mlp_params(self.h, _c.c_void_p(buf.ctypes.data), 1, int(which))
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_mlp_params")
+        return buf
+
+    def set_params(self, vec):
+        import numpy as np
+        buf = np.ascontiguousarray(vec, dtype=np.float32)
+        rc = load().rhosvd_mlp_params(self.h, _c.c_void_p(buf.ctypes.data), 0, 0)
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_mlp_params")
+
+
+def rhosvd_features(centres, loga, c, cbox, la, lb, stream=None):
+    """(3, 128) float32 features of one Gaussian sum (device float64 inputs)."""
+    torch = _torch()
+    out = torch.empty(3, 128, dtype=torch.float32, device=centres.device)
+    rc = load().rhosvd_features(_c.c_void_p(centres.data_ptr()), _c.c_void_p(loga.data_ptr()),
+                                _c.c_void_p(c.data_ptr()), int(c.numel()), float(cbox), float(la), float(lb),
+                                _c.c_void_p(out.data_ptr()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_features")
+    return out
+
+
+def rhosvd_chebyshev(n, b, device="cuda", stream=None):
+    """Q_T: n x 64 column-major float64 (orthonormal discrete Chebyshev basis of the grid)."""
+    torch = _torch()
+    T = torch.empty(64, n, dtype=torch.float64, device=device)
+    rc = load().rhosvd_chebyshev(int(n), float(b), _c.c_void_p(T.data_ptr()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_chebyshev")
+    return T.t()
+
+
+def rhosvd_proj_target(QT, Z, r, stream=None):
+    """G (64 x 64 float32, G[i + 64 i']) of the leading r columns of Z (column-major)."""
+    torch = _torch()
+    G = torch.empty(64 * 64, dtype=torch.float32, device=Z.device)
+    ldz = max(Z.stride(1), Z.shape[0])
+    rc = load().rhosvd_proj_target(int(QT.shape[0]), _c.c_void_p(QT.data_ptr()), _c.c_void_p(Z.data_ptr()), ldz,
+                                   int(r), _c.c_void_p(G.data_ptr()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_proj_target")
+    return G
+
+
+def rhosvd_proposal_basis(QT, Y, stream=None):
+    """Q0 (n x 32 column-major float64) from one mode's network output Y (2048 float32)."""
+    torch = _torch()
+    n = int(QT.shape[0])
+    Q0 = torch.empty(32, n, dtype=torch.float64, device=Y.device)
+    rc = load().rhosvd_proposal_basis(n, _c.c_void_p(QT.data_ptr()), _c.c_void_p(Y.data_ptr()),
+                                      _c.c_void_p(Q0.data_ptr()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_proposal_basis")
+    return Q0.t()
+

@@ -113,8 +113,10 @@ inline size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 // Workspace plan: sizes and byte offsets, a pure function of sizes and options.
 struct Plan {
     int n[3], R, rmax, kin[3], direct[3];
+    int kb[3];            // basis capacity of mode l: k_l, plus kdef for a sketched mode
     int KW;               // basis capacity: max k_l over modes + kdef
     int kdef;             // width of the deflation sketch (0: none)
+    int start;            // a caller's start basis replaces the random sketch
     int NQ;               // max n_l over modes
     int ks_sketch, ks_gram, ks_bbt;
     size_t o_cpart, o_colmax, o_defl, o_defT;
@@ -145,11 +147,12 @@ int choose_split(int tiles, int K)
 
 int tiles_of(int M, int N) { return ((M + 63) / 64) * ((N + 63) / 64); }
 
-int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
+int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0)
 {
     if (!cp || !o) return RHOSVD_ERR_INVALID_ARG;
     if (cp->R < 0) return RHOSVD_ERR_INVALID_ARG;
     if (o->r_max < 1 || o->r_max > KMAX || o->oversample < 0) return RHOSVD_ERR_INVALID_ARG;
+    if (k0 < 0 || k0 > KMAX - 64) return RHOSVD_ERR_INVALID_ARG;
     if (o->precision != RHOSVD_PLAIN_FP64 && o->precision != RHOSVD_MIXED) return RHOSVD_ERR_INVALID_ARG;
     if (!(o->eps >= 0.0)) return RHOSVD_ERR_INVALID_ARG;
     memset(p, 0, sizeof(*p));
@@ -171,7 +174,7 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
             p->kin[l] = cp->n[l];
         } else {
             p->direct[l] = 0;
-            int k = kcap;
+            int k = k0 > 0 ? k0 : kcap;             // a start basis fixes the subspace width
             if (cp->R > 0 && k > cp->R) k = cp->R;
             if (k < 1) k = 1;
             p->kin[l] = k;
@@ -182,6 +185,9 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p)
     p->kdef = 0;
     for (int l = 0; l < 3; ++l)
         if (!p->direct[l] && cp->R > p->kin[l]) p->kdef = kdef;   // only a sketched mode can miss directions
+    if (p->kdef > 0 && p->KW + p->kdef > KMAX) p->kdef = KMAX - p->KW;
+    p->start = k0 > 0;
+    for (int l = 0; l < 3; ++l) p->kb[l] = p->kin[l] + (p->direct[l] ? 0 : p->kdef);
     p->KW += p->kdef;
     const int R = cp->R > 0 ? cp->R : 1;
     const long long NK = (long long)p->NQ * p->KW, KK = (long long)p->KW * p->KW;
@@ -311,11 +317,18 @@ extern "C" int rhosvd_subspace_width(const rhosvd_cp* cp, const rhosvd_opts* opt
     return p.kin[mode];
 }
 
-extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rhosvd_tucker* out,
-                          void* workspace, size_t workspace_bytes, void* stream)
+struct StartBasis {
+    const double* Q0[3];   // n_l x k0, column-major, leading dimension ld[l]
+    int ld[3];
+    int k0;
+    int iters;             // 0: Y = Q0; 1: Y = U~ (U~^T Q0)
+};
+
+static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBasis* sb0, const rhosvd_tucker* out,
+                    void* workspace, size_t workspace_bytes, void* stream)
 {
     Plan p;
-    int rc = make_plan(cp, opts, &p);
+    int rc = make_plan(cp, opts, &p, sb0 ? sb0->k0 : 0);
     if (rc) return rc;
     if (!out || !out->info || !out->beta) return RHOSVD_ERR_INVALID_ARG;
     for (int l = 0; l < 3; ++l) {
@@ -462,7 +475,106 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             g.mode = l;
             gb.p[b] = g;
         }
-        if (mixed) {
+        if (p.start && sb0->iters == 0) {
+            // the caller's start basis itself is orthonormalised (no pass over U~)
+            for (int b = 0; b < nsk; ++b) {
+                const int l = sk.m[b];
+                if (cudaMemcpy2DAsync(bufA + l * NK, sizeof(double) * p.n[l], sb0->Q0[l], sizeof(double) * sb0->ld[l],
+                                      sizeof(double) * p.n[l], p.kin[l], cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                    return RHOSVD_ERR_CUDA;
+            }
+        } else if (p.start) {
+            // one subspace iteration from the caller's start basis replaces the random sketch:
+            // P = U~^T Q0 (R x k0, column-major in the B buffer), Y = U~ P
+            if (mixed) {
+                OzSliceArgs sq, sp;
+                memset(&sq, 0, sizeof(sq));
+                memset(&sp, 0, sizeof(sp));
+                sq.S = sp.S = 6;
+                OzBatch o1, o2;
+                memset(&o1, 0, sizeof(o1));
+                memset(&o2, 0, sizeof(o2));
+                o1.nbatch = o2.nbatch = nsk;
+                o1.err = o2.err = ozerr;
+                for (int b = 0; b < nsk; ++b) {
+                    const int l = sk.m[b];
+                    double* P = Bm + (size_t)l * KW * R;
+                    sq.X[b] = sb0->Q0[l];
+                    sq.rs[b] = sb0->ld[l];
+                    sq.cs[b] = 1;
+                    sq.rows[b] = p.kin[l];
+                    sq.K[b] = p.n[l];
+                    sq.planes[b] = pP2 + l * p.sP2;
+                    sq.pstride[b] = (long long)p.kin[l] * p.ldn;
+                    sq.ld[b] = p.ldn;
+                    sq.exps[b] = eP2 + l * EX;
+                    OzProblem& q = o1.p[b];
+                    q.A = OzPlanes{pU2 + l * p.sU2, (long long)R * p.ldn, p.ldn, eU2 + l * EX, 0};
+                    q.B = OzPlanes{sq.planes[b], sq.pstride[b], p.ldn, sq.exps[b], 0};
+                    q.M = R;
+                    q.N = p.kin[l];
+                    q.K = p.n[l];
+                    q.C = P;
+                    q.crs = 1;
+                    q.ccs = R;
+                    sp.X[b] = P;
+                    sp.rs[b] = R;
+                    sp.cs[b] = 1;
+                    sp.rows[b] = p.kin[l];
+                    sp.K[b] = R;
+                    sp.planes[b] = pP1 + l * p.sP1;
+                    sp.pstride[b] = (long long)p.kin[l] * p.ldR;
+                    sp.ld[b] = p.ldR;
+                    sp.exps[b] = eP1 + l * EX;
+                    OzProblem& q2 = o2.p[b];
+                    q2.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1};
+                    q2.B = OzPlanes{sp.planes[b], sp.pstride[b], p.ldR, sp.exps[b], 0};
+                    q2.M = p.n[l];
+                    q2.N = p.kin[l];
+                    q2.K = R;
+                    q2.C = bufA + l * NK;
+                    q2.crs = 1;
+                    q2.ccs = p.n[l];
+                }
+                STAGE("sketch", launch_oz_slice(sq, nsk, st));
+                STAGE("sketch", launch_ozgemm(o1, OZ_F64_STORE, st));
+                STAGE("sketch", launch_oz_slice(sp, nsk, st));
+                STAGE("sketch", launch_ozgemm(o2, OZ_F64_STORE, st));
+            } else {
+                GemmBatch g1, g2;
+                memset(&g1, 0, sizeof(g1));
+                g1.nbatch = nsk;
+                g1.ksplit = 1;
+                g1.bkind = B_PLAIN;
+                g2 = g1;
+                for (int b = 0; b < nsk; ++b) {
+                    const int l = sk.m[b];
+                    double* P = Bm + (size_t)l * KW * R;
+                    GemmProblem a = blank_problem();
+                    a.A = Mat{Un + l * US, (long long)p.n[l], 1};            // A(nu, x) = U~(x, nu)
+                    a.B = Mat{sb0->Q0[l], 1, (long long)sb0->ld[l]};       // B(x, j) = Q0(x, j)
+                    a.C = P;
+                    a.crs = 1;
+                    a.ccs = R;
+                    a.M = R;
+                    a.N = p.kin[l];
+                    a.K = p.n[l];
+                    g1.p[b] = a;
+                    GemmProblem c = blank_problem();
+                    c.A = Mat{Un + l * US, 1, (long long)p.n[l]};            // A(x, nu) = U~(x, nu)
+                    c.B = Mat{P, 1, (long long)R};                          // B(nu, j) = P(nu, j)
+                    c.C = bufA + l * NK;
+                    c.crs = 1;
+                    c.ccs = p.n[l];
+                    c.M = p.n[l];
+                    c.N = p.kin[l];
+                    c.K = R;
+                    g2.p[b] = c;
+                }
+                STAGE("sketch", launch_gemm(g1, st));
+                STAGE("sketch", launch_gemm(g2, st));
+            }
+        } else if (mixed) {
             OzBatch ob;
             memset(&ob, 0, sizeof(ob));
             ob.nbatch = nsk;
@@ -725,7 +837,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             g.C = Bm + (size_t)l * KW * R;
             g.crs = 1;
             g.ccs = KW;
-            g.M = p.kin[l];
+            g.M = p.kb[l];
             g.dM = &S->m[l];
             g.N = R;
             g.K = p.n[l];
@@ -743,18 +855,18 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 sq.X[l] = Qfin[l];
                 sq.rs[l] = ldq[l];
                 sq.cs[l] = 1;
-                sq.rows[l] = p.kin[l];
+                sq.rows[l] = p.kb[l];
                 sq.drows[l] = &S->m[l];
                 sq.K[l] = p.n[l];
                 sq.planes[l] = pP2 + l * p.sP2;
-                sq.pstride[l] = (long long)p.kin[l] * p.ldn;
+                sq.pstride[l] = (long long)p.kb[l] * p.ldn;
                 sq.ld[l] = p.ldn;
                 sq.exps[l] = eP2 + l * EX;
                 OzProblem& q = ob.p[l];
                 q.A = OzPlanes{pU2 + l * p.sU2, (long long)R * p.ldn, p.ldn, eU2 + l * EX, 0};
-                q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.kin[l] * p.ldn, p.ldn, eP2 + l * EX, 0};
+                q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.kb[l] * p.ldn, p.ldn, eP2 + l * EX, 0};
                 q.M = R;
-                q.N = p.kin[l];
+                q.N = p.kb[l];
                 q.dN = &S->m[l];
                 q.K = p.n[l];
                 q.C = Bm + (size_t)l * KW * R;
@@ -781,8 +893,8 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             g.C = G + l * KK;
             g.crs = 1;
             g.ccs = KW;
-            g.M = p.kin[l];
-            g.N = p.kin[l];
+            g.M = p.kb[l];
+            g.N = p.kb[l];
             g.K = R;
             g.dM = &S->m[l];
             g.dN = &S->m[l];
@@ -802,17 +914,17 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 sg.X[l] = Bm + (size_t)l * KW * R;
                 sg.rs[l] = 1;
                 sg.cs[l] = KW;
-                sg.rows[l] = p.kin[l];
+                sg.rows[l] = p.kb[l];
                 sg.drows[l] = &S->m[l];
                 sg.K[l] = R;
                 sg.planes[l] = pP1 + l * p.sP1;
-                sg.pstride[l] = (long long)p.kin[l] * p.ldR;
+                sg.pstride[l] = (long long)p.kb[l] * p.ldR;
                 sg.ld[l] = p.ldR;
                 sg.exps[l] = eP1 + l * EX;
                 OzProblem& q = ob.p[l];
                 q.A = OzPlanes{sg.planes[l], sg.pstride[l], p.ldR, sg.exps[l], 0};
                 q.B = q.A;
-                q.M = q.N = p.kin[l];
+                q.M = q.N = p.kb[l];
                 q.dM = q.dN = &S->m[l];
                 q.K = R;
                 q.C = G + l * KK;
@@ -873,9 +985,9 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             g.crs = 1;
             g.ccs = p.n[l];
             g.M = p.n[l];
-            g.N = p.kin[l];
+            g.N = p.kb[l];
             g.dN = &S->rhi[l];
-            g.K = p.kin[l];
+            g.K = p.kb[l];
             g.dK = &S->m[l];
             gz.p[l] = g;
             GemmProblem h = blank_problem();
@@ -884,10 +996,10 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             h.C = Vw + l * VS;
             h.crs = 1;
             h.ccs = KW;
-            h.M = p.kin[l];
+            h.M = p.kb[l];
             h.dM = &S->rhi[l];
             h.N = R;
-            h.K = p.kin[l];
+            h.K = p.kb[l];
             h.dK = &S->m[l];
             gv.p[l] = h;
             // residual energy ||U_normalised - Z_hi V_hi||_F^2 (no output matrix)
@@ -896,7 +1008,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
             e.B = Mat{Vw + l * VS, 1, KW};
             e.M = p.n[l];
             e.N = R;
-            e.K = p.kin[l];
+            e.K = p.kb[l];
             e.dK = &S->rhi[l];
             e.rref = Un + l * US;
             e.rref_ld = p.n[l];
@@ -918,7 +1030,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 sq.rs[l] = 1;
                 sq.cs[l] = ldq[l];
                 sq.rows[l] = p.n[l];
-                sq.K[l] = p.kin[l];
+                sq.K[l] = p.kb[l];
                 sq.dK[l] = &S->m[l];
                 sq.planes[l] = pP2 + l * p.sP2;
                 sq.pstride[l] = (long long)p.n[l] * p.ldk;
@@ -927,21 +1039,21 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 sw.X[l] = W + l * KK;
                 sw.rs[l] = KW;
                 sw.cs[l] = 1;
-                sw.rows[l] = p.kin[l];
+                sw.rows[l] = p.kb[l];
                 sw.drows[l] = &S->rhi[l];
-                sw.K[l] = p.kin[l];
+                sw.K[l] = p.kb[l];
                 sw.dK[l] = &S->m[l];
                 sw.planes[l] = pP1 + l * p.sP1;
-                sw.pstride[l] = (long long)p.kin[l] * p.ldk;
+                sw.pstride[l] = (long long)p.kb[l] * p.ldk;
                 sw.ld[l] = p.ldk;
                 sw.exps[l] = eP1 + l * EX;
                 OzProblem& q = oz.p[l];
                 q.A = OzPlanes{sq.planes[l], sq.pstride[l], p.ldk, sq.exps[l], 0};
                 q.B = OzPlanes{sw.planes[l], sw.pstride[l], p.ldk, sw.exps[l], 0};
                 q.M = p.n[l];
-                q.N = p.kin[l];
+                q.N = p.kb[l];
                 q.dN = &S->rhi[l];
-                q.K = p.kin[l];
+                q.K = p.kb[l];
                 q.dK = &S->m[l];
                 q.C = Zw + l * NK;
                 q.crs = 1;
@@ -968,7 +1080,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 s1.rs[l] = KW;
                 s1.cs[l] = 1;
                 s1.rows[l] = R;
-                s1.K[l] = p.kin[l];
+                s1.K[l] = p.kb[l];
                 s1.dK[l] = &S->m[l];
                 s1.planes[l] = pP1 + l * p.sP1;
                 s1.pstride[l] = (long long)R * p.ldk;
@@ -976,22 +1088,22 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 s2.X[l] = W + l * KK;
                 s2.rs[l] = KW;
                 s2.cs[l] = 1;
-                s2.rows[l] = p.kin[l];
+                s2.rows[l] = p.kb[l];
                 s2.drows[l] = &S->rhi[l];
-                s2.K[l] = p.kin[l];
+                s2.K[l] = p.kb[l];
                 s2.dK[l] = &S->m[l];
                 s2.planes[l] = pP2 + l * p.sP2;
-                s2.pstride[l] = (long long)p.kin[l] * p.ldk;
+                s2.pstride[l] = (long long)p.kb[l] * p.ldk;
                 s2.ld[l] = p.ldk;
                 s1.exps[l] = eP1 + l * EX;
                 s2.exps[l] = eP2 + l * EX;
                 OzProblem& q = ob.p[l];
                 q.A = OzPlanes{pP1 + l * p.sP1, (long long)R * p.ldk, p.ldk, eP1 + l * EX, 0};
-                q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.kin[l] * p.ldk, p.ldk, eP2 + l * EX, 0};
+                q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.kb[l] * p.ldk, p.ldk, eP2 + l * EX, 0};
                 q.M = R;
-                q.N = p.kin[l];
+                q.N = p.kb[l];
                 q.dN = &S->rhi[l];
-                q.K = p.kin[l];
+                q.K = p.kb[l];
                 q.dK = &S->m[l];
                 q.C = Vw + l * VS;
                 q.crs = KW;
@@ -1010,7 +1122,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 s1.rs[l] = KW;
                 s1.cs[l] = 1;
                 s1.rows[l] = R;
-                s1.K[l] = p.kin[l];
+                s1.K[l] = p.kb[l];
                 s1.dK[l] = &S->rhi[l];
                 s1.planes[l] = pP1 + l * p.sP1;
                 s1.pstride[l] = (long long)R * p.ldk;
@@ -1020,7 +1132,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 s2.cs[l] = p.n[l];
                 s2.rows[l] = p.n[l];
                 s2.drows[l] = nullptr;
-                s2.K[l] = p.kin[l];
+                s2.K[l] = p.kb[l];
                 s2.dK[l] = &S->rhi[l];
                 s2.planes[l] = pP2 + l * p.sP2;
                 s2.pstride[l] = (long long)p.n[l] * p.ldk;
@@ -1032,7 +1144,7 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                 q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.n[l] * p.ldk, p.ldk, eP2 + l * EX, 0};
                 q.M = R;
                 q.N = p.n[l];
-                q.K = p.kin[l];
+                q.K = p.kb[l];
                 q.dK = &S->rhi[l];
                 q.ref = Un + l * US;
                 q.ref_rs = p.n[l];
@@ -1155,6 +1267,35 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
         }
     }
     return RHOSVD_OK;
+}
+
+extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rhosvd_tucker* out,
+                          void* workspace, size_t workspace_bytes, void* stream)
+{
+    return c2t_impl(cp, opts, nullptr, out, workspace, workspace_bytes, stream);
+}
+
+extern "C" size_t rhosvd_c2t_start_workspace_size(const rhosvd_cp* cp, const rhosvd_opts* opts, int k0)
+{
+    Plan p;
+    if (k0 < 1 || make_plan(cp, opts, &p, k0) != RHOSVD_OK) return 0;
+    return p.total;
+}
+
+extern "C" int rhosvd_c2t_start(const rhosvd_cp* cp, const rhosvd_opts* opts, const double* const Q0[3],
+                                const int ld[3], int k0, int iters, const rhosvd_tucker* out, void* workspace,
+                                size_t workspace_bytes, void* stream)
+{
+    if (!cp || !Q0 || !ld || k0 < 1 || iters < 0 || iters > 1) return RHOSVD_ERR_INVALID_ARG;
+    StartBasis sb;
+    for (int l = 0; l < 3; ++l) {
+        if (!Q0[l] || ld[l] < cp->n[l]) return RHOSVD_ERR_INVALID_ARG;
+        sb.Q0[l] = Q0[l];
+        sb.ld[l] = ld[l];
+    }
+    sb.k0 = k0;
+    sb.iters = iters;
+    return c2t_impl(cp, opts, &sb, out, workspace, workspace_bytes, stream);
 }
 
 extern "C" int rhosvd_cp_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, double* const U_out[3],

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
     constexpr int MINCAD = oz_acc_cad(SA, SB, NE, NU - 1) < oz_acc_cad(SA, SB, NE, 0)
                                ? oz_acc_cad(SA, SB, NE, NU - 1) : oz_acc_cad(SA, SB, NE, 0);
     static_assert(NT % 32 == 0 && NT >= 32 && NU * NT <= 512, "tile: 8-column TMEM loads per thread quarter");
-    static_assert(GMAX >= 2 && GMAX <= SA + SB && NACC >= 2, "groups");
+    static_assert(GMAX >= 2 && GMAX <= SA + SB && NACC >= 1 && (NACC >= 2 || GMAX == 2), "groups");
     static_assert(oz_exact_ok(SA, SB, NE), "an exact group needs at most 8 pairs");
     const int nsplit = batch.nsplit > 1 ? batch.nsplit : 1;
     const int split = blockIdx.z % nsplit;
@@ -486,6 +486,7 @@ int launch_ozgemm(const OzBatch& b, OzKind kind, cudaStream_t st)
     case OZ_F64_RESID: return run_oz<6, 6, 8, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_RESID, OZ_NT6, 7>(b, st);
     case OZ_SKETCH: return run_oz<6, 1, 7, OZ_A_PLANES, OZ_B_SIGN, OZ_EPI_STORE, 96, 5>(b, st);
     case OZ_CORE: return run_oz<4, 4, 5, OZ_A_KR, OZ_B_PLANES, OZ_EPI_STORE, 160, 3>(b, st);
+    case OZ_BF16: return run_oz<1, 1, 2, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_STORE, 128, 1>(b, st);
     }
     return RHOSVD_ERR_INVALID_ARG;
 }

@@ -146,7 +146,10 @@ int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st);
 
 // the four instantiations: FP64-class product (S = 6, all groups exact) storing C or reducing
 // the residual energy; range sketch against Rademacher signs; Khatri-Rao core (S = 4)
-enum OzKind { OZ_F64_STORE = 0, OZ_F64_RESID = 1, OZ_SKETCH = 2, OZ_CORE = 3 };
+enum OzKind { OZ_F64_STORE = 0, OZ_F64_RESID = 1, OZ_SKETCH = 2, OZ_CORE = 3, OZ_BF16 = 4 };
+// OZ_BF16: one plane per operand holding arbitrary BF16 values (not digits), exponents 8 and 8
+// (scale 2^0), FP32 accumulation read back every 256 K: a plain BF16 GEMM with FP64 output,
+// used by the learned-proposal network.
 int launch_ozgemm(const OzBatch& b, OzKind kind, cudaStream_t st);
 
 // split count for an M x N x K product: enough CTAs for two per SM, at least 4 stages each

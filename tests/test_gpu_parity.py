@@ -135,6 +135,28 @@ def test_gauss_sketch_ragged(rhosvd_cuda):
     assert d is not None
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_width_sketch_grown_by_deflation(rhosvd_cuda, precision):
+    """No oversampling: the first sketch keeps all its k = 106 columns, and the deflation sketch
+    grows the basis past k.  Every product after the basis (B = Q^T U, B B^T, Z, V, residual)
+    must cover the grown width.  Fixed ranks give element-wise parity; with the eps rule the
+    rank may exceed the oracle's by one (the basis misses a little more energy than a wider
+    sketch), but the measured error must meet the rule."""
+    P = rhosvd_cuda
+    cp = workloads.gaussian_sum(384, 600, 7)
+    g, o, d = check_case(P, cp.U, cp.xi, 1e-6, r_max=106, oversample=0, ranks=(100, 100, 100),
+                         precision=precision)
+    assert max(g["info"].k[l] for l in range(3)) > 106
+    assert d is not None
+    o = oracle.c2t(cp.U, cp.xi, eps=1e-6)
+    g = run_gpu(P, cp.U, cp.xi, 1e-6, r_max=106, oversample=0, precision=precision)
+    info = g["info"]
+    assert info.status == 0, P.rhosvd_strerror(info.status)
+    for l in range(3):
+        assert o["ranks"][l] <= g["ranks"][l] <= o["ranks"][l] + 1, (l, g["ranks"], o["ranks"])
+        assert info.tail[l] ** 2 <= 1e-12 * info.total[l] * (1 + 1e-9)
+
+
 def test_hadamard_then_reduce(rhosvd_cuda):
     P = rhosvd_cuda
     import torch

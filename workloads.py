@@ -6,7 +6,7 @@ A = sum_k xi_k u1_k (x) u2_k (x) u3_k (paper Sec. 2.1, eq. can_A3).  It holds no
 of the RHOSVD arithmetic; both the CPU oracle (``oracle/``) and the CUDA library
 consume what it returns.
 
-Grid (paper Sec. 3 "centers of discretization intervals", Sec. 4.1 mesh h=2b/n):
+Grid (paper Sec. 3 collocation at the interval midpoints, Sec. 4.1 mesh h=2b/n):
 cell centres x_i = -b + (i - 1/2) h, h = 2b/n, i = 1..n.  Factor columns are the
 Gaussians sampled at those points (collocation).
 
@@ -160,3 +160,21 @@ def random_cp(n, R, seed, signed=True, dist="normal") -> CP:
             U.append(np.asfortranarray(g.random((ns[l], R))))
     xi = g.standard_normal(R) if signed else g.random(R) + 0.1
     return CP(U=U, xi=xi.astype(np.float64), meta=dict(kind="random", seed=seed))
+
+
+def gaussian_sum_device(n: int, R: int, seed: int, device="cuda", **kw):
+    """gaussian_sum(n, R, seed) with the factor columns evaluated on the device (torch):
+    returns (U list of column-major float64 CUDA tensors, xi, params) where params holds the
+    centres (R x 3), log-exponents and weights as CUDA float64 tensors (the inputs of the
+    learned proposal's features).  Same parameter draws as gaussian_sum."""
+    import torch
+    x, centres, a, c = gaussian_sum_params(n, R, seed, **kw)
+    xt = torch.from_numpy(x).to(device)
+    at = torch.from_numpy(a).to(device)
+    U = []
+    for l in range(3):
+        d = xt[:, None] - torch.from_numpy(centres[:, l].copy()).to(device)[None, :]
+        U.append(torch.exp(-at[None, :] * d * d).t().contiguous().t())
+    params = dict(centres=torch.from_numpy(np.ascontiguousarray(centres)).to(device),
+                  loga=torch.from_numpy(np.log(a)).to(device), c=torch.from_numpy(c).to(device))
+    return U, torch.from_numpy(c).to(device), params
