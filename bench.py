@@ -305,6 +305,98 @@ def batched_leg(P, dev, steps, warmup, precision):
             "l2": "inputs (about 10 GB) larger than L2"}
 
 
+LEARNED = dict(workload="learned_proposal_n1024_R2000_8000", n=1024, R_range=[2000, 8000], eps=1e-6,
+               r_max=160, oversample=32, seed=5, nprop=32, train_seed=10**6, eval_seed=10**6 + 20000,
+               batch=256, lr=1e-3, epochs=10)
+
+
+def _quantiles(v):
+    import numpy as np
+    v = np.asarray(v, dtype=np.float64)
+    return {"p10": float(np.quantile(v, 0.1)), "p50": float(np.quantile(v, 0.5)), "p90": float(np.quantile(v, 0.9))}
+
+
+def learned_leg(P, dev, n_train, n_eval, precision):
+    """The learned-proposal workload (n = 1024, R log-uniform in [2000, 8000], eps = 1e-6): the
+    network is trained on the GPU, by the library's own kernels, on the leading bases the method
+    without it computes for n_train instances, then evaluated on n_eval held-out seeds.  Reports
+    the energy its 32-vector subspace misses (no pass over U, and after one subspace iteration)
+    against a random start of the same width and against the best 32-vector subspace, the
+    fallback rate of the proposal -> iteration -> plain path at eps, and that path's wall time
+    per reduction next to the plain call's."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_2201_12663_gb300 import learned
+    L = LEARNED
+    opts = dict(eps=L["eps"], r_max=L["r_max"], oversample=L["oversample"], seed=L["seed"],
+                precision=PRECISIONS[precision])
+    prop = learned.LearnedProposal(L["n"], batch_max=L["batch"], seed=0)
+    t0 = time.perf_counter()
+    X, G, ranks = [], [], []
+    for n, R, s in workloads.learned_instances(n_train, L["train_seed"], L["n"], tuple(L["R_range"])):
+        U, xi, params = workloads.gaussian_sum_device(n, R, s, dev)
+        res = P.rhosvd_c2t(U, xi, **opts)
+        info = res.info()
+        if info.status != 0:
+            continue
+        f = prop.features(params)
+        for l in range(3):
+            X.append(f[l])
+            G.append(prop.target(res.Z[l], max(1, info.r[l])))
+        ranks.append([info.r[l] for l in range(3)])
+    X, G = torch.stack(X), torch.stack(G)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    steps = max(300, L["epochs"] * X.shape[0] // L["batch"])
+    t0 = time.perf_counter()
+    losses = learned.train(prop, X, G, steps=steps, batch=L["batch"], lr=L["lr"])
+    t_train = time.perf_counter() - t0
+    del X, G
+    g = torch.Generator(device=dev).manual_seed(0)
+    missed = {k: [] for k in ("learned_iters0", "learned_iters1", "random_iters0", "random_iters1", "best_32")}
+    fallbacks, path_ok, t_plain, t_path = 0, 0, 0.0, 0.0
+    fixed = {**opts, "ranks": (L["nprop"],) * 3, "deflate": -1}
+    for n, R, s in workloads.learned_instances(n_eval, L["eval_seed"], L["n"], tuple(L["R_range"])):
+        U, xi, params = workloads.gaussian_sum_device(n, R, s, dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = P.rhosvd_c2t(U, xi, **opts)
+        info = res.info()
+        t_plain += time.perf_counter() - t0
+        sig = res.sigma.cpu().numpy()
+        for l in range(3):
+            tail = float(np.sum(sig[l, L["nprop"]:info.k[l]] ** 2))
+            missed["best_32"].append((info.resid[l] + tail) / info.total[l])
+        t0 = time.perf_counter()
+        res2, fell = learned.reduce_learned(prop, U, xi, params, attempts=(0, 1), **opts)
+        st2 = res2.info().status
+        t_path += time.perf_counter() - t0
+        fallbacks += int(fell)
+        starts = {"learned": prop.propose(prop.features(params)),
+                  "random": [torch.randn(L["nprop"], n, generator=g, device=dev, dtype=torch.float64).t()
+                             for _ in range(3)]}
+        for k, Q0 in starts.items():
+            for it in (0, 1):
+                r3 = P.rhosvd_c2t_start(U, xi, Q0, iters=it, **fixed).info()
+                for l in range(3):
+                    missed[f"{k}_iters{it}"].append(r3.resid[l] / r3.total[l])
+        path_ok += int(st2 == 0)
+    q = {k: _quantiles(v) for k, v in missed.items()}
+    prop.mlp.close()
+    return {**L, "precision": precision, "n_train": n_train, "n_eval": n_eval, "train_samples": 3 * len(ranks),
+            "train_steps": steps, "loss_first10": float(np.mean(losses[:10])), "loss_last10": float(np.mean(losses[-10:])),
+            "data_s": t_data, "train_s": t_train,
+            "eps_ranks_p50": [int(np.median([r[l] for r in ranks])) for l in range(3)],
+            "missed_energy": q, "missed_energy_is": "residual energy outside the 32-vector subspace / total, per mode",
+            "fallback_rate": fallbacks / max(1, n_eval), "path_status_ok": path_ok,
+            "eps_at_50pct_accept_iters1": float(np.sqrt(q["learned_iters1"]["p50"])),
+            "ms_per_reduction_plain": 1000.0 * t_plain / max(1, n_eval),
+            "ms_per_reduction_learned_path": 1000.0 * t_path / max(1, n_eval),
+            "speedup_vs_plain": t_plain / max(t_path, 1e-12),
+            "timing": "host wall clock with synchronisation per reduction (the path decides on the host)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -495,6 +587,8 @@ def run_ours(args):
             "clocks": clocks, "wall_s_timed": t_wall, "parallelism": f"replicas{world}"}
     if not args.no_batched:
         line["batched"] = batched_leg(P, dev, args.steps, args.warmup, main_prec)
+    if args.learned_train > 0:
+        line["learned"] = learned_leg(P, dev, args.learned_train, args.learned_eval, main_prec)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample()
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -515,6 +609,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--precision", choices=["mixed", "plain"], default="mixed")
+    ap.add_argument("--learned-train", type=int, default=600,
+                    help="training instances of the learned-proposal leg (0 skips it; the full workload is 20000)")
+    ap.add_argument("--learned-eval", type=int, default=60, help="held-out instances (the full workload is 2000)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -71,12 +71,16 @@ def train(prop, X, G, steps=200, batch=64, lr=1e-3, seed=0):
     return [float(x.item()) for x in losses]
 
 
-def reduce_learned(prop, U, xi, params, iters=1, **opts):
-    """Proposal -> rhosvd_c2t_start (iters subspace iterations + the deflation sketch); if the
-    captured energy falls short of 1 - eps^2 (status RHOSVD_ERR_SKETCH) the plain rhosvd_c2t is
-    run instead.  Returns (result, fallback_used)."""
+def reduce_learned(prop, U, xi, params, attempts=(0, 1), **opts):
+    """Proposal -> acceptance test -> subspace iteration -> fallback.  Each entry of attempts is a
+    rhosvd_c2t_start call with that many subspace iterations (0: the proposal itself, one pass
+    over U for B = Q0^T U and the residual).  An attempt is accepted when the measured residual
+    energy meets the eps rule (status 0); when it falls short of 1 - eps^2 (status
+    RHOSVD_ERR_SKETCH) the next attempt runs, and after the last one the plain rhosvd_c2t.
+    Returns (result, fallback_used)."""
     Q0 = prop.propose(prop.features(params))
-    res = rhosvd_c2t_start(U, xi, Q0, iters=iters, **opts)
-    if res.info().status == RHOSVD_ERR_SKETCH:
-        return rhosvd_c2t(U, xi, **opts), True
-    return res, False
+    for it in attempts:
+        res = rhosvd_c2t_start(U, xi, Q0, iters=it, **opts)
+        if res.info().status != RHOSVD_ERR_SKETCH:
+            return res, False
+    return rhosvd_c2t(U, xi, **opts), True

@@ -135,11 +135,28 @@ def batched_gaussian_sums(count: int = 512, seed0: int = 0, n_choices=(128, 256,
     return [(int(ns[i]), int(Rs[i]), seed0 + i) for i in range(count)]
 
 
+def learned_instances(count: int, first_seed: int, n: int = 1024, R_range=(2000, 8000)):
+    """Shapes and seeds of the learned-proposal workload: instance i uses seed first_seed + i
+    and R_i = round(exp(uniform(log R_lo, log R_hi))) drawn with PCG64([first_seed + i, 1]) (a
+    stream apart from the instance's own Gaussian parameters).  Training uses first_seed = 10**6,
+    held-out evaluation the seeds after the largest training set (10**6 + 20000 on).
+    Returns a list of (n, R, seed)."""
+    out = []
+    for i in range(count):
+        s = first_seed + i
+        g = np.random.default_rng([s, 1])
+        R = int(np.rint(np.exp(g.uniform(math.log(R_range[0]), math.log(R_range[1])))))
+        out.append((int(n), R, s))
+    return out
+
+
 # Named workloads (sizes, distributions and thresholds).
 CONFIGS = {
     "gauss_n128_R200": dict(n=128, R=200, seed=0, eps=1e-6),
     "hadamard_n1024_R64x64": dict(n=1024, Ra=64, Rb=64, seeds=(0, 1), eps=1e-7),
     "newton_lr_n2048_N1000": dict(n=2048, N=1000, seed=0, eps=1e-6),
+    "learned_n1024_R2000_8000": dict(n=1024, R_range=(2000, 8000), train_seed=10**6, n_train=20000,
+                                     eval_seed=10**6 + 20000, n_eval=2000, eps=1e-6, nprop=32),
 }
 
 
