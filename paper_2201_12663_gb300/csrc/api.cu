@@ -605,7 +605,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         // columns (outputs); d0out: the first pass's largest Gram diagonal (optional); d0ref,
         // floor_rel: absolute pivot floor floor_rel * d0ref (optional)
         auto cholqr3 = [&](double* bIn, double* bTmp, const int* kh, const int* dk0, int* dm, int* dkx,
-                           double* d0out, const double* d0ref, double floor_rel) -> int {
+                           double* d0out, const double* d0ref, double floor_rel, int* dnear) -> int {
         const double tols[3] = {1e-15, 1e-11, 0.0};
         const int pivots[3] = {1, 1, 0};
         for (int pass = 0; pass < 3; ++pass) {
@@ -672,13 +672,13 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 STAGE("cholqr_gram", launch_gemm_splitk(g2, part, st));
             }
             const int* dk = (pass == 0) ? dk0 : dm;
+            // Y = X P Lt^{-T}: the triangular inverse scattered into W (the Gram's buffer), then
+            // one GEMM over the kx columns of X (a near-identity Gram has W written by the Cholesky)
+            double* Wq = G;
             STAGE("cholqr_chol", launch_chol(sk, G, KK, KW, dk, dkx, L, KK, KW, perm, KW, dm, S->piv_fail,
                                              pivots[pass], tols[pass], nsk, KW, pass == 0 ? d0out : nullptr,
-                                             d0ref, floor_rel, st));
-            // Y = X P Lt^{-T}: the triangular inverse scattered into W (the Gram's buffer), then
-            // one GEMM over the kx columns of X
-            double* Wq = G;
-            STAGE("cholqr_trinv", launch_trinv(sk, L, KK, KW, perm, KW, dkx, dm, Wq, KK, KW, nsk, st));
+                                             d0ref, floor_rel, Wq, KK, KW, dnear, st));
+            STAGE("cholqr_trinv", launch_trinv(sk, L, KK, KW, perm, KW, dkx, dm, Wq, KK, KW, dnear, nsk, st));
             if (mixed) {
                 OzSliceArgs sx, sw;
                 memset(&sx, 0, sizeof(sx));
@@ -753,7 +753,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         return 0;
         };
         {
-            const int rc = cholqr3(bufA, bufB, p.kin, S->kin, S->m, S->kx, S->gmax, nullptr, 0.0);
+            const int rc = cholqr3(bufA, bufB, p.kin, S->kin, S->m, S->kx, S->gmax, nullptr, 0.0, S->near);
             if (rc) return rc;
         }
         if (p.kdef > 0) {
@@ -815,7 +815,8 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 STAGE("deflate_project", launch_deflate(sk, bufB, Ydf, NK, p.n, S->m, p.kdef, Tdf,
                                                         (long long)KMAX * p.kdef, nsk, p.NQ, st));
             {
-                const int rc = cholqr3(Ydf, Qdf, kdh, S->kdef, S->mdef, S->kxdef, nullptr, S->gmax, 1e-26);
+                const int rc = cholqr3(Ydf, Qdf, kdh, S->kdef, S->mdef, S->kxdef, nullptr, S->gmax, 1e-26,
+                                       S->neardef);
                 if (rc) return rc;
             }
             STAGE("deflate_append", launch_append(sk, bufB, Qdf, NK, p.n, S->m, S->mdef, nsk, p.NQ, p.kdef, st));

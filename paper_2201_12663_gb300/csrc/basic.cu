@@ -37,7 +37,18 @@ __global__ void k_colnorms(NormArgs a)
         int ex;
         frexp(mx, &ex);               // mx < 2^ex
         double s = 0.0;
-        if (ex > -1022 && ex < 1022) {
+        if (ex > -450 && ex < 450) {
+            // squares stay in [2^-902, 2^900): no scaling needed, one FP64 operation an element
+            // (terms that would square to subnormals lie below 2^-1022 / max^2 <= 2^-120 of the sum)
+            for (int i = lane; i < n; i += 32) s = fma(u[i], u[i], s);
+            s = warp_sum(s);
+            nrm = sqrt(s);
+            if (lane == 0) {
+                a.norms[(long long)l * a.R + warp] = nrm;
+                a.colmax[(long long)l * a.R + warp] = mx;
+            }
+            return;
+        } else if (ex > -1022 && ex < 1022) {
             const double sc = __hiloint2double((1023 - ex) << 20, 0);     // 2^-ex
             for (int i = lane; i < n; i += 32) {
                 const double t = u[i] * sc;
@@ -120,10 +131,12 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
     }
     double s = 0.0;
     const int lim = P ? ns.ld[l] : n;
+    // one multiply an element when s1 s2 is exact (s2 = 1 unless the exponent is extreme)
+    const bool one = s2 == 1.0;
     for (int i = lane; i < lim; i += 32) {
         double v = 0.0;
         if (i < n) {
-            v = keep ? (u[i] * s1) * s2 : 0.0;
+            v = keep ? (one ? u[i] * s1 : (u[i] * s1) * s2) : 0.0;
             dst[i] = v;
             s = fma(v, v, s);
         }

@@ -1,0 +1,596 @@
+// cluster.cu -- the small dense factorisations of one mode spread over a thread-block cluster.
+//
+// On this part the FP64 pipe issues about two fused multiply-adds per clock per SM, so a k x k
+// factorisation held by one block (one SM per mode) is bound by that SM's FP64 issue.  Here C
+// blocks of a cluster (16 where the device schedules such clusters, else the portable 8) share
+// one mode: each owns the rows i = rank + li C of the trailing matrix, in full length, in its
+// shared memory; the vectors every block needs are all-gathered through distributed shared
+// memory, and a step's phases are separated by cluster barriers (hardware barriers, no
+// spin-waits).  Every block computes the step's scalars itself from the same gathered values
+// in the same order, so all blocks take identical branches and arrive at every barrier.
+#include "internal.cuh"
+#include <cooperative_groups.h>
+#include <limits.h>
+
+namespace cg = cooperative_groups;
+
+namespace rh {
+
+constexpr int TC_THREADS = 256;
+
+// ------------------------------------------------------------------ tridiagonalisation
+// Householder reduction of the symmetric k x k matrix A (full storage, ld lda, lower triangle
+// read) to tridiagonal form.  Reflector j (j = 0..k-3): x = A(j+1:k, j),
+// alpha = -sign(x_0) ||x||, v = x - alpha e_1, tau = 2 / v^T v; the trailing block gets
+// A <- H A H via p = tau A v, w = p - (tau/2)(p^T v) v, A <- A - v w^T - w v^T.  Output: d
+// (diagonal), e (sub-diagonal), tau, and v stored in A(j+1:k, j) for the back-transformation.
+// Block `rank` holds rows i = rank + li C (full rows, ld k).  Per step:
+//   A  the owners send column j of their rows (x) and their part of ||x(2:)||^2 to every block;
+//      cluster barrier;
+//   B  every block forms alpha, tau and v; p_i = tau A(i, :) v for its rows, sent to every block
+//      with its part of p^T v; cluster barrier;
+//   C  every block forms w and updates its rows.
+// The gather buffers need no double buffering: a block writes step j+1's x only after passing
+// step j's second barrier (all blocks have finished reading step j's x), and step j+1's p only
+// after step j+1's first barrier (all blocks have finished step j's update, the last read of p).
+// The update applies to element (i, c) and to its mirror (c, i) the same operations on the
+// same operands, fma(-v_lo, w_hi, fma(-w_lo, v_hi, a)) with lo = min(i, c), hi = max(i, c), so
+// the full-row storage stays exactly symmetric.
+template <int C>
+__global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, double* A, long long astride, int lda,
+                                                                const int* dk, double* d, double* e, double* tau,
+                                                                int vstride)
+{
+    constexpr int ROWS = (KMAX + C - 1) / C;                       // rows a block owns at most
+    constexpr int RP2 = ROWS <= 8 ? 8 : (ROWS <= 16 ? 16 : 32);    // ... rounded up to a power of two
+    constexpr int NCH = TC_THREADS / RP2;                          // column chunks per row in A v
+    static_assert(ROWS <= 32 && NCH >= 1 && NCH <= 32 && (NCH & (NCH - 1)) == 0, "row split");
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int b = mm.m[blockIdx.y];
+    const int k = dk[b];
+    A += b * astride;
+    d += b * vstride;
+    e += b * vstride;
+    tau += b * vstride;
+    extern __shared__ double Srow[];
+    __shared__ double xg[KMAX], pg[KMAX], vl[KMAX], wl[KMAX], ploc[32];
+    __shared__ double nrm[C], pvp[C];
+    __shared__ double sc[3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nloc = rank < k ? (k - rank + C - 1) / C : 0;
+    // the owned rows from the lower triangle: A(i, c) = A[c lda + i] for c <= i, A[i lda + c] above
+    for (int idx = tid; idx < nloc * k; idx += TC_THREADS) {
+        const int li = idx / k, c = idx - li * k;
+        const int i = rank + li * C;
+        Srow[idx] = c <= i ? A[(long long)c * lda + i] : A[(long long)i * lda + c];
+    }
+    cl.sync();                     // every block resident and loaded before the first remote store
+    for (int j = 0; j + 2 < k; ++j) {
+        const int c0 = j + 1, len = k - c0;
+        const int li0 = c0 <= rank ? 0 : (c0 - rank + C - 1) / C;  // first owned row >= c0
+        const int nr = nloc > li0 ? nloc - li0 : 0;
+        // ---- A: x = column j of the owned rows, and the owned part of the tail norm
+        if (tid < nr * C) {
+            const int r = tid / C, dst = tid - r * C;
+            const int li = li0 + r;
+            cl.map_shared_rank(xg, dst)[rank + li * C] = Srow[li * k + j];
+        }
+        if (warp == TC_THREADS / 32 - 1) {
+            double s = 0.0;
+            if (lane < nr) {
+                const int li = li0 + lane;
+                if (rank + li * C > c0) {
+                    const double x = Srow[li * k + j];
+                    s = x * x;
+                }
+            }
+            s = warp_sum(s);
+            if (lane < C) cl.map_shared_rank(nrm, lane)[rank] = s;
+        }
+        cl.sync();
+        if (warp == 0) {
+            // the C partial norms by a shuffle tree (same order in every block)
+            const double t2 = warp_sum(lane < C ? nrm[lane] : 0.0);
+            if (lane == 0) {
+            const double x0 = xg[c0];
+            double tj = 0.0, al = x0;
+            if (t2 != 0.0) {
+                const double xn = sqrt(x0 * x0 + t2);
+                al = (x0 >= 0.0) ? -xn : xn;
+                const double v0 = x0 - al;
+                tj = 2.0 / (v0 * v0 + t2);
+            }
+            sc[0] = tj;
+            sc[1] = al;
+            if (rank == 0) {
+                tau[j] = tj;
+                e[j] = al;
+            }
+            if (j % C == rank) d[j] = Srow[(j / C) * k + j];
+            }
+        }
+        __syncthreads();
+        const double t_j = sc[0], alpha = sc[1];
+        for (int c = c0 + tid; c < k; c += TC_THREADS)
+            vl[c] = (t_j == 0.0) ? 0.0 : (c == c0 ? xg[c0] - alpha : xg[c]);
+        __syncthreads();
+        if (tid < nr) {                                // the reflector, for the back-transformation
+            const int i = rank + (li0 + tid) * C;
+            A[(long long)j * lda + i] = vl[i];
+        }
+        // ---- B: p = tau A v on the owned rows
+        if (t_j != 0.0) {
+            const int r = tid / NCH, ch = tid - r * NCH;
+            double acc = 0.0, acc2 = 0.0;             // two chains: FP64 latency, not issue, bounds this
+            if (r < nr) {
+                const double* row = Srow + (li0 + r) * k;
+                int c = c0 + ch;
+                for (; c + NCH < k; c += 2 * NCH) {
+                    acc = fma(row[c], vl[c], acc);
+                    acc2 = fma(row[c + NCH], vl[c + NCH], acc2);
+                }
+                if (c < k) acc = fma(row[c], vl[c], acc);
+            }
+            acc += acc2;
+            for (int o = NCH / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (ch == 0 && r < nr) ploc[r] = t_j * acc;
+            __syncthreads();
+            if (tid < nr * C) {
+                const int r2 = tid / C, dst = tid - r2 * C;
+                cl.map_shared_rank(pg, dst)[rank + (li0 + r2) * C] = ploc[r2];
+            }
+            if (warp == TC_THREADS / 32 - 1) {
+                double s = 0.0;
+                if (lane < nr) s = ploc[lane] * vl[rank + (li0 + lane) * C];
+                s = warp_sum(s);
+                if (lane < C) cl.map_shared_rank(pvp, lane)[rank] = s;
+            }
+        }
+        cl.sync();
+        // ---- C: w = p - (tau/2)(p^T v) v, then the rank-2 update of the owned rows
+        if (t_j != 0.0) {
+            if (warp == 0) {
+                const double t2 = warp_sum(lane < C ? pvp[lane] : 0.0);
+                if (lane == 0) sc[2] = 0.5 * t_j * t2;
+            }
+            __syncthreads();
+            const double Kc = sc[2];
+            for (int c = c0 + tid; c < k; c += TC_THREADS) wl[c] = pg[c] - Kc * vl[c];
+            __syncthreads();
+            // a warp per owned row, lanes along the columns; the operands are put in (lo, hi)
+            // order by selects
+            for (int r = warp; r < nr; r += TC_THREADS / 32) {
+                const int li = li0 + r, i = rank + li * C;
+                const double vi = vl[i], wi = wl[i];
+                double* row = Srow + li * k;
+                for (int c = c0 + lane; c < k; c += 32) {
+                    const double vc = vl[c], wc = wl[c];
+                    const bool up = c >= i;
+                    const double x1 = up ? vi : vc, y1 = up ? wc : wi;
+                    const double x2 = up ? wi : wc, y2 = up ? vc : vi;
+                    row[c] = fma(-x1, y1, fma(-x2, y2, row[c]));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (k >= 2) {
+            if ((k - 2) % C == rank) d[k - 2] = Srow[((k - 2) / C) * k + (k - 2)];
+            if ((k - 1) % C == rank) {
+                d[k - 1] = Srow[((k - 1) / C) * k + (k - 1)];
+                e[k - 2] = Srow[((k - 1) / C) * k + (k - 2)];
+            }
+            if (rank == 0) tau[k - 2] = 0.0;
+        } else if (k == 1 && rank == 0) {
+            d[0] = Srow[0];
+        }
+    }
+    cl.sync();                     // no block leaves while a peer could still address its memory
+}
+
+// ------------------------------------------------------------------ pivoted Cholesky
+// Pivoted Cholesky P^T G P = Lt Lt^T of the k x k Gram G (left-looking, diagonal pivoting; rank
+// revealing for a PSD Gram Y^T Y).  Stops at the first pivot <= tol max(diag G), or <= 0, or <=
+// the absolute floor floor_rel d0_ref (the numerical rank m); without pivoting a stop raises
+// `fail`.  Output: Lt directly, slot u holding the row chosen at step u (Lt(u, s) at
+// L[s ldl + u]); perm[u] the original index of slot u for every slot (rows never chosen take the
+// slots m.. in increasing index); dm_out = m, kx_out = k; d0_out = max(diag G) if given.
+// A near-identity Gram G = I + E (the last CholeskyQR pass, whose input is orthonormal to
+// rounding) with ||E||_F^2 <= 1e-16 takes the factor I + F, F = strict_lower(E) + diag(E)/2:
+// (I + F)(I + F)^T = G + F F^T and ||F F^T||_F <= ||E||_F^2, far below the factorisation's own
+// rounding (~k u); no pivot is needed (every diagonal is 1 +- 1e-8).
+// The rows are spread over the cluster and never swapped: block `rank` keeps, for its rows
+// i = rank + li C, row i of G (ld k), the computed L(i, 0..s) (ld k) and the Schur diagonal.
+// Step t:
+//   every block sends its best active row (diagonal bits as the key, ties to the smaller
+//   index) to every block; cluster barrier; every block picks the same pivot q from the C
+//   candidates in rank order; the owner of q sets L(q, t) = sqrt(d_q); every block copies the
+//   finished L(q, 0..t-1) from the owner's shared memory and computes
+//   L(i, t) = (G(i, q) - sum_s L(i, s) L(q, s)) / L(q, t) and d_i -= L(i, t)^2 for its active rows.
+// One cluster barrier a step: candidates go to buffers of the step's parity (a block can be
+// at most one step ahead of the slowest reader), and the pivot row read from the owner is
+// final (a chosen row is never written again).
+template <int C>
+__global__ void __launch_bounds__(TC_THREADS) k_chol_cluster(ModeMap mm, const double* G, long long gstride, int ldg,
+                                                             const int* dk, int* kx_out, double* L, long long lstride,
+                                                             int ldl, int* perm, int pstride, int* dm_out, int* fail,
+                                                             int pivot, double tol, double* d0_out,
+                                                             const double* d0_ref, double floor_rel, double* W,
+                                                             long long wstride, int ldw, int* near_out)
+{
+    constexpr int ROWS = (KMAX + C - 1) / C;
+    constexpr int RP2 = ROWS <= 8 ? 8 : (ROWS <= 16 ? 16 : 32);
+    constexpr int NCH = TC_THREADS / RP2;                 // chunks of the dot products per row
+    static_assert(ROWS <= 32 && NCH >= 1 && NCH <= 32 && (NCH & (NCH - 1)) == 0, "row split");
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int b = mm.m[blockIdx.y];
+    const int k = dk[b];
+    G += b * gstride;
+    L += b * lstride;
+    W += b * wstride;
+    perm += b * pstride;
+    extern __shared__ double dyn[];
+    double* Grow = dyn;                                    // ROWS x k
+    double* Lrow = dyn + (size_t)ROWS * k;                 // ROWS x k
+    __shared__ double lq[KMAX];
+    __shared__ double dsh[32];
+    __shared__ int act[32], pos[32], slot[32];
+    __shared__ long long ckey[2][C];
+    __shared__ int cidx[2][C];
+    __shared__ double cdp[2][C], cnear[C];
+    __shared__ int pivs[KMAX];
+    __shared__ unsigned char chosen[KMAX];
+    __shared__ double red[TC_THREADS / 32];
+    __shared__ double s_rp, s_piv;
+    __shared__ int s_q, s_stop, s_nact;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nloc = rank < k ? (k - rank + C - 1) / C : 0;
+    // row i of G = column i (G is symmetric)
+    for (int li = warp; li < nloc; li += TC_THREADS / 32) {
+        const int i = rank + li * C;
+        for (int c = lane; c < k; c += 32) Grow[li * k + c] = G[(long long)i * ldg + c];
+    }
+    if (tid < 32) {
+        act[tid] = tid;
+        pos[tid] = tid;
+        slot[tid] = -1;
+    }
+    for (int i = tid; i < k; i += TC_THREADS) chosen[i] = 0;
+    if (tid == 0) s_nact = nloc;
+    __syncthreads();
+    if (tid < nloc) dsh[tid] = Grow[tid * k + rank + tid * C];
+    // largest diagonal of G (every block reads all of it: k values)
+    double dmx = 0.0;
+    for (int i = tid; i < k; i += TC_THREADS) dmx = fmax(dmx, G[(long long)i * ldg + i]);
+    dmx = warp_max(dmx);
+    if (lane == 0) red[warp] = dmx;
+    __syncthreads();
+    double d0max = 0.0;
+    for (int w = 0; w < TC_THREADS / 32; ++w) d0max = fmax(d0max, red[w]);
+    if (d0_out && rank == 0 && tid == 0) d0_out[b] = d0max;
+    const double dfloor = d0_ref ? floor_rel * d0_ref[b] : 0.0;
+    // near-identity shortcut: ||G - I||_F^2 from the owned rows, summed over the blocks in
+    // rank order
+    const bool try_near = dfloor < 0.5 && tol * d0max < 0.5;
+    if (try_near) {
+        double s = 0.0;
+        for (int li = warp; li < nloc; li += TC_THREADS / 32) {
+            const int i = rank + li * C;
+            for (int c = lane; c < k; c += 32) {
+                const double g = Grow[li * k + c];
+                const double ev = (c == i) ? g - 1.0 : g;
+                s = fma(ev, ev, s);
+            }
+        }
+        s = warp_sum(s);
+        __syncthreads();
+        if (lane == 0) red[warp] = s;
+        __syncthreads();
+        if (tid < C) {
+            double t = 0.0;
+            for (int w = 0; w < TC_THREADS / 32; ++w) t += red[w];
+            cl.map_shared_rank(cnear, tid)[rank] = t;
+        }
+    }
+    cl.sync();                     // all blocks loaded (and near-identity parts exchanged)
+    if (try_near) {
+        double s = 0.0;
+        for (int r = 0; r < C; ++r) s += cnear[r];
+        if (s <= 1e-16) {
+            // the inverse directly, in the layout of the triangular inverse (W(perm[j], t) =
+            // Lt^{-1}(t, j), perm = identity): Lt^{-1} = I - F to first order (error ||F||^2),
+            // so W(j, t) = -G(t, j) for t > j, 1 - (G(j, j) - 1)/2 on the diagonal, 0 below.
+            // W may share G's buffer: every block read its rows before the barrier above.
+            for (int li = warp; li < nloc; li += TC_THREADS / 32) {
+                const int j = rank + li * C;
+                for (int t = lane; t < k; t += 32) {
+                    const double g = Grow[li * k + t];
+                    W[(long long)t * ldw + j] = t < j ? 0.0 : (t == j ? fma(-0.5, g - 1.0, 1.0) : -g);
+                }
+            }
+            if (rank == 0) {
+                for (int t = tid; t < k; t += TC_THREADS) perm[t] = t;
+                if (tid == 0) {
+                    dm_out[b] = k;
+                    kx_out[b] = k;
+                    if (near_out) near_out[b] = 1;
+                }
+            }
+            cl.sync();
+            return;
+        }
+    }
+    int m = k;
+    for (int t = 0; t < k; ++t) {
+        const int par = t & 1;
+        // ---- this block's candidate
+        if (warp == 0) {
+            const int na = s_nact;
+            long long key = LLONG_MIN;
+            int idx = INT_MAX;
+            double dv = 0.0;
+            if (lane < na) {
+                const int li = act[lane];
+                dv = dsh[li];
+                const long long bits = __double_as_longlong(dv);
+                key = pivot ? (bits >= 0 ? bits : -1) : -1;
+                idx = rank + li * C;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+                const double d2 = __shfl_xor_sync(0xffffffffu, dv, o);
+                if (k2 > key || (k2 == key && i2 < idx)) {
+                    key = k2;
+                    idx = i2;
+                    dv = d2;
+                }
+            }
+            if (lane < C) {
+                cl.map_shared_rank(&ckey[par][0], lane)[rank] = key;
+                cl.map_shared_rank(&cidx[par][0], lane)[rank] = idx;
+                cl.map_shared_rank(&cdp[par][0], lane)[rank] = dv;
+            }
+        }
+        cl.sync();
+        // ---- the pivot: without pivoting the row of index t, else the best of the C candidates
+        // (a shuffle tree in warp 0: the same maximum, ties to the smaller index, as any order)
+        if (warp == 0) {
+            int q = t;
+            double dp = 0.0;
+            if (pivot) {
+                long long kr = LLONG_MIN;
+                int ir = INT_MAX;
+                double dr = 0.0;
+                if (lane < C) {
+                    kr = ckey[par][lane];
+                    ir = cidx[par][lane];
+                    dr = cdp[par][lane];
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const long long k2 = __shfl_xor_sync(0xffffffffu, kr, o);
+                    const int i2 = __shfl_xor_sync(0xffffffffu, ir, o);
+                    const double d2 = __shfl_xor_sync(0xffffffffu, dr, o);
+                    if (k2 > kr || (k2 == kr && i2 < ir)) {
+                        kr = k2;
+                        ir = i2;
+                        dr = d2;
+                    }
+                }
+                q = ir;
+                dp = dr;
+            } else {
+                // every key is -1: the smallest active index is t (rows are taken in order)
+                dp = cdp[par][t % C];
+            }
+            if (lane == 0) {
+                const bool stop = q >= k || !(dp > tol * d0max) || !(dp > 0.0) || !(dp > dfloor);
+                s_stop = stop;
+                s_q = q;
+                if (!stop) {
+                    const double rp = rsqrt(dp);           // one dependent chain instead of sqrt, then 1 / x
+                    const double piv = dp * rp;
+                    s_piv = piv;
+                    s_rp = rp;
+                    pivs[t] = q;
+                    chosen[q] = 1;
+                    if (q % C == rank) {               // the owner: L(q, t), and q leaves the active set
+                        const int lq_ = q / C;
+                        Lrow[lq_ * k + t] = piv;
+                        slot[lq_] = t;
+                        const int p0 = pos[lq_], last = act[s_nact - 1];
+                        act[p0] = last;
+                        pos[last] = p0;
+                        s_nact = s_nact - 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (s_stop) {
+            if (!pivot && tid == 0 && fail && rank == 0) fail[b] = 1;
+            m = t;
+            break;
+        }
+        const int q = s_q;
+        {
+            const double* src = cl.map_shared_rank(Lrow, q % C) + (size_t)(q / C) * k;
+            for (int s2 = tid; s2 < t; s2 += TC_THREADS) lq[s2] = src[s2];
+        }
+        __syncthreads();
+        // ---- column t for the active rows
+        const int na = s_nact;
+        const double rp = s_rp;
+        {
+            const int r = tid / NCH, ch = tid - r * NCH;
+            double acc = 0.0, acc2 = 0.0;
+            int li = 0;
+            if (r < na) {
+                li = act[r];
+                const double* row = Lrow + li * k;
+                int s2 = ch;
+                for (; s2 + NCH < t; s2 += 2 * NCH) {
+                    acc = fma(row[s2], lq[s2], acc);
+                    acc2 = fma(row[s2 + NCH], lq[s2 + NCH], acc2);
+                }
+                if (s2 < t) acc = fma(row[s2], lq[s2], acc);
+            }
+            acc += acc2;
+            for (int o = NCH / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (ch == 0 && r < na) {
+                const double lit = (Grow[li * k + q] - acc) * rp;
+                Lrow[li * k + t] = lit;
+                dsh[li] -= lit * lit;
+            }
+        }
+        __syncthreads();
+    }
+    // ---- outputs: the chosen rows of Lt in slot order, the permutation, the counts
+    for (int li = warp; li < nloc; li += TC_THREADS / 32) {
+        const int u = slot[li];
+        if (u < 0 || u >= m) continue;
+        for (int s2 = lane; s2 <= u; s2 += 32) L[(long long)s2 * ldl + u] = Lrow[li * k + s2];
+    }
+    if (rank == 0) {
+        for (int u = tid; u < m; u += TC_THREADS) perm[u] = pivs[u];
+        __syncthreads();
+        if (tid == 0) {
+            int u = m;
+            for (int i = 0; i < k; ++i)
+                if (!chosen[i]) perm[u++] = i;
+            dm_out[b] = m;
+            kx_out[b] = k;
+            if (near_out) near_out[b] = 0;
+        }
+    }
+    cl.sync();                     // no block leaves while a peer could still read its memory
+}
+
+template <int C>
+static int launch_tridiag_c(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e,
+                            double* tau, int vstride, int nb, int kbound, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        const int smax = (int)(sizeof(double) * ((KMAX + C - 1) / C) * KMAX);
+        if (cudaFuncSetAttribute(k_tridiag_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax) != cudaSuccess)
+            return RHOSVD_ERR_CUDA;
+        if (C > 8 && cudaFuncSetAttribute(k_tridiag_cluster<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                         cudaSuccess)
+            return RHOSVD_ERR_CUDA;
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, nb, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = sizeof(double) * (size_t)((kbound + C - 1) / C) * (size_t)kbound;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_tridiag_cluster<C>, mm, A, astride, lda, dk, d, e, tau, vstride) != cudaSuccess)
+        return RHOSVD_ERR_CUDA;
+    count_launch();
+    return 0;
+}
+
+template <int C>
+static int launch_chol_c(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int* kx_out, double* L,
+                         long long lstride, int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot,
+                         double tol, int nb, int kbound, double* d0_out, const double* d0_ref, double floor_rel,
+                         double* W, long long wstride, int ldw, int* near_out, cudaStream_t st)
+{
+    constexpr int ROWS = (KMAX + C - 1) / C;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_chol_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(double) * 2 * ROWS * KMAX)) != cudaSuccess)
+            return RHOSVD_ERR_CUDA;
+        if (C > 8 &&
+            cudaFuncSetAttribute(k_chol_cluster<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+            return RHOSVD_ERR_CUDA;
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, nb, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = sizeof(double) * 2 * (size_t)ROWS * (size_t)kbound;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_chol_cluster<C>, mm, G, gstride, ldg, dk, kx_out, L, lstride, ldl, perm, pstride,
+                           dm_out, fail, pivot, tol, d0_out, d0_ref, floor_rel, W, wstride, ldw, near_out) != cudaSuccess)
+        return RHOSVD_ERR_CUDA;
+    count_launch();
+    return 0;
+}
+
+// Cluster width for a kernel: 16 if a 16-block cluster of its blocks (smem16 bytes of dynamic
+// shared memory each) can be resident, else 8 (portable).  Decided once per kernel.
+template <typename Kern>
+static int query_width(Kern kern, size_t smem16, int& width)
+{
+    if (width == 0) {
+        width = 8;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem16) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(16, 1, 1);
+            cfg.blockDim = dim3(TC_THREADS, 1, 1);
+            cfg.dynamicSmemBytes = smem16;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 16;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) width = 16;
+        }
+        cudaGetLastError();        // a refused query leaves no sticky error behind
+    }
+    return width;
+}
+
+int launch_tridiag_cluster(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e,
+                           double* tau, int vstride, int nb, int kbound, cudaStream_t st)
+{
+    if (kbound > KMAX) return RHOSVD_ERR_INVALID_ARG;
+    static int width = 0;
+    if (query_width(k_tridiag_cluster<16>, sizeof(double) * ((KMAX + 15) / 16) * KMAX, width) == 16)
+        return launch_tridiag_c<16>(mm, A, astride, lda, dk, d, e, tau, vstride, nb, kbound, st);
+    return launch_tridiag_c<8>(mm, A, astride, lda, dk, d, e, tau, vstride, nb, kbound, st);
+}
+
+}  // namespace rh
+
+namespace rh {
+
+int launch_chol_cluster(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int* kx_out, double* L,
+                        long long lstride, int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot,
+                        double tol, int nb, int kbound, double* d0_out, const double* d0_ref, double floor_rel,
+                        double* W, long long wstride, int ldw, int* near_out, cudaStream_t st)
+{
+    if (kbound > KMAX) return RHOSVD_ERR_INVALID_ARG;
+    static int width = 0;
+    if (query_width(k_chol_cluster<16>, sizeof(double) * 2 * ((KMAX + 15) / 16) * KMAX, width) == 16)
+        return launch_chol_c<16>(mm, G, gstride, ldg, dk, kx_out, L, lstride, ldl, perm, pstride, dm_out, fail, pivot,
+                                 tol, nb, kbound, d0_out, d0_ref, floor_rel, W, wstride, ldw, near_out, st);
+    return launch_chol_c<8>(mm, G, gstride, ldg, dk, kx_out, L, lstride, ldl, perm, pstride, dm_out, fail, pivot, tol,
+                            nb, kbound, d0_out, d0_ref, floor_rel, W, wstride, ldw, near_out, st);
+}
+
+}  // namespace rh

@@ -21,6 +21,8 @@ struct DevState {
     int kdef[3];        // width of the deflation sketch (second range sketch)
     int mdef[3];        // deflation directions kept
     int kxdef[3];       // columns of the deflation CholeskyQR input
+    int near[3];        // the last Cholesky of the basis took the near-identity path (W written)
+    int neardef[3];     // the same for the deflation basis
     double gmax[3];     // largest diagonal of the first sketch's Gram (scale of the sketch)
     double shift[3];    // shift used for the LDL^T representation of the tridiagonal
     double trace[3];    // trace(B B^T) = ||B||_F^2
@@ -58,29 +60,40 @@ __device__ inline double warp_max(double v)
     return v;
 }
 
-// Block-wide sum; `red` must hold blockDim.x/32 doubles.  All threads get the result.
+// Block-wide sum; `red` must hold blockDim.x/32 doubles.  All threads get the result.  Warp 0
+// adds the warp partials by a shuffle tree and broadcasts through shared memory: FP64 adds are
+// slow on this part, and every thread adding all partials itself cost more than the data pass
+// in a large block.
 __device__ inline double block_sum(double v, double* red)
 {
+    __shared__ double bcast;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     v = warp_sum(v);
     __syncthreads();
     if (lane == 0) red[wid] = v;
     __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += red[w];
-    return t;
+    if (wid == 0) {
+        const double t = warp_sum(lane < nw ? red[lane] : 0.0);
+        if (lane == 0) bcast = t;
+    }
+    __syncthreads();
+    return bcast;
 }
 
 __device__ inline double block_max(double v, double* red)
 {
+    __shared__ double bcast;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     v = warp_max(v);
     __syncthreads();
     if (lane == 0) red[wid] = v;
     __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t = fmax(t, red[w]);
-    return t;
+    if (wid == 0) {
+        const double t = warp_max(lane < nw ? red[lane] : 0.0);
+        if (lane == 0) bcast = t;
+    }
+    __syncthreads();
+    return bcast;
 }
 
 // Record the first device-side error in the info record.
@@ -259,9 +272,12 @@ int launch_transpose_v(const double* src, long long sstride, int lds, float2* ds
 int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, int kdef, cudaStream_t st);
 int launch_hadamard(const HadArgs& a, cudaStream_t st);
 int launch_cpsum(const SumArgs& a, cudaStream_t st);
+// With a near-identity Gram the factor's inverse is written to W directly (the layout of
+// launch_trinv) and near_out[b] = 1, which launch_trinv then skips; else near_out[b] = 0.
 int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int* kx_out, double* L,
                 long long lstride, int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot, double tol, int nb,
-                int kbound, double* d0_out, const double* d0_ref, double floor_rel, cudaStream_t st);
+                int kbound, double* d0_out, const double* d0_ref, double floor_rel, double* W, long long wstride,
+                int ldw, int* near_out, cudaStream_t st);
 // Deflation of the second range sketch against the basis Q (n x m, ld n per mode):
 // T = Q^T Y, then Y -= Q T (k2 columns of Y, ld n).
 int launch_deflate(ModeMap mm, const double* Q, double* Y, long long nk, const int n[3], const int* dm, int k2,
@@ -270,11 +286,20 @@ int launch_deflate(ModeMap mm, const double* Q, double* Y, long long nk, const i
 int launch_append(ModeMap mm, double* Q, const double* Q2, long long nk, const int n[3], int* dm, const int* dm2,
                   int nb, int nmax, int k2, cudaStream_t st);
 int launch_trinv(ModeMap mm, const double* L, long long lstride, int ldl, const int* perm, int pstride,
-                 const int* dkx, const int* dm, double* W, long long wstride, int ldw, int nb, cudaStream_t st);
+                 const int* dkx, const int* dm, double* W, long long wstride, int ldw, const int* near, int nb,
+                 cudaStream_t st);
 int launch_trace(ModeMap mm, const double* A, long long astride, int lda, const int* dk, double* trace, int nb,
                  cudaStream_t st);
 int launch_tridiag(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e, double* tau,
                    int vstride, int nb, int kbound, cudaStream_t st);
+// The pivoted Cholesky and the tridiagonal reduction on a thread-block cluster per mode
+// (cluster.cu); kbound <= KMAX.
+int launch_chol_cluster(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int* kx_out, double* L,
+                        long long lstride, int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot,
+                        double tol, int nb, int kbound, double* d0_out, const double* d0_ref, double floor_rel,
+                        double* W, long long wstride, int ldw, int* near_out, cudaStream_t st);
+int launch_tridiag_cluster(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e,
+                           double* tau, int vstride, int nb, int kbound, cudaStream_t st);
 int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D, double* Lo,
                    double* mu, DevState* s, int nb, cudaStream_t st);
 int launch_rank(const RankArgs& a, cudaStream_t st);

@@ -361,50 +361,148 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
 }
 
 // ---------------------------------------------------------------- digit-plane slicer
-// One warp per operand row: optional exponent pass, then S planes written along k.
-__global__ void k_oz_slice(OzSliceArgs a)
+// Two kernels.  k_oz_rowexp: the per-row exponent E_i = e(max_k |x_ik|) (|x| < 2^E, the frexp
+// exponent, clamped to [-126, 127]; -126 for an all-zero row) from the integer exponent fields,
+// reading along whichever operand dimension is contiguous.  k_oz_slice_tile: 32 rows x 64 k per
+// block, staged in shared memory so that both the loads (either layout) and the plane stores
+// (k contiguous) are coalesced.
+
+// frexp exponent of x from its bits (x = f 2^e, 0.5 <= |f| < 1); -4096 for zero; subnormals read
+// as -1022 (they clamp to -126 anyway)
+__device__ __forceinline__ int oz_frexp_exp(double x)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    if ((bits << 1) == 0) return -4096;
+    return ef == 0 ? -1022 : ef - 1022;
+}
+
+constexpr int OZ_RE_ROWS = 8;       // rows a block of k_oz_rowexp (rows-contiguous layout)
+
+__global__ void k_oz_rowexp(OzSliceArgs a)
 {
     const int b = blockIdx.y;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int rows = a.drows[b] ? *a.drows[b] : a.rows[b];
-    if (warp >= a.rows[b]) return;
+    const int rows = a.rows[b];
+    const int live = a.drows[b] ? *a.drows[b] : rows;
     const int K = a.dK[b] ? *a.dK[b] : a.K[b];
-    const int ld = a.ld[b];
-    uint16_t* P = a.planes[b];
-    const long long ps = a.pstride[b];
     const double* X = a.X[b];
     const double* ks = a.kscale[b];
-    const bool live = warp < rows;
-    int E = a.exp0;
-    if (a.exps[b]) {
-        double mx = 0.0;
-        if (live)
-            for (int k = lane; k < K; k += 32) {
-                double x = X[(long long)warp * a.rs[b] + (long long)k * a.cs[b]];
-                if (ks) x *= ks[k];
-                mx = fmax(mx, fabs(x));
+    const long long rs = a.rs[b], cs = a.cs[b];
+    const int tid = threadIdx.x;
+    __shared__ int emax[32];
+    const int r0 = blockIdx.x * OZ_RE_ROWS;
+    if (r0 >= rows) return;
+    if (tid < 32) emax[tid] = -4096;
+    __syncthreads();
+    if (rs == 1) {
+        // rows contiguous: a warp reads 8 rows x 4 k (four 64-byte segments)
+        const int i = r0 + (tid & (OZ_RE_ROWS - 1)), kk = tid / OZ_RE_ROWS;
+        int e = -4096;
+        constexpr int STEP = 256 / OZ_RE_ROWS;
+        if (i < live) {
+            // eight independent loads in flight per thread
+            int k = kk;
+            for (; k + 7 * STEP < K; k += 8 * STEP) {
+                double x[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) x[q] = X[(long long)i + (long long)(k + q * STEP) * cs];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) e = max(e, oz_frexp_exp(ks ? x[q] * ks[k + q * STEP] : x[q]));
             }
-        mx = warp_max(mx);
-        if (mx > 0.0) {
-            int ex;
-            frexp(mx, &ex);          // mx < 2^ex
-            E = ex;
-        } else {
-            E = -126;
+            for (; k < K; k += STEP) {
+                double x = X[(long long)i + (long long)k * cs];
+                if (ks) x *= ks[k];
+                e = max(e, oz_frexp_exp(x));
+            }
         }
-        if (E < -126) E = -126;
-        if (E > 127) E = 127;
-        if (lane == 0) a.exps[b][warp] = (signed char)E;
+        atomicMax(&emax[tid & (OZ_RE_ROWS - 1)], e);
+    } else {
+        // k contiguous (or strided both ways): a warp per row, lanes along k
+        const int lane = tid & 31, w = tid >> 5;
+        const int i = r0 + w;
+        int e = -4096;
+        if (w < OZ_RE_ROWS && i < live) {
+            int k = lane;
+            for (; k + 7 * 32 < K; k += 8 * 32) {
+                double x[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) x[q] = X[(long long)i * rs + (long long)(k + q * 32) * cs];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) e = max(e, oz_frexp_exp(ks ? x[q] * ks[k + q * 32] : x[q]));
+            }
+            for (; k < K; k += 32) {
+                double x = X[(long long)i * rs + (long long)k * cs];
+                if (ks) x *= ks[k];
+                e = max(e, oz_frexp_exp(x));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        if (lane == 0 && w < OZ_RE_ROWS) emax[w] = e;
     }
-    for (int k = lane; k < ld; k += 32) {
-        double x = 0.0;
-        if (live && k < K) {
-            x = X[(long long)warp * a.rs[b] + (long long)k * a.cs[b]];
-            if (ks) x *= ks[k];
+    __syncthreads();
+    if (tid < OZ_RE_ROWS && r0 + tid < rows) {
+        int E = emax[tid];
+        if (E == -4096) E = -126;
+        E = min(127, max(-126, E));
+        a.exps[b][r0 + tid] = (signed char)E;
+    }
+}
+
+constexpr int OZ_ST_R = 32, OZ_ST_K = 64;
+
+// S as a template argument: the digit loops unroll and the digits stay in registers.
+template <int S>
+__global__ void __launch_bounds__(256) k_oz_slice_tile(OzSliceArgs a)
+{
+    const int b = blockIdx.z;
+    const int rows = a.rows[b];
+    const int ld = a.ld[b];
+    const int i0 = blockIdx.y * OZ_ST_R, k0 = blockIdx.x * OZ_ST_K;
+    if (i0 >= rows || k0 >= ld) return;
+    const int live = a.drows[b] ? *a.drows[b] : rows;
+    const int K = a.dK[b] ? *a.dK[b] : a.K[b];
+    const double* X = a.X[b];
+    const double* ks = a.kscale[b];
+    const long long rs = a.rs[b], cs = a.cs[b];
+    __shared__ double T[OZ_ST_R][OZ_ST_K + 1];
+    const int tid = threadIdx.x;
+    if (rs == 1) {
+        const int r = tid & 31;
+        for (int kk = tid >> 5; kk < OZ_ST_K; kk += 8) {
+            const int i = i0 + r, k = k0 + kk;
+            double x = 0.0;
+            if (i < live && k < K) {
+                x = X[(long long)i + (long long)k * cs];
+                if (ks) x *= ks[k];
+            }
+            T[r][kk] = x;
         }
-        uint16_t d[8];
-        oz_digits(x, E, a.S, d);
-        for (int s = 0; s < a.S; ++s) P[s * ps + (long long)warp * ld + k] = d[s];
+    } else {
+        const int kk = tid & (OZ_ST_K - 1);
+        for (int r = tid / OZ_ST_K; r < OZ_ST_R; r += 256 / OZ_ST_K) {
+            const int i = i0 + r, k = k0 + kk;
+            double x = 0.0;
+            if (i < live && k < K) {
+                x = X[(long long)i * rs + (long long)k * cs];
+                if (ks) x *= ks[k];
+            }
+            T[r][kk] = x;
+        }
+    }
+    __syncthreads();
+    uint16_t* P = a.planes[b];
+    const long long ps = a.pstride[b];
+    const int kk = tid & (OZ_ST_K - 1), k = k0 + kk;
+    if (k >= ld) return;
+    for (int r = tid / OZ_ST_K; r < OZ_ST_R; r += 256 / OZ_ST_K) {
+        const int i = i0 + r;
+        if (i >= rows) break;
+        const int E = a.exps[b] ? (int)a.exps[b][i] : a.exp0;
+        uint16_t d[S];
+        oz_digits(T[r][kk], E, S, d);
+        uint16_t* q = P + (long long)i * ld + k;
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) q[s2 * ps] = d[s2];
     }
 }
 
@@ -438,11 +536,28 @@ int oz_choose_split(int M, int N, int K, int nt, int nbatch)
 
 int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st)
 {
-    int rmax = 0;
-    for (int b = 0; b < nb; ++b) rmax = max(rmax, a.rows[b]);
-    if (rmax <= 0) return 0;
-    dim3 grid((rmax + 7) / 8, nb);
-    k_oz_slice<<<grid, 256, 0, st>>>(a);
+    int rmax = 0, ldmax = 0;
+    bool exps = false;
+    for (int b = 0; b < nb; ++b) {
+        rmax = max(rmax, a.rows[b]);
+        ldmax = max(ldmax, a.ld[b]);
+        exps = exps || a.exps[b] != nullptr;
+    }
+    if (rmax <= 0 || ldmax <= 0) return 0;
+    if (exps) {
+        // every problem of one call either has exponents or not (the slicers are per operand)
+        for (int b = 0; b < nb; ++b)
+            if (!a.exps[b]) return RHOSVD_ERR_INVALID_ARG;
+        k_oz_rowexp<<<dim3((rmax + OZ_RE_ROWS - 1) / OZ_RE_ROWS, nb), 256, 0, st>>>(a);
+        RH_CHECK_LAUNCH();
+    }
+    dim3 grid((ldmax + OZ_ST_K - 1) / OZ_ST_K, (rmax + OZ_ST_R - 1) / OZ_ST_R, nb);
+    switch (a.S) {
+    case 6: k_oz_slice_tile<6><<<grid, 256, 0, st>>>(a); break;
+    case 4: k_oz_slice_tile<4><<<grid, 256, 0, st>>>(a); break;
+    case 1: k_oz_slice_tile<1><<<grid, 256, 0, st>>>(a); break;
+    default: return RHOSVD_ERR_INVALID_ARG;
+    }
     RH_CHECK_LAUNCH();
     return 0;
 }

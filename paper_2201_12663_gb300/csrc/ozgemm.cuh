@@ -87,17 +87,19 @@ enum OzASrc { OZ_A_PLANES = 0, OZ_A_KR = 1 };
 enum OzBSrc { OZ_B_PLANES = 0, OZ_B_SIGN = 1 };
 enum OzEpi { OZ_EPI_STORE = 0, OZ_EPI_RESID = 1 };
 
-// S digit planes (bf16 bit patterns) of the signed integer F = +-round(|x| 2^(8S - E))
+// S digit planes (bf16 bit patterns) of the signed integer F = +-round(|x| 2^(8S - E)).
+// Digit s (s = 1..S) is d 2^(-8(s-1)) with d < 2^8 (s > 1) or d <= 2^8 (s = 1): at most eight
+// significant bits and a power-of-two scale, so the float d * 2^(-8(s-1)) is exact and its bf16
+// pattern is the float's upper half (no rounding); the sign is the top bit.
 __device__ __forceinline__ void oz_digits_int(long long F, int S, uint16_t* out)
 {
     const bool neg = F < 0;
     const unsigned long long A = (unsigned long long)(neg ? -F : F);
+    const unsigned sgn = neg ? 0x8000u : 0u;
     for (int s = 1; s <= S; ++s) {
         const int d = (int)((A >> (8 * (S - s))) & (s == 1 ? 0x1FFull : 0xFFull));
-        float v = ldexpf((float)d, -8 * (s - 1));
-        if (neg) v = -v;
-        const __nv_bfloat16 b = __float2bfloat16_rn(v);
-        out[s - 1] = *reinterpret_cast<const uint16_t*>(&b);
+        const float v = (float)d * __int_as_float((127 - 8 * (s - 1)) << 23);
+        out[s - 1] = d ? (uint16_t)((__float_as_uint(v) >> 16) | sgn) : (uint16_t)0;
     }
 }
 

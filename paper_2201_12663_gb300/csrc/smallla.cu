@@ -1,9 +1,7 @@
-// smallla.cu -- small dense FP64 linear algebra on k x k (k <= RHOSVD_K_MAX) matrices,
-// one thread block per mode:
-//   * left-looking Cholesky with optional diagonal pivoting and a relative stopping
-//     tolerance (rank revealing for the PSD Gram Y^T Y) and the row-wise triangular solve
-//     that turns Y into an orthonormal basis (CholeskyQR with pivoting, three passes);
-//   * Householder reduction of the symmetric M = B B^T to tridiagonal form;
+// smallla.cu -- small dense FP64 linear algebra on k x k (k <= RHOSVD_K_MAX) matrices:
+//   * the triangular inverse that turns Y into an orthonormal basis (CholeskyQR with
+//     pivoting, three passes; the pivoted Cholesky itself and the Householder reduction of
+//     M = B B^T to tridiagonal form run on a thread-block cluster per mode, cluster.cu);
 //   * eigenvalues of the tridiagonal from an LDL^T representation of T + s I by bisection
 //     on the differential stationary qd negative count (relative accuracy for the graded,
 //     positive spectra a Gram of a normalised side matrix has);
@@ -18,298 +16,17 @@
 
 namespace rh {
 
-// ------------------------------------------------------------------ pivoted Cholesky
-// Pivoted Cholesky P^T G P = Lt Lt^T (left-looking, one block per mode).  Rows are kept in
-// pivot order: slot t holds the row chosen at step t, the active rows sit packed in slots
-// (t, k), and choosing a pivot swaps it into slot t (its computed part of Lt moves with it).
-// So Lt is stored directly (Lt(i, s) at L[s * ldl + i]), each step's active rows fill whole
-// warps, and perm[t] is the original index of slot t -- for every slot, also those left
-// after a rank stop (their rows are not factorised).  Stops at the first pivot <= tol *
-// max(diag G) (the numerical rank m); without pivoting that raises `fail`.  kx_out[b] = k.
-__global__ void k_chol_piv(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int hk,
-                           int* kx_out, double* L, long long lstride, int ldl, int* perm, int pstride,
-                           int* dm_out, int* fail, int pivot, double tol, double* d0_out, const double* d0_ref,
-                           double floor_rel)
-{
-    const int b = mm.m[blockIdx.x];
-    const int k = dk ? dk[b] : hk;
-    G += b * gstride;
-    L += b * lstride;
-    perm += b * pstride;
-    __shared__ double dsh[KMAX];
-    __shared__ int orig[KMAX];
-    __shared__ double red[32];
-    __shared__ int redi[32];
-    __shared__ int s_q;
-    __shared__ double s_piv;
-    const int i = threadIdx.x;
-    if (i < k) { dsh[i] = G[(long long)i * ldg + i]; orig[i] = i; }
-    __syncthreads();
-    const double d0max = block_max((i < k) ? dsh[i] : 0.0, red);
-    if (d0_out && i == 0) d0_out[b] = d0max;
-    const double dfloor = d0_ref ? floor_rel * d0_ref[b] : 0.0;
-    int m = k;
-    for (int t = 0; t < k; ++t) {
-        // pivot: first slot of the largest remaining diagonal
-        if (pivot) {
-            double v = (i >= t && i < k) ? dsh[i] : -DBL_MAX;   // below any active diagonal
-            int idx = i;
-            for (int o = 16; o > 0; o >>= 1) {
-                const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-                const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-                if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
-            }
-            __syncthreads();
-            if ((i & 31) == 0) { red[i >> 5] = v; redi[i >> 5] = idx; }
-            __syncthreads();
-            if (i == 0) {
-                double bv = -DBL_MAX;
-                int bi = t;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-                    if (red[w] > bv || (red[w] == bv && redi[w] < bi)) { bv = red[w]; bi = redi[w]; }
-                s_q = bi;
-                s_piv = bv;
-            }
-        } else if (i == 0) {
-            s_q = t;
-            s_piv = dsh[t];
-        }
-        __syncthreads();
-        const int q = s_q;
-        const double dp = s_piv;
-        if (!(dp > tol * d0max) || !(dp > 0.0) || !(dp > dfloor)) {
-            if (!pivot && i == 0 && fail) fail[b] = 1;
-            m = t;
-            break;
-        }
-        if (q != t) {           // move the pivot row into slot t
-            for (int c = i; c < t; c += blockDim.x) {
-                const double x = L[(long long)c * ldl + t];
-                L[(long long)c * ldl + t] = L[(long long)c * ldl + q];
-                L[(long long)c * ldl + q] = x;
-            }
-            if (i == 0) {
-                const int o = orig[t];
-                orig[t] = orig[q];
-                orig[q] = o;
-                dsh[q] = dsh[t];
-                dsh[t] = dp;
-            }
-        }
-        __syncthreads();
-        const double piv = sqrt(dp);
-        const double rp = 1.0 / piv;
-        if (i == 0) L[(long long)t * ldl + t] = piv;
-        const int row = t + 1 + i;
-        if (row < k) {
-            const double* Lr = L + row;
-            const double* Lt = L + t;
-            double a0 = G[(long long)orig[t] * ldg + orig[row]], a1 = 0.0, a2 = 0.0, a3 = 0.0;
-            int c = 0;
-            for (; c + 3 < t; c += 4) {
-                a0 = fma(-Lr[(long long)c * ldl], Lt[(long long)c * ldl], a0);
-                a1 = fma(-Lr[(long long)(c + 1) * ldl], Lt[(long long)(c + 1) * ldl], a1);
-                a2 = fma(-Lr[(long long)(c + 2) * ldl], Lt[(long long)(c + 2) * ldl], a2);
-                a3 = fma(-Lr[(long long)(c + 3) * ldl], Lt[(long long)(c + 3) * ldl], a3);
-            }
-            for (; c < t; ++c) a0 = fma(-Lr[(long long)c * ldl], Lt[(long long)c * ldl], a0);
-            const double lit = ((a0 + a1) + (a2 + a3)) * rp;
-            L[(long long)t * ldl + row] = lit;
-            dsh[row] -= lit * lit;
-        }
-        __syncthreads();
-    }
-    for (int t = i; t < k; t += blockDim.x) perm[t] = orig[t];
-    if (i == 0) {
-        dm_out[b] = m;
-        kx_out[b] = k;
-    }
-}
-
-// ---- shared-memory forms (k up to SM_PACK_K): the factor lives in shared memory as a packed
-// lower triangle, column c (rows c .. k-1) at pk_off(c, k) + row - c, and every step spreads
-// its dot products over row groups of 32 x column chunks so that all 16 warps issue FP64 work
-// (on this part the FP64 pipe, not memory, is the limit).
-constexpr int SM_THREADS = 512;
-constexpr int SM_PACK_K = 224;          // 224 * 225 / 2 doubles = 197 KB
-
-__device__ __forceinline__ int pk_off(int c, int k) { return c * k - ((c * (c - 1)) >> 1); }
-
-// Row-group x column-chunk split of a step with nr rows and nc terms a row: tasks (rg, ch),
-// rg < ceil(nr / 32), ch < nch; warp w takes tasks w, w + 16, ...
-struct SplitRC {
-    int rg, nch, clen;
-    __device__ SplitRC(int nr, int nc)
-    {
-        rg = (nr + 31) >> 5;
-        nch = rg >= 16 ? 1 : 16 / rg;
-        clen = (nc + nch - 1) / nch;
-        if (clen == 0) clen = 1;
-    }
-};
-
-// Same factorisation as k_chol_piv, with Lt in shared memory (dynamic, k(k+1)/2 doubles).
-__global__ void __launch_bounds__(SM_THREADS) k_chol_smem(ModeMap mm, const double* G, long long gstride, int ldg,
-                                                         const int* dk, int* kx_out, double* L, long long lstride,
-                                                         int ldl, int* perm, int pstride, int* dm_out, int* fail,
-                                                         int pivot, double tol, double* d0_out, const double* d0_ref,
-                                                         double floor_rel)
-{
-    const int b = mm.m[blockIdx.x];
-    const int k = dk[b];
-    G += b * gstride;
-    L += b * lstride;
-    perm += b * pstride;
-    extern __shared__ double Ls[];
-    __shared__ double dsh[KMAX];
-    __shared__ int orig[KMAX];
-    __shared__ double part[SM_THREADS];
-    __shared__ double red[33];
-    __shared__ int redi[32];
-    __shared__ long long redl[32];
-    __shared__ int s_q;
-    __shared__ double s_piv;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < k) { dsh[tid] = G[(long long)tid * ldg + tid]; orig[tid] = tid; }
-    __syncthreads();
-    double d0max = 0.0;
-    {
-        double v = tid < k ? dsh[tid] : 0.0;
-        v = warp_max(v);
-        if (lane == 0) red[warp] = v;
-        __syncthreads();
-        for (int w = 0; w < SM_THREADS / 32; ++w) d0max = fmax(d0max, red[w]);
-        __syncthreads();
-    }
-    if (d0_out && tid == 0) d0_out[b] = d0max;
-    // absolute floor (deflation sketch): a pivot must also exceed floor_rel times the first
-    // sketch's scale, so that cancellation noise never becomes a basis direction
-    const double dfloor = d0_ref ? floor_rel * d0_ref[b] : 0.0;
-    // Scalar FP64 work (the stop test, sqrt, reciprocal) is done once by thread 0 and shared:
-    // FP64 is a slow pipe here, and 16 warps repeating it would cost more than the dot products.
-    // The pivot search compares bit patterns on the integer pipe (a non-negative double orders
-    // like its bits; a negative Schur diagonal maps to -1, a finished slot to LLONG_MIN, so that
-    // with every remaining diagonal negative the search still lands on an active slot and the
-    // stop test ends the factorisation).
-    __shared__ double s_rp;
-    __shared__ int s_stop;
-    int m = k;
-    for (int t = 0; t < k; ++t) {
-        if (pivot) {
-            long long key = LLONG_MIN;         // finished or absent slots lose to every active one
-            if (tid >= t && tid < k) {
-                const long long bits = __double_as_longlong(dsh[tid]);
-                key = bits >= 0 ? bits : -1;    // a negative diagonal ranks below all others
-            }
-            int idx = tid;
-            for (int o = 16; o > 0; o >>= 1) {
-                const long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-                const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-                if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
-            }
-            if (lane == 0) { redl[warp] = key; redi[warp] = idx; }
-            __syncthreads();
-            if (tid == 0) {
-                long long bk = LLONG_MIN;
-                int bi = t;
-                for (int w = 0; w < SM_THREADS / 32; ++w)
-                    if (redl[w] > bk || (redl[w] == bk && redi[w] < bi)) { bk = redl[w]; bi = redi[w]; }
-                s_q = bi;
-            }
-        } else if (tid == 0) {
-            s_q = t;
-        }
-        if (tid == 0) {
-            const double dp = dsh[s_q];
-            const bool stop = !(dp > tol * d0max) || !(dp > 0.0) || !(dp > dfloor);
-            s_stop = stop;
-            s_piv = dp;
-            if (!stop) {
-                const double piv = sqrt(dp);
-                s_rp = 1.0 / piv;
-                Ls[pk_off(t, k)] = piv;
-            }
-        }
-        __syncthreads();
-        const int q = s_q;
-        const double dp = s_piv;
-        if (s_stop) {
-            if (!pivot && tid == 0 && fail) fail[b] = 1;
-            m = t;
-            break;
-        }
-        if (q != t) {
-            for (int c = tid; c < t; c += SM_THREADS) {
-                const int o = pk_off(c, k) - c;
-                const double x = Ls[o + t];
-                Ls[o + t] = Ls[o + q];
-                Ls[o + q] = x;
-            }
-            if (tid == 0) {
-                const int o = orig[t];
-                orig[t] = orig[q];
-                orig[q] = o;
-                dsh[q] = dsh[t];
-                dsh[t] = dp;
-            }
-        }
-        __syncthreads();
-        const int nr = k - t - 1;
-        const SplitRC sp(nr, t);
-        for (int task = warp; task < sp.rg * sp.nch; task += SM_THREADS / 32) {
-            const int rg = task / sp.nch, ch = task - rg * sp.nch;
-            const int r = t + 1 + rg * 32 + lane;
-            double a0 = 0.0, a1 = 0.0;
-            if (r < k) {
-                const int cb = ch * sp.clen, ce = min(t, cb + sp.clen);
-                int c = cb;
-                for (; c + 1 < ce; c += 2) {
-                    const int o0 = pk_off(c, k) - c, o1 = pk_off(c + 1, k) - c - 1;
-                    a0 = fma(Ls[o0 + r], Ls[o0 + t], a0);
-                    a1 = fma(Ls[o1 + r], Ls[o1 + t], a1);
-                }
-                if (c < ce) {
-                    const int o0 = pk_off(c, k) - c;
-                    a0 = fma(Ls[o0 + r], Ls[o0 + t], a0);
-                }
-            }
-            part[task * 32 + lane] = a0 + a1;
-        }
-        __syncthreads();
-        const double rp = s_rp;
-        const int ot = pk_off(t, k) - t;
-        if (tid < nr) {
-            const int r = t + 1 + tid;
-            double sacc = G[(long long)orig[t] * ldg + orig[r]];
-            const int rg = tid >> 5;
-            for (int ch = 0; ch < sp.nch; ++ch) sacc -= part[(rg * sp.nch + ch) * 32 + lane];
-            const double lit = sacc * rp;
-            Ls[ot + r] = lit;
-            dsh[r] -= lit * lit;
-        }
-        __syncthreads();
-    }
-    for (int t = tid; t < k; t += SM_THREADS) perm[t] = orig[t];
-    for (int c = warp; c < m; c += SM_THREADS / 32) {
-        const int o = pk_off(c, k) - c;
-        for (int r = c + lane; r < m; r += 32) L[(long long)c * ldl + r] = Ls[o + r];
-    }
-    if (tid == 0) {
-        dm_out[b] = m;
-        kx_out[b] = k;
-    }
-}
-
 // ------------------------------------------------------------------ triangular inverse
-// Lt^{-1} of the m x m factor of k_chol_piv, scattered into W (kx x m, ld ldw) so that
+// Lt^{-1} of the m x m pivoted Cholesky factor (launch_chol), scattered into W (kx x m, ld ldw) so that
 // Q = X W = X P Lt^{-T} (the CholeskyQR factor) is one GEMM: W(perm[j], t) = Lt^{-1}(t, j) for
 // t >= j, 0 for t < j; rows perm[j], m <= j < kx (columns of X left out) are zero.
 // Column j of Lt^{-1} by forward substitution with column axpys: one warp per column, lane l
 // holding entries l, l + 32, ...  grid: (ceil(KMAX / 4), nmodes), block 128.
 __global__ void k_trinv(ModeMap mm, const double* L, long long lstride, int ldl, const int* perm, int pstride,
-                        const int* dkx, const int* dm, double* W, long long wstride, int ldw)
+                        const int* dkx, const int* dm, double* W, long long wstride, int ldw, const int* near)
 {
     const int b = mm.m[blockIdx.y];
+    if (near && near[b]) return;          // the Cholesky wrote W itself (near-identity Gram)
     const int m = dm[b], kx = dkx[b];
     L += b * lstride;
     perm += b * pstride;
@@ -438,197 +155,6 @@ int launch_append(ModeMap mm, double* Q, const double* Q2, long long nk, const i
     return 0;
 }
 
-// ------------------------------------------------------------------ tridiagonalisation
-// A: k x k symmetric (full storage, leading dimension lda, batch stride astride), in place.
-// Reflector j (j = 0..k-3): x = A(j+1:k, j), alpha = -sign(x_0)||x||, v = x - alpha e_1,
-// tau = 2 / v^T v; the trailing block gets A <- H A H via p = tau A v, w = p - (tau/2)(p^T v) v,
-// A <- A - v w^T - w v^T.  Output: d (diagonal), e (sub-diagonal), tau, and v stored in
-// A(j+1:k, j).
-__global__ void k_tridiag(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e,
-                          double* tau, int vstride)
-{
-    const int b = mm.m[blockIdx.x];
-    const int k = dk[b];
-    A += b * astride;
-    d += b * vstride;
-    e += b * vstride;
-    tau += b * vstride;
-    __shared__ double v[KMAX], w[KMAX];
-    __shared__ double red[32];
-    const int i = threadIdx.x;
-    for (int j = 0; j + 2 < k; ++j) {
-        const int len = k - j - 1;                 // rows j+1..k-1
-        const int gi = j + 1 + i;
-        double xi = (i < len) ? A[(long long)j * lda + gi] : 0.0;
-        const double x0 = A[(long long)j * lda + j + 1];
-        double tailsq = block_sum((i >= 1 && i < len) ? xi * xi : 0.0, red);
-        double t_j, alpha;
-        if (tailsq == 0.0) {
-            t_j = 0.0;
-            alpha = x0;
-            if (i < len) v[i] = 0.0;
-        } else {
-            const double xn = sqrt(x0 * x0 + tailsq);
-            alpha = (x0 >= 0.0) ? -xn : xn;
-            const double v0 = x0 - alpha;
-            const double vtv = v0 * v0 + tailsq;
-            t_j = 2.0 / vtv;
-            if (i < len) v[i] = (i == 0) ? v0 : xi;
-        }
-        __syncthreads();
-        if (i == 0) { tau[j] = t_j; e[j] = alpha; d[j] = A[(long long)j * lda + j]; }
-        if (t_j != 0.0) {
-            // p = tau * A22 v (row i of the trailing block)
-            double pi = 0.0;
-            if (i < len) {
-                for (int c = 0; c < len; ++c) pi += A[(long long)(j + 1 + c) * lda + gi] * v[c];
-                pi *= t_j;
-            }
-            const double ptv = block_sum((i < len) ? pi * v[i] : 0.0, red);
-            const double Kc = 0.5 * t_j * ptv;
-            if (i < len) w[i] = pi - Kc * v[i];
-            __syncthreads();
-            if (i < len) {
-                const double vi = v[i], wi = w[i];
-                for (int c = 0; c < len; ++c) {
-                    double* a = &A[(long long)(j + 1 + c) * lda + gi];
-                    *a -= vi * w[c] + wi * v[c];
-                }
-            }
-        }
-        __syncthreads();
-        if (i < len) A[(long long)j * lda + gi] = v[i];   // keep the reflector
-        __syncthreads();
-    }
-    if (i == 0) {
-        if (k >= 2) {
-            d[k - 2] = A[(long long)(k - 2) * lda + (k - 2)];
-            d[k - 1] = A[(long long)(k - 1) * lda + (k - 1)];
-            e[k - 2] = A[(long long)(k - 2) * lda + (k - 1)];
-            tau[k - 2] = 0.0;
-        } else if (k == 1) {
-            d[0] = A[0];
-        }
-    }
-}
-
-// Same reduction as k_tridiag with the trailing block in shared memory (packed lower
-// triangle): p = A22 v by row groups x column chunks, the rank-2 update on the lower triangle
-// only (column c by a warp, rows i >= c by its lanes).
-__global__ void __launch_bounds__(SM_THREADS) k_tridiag_smem(ModeMap mm, double* A, long long astride, int lda,
-                                                            const int* dk, double* d, double* e, double* tau,
-                                                            int vstride)
-{
-    const int b = mm.m[blockIdx.x];
-    const int k = dk[b];
-    A += b * astride;
-    d += b * vstride;
-    e += b * vstride;
-    tau += b * vstride;
-    extern __shared__ double S[];
-    __shared__ double v[KMAX], w[KMAX];
-    __shared__ double part[SM_THREADS];
-    __shared__ double red[33];
-    __shared__ double sc[2];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int c = warp; c < k; c += SM_THREADS / 32) {
-        const int o = pk_off(c, k) - c;
-        for (int i = c + lane; i < k; i += 32) S[o + i] = A[(long long)c * lda + i];
-    }
-    __syncthreads();
-    for (int j = 0; j + 2 < k; ++j) {
-        const int len = k - j - 1, c0 = j + 1;
-        const int oj = pk_off(j, k) - j;
-        const double x0 = S[oj + c0];
-        const double xi = (tid >= 1 && tid < len) ? S[oj + c0 + tid] : 0.0;
-        // tail norm, then alpha and tau by thread 0 (one FP64 sqrt and division, shared)
-        double ts = xi * xi;
-        const int nwa = (len + 31) >> 5;
-        if (warp < nwa) ts = warp_sum(ts);
-        if (lane == 0 && warp < nwa) red[warp] = ts;
-        __syncthreads();
-        if (warp == 0) {
-            double t2 = lane < nwa ? red[lane] : 0.0;
-            t2 = warp_sum(t2);
-            if (lane == 0) {
-                double tj = 0.0, al = x0;
-                if (t2 != 0.0) {
-                    const double xn = sqrt(x0 * x0 + t2);
-                    al = (x0 >= 0.0) ? -xn : xn;
-                    const double v0 = x0 - al;
-                    tj = 2.0 / (v0 * v0 + t2);
-                }
-                sc[0] = tj;
-                sc[1] = al;
-            }
-        }
-        __syncthreads();
-        const double t_j = sc[0], alpha = sc[1];
-        if (tid < len) {
-            const double vi = (t_j == 0.0) ? 0.0 : (tid == 0 ? x0 - alpha : xi);
-            v[tid] = vi;
-            A[(long long)j * lda + c0 + tid] = vi;       // the reflector, for the back-transformation
-        }
-        if (tid == 0) { tau[j] = t_j; e[j] = alpha; d[j] = S[oj + j]; }
-        __syncthreads();
-        if (t_j != 0.0) {
-            const SplitRC sp(len, len);
-            for (int task = warp; task < sp.rg * sp.nch; task += SM_THREADS / 32) {
-                const int rg = task / sp.nch, ch = task - rg * sp.nch;
-                const int i = rg * 32 + lane;
-                double acc = 0.0;
-                if (i < len) {
-                    const int gi = c0 + i;
-                    const int cb = ch * sp.clen, ce = min(len, cb + sp.clen);
-                    const int oi = pk_off(gi, k) - gi;
-                    for (int c = cb; c < ce; ++c) {
-                        const int gc = c0 + c;
-                        const int idx = gi >= gc ? pk_off(gc, k) - gc + gi : oi + gc;
-                        acc = fma(S[idx], v[c], acc);
-                    }
-                }
-                part[task * 32 + lane] = acc;
-            }
-            __syncthreads();
-            double pi = 0.0;
-            if (tid < len) {
-                const int rg = tid >> 5;
-                for (int ch = 0; ch < sp.nch; ++ch) pi += part[(rg * sp.nch + ch) * 32 + lane];
-                pi *= t_j;
-            }
-            double pv = tid < len ? pi * v[tid] : 0.0;
-            if (warp < nwa) pv = warp_sum(pv);
-            if (lane == 0 && warp < nwa) red[warp] = pv;
-            __syncthreads();
-            if (warp == 0) {
-                double t2 = lane < nwa ? red[lane] : 0.0;
-                t2 = warp_sum(t2);
-                if (lane == 0) sc[0] = 0.5 * t_j * t2;
-            }
-            __syncthreads();
-            const double Kc = sc[0];
-            if (tid < len) w[tid] = pi - Kc * v[tid];
-            __syncthreads();
-            for (int c = warp; c < len; c += SM_THREADS / 32) {
-                const double vc = v[c], wc = w[c];
-                double* Sc = S + pk_off(c0 + c, k) - (c0 + c) + c0;    // row i (relative) at Sc[i]
-                for (int i = c + lane; i < len; i += 32) Sc[i] = fma(-v[i], wc, fma(-w[i], vc, Sc[i]));
-            }
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        if (k >= 2) {
-            d[k - 2] = S[pk_off(k - 2, k)];
-            d[k - 1] = S[pk_off(k - 1, k)];
-            e[k - 2] = S[pk_off(k - 2, k) + 1];
-            tau[k - 2] = 0.0;
-        } else if (k == 1) {
-            d[0] = S[0];
-        }
-    }
-}
-
 // ------------------------------------------------------------------ eigenvalues
 // Number of eigenvalues of L D L^T below x: the signs of the pivots D+_i of the stationary qd
 // transform L D L^T - x I = L+ D+ L+^T (t_0 = -x, D+_i = D_i + t_i, t_{i+1} = t_i W_i / D+_i - x,
@@ -668,67 +194,90 @@ __device__ __forceinline__ int negcount(const double* D, const double* W, int k,
     return c;
 }
 
-// LDL^T = T + s I with s > 0 multiplied by 4 until every pivot is positive (one thread per
-// mode).  Writes D, Lo, the shift s and an upper bound of the spectrum of L D L^T.
+// LDL^T = T + s I with s > 0 multiplied by 4 until every pivot is positive (one warp per
+// mode: the norms by all lanes, the recurrence by lane 0).  Writes D, Lo, the shift s and an
+// upper bound of the spectrum of L D L^T.
 __global__ void k_ldl(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D,
                       double* Lo, DevState* st)
 {
     const int b = mm.m[blockIdx.x];
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
     const int k = dk[b];
     d += b * vstride;
     e += b * vstride;
     D += b * vstride;
     Lo += b * vstride;
+    // d and e in shared memory: the recurrence below is one serial chain, and a global load
+    // on it would cost an L2 round trip a step
+    __shared__ double ds[KMAX], es[KMAX];
     double tnorm = 0.0;
-    for (int i = 0; i < k; ++i) {
-        double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
+    for (int i = lane; i < k; i += 32) {
+        ds[i] = d[i];
+        es[i] = i + 1 < k ? e[i] : 0.0;
+        const double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
         tnorm = fmax(tnorm, r);
     }
-    double s = fmax(4.0 * k * DBL_EPSILON * tnorm, DBL_MIN);
-    bool ok = false;
-    for (int tries = 0; tries < 60 && !ok; ++tries) {
-        ok = true;
-        double Dc = d[0] + s;
-        for (int i = 0; i < k; ++i) {
-            if (!(Dc > 0.0)) { ok = false; break; }
-            D[i] = Dc;
-            if (i + 1 < k) {
-                const double l = e[i] / Dc;
-                Lo[i] = l;
-                Dc = d[i + 1] + s - l * e[i];
-            } else {
-                Lo[i] = 0.0;
+    tnorm = warp_max(tnorm);
+    __syncwarp();
+    __shared__ double s_shift;
+    if (lane == 0) {
+        double s = fmax(4.0 * k * DBL_EPSILON * tnorm, DBL_MIN);
+        bool ok = false;
+        for (int tries = 0; tries < 60 && !ok; ++tries) {
+            ok = true;
+            double Dc = ds[0] + s;
+            for (int i = 0; i < k; ++i) {
+                if (!(Dc > 0.0)) { ok = false; break; }
+                D[i] = Dc;
+                if (i + 1 < k) {
+                    const double l = es[i] / Dc;
+                    Lo[i] = l;
+                    Dc = ds[i + 1] + s - l * es[i];
+                } else {
+                    Lo[i] = 0.0;
+                }
             }
+            if (!ok) s *= 4.0;
         }
-        if (!ok) s *= 4.0;
+        if (!ok) st->piv_fail[b] = 1;
+        s_shift = s;
     }
-    if (!ok) st->piv_fail[b] = 1;
+    __syncwarp();
+    const double s = s_shift;
     double hi = 0.0;
-    for (int i = 0; i < k; ++i) {
-        double r = d[i] + s + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
+    for (int i = lane; i < k; i += 32) {
+        const double r = d[i] + s + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
         hi = fmax(hi, r);
     }
-    st->shift[b] = s;
-    st->specmax[b] = hi * (1.0 + 8.0 * DBL_EPSILON) + DBL_MIN;
+    hi = warp_max(hi);
+    if (lane == 0) {
+        st->shift[b] = s;
+        st->specmax[b] = hi * (1.0 + 8.0 * DBL_EPSILON) + DBL_MIN;
+    }
 }
 
-// Eigenvalue a (ascending) of L D L^T by multisection: one warp per eigenvalue, each lane
-// counts at one of 32 points inside the current bracket, and the bracket shrinks to the two
-// neighbouring points around the eigenvalue (33-fold per round).  Points are spaced
-// geometrically while hi > 4 lo (relative accuracy across the whole spectrum), linearly after.
-// The bracket starts at [s/2, specmax]: T + s I has no eigenvalue below s (1 - k u ||T|| / s).
-// About 12 rounds reach hi - lo <= 2 u hi.
-// grid: (ceil(KMAX / EIG_WARPS), nmodes), block: 32 EIG_WARPS threads.
+// Eigenvalue a (ascending) of L D L^T by multisection: EIG_P lanes per eigenvalue (32 / EIG_P
+// eigenvalues a warp), each lane counting at one of EIG_P points inside the current bracket; the
+// bracket shrinks to the two neighbouring points around the eigenvalue ((EIG_P + 1)-fold per
+// round).  Points are spaced geometrically while hi > 4 lo (relative accuracy across the whole
+// spectrum), linearly after.  The bracket starts at [s/2, specmax]: T + s I has no eigenvalue
+// below s (1 - k u ||T|| / s).  A count is one serial chain of k steps, two dependent FP64
+// operations each, and FP64 latency on this part is long: the cost is the number of rounds, so
+// every lane of a warp serves one eigenvalue (EIG_P = 32, about 12 rounds to
+// hi - lo <= 2 u hi; 4 points a round took twice as long).  A group that has converged keeps
+// its bracket while the warp's other groups finish.
+// grid: (ceil(KMAX / (EIG_WARPS * 32 / EIG_P)), nmodes), block: 32 EIG_WARPS threads.
+constexpr int EIG_P = 32;
 constexpr int EIG_WARPS = 4;
 
 __global__ void k_bisect(ModeMap mm, const double* Dg, const double* Lg, int vstride, const int* dk,
                          double* mu, const DevState* st)
 {
+    constexpr int PER_WARP = 32 / EIG_P, PER_BLOCK = EIG_WARPS * PER_WARP;
     const int b = mm.m[blockIdx.y];
     const int k = dk[b];
     __shared__ double Dsh[KMAX], Wsh[KMAX];
-    if (blockIdx.x * EIG_WARPS >= k) return;
+    if (blockIdx.x * PER_BLOCK >= k) return;
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         const double d = Dg[b * vstride + i];
         const double l = (i + 1 < k) ? Lg[b * vstride + i] : 0.0;
@@ -737,27 +286,34 @@ __global__ void k_bisect(ModeMap mm, const double* Dg, const double* Lg, int vst
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int a = blockIdx.x * EIG_WARPS + (threadIdx.x >> 5);
-    if (a >= k) return;
+    const int grp = lane / EIG_P, j = lane - grp * EIG_P + 1;
+    const int a = blockIdx.x * PER_BLOCK + (threadIdx.x >> 5) * PER_WARP + grp;
+    const unsigned gbits = EIG_P == 32 ? 0xffffffffu : ((1u << (EIG_P & 31)) - 1u);
+    const unsigned gmask = gbits << ((grp * EIG_P) & 31);
     double lo = 0.5 * st->shift[b], hi = st->specmax[b];
-    const int j = lane + 1;
-    for (int round = 0; round < 64; ++round) {
-        if (hi - lo <= 2.0 * DBL_EPSILON * hi) break;
-        double x = fma(hi - lo, (double)j * (1.0 / 33.0), lo);
+    bool done = a >= k;
+    for (int round = 0; round < 160; ++round) {
+        if (!done && hi - lo <= 2.0 * DBL_EPSILON * hi) done = true;
+        if (__all_sync(0xffffffffu, done)) break;
+        double x = fma(hi - lo, (double)j * (1.0 / (EIG_P + 1)), lo);
         if (hi > 4.0 * lo) {
             const float lr = log2f((float)(hi / lo));
-            const double g = lo * (double)exp2f(lr * (float)j * (1.0f / 33.0f));
+            const double g = lo * (double)exp2f(lr * (float)j * (1.0f / (EIG_P + 1)));
             if (g > lo && g < hi) x = g;
         }
-        const bool below = negcount(Dsh, Wsh, k, x) <= a;     // lambda_a >= x
-        const unsigned m = __ballot_sync(0xffffffffu, below);
-        const int f = (~m) ? __ffs(~m) - 1 : 32;               // first point above lambda_a
-        const double xl = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
-        const double xh = __shfl_sync(0xffffffffu, x, f < 32 ? f : 31);
-        if (f > 0) lo = xl;
-        if (f < 32) hi = xh;
+        const bool below = !done && negcount(Dsh, Wsh, k, x) <= a;     // lambda_a >= x
+        const unsigned m = (__ballot_sync(0xffffffffu, below) & gmask) >> ((grp * EIG_P) & 31);
+        const unsigned above = ~m & gbits;
+        const int f = above ? __ffs(above) - 1 : EIG_P;                // first point above lambda_a
+        const int base = grp * EIG_P;
+        const double xl = __shfl_sync(0xffffffffu, x, base + (f > 0 ? f - 1 : 0));
+        const double xh = __shfl_sync(0xffffffffu, x, base + (f < EIG_P ? f : EIG_P - 1));
+        if (!done) {
+            if (f > 0) lo = xl;
+            if (f < EIG_P) hi = xh;
+        }
     }
-    if (lane == 0) mu[b * vstride + a] = 0.5 * (lo + hi);
+    if (j == 1 && a < k) mu[b * vstride + a] = 0.5 * (lo + hi);
 }
 
 // ------------------------------------------------------------------ rank rule
@@ -1004,32 +560,19 @@ __global__ void k_trace(ModeMap mm, const double* A, long long astride, int lda,
 
 int launch_chol(ModeMap mm, const double* G, long long gstride, int ldg, const int* dk, int* kx_out, double* L,
                 long long lstride, int ldl, int* perm, int pstride, int* dm_out, int* fail, int pivot, double tol, int nb,
-                int kbound, double* d0_out, const double* d0_ref, double floor_rel, cudaStream_t st)
+                int kbound, double* d0_out, const double* d0_ref, double floor_rel, double* W, long long wstride,
+                int ldw, int* near_out, cudaStream_t st)
 {
-    if (kbound <= SM_PACK_K) {
-        const size_t smem = sizeof(double) * (size_t)kbound * (kbound + 1) / 2;
-        static bool attr = false;
-        if (!attr) {
-            if (cudaFuncSetAttribute(k_chol_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(sizeof(double) * SM_PACK_K * (SM_PACK_K + 1) / 2)) != cudaSuccess)
-                return RHOSVD_ERR_CUDA;
-            attr = true;
-        }
-        k_chol_smem<<<nb, SM_THREADS, smem, st>>>(mm, G, gstride, ldg, dk, kx_out, L, lstride, ldl, perm, pstride,
-                                                  dm_out, fail, pivot, tol, d0_out, d0_ref, floor_rel);
-    } else {
-        k_chol_piv<<<nb, KMAX, 0, st>>>(mm, G, gstride, ldg, dk, 0, kx_out, L, lstride, ldl, perm, pstride, dm_out,
-                                        fail, pivot, tol, d0_out, d0_ref, floor_rel);
-    }
-    RH_CHECK_LAUNCH();
-    return 0;
+    return launch_chol_cluster(mm, G, gstride, ldg, dk, kx_out, L, lstride, ldl, perm, pstride, dm_out, fail, pivot,
+                               tol, nb, kbound, d0_out, d0_ref, floor_rel, W, wstride, ldw, near_out, st);
 }
 
 int launch_trinv(ModeMap mm, const double* L, long long lstride, int ldl, const int* perm, int pstride,
-                 const int* dkx, const int* dm, double* W, long long wstride, int ldw, int nb, cudaStream_t st)
+                 const int* dkx, const int* dm, double* W, long long wstride, int ldw, const int* near, int nb,
+                 cudaStream_t st)
 {
     dim3 grid((KMAX + 3) / 4, nb);
-    k_trinv<<<grid, 128, 0, st>>>(mm, L, lstride, ldl, perm, pstride, dkx, dm, W, wstride, ldw);
+    k_trinv<<<grid, 128, 0, st>>>(mm, L, lstride, ldl, perm, pstride, dkx, dm, W, wstride, ldw, near);
     RH_CHECK_LAUNCH();
     return 0;
 }
@@ -1045,21 +588,7 @@ int launch_trace(ModeMap mm, const double* A, long long astride, int lda, const 
 int launch_tridiag(ModeMap mm, double* A, long long astride, int lda, const int* dk, double* d, double* e, double* tau,
                    int vstride, int nb, int kbound, cudaStream_t st)
 {
-    if (kbound <= SM_PACK_K) {
-        const size_t smem = sizeof(double) * (size_t)kbound * (kbound + 1) / 2;
-        static bool attr = false;
-        if (!attr) {
-            if (cudaFuncSetAttribute(k_tridiag_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(sizeof(double) * SM_PACK_K * (SM_PACK_K + 1) / 2)) != cudaSuccess)
-                return RHOSVD_ERR_CUDA;
-            attr = true;
-        }
-        k_tridiag_smem<<<nb, SM_THREADS, smem, st>>>(mm, A, astride, lda, dk, d, e, tau, vstride);
-    } else {
-        k_tridiag<<<nb, KMAX, 0, st>>>(mm, A, astride, lda, dk, d, e, tau, vstride);
-    }
-    RH_CHECK_LAUNCH();
-    return 0;
+    return launch_tridiag_cluster(mm, A, astride, lda, dk, d, e, tau, vstride, nb, kbound, st);
 }
 
 int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D, double* Lo,
@@ -1067,7 +596,8 @@ int launch_eigvals(ModeMap mm, const double* d, const double* e, int vstride, co
 {
     k_ldl<<<nb, 32, 0, st>>>(mm, d, e, vstride, dk, D, Lo, s);
     RH_CHECK_LAUNCH();
-    dim3 grid((KMAX + EIG_WARPS - 1) / EIG_WARPS, nb);
+    constexpr int per_block = EIG_WARPS * (32 / EIG_P);
+    dim3 grid((KMAX + per_block - 1) / per_block, nb);
     k_bisect<<<grid, 32 * EIG_WARPS, 0, st>>>(mm, D, Lo, vstride, dk, mu, s);
     RH_CHECK_LAUNCH();
     return 0;
