@@ -259,6 +259,16 @@ int rhosvd_proj_target(int n, const double* Q, const double* Z, int ldz, int r, 
  * the network's output for that mode (FP32). */
 int rhosvd_proposal_basis(int n, const double* QT, const float* Y, double* Q0, void* stream);
 
+/* ---------------------------------------------------------------- numerics self-test (no paper
+ * counterpart: test support)
+ *
+ * rhosvd_selftest_fastmath evaluates, for n device doubles x, the short-latency reciprocal and
+ * reciprocal square root the small factorisations use on their serial chains (an FP32
+ * estimate of the exponent-scaled argument refined by two Newton-Raphson steps in FP64):
+ * rcp[i] ~ 1/x[i], rsq[i] ~ 1/sqrt(x[i]) (device arrays of n doubles, caller-owned).  Returns
+ * RHOSVD_ERR_INVALID_ARG for n < 0 or null pointers with n > 0; asynchronous on `stream`. */
+int rhosvd_selftest_fastmath(const double* x, double* rcp, double* rsq, int n, void* stream);
+
 /* ---------------------------------------------------------------- tracing (no paper
  * counterpart: observability of the library itself) */
 

@@ -142,6 +142,8 @@ def load(build_if_missing: bool = False):
                                          _c.c_void_p]
         L.rhosvd_proposal_basis.restype = _c.c_int
         L.rhosvd_proposal_basis.argtypes = [_c.c_int, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_selftest_fastmath.restype = _c.c_int
+        L.rhosvd_selftest_fastmath.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p]
         L.rhosvd_launch_count.restype = _c.c_longlong
         L.rhosvd_profile_enable.restype = _c.c_int
         L.rhosvd_profile_enable.argtypes = [_c.c_int]
@@ -219,6 +221,18 @@ def rhosvd_strerror(code: int) -> str:
         return load().rhosvd_strerror(int(code)).decode()
     except Exception:                                  # library unavailable
         return f"status {code}"
+
+
+def rhosvd_selftest_fastmath(x, stream=None):
+    """(1/x, 1/sqrt(x)) by the library's short-latency device helpers (float64 CUDA tensor x)."""
+    torch = _torch()
+    x = x.contiguous()
+    rcp, rsq = torch.empty_like(x), torch.empty_like(x)
+    rc = load().rhosvd_selftest_fastmath(_c.c_void_p(x.data_ptr()), _c.c_void_p(rcp.data_ptr()),
+                                         _c.c_void_p(rsq.data_ptr()), int(x.numel()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_selftest_fastmath")
+    return rcp, rsq
 
 
 def rhosvd_launch_count() -> int:

@@ -397,3 +397,23 @@ int launch_cpsum(const SumArgs& a, cudaStream_t st)
 }
 
 }  // namespace rh
+
+// ---------------------------------------------------------------- self-test of the fast helpers
+namespace {
+__global__ void k_selftest_fastmath(const double* x, double* rcp, double* rsq, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        rcp[i] = rh::fast_rcp(x[i]);
+        rsq[i] = rh::fast_rsqrt(x[i]);
+    }
+}
+}  // namespace
+
+extern "C" int rhosvd_selftest_fastmath(const double* x, double* rcp, double* rsq, int n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !rcp || !rsq))) return RHOSVD_ERR_INVALID_ARG;
+    if (n == 0) return RHOSVD_OK;
+    k_selftest_fastmath<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, (cudaStream_t)stream>>>(x, rcp, rsq, n);
+    rh::count_launch();
+    return cudaGetLastError() == cudaSuccess ? RHOSVD_OK : RHOSVD_ERR_CUDA;
+}

@@ -54,9 +54,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
     e += b * vstride;
     tau += b * vstride;
     extern __shared__ double Srow[];
-    __shared__ double xg[KMAX], pg[KMAX], vl[KMAX], wl[KMAX], ploc[32];
+    __shared__ double xg[KMAX], pg[KMAX], vl[KMAX], wl[KMAX], ploc[32], qloc[32];
+    __shared__ double dsh[KMAX], esh[KMAX], tsh[KMAX];
     __shared__ double nrm[C], pvp[C];
-    __shared__ double sc[3];
+    __shared__ double sc[4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nloc = rank < k ? (k - rank + C - 1) / C : 0;
     // the owned rows from the lower triangle: A(i, c) = A[c lda + i] for c <= i, A[i lda + c] above
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
     }
     cl.sync();                     // every block resident and loaded before the first remote store
     for (int j = 0; j + 2 < k; ++j) {
-        const int c0 = j + 1, len = k - c0;
+        const int c0 = j + 1;
         const int li0 = c0 <= rank ? 0 : (c0 - rank + C - 1) / C;  // first owned row >= c0
         const int nr = nloc > li0 ? nloc - li0 : 0;
         // ---- A: x = column j of the owned rows, and the owned part of the tail norm
@@ -89,62 +90,69 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
             if (lane < C) cl.map_shared_rank(nrm, lane)[rank] = s;
         }
         cl.sync();
-        if (warp == 0) {
-            // the C partial norms by a shuffle tree (same order in every block)
-            const double t2 = warp_sum(lane < C ? nrm[lane] : 0.0);
+        // ---- B: the Householder scalars in the last warp while warps 0..6 form
+        // q_i = sum_{c > c0} A(i, c) x_c for the owned rows: v differs from x only in entry c0,
+        // so A v = q + A(:, c0) v0 needs no scalar until the end, and the scalar chain (a square
+        // root and a reciprocal, long dependent FP64 sequences) runs beside the product
+        if (warp == TC_THREADS / 32 - 1) {
+            const double t2 = warp_sum(lane < C ? nrm[lane] : 0.0);   // same tree in every block
             if (lane == 0) {
-            const double x0 = xg[c0];
-            double tj = 0.0, al = x0;
-            if (t2 != 0.0) {
-                const double xn = sqrt(x0 * x0 + t2);
-                al = (x0 >= 0.0) ? -xn : xn;
-                const double v0 = x0 - al;
-                tj = 2.0 / (v0 * v0 + t2);
-            }
-            sc[0] = tj;
-            sc[1] = al;
-            if (rank == 0) {
-                tau[j] = tj;
-                e[j] = al;
-            }
-            if (j % C == rank) d[j] = Srow[(j / C) * k + j];
-            }
-        }
-        __syncthreads();
-        const double t_j = sc[0], alpha = sc[1];
-        for (int c = c0 + tid; c < k; c += TC_THREADS)
-            vl[c] = (t_j == 0.0) ? 0.0 : (c == c0 ? xg[c0] - alpha : xg[c]);
-        __syncthreads();
-        if (tid < nr) {                                // the reflector, for the back-transformation
-            const int i = rank + (li0 + tid) * C;
-            A[(long long)j * lda + i] = vl[i];
-        }
-        // ---- B: p = tau A v on the owned rows
-        if (t_j != 0.0) {
-            const int r = tid / NCH, ch = tid - r * NCH;
-            double acc = 0.0, acc2 = 0.0;             // two chains: FP64 latency, not issue, bounds this
-            if (r < nr) {
-                const double* row = Srow + (li0 + r) * k;
-                int c = c0 + ch;
-                for (; c + NCH < k; c += 2 * NCH) {
-                    acc = fma(row[c], vl[c], acc);
-                    acc2 = fma(row[c + NCH], vl[c + NCH], acc2);
+                const double x0 = xg[c0];
+                double tj = 0.0, al = x0, v0 = 0.0;
+                if (t2 != 0.0) {
+                    const double s2 = fma(x0, x0, t2);
+                    const double xn = s2 * fast_rsqrt(s2);
+                    al = (x0 >= 0.0) ? -xn : xn;
+                    v0 = x0 - al;
+                    tj = 2.0 * fast_rcp(fma(v0, v0, t2));
                 }
-                if (c < k) acc = fma(row[c], vl[c], acc);
+                sc[0] = tj;
+                sc[1] = al;
+                sc[2] = v0;
+                tsh[j] = tj;                           // outputs stay in shared memory until the end:
+                esh[j] = al;                           // a global store pending at a cluster barrier
+                if (j % C == rank) dsh[j] = Srow[(j / C) * k + j];   // costs ~1200 cycles there
             }
-            acc += acc2;
-            for (int o = NCH / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (ch == 0 && r < nr) ploc[r] = t_j * acc;
-            __syncthreads();
+        } else {
+            constexpr int MV_ROWS = (TC_THREADS - 32) / NCH;
+            for (int rb = 0; rb < nr; rb += MV_ROWS) {
+                const int r = rb + tid / NCH, ch = tid - (tid / NCH) * NCH;
+                double acc = 0.0, acc2 = 0.0;             // two chains: FP64 latency bounds this
+                if (r < nr) {
+                    const double* row = Srow + (li0 + r) * k;
+                    int c = c0 + 1 + ch;
+                    for (; c + NCH < k; c += 2 * NCH) {
+                        acc = fma(row[c], xg[c], acc);
+                        acc2 = fma(row[c + NCH], xg[c + NCH], acc2);
+                    }
+                    if (c < k) acc = fma(row[c], xg[c], acc);
+                }
+                acc += acc2;
+                for (int o = NCH / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (ch == 0 && r < nr) qloc[r] = acc;
+            }
+        }
+        __syncthreads();
+        const double t_j = sc[0], v0 = sc[2];
+        for (int c = c0 + tid; c < k; c += TC_THREADS)
+            vl[c] = (t_j == 0.0) ? 0.0 : (c == c0 ? v0 : xg[c]);
+        if (tid < nr) {
+            const int li = li0 + tid, i = rank + li * C;
+            const double vi = (t_j == 0.0) ? 0.0 : (i == c0 ? v0 : xg[i]);
+            ploc[tid] = t_j * fma(Srow[li * k + c0], v0, qloc[tid]);
+            Srow[li * k + j] = vi;                     // the reflector: column j of the row is dead now
+        }
+        __syncthreads();
+        if (t_j != 0.0) {
             if (tid < nr * C) {
                 const int r2 = tid / C, dst = tid - r2 * C;
                 cl.map_shared_rank(pg, dst)[rank + (li0 + r2) * C] = ploc[r2];
             }
             if (warp == TC_THREADS / 32 - 1) {
-                double s = 0.0;
-                if (lane < nr) s = ploc[lane] * vl[rank + (li0 + lane) * C];
-                s = warp_sum(s);
-                if (lane < C) cl.map_shared_rank(pvp, lane)[rank] = s;
+                double s3 = 0.0;
+                if (lane < nr) s3 = ploc[lane] * vl[rank + (li0 + lane) * C];
+                s3 = warp_sum(s3);
+                if (lane < C) cl.map_shared_rank(pvp, lane)[rank] = s3;
             }
         }
         cl.sync();
@@ -152,10 +160,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
         if (t_j != 0.0) {
             if (warp == 0) {
                 const double t2 = warp_sum(lane < C ? pvp[lane] : 0.0);
-                if (lane == 0) sc[2] = 0.5 * t_j * t2;
+                if (lane == 0) sc[3] = 0.5 * t_j * t2;
             }
             __syncthreads();
-            const double Kc = sc[2];
+            const double Kc = sc[3];
             for (int c = c0 + tid; c < k; c += TC_THREADS) wl[c] = pg[c] - Kc * vl[c];
             __syncthreads();
             // a warp per owned row, lanes along the columns; the operands are put in (lo, hi)
@@ -175,6 +183,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
         }
         __syncthreads();
     }
+    // ---- outputs: reflectors of the owned rows (A(i, j) = v_i of step j, j < min(i, k - 2)),
+    // d for the owned rows, e and tau (every block holds them; block 0 writes)
+    for (int li = warp; li < nloc; li += TC_THREADS / 32) {
+        const int i = rank + li * C;
+        const int jmax = min(i, k - 2);
+        for (int j = lane; j < jmax; j += 32) A[(long long)j * lda + i] = Srow[li * k + j];
+    }
+    for (int j = rank + tid * C; j + 2 < k; j += TC_THREADS * C) d[j] = dsh[j];
+    if (rank == 0)
+        for (int j = tid; j + 2 < k; j += TC_THREADS) {
+            e[j] = esh[j];
+            tau[j] = tsh[j];
+        }
     if (tid == 0) {
         if (k >= 2) {
             if ((k - 2) % C == rank) d[k - 2] = Srow[((k - 2) / C) * k + (k - 2)];
@@ -191,27 +212,31 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
 }
 
 // ------------------------------------------------------------------ pivoted Cholesky
-// Pivoted Cholesky P^T G P = Lt Lt^T of the k x k Gram G (left-looking, diagonal pivoting; rank
-// revealing for a PSD Gram Y^T Y).  Stops at the first pivot <= tol max(diag G), or <= 0, or <=
-// the absolute floor floor_rel d0_ref (the numerical rank m); without pivoting a stop raises
+// Pivoted Cholesky P^T G P = Lt Lt^T of the k x k Gram G (diagonal pivoting; rank revealing
+// for a PSD Gram Y^T Y).  Stops at the first pivot <= tol max(diag G), or <= 0, or <= the
+// absolute floor floor_rel d0_ref (the numerical rank m); without pivoting a stop raises
 // `fail`.  Output: Lt directly, slot u holding the row chosen at step u (Lt(u, s) at
 // L[s ldl + u]); perm[u] the original index of slot u for every slot (rows never chosen take the
 // slots m.. in increasing index); dm_out = m, kx_out = k; d0_out = max(diag G) if given.
 // A near-identity Gram G = I + E (the last CholeskyQR pass, whose input is orthonormal to
 // rounding) with ||E||_F^2 <= 1e-16 takes the factor I + F, F = strict_lower(E) + diag(E)/2:
 // (I + F)(I + F)^T = G + F F^T and ||F F^T||_F <= ||E||_F^2, far below the factorisation's own
-// rounding (~k u); no pivot is needed (every diagonal is 1 +- 1e-8).
-// The rows are spread over the cluster and never swapped: block `rank` keeps, for its rows
-// i = rank + li C, row i of G (ld k), the computed L(i, 0..s) (ld k) and the Schur diagonal.
-// Step t:
-//   every block sends its best active row (diagonal bits as the key, ties to the smaller
-//   index) to every block; cluster barrier; every block picks the same pivot q from the C
-//   candidates in rank order; the owner of q sets L(q, t) = sqrt(d_q); every block copies the
-//   finished L(q, 0..t-1) from the owner's shared memory and computes
-//   L(i, t) = (G(i, q) - sum_s L(i, s) L(q, s)) / L(q, t) and d_i -= L(i, t)^2 for its active rows.
-// One cluster barrier a step: candidates go to buffers of the step's parity (a block can be
-// at most one step ahead of the slowest reader), and the pivot row read from the owner is
-// final (a chosen row is never written again).
+// rounding (~k u); no pivot is needed (every diagonal is 1 +- 1e-8).  Its inverse is written to
+// W directly (the layout of the triangular inverse) and near_out[b] = 1.
+// Right-looking over the cluster: block `rank` keeps, for its rows i = rank + li C, the current
+// Schur complement row S(i, :) (ld k), the computed L(i, 0..t) (ld k) and the Schur diagonal.
+// Step t (one cluster barrier):
+//   pick the pivot q from the C candidates gathered at the last barrier (diagonal bits as the
+//   key, ties to the smaller index; the same choice in every block);
+//   apply step t-1's rank-1 update S(i, j) -= L(i, t-1) L(j, t-1) to the owned active rows over
+//   the active columns (L(:, t-1) was gathered at the last barrier);
+//   L(i, t) = S(i, q) / sqrt(d_q), d_i -= L(i, t)^2 for the owned active rows;
+//   send the owned entries of L(:, t) and the block's best row for step t+1 to every block;
+//   cluster barrier.
+// Every block sends about (k - t) / C values a step and receives k - t: no block serves the
+// others (a left-looking form has every block read the pivot row from its one owner).  Both
+// buffers alternate by step parity: a block writes step t+1's data only after passing step t's
+// barrier, and step t+2's after step t+1's, when every reader of step t's data is done.
 template <int C>
 __global__ void __launch_bounds__(TC_THREADS) k_chol_cluster(ModeMap mm, const double* G, long long gstride, int ldg,
                                                              const int* dk, int* kx_out, double* L, long long lstride,
@@ -221,9 +246,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_cluster(ModeMap mm, const d
                                                              long long wstride, int ldw, int* near_out)
 {
     constexpr int ROWS = (KMAX + C - 1) / C;
-    constexpr int RP2 = ROWS <= 8 ? 8 : (ROWS <= 16 ? 16 : 32);
-    constexpr int NCH = TC_THREADS / RP2;                 // chunks of the dot products per row
-    static_assert(ROWS <= 32 && NCH >= 1 && NCH <= 32 && (NCH & (NCH - 1)) == 0, "row split");
+    static_assert(ROWS <= 32, "row split");
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int b = mm.m[blockIdx.y];
@@ -233,35 +256,43 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_cluster(ModeMap mm, const d
     W += b * wstride;
     perm += b * pstride;
     extern __shared__ double dyn[];
-    double* Grow = dyn;                                    // ROWS x k
+    double* Srow = dyn;                                    // ROWS x k
     double* Lrow = dyn + (size_t)ROWS * k;                 // ROWS x k
-    __shared__ double lq[KMAX];
+    __shared__ double colbuf[2][KMAX];
     __shared__ double dsh[32];
     __shared__ int act[32], pos[32], slot[32];
+    __shared__ int gact[KMAX], gpos[KMAX];
     __shared__ long long ckey[2][C];
     __shared__ int cidx[2][C];
     __shared__ double cdp[2][C], cnear[C];
     __shared__ int pivs[KMAX];
     __shared__ unsigned char chosen[KMAX];
     __shared__ double red[TC_THREADS / 32];
-    __shared__ double s_rp, s_piv;
-    __shared__ int s_q, s_stop, s_nact;
+    __shared__ double s_rp;
+    __shared__ int s_q, s_stop, s_nact, s_gna;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nloc = rank < k ? (k - rank + C - 1) / C : 0;
     // row i of G = column i (G is symmetric)
     for (int li = warp; li < nloc; li += TC_THREADS / 32) {
         const int i = rank + li * C;
-        for (int c = lane; c < k; c += 32) Grow[li * k + c] = G[(long long)i * ldg + c];
+        for (int c = lane; c < k; c += 32) Srow[li * k + c] = G[(long long)i * ldg + c];
     }
     if (tid < 32) {
         act[tid] = tid;
         pos[tid] = tid;
         slot[tid] = -1;
     }
-    for (int i = tid; i < k; i += TC_THREADS) chosen[i] = 0;
-    if (tid == 0) s_nact = nloc;
+    for (int i = tid; i < k; i += TC_THREADS) {
+        chosen[i] = 0;
+        gact[i] = i;
+        gpos[i] = i;
+    }
+    if (tid == 0) {
+        s_nact = nloc;
+        s_gna = k;
+    }
     __syncthreads();
-    if (tid < nloc) dsh[tid] = Grow[tid * k + rank + tid * C];
+    if (tid < nloc) dsh[tid] = Srow[tid * k + rank + tid * C];
     // largest diagonal of G (every block reads all of it: k values)
     double dmx = 0.0;
     for (int i = tid; i < k; i += TC_THREADS) dmx = fmax(dmx, G[(long long)i * ldg + i]);
@@ -280,7 +311,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_cluster(ModeMap mm, const d
         for (int li = warp; li < nloc; li += TC_THREADS / 32) {
             const int i = rank + li * C;
             for (int c = lane; c < k; c += 32) {
-                const double g = Grow[li * k + c];
+                const double g = Srow[li * k + c];
                 const double ev = (c == i) ? g - 1.0 : g;
                 s = fma(ev, ev, s);
             }
@@ -307,7 +338,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_cluster(ModeMap mm, const d
             for (int li = warp; li < nloc; li += TC_THREADS / 32) {
                 const int j = rank + li * C;
                 for (int t = lane; t < k; t += 32) {
-                    const double g = Grow[li * k + t];
+                    const double g = Srow[li * k + t];
                     W[(long long)t * ldw + j] = t < j ? 0.0 : (t == j ? fma(-0.5, g - 1.0, 1.0) : -g);
                 }
             }
@@ -323,83 +354,75 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_cluster(ModeMap mm, const d
             return;
         }
     }
+    // this block's best active row for a step, sent to every block (warp 0)
+    auto send_candidate = [&](int par) {
+        const int na = s_nact;
+        long long key = LLONG_MIN;
+        int idx = INT_MAX;
+        double dv = 0.0;
+        if (lane < na) {
+            const int li = act[lane];
+            dv = dsh[li];
+            const long long bits = __double_as_longlong(dv);
+            key = pivot ? (bits >= 0 ? bits : -1) : -1;   // unpivoted: every key ties, the index decides
+            idx = rank + li * C;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+            const double d2 = __shfl_xor_sync(0xffffffffu, dv, o);
+            if (k2 > key || (k2 == key && i2 < idx)) {
+                key = k2;
+                idx = i2;
+                dv = d2;
+            }
+        }
+        if (lane < C) {
+            cl.map_shared_rank(&ckey[par][0], lane)[rank] = key;
+            cl.map_shared_rank(&cidx[par][0], lane)[rank] = idx;
+            cl.map_shared_rank(&cdp[par][0], lane)[rank] = dv;
+        }
+    };
+    if (warp == 0) send_candidate(0);
+    cl.sync();
     int m = k;
     for (int t = 0; t < k; ++t) {
         const int par = t & 1;
-        // ---- this block's candidate
+        // ---- the pivot: the best of the C candidates (a shuffle tree in warp 0: the same
+        // maximum, ties to the smaller index, in any order)
         if (warp == 0) {
-            const int na = s_nact;
-            long long key = LLONG_MIN;
-            int idx = INT_MAX;
-            double dv = 0.0;
-            if (lane < na) {
-                const int li = act[lane];
-                dv = dsh[li];
-                const long long bits = __double_as_longlong(dv);
-                key = pivot ? (bits >= 0 ? bits : -1) : -1;
-                idx = rank + li * C;
+            long long kr = LLONG_MIN;
+            int ir = INT_MAX;
+            double dr = 0.0;
+            if (lane < C) {
+                kr = ckey[par][lane];
+                ir = cidx[par][lane];
+                dr = cdp[par][lane];
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-                const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-                const double d2 = __shfl_xor_sync(0xffffffffu, dv, o);
-                if (k2 > key || (k2 == key && i2 < idx)) {
-                    key = k2;
-                    idx = i2;
-                    dv = d2;
+                const long long k2 = __shfl_xor_sync(0xffffffffu, kr, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, ir, o);
+                const double d2 = __shfl_xor_sync(0xffffffffu, dr, o);
+                if (k2 > kr || (k2 == kr && i2 < ir)) {
+                    kr = k2;
+                    ir = i2;
+                    dr = d2;
                 }
-            }
-            if (lane < C) {
-                cl.map_shared_rank(&ckey[par][0], lane)[rank] = key;
-                cl.map_shared_rank(&cidx[par][0], lane)[rank] = idx;
-                cl.map_shared_rank(&cdp[par][0], lane)[rank] = dv;
-            }
-        }
-        cl.sync();
-        // ---- the pivot: without pivoting the row of index t, else the best of the C candidates
-        // (a shuffle tree in warp 0: the same maximum, ties to the smaller index, as any order)
-        if (warp == 0) {
-            int q = t;
-            double dp = 0.0;
-            if (pivot) {
-                long long kr = LLONG_MIN;
-                int ir = INT_MAX;
-                double dr = 0.0;
-                if (lane < C) {
-                    kr = ckey[par][lane];
-                    ir = cidx[par][lane];
-                    dr = cdp[par][lane];
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const long long k2 = __shfl_xor_sync(0xffffffffu, kr, o);
-                    const int i2 = __shfl_xor_sync(0xffffffffu, ir, o);
-                    const double d2 = __shfl_xor_sync(0xffffffffu, dr, o);
-                    if (k2 > kr || (k2 == kr && i2 < ir)) {
-                        kr = k2;
-                        ir = i2;
-                        dr = d2;
-                    }
-                }
-                q = ir;
-                dp = dr;
-            } else {
-                // every key is -1: the smallest active index is t (rows are taken in order)
-                dp = cdp[par][t % C];
             }
             if (lane == 0) {
+                const int q = ir;
+                const double dp = dr;
                 const bool stop = q >= k || !(dp > tol * d0max) || !(dp > 0.0) || !(dp > dfloor);
                 s_stop = stop;
                 s_q = q;
                 if (!stop) {
-                    const double rp = rsqrt(dp);           // one dependent chain instead of sqrt, then 1 / x
-                    const double piv = dp * rp;
-                    s_piv = piv;
+                    const double rp = fast_rsqrt(dp);      // one short chain instead of sqrt, then 1 / x
                     s_rp = rp;
                     pivs[t] = q;
                     chosen[q] = 1;
-                    if (q % C == rank) {               // the owner: L(q, t), and q leaves the active set
+                    if (q % C == rank) {               // the owner: L(q, t), and q leaves the active rows
                         const int lq_ = q / C;
-                        Lrow[lq_ * k + t] = piv;
+                        Lrow[lq_ * k + t] = dp * rp;
                         slot[lq_] = t;
                         const int p0 = pos[lq_], last = act[s_nact - 1];
                         act[p0] = last;
@@ -416,37 +439,45 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_cluster(ModeMap mm, const d
             break;
         }
         const int q = s_q;
-        {
-            const double* src = cl.map_shared_rank(Lrow, q % C) + (size_t)(q / C) * k;
-            for (int s2 = tid; s2 < t; s2 += TC_THREADS) lq[s2] = src[s2];
-        }
-        __syncthreads();
-        // ---- column t for the active rows
-        const int na = s_nact;
         const double rp = s_rp;
-        {
-            const int r = tid / NCH, ch = tid - r * NCH;
-            double acc = 0.0, acc2 = 0.0;
-            int li = 0;
-            if (r < na) {
-                li = act[r];
-                const double* row = Lrow + li * k;
-                int s2 = ch;
-                for (; s2 + NCH < t; s2 += 2 * NCH) {
-                    acc = fma(row[s2], lq[s2], acc);
-                    acc2 = fma(row[s2 + NCH], lq[s2 + NCH], acc2);
+        const int na = s_nact, gna = s_gna;
+        // ---- step t-1's update of the owned active rows over the active columns (q still
+        // among them: its column is read next)
+        if (t > 0) {
+            const double* lc = &colbuf[par ^ 1][0];
+            for (int r = warp; r < na; r += TC_THREADS / 32) {
+                const int li = act[r];
+                const double lit = Lrow[li * k + t - 1];
+                double* row = Srow + li * k;
+                for (int u = lane; u < gna; u += 32) {
+                    const int j = gact[u];
+                    row[j] = fma(-lit, lc[j], row[j]);
                 }
-                if (s2 < t) acc = fma(row[s2], lq[s2], acc);
             }
-            acc += acc2;
-            for (int o = NCH / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (ch == 0 && r < na) {
-                const double lit = (Grow[li * k + q] - acc) * rp;
-                Lrow[li * k + t] = lit;
-                dsh[li] -= lit * lit;
-            }
+            __syncthreads();
+        }
+        // ---- column t of the owned active rows, the new Schur diagonal
+        if (tid < na) {
+            const int li = act[tid];
+            const double lit = Srow[li * k + q] * rp;
+            Lrow[li * k + t] = lit;
+            dsh[li] = fma(-lit, lit, dsh[li]);
         }
         __syncthreads();
+        // ---- send the owned entries of L(:, t) and the next candidate; q leaves the active columns
+        if (tid < na * C) {
+            const int r = tid / C, dst = tid - r * C;
+            const int li = act[r];
+            cl.map_shared_rank(&colbuf[par][0], dst)[rank + li * C] = Lrow[li * k + t];
+        }
+        if (warp == 0) send_candidate(par ^ 1);
+        if (tid == 32) {
+            const int p0 = gpos[q], last = gact[gna - 1];
+            gact[p0] = last;
+            gpos[last] = p0;
+            s_gna = gna - 1;
+        }
+        cl.sync();
     }
     // ---- outputs: the chosen rows of Lt in slot order, the permutation, the counts
     for (int li = warp; li < nloc; li += TC_THREADS / 32) {
@@ -466,7 +497,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_cluster(ModeMap mm, const d
             if (near_out) near_out[b] = 0;
         }
     }
-    cl.sync();                     // no block leaves while a peer could still read its memory
+    cl.sync();                     // no block leaves while a peer could still write its memory
 }
 
 template <int C>

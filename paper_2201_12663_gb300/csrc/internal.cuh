@@ -96,6 +96,42 @@ __device__ inline double block_max(double v, double* red)
     return bcast;
 }
 
+// Short-latency reciprocal and reciprocal square root for serial FP64 chains.  Dependent FP64
+// operations are slow on this part, and the IEEE division and square root are long sequences;
+// these take an FP32 estimate of the exponent-scaled argument (exact scaling by a power of two
+// through the exponent field) and refine it by Newton-Raphson iterations in FP64:
+//   1/d:        y <- y + y (1 - d y)                 (error squares each step)
+//   1/sqrt(s):  y <- y + y (1/2 - (s y / 2) y)       (error squares each step)
+// Two steps take the FP32 estimate (relative error < 2^-22) below 2^-88 before rounding, so the
+// results are within a few units in the last place of the correctly rounded values (checked
+// against CUDA's 1/x and 1/sqrt(x) by rhosvd_selftest_fastmath).  Arguments outside the normal
+// range, zeros, infinities and NaNs take the IEEE operation.
+__device__ __forceinline__ double fast_rcp(double d)
+{
+    const int hi = __double2hiint(d), lo = __double2loint(d);
+    const int be = (hi >> 20) & 0x7FF;
+    if (be < 2 || be > 2044) return 1.0 / d;
+    const double m = __hiloint2double((hi & 0x800FFFFF) | (1023 << 20), lo);      // d 2^(1023 - be), |m| in [1, 2)
+    double y = (double)(1.0f / (float)m);
+    y = fma(y, fma(-m, y, 1.0), y);
+    y = fma(y, fma(-m, y, 1.0), y);
+    return y * __hiloint2double((2046 - be) << 20, 0);                              // times 2^(1023 - be)
+}
+
+__device__ __forceinline__ double fast_rsqrt(double s)
+{
+    const int hi = __double2hiint(s), lo = __double2loint(s);
+    const int be = (hi >> 20) & 0x7FF;
+    if (s <= 0.0 || be < 2 || be > 2044) return 1.0 / sqrt(s);
+    const int e = be - 1023, h = e >> 1;                       // s = m 2^(2h), m in [1, 4)
+    const double m = __hiloint2double((hi & 0x000FFFFF) | ((1023 + e - 2 * h) << 20), lo);
+    double y = (double)rsqrtf((float)m);
+    double hm = 0.5 * m;
+    y = fma(y, fma(-hm * y, y, 0.5), y);
+    y = fma(y, fma(-hm * y, y, 0.5), y);
+    return y * __hiloint2double((1023 - h) << 20, 0);                                // times 2^-h
+}
+
 // Record the first device-side error in the info record.
 __device__ inline void set_status(rhosvd_info* info, int code)
 {
