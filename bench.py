@@ -37,8 +37,8 @@ PRECISIONS = {"mixed": 1, "plain": 0}
 # tensor-core digit-plane products per FP64-class product in the mixed form: 6-digit operands
 # with every pair s + t <= 8 (26); the sketch against a +-1 operand (6); the core with 4-digit
 # operands, pairs s + t <= 5 (10)
-MIXED_PAIRS = {"sketch": 6, "project": 26, "v_hi": 26, "residual": 26, "z_hi": 26, "gram_bbt": 26,
-               "cholqr_gram": 26, "cholqr_apply": 26, "core": 10}
+MIXED_PAIRS = {"sketch": 7, "project": 34, "v_hi": 34, "residual": 34, "z_hi": 34, "gram_bbt": 34,
+               "cholqr_gram": 34, "cholqr_apply": 34, "core": 10}
 # DRAM bytes per launch of a stage's kernel from an ncu capture of the same code (None when the
 # kernel has changed since): profiles/chol_smem_hadamard_n1024_R64x64.md
 NCU_TRAFFIC = {"cholqr_chol": 0.530e6}

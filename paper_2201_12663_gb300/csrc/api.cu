@@ -238,16 +238,16 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0)
         p->ldR = up8(R);
         p->ldn = up8(p->NQ);
         p->ldk = up8(p->KW);
-        p->sU1 = 6LL * p->NQ * p->ldR;
-        p->sU2 = 6LL * R * p->ldn;
+        p->sU1 = (long long)OZ_S64 * p->NQ * p->ldR;
+        p->sU2 = (long long)OZ_S64 * R * p->ldn;
         long long a1 = (long long)R * p->ldk, a2 = (long long)p->KW * p->ldR, a3 = (long long)p->KW * p->ldk;
         a1 = a1 > a2 ? a1 : a2;
-        p->sP1 = 6LL * (a1 > a3 ? a1 : a3);
+        p->sP1 = (long long)OZ_S64 * (a1 > a3 ? a1 : a3);
         long long b1 = (long long)p->KW * p->ldn, b2 = (long long)p->KW * p->ldk, b3 = (long long)p->NQ * p->ldk;
         long long bm = b1 > b2 ? b1 : b2;
         bm = bm > b3 ? bm : b3;
         bm = bm > a2 ? bm : a2;
-        p->sP2 = 6LL * bm;
+        p->sP2 = (long long)OZ_S64 * bm;
         p->o_pU1 = take(sizeof(uint16_t) * 3 * (size_t)p->sU1);
         p->o_pU2 = take(sizeof(uint16_t) * 3 * (size_t)p->sU2);
         p->o_pP1 = take(sizeof(uint16_t) * 3 * (size_t)p->sP1);
@@ -490,7 +490,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 OzSliceArgs sq, sp;
                 memset(&sq, 0, sizeof(sq));
                 memset(&sp, 0, sizeof(sp));
-                sq.S = sp.S = 6;
+                sq.S = sp.S = OZ_S64;
                 OzBatch o1, o2;
                 memset(&o1, 0, sizeof(o1));
                 memset(&o2, 0, sizeof(o2));
@@ -636,7 +636,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 // every digit group is exact, so the Gram keeps FP64-class accuracy
                 OzSliceArgs sg;
                 memset(&sg, 0, sizeof(sg));
-                sg.S = 6;
+                sg.S = OZ_S64;
                 OzBatch ob;
                 memset(&ob, 0, sizeof(ob));
                 ob.nbatch = nsk;
@@ -683,7 +683,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 OzSliceArgs sx, sw;
                 memset(&sx, 0, sizeof(sx));
                 memset(&sw, 0, sizeof(sw));
-                sx.S = sw.S = 6;
+                sx.S = sw.S = OZ_S64;
                 OzBatch ob;
                 memset(&ob, 0, sizeof(ob));
                 ob.nbatch = nsk;
@@ -847,7 +847,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         if (mixed) {
             OzSliceArgs sq;
             memset(&sq, 0, sizeof(sq));
-            sq.S = 6;
+            sq.S = OZ_S64;
             OzBatch ob;
             memset(&ob, 0, sizeof(ob));
             ob.nbatch = 3;
@@ -905,7 +905,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             // M = B B^T on the tensor cores: rows i of B (k = nu, stride KW)
             OzSliceArgs sg;
             memset(&sg, 0, sizeof(sg));
-            sg.S = 6;
+            sg.S = OZ_S64;
             OzBatch ob;
             memset(&ob, 0, sizeof(ob));
             ob.nbatch = 3;
@@ -1021,7 +1021,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             OzSliceArgs sq, sw;
             memset(&sq, 0, sizeof(sq));
             memset(&sw, 0, sizeof(sw));
-            sq.S = sw.S = 6;
+            sq.S = sw.S = OZ_S64;
             OzBatch oz;
             memset(&oz, 0, sizeof(oz));
             oz.nbatch = 3;
@@ -1071,7 +1071,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             OzSliceArgs s1, s2;
             memset(&s1, 0, sizeof(s1));
             memset(&s2, 0, sizeof(s2));
-            s1.S = s2.S = 6;
+            s1.S = s2.S = OZ_S64;
             OzBatch ob;
             memset(&ob, 0, sizeof(ob));
             ob.nbatch = 3;

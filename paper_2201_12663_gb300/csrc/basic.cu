@@ -93,7 +93,7 @@ __global__ void k_terms(const double* norms, const double* xi, int R, double* ke
 // terms (to about one ulp), zero columns for dropped terms; nn2 = ||Un(:, nu)||^2 as stored.
 // u / d is u * (2^-e / f) with d = f 2^e, f in [0.5, 1) (one FP64 multiply an entry; two exact
 // power-of-two steps when 2^-e would leave the range).  With digit planes requested, column nu
-// is also cut into S = 6 planes as operand row nu (k = x) with exponent E_nu from
+// is also cut into OZ_S64 planes as operand row nu (k = x) with exponent E_nu from
 // max |Un(:, nu)| = colmax * scale (the same multiply as the entries, so max < 2^E_nu holds
 // exactly).  One warp per column, grid (ceil(R/8), 3).
 __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long long ustride, double* nn2, NormSlice ns)
@@ -141,11 +141,11 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
             s = fma(v, v, s);
         }
         if (P) {
-            uint16_t dg[6];
-            oz_digits(v, E, 6, dg);
+            uint16_t dg[OZ_S64];
+            oz_digits(v, E, OZ_S64, dg, OZ_W64);
             uint16_t* q = P + (long long)warp * ns.ld[l] + i;
 #pragma unroll
-            for (int t = 0; t < 6; ++t) q[t * ns.pstride[l]] = dg[t];
+            for (int t = 0; t < OZ_S64; ++t) q[t * ns.pstride[l]] = dg[t];
         }
     }
     s = warp_sum(s);
@@ -172,11 +172,11 @@ __global__ void k_slice_t(SliceTArgs a)
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int x = x0 + i, nu = nu0 + threadIdx.x;
         if (x >= rows || nu >= ld) continue;
-        uint16_t dg[6];
-        oz_digits(tile[threadIdx.x][i], a.E0, 6, dg);
+        uint16_t dg[OZ_S64];
+        oz_digits(tile[threadIdx.x][i], a.E0, OZ_S64, dg, OZ_W64);
         uint16_t* q = P + (long long)x * ld + nu;
 #pragma unroll
-        for (int t = 0; t < 6; ++t) q[t * a.pstride[b]] = dg[t];
+        for (int t = 0; t < OZ_S64; ++t) q[t * a.pstride[b]] = dg[t];
     }
 }
 

@@ -4,9 +4,11 @@
 // planes sit in shared memory in the canonical K-major layout without swizzle (8-row x 16-byte
 // core matrices, LBO = 128 B along K, SBO = 512 B along M/N).  One thread issues the
 // tcgen05.mma instructions (kind::f16, BF16 in, FP32 accumulate) for every digit pair (s, t)
-// with s + t <= GMAX into TMEM accumulators, one per group g = s + t.  A group of np pairs is
-// exact while np * 2^16 * (its K since the last readback) < 2^24, so it is read back into
-// double-float registers every 8 / np stages (rounded down to a power of two).  With fewer
+// with s + t <= GMAX into TMEM accumulators, one per group g = s + t.  A group of np pairs of
+// W-bit digits is exact while np * 2^(2W) * (its K since the last readback) < 2^24, so it is read
+// back into double-float registers at that cadence (for the 7-bit FP64-class digits: every 4
+// stages for the largest groups, every 8 for the others; with 8-bit digits the largest groups
+// would need a readback, and a wait for the stage's MMAs, after every stage).  With fewer
 // accumulators than groups, the last one takes the remaining (smallest) groups; it is inexact
 // but read back at the shortest cadence, so its FP32 partial sums never span more than a few
 // stages (the tensor cores' FP32 accumulation drops the bits of each product below the
@@ -94,23 +96,33 @@ __host__ __device__ constexpr int oz_npairs(int SA, int SB, int g)
     return c;
 }
 
-// readback cadence (stages of 32 K) of an exact group of np pairs: np * 2^16 * 32 c <= 2^24
-__host__ __device__ constexpr int oz_cad(int np) { return np <= 1 ? 8 : (np == 2 ? 4 : (np <= 4 ? 2 : 1)); }
+// readback cadence (stages of 32 K) of an exact group of np pairs of W-bit digits: the group's
+// FP32 sum stays exact while np 2^(2W) 32 c <= 2^24, i.e. c <= 2^(19 - 2W) / np; a power of two,
+// at most 8
+__host__ __device__ constexpr int oz_cad(int np, int W)
+{
+    const int lim = (1 << (19 - 2 * W)) / (np > 0 ? np : 1);
+    int c = 1;
+    while (c * 2 <= lim && c * 2 <= 8) c *= 2;
+    return c;
+}
 
 // cadence of accumulator a when accumulators 0 .. NE-1 hold the exact groups g = a + 2 and
 // accumulator NE (if any) the rest, which is read back at the shortest exact cadence
-__host__ __device__ constexpr int oz_acc_cad(int SA, int SB, int NE, int a)
+__host__ __device__ constexpr int oz_acc_cad(int SA, int SB, int NE, int a, int W)
 {
-    if (a < NE) return oz_cad(oz_npairs(SA, SB, a + 2));
+    if (a < NE) return oz_cad(oz_npairs(SA, SB, a + 2), W);
     int m = 8;
-    for (int e = 0; e < NE; ++e) m = oz_cad(oz_npairs(SA, SB, e + 2)) < m ? oz_cad(oz_npairs(SA, SB, e + 2)) : m;
+    for (int e = 0; e < NE; ++e)
+        m = oz_cad(oz_npairs(SA, SB, e + 2), W) < m ? oz_cad(oz_npairs(SA, SB, e + 2), W) : m;
     return m;
 }
 
-__host__ __device__ constexpr bool oz_exact_ok(int SA, int SB, int NE)
+// every exact group fits one stage: np 2^(2W) 32 <= 2^24
+__host__ __device__ constexpr bool oz_exact_ok(int SA, int SB, int NE, int W)
 {
     for (int e = 0; e < NE; ++e)
-        if (oz_npairs(SA, SB, e + 2) > 8) return false;
+        if (oz_npairs(SA, SB, e + 2) > (1 << (19 - 2 * W))) return false;
     return true;
 }
 
@@ -121,7 +133,7 @@ __device__ __forceinline__ int oz_dim(const int* d, int h) { return d ? *d : h; 
 
 }  // namespace
 
-template <int SA, int SB, int GMAX, int ASRC, int BSRC, int EPI, int NT, int NACC>
+template <int SA, int SB, int GMAX, int ASRC, int BSRC, int EPI, int NT, int NACC, int W>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
 {
     constexpr int A_PLANE = OZ_BM * OZ_BK * 2;
@@ -131,11 +143,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
     constexpr int NG = GMAX - 1;                // groups g = 2 .. GMAX
     constexpr int NE = NACC >= NG ? NG : NACC - 1;   // exact accumulators
     constexpr int NU = NACC >= NG ? NG : NACC;       // accumulators in use
-    constexpr int MINCAD = oz_acc_cad(SA, SB, NE, NU - 1) < oz_acc_cad(SA, SB, NE, 0)
-                               ? oz_acc_cad(SA, SB, NE, NU - 1) : oz_acc_cad(SA, SB, NE, 0);
+    constexpr int MINCAD = oz_acc_cad(SA, SB, NE, NU - 1, W) < oz_acc_cad(SA, SB, NE, 0, W)
+                               ? oz_acc_cad(SA, SB, NE, NU - 1, W) : oz_acc_cad(SA, SB, NE, 0, W);
     static_assert(NT % 32 == 0 && NT >= 32 && NU * NT <= 512, "tile: 8-column TMEM loads per thread quarter");
     static_assert(GMAX >= 2 && GMAX <= SA + SB && NACC >= 1 && (NACC >= 2 || GMAX == 2), "groups");
-    static_assert(oz_exact_ok(SA, SB, NE), "an exact group needs at most 8 pairs");
+    static_assert(oz_exact_ok(SA, SB, NE, W), "an exact group must fit one stage");
+    static_assert(W == 7 || W == 8, "digit width");
     const int nsplit = batch.nsplit > 1 ? batch.nsplit : 1;
     const int split = blockIdx.z % nsplit;
     const OzProblem& P = batch.p[blockIdx.z / nsplit];
@@ -204,7 +217,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
                 uint16_t d[8][SA];
                 const int jj = gi % r2, mm = gi / r2;
                 const int Er = (P.kr.e2 && gi < M) ? (int)P.kr.e2[jj] + (int)P.kr.e3[mm] : 0;
-                const float TWO_8S = __int_as_float((127 + 8 * SA - Er) << 23);     // 2^(8 SA - E)
+                const float TWO_8S = __int_as_float((127 + W * SA - Er) << 23);     // 2^(W SA - E)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     long long F = 0;
@@ -216,7 +229,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
                         pe = fmaf(a.x, b.y, fmaf(a.y, b.x, pe));
                         F = __float2ll_rn(ph * TWO_8S) + __float2ll_rn(pe * TWO_8S);
                     }
-                    oz_digits_int(F, SA, d[q]);
+                    oz_digits_int(F, SA, d[q], W);
                 }
 #pragma unroll
                 for (int s = 0; s < SA; ++s) {
@@ -296,7 +309,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
                 for (int t = 1; t <= SB; ++t) {
                     if (s + t > GMAX) continue;
                     const int a = (s + t - 2) < NE ? (s + t - 2) : NE;
-                    const int cad = oz_acc_cad(SA, SB, NE, a);
+                    const int cad = oz_acc_cad(SA, SB, NE, a, W);
                     // the first MMA of a group after its readback overwrites the accumulator
                     const uint32_t acc = ((kt % cad) != 0 || started[a]) ? 1u : 0u;
                     started[a] = true;
@@ -322,7 +335,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int a = NU - 1; a >= 0; --a) {
-                const int cad = oz_acc_cad(SA, SB, NE, a);
+                const int cad = oz_acc_cad(SA, SB, NE, a, W);
                 if (last || (kt % cad) == cad - 1) readback(tmem + (uint32_t)(a * NT));
             }
         }
@@ -338,10 +351,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
     for (int c = 0; c < NQ; ++c) {
         const int col = j0 + cg * NQ + c;
         if (row >= M || col >= N) continue;
-        const int eb = BSRC == OZ_B_PLANES ? (P.B.exps ? (int)P.B.exps[col] : P.B.exp0) : 8;
-        // 2^(ea + eb - 16) built from its exponent bits (ea + eb in [-252, 254]: always normal),
-        // so the scaling is one exact multiply instead of an ldexp call on the FP64 pipe
-        const double sc = __hiloint2double((ea + eb - 16 + 1023) << 20, 0);
+        const int eb = BSRC == OZ_B_PLANES ? (P.B.exps ? (int)P.B.exps[col] : P.B.exp0) : W;
+        // x = 2^(E - W) sum_s plane_s, so a product carries 2^(ea + eb - 2W), built from its
+        // exponent bits (ea + eb in [-252, 254]: always normal): one exact multiply instead of an
+        // ldexp call on the FP64 pipe
+        const double sc = __hiloint2double((ea + eb - 2 * W + 1023) << 20, 0);
         const double v = ((double)hi[c] + (double)lo[c]) * sc;
         if (EPI == OZ_EPI_STORE) {
             Cout[(long long)row * crs + (long long)col * ccs] = v;
@@ -499,7 +513,7 @@ __global__ void __launch_bounds__(256) k_oz_slice_tile(OzSliceArgs a)
         if (i >= rows) break;
         const int E = a.exps[b] ? (int)a.exps[b][i] : a.exp0;
         uint16_t d[S];
-        oz_digits(T[r][kk], E, S, d);
+        oz_digits(T[r][kk], E, S, d, S == OZ_S64 ? OZ_W64 : 8);
         uint16_t* q = P + (long long)i * ld + k;
 #pragma unroll
         for (int s2 = 0; s2 < S; ++s2) q[s2 * ps] = d[s2];
@@ -553,7 +567,7 @@ int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st)
     }
     dim3 grid((ldmax + OZ_ST_K - 1) / OZ_ST_K, (rmax + OZ_ST_R - 1) / OZ_ST_R, nb);
     switch (a.S) {
-    case 6: k_oz_slice_tile<6><<<grid, 256, 0, st>>>(a); break;
+    case OZ_S64: k_oz_slice_tile<OZ_S64><<<grid, 256, 0, st>>>(a); break;
     case 4: k_oz_slice_tile<4><<<grid, 256, 0, st>>>(a); break;
     case 1: k_oz_slice_tile<1><<<grid, 256, 0, st>>>(a); break;
     default: return RHOSVD_ERR_INVALID_ARG;
@@ -562,7 +576,7 @@ int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st)
     return 0;
 }
 
-template <int SA, int SB, int GMAX, int ASRC, int BSRC, int EPI, int NT, int NACC>
+template <int SA, int SB, int GMAX, int ASRC, int BSRC, int EPI, int NT, int NACC, int W>
 static int run_oz(const OzBatch& b, cudaStream_t st)
 {
     int Mh = 0, Nh = 0;
@@ -575,7 +589,7 @@ static int run_oz(const OzBatch& b, cudaStream_t st)
     constexpr int SMEM = 2 * STAGE;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_ozgemm<SA, SB, GMAX, ASRC, BSRC, EPI, NT, NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_ozgemm<SA, SB, GMAX, ASRC, BSRC, EPI, NT, NACC, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SMEM) != cudaSuccess)
             return RHOSVD_ERR_CUDA;
         attr = true;
@@ -583,7 +597,7 @@ static int run_oz(const OzBatch& b, cudaStream_t st)
     const int nsplit = b.nsplit > 1 ? b.nsplit : 1;
     if (nsplit > 1 && EPI != OZ_EPI_STORE) return RHOSVD_ERR_INVALID_ARG;
     dim3 grid((Mh + OZ_BM - 1) / OZ_BM, (Nh + NT - 1) / NT, b.nbatch * nsplit);
-    k_ozgemm<SA, SB, GMAX, ASRC, BSRC, EPI, NT, NACC><<<grid, OZ_THREADS, SMEM, st>>>(b);
+    k_ozgemm<SA, SB, GMAX, ASRC, BSRC, EPI, NT, NACC, W><<<grid, OZ_THREADS, SMEM, st>>>(b);
     RH_CHECK_LAUNCH();
     if (nsplit > 1) {
         const long long mn = (long long)Mh * Nh;
@@ -597,11 +611,13 @@ static int run_oz(const OzBatch& b, cudaStream_t st)
 int launch_ozgemm(const OzBatch& b, OzKind kind, cudaStream_t st)
 {
     switch (kind) {
-    case OZ_F64_STORE: return run_oz<6, 6, 8, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_STORE, OZ_NT6, 7>(b, st);
-    case OZ_F64_RESID: return run_oz<6, 6, 8, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_RESID, OZ_NT6, 7>(b, st);
-    case OZ_SKETCH: return run_oz<6, 1, 7, OZ_A_PLANES, OZ_B_SIGN, OZ_EPI_STORE, 96, 5>(b, st);
-    case OZ_CORE: return run_oz<4, 4, 5, OZ_A_KR, OZ_B_PLANES, OZ_EPI_STORE, 160, 3>(b, st);
-    case OZ_BF16: return run_oz<1, 1, 2, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_STORE, 128, 1>(b, st);
+    case OZ_F64_STORE:
+        return run_oz<OZ_S64, OZ_S64, 9, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_STORE, OZ_NT6, 8, OZ_W64>(b, st);
+    case OZ_F64_RESID:
+        return run_oz<OZ_S64, OZ_S64, 9, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_RESID, OZ_NT6, 8, OZ_W64>(b, st);
+    case OZ_SKETCH: return run_oz<OZ_S64, 1, 8, OZ_A_PLANES, OZ_B_SIGN, OZ_EPI_STORE, 96, 5, OZ_W64>(b, st);
+    case OZ_CORE: return run_oz<4, 4, 5, OZ_A_KR, OZ_B_PLANES, OZ_EPI_STORE, 160, 3, 8>(b, st);
+    case OZ_BF16: return run_oz<1, 1, 2, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_STORE, 128, 1, 8>(b, st);
     }
     return RHOSVD_ERR_INVALID_ARG;
 }

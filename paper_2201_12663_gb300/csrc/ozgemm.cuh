@@ -22,7 +22,7 @@ namespace rh {
 constexpr int OZ_BM = 128;      // rows of a CTA tile (TMEM lanes)
 constexpr int OZ_BK = 32;       // K per pipeline stage
 constexpr int OZ_THREADS = 512; // 16 warps
-constexpr int OZ_NT6 = 64;      // tile width of the S = 6 products (seven 64-column accumulators)
+constexpr int OZ_NT6 = 64;      // tile width of the FP64-class products (eight 64-column accumulators)
 
 // Operand given as digit planes in global memory: plane p, operand row i, k at
 // base[p * pstride + i * ld + k] (bf16 bit patterns), ld a multiple of 8.
@@ -87,42 +87,50 @@ enum OzASrc { OZ_A_PLANES = 0, OZ_A_KR = 1 };
 enum OzBSrc { OZ_B_PLANES = 0, OZ_B_SIGN = 1 };
 enum OzEpi { OZ_EPI_STORE = 0, OZ_EPI_RESID = 1 };
 
-// S digit planes (bf16 bit patterns) of the signed integer F = +-round(|x| 2^(8S - E)).
-// Digit s (s = 1..S) is d 2^(-8(s-1)) with d < 2^8 (s > 1) or d <= 2^8 (s = 1): at most eight
-// significant bits and a power-of-two scale, so the float d * 2^(-8(s-1)) is exact and its bf16
+// FP64-class operands are cut into OZ_S64 digits of OZ_W64 bits (49 bits in all); the
+// Khatri-Rao core and the plain BF16 product keep 8-bit digits.  A product of two W-bit digits
+// is below 2^(2W): with W = 7 a group of up to 7 digit pairs stays exact in FP32 for 4 stages of
+// 32 (np 2^14 128 < 2^24), so the accumulators are read back every 4 stages instead of every one.
+constexpr int OZ_S64 = 7, OZ_W64 = 7;
+
+// S digit planes (bf16 bit patterns) of the signed integer F = +-round(|x| 2^(W S - E)).
+// Digit s (s = 1..S) is d 2^(-W(s-1)) with d < 2^W (s > 1) or d <= 2^W (s = 1): at most eight
+// significant bits and a power-of-two scale, so the float d * 2^(-W(s-1)) is exact and its bf16
 // pattern is the float's upper half (no rounding); the sign is the top bit.
-__device__ __forceinline__ void oz_digits_int(long long F, int S, uint16_t* out)
+__device__ __forceinline__ void oz_digits_int(long long F, int S, uint16_t* out, int W = 8)
 {
     const bool neg = F < 0;
     const unsigned long long A = (unsigned long long)(neg ? -F : F);
     const unsigned sgn = neg ? 0x8000u : 0u;
     for (int s = 1; s <= S; ++s) {
-        const int d = (int)((A >> (8 * (S - s))) & (s == 1 ? 0x1FFull : 0xFFull));
-        const float v = (float)d * __int_as_float((127 - 8 * (s - 1)) << 23);
+        const unsigned long long mask = s == 1 ? ((2ull << W) - 1) : ((1ull << W) - 1);
+        const int d = (int)((A >> (W * (S - s))) & mask);
+        const float v = (float)d * __int_as_float((127 - W * (s - 1)) << 23);
         out[s - 1] = d ? (uint16_t)((__float_as_uint(v) >> 16) | sgn) : (uint16_t)0;
     }
 }
 
-// digit planes of one FP64 value for exponent E (|x| < 2^E): writes S bf16 bit patterns
-__device__ __forceinline__ void oz_digits(double x, int E, int S, uint16_t* out)
+// digit planes of one FP64 value for exponent E (|x| < 2^E): writes S bf16 bit patterns of
+// W-bit digits
+__device__ __forceinline__ void oz_digits(double x, int E, int S, uint16_t* out, int W = 8)
 {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const int ef = (int)((bits >> 52) & 0x7FF);
     unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
     int e;
     if (ef == 0) { e = -1022; } else { m |= 0x10000000000000ull; e = ef - 1023; }
-    // |x| = m 2^(e-52); F = round(|x| 2^(8S - E)) = round(m 2^(e - 52 + 8S - E))
-    const int sh = 52 - (e + 8 * S - E);
+    // |x| = m 2^(e-52); F = round(|x| 2^(W S - E)) = round(m 2^(e - 52 + W S - E))
+    const int sh = 52 - (e + W * S - E);
     unsigned long long F;
     if (m == 0 || sh >= 64) {
         F = 0;
     } else if (sh <= 0) {
-        F = 1ull << (8 * S);     // |x| >= 2^E does not occur for a valid exponent; saturate
+        F = 1ull << (W * S);     // |x| >= 2^E does not occur for a valid exponent; saturate
     } else {
         F = (m + (1ull << (sh - 1))) >> sh;
     }
     const long long Fs = (long long)F;
-    oz_digits_int((bits >> 63) ? -Fs : Fs, S, out);
+    oz_digits_int((bits >> 63) ? -Fs : Fs, S, out, W);
 }
 
 // Digit planes of an operand: operand row i < rows, k < K reads X[i * rs + k * cs] (times
