@@ -40,8 +40,8 @@ PRECISIONS = {"mixed": 1, "plain": 0}
 MIXED_PAIRS = {"sketch": 7, "project": 34, "v_hi": 34, "residual": 34, "z_hi": 34, "gram_bbt": 34,
                "cholqr_gram": 34, "cholqr_apply": 34, "core": 10}
 # DRAM bytes per launch of a stage's kernel from an ncu capture of the same code (None when the
-# kernel has changed since): profiles/chol_smem_hadamard_n1024_R64x64.md
-NCU_TRAFFIC = {"cholqr_chol": 0.530e6}
+# kernel has changed since): profiles/chol_cluster_hadamard_n1024_R64x64.md
+NCU_TRAFFIC = {"cholqr_chol": 0.951e6}
 METRIC = "RHOSVD reductions/s at stated rel. err: mixed/learned vs FP64 plain, 1×GB300"
 UNIT = "reductions/s"
 FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (CUDA-core and tensor) rate
@@ -562,7 +562,7 @@ def run_ours(args):
                     "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(name),
                     "peak_source": "GB300 nominal FP64 rate 1.25 TFLOP/s (of fallback: MEASURED_PEAKS.json has "
                                    "no FP64 entry)",
-                    "note": "sequential factorisation in one block per mode: latency and FP64 issue of one SM",
+                    "note": "sequential pivot steps on a 16-block cluster per mode: bound by the per-step exchange and cluster barrier, not by FP64 issue or memory",
                     "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": fl}
         else:
             roof = {"bound": "alu", "kernel": name, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

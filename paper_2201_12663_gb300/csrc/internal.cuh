@@ -42,10 +42,16 @@ __host__ __device__ inline uint64_t splitmix64(uint64_t x)
     return x ^ (x >> 31);
 }
 
-__host__ __device__ inline double rademacher(uint64_t seed, int mode, long long nu, int c)
+// the sign as a bit (1: +1), for producers that must stay off the FP64 pipe
+__host__ __device__ inline int rademacher_bit(uint64_t seed, int mode, long long nu, int c)
 {
     uint64_t h = splitmix64(seed ^ ((uint64_t)mode << 56) ^ ((uint64_t)nu * 4ull + (uint64_t)(c >> 6)));
-    return ((h >> (c & 63)) & 1ull) ? 1.0 : -1.0;
+    return (int)((h >> (c & 63)) & 1ull);
+}
+
+__host__ __device__ inline double rademacher(uint64_t seed, int mode, long long nu, int c)
+{
+    return rademacher_bit(seed, mode, nu, c) ? 1.0 : -1.0;
 }
 
 __device__ inline double warp_sum(double v)

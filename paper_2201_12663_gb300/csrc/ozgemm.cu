@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
                 for (int q = 0; q < 8; ++q) {
                     d[q] = 0;
                     if (gj < N && gk + q < kbase + K)
-                        d[q] = rademacher(P.seed, P.mode, gk + q, gj) > 0.0 ? (uint16_t)0x3F80 : (uint16_t)0xBF80;
+                        d[q] = rademacher_bit(P.seed, P.mode, gk + q, gj) ? (uint16_t)0x3F80 : (uint16_t)0xBF80;
                 }
                 uint4 v;
                 v.x = (uint32_t)d[0] | ((uint32_t)d[1] << 16);
