@@ -457,6 +457,7 @@ __global__ void k_copy2d(CopyArgs a)
 // stationary qd  L D L^T - mu I = L+ D+ L+^T (top down, s_i), progressive qd
 // L D L^T - mu I = U- D- U-^T (bottom up, p_i), gamma_r = s_r + p_r + mu, twist at
 // argmin |gamma_r|; z_r = 1, z_i = -L+_i z_{i+1} above, z_{i+1} = -U-_i z_i below.
+// One thread per vector; grid (ceil(rmax / 16), nmodes), 16 threads a block.
 __global__ void k_eigvecs(ModeMap mm, const double* D, const double* Lo, const double* mu, int vstride, const int* dk,
                           const DevState* st, double* W, long long wstride, int ldw)
 {
@@ -519,29 +520,66 @@ __global__ void k_eigvecs(ModeMap mm, const double* D, const double* Lo, const d
 }
 
 // ------------------------------------------------------------------ back-transformation
-// y <- H_0 H_1 ... H_{k-3} y for each of the r columns (one warp per column); H_j uses the
-// reflector stored in A(j+1:k, j) and tau[j].
+// y <- H_0 H_1 ... H_{k-3} y for each of the r columns (one warp per column, 4 a block); H_j
+// uses the reflector stored in A(j+1:k, j) and tau[j].  The column lives in registers (lane l
+// holds entries l, l + 32, ...), and the reflectors are staged in shared memory 16 at a time by
+// the whole block, so a reflector costs one warp reduction instead of an L2 round trip.
+// grid: (ceil(KMAX / 4), nmodes), block 128.
+constexpr int BT_CH = 16;
+
 __global__ void k_backtransform(ModeMap mm, const double* A, long long astride, int lda, const double* tau, int vstride,
                                 const int* dk, const DevState* st, double* W, long long wstride, int ldw)
 {
     const int b = mm.m[blockIdx.y];
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k = dk[b];
     const int r = st->rhi[b];
-    if (warp >= r) return;
+    const int v0 = blockIdx.x * 4;
+    if (v0 >= r) return;
     A += b * astride;
     tau += b * vstride;
-    double* y = W + b * wstride + (long long)warp * ldw;
-    for (int j = k - 3; j >= 0; --j) {
-        const double t = tau[j];
-        if (t == 0.0) continue;
-        const double* vcol = A + (long long)j * lda;
-        double dot = 0.0;
-        for (int i = j + 1 + lane; i < k; i += 32) dot += vcol[i] * y[i];
-        dot = warp_sum(dot) * t;
-        for (int i = j + 1 + lane; i < k; i += 32) y[i] -= dot * vcol[i];
-        __syncwarp();
+    const int vec = v0 + warp;
+    const bool live = vec < r;
+    double* y = W + b * wstride + (long long)vec * ldw;
+    constexpr int NQ = KMAX / 32;
+    const int kp = (k + 31) & ~31;
+    double yr[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int i = lane + 32 * q;
+        yr[q] = (live && i < k) ? y[i] : 0.0;
+    }
+    __shared__ double Vs[BT_CH][KMAX];
+    __shared__ double ts[BT_CH];
+    for (int jhi = k - 3; jhi >= 0; jhi -= BT_CH) {
+        const int nc = jhi + 1 < BT_CH ? jhi + 1 : BT_CH;       // reflectors jhi, jhi-1, .. jhi-nc+1
+        __syncthreads();                                      // the previous chunk is applied
+        for (int idx = tid; idx < nc * kp; idx += blockDim.x) {
+            const int c = idx / kp, i = idx - c * kp, j = jhi - c;
+            Vs[c][i] = (i > j && i < k) ? A[(long long)j * lda + i] : 0.0;
+        }
+        if (tid < nc) ts[tid] = tau[jhi - tid];
+        __syncthreads();
+        if (!live) continue;
+        for (int c = 0; c < nc; ++c) {
+            const double t = ts[c];
+            if (t == 0.0) continue;
+            double dot = 0.0;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (32 * q < kp) dot = fma(Vs[c][lane + 32 * q], yr[q], dot);
+            dot = warp_sum(dot) * t;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (32 * q < kp) yr[q] = fma(-dot, Vs[c][lane + 32 * q], yr[q]);
+        }
+    }
+    if (live) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int i = lane + 32 * q;
+            if (i < k) y[i] = yr[q];
+        }
     }
 }
 
@@ -643,8 +681,11 @@ int launch_copy2d(const double* src, long long sstride, const int lds[3], double
 int launch_eigvecs(ModeMap mm, const double* D, const double* Lo, const double* mu, int vstride, const int* dk,
                    const DevState* s, double* W, long long wstride, int ldw, int rmax, int nb, cudaStream_t st)
 {
-    dim3 grid((rmax + 63) / 64, nb);
-    k_eigvecs<<<grid, 64, 0, st>>>(mm, D, Lo, mu, vstride, dk, s, W, wstride, ldw);
+    // 16 vectors a block: each vector is a serial chain, and a warp-wide FP64 instruction costs the
+    // SM's FP64 pipe 16 cycles, so the vectors are spread over many SMs rather than packed
+    constexpr int VPB = 16;
+    dim3 grid((rmax + VPB - 1) / VPB, nb);
+    k_eigvecs<<<grid, VPB, 0, st>>>(mm, D, Lo, mu, vstride, dk, s, W, wstride, ldw);
     RH_CHECK_LAUNCH();
     return 0;
 }
