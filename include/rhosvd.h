@@ -259,6 +259,43 @@ int rhosvd_proj_target(int n, const double* Q, const double* Z, int ldz, int r, 
  * the network's output for that mode (FP32). */
 int rhosvd_proposal_basis(int n, const double* QT, const float* Y, double* Q0, void* stream);
 
+/* ---------------------------------------------------------------- Tucker-to-canonical transform
+ * (Sec. 2.4, Remark rem_can_red, eqs. T2C_slice, T2C_SVD, beta_R)
+ *
+ * rhosvd_t2c turns a Tucker tensor A = beta x_1 Z1 x_2 Z2 x_3 Z3 into a canonical one by the
+ * SVDs of the core's slices along the third mode, B_m = beta(:, :, m):
+ *   A_R = sum_m sum_{k <= p_m} sigma_k(B_m) (Z1 u_k) (x) (Z2 v_k) (x) Z3(:, m),
+ * keeping the singular values above delta = eps ||beta||_F / (r3 sqrt(min(r1, r2))) (the
+ * remark's eps / r^{3/2} for an r x r x r core, eps relative), so ||beta - beta_R||_F <=
+ * eps ||beta||_F and, for orthonormal Z_l, ||A - A_R||_F is the same.  Canonical rank
+ * R = sum_m p_m <= r3 min(r1, r2).  The C2C reduction is rhosvd_c2t followed by rhosvd_t2c.
+ *
+ *   t          the Tucker tensor (device pointers; Z_l column-major, n_l x r_l, ld ldz[l] >= n_l;
+ *              beta r1 x r2 x r3 with entry (i, j, m) at beta[i + r1 (j + r2 m)], as rhosvd_c2t
+ *              writes it); r1 r2 <= RHOSVD_T2C_SLICE_MAX and r1, r2 <= 1024 (a slice is
+ *              factorised in one block's shared memory)
+ *   eps        relative accuracy, >= 0 (0 keeps every nonzero singular value)
+ *   R_max      capacity of the outputs (columns); U[l] n_l x R_max with leading dimension
+ *              ldu[l] >= n_l, xi R_max (device, caller-owned)
+ *   R_out      device int: the canonical rank R (also when it exceeds R_max)
+ *   p_out      device int[r3] (may be NULL): p_m per slice
+ *   status     device int: RHOSVD_OK, or RHOSVD_ERR_RANK_OVERFLOW when R > R_max (then U and xi
+ *              are not written)
+ *   workspace  device, >= rhosvd_t2c_workspace_size(t) bytes, 256-byte aligned
+ * Host-side checks return RHOSVD_ERR_INVALID_ARG / RHOSVD_ERR_WORKSPACE; asynchronous on
+ * `stream`.  Each slice's SVD is a one-sided Jacobi (bounded to 40 sweeps). */
+#define RHOSVD_T2C_SLICE_MAX 25600
+typedef struct {
+    int n[3];
+    int r[3];
+    const double* Z[3];
+    int ldz[3];
+    const double* beta;
+} rhosvd_tucker_in;
+size_t rhosvd_t2c_workspace_size(const rhosvd_tucker_in* t);
+int rhosvd_t2c(const rhosvd_tucker_in* t, double eps, int R_max, double* const U[3], const int ldu[3], double* xi,
+               int* R_out, int* p_out, int* status, void* workspace, size_t bytes, void* stream);
+
 /* ---------------------------------------------------------------- numerics self-test (no paper
  * counterpart: test support)
  *

@@ -60,6 +60,11 @@ class rhosvd_tucker(_c.Structure):
                 ("xi_out", _c.c_void_p), ("info", _c.c_void_p)]
 
 
+class rhosvd_tucker_in(_c.Structure):
+    _fields_ = [("n", _c.c_int * 3), ("r", _c.c_int * 3), ("Z", _c.c_void_p * 3), ("ldz", _c.c_int * 3),
+                ("beta", _c.c_void_p)]
+
+
 class RhosvdError(RuntimeError):
     def __init__(self, code, where=""):
         self.code = code
@@ -142,6 +147,12 @@ def load(build_if_missing: bool = False):
                                          _c.c_void_p]
         L.rhosvd_proposal_basis.restype = _c.c_int
         L.rhosvd_proposal_basis.argtypes = [_c.c_int, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_t2c_workspace_size.restype = _c.c_size_t
+        L.rhosvd_t2c_workspace_size.argtypes = [_c.POINTER(rhosvd_tucker_in)]
+        L.rhosvd_t2c.restype = _c.c_int
+        L.rhosvd_t2c.argtypes = [_c.POINTER(rhosvd_tucker_in), _c.c_double, _c.c_int, _c.c_void_p * 3, _c.c_int * 3,
+                                 _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_size_t,
+                                 _c.c_void_p]
         L.rhosvd_selftest_fastmath.restype = _c.c_int
         L.rhosvd_selftest_fastmath.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p]
         L.rhosvd_launch_count.restype = _c.c_longlong
@@ -221,6 +232,69 @@ def rhosvd_strerror(code: int) -> str:
         return load().rhosvd_strerror(int(code)).decode()
     except Exception:                                  # library unavailable
         return f"status {code}"
+
+
+@dataclass
+class CanonicalResult:
+    """Device outputs of one rhosvd_t2c call: factors U[l] (n_l x R_max, column-major), weights
+    xi, and device ints R (canonical rank), status, p (per slice)."""
+    U: list
+    xi: object
+    R_dev: object
+    status_dev: object
+    p: object
+
+    def rank(self):
+        """Synchronise the current stream; (R, status)."""
+        torch = _torch()
+        torch.cuda.current_stream().synchronize()
+        return int(self.R_dev.item()), int(self.status_dev.item())
+
+
+def rhosvd_t2c(Z, beta, eps, R_max, workspace=None, stream=None) -> CanonicalResult:
+    """Tucker-to-canonical transform.  Z: three column-major float64 CUDA matrices (n_l x r_l);
+    beta: float64 CUDA tensor of r1*r2*r3 entries, (i, j, m) at i + r1 (j + r2 m)."""
+    torch = _torch()
+    L = load()
+    t = rhosvd_tucker_in()
+    r = [int(z.shape[1]) for z in Z]
+    for l in range(3):
+        t.n[l] = int(Z[l].shape[0])
+        t.r[l] = r[l]
+        t.Z[l] = Z[l].data_ptr()
+        t.ldz[l] = int(Z[l].stride(1)) if r[l] > 1 else max(int(Z[l].shape[0]), 1)
+        if r[l] > 0 and Z[l].stride(0) != 1:
+            raise ValueError("Z must be column-major")
+    t.beta = beta.data_ptr() if beta.numel() else None
+    need = int(L.rhosvd_t2c_workspace_size(_c.byref(t)))
+    if need == 0:
+        raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_t2c_workspace_size")
+    dev = Z[0].device
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    cap = max(int(R_max), 0)
+    U = [torch.empty(max(cap, 1), t.n[l], dtype=torch.float64, device=dev).t() for l in range(3)]
+    xi = torch.empty(max(cap, 1), dtype=torch.float64, device=dev)
+    R_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+    st_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+    p = torch.zeros(max(r[2], 1), dtype=torch.int32, device=dev)
+    ptrs = (_c.c_void_p * 3)(*[U[l].data_ptr() for l in range(3)])
+    ldu = (_c.c_int * 3)(*[max(t.n[l], 1) for l in range(3)])
+    rc = L.rhosvd_t2c(_c.byref(t), float(eps), cap, ptrs, ldu, _c.c_void_p(xi.data_ptr()),
+                      _c.c_void_p(R_dev.data_ptr()), _c.c_void_p(p.data_ptr()), _c.c_void_p(st_dev.data_ptr()),
+                      _c.c_void_p(workspace.data_ptr()), need, _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_t2c")
+    return CanonicalResult(U=U, xi=xi, R_dev=R_dev, status_dev=st_dev, p=p)
+
+
+def rhosvd_c2c(U, xi, eps_tucker, eps_t2c, R_max, **c2t_opts):
+    """Canonical-to-canonical reduction: rhosvd_c2t, then rhosvd_t2c of its Tucker tensor.
+    Returns (CanonicalResult, TuckerResult)."""
+    tk = rhosvd_c2t(U, xi, eps=eps_tucker, **c2t_opts)
+    r, beta, Z = tk.tucker()
+    flat = tk.beta[: r[0] * r[1] * r[2]]
+    return rhosvd_t2c(Z, flat, eps_t2c, R_max), tk
 
 
 def rhosvd_selftest_fastmath(x, stream=None):

@@ -150,6 +150,26 @@ def learned_instances(count: int, first_seed: int, n: int = 1024, R_range=(2000,
     return out
 
 
+def tucker_tensor(n, r, seed, decay=0.15):
+    """A seeded Tucker tensor (Z, beta) for the Tucker-to-canonical transform: Z_l (n_l x r_l)
+    with orthonormal columns (QR of Gaussian matrices), and a core whose mode-3 slice m is
+    A_m diag(s_m) B_m^T + noise, A_m, B_m random orthonormal, s_m(k) = exp(-decay k - 0.05 m)
+    scaled by a uniform [0.5, 2] factor; noise 1e-3 of the smallest s_m.  Draw order with
+    PCG64(seed): Z_1, Z_2, Z_3, then per slice A_m, B_m, the factor, the noise.
+    Returns (Z list of column-major float64 arrays, beta (r1, r2, r3) array)."""
+    g = np.random.default_rng(seed)
+    Z = [np.asfortranarray(np.linalg.qr(g.standard_normal((n[l], r[l])))[0]) for l in range(3)]
+    r1, r2, r3 = r
+    q = min(r1, r2)
+    beta = np.zeros((r1, r2, r3))
+    for m in range(r3):
+        A = np.linalg.qr(g.standard_normal((r1, q)))[0]
+        B = np.linalg.qr(g.standard_normal((r2, q)))[0]
+        s = np.exp(-decay * np.arange(q) - 0.05 * m) * g.uniform(0.5, 2.0)
+        beta[:, :, m] = (A * s) @ B.T + 1e-3 * s[-1] * g.standard_normal((r1, r2))
+    return Z, np.asfortranarray(beta)
+
+
 # Named workloads (sizes, distributions and thresholds).
 CONFIGS = {
     "gauss_n128_R200": dict(n=128, R=200, seed=0, eps=1e-6),
