@@ -397,6 +397,49 @@ def learned_leg(P, dev, n_train, n_eval, precision):
             "timing": "host wall clock with synchronisation per reduction (the path decides on the host)"}
 
 
+T2C = dict(workload="t2c_of_the_bench_reduction", eps=1e-5, source="Tucker tensor of the timed reduction (mixed form)")
+
+
+def t2c_leg(P, out, steps, warmup):
+    """Tucker-to-canonical transform of the bench reduction's Tucker tensor at eps = 1e-5 (the
+    paper's T2C threshold): CUDA-event time per transform, the canonical rank, and the oracle
+    (numpy slice SVDs) timed on the host for the same core.  Algorithmic FP64 work per slice:
+    the Golub-Kahan count 4 r1 r2^2 + 8 r2^3 for singular values and left vectors, plus
+    2 (n1 r1 + r1 r2 + n2 r2) per kept triple for the factors."""
+    import numpy as np
+    import torch
+    from oracle import t2c as ot
+    r, beta3, Z = out.tucker()
+    flat = out.beta[: r[0] * r[1] * r[2]]
+    cap = r[2] * min(r[0], r[1])
+    res = P.rhosvd_t2c(Z, flat, T2C["eps"], cap)
+    for _ in range(max(warmup, 1)):
+        res = P.rhosvd_t2c(Z, flat, T2C["eps"], cap, out=res)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        P.rhosvd_t2c(Z, flat, T2C["eps"], cap, out=res)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    R, st = res.rank()
+    p = res.p[: r[2]].cpu().numpy()
+    n = [int(z.shape[0]) for z in Z]
+    fl = r[2] * (4.0 * r[0] * r[1] ** 2 + 8.0 * r[1] ** 3) + R * 2.0 * (n[0] * r[0] + r[0] * r[1] + n[1] * r[1])
+    bh = beta3.cpu().numpy()
+    t0 = time.perf_counter()
+    ref = ot.t2c_core(bh, T2C["eps"])
+    t_or = time.perf_counter() - t0
+    return {**T2C, "core": r, "ms_per_t2c": ms, "canonical_rank": R, "status": st,
+            "rank_bound": cap, "p_min_median_max": [int(p.min()), int(np.median(p)), int(p.max())],
+            "oracle_rank": ref["R"], "oracle_s": t_or, "oracle_cores": 1,
+            "roofline": {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "work": "Golub-Kahan count per slice + factor GEMVs",
+                         "peak_source": "GB300 nominal FP64 rate (of fallback)"}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -589,6 +632,8 @@ def run_ours(args):
         line["batched"] = batched_leg(P, dev, args.steps, args.warmup, main_prec)
     if args.learned_train > 0:
         line["learned"] = learned_leg(P, dev, args.learned_train, args.learned_eval, main_prec)
+    if not args.no_t2c:
+        line["t2c"] = t2c_leg(P, out, max(3, args.steps // 2), args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample()
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -608,6 +653,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload leg")
+    ap.add_argument("--no-t2c", action="store_true", help="skip the Tucker-to-canonical leg")
     ap.add_argument("--precision", choices=["mixed", "plain"], default="mixed")
     ap.add_argument("--learned-train", type=int, default=600,
                     help="training instances of the learned-proposal leg (0 skips it; the full workload is 20000)")

@@ -283,7 +283,9 @@ int rhosvd_proposal_basis(int n, const double* QT, const float* Y, double* Q0, v
  *              are not written)
  *   workspace  device, >= rhosvd_t2c_workspace_size(t) bytes, 256-byte aligned
  * Host-side checks return RHOSVD_ERR_INVALID_ARG / RHOSVD_ERR_WORKSPACE; asynchronous on
- * `stream`.  Each slice's SVD is a one-sided Jacobi (bounded to 40 sweeps). */
+ * `stream`.  Each slice's SVD: a Householder QR with column pivoting, then one-sided Jacobi on
+ * the rows of R (bounded to 40 sweeps; about 8 on the bench's core), kept left vectors
+ * re-orthonormalised. */
 #define RHOSVD_T2C_SLICE_MAX 25600
 typedef struct {
     int n[3];

@@ -251,7 +251,7 @@ class CanonicalResult:
         return int(self.R_dev.item()), int(self.status_dev.item())
 
 
-def rhosvd_t2c(Z, beta, eps, R_max, workspace=None, stream=None) -> CanonicalResult:
+def rhosvd_t2c(Z, beta, eps, R_max, workspace=None, stream=None, out=None) -> CanonicalResult:
     """Tucker-to-canonical transform.  Z: three column-major float64 CUDA matrices (n_l x r_l);
     beta: float64 CUDA tensor of r1*r2*r3 entries, (i, j, m) at i + r1 (j + r2 m)."""
     torch = _torch()
@@ -273,11 +273,14 @@ def rhosvd_t2c(Z, beta, eps, R_max, workspace=None, stream=None) -> CanonicalRes
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
     cap = max(int(R_max), 0)
-    U = [torch.empty(max(cap, 1), t.n[l], dtype=torch.float64, device=dev).t() for l in range(3)]
-    xi = torch.empty(max(cap, 1), dtype=torch.float64, device=dev)
-    R_dev = torch.zeros(1, dtype=torch.int32, device=dev)
-    st_dev = torch.zeros(1, dtype=torch.int32, device=dev)
-    p = torch.zeros(max(r[2], 1), dtype=torch.int32, device=dev)
+    if out is not None:           # reuse the buffers of an earlier call (same shapes, capacity >= R_max)
+        U, xi, R_dev, st_dev, p = out.U, out.xi, out.R_dev, out.status_dev, out.p
+    else:
+        U = [torch.empty(max(cap, 1), t.n[l], dtype=torch.float64, device=dev).t() for l in range(3)]
+        xi = torch.empty(max(cap, 1), dtype=torch.float64, device=dev)
+        R_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+        st_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+        p = torch.zeros(max(r[2], 1), dtype=torch.int32, device=dev)
     ptrs = (_c.c_void_p * 3)(*[U[l].data_ptr() for l in range(3)])
     ldu = (_c.c_int * 3)(*[max(t.n[l], 1) for l in range(3)])
     rc = L.rhosvd_t2c(_c.byref(t), float(eps), cap, ptrs, ldu, _c.c_void_p(xi.data_ptr()),

@@ -41,16 +41,19 @@ __global__ void k_t2c_norm(T2cDims d, double* delta)
     }
 }
 
-// One-sided Jacobi (Hestenes) on the slice B_m (r1 x r2, column-major in shared memory): each
-// pair of columns (a, b) is rotated so that a^T b = 0, t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
-// zeta = (b^T b - a^T a) / (2 a^T b), until every pair is orthogonal to 1e-14 of ||a|| ||b|| (or
-// T2C_SWEEPS sweeps); the columns end as u_k sigma_k.  Pairs by the round-robin (circle)
-// schedule over r2 rounded up to even positions (position 0 fixed, the others rotated by the
-// round), a warp per pair, a block barrier per round.  Then sigma_k = ||column k||, ranked
-// descending (ties to the smaller index), p_m = #{sigma > delta}; the kept u_k = column / sigma_k
-// go to uws (r1 x r2 per slice, ranked order) and every sigma to sws (r2 per slice).
+// SVD of the slice B_m (r1 x r2, column-major in shared memory) by preconditioned one-sided
+// Jacobi: a Householder QR with column pivoting B P = Q R (in place), then rotations of pairs of
+// rows of R (a^T b = 0 with t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b^T b - a^T a) /
+// (2 a^T b)) until every pair is orthogonal to 64 r1 u of ||a|| ||b|| (or T2C_SWEEPS sweeps; the
+// count is written to sweeps[m]).  The pivoting grades R's rows, so few sweeps are needed (about
+// 28 without it on the bench's core slices).  The rows end as sigma_k times the right singular
+// vectors of B P.  Pairs by the round-robin (circle) schedule over q = min(r1, r2) rounded up to
+// even positions, a warp per pair, a block barrier per round.  Then sigma_k = ||row k||, ranked
+// descending (ties to the smaller index), p_m = #{sigma > delta}; the kept left vectors
+// u_k = B v_k / sigma_k (v_k = P row_k / sigma_k, from the slice in global memory) go to uws
+// (r1 x r2 per slice, ranked order) and every sigma to sws (r2 per slice).
 __global__ void __launch_bounds__(T2C_THREADS) k_t2c_slice(T2cDims d, const double* delta, double* uws, double* sws,
-                                                         int* p_out)
+                                                         int* p_out, int* sweeps)
 {
     const int m = blockIdx.x;
     const int r1 = d.r[0], r2 = d.r[1];
@@ -60,54 +63,160 @@ __global__ void __launch_bounds__(T2C_THREADS) k_t2c_slice(T2cDims d, const doub
     double* Bs = t2c_smem;                               // r1 x r2
     double* sg = Bs + (size_t)r1 * r2;                   // r2
     int* rk = reinterpret_cast<int*>(sg + r2);           // r2
+    int* perm = rk + r2;                                 // r2: the column pivoting
     __shared__ int s_rot, s_p;
     const double* Bg = d.beta + (long long)m * r1 * r2;
-    for (int e = tid; e < r1 * r2; e += T2C_THREADS) Bs[e] = Bg[e];
+    double f2 = 0.0;
+    for (int e = tid; e < r1 * r2; e += T2C_THREADS) {
+        const double x = Bg[e];
+        Bs[e] = x;
+        f2 = fma(x, x, f2);
+    }
     if (tid == 0) s_p = 0;
+    __shared__ double red[T2C_THREADS / 32];
+    f2 = block_sum(f2, red);
+    // convergence: |a^T b| <= tol ||a|| ||b||, tol a few times r1 u (below that the rounding of
+    // the dot products decides).  A pair with a column below 1e-6 delta (or 1e-17 ||B_m||) is not
+    // rotated: such a column moves no singular value above delta by more than ~1e-12 delta,
+    // and noise-level columns would otherwise keep rotating among themselves
+    const double tol = 64.0 * r1 * DBL_EPSILON;
+    const double dl0 = delta[0];
+    const double tiny = fmax(1e-34 * f2, 1e-12 * dl0 * dl0);
+    // ---- QR with column pivoting (Householder, in place): B P = Q R; R's rows are graded,
+    // which makes the Jacobi sweeps below converge in a few sweeps (preconditioned one-sided
+    // Jacobi).  Column norms of the trailing rows are recomputed at every step.
+    const int q = r1 < r2 ? r1 : r2;
+    __shared__ int s_piv;
+    __shared__ double s_tau, s_alpha;
+    for (int c = tid; c < r2; c += T2C_THREADS) perm[c] = c;
     __syncthreads();
-    const int np = (r2 + 1) & ~1;
+    for (int j = 0; j < q; ++j) {
+        for (int c = j + warp; c < r2; c += NW) {
+            const double* cc = Bs + (size_t)c * r1;
+            double ss = 0.0;
+            for (int i = j + lane; i < r1; i += 32) ss = fma(cc[i], cc[i], ss);
+            ss = warp_sum(ss);
+            if (lane == 0) sg[c] = ss;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double bv = -1.0;
+            int bi = r2;
+            for (int c = j + lane; c < r2; c += 32)
+                if (sg[c] > bv) { bv = sg[c]; bi = c; }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
+            }
+            if (lane == 0) s_piv = bi;
+        }
+        __syncthreads();
+        const int pv = s_piv;
+        if (pv != j) {
+            double* cj = Bs + (size_t)j * r1;
+            double* cp = Bs + (size_t)pv * r1;
+            for (int i = tid; i < r1; i += T2C_THREADS) {
+                const double x = cj[i];
+                cj[i] = cp[i];
+                cp[i] = x;
+            }
+            if (tid == 0) {
+                const int t0 = perm[j];
+                perm[j] = perm[pv];
+                perm[pv] = t0;
+                const double x = sg[j];
+                sg[j] = sg[pv];
+                sg[pv] = x;
+            }
+        }
+        __syncthreads();
+        double* cj = Bs + (size_t)j * r1;
+        if (tid == 0) {
+            const double x0 = cj[j], n2 = sg[j];
+            double tau = 0.0, alpha = x0;
+            if (n2 > 0.0) {
+                const double xn = sqrt(n2);
+                alpha = x0 >= 0.0 ? -xn : xn;
+                const double v0 = x0 - alpha;
+                tau = 2.0 / (n2 - x0 * x0 + v0 * v0);
+                cj[j] = v0;                          // the reflector v = x - alpha e_1, in place
+            }
+            s_tau = tau;
+            s_alpha = alpha;
+        }
+        __syncthreads();
+        const double tau = s_tau;
+        if (tau != 0.0) {
+            for (int c = j + 1 + warp; c < r2; c += NW) {
+                double* cc = Bs + (size_t)c * r1;
+                double w = 0.0;
+                for (int i = j + lane; i < r1; i += 32) w = fma(cj[i], cc[i], w);
+                w = warp_sum(w) * tau;
+                for (int i = j + lane; i < r1; i += 32) cc[i] = fma(-w, cj[i], cc[i]);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) cj[j] = s_alpha;               // R(j, j)
+        for (int i = j + 1 + tid; i < r1; i += T2C_THREADS) cj[i] = 0.0;
+        __syncthreads();
+    }
+    // ---- one-sided Jacobi on the q rows of R (row i: entries (i, c) at Bs[i + r1 c], c < r2):
+    // rotate row pairs until orthogonal; the rows end as sigma_k times the right singular
+    // vectors of B P
+    const int np = (q + 1) & ~1;
+    int nsw = 0;
     for (int sweep = 0; sweep < T2C_SWEEPS && np >= 2; ++sweep) {
+        nsw = sweep + 1;
         if (tid == 0) s_rot = 0;
+        // row norms, recomputed each sweep and updated by the rotations within it
+        // (a'^T a' = a^T a - t a^T b, b'^T b' = b^T b + t a^T b): one dot product a pair
+        for (int k = warp; k < q; k += NW) {
+            double ss = 0.0;
+            for (int c = lane; c < r2; c += 32) {
+                const double x = Bs[k + (size_t)r1 * c];
+                ss = fma(x, x, ss);
+            }
+            ss = warp_sum(ss);
+            if (lane == 0) sg[k] = ss;
+        }
         __syncthreads();
         for (int t = 0; t < np - 1; ++t) {
             for (int pp = warp; pp < np / 2; pp += NW) {
                 const int q2 = np - 1 - pp;
                 const int a = pp == 0 ? 0 : 1 + (pp - 1 + t) % (np - 1);
                 const int b = 1 + (q2 - 1 + t) % (np - 1);
-                if (a >= r2 || b >= r2) continue;                   // the padding position
-                double* ca = Bs + (size_t)a * r1;
-                double* cb = Bs + (size_t)b * r1;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = lane; i < r1; i += 32) {
-                    const double x = ca[i], y = cb[i];
-                    al = fma(x, x, al);
-                    be = fma(y, y, be);
-                    ga = fma(x, y, ga);
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    al += __shfl_xor_sync(0xffffffffu, al, o);
-                    be += __shfl_xor_sync(0xffffffffu, be, o);
-                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
-                }
-                double c = 1.0, sn = 0.0;
+                if (a >= q || b >= q) continue;                    // the padding position
+                const double al = sg[a], be = sg[b];
+                double ga = 0.0;
+                for (int c = lane; c < r2; c += 32) ga = fma(Bs[a + (size_t)r1 * c], Bs[b + (size_t)r1 * c], ga);
+                ga = warp_sum(ga);
+                double cs = 1.0, sn = 0.0;
                 int rot = 0;
-                if (lane == 0 && ga != 0.0 && fabs(ga) > 1e-14 * sqrt(al * be)) {
-                    const double zeta = (be - al) / (2.0 * ga);
-                    const double az = fabs(zeta);
-                    const double root = az > 1e100 ? az : sqrt(fma(zeta, zeta, 1.0));
-                    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (az + root);
-                    c = 1.0 / sqrt(fma(tt, tt, 1.0));
-                    sn = c * tt;
+                if (lane == 0 && ga != 0.0 && al > tiny && be > tiny && fabs(ga) > tol * sqrt(al * be)) {
+                    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) = sign(d h) |h| / (|d| + sqrt(d^2 + h^2))
+                    // with h = 2 a^T b, d = b^T b - a^T a: one reciprocal square root and one
+                    // reciprocal on the short-latency helpers (few FP64 instructions)
+                    const double h = 2.0 * ga, dd = be - al;
+                    const double qq = fma(dd, dd, h * h);
+                    const double root = qq * fast_rsqrt(qq);
+                    const double tt = ((dd >= 0.0) == (h >= 0.0) ? fabs(h) : -fabs(h)) * fast_rcp(fabs(dd) + root);
+                    cs = fast_rsqrt(fma(tt, tt, 1.0));
+                    sn = cs * tt;
                     rot = 1;
+                    sg[a] = fma(-tt, ga, al);
+                    sg[b] = fma(tt, ga, be);
                 }
                 rot = __shfl_sync(0xffffffffu, rot, 0);
                 if (rot) {
-                    c = __shfl_sync(0xffffffffu, c, 0);
+                    cs = __shfl_sync(0xffffffffu, cs, 0);
                     sn = __shfl_sync(0xffffffffu, sn, 0);
-                    for (int i = lane; i < r1; i += 32) {
-                        const double x = ca[i], y = cb[i];
-                        ca[i] = fma(c, x, -sn * y);
-                        cb[i] = fma(sn, x, c * y);
+                    for (int c = lane; c < r2; c += 32) {
+                        double* xa = Bs + a + (size_t)r1 * c;
+                        double* xb = Bs + b + (size_t)r1 * c;
+                        const double x = *xa, y = *xb;
+                        *xa = fma(cs, x, -sn * y);
+                        *xb = fma(sn, x, cs * y);
                     }
                     if (lane == 0) s_rot = 1;
                 }
@@ -118,15 +227,18 @@ __global__ void __launch_bounds__(T2C_THREADS) k_t2c_slice(T2cDims d, const doub
         __syncthreads();                                  // every thread has read s_rot
         if (!any) break;
     }
-    // singular values, their descending ranks, the count above delta
+    // singular values (row norms), their descending ranks, the count above delta
     const double dl = delta[0];
-    for (int k = warp; k < r2; k += NW) {
-        const double* ck = Bs + (size_t)k * r1;
+    for (int k = warp; k < q; k += NW) {
         double ss = 0.0;
-        for (int i = lane; i < r1; i += 32) ss = fma(ck[i], ck[i], ss);
+        for (int c = lane; c < r2; c += 32) {
+            const double x = Bs[k + (size_t)r1 * c];
+            ss = fma(x, x, ss);
+        }
         ss = warp_sum(ss);
         if (lane == 0) sg[k] = sqrt(ss);
     }
+    for (int k = q + tid; k < r2; k += T2C_THREADS) sg[k] = 0.0;   // B has at most q nonzero values
     __syncthreads();
     for (int k = tid; k < r2; k += T2C_THREADS) {
         const double v = sg[k];
@@ -138,14 +250,59 @@ __global__ void __launch_bounds__(T2C_THREADS) k_t2c_slice(T2cDims d, const doub
     __syncthreads();
     const int p = s_p;
     for (int k = tid; k < r2; k += T2C_THREADS) sws[(long long)m * r2 + rk[k]] = sg[k];
-    for (int k = warp; k < r2; k += NW) {
+    // left vectors u = B v / sigma with v = P row / sigma: u = sum_c B(:, perm[c]) row(c) / sigma^2,
+    // from the slice as it came in (global memory)
+    for (int k = warp; k < q; k += NW) {
         if (rk[k] >= p) continue;
-        const double inv = 1.0 / sg[k];
-        const double* ck = Bs + (size_t)k * r1;
+        const double inv2 = 1.0 / (sg[k] * sg[k]);
         double* uk = uws + ((long long)m * r2 + rk[k]) * r1;
-        for (int i = lane; i < r1; i += 32) uk[i] = ck[i] * inv;
+        for (int i = lane; i < r1; i += 32) {
+            double acc = 0.0;
+            for (int c = 0; c < r2; ++c) acc = fma(Bg[i + (long long)r1 * perm[c]], Bs[k + (size_t)r1 * c], acc);
+            uk[i] = acc * inv2;
+        }
     }
-    if (tid == 0) p_out[m] = p;
+    // Re-orthonormalise the kept u in descending order (classical Gram-Schmidt, two passes).
+    // u = B v / sigma carries an error in v along a larger singular direction j multiplied by
+    // sigma_j / sigma_k, but that error lies in the span of the larger kept vectors, which the
+    // projection removes; beta_R = U_p U_p^T B_m then only needs U_p to span the right space.
+    __syncthreads();                                  // uws of this slice written by the block
+    double* Us = Bs;                                  // p x r1, u_k at Us + k r1 (Bs is free now)
+    const double* ug = uws + (long long)m * r2 * r1;
+    for (int e = tid; e < p * r1; e += T2C_THREADS) Us[e] = ug[e];
+    __syncthreads();
+    __shared__ double red2[T2C_THREADS / 32];
+    for (int k = 0; k < p; ++k) {
+        double* uk = Us + (size_t)k * r1;
+        for (int pass = 0; pass < 2 && k > 0; ++pass) {
+            for (int j = warp; j < k; j += NW) {
+                const double* uj = Us + (size_t)j * r1;
+                double dd = 0.0;
+                for (int i = lane; i < r1; i += 32) dd = fma(uj[i], uk[i], dd);
+                dd = warp_sum(dd);
+                if (lane == 0) sg[j] = dd;
+            }
+            __syncthreads();
+            for (int i = tid; i < r1; i += T2C_THREADS) {
+                double acc = 0.0;
+                for (int j = 0; j < k; ++j) acc = fma(sg[j], Us[(size_t)j * r1 + i], acc);
+                uk[i] -= acc;
+            }
+            __syncthreads();
+        }
+        double nn = 0.0;
+        for (int i = tid; i < r1; i += T2C_THREADS) nn = fma(uk[i], uk[i], nn);
+        nn = block_sum(nn, red2);
+        const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+        for (int i = tid; i < r1; i += T2C_THREADS) uk[i] *= inv;
+        __syncthreads();
+    }
+    double* uw = uws + (long long)m * r2 * r1;
+    for (int e = tid; e < p * r1; e += T2C_THREADS) uw[e] = Us[e];
+    if (tid == 0) {
+        p_out[m] = p;
+        sweeps[m] = nsw;
+    }
 }
 
 // Exclusive offsets of the kept triples per slice, the total rank R, and the capacity check
@@ -229,7 +386,7 @@ __global__ void k_t2c_empty(int* R_out, int* status)
 namespace {
 
 struct T2cPlan {
-    size_t o_delta, o_p, o_offs, o_sws, o_uws, total;
+    size_t o_delta, o_p, o_offs, o_sws, o_uws, o_sweeps, total;
 };
 
 int t2c_plan(const rhosvd_tucker_in* t, T2cPlan* pl)
@@ -246,6 +403,7 @@ int t2c_plan(const rhosvd_tucker_in* t, T2cPlan* pl)
     pl->o_offs = take(sizeof(int) * (r3 > 0 ? r3 : 1));
     pl->o_sws = take(sizeof(double) * (r2 * r3 > 0 ? r2 * r3 : 1));
     pl->o_uws = take(sizeof(double) * (r1 * r2 * r3 > 0 ? r1 * r2 * r3 : 1));
+    pl->o_sweeps = take(sizeof(int) * (r3 > 0 ? r3 : 1));
     pl->total = o;
     return 0;
 }
@@ -299,15 +457,15 @@ extern "C" int rhosvd_t2c(const rhosvd_tucker_in* t, double eps, int R_max, doub
     double* uws = (double*)(ws + pl.o_uws);
     rh::k_t2c_norm<<<1, 1024, 0, st>>>(d, delta);
     rh::count_launch();
-    const size_t smem = sizeof(double) * ((size_t)r1 * r2 + r2) + sizeof(int) * r2;
+    const size_t smem = sizeof(double) * ((size_t)r1 * r2 + r2) + sizeof(int) * 2 * r2;
     static bool attr = false;
     if (!attr) {
-        const size_t smax = sizeof(double) * ((size_t)RHOSVD_T2C_SLICE_MAX + rh::KMAX_T2C_R) + sizeof(int) * rh::KMAX_T2C_R;
+        const size_t smax = sizeof(double) * ((size_t)RHOSVD_T2C_SLICE_MAX + rh::KMAX_T2C_R) + sizeof(int) * 2 * rh::KMAX_T2C_R;
         if (cudaFuncSetAttribute(rh::k_t2c_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax) != cudaSuccess)
             return RHOSVD_ERR_CUDA;
         attr = true;
     }
-    rh::k_t2c_slice<<<r3, rh::T2C_THREADS, smem, st>>>(d, delta, uws, sws, p);
+    rh::k_t2c_slice<<<r3, rh::T2C_THREADS, smem, st>>>(d, delta, uws, sws, p, (int*)(ws + pl.o_sweeps));
     rh::count_launch();
     rh::k_t2c_offsets<<<1, 32, 0, st>>>(p, r3, R_max, offs, R_out, status);
     rh::count_launch();
