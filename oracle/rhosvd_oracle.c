@@ -139,7 +139,9 @@ int orc_householder_r(int m, int n, double* A, int lda, double* Rout)
  * c = 1/sqrt(1+t^2), s = c t.  A pair counts as orthogonal when |gamma| <= tol sqrt(alpha beta),
  * tol = m u.  A column whose norm is <= m u ||A||_F is numerically zero (its singular value is
  * below what FP64 resolves in A) and is not rotated; without this rule rotations among such
- * noise-level columns never settle.
+ * noise-level columns never settle.  Its singular value is reported as exactly 0 and its left
+ * vector as a zero column: the noise left in it is not orthogonal to the other columns, so it
+ * is no singular vector, and an epsilon-rank taken with eps = 0 must not count it.
  * Output: sigma (n values, descending) and Z (m x n, column i <-> sigma_i; zero column
  * for sigma_i = 0).  A is overwritten.  Returns sweeps used, or ORC_ERR_NOTCONV.
  */
@@ -184,7 +186,11 @@ int orc_jacobi_left(int m, int n, double* A, double* sigma, double* Z, int max_s
     int* idx = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     double* s = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     if (!idx || !s) { free(idx); free(s); return ORC_ERR_NOMEM; }
-    for (int j = 0; j < n; ++j) { idx[j] = j; s[j] = orc_col_norm(m, A + (size_t)j * m); }
+    for (int j = 0; j < n; ++j) {
+        idx[j] = j;
+        s[j] = orc_col_norm(m, A + (size_t)j * m);
+        if (s[j] * s[j] <= negligible) s[j] = 0.0;          /* numerically zero column */
+    }
     for (int a = 0; a < n; ++a) {
         int best = a;
         for (int b = a + 1; b < n; ++b) if (s[idx[b]] > s[idx[best]]) best = b;

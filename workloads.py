@@ -170,6 +170,29 @@ def tucker_tensor(n, r, seed, decay=0.15):
     return Z, np.asfortranarray(beta)
 
 
+def newton_kernel(n: int = 257, b: float = 10.0, M: int = 9, h: float = 0.7,
+                  long_range: bool = False) -> CP:
+    """The discretised Newton kernel 1/|x| as the R = 2M+1 term canonical tensor P_R of the
+    sinc quadrature (Sec. 4.1, eqs. laplace, sinc_Newt, Laplace_Newton, galten_int,
+    sinc_general): t_k = e^{k h}, p_k = (2/sqrt(pi)) h e^{k h}, k = -M..M, and the factor
+    columns b_i(t_k) = cell average of exp(-t_k^2 x^2) over cell i of the n-cell grid on [-b, b]
+    (piecewise-constant basis; with n odd the middle cell is centred on the singularity):
+        b_i(t) = sqrt(pi) / (2 t h_x) [erf(t (x_i + h_x/2)) - erf(t (x_i - h_x/2))].
+    All three modes share one factor matrix; the weights are xi_k = p_k.  long_range keeps the
+    terms with t_k <= 1 (k <= 0, eq. RS_repres): R_l = M + 1.  No random draws."""
+    from scipy.special import erf
+    x = grid(n, b)
+    hx = 2.0 * b / n
+    k = np.arange(-M, (0 if long_range else M) + 1, dtype=np.float64)
+    t = np.exp(k * h)
+    p = (2.0 / math.sqrt(math.pi)) * h * t
+    lo = (x - hx / 2)[:, None] * t[None, :]
+    hi = (x + hx / 2)[:, None] * t[None, :]
+    B = np.asfortranarray(math.sqrt(math.pi) / (2.0 * hx * t[None, :]) * (erf(hi) - erf(lo)))
+    return CP(U=[B, B.copy(order="F"), B.copy(order="F")], xi=p.astype(np.float64),
+              meta=dict(kind="newton_kernel", n=n, b=b, M=M, h=h, long_range=long_range))
+
+
 # Named workloads (sizes, distributions and thresholds).
 CONFIGS = {
     "gauss_n128_R200": dict(n=128, R=200, seed=0, eps=1e-6),
