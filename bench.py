@@ -440,6 +440,72 @@ def t2c_leg(P, out, steps, warmup):
                          "peak_source": "GB300 nominal FP64 rate (of fallback)"}}
 
 
+POLY = dict(workload="newton_cube_n257_eps1e-5", n=257, eps_tucker=1e-5, eps_t2c=1e-5,
+            kernel="sinc Newton kernel R=19 (t_k = e^{0.7k}, k=-9..9), long-range part R_l=10 (k<=0)",
+            paper_soft={"full": {"R_in": 6859, "tucker": 13, "canonical": 122},
+                        "long_range": {"R_in": 1000, "tucker": 8, "canonical": 58}})
+
+
+def poly_leg(P, steps, warmup, precision):
+    """The cube P^(3) = P (.) P (.) P of the discretised Newton kernel at n = 257, eps = 1e-5, as the
+    paper's Sec. 5 example: directly (two Hadamard products to rank 19^3 = 6859, or 10^3 for the
+    long-range part, then one C2C) and by the Horner scheme (coefficients 0, 0, 0, 1: a reduction
+    after every product).  Time per cube (CUDA events around the whole call, which synchronises
+    for the ranks), the ranks, and the oracle timed on the host for the same inputs."""
+    import numpy as np
+    import torch
+    import workloads
+    from oracle import horner as oh
+    out = {**POLY}
+    for name, lr in (("full", False), ("long_range", True)):
+        cp = workloads.newton_kernel(n=POLY["n"], long_range=lr)
+        U = [P.to_device_factor(u) for u in cp.U]
+        x = torch.from_numpy(cp.xi).cuda()
+
+        def direct():
+            U2, x2 = P.rhosvd_cp_hadamard(U, x, U, x)
+            U3, x3 = P.rhosvd_cp_hadamard(U2, x2, U, x)
+            return P.rhosvd_c2c(U3, x3, POLY["eps_tucker"], POLY["eps_t2c"], R_max=4000, r_max=64,
+                                precision=PRECISIONS[precision])
+
+        def horner():
+            return P.rhosvd_cp_horner(U, x, [0, 0, 0, 1], POLY["eps_tucker"], POLY["eps_t2c"], R_max=2000,
+                                      r_max=64, precision=PRECISIONS[precision])
+
+        rec = {}
+        for tag, fn in (("direct", direct), ("horner", horner)):
+            for _ in range(max(warmup, 1)):
+                res = fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                res = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            if tag == "direct":
+                can, tk = res
+                R, st = can.rank()
+                info = tk.info()
+                rec[tag] = {"ms": ms, "R_in": cp.R ** 3, "tucker": [info.r[l] for l in range(3)], "canonical": R,
+                            "status": st}
+            else:
+                rec[tag] = {"ms": ms, "canonical": res.R,
+                            "steps": [{"R_in": s_["R_in"], "tucker": s_["r"], "R": s_["R"]} for s_ in res.steps]}
+        t0 = time.perf_counter()
+        od = oh.power_direct(cp.U, cp.xi, 3, POLY["eps_tucker"], POLY["eps_t2c"])
+        t_d = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ohr = oh.horner(cp.U, cp.xi, [0, 0, 0, 1], POLY["eps_tucker"], POLY["eps_t2c"])
+        t_h = time.perf_counter() - t0
+        rec["oracle"] = {"direct_s": t_d, "tucker": od["tucker"]["ranks"], "canonical": od["R"], "horner_s": t_h,
+                         "horner_canonical": ohr["R"], "cores": 1}
+        rec["speedup_vs_oracle"] = {"direct": t_d * 1e3 / rec["direct"]["ms"], "horner": t_h * 1e3 / rec["horner"]["ms"]}
+        out[name] = rec
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -634,6 +700,8 @@ def run_ours(args):
         line["learned"] = learned_leg(P, dev, args.learned_train, args.learned_eval, main_prec)
     if not args.no_t2c:
         line["t2c"] = t2c_leg(P, out, max(3, args.steps // 2), args.warmup)
+    if not args.no_poly:
+        line["poly"] = poly_leg(P, max(3, args.steps // 2), args.warmup, main_prec)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample()
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -654,6 +722,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--no-t2c", action="store_true", help="skip the Tucker-to-canonical leg")
+    ap.add_argument("--no-poly", action="store_true", help="skip the Newton-cube / Horner leg")
     ap.add_argument("--precision", choices=["mixed", "plain"], default="mixed")
     ap.add_argument("--learned-train", type=int, default=600,
                     help="training instances of the learned-proposal leg (0 skips it; the full workload is 20000)")

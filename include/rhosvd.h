@@ -65,7 +65,9 @@ typedef struct rhosvd_cp {
 typedef struct rhosvd_opts {
     double eps;             /* relative Frobenius threshold per mode: r_l is the smallest r
                                with sum_{k>r} sigma_{l,k}^2 <= eps^2 sum_k sigma_{l,k}^2
-                               (the epsilon-threshold of Thm. 2.3)                        */
+                               (the epsilon-threshold of Thm. 2.3); energy at or below the
+                               FP64 resolution (n_l u)^2 sum_k sigma_{l,k}^2 counts as zero,
+                               so eps = 0 keeps every direction FP64 resolves             */
     int ranks[3];           /* > 0: fixed r_l = min(ranks[l], rank bound); 0: use eps     */
     int r_max;              /* capacity of the outputs; 1 <= r_max <= RHOSVD_K_MAX        */
     int oversample;         /* sketch columns beyond r_max (k = r_max + oversample)       */
@@ -297,6 +299,50 @@ typedef struct {
 size_t rhosvd_t2c_workspace_size(const rhosvd_tucker_in* t);
 int rhosvd_t2c(const rhosvd_tucker_in* t, double eps, int R_max, double* const U[3], const int ldu[3], double* xi,
                int* R_out, int* p_out, int* status, void* workspace, size_t bytes, void* stream);
+
+/* ---------------------------------------------------------------- polynomials of a canonical tensor
+ * (Sec. 5: the tensor-valued polynomial P(A) = a_0 I + a_1 A + ... + a_n A^n of a reference
+ * tensor, products taken entrywise, evaluated by the Horner scheme with the RHOSVD)
+ *
+ * rhosvd_cp_horner sets Y_n = a_n I (I the all-ones tensor, a rank-one term) and, for k = n-1
+ * down to 0,
+ *     Y_k = C2C( A (.) Y_{k+1} + a_k I ),
+ * (.) the Hadamard product in rhosvd_cp_hadamard's term order (term i + R_A j), the constant
+ * appended as the last term (left out when a_k = 0), and C2C = rhosvd_c2t with `opts` followed by
+ * rhosvd_t2c with eps_t2c: one product and one reduction per degree.  Trailing zero coefficients
+ * are dropped (the degree is that of the last nonzero a_k; the zero polynomial gives R = 0, a
+ * constant gives the rank-one a_0 I without a reduction).  With exact reductions Y_0 = P(A);
+ * otherwise Y_0 - P(A) = sum_k A^k (.) E_k, E_k the error of reduction k.
+ *
+ *   A          the reference tensor (device factors and weights, as for rhosvd_c2t)
+ *   coeffs     host array a_0 .. a_{ncoeffs-1}, finite; ncoeffs >= 1
+ *   opts       options of every RHOSVD; r_max^2 <= RHOSVD_T2C_SLICE_MAX
+ *   eps_t2c    relative accuracy of every T2C, >= 0
+ *   R_max      canonical capacity: every Y_k must have rank <= R_max (R_max >= 1)
+ *   U_out, ldu, xi_out  device, caller-owned: U_out[l] n_l x R_max (ld ldu[l] >= n_l), xi_out R_max
+ *              values; they hold each Y_k in turn and the result Y_0 at the end
+ *   R_out      host int: the rank of Y_0 (columns 0 .. R_out-1 of U_out)
+ *   steps      host array of ncoeffs - 1 records (may be NULL), one per reduction in the order
+ *              k = n-1 .. 0: the rank R_in entering it, the Tucker ranks r, the canonical rank R
+ *              and the step's status
+ *   workspace  device, >= rhosvd_cp_horner_workspace_size(A, ncoeffs, opts, R_max) bytes, 256-byte
+ *              aligned (it holds the product of rank R_A R_max + 1 and the RHOSVD and T2C scratch)
+ * Returns RHOSVD_OK or the first error: INVALID_ARG, WORKSPACE or CUDA from the host checks, or
+ * the device status of a reduction (RANK_OVERFLOW when a Tucker rank exceeds r_max or a canonical
+ * rank exceeds R_max, NOT_CONVERGED, NONFINITE, SKETCH, TIMEOUT), with the records up to the
+ * failing step filled.  The ranks of each step size the next launches, so the call synchronises
+ * `stream` twice per degree and returns with the stream idle. */
+typedef struct rhosvd_horner_step {
+    int k;                  /* the coefficient index of this step                          */
+    int R_in;               /* rank of A (.) Y_{k+1} + a_k I                               */
+    int r[3];               /* Tucker ranks of its RHOSVD                                  */
+    int R;                  /* canonical rank of Y_k after T2C                             */
+    int status;             /* RHOSVD_OK or the step's device status                       */
+} rhosvd_horner_step;
+size_t rhosvd_cp_horner_workspace_size(const rhosvd_cp* A, int ncoeffs, const rhosvd_opts* opts, int R_max);
+int rhosvd_cp_horner(const rhosvd_cp* A, const double* coeffs, int ncoeffs, const rhosvd_opts* opts,
+                     double eps_t2c, int R_max, double* const U_out[3], const int ldu[3], double* xi_out,
+                     int* R_out, rhosvd_horner_step* steps, void* workspace, size_t bytes, void* stream);
 
 /* ---------------------------------------------------------------- numerics self-test (no paper
  * counterpart: test support)

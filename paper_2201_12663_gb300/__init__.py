@@ -65,6 +65,10 @@ class rhosvd_tucker_in(_c.Structure):
                 ("beta", _c.c_void_p)]
 
 
+class rhosvd_horner_step(_c.Structure):
+    _fields_ = [("k", _c.c_int), ("R_in", _c.c_int), ("r", _c.c_int * 3), ("R", _c.c_int), ("status", _c.c_int)]
+
+
 class RhosvdError(RuntimeError):
     def __init__(self, code, where=""):
         self.code = code
@@ -153,6 +157,14 @@ def load(build_if_missing: bool = False):
         L.rhosvd_t2c.argtypes = [_c.POINTER(rhosvd_tucker_in), _c.c_double, _c.c_int, _c.c_void_p * 3, _c.c_int * 3,
                                  _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_size_t,
                                  _c.c_void_p]
+        L.rhosvd_cp_horner_workspace_size.restype = _c.c_size_t
+        L.rhosvd_cp_horner_workspace_size.argtypes = [_c.POINTER(rhosvd_cp), _c.c_int, _c.POINTER(rhosvd_opts),
+                                                      _c.c_int]
+        L.rhosvd_cp_horner.restype = _c.c_int
+        L.rhosvd_cp_horner.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(_c.c_double), _c.c_int,
+                                       _c.POINTER(rhosvd_opts), _c.c_double, _c.c_int, _c.c_void_p * 3,
+                                       _c.c_int * 3, _c.c_void_p, _c.POINTER(_c.c_int),
+                                       _c.POINTER(rhosvd_horner_step), _c.c_void_p, _c.c_size_t, _c.c_void_p]
         L.rhosvd_selftest_fastmath.restype = _c.c_int
         L.rhosvd_selftest_fastmath.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p]
         L.rhosvd_launch_count.restype = _c.c_longlong
@@ -298,6 +310,58 @@ def rhosvd_c2c(U, xi, eps_tucker, eps_t2c, R_max, **c2t_opts):
     r, beta, Z = tk.tucker()
     flat = tk.beta[: r[0] * r[1] * r[2]]
     return rhosvd_t2c(Z, flat, eps_t2c, R_max), tk
+
+
+class PolynomialResult:
+    """Outputs of rhosvd_cp_horner: factors U[l] (n_l x R_max, column-major; columns < R hold
+    P(A)), weights xi, the rank R and one record per reduction (dicts k, R_in, r, R, status)."""
+
+    def __init__(self, U, xi, R, steps):
+        self.U, self.xi, self.R, self.steps = U, xi, R, steps
+
+
+def rhosvd_cp_horner(U, xi, coeffs, eps_tucker, eps_t2c, R_max, r_max=64, oversample=32, seed=0,
+                     precision=RHOSVD_PLAIN_FP64, deflate=0, workspace=None, stream=None, out=None):
+    """P(A) = sum_k coeffs[k] A^k (Hadamard powers) of the CP tensor A = (U, xi) by the Horner
+    scheme with a C2C reduction after every product.  Synchronises the stream.  Raises
+    RhosvdError on a host or device error (the records up to it are in err.steps)."""
+    torch = _torch()
+    L = load()
+    cp = make_cp(U, xi)
+    opts = make_opts(eps_tucker, (0, 0, 0), r_max, oversample, seed, precision, deflate)
+    c = [float(a) for a in coeffs]
+    nc = len(c)
+    need = int(L.rhosvd_cp_horner_workspace_size(_c.byref(cp), nc, _c.byref(opts), int(R_max)))
+    if need == 0:
+        raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_cp_horner_workspace_size")
+    dev = U[0].device
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    if out is None:
+        Uo = [torch.empty(int(R_max), cp.n[l], dtype=torch.float64, device=dev).t() for l in range(3)]
+        xo = torch.empty(int(R_max), dtype=torch.float64, device=dev)
+    else:
+        Uo, xo = out
+    ptrs = (_c.c_void_p * 3)(*[Uo[l].data_ptr() for l in range(3)])
+    ldu = (_c.c_int * 3)(*[cp.n[l] for l in range(3)])
+    for l in range(3):
+        if Uo[l].stride(0) != 1 or (Uo[l].shape[1] > 1 and Uo[l].stride(1) != cp.n[l]):
+            raise ValueError("output factors must be column-major with leading dimension n_l")
+    carr = (_c.c_double * nc)(*c)
+    steps = (rhosvd_horner_step * max(nc - 1, 1))()
+    for s in steps:
+        s.k = -1                                  # records the call fills have k >= 0
+    R = _c.c_int(0)
+    rc = L.rhosvd_cp_horner(_c.byref(cp), carr, nc, _c.byref(opts), float(eps_t2c), int(R_max), ptrs, ldu,
+                            _c.c_void_p(xo.data_ptr()), _c.byref(R), steps, _c.c_void_p(workspace.data_ptr()), need,
+                            _stream_handle(stream))
+    recs = [dict(k=s.k, R_in=s.R_in, r=list(s.r), R=s.R, status=s.status) for s in steps[: max(nc - 1, 0)]
+            if s.k >= 0]
+    if rc != RHOSVD_OK:
+        err = RhosvdError(rc, "rhosvd_cp_horner")
+        err.steps = recs
+        raise err
+    return PolynomialResult(Uo, xo, int(R.value), recs)
 
 
 def rhosvd_selftest_fastmath(x, stream=None):

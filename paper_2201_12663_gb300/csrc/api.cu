@@ -1181,6 +1181,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
     if (fa.nchunk > rh::RITZ_CHUNKS) fa.nchunk = rh::RITZ_CHUNKS;
     for (int l = 0; l < 3; ++l) {
         fa.ranks[l] = opts->ranks[l];
+        fa.n[l] = p.n[l];
         fa.ntiles[l] = mixed ? ((R + OZ_BM - 1) / OZ_BM) * ((p.NQ + OZ_NT6 - 1) / OZ_NT6) : (int)p.rp_stride;
     }
     STAGE("rank_final", launch_rank_final(fa, st));

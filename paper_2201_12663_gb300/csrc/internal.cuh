@@ -278,6 +278,7 @@ struct FinalArgs {
     long long rpstride;
     double* cpart;           // Ritz energy partials: [mode][chunk][KMAX]
     int nchunk;              // chunks of nu (at most RITZ_CHUNKS)
+    int n[3];                // mode sizes (the FP64 noise floor of a mode's energies)
 };
 constexpr int RITZ_CHUNKS = 256;
 

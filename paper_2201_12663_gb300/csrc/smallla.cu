@@ -400,7 +400,11 @@ __global__ void k_rank_final(FinalArgs a)
     __syncthreads();
     if (threadIdx.x != 0) return;
     const double total = a.st->total[b];
-    const double thr = a.eps * a.eps * total;
+    // energy at or below the FP64 resolution of the n_l x R side matrix, (n_l u)^2 ||U||_F^2,
+    // counts as zero: with eps = 0 (or below n_l u) the rank keeps every resolvable direction
+    // and rounding left in the residual is no missed sketch energy
+    const double floor_rel = (double)a.n[b] * DBL_EPSILON;
+    const double thr = fmax(a.eps * a.eps, floor_rel * floor_rel) * total;
     int r;
     if (a.ranks[b] > 0 || total == 0.0 || (a.ranks[b] == 0 && a.eps >= 1.0)) {
         r = rhi;
