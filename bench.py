@@ -545,16 +545,20 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def make_form(prec):
+    def make_form(prec, fused=args.fused):
         opts = dict(eps=WORKLOAD["eps"], r_max=WORKLOAD["r_max"], oversample=WORKLOAD["oversample"], seed=12345,
                     precision=PRECISIONS[prec])
         cp = P.make_cp(Uc, xc)
         ws = torch.empty(P.rhosvd_c2t_workspace_size(cp, P.make_opts(**opts)), dtype=torch.uint8, device=dev)
         out = P.alloc_tucker([n, n, n], R, WORKLOAD["r_max"], dev)
 
-        def step():
-            P.rhosvd_cp_hadamard(Ua, xa, Ub, xb, U_out=Uc, xi_out=xc)
-            P.rhosvd_c2t(Uc, xc, out=out, workspace=ws, **opts)
+        if fused:       # the product's columns formed inside the reduction, never stored
+            def step():
+                P.rhosvd_c2t_hadamard(Ua, xa, Ub, xb, out=out, workspace=ws, **opts)
+        else:           # the product stored by rhosvd_cp_hadamard, then reduced
+            def step():
+                P.rhosvd_cp_hadamard(Ua, xa, Ub, xb, U_out=Uc, xi_out=xc)
+                P.rhosvd_c2t(Uc, xc, out=out, workspace=ws, **opts)
         return step, out, ws
 
     def time_form(step, out, steps, profile):
@@ -598,6 +602,10 @@ def run_ours(args):
     # the other form, same run, same inputs (comparison; not the headline)
     step2, out2, ws2 = make_form(other)
     ms2, prof2, _, info2 = time_form(step2, out2, max(3, args.steps // 2), False)
+    # the same precision with the product formed inside the reduction (or stored, under --fused)
+    step3, out3, ws3 = make_form(main_prec, fused=not args.fused)
+    ms3, _, _, _ = time_form(step3, out3, max(3, args.steps // 2), False)
+    del ws3
 
     # agreement of the two forms (Tucker tensors), computed on the device with torch
     def tucker_of(res):
@@ -682,6 +690,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64 (mixed: bf16 digit planes, fp32 accumulate)" if main_prec == "mixed"
             else "f64", "data": "synthetic",
             "config": {**WORKLOAD, "precision": main_prec,
+                       "product": "formed inside the reduction (rhosvd_c2t_hadamard)" if args.fused
+                       else "stored by rhosvd_cp_hadamard, then reduced",
                        "l2": "flushed (256 MB write) before every timed step",
                        "ranks": [info.r[l] for l in range(3)], "k": [info.k[l] for l in range(3)],
                        "tails": [info.tail[l] for l in range(3)]},
@@ -690,6 +700,10 @@ def run_ours(args):
             f"{other}_form": {"value": world * 1000.0 / ms2, "ms_per_step": ms2,
                               "stage_ms_per_step": {k: v[1] / max(3, args.steps // 2) for k, v in prof2.items()}},
             "speedup_vs_other_form": ms2 / ms_per_step,
+            ("fused_product" if not args.fused else "stored_product"): {
+                "ms_per_step": ms3, "value": world * 1000.0 / ms3,
+                "note": "same precision; rhosvd_c2t_hadamard (no stored product)" if not args.fused
+                else "same precision; rhosvd_cp_hadamard into a buffer, then rhosvd_c2t"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "stage_shares": shares,
             "stage_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
@@ -723,6 +737,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--no-t2c", action="store_true", help="skip the Tucker-to-canonical leg")
     ap.add_argument("--no-poly", action="store_true", help="skip the Newton-cube / Horner leg")
+    ap.add_argument("--fused", action="store_true",
+                    help="headline step forms the Hadamard product inside the reduction (rhosvd_c2t_hadamard)")
     ap.add_argument("--precision", choices=["mixed", "plain"], default="mixed")
     ap.add_argument("--learned-train", type=int, default=600,
                     help="training instances of the learned-proposal leg (0 skips it; the full workload is 20000)")

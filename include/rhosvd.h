@@ -156,6 +156,20 @@ int rhosvd_cp_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, double* const U_o
 int rhosvd_cp_sum(double alpha, const rhosvd_cp* a, double beta, const rhosvd_cp* b,
                   double* const U_out[3], const int ld_out[3], double* xi_out, void* stream);
 
+/*
+ * RHOSVD of the Hadamard product a (.) b without storing it (Sec. 3 eq. rho_ten reduced by
+ * Def. 2.2): the same result as rhosvd_cp_hadamard into a buffer followed by rhosvd_c2t of that
+ * buffer, bit for bit, but the norms and the normalised side matrices are formed from the columns
+ * a^(l)_i .* b^(l)_j (term nu = i + Ra j, weight xa_i xb_j) as they are read, so the n_l x Ra Rb
+ * product factors are never written to or read back from memory.  `out` is as for rhosvd_c2t
+ * with R = Ra Rb (V: r_max x Ra Rb, xi_out: Ra Rb values).  Equal mode sizes; Ra Rb < 2^31.
+ * Workspace: rhosvd_c2t_hadamard_workspace_size(a, b, opts) bytes (that of rhosvd_c2t for a
+ * tensor of rank Ra Rb).  Errors as rhosvd_c2t.
+ */
+size_t rhosvd_c2t_hadamard_workspace_size(const rhosvd_cp* a, const rhosvd_cp* b, const rhosvd_opts* opts);
+int rhosvd_c2t_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, const rhosvd_opts* opts, const rhosvd_tucker* out,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------- allocation-free variant
  * (the paper has no counterpart: this serves callers of the library, not the method)
  *

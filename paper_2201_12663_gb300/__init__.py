@@ -157,6 +157,12 @@ def load(build_if_missing: bool = False):
         L.rhosvd_t2c.argtypes = [_c.POINTER(rhosvd_tucker_in), _c.c_double, _c.c_int, _c.c_void_p * 3, _c.c_int * 3,
                                  _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_size_t,
                                  _c.c_void_p]
+        L.rhosvd_c2t_hadamard_workspace_size.restype = _c.c_size_t
+        L.rhosvd_c2t_hadamard_workspace_size.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_cp),
+                                                         _c.POINTER(rhosvd_opts)]
+        L.rhosvd_c2t_hadamard.restype = _c.c_int
+        L.rhosvd_c2t_hadamard.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts),
+                                          _c.POINTER(rhosvd_tucker), _c.c_void_p, _c.c_size_t, _c.c_void_p]
         L.rhosvd_cp_horner_workspace_size.restype = _c.c_size_t
         L.rhosvd_cp_horner_workspace_size.argtypes = [_c.POINTER(rhosvd_cp), _c.c_int, _c.POINTER(rhosvd_opts),
                                                       _c.c_int]
@@ -476,6 +482,31 @@ def rhosvd_c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0
                       _c.c_size_t(workspace.numel()), _stream_handle(stream))
     if rc != RHOSVD_OK:
         raise RhosvdError(rc, "rhosvd_c2t")
+    return out
+
+
+def rhosvd_c2t_hadamard(Ua, xa, Ub, xb, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0, out=None,
+                        workspace=None, stream=None, with_V=False, with_xi=False, precision=RHOSVD_PLAIN_FP64,
+                        deflate=0) -> TuckerResult:
+    """RHOSVD of the Hadamard product of the CP tensors (Ua, xa) and (Ub, xb), the product's
+    columns formed as they are read (bit-identical to rhosvd_cp_hadamard + rhosvd_c2t)."""
+    torch = _torch()
+    L = load()
+    a, b = make_cp(Ua, xa), make_cp(Ub, xb)
+    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate)
+    need = int(L.rhosvd_c2t_hadamard_workspace_size(_c.byref(a), _c.byref(b), _c.byref(opts)))
+    if need == 0:
+        raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_c2t_hadamard_workspace_size")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=Ua[0].device)
+    if out is None:
+        out = alloc_tucker([a.n[l] for l in range(3)], a.R * b.R, r_max, Ua[0].device, with_V, with_xi)
+    t = tucker_struct(out)
+    rc = L.rhosvd_c2t_hadamard(_c.byref(a), _c.byref(b), _c.byref(opts), _c.byref(t),
+                               _c.c_void_p(workspace.data_ptr()), _c.c_size_t(workspace.numel()),
+                               _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_c2t_hadamard")
     return out
 
 

@@ -324,8 +324,16 @@ struct StartBasis {
     int iters;             // 0: Y = Q0; 1: Y = U~ (U~^T Q0)
 };
 
+// Second factor of a Hadamard product reduced without storing it: cp holds the first factor's
+// columns with R = Ra Rb, and term nu = i + Ra j is cp's column i times b's column j.
+struct HadSrc {
+    const rhosvd_cp* b;
+    int Ra;
+    const double* xa;
+};
+
 static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBasis* sb0, const rhosvd_tucker* out,
-                    void* workspace, size_t workspace_bytes, void* stream)
+                    void* workspace, size_t workspace_bytes, void* stream, const HadSrc* had = nullptr)
 {
     Plan p;
     int rc = make_plan(cp, opts, &p, sb0 ? sb0->k0 : 0);
@@ -397,8 +405,15 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
 
     // ---- a1: column norms, normalised weights (Sec. 2.1)
     NormArgs na;
+    memset(&na, 0, sizeof(na));
     for (int l = 0; l < 3; ++l) { na.U[l] = cp->U[l]; na.ld[l] = cp->ld[l]; na.n[l] = p.n[l]; }
     na.R = R;
+    if (had) {
+        for (int l = 0; l < 3; ++l) { na.B[l] = had->b->U[l]; na.ldb[l] = had->b->ld[l]; }
+        na.Ra = had->Ra;
+        na.xa = had->xa;
+        na.xb = had->b->xi;
+    }
     na.norms = norms;
     na.colmax = colmax;
     STAGE("colnorms", launch_colnorms(na, st));
@@ -1275,6 +1290,43 @@ extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rh
                           void* workspace, size_t workspace_bytes, void* stream)
 {
     return c2t_impl(cp, opts, nullptr, out, workspace, workspace_bytes, stream);
+}
+
+// The virtual canonical tensor of the product a (.) b: a's columns with rank Ra Rb (its
+// columns are never read past Ra; the product source supplies every term).
+static int had_view(const rhosvd_cp* a, const rhosvd_cp* b, rhosvd_cp* v)
+{
+    if (!a || !b || a->R < 0 || b->R < 0) return RHOSVD_ERR_INVALID_ARG;
+    if ((long long)a->R * b->R > 0x7fffffffLL) return RHOSVD_ERR_INVALID_ARG;
+    for (int l = 0; l < 3; ++l) {
+        if (a->n[l] != b->n[l] || b->ld[l] < b->n[l]) return RHOSVD_ERR_INVALID_ARG;
+        if (a->R > 0 && b->R > 0 && (!a->U[l] || !b->U[l])) return RHOSVD_ERR_INVALID_ARG;
+    }
+    if (a->R > 0 && b->R > 0 && (!a->xi || !b->xi)) return RHOSVD_ERR_INVALID_ARG;
+    *v = *a;
+    v->R = a->R * b->R;
+    return RHOSVD_OK;
+}
+
+extern "C" size_t rhosvd_c2t_hadamard_workspace_size(const rhosvd_cp* a, const rhosvd_cp* b,
+                                                     const rhosvd_opts* opts)
+{
+    rhosvd_cp v;
+    if (had_view(a, b, &v) != RHOSVD_OK) return 0;
+    return rhosvd_c2t_workspace_size(&v, opts);
+}
+
+extern "C" int rhosvd_c2t_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, const rhosvd_opts* opts,
+                                   const rhosvd_tucker* out, void* workspace, size_t workspace_bytes, void* stream)
+{
+    rhosvd_cp v;
+    int rc = had_view(a, b, &v);
+    if (rc) return rc;
+    HadSrc h;
+    h.b = b;
+    h.Ra = a->R;
+    h.xa = a->xi;
+    return c2t_impl(&v, opts, nullptr, out, workspace, workspace_bytes, stream, v.R > 0 ? &h : nullptr);
 }
 
 extern "C" size_t rhosvd_c2t_start_workspace_size(const rhosvd_cp* cp, const rhosvd_opts* opts, int k0)

@@ -10,13 +10,34 @@ namespace rh {
 // non-negative double orders like its bits; NaN patterns sort above Inf), then
 // ||u|| = 2^ex sqrt(sum (u_i 2^-ex)^2) with max |u_i| < 2^ex, so the scaling is exact and the
 // squares neither underflow nor overflow.  Writes the norm and max |u_i|.  grid (ceil(R/8), 3).
+// Column nu of mode l: the stored column, or (PROD) the entrywise product of the two factor
+// columns it stands for, nu = i + Ra j (one FP64 multiply, as rhosvd_cp_hadamard stores it).
+template <bool PROD>
+struct Col {
+    const double* a;
+    const double* b;
+    __device__ Col(const NormArgs& na, int l, int nu)
+    {
+        if (PROD) {
+            const int i = nu % na.Ra, j = nu / na.Ra;
+            a = na.U[l] + (long long)i * na.ld[l];
+            b = na.B[l] + (long long)j * na.ldb[l];
+        } else {
+            a = na.U[l] + (long long)nu * na.ld[l];
+            b = nullptr;
+        }
+    }
+    __device__ __forceinline__ double operator[](int x) const { return PROD ? a[x] * b[x] : a[x]; }
+};
+
+template <bool PROD>
 __global__ void k_colnorms(NormArgs a)
 {
     const int l = blockIdx.y;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= a.R) return;
-    const double* u = a.U[l] + (long long)warp * a.ld[l];
+    const Col<PROD> u(a, l, warp);
     const int n = a.n[l];
     long long mb = 0;
     for (int i = lane; i < n; i += 32) {
@@ -40,7 +61,10 @@ __global__ void k_colnorms(NormArgs a)
         if (ex > -450 && ex < 450) {
             // squares stay in [2^-902, 2^900): no scaling needed, one FP64 operation an element
             // (terms that would square to subnormals lie below 2^-1022 / max^2 <= 2^-120 of the sum)
-            for (int i = lane; i < n; i += 32) s = fma(u[i], u[i], s);
+            for (int i = lane; i < n; i += 32) {
+                const double v = u[i];
+                s = fma(v, v, s);
+            }
             s = warp_sum(s);
             nrm = sqrt(s);
             if (lane == 0) {
@@ -71,14 +95,76 @@ __global__ void k_colnorms(NormArgs a)
     }
 }
 
+// k_colnorms for a Hadamard-product source with n_l <= 32 NR: the warp forms its column once
+// into registers (lane holds entries lane + 32 k) and takes the maximum and the sum from there,
+// in the same per-lane order as k_colnorms (so the norms agree bit for bit).
+template <int NR>
+__global__ void k_colnorms_prod(NormArgs a)
+{
+    const int l = blockIdx.y;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= a.R) return;
+    const Col<true> u(a, l, warp);
+    const int n = a.n[l];
+    double v[NR];
+    long long mb = 0;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int i = lane + 32 * k;
+        v[k] = i < n ? u[i] : 0.0;
+        const long long b = __double_as_longlong(v[k]) & 0x7FFFFFFFFFFFFFFFll;
+        mb = b > mb ? b : mb;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long b = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = b > mb ? b : mb;
+    }
+    const double mx = __longlong_as_double(mb);
+    double nrm;
+    if (mb == 0) {
+        nrm = 0.0;
+    } else if (mb >= 0x7FF0000000000000ll) {
+        nrm = mx;
+    } else {
+        int ex;
+        frexp(mx, &ex);
+        double s = 0.0;
+        if (ex > -450 && ex < 450) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+                if (lane + 32 * k < n) s = fma(v[k], v[k], s);
+            nrm = sqrt(warp_sum(s));
+        } else {
+            const int e1 = -ex / 2, e2 = -ex - e1;
+            const bool one = ex > -1022 && ex < 1022;
+            const double sc = one ? __hiloint2double((1023 - ex) << 20, 0) : 1.0;
+            const double sc1 = one ? 1.0 : ldexp(1.0, e1), sc2 = one ? 1.0 : ldexp(1.0, e2);
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+                if (lane + 32 * k < n) {
+                    const double t = one ? v[k] * sc : (v[k] * sc1) * sc2;
+                    s = fma(t, t, s);
+                }
+            nrm = ldexp(sqrt(warp_sum(s)), ex);
+        }
+    }
+    if (lane == 0) {
+        a.norms[(long long)l * a.R + warp] = nrm;
+        a.colmax[(long long)l * a.R + warp] = mx;
+    }
+}
+
 // Per term: keep iff all three norms are finite and nonzero (keep[nu] = 1 or 0), weight
 // xi' = xi prod_l ||u_l|| (0 for a dropped term).  Non-finite data sets NONFINITE.
-__global__ void k_terms(const double* norms, const double* xi, int R, double* keepf, double* xin,
-                        double* xi_user, rhosvd_info* info)
+template <bool PROD>
+__global__ void k_terms(NormArgs a, const double* xi, double* keepf, double* xin, double* xi_user, rhosvd_info* info)
 {
+    const int R = a.R;
+    const double* norms = a.norms;
     for (int nu = blockIdx.x * blockDim.x + threadIdx.x; nu < R; nu += gridDim.x * blockDim.x) {
         const double d0 = norms[nu], d1 = norms[R + nu], d2 = norms[2 * R + nu];
-        const double x = xi[nu];
+        const double x = PROD ? a.xa[nu % a.Ra] * a.xb[nu / a.Ra] : xi[nu];
         const bool fin = isfinite(d0) && isfinite(d1) && isfinite(d2) && isfinite(x);
         if (!fin) set_status(info, RHOSVD_ERR_NONFINITE);
         const bool keep = fin && d0 > 0.0 && d1 > 0.0 && d2 > 0.0;
@@ -96,6 +182,7 @@ __global__ void k_terms(const double* norms, const double* xi, int R, double* ke
 // is also cut into OZ_S64 planes as operand row nu (k = x) with exponent E_nu from
 // max |Un(:, nu)| = colmax * scale (the same multiply as the entries, so max < 2^E_nu holds
 // exactly).  One warp per column, grid (ceil(R/8), 3).
+template <bool PROD>
 __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long long ustride, double* nn2, NormSlice ns)
 {
     const int l = blockIdx.y;
@@ -103,7 +190,7 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
     const int lane = threadIdx.x & 31;
     if (warp >= a.R) return;
     const int n = a.n[l];
-    const double* u = a.U[l] + (long long)warp * a.ld[l];
+    const Col<PROD> u(a, l, warp);
     double* dst = Un + l * ustride + (long long)warp * n;
     const bool keep = keepf[warp] != 0.0;
     const double d = a.norms[(long long)l * a.R + warp];
@@ -336,7 +423,11 @@ int launch_colnorms(const NormArgs& a, cudaStream_t st)
 {
     if (a.R <= 0) return 0;
     dim3 grid((a.R + 7) / 8, 3);
-    k_colnorms<<<grid, 256, 0, st>>>(a);
+    const int nmax = a.n[0] > a.n[1] ? (a.n[0] > a.n[2] ? a.n[0] : a.n[2]) : (a.n[1] > a.n[2] ? a.n[1] : a.n[2]);
+    if (a.Ra > 0 && nmax <= 256) k_colnorms_prod<8><<<grid, 256, 0, st>>>(a);
+    else if (a.Ra > 0 && nmax <= 1024) k_colnorms_prod<32><<<grid, 256, 0, st>>>(a);
+    else if (a.Ra > 0) k_colnorms<true><<<grid, 256, 0, st>>>(a);
+    else k_colnorms<false><<<grid, 256, 0, st>>>(a);
     RH_CHECK_LAUNCH();
     return 0;
 }
@@ -347,10 +438,12 @@ int launch_terms(const NormArgs& na, const double* xi, double* keepf, double* xi
 {
     const int R = na.R;
     if (R > 0) {
-        k_terms<<<(R + 255) / 256, 256, 0, st>>>(na.norms, xi, R, keepf, xin, xi_user, info);
+        if (na.Ra > 0) k_terms<true><<<(R + 255) / 256, 256, 0, st>>>(na, xi, keepf, xin, xi_user, info);
+        else k_terms<false><<<(R + 255) / 256, 256, 0, st>>>(na, xi, keepf, xin, xi_user, info);
         RH_CHECK_LAUNCH();
         dim3 grid((R + 7) / 8, 3);
-        k_normalize<<<grid, 256, 0, st>>>(na, keepf, Un, ustride, nn2, ns);
+        if (na.Ra > 0) k_normalize<true><<<grid, 256, 0, st>>>(na, keepf, Un, ustride, nn2, ns);
+        else k_normalize<false><<<grid, 256, 0, st>>>(na, keepf, Un, ustride, nn2, ns);
         RH_CHECK_LAUNCH();
     }
     k_term_totals<<<1, 1024, 0, st>>>(nn2, keepf, xin, R, total, info);

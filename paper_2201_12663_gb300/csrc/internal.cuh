@@ -205,6 +205,13 @@ struct NormArgs {
     int R;
     double* norms;      // 3 x R
     double* colmax;     // 3 x R: max |u_i| of each column
+    // Hadamard-product source (Ra > 0): column nu = i + Ra j is U[l](:, i) .* B[l](:, j) and its
+    // weight xa[i] xb[j], formed on the fly (the same FP64 products rhosvd_cp_hadamard stores)
+    const double* B[3];
+    int ldb[3];
+    int Ra;
+    const double* xa;
+    const double* xb;
 };
 
 // Digit planes of the normalised columns, cut while they are written (mixed form): column nu
