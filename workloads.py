@@ -193,6 +193,98 @@ def newton_kernel(n: int = 257, b: float = 10.0, M: int = 9, h: float = 0.7,
               meta=dict(kind="newton_kernel", n=n, b=b, M=M, h=h, long_range=long_range))
 
 
+def point_grid(n_cells: int, b: float) -> np.ndarray:
+    """Collocation grid including the origin (Sec. 4.1, for continuous radial functions the mode
+    size becomes n+1): x_i = -b + i 2b/n_cells, i = 0..n_cells."""
+    return -b + np.arange(n_cells + 1, dtype=np.float64) * (2.0 * b / n_cells)
+
+
+def lattice(n_cells: int, L, m: int):
+    """Nodes of an L1 x L2 x L3 lattice centred on the origin with spacing m grid steps, on the
+    grid of point_grid(n_cells, .) (m even or L odd keeps every node on a grid point).  Returns
+    the (N, 3) grid indices, node j = j1 + L1 (j2 + L2 j3)."""
+    c = n_cells // 2
+    ax = [c + np.round((np.arange(L[l]) - (L[l] - 1) / 2.0) * m).astype(np.int64) for l in range(3)]
+    I = np.stack(np.meshgrid(ax[0], ax[1], ax[2], indexing="ij"), axis=-1)
+    I = I.transpose(2, 1, 0, 3).reshape(-1, 3)           # j1 fastest
+    if I.min() < 0 or I.max() > n_cells:
+        raise ValueError("lattice leaves the grid")
+    return np.ascontiguousarray(I)
+
+
+def slater_sinc_nodes(lam: float = 0.5, h: float = 1.56, k_lo: int = -2, k_hi: int = 2):
+    """Gaussian exponents tau_k and weights p_k of the sinc rule for the Slater function
+    exp(-lam |x|) = exp(-2 sqrt(alpha rho)), rho = |x|^2, alpha = lam^2 / 4, from its Laplace
+    transform with weight sqrt(alpha/pi) tau^{-3/2} exp(-alpha/tau) (Sec. 4.3, eq.
+    Slater_Laplace_tr, Lemma lem:sincSlater): tau = e^u, step h,
+        tau_k = e^{k h},  p_k = h sqrt(alpha/pi) tau_k^{-1/2} exp(-alpha/tau_k).
+    exp(-lam |x|) ~ sum_k p_k exp(-tau_k |x|^2).  Long range: tau_k <= 1 (k <= 0).  Defaults:
+    R = 5 terms, R_l = 3 (k = -2..0), h from minimising the maximum error over |x| in [1, 20]
+    at lam = 0.5 (about 4e-3)."""
+    al = lam * lam / 4.0
+    k = np.arange(k_lo, k_hi + 1, dtype=np.float64)
+    tau = np.exp(k * h)
+    p = h * math.sqrt(al / math.pi) * tau ** -0.5 * np.exp(-al / tau)
+    return tau, p
+
+
+def slater_amplitude(x, y, z, c1: float = 6.0, c2: float = 0.1):
+    """F(x,y,z) = c1 cos(x + 2y + 4z) exp(-c2 sqrt(x^2 + 2y^2 + 4z^2)) (Sec. 4.4, eq. func2)."""
+    return c1 * np.cos(x + 2 * y + 4 * z) * np.exp(-c2 * np.sqrt(x * x + 2 * y * y + 4 * z * z))
+
+
+def multi_slater_long_range(n_cells: int = 384, b: float = 10.0, L=(4, 4, 4), m: int = 20, lam: float = 0.5,
+                            h: float = 1.56, amplitudes: str = "random", seed: int = 0) -> CP:
+    """Long-range part G_{N,l} = sum_j c_j W_j G_l of a sum of Slater functions placed on the nodes
+    of an L1 x L2 x L3 lattice (Sec. 4.4, eq. Slater_interp_multi; Tables Tab:random_ranks and
+    Tab:func_ranks): every node contributes the R_l long-range Gaussians of slater_sinc_nodes
+    centred on it (collocation on point_grid(n_cells, b), nodes on grid points, so the shifted
+    reference vectors are the Gaussians sampled at the grid).  Amplitudes c_j: "random" draws
+    U[-5, 5] with PCG64(seed) in node order; "func" evaluates slater_amplitude at the node.
+    Term index nu = j R_l + k.  R = N R_l."""
+    x = point_grid(n_cells, b)
+    idx = lattice(n_cells, L, m)
+    N = idx.shape[0]
+    tau, p = slater_sinc_nodes(lam, h)
+    keep = tau <= 1.0
+    tau, p = tau[keep], p[keep]
+    Rl = tau.shape[0]
+    if amplitudes == "random":
+        c = np.random.default_rng(seed).uniform(-5.0, 5.0, size=N)
+    elif amplitudes == "func":
+        c = slater_amplitude(x[idx[:, 0]], x[idx[:, 1]], x[idx[:, 2]])
+    else:
+        raise ValueError(amplitudes)
+    expo = np.tile(tau, N)
+    U = [gaussian_columns(x, np.repeat(x[idx[:, l]], Rl), expo) for l in range(3)]
+    xi = (np.repeat(c, Rl) * np.tile(p, N)).astype(np.float64)
+    return CP(U=U, xi=xi, meta=dict(kind="multi_slater_long_range", n_cells=n_cells, b=b, L=tuple(L), m=m,
+                                    lam=lam, h=h, amplitudes=amplitudes, seed=seed, N=N, R_l=Rl, idx=idx, c=c))
+
+
+def newton_lattice_long_range(n_cells: int = 384, b: float = 24.0, L=(16, 16, 16), m: int = 24, h: float = 0.4,
+                              k_lo: int = -19, seed: int = 0) -> CP:
+    """Collective long-range Newton potential P_l = sum_j z_j W_j P_{R_l} of N = L1 L2 L3 charges on
+    the nodes of a lattice (Sec. 4.2, eq. RS_repres; Lemma lem:InterEnergy): the long-range sinc
+    Gaussians t_k <= 1 of newton_sinc_nodes(h, k_lo, 0) centred on every node, collocation on
+    point_grid(n_cells, b).  Charges z_j ~ U[-1, 1] from PCG64(seed) in node order.  Term
+    nu = j R_l + k, weight z_j p_k.  meta: idx (N x 3 grid indices), z, coords (N x 3), p0 =
+    P_{R_l}(0) = sum_k p_k (the single reference kernel's long-range part at its centre)."""
+    x = point_grid(n_cells, b)
+    idx = lattice(n_cells, L, m)
+    N = idx.shape[0]
+    t, p = newton_sinc_nodes(h, k_lo, 0)
+    Rl = t.shape[0]
+    z = np.random.default_rng(seed).uniform(-1.0, 1.0, size=N)
+    expo = np.tile(t * t, N)
+    U = [gaussian_columns(x, np.repeat(x[idx[:, l]], Rl), expo) for l in range(3)]
+    xi = (np.repeat(z, Rl) * np.tile(p, N)).astype(np.float64)
+    coords = np.stack([x[idx[:, l]] for l in range(3)], axis=1)
+    return CP(U=U, xi=xi, meta=dict(kind="newton_lattice_long_range", n_cells=n_cells, b=b, L=tuple(L), m=m, h=h,
+                                    k_lo=k_lo, seed=seed, N=N, R_l=Rl, idx=idx, z=z, coords=coords,
+                                    p0=float(p.sum()), t=t, p=p))
+
+
 # Named workloads (sizes, distributions and thresholds).
 CONFIGS = {
     "gauss_n128_R200": dict(n=128, R=200, seed=0, eps=1e-6),
