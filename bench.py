@@ -506,6 +506,89 @@ def poly_leg(P, steps, warmup, precision):
     return out
 
 
+# the paper's printed long-range Slater ranks (Tables Tab:random_ranks and Tab:func_ranks):
+# lattice -> (Tucker ranks, R_ini, R_comp); context only (other discretisation, garbled captions)
+PAPER_SLATER = {
+    "random": {(4, 4, 4): ([13] * 3, 192, 56), (6, 6, 6): ([15] * 3, 649, 95), (8, 8, 8): ([19] * 3, 1536, 131),
+               (16, 16, 8): ([32, 32, 19], 6141, 253), (16, 16, 16): ([32] * 3, 12288, 380)},
+    "func": {(4, 4, 4): ([7] * 3, 256, 25), (6, 6, 6): ([7] * 3, 648, 23), (8, 8, 8): ([7] * 3, 1536, 30),
+             (16, 16, 8): ([10, 9, 6], 6144, 47), (16, 16, 16): ([10, 9, 8], 12288, 55)},
+}
+
+
+def rs_leg(P, steps, warmup, precision):
+    """Range-separated workloads (Sec. 4.2-4.4): the C2C reduction of the long-range multi-Slater
+    lattice sums at eps_Tucker = 1e-3, eps_T2C = 1e-5 (the paper's rank tables; ours beside the
+    printed ones), and the interaction energy of 16^3 lattice charges from the C2C-reduced
+    long-range Newton potential (Lemma lem:InterEnergy) against the unreduced potential and the
+    direct O(N^2) Coulomb sum (the oracle, timed on the host)."""
+    import numpy as np
+    import torch
+    import workloads
+    from oracle import energy as oe
+    out = {"slater": {}}
+
+    def timed(fn):
+        for _ in range(max(warmup, 1)):
+            res = fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            res = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return res, e0.elapsed_time(e1) / steps
+
+    for name in ("slater_lattice_random_n384", "slater_lattice_func_n232"):
+        C = dict(workloads.CONFIGS[name])
+        lattices, eps_t, eps_c = C.pop("lattices"), C.pop("eps_tucker"), C.pop("eps_t2c")
+        rows = []
+        for L in lattices:
+            cp = workloads.multi_slater_long_range(L=L, **C)
+            U = [P.to_device_factor(u) for u in cp.U]
+            x = torch.from_numpy(cp.xi).cuda()
+            (can, tk), ms = timed(lambda: P.rhosvd_c2c(U, x, eps_t, eps_c, R_max=64 * 64, r_max=64,
+                                                       precision=PRECISIONS[precision]))
+            R, st = can.rank()
+            info = tk.info()
+            pt = PAPER_SLATER[C["amplitudes"]][tuple(L)]
+            rows.append({"lattice": list(L), "N": cp.meta["N"], "R_ini": cp.R, "tucker": [info.r[l] for l in range(3)],
+                         "R_comp": R, "status": st or info.status, "ms_c2c": ms,
+                         "paper": {"tucker": pt[0], "R_ini": pt[1], "R_comp": pt[2]}})
+            del U, x, can, tk
+        out["slater"][name] = {"n_points": C["n_cells"] + 1, "eps_tucker": eps_t, "eps_t2c": eps_c, "rows": rows}
+
+    C = dict(workloads.CONFIGS["newton_lattice_energy_N4096"])
+    eps_t, eps_c = C.pop("eps_tucker"), C.pop("eps_t2c")
+    cp = workloads.newton_lattice_long_range(**C)
+    M = cp.meta
+    U = [P.to_device_factor(u) for u in cp.U]
+    x = torch.from_numpy(cp.xi).cuda()
+    z = torch.from_numpy(M["z"]).cuda()
+    (can, tk), ms_c2c = timed(lambda: P.rhosvd_c2c(U, x, eps_t, eps_c, R_max=160 * 160, r_max=160,
+                                                   precision=PRECISIONS[precision]))
+    R, st = can.rank()
+    info = tk.info()
+    Ur = [can.U[l][:, :R] for l in range(3)]
+    xr = can.xi[:R].contiguous()
+    (E_red, _), ms_e_red = timed(lambda: P.rhosvd_rs_energy(Ur, xr, M["idx"], z, M["p0"]))
+    (E_full, _), ms_e_full = timed(lambda: P.rhosvd_rs_energy(U, x, M["idx"], z, M["p0"]))
+    t0 = time.perf_counter()
+    Ec = oe.pair_sum(M["coords"], M["z"], oe.coulomb)
+    t_c = time.perf_counter() - t0
+    Er, Ef = float(E_red.item()), float(E_full.item())
+    out["energy"] = {"workload": "newton_lattice_energy_N4096", "N": M["N"], "R_l": M["R_l"], "R_ini": cp.R,
+                     "n_points": C["n_cells"] + 1, "eps_tucker": eps_t, "eps_t2c": eps_c,
+                     "tucker": [info.r[l] for l in range(3)], "R_comp": R, "status": st or info.status,
+                     "ms_c2c": ms_c2c, "ms_energy_reduced": ms_e_red, "ms_energy_unreduced": ms_e_full,
+                     "E_reduced": Er, "E_unreduced": Ef, "E_coulomb_direct": Ec,
+                     "rel_diff_reduced_vs_unreduced": abs(Er - Ef) / abs(Ef),
+                     "rel_diff_unreduced_vs_coulomb": abs(Ef - Ec) / abs(Ec),
+                     "oracle_coulomb_s": t_c, "oracle_cores": 1}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -716,6 +799,8 @@ def run_ours(args):
         line["t2c"] = t2c_leg(P, out, max(3, args.steps // 2), args.warmup)
     if not args.no_poly:
         line["poly"] = poly_leg(P, max(3, args.steps // 2), args.warmup, main_prec)
+    if not args.no_rs:
+        line["rs"] = rs_leg(P, 3, 1, main_prec)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample()
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -737,6 +822,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--no-t2c", action="store_true", help="skip the Tucker-to-canonical leg")
     ap.add_argument("--no-poly", action="store_true", help="skip the Newton-cube / Horner leg")
+    ap.add_argument("--no-rs", action="store_true", help="skip the range-separated Slater / energy leg")
     ap.add_argument("--fused", action="store_true",
                     help="headline step forms the Hadamard product inside the reduction (rhosvd_c2t_hadamard)")
     ap.add_argument("--precision", choices=["mixed", "plain"], default="mixed")

@@ -358,6 +358,28 @@ int rhosvd_cp_horner(const rhosvd_cp* A, const double* coeffs, int ncoeffs, cons
                      double eps_t2c, int R_max, double* const U_out[3], const int ldu[3], double* xi_out,
                      int* R_out, rhosvd_horner_step* steps, void* workspace, size_t bytes, void* stream);
 
+/* ---------------------------------------------------------------- entries at nodes and the
+ * interaction energy from a long-range potential (Sec. 4.2, Lemma lem:InterEnergy, eq.
+ * EnergyFree_Tensor)
+ *
+ * rhosvd_cp_sample writes the entries of the canonical tensor `cp` at N grid nodes:
+ *   out[j] = sum_k xi_k U1[i1_j, k] U2[i2_j, k] U3[i3_j, k],  i_l,j = idx[l N + j]
+ * (idx: device int array of 3 N zero-based grid indices, mode-major; out: device, N doubles).
+ * A node whose index leaves [0, n_l) gets NaN (no memory outside the factors is read).
+ *
+ * rhosvd_rs_energy evaluates, for N charges z_j (device) sitting on the nodes idx of the grid of
+ * the collective long-range potential P_long = sum_j z_j (shifted long-range reference kernel),
+ *   E_N = 1/2 sum_j z_j P_long(x_j) - 1/2 p0 sum_j z_j^2,
+ * where p0 = P_{R_l}(0) is the single reference kernel's long-range part at its own centre (host
+ * double).  P_long may be the generated N R_l-term sum or its RHOSVD/C2C reduction; the work is
+ * O(R N).  p_out (device, N doubles) receives the samples P_long(x_j); energy (device, 1 double)
+ * the result.  Both calls are asynchronous on `stream`; sums run in a fixed order, so results do
+ * not depend on the launch.  Errors: RHOSVD_ERR_INVALID_ARG (sizes, NULL pointers, non-finite
+ * p0), RHOSVD_ERR_CUDA. */
+int rhosvd_cp_sample(const rhosvd_cp* cp, int N, const int* idx, double* out, void* stream);
+int rhosvd_rs_energy(const rhosvd_cp* P_long, int N, const int* idx, const double* z, double p0, double* p_out,
+                     double* energy, void* stream);
+
 /* ---------------------------------------------------------------- numerics self-test (no paper
  * counterpart: test support)
  *

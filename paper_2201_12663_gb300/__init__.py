@@ -163,6 +163,11 @@ def load(build_if_missing: bool = False):
         L.rhosvd_c2t_hadamard.restype = _c.c_int
         L.rhosvd_c2t_hadamard.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts),
                                           _c.POINTER(rhosvd_tucker), _c.c_void_p, _c.c_size_t, _c.c_void_p]
+        L.rhosvd_cp_sample.restype = _c.c_int
+        L.rhosvd_cp_sample.argtypes = [_c.POINTER(rhosvd_cp), _c.c_int, _c.c_void_p, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_rs_energy.restype = _c.c_int
+        L.rhosvd_rs_energy.argtypes = [_c.POINTER(rhosvd_cp), _c.c_int, _c.c_void_p, _c.c_void_p, _c.c_double,
+                                       _c.c_void_p, _c.c_void_p, _c.c_void_p]
         L.rhosvd_cp_horner_workspace_size.restype = _c.c_size_t
         L.rhosvd_cp_horner_workspace_size.argtypes = [_c.POINTER(rhosvd_cp), _c.c_int, _c.POINTER(rhosvd_opts),
                                                       _c.c_int]
@@ -368,6 +373,46 @@ def rhosvd_cp_horner(U, xi, coeffs, eps_tucker, eps_t2c, R_max, r_max=64, oversa
         err.steps = recs
         raise err
     return PolynomialResult(Uo, xo, int(R.value), recs)
+
+
+def _node_index(idx):
+    """(N, 3) integer grid indices -> device int32 array of 3 N, mode-major."""
+    torch = _torch()
+    t = idx if isinstance(idx, torch.Tensor) else torch.as_tensor(idx)
+    return t.to(device="cuda", dtype=torch.int32).t().contiguous().reshape(-1)
+
+
+def rhosvd_cp_sample(U, xi, idx, out=None, stream=None):
+    """Entries of the CP tensor (U, xi) at the (N, 3) grid indices idx; float64 CUDA tensor of N."""
+    torch = _torch()
+    L = load()
+    cp = make_cp(U, xi)
+    ix = _node_index(idx)
+    N = ix.numel() // 3
+    if out is None:
+        out = torch.empty(max(N, 1), dtype=torch.float64, device=U[0].device)
+    rc = L.rhosvd_cp_sample(_c.byref(cp), N, _c.c_void_p(ix.data_ptr()), _c.c_void_p(out.data_ptr()),
+                            _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_cp_sample")
+    return out[:N]
+
+
+def rhosvd_rs_energy(U, xi, idx, z, p0, stream=None):
+    """Interaction energy of the charges z (CUDA float64, N) at the grid nodes idx from the
+    long-range potential (U, xi); returns (energy device scalar tensor, samples)."""
+    torch = _torch()
+    L = load()
+    cp = make_cp(U, xi)
+    ix = _node_index(idx)
+    N = ix.numel() // 3
+    p = torch.empty(max(N, 1), dtype=torch.float64, device=U[0].device)
+    E = torch.empty(1, dtype=torch.float64, device=U[0].device)
+    rc = L.rhosvd_rs_energy(_c.byref(cp), N, _c.c_void_p(ix.data_ptr()), _c.c_void_p(z.data_ptr()), float(p0),
+                            _c.c_void_p(p.data_ptr()), _c.c_void_p(E.data_ptr()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_rs_energy")
+    return E, p[:N]
 
 
 def rhosvd_selftest_fastmath(x, stream=None):

@@ -292,6 +292,16 @@ CONFIGS = {
     "newton_lr_n2048_N1000": dict(n=2048, N=1000, seed=0, eps=1e-6),
     "learned_n1024_R2000_8000": dict(n=1024, R_range=(2000, 8000), train_seed=10**6, n_train=20000,
                                      eval_seed=10**6 + 20000, n_eval=2000, eps=1e-6, nprop=32),
+    # long-range multi-Slater lattice sums (Tables Tab:random_ranks, Tab:func_ranks), C2C thresholds
+    "slater_lattice_random_n384": dict(n_cells=384, b=10.0, m=20, lam=0.5, h=1.56, amplitudes="random", seed=0,
+                                       lattices=[(4, 4, 4), (6, 6, 6), (8, 8, 8), (16, 16, 8), (16, 16, 16)],
+                                       eps_tucker=1e-3, eps_t2c=1e-5),
+    "slater_lattice_func_n232": dict(n_cells=232, b=10.0, m=12, lam=0.5, h=1.56, amplitudes="func", seed=0,
+                                     lattices=[(4, 4, 4), (6, 6, 6), (8, 8, 8), (16, 16, 8), (16, 16, 16)],
+                                     eps_tucker=1e-3, eps_t2c=1e-5),
+    # interaction energy of 16^3 charges from the reduced long-range potential (Lemma lem:InterEnergy)
+    "newton_lattice_energy_N4096": dict(n_cells=384, b=24.0, L=(16, 16, 16), m=24, h=0.4, k_lo=-40, seed=0,
+                                        eps_tucker=1e-6, eps_t2c=1e-8),
 }
 
 
