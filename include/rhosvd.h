@@ -140,6 +140,32 @@ int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rhosvd_tucker
                void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * RHOSVD followed by ALS sweeps toward the best rank-r Tucker approximation (Sec. 2.2, the ALS
+ * step after Def. 2.2, eq. can_A_Tuck_als).  The ranks r_l are the RHOSVD's (eps rule or fixed).
+ * One sweep updates the modes 0, 1, 2 in turn: with the other two factors fixed, the contraction
+ * of the canonical tensor with them has the mode-l unfolding U~_l diag(xi') (V_m2 (.) V_m1)^T
+ * (V_m = Z_m^T U~_m), and Z_l becomes its r_l leading left singular vectors.  The step is taken
+ * inside the RHOSVD's orthonormal basis Q_l of the side matrix (the sketch range, or the identity
+ * for a direct mode): C_l = (Q_l^T U~_l) diag(xi') (V_m2 (.) V_m1)^T, W_l = the r_l leading
+ * eigenvectors of C_l C_l^T, Z_l = Q_l W_l.  Each step cannot lower the captured energy
+ * ||beta||^2, so the Tucker error ||A||^2 - ||beta||^2 never grows.  All ALS products run in FP64
+ * on the CUDA cores (the RHOSVD part follows opts->precision).
+ *   sweeps     0 .. RHOSVD_ALS_MAX_SWEEPS (0 = plain rhosvd_c2t)
+ *   out        as rhosvd_c2t: Z, beta and V are the refined ones; sigma and info (tail, resid)
+ *              describe the RHOSVD start
+ *   energy     host array of 6 sweeps doubles or NULL: for step s = 3 sweep + l, energy[2 s] is
+ *              ||beta||^2 before and energy[2 s + 1] after the mode-l update (the call then
+ *              synchronises `stream`; with NULL it stays asynchronous)
+ *   workspace  rhosvd_c2t_als_workspace_size(cp, opts, sweeps) bytes (the RHOSVD's plus the
+ *              r_max^2-column contraction C_l and its Gram partials)
+ * Errors as rhosvd_c2t.
+ */
+#define RHOSVD_ALS_MAX_SWEEPS 8
+size_t rhosvd_c2t_als_workspace_size(const rhosvd_cp* cp, const rhosvd_opts* opts, int sweeps);
+int rhosvd_c2t_als(const rhosvd_cp* cp, const rhosvd_opts* opts, int sweeps, const rhosvd_tucker* out,
+                   double* energy, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Hadamard (entrywise) product of two canonical tensors with equal mode sizes
  * (Sec. 3 eq. rho_ten; Lemma 4.2): term nu = i + Ra * j of the result has columns
  * u^(l)_nu = a^(l)_i .* b^(l)_j and weight xa_i * xb_j; rank Ra * Rb.

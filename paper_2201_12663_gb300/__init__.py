@@ -157,6 +157,12 @@ def load(build_if_missing: bool = False):
         L.rhosvd_t2c.argtypes = [_c.POINTER(rhosvd_tucker_in), _c.c_double, _c.c_int, _c.c_void_p * 3, _c.c_int * 3,
                                  _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_size_t,
                                  _c.c_void_p]
+        L.rhosvd_c2t_als_workspace_size.restype = _c.c_size_t
+        L.rhosvd_c2t_als_workspace_size.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts), _c.c_int]
+        L.rhosvd_c2t_als.restype = _c.c_int
+        L.rhosvd_c2t_als.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_opts), _c.c_int,
+                                     _c.POINTER(rhosvd_tucker), _c.POINTER(_c.c_double), _c.c_void_p, _c.c_size_t,
+                                     _c.c_void_p]
         L.rhosvd_c2t_hadamard_workspace_size.restype = _c.c_size_t
         L.rhosvd_c2t_hadamard_workspace_size.argtypes = [_c.POINTER(rhosvd_cp), _c.POINTER(rhosvd_cp),
                                                          _c.POINTER(rhosvd_opts)]
@@ -528,6 +534,33 @@ def rhosvd_c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0
     if rc != RHOSVD_OK:
         raise RhosvdError(rc, "rhosvd_c2t")
     return out
+
+
+def rhosvd_c2t_als(U, xi, sweeps=1, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0, out=None,
+                   workspace=None, stream=None, with_V=False, with_xi=False, precision=RHOSVD_PLAIN_FP64,
+                   deflate=0, energies=True):
+    """RHOSVD followed by `sweeps` ALS sweeps.  Returns (TuckerResult, energies) where energies is
+    a list of (before, after) captured energies ||beta||^2 per mode step (the call then
+    synchronises), or None with energies=False."""
+    torch = _torch()
+    L = load()
+    cp = make_cp(U, xi)
+    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate)
+    need = int(L.rhosvd_c2t_als_workspace_size(_c.byref(cp), _c.byref(opts), int(sweeps)))
+    if need == 0:
+        raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_c2t_als_workspace_size")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=U[0].device)
+    if out is None:
+        out = alloc_tucker([cp.n[l] for l in range(3)], cp.R, r_max, U[0].device, with_V, with_xi)
+    t = tucker_struct(out)
+    e = (_c.c_double * max(6 * int(sweeps), 1))() if energies else None
+    rc = L.rhosvd_c2t_als(_c.byref(cp), _c.byref(opts), int(sweeps), _c.byref(t), e,
+                          _c.c_void_p(workspace.data_ptr()), _c.c_size_t(workspace.numel()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_c2t_als")
+    hist = [(e[2 * s], e[2 * s + 1]) for s in range(3 * int(sweeps))] if energies else None
+    return out, hist
 
 
 def rhosvd_c2t_hadamard(Ua, xa, Ub, xb, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0, out=None,

@@ -132,6 +132,9 @@ struct Plan {
     size_t o_ozpart;      // their partial sums
     long long sU1, sU2, sP1, sP2; // per-mode plane-set sizes (elements)
     long long rp_stride;   // residual partials per mode (tiles of the residual GEMM)
+    // ALS refinement (als > 0 sweeps): C_l (KW x rmax^2), split-K partials of G_l, energies
+    int als, ks_als;
+    size_t o_als_C, o_als_part, o_als_e, o_als_q, o_als_k;
     size_t total;
 };
 
@@ -147,7 +150,7 @@ int choose_split(int tiles, int K)
 
 int tiles_of(int M, int N) { return ((M + 63) / 64) * ((N + 63) / 64); }
 
-int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0)
+int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, int als = 0)
 {
     if (!cp || !o) return RHOSVD_ERR_INVALID_ARG;
     if (cp->R < 0) return RHOSVD_ERR_INVALID_ARG;
@@ -270,6 +273,16 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0)
         if (3LL * p->oz_s_bbt * KK > zp) zp = 3LL * p->oz_s_bbt * KK;
         p->o_ozpart = take(sizeof(double) * (size_t)zp);
     }
+    p->als = als;
+    if (als > 0) {
+        const long long KC = (long long)p->rmax * p->rmax;
+        p->ks_als = choose_split(tiles_of(p->KW, p->KW), (int)KC);
+        p->o_als_C = take(sizeof(double) * (size_t)p->KW * (size_t)KC);
+        p->o_als_part = take(sizeof(double) * (size_t)p->ks_als * KK);
+        p->o_als_e = take(sizeof(double) * 6 * (size_t)als);
+        p->o_als_q = take(sizeof(double) * rh::KMAX);
+        p->o_als_k = take(sizeof(int) * 3);
+    }
     p->total = off;
     return RHOSVD_OK;
 }
@@ -333,10 +346,11 @@ struct HadSrc {
 };
 
 static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBasis* sb0, const rhosvd_tucker* out,
-                    void* workspace, size_t workspace_bytes, void* stream, const HadSrc* had = nullptr)
+                    void* workspace, size_t workspace_bytes, void* stream, const HadSrc* had = nullptr,
+                    int als_sweeps = 0)
 {
     Plan p;
-    int rc = make_plan(cp, opts, &p, sb0 ? sb0->k0 : 0);
+    int rc = make_plan(cp, opts, &p, sb0 ? sb0->k0 : 0, als_sweeps);
     if (rc) return rc;
     if (!out || !out->info || !out->beta) return RHOSVD_ERR_INVALID_ARG;
     for (int l = 0; l < 3; ++l) {
@@ -1201,6 +1215,114 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
     }
     STAGE("rank_final", launch_rank_final(fa, st));
 
+    if (R > 0 && p.als > 0) {
+        // ---- ALS refinement (eq. can_A_Tuck_als), modes 0, 1, 2 in turn, inside the basis Q_l:
+        //      C_l = B_l diag(xi') (V_m2 (.) V_m1)^T, G_l = C_l C_l^T, W_l = its r_l leading
+        //      eigenvectors, V_l = W_l^T B_l; at the end Z_l = Q_l W_l.  The ranks stay r_l.
+        double* Cb = (double*)(ws + p.o_als_C);
+        double* Gpart = (double*)(ws + p.o_als_part);
+        double* Eh = (double*)(ws + p.o_als_e);
+        double* qpart = (double*)(ws + p.o_als_q);
+        int* kk = (int*)(ws + p.o_als_k);
+        const int KC = rmax * rmax;
+        for (int sw = 0; sw < p.als; ++sw) {
+            for (int l = 0; l < 3; ++l) {
+                const int m1 = l == 0 ? 1 : 0, m2 = l == 2 ? 1 : 2;
+                const int step = 3 * sw + l;
+                ModeMap one = {{l, l, l}};
+                double* Bl = Bm + (size_t)l * KW * R;
+                double* Gl = G + l * KK;
+                double* Wl = W + l * KK;
+                STAGE("als_prep", launch_als_set(S, l, kk, st));
+                GemmBatch gcb;
+                memset(&gcb, 0, sizeof(gcb));
+                gcb.nbatch = 1;
+                gcb.ksplit = 1;
+                gcb.bkind = B_KR;
+                GemmProblem c = blank_problem();
+                c.A = Mat{Bl, 1, KW};
+                c.C = Cb;
+                c.crs = 1;
+                c.ccs = KW;
+                c.M = p.kb[l];
+                c.dM = &S->m[l];
+                c.N = KC;
+                c.N_from_r2r3 = 1;
+                c.dNa = &S->r[m1];
+                c.dNb = &S->r[m2];
+                c.K = R;
+                c.V2 = Vw + m1 * VS;
+                c.V3 = Vw + m2 * VS;
+                c.xi = xin;
+                c.ldv = KW;
+                gcb.p[0] = c;
+                STAGE("als_contract", launch_gemm(gcb, st));
+                GemmBatch ggb;
+                memset(&ggb, 0, sizeof(ggb));
+                ggb.nbatch = 1;
+                ggb.ksplit = p.ks_als;
+                ggb.bkind = B_PLAIN;
+                GemmProblem g = blank_problem();
+                g.A = Mat{Cb, 1, KW};
+                g.B = Mat{Cb, KW, 1};
+                g.C = Gl;
+                g.crs = 1;
+                g.ccs = KW;
+                g.M = g.N = p.kb[l];
+                g.dM = g.dN = &S->m[l];
+                g.K = KC;
+                g.dK = &kk[l];
+                ggb.p[0] = g;
+                STAGE("als_gram", launch_gemm_splitk(ggb, Gpart, st));
+                STAGE("als_energy", launch_als_energy_before(Gl, KW, Wl, KW, &S->m[l], &S->r[l], rmax, qpart,
+                                                             Eh + 2 * step, st));
+                STAGE("als_eig", launch_tridiag(one, G, KK, KW, S->m, vd, ve, vtau, vs, 1, KW, st));
+                STAGE("als_eig", launch_eigvals(one, vd, ve, vs, S->m, vD, vL, vmu, S, 1, st));
+                STAGE("als_eig", launch_eigvecs(one, vD, vL, vmu, vs, S->m, S, W, KK, KW, KW, 1, st));
+                STAGE("als_eig", launch_backtransform(one, G, KK, KW, vtau, vs, S->m, S, W, KK, KW, KW, 1, st));
+                STAGE("als_energy", launch_als_energy_after(vmu + l * vs, S, l, Eh + 2 * step + 1, st));
+                GemmBatch gvb;
+                memset(&gvb, 0, sizeof(gvb));
+                gvb.nbatch = 1;
+                gvb.ksplit = 1;
+                gvb.bkind = B_PLAIN;
+                GemmProblem h = blank_problem();
+                h.A = Mat{Wl, KW, 1};
+                h.B = Mat{Bl, 1, KW};
+                h.C = Vw + l * VS;
+                h.crs = 1;
+                h.ccs = KW;
+                h.M = p.kb[l];
+                h.dM = &S->r[l];
+                h.N = R;
+                h.K = p.kb[l];
+                h.dK = &S->m[l];
+                gvb.p[0] = h;
+                STAGE("als_v", launch_gemm(gvb, st));
+            }
+        }
+        GemmBatch gzb;
+        memset(&gzb, 0, sizeof(gzb));
+        gzb.nbatch = 3;
+        gzb.ksplit = 1;
+        gzb.bkind = B_PLAIN;
+        for (int l = 0; l < 3; ++l) {
+            GemmProblem g = blank_problem();
+            g.A = Mat{Qfin[l], 1, (long long)ldq[l]};
+            g.B = Mat{W + l * KK, 1, KW};
+            g.C = Zw + l * NK;
+            g.crs = 1;
+            g.ccs = p.n[l];
+            g.M = p.n[l];
+            g.N = p.kb[l];
+            g.dN = &S->r[l];
+            g.K = p.kb[l];
+            g.dK = &S->m[l];
+            gzb.p[l] = g;
+        }
+        STAGE("als_z", launch_gemm(gzb, st));
+    }
+
     if (R > 0) {
         // ---- outputs: Z = Z_hi(:, :r), optional V = V_hi(:r, :)
         double* zd[3] = {out->Z[0], out->Z[1], out->Z[2]};
@@ -1327,6 +1449,29 @@ extern "C" int rhosvd_c2t_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, const
     h.Ra = a->R;
     h.xa = a->xi;
     return c2t_impl(&v, opts, nullptr, out, workspace, workspace_bytes, stream, v.R > 0 ? &h : nullptr);
+}
+
+extern "C" size_t rhosvd_c2t_als_workspace_size(const rhosvd_cp* cp, const rhosvd_opts* opts, int sweeps)
+{
+    Plan p;
+    if (sweeps < 0 || make_plan(cp, opts, &p, 0, sweeps) != RHOSVD_OK) return 0;
+    return p.total;
+}
+
+extern "C" int rhosvd_c2t_als(const rhosvd_cp* cp, const rhosvd_opts* opts, int sweeps, const rhosvd_tucker* out,
+                              double* energy, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (sweeps < 0 || sweeps > RHOSVD_ALS_MAX_SWEEPS) return RHOSVD_ERR_INVALID_ARG;
+    int rc = c2t_impl(cp, opts, nullptr, out, workspace, workspace_bytes, stream, nullptr, sweeps);
+    if (rc || !energy || sweeps == 0) return rc;
+    Plan p;
+    if (make_plan(cp, opts, &p, 0, sweeps) != RHOSVD_OK) return RHOSVD_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(energy, (char*)workspace + p.o_als_e, sizeof(double) * 6 * (size_t)sweeps,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RHOSVD_ERR_CUDA;
+    return RHOSVD_OK;
 }
 
 extern "C" size_t rhosvd_c2t_start_workspace_size(const rhosvd_cp* cp, const rhosvd_opts* opts, int k0)

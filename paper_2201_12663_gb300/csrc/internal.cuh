@@ -362,6 +362,12 @@ int launch_backtransform(ModeMap mm, const double* A, long long astride, int lda
                          const int* dk, const DevState* s, double* W, long long wstride, int ldw, int rmax,
                          int nb, cudaStream_t st);
 
+// ALS refinement helpers (als.cu): step sizes and the captured energy before/after a mode step
+int launch_als_set(DevState* s, int l, int* kk, cudaStream_t st);
+int launch_als_energy_before(const double* G, int ldg, const double* W, int ldw, const int* dm, const int* dr,
+                             int rmax, double* part, double* out, cudaStream_t st);
+int launch_als_energy_after(const double* mu, const DevState* s, int l, double* out, cudaStream_t st);
+
 }  // namespace rh
 
 namespace rh {
