@@ -43,12 +43,13 @@ extern "C" {
 #define RHOSVD_ERR_TIMEOUT (-9)         /* device: a bounded wait inside a kernel gave up      */
 
 #define RHOSVD_PLAIN_FP64 0             /* every step in FP64 on the CUDA cores              */
-#define RHOSVD_MIXED 1                  /* the large contractions (range sketch, projection, Ritz
-                                           vectors, residual, core) on the tcgen05 tensor cores
-                                           with exact 8-bit BF16 digit planes and FP32 accumulation
-                                           read back into double-float (about 2^-40 of sum|a||b|);
-                                           the Grams (they square the condition number) and the
-                                           small factorisations stay FP64                      */
+#define RHOSVD_MIXED 1                  /* the large contractions (range sketch, Grams,
+                                           projection, Ritz vectors, residual, core) on the
+                                           tcgen05 tensor cores with exact digit planes held as
+                                           BF16 (seven 7-bit digits for the FP64-class products,
+                                           four 8-bit digits for the core) and FP32 accumulation
+                                           read back into FP64 (about 2^-40 of sum|a||b| for the
+                                           core); the small factorisations stay FP64           */
 
 #define RHOSVD_K_MAX 256                /* largest subspace width k handled on the device    */
 
@@ -427,6 +428,11 @@ long long rhosvd_launch_count(void);
  * recorded on the call's stream (the events come from a pool the library creates on first
  * use; at most 4096 stages are kept between reads). */
 int rhosvd_profile_enable(int on);
+
+/* Restrict the per-stage timing to the stages named `stage` (a copy of at most 63 characters is
+ * kept; NULL or "" times every stage again).  With a filter, the other stages record no events,
+ * so one kernel can be timed inside a timed region without perturbing the rest. */
+int rhosvd_profile_filter(const char* stage);
 
 /* Wait for the recorded events, then write one line "stage count total_ms" per stage into
  * buf (host memory, len bytes, NUL-terminated when it fits) and clear the records.

@@ -187,6 +187,8 @@ def load(build_if_missing: bool = False):
         L.rhosvd_launch_count.restype = _c.c_longlong
         L.rhosvd_profile_enable.restype = _c.c_int
         L.rhosvd_profile_enable.argtypes = [_c.c_int]
+        L.rhosvd_profile_filter.restype = _c.c_int
+        L.rhosvd_profile_filter.argtypes = [_c.c_char_p]
         L.rhosvd_profile_read.restype = _c.c_int
         L.rhosvd_profile_read.argtypes = [_c.c_char_p, _c.c_int]
         _lib = L
@@ -439,6 +441,11 @@ def rhosvd_launch_count() -> int:
 
 def rhosvd_profile_enable(on: bool) -> bool:
     return bool(load().rhosvd_profile_enable(1 if on else 0))
+
+
+def rhosvd_profile_filter(stage=None) -> int:
+    """Time only the stages named `stage` (None: every stage)."""
+    return int(load().rhosvd_profile_filter(stage.encode() if stage else None))
 
 
 def rhosvd_profile_read() -> dict:

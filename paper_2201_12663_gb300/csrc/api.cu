@@ -45,10 +45,13 @@ cudaEvent_t pool_event()
     return e;
 }
 
+char g_prof_filter[64] = {0};
+
 int prof_begin(const char* name, cudaStream_t st)
 {
     if (!g_prof_on) return -1;
     std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_filter[0] && strcmp(name, g_prof_filter) != 0) return -1;
     if (g_prof_n >= PROF_MAX) return -1;
     cudaEvent_t a = pool_event(), b = pool_event();
     if (!a || !b) return -1;
@@ -81,6 +84,17 @@ extern "C" int rhosvd_profile_enable(int on)
     const int prev = g_prof_on;
     g_prof_on = on ? 1 : 0;
     return prev;
+}
+
+extern "C" int rhosvd_profile_filter(const char* stage)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_filter[0] = 0;
+    if (stage) {
+        strncpy(g_prof_filter, stage, sizeof(g_prof_filter) - 1);
+        g_prof_filter[sizeof(g_prof_filter) - 1] = 0;
+    }
+    return RHOSVD_OK;
 }
 
 extern "C" int rhosvd_profile_read(char* buf, int len)
