@@ -12,6 +12,8 @@ The remark, for a core beta of size r1 x r2 x r3 (slices along the third mode):
 Reading of the threshold (the remark states eps / r^{3/2} for an r x r x r core with an absolute
 eps): delta = eps ||beta||_F / (r3 sqrt(min(r1, r2))), so that every slice drops at most
 min(r1, r2) values below delta and the remark's bound becomes ||beta - beta_R|| <= eps ||beta||.
+A singular value at or below the slice's FP64 resolution min(r1, r2) u ||B_m||_F counts as zero
+(also for eps = 0): it is rounding, not a direction of the slice.
 The canonical factors of the whole tensor A = beta x_1 Z1 x_2 Z2 x_3 Z3 are
   xi_(m,k) = sigma_k(B_m),  u1 = Z1 u_k,  u2 = Z2 v_k,  u3 = Z3(:, m).
 """
@@ -38,7 +40,8 @@ def t2c_core(beta, eps):
     for m in range(r3):
         Bm = beta[:, :, m]
         U, s, Vt = np.linalg.svd(Bm, full_matrices=False)
-        p = int(np.sum(s > delta))
+        floor = min(r1, r2) * np.finfo(np.float64).eps * float(np.linalg.norm(Bm))
+        p = int(np.sum(s > max(delta, floor)))
         out["p"].append(p)
         out["sigma"].append(s[:p].copy())
         out["U"].append(U[:, :p].copy())

@@ -227,8 +227,11 @@ __global__ void __launch_bounds__(T2C_THREADS) k_t2c_slice(T2cDims d, const doub
         __syncthreads();                                  // every thread has read s_rot
         if (!any) break;
     }
-    // singular values (row norms), their descending ranks, the count above delta
-    const double dl = delta[0];
+    // singular values (row norms), their descending ranks, the count above delta; a value at or
+    // below the slice's FP64 resolution q u ||B_m||_F counts as zero even for delta = 0 (its left
+    // vector B v / sigma would be rounding noise, and re-orthonormalising noise leaves U_p
+    // non-orthonormal)
+    const double dl = fmax(delta[0], (double)q * DBL_EPSILON * sqrt(f2));
     for (int k = warp; k < q; k += NW) {
         double ss = 0.0;
         for (int c = lane; c < r2; c += 32) {

@@ -134,3 +134,16 @@ def test_newton_cube_full_size(rhosvd_cuda, long_range):
     assert float(torch.linalg.norm(Yh - cube)) <= bnd
     oh_ = oh.horner(cp.U, cp.xi, [0, 0, 0, 1], eps_t, eps_c)
     _ranks_close(h.steps, oh_["steps"])
+
+
+@pytest.mark.parametrize("coeffs", [[0.5, -1.0, 2.0], [0.0, 0.0, 1.0]])
+def test_horner_exact_with_rank_deficient_cores(rhosvd_cuda, coeffs):
+    """n = 20 with every Tucker rank at n after the second product: the cores carry singular values
+    at rounding level, which T2C must treat as zero (else its re-orthonormalised left vectors are
+    noise and the C2C is off by O(1))."""
+    P = rhosvd_cuda
+    cp = workloads.gaussian_sum(20, 4, 2, b=3.0, centre_box=1.5, a_range=(0.3, 2.0))
+    U, x = _dev(P, cp.U, cp.xi)
+    res = P.rhosvd_cp_horner(U, x, coeffs, 0.0, 0.0, R_max=400, r_max=20)
+    ref = npoly.polyval(ot.full_from_cp(cp.U, cp.xi), np.asarray(coeffs, dtype=np.float64))
+    assert np.abs(_full_gpu(res) - ref).max() <= 1e-12 * np.abs(ref).max()
