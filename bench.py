@@ -760,6 +760,17 @@ def run_ours(args):
     step3, out3, ws3 = make_form(main_prec, fused=not args.fused)
     ms3, _, _, _ = time_form(step3, out3, max(3, args.steps // 2), False)
     del ws3
+    # the headline step captured once into a CUDA graph (rhosvd_graph_*) and replayed
+    gstream = torch.cuda.Stream()
+    with torch.cuda.stream(gstream):
+        step4, out4, ws4 = make_form(main_prec)
+        for _ in range(3):
+            step4()
+        torch.cuda.synchronize()
+        graph = P.rhosvd_capture(step4, gstream)
+        ms4, _, _, info4 = time_form(lambda: graph.replay(gstream), out4, max(3, args.steps // 2), False)
+        graph.close()
+    del ws4
 
     # agreement of the two forms (Tucker tensors), computed on the device with torch
     def tucker_of(res):
@@ -856,6 +867,9 @@ def run_ours(args):
             f"{other}_form": {"value": world * 1000.0 / ms2, "ms_per_step": ms2,
                               "stage_ms_per_step": {k: v[1] / max(3, args.steps // 2) for k, v in prof2.items()}},
             "speedup_vs_other_form": ms2 / ms_per_step,
+            "graph_replay": {"ms_per_step": ms4, "value": world * 1000.0 / ms4,
+                             "ranks": [info4.r[l] for l in range(3)],
+                             "note": "the same step captured once (rhosvd_graph_begin/end) and replayed"},
             ("fused_product" if not args.fused else "stored_product"): {
                 "ms_per_step": ms3, "value": world * 1000.0 / ms3,
                 "note": "same precision; rhosvd_c2t_hadamard (no stored product)" if not args.fused

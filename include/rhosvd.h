@@ -317,7 +317,8 @@ int rhosvd_proposal_basis(int n, const double* QT, const float* Y, double* Q0, v
  *              beta r1 x r2 x r3 with entry (i, j, m) at beta[i + r1 (j + r2 m)], as rhosvd_c2t
  *              writes it); r1 r2 <= RHOSVD_T2C_SLICE_MAX and r1, r2 <= 1024 (a slice is
  *              factorised in one block's shared memory)
- *   eps        relative accuracy, >= 0 (0 keeps every nonzero singular value)
+ *   eps        relative accuracy, >= 0 (0 keeps every singular value above the slice's FP64
+ *              resolution min(r1, r2) u ||B_m||_F; values at or below it count as zero)
  *   R_max      capacity of the outputs (columns); U[l] n_l x R_max with leading dimension
  *              ldu[l] >= n_l, xi R_max (device, caller-owned)
  *   R_out      device int: the canonical rank R (also when it exceeds R_max)
@@ -419,6 +420,22 @@ int rhosvd_selftest_fastmath(const double* x, double* rcp, double* rsq, int n, v
 
 /* ---------------------------------------------------------------- tracing (no paper
  * counterpart: observability of the library itself) */
+
+/* Replayable call sequences (no paper counterpart: serving the same shapes repeatedly).
+ * rhosvd_graph_begin starts capturing the library calls made on `stream` by this thread (a
+ * created stream, not the legacy NULL stream) into a CUDA graph; rhosvd_graph_end stops, builds
+ * the executable graph and returns its handle; rhosvd_graph_launch replays every captured kernel
+ * on `stream` with the pointers of the capture (new inputs go into the same buffers);
+ * rhosvd_graph_destroy frees it.  Calls whose ranks size later launches on the host
+ * (rhosvd_cp_horner, rhosvd_c2t_als with energies) cannot be captured; every call that keeps its
+ * ranks on the device (rhosvd_c2t, its fused, start and ALS forms without energies, the
+ * products and sums, rhosvd_t2c, the energy) can.  Stage timing must be off or filtered while
+ * capturing.  Errors: RHOSVD_ERR_INVALID_ARG (NULL stream or handle, nested capture),
+ * RHOSVD_ERR_CUDA. */
+int rhosvd_graph_begin(void* stream);
+int rhosvd_graph_end(void* stream, void** graph);
+int rhosvd_graph_launch(void* graph, void* stream);
+int rhosvd_graph_destroy(void* graph);
 
 /* Number of CUDA kernel launches the library has made since it was loaded (all threads). */
 long long rhosvd_launch_count(void);

@@ -187,6 +187,14 @@ def load(build_if_missing: bool = False):
         L.rhosvd_launch_count.restype = _c.c_longlong
         L.rhosvd_profile_enable.restype = _c.c_int
         L.rhosvd_profile_enable.argtypes = [_c.c_int]
+        L.rhosvd_graph_begin.restype = _c.c_int
+        L.rhosvd_graph_begin.argtypes = [_c.c_void_p]
+        L.rhosvd_graph_end.restype = _c.c_int
+        L.rhosvd_graph_end.argtypes = [_c.c_void_p, _c.POINTER(_c.c_void_p)]
+        L.rhosvd_graph_launch.restype = _c.c_int
+        L.rhosvd_graph_launch.argtypes = [_c.c_void_p, _c.c_void_p]
+        L.rhosvd_graph_destroy.restype = _c.c_int
+        L.rhosvd_graph_destroy.argtypes = [_c.c_void_p]
         L.rhosvd_profile_filter.restype = _c.c_int
         L.rhosvd_profile_filter.argtypes = [_c.c_char_p]
         L.rhosvd_profile_read.restype = _c.c_int
@@ -441,6 +449,47 @@ def rhosvd_launch_count() -> int:
 
 def rhosvd_profile_enable(on: bool) -> bool:
     return bool(load().rhosvd_profile_enable(1 if on else 0))
+
+
+class Graph:
+    """A captured sequence of library calls (see rhosvd_graph_begin); replay() launches it."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def replay(self, stream=None):
+        rc = load().rhosvd_graph_launch(self.handle, _stream_handle(stream))
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_graph_launch")
+
+    def close(self):
+        if self.handle:
+            load().rhosvd_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rhosvd_capture(fn, stream):
+    """Run fn() under capture on `stream` (a torch.cuda.Stream, not the default stream); returns
+    a Graph replaying the library kernels fn launched."""
+    L = load()
+    h = _stream_handle(stream)
+    rc = L.rhosvd_graph_begin(h)
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_graph_begin")
+    try:
+        fn()
+    finally:
+        g = _c.c_void_p()
+        rc = L.rhosvd_graph_end(h, _c.byref(g))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_graph_end")
+    return Graph(g.value)
 
 
 def rhosvd_profile_filter(stage=None) -> int:

@@ -5,6 +5,7 @@
 #include "ozgemm.cuh"
 #include <atomic>
 #include <mutex>
+#include <new>
 #include <stdio.h>
 #include <string.h>
 
@@ -84,6 +85,68 @@ extern "C" int rhosvd_profile_enable(int on)
     const int prev = g_prof_on;
     g_prof_on = on ? 1 : 0;
     return prev;
+}
+
+// ---- replayable sequences of library calls (CUDA graphs)
+namespace {
+struct GraphRec {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    long long launches;
+};
+thread_local long long g_capture_start = -1;
+}  // namespace
+
+extern "C" int rhosvd_graph_begin(void* stream)
+{
+    if (!stream || g_capture_start >= 0) return RHOSVD_ERR_INVALID_ARG;
+    if (cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return RHOSVD_ERR_CUDA;
+    g_capture_start = g_launches.load();
+    return RHOSVD_OK;
+}
+
+extern "C" int rhosvd_graph_end(void* stream, void** graph)
+{
+    if (!stream || !graph || g_capture_start < 0) return RHOSVD_ERR_INVALID_ARG;
+    const long long n = g_launches.load() - g_capture_start;
+    g_capture_start = -1;
+    *graph = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture((cudaStream_t)stream, &g) != cudaSuccess || !g) return RHOSVD_ERR_CUDA;
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return RHOSVD_ERR_CUDA;
+    }
+    GraphRec* r = new (std::nothrow) GraphRec{g, ex, n};
+    if (!r) {
+        cudaGraphExecDestroy(ex);
+        cudaGraphDestroy(g);
+        return RHOSVD_ERR_CUDA;
+    }
+    g_launches.fetch_sub(n);          // counted again at every replay
+    *graph = r;
+    return RHOSVD_OK;
+}
+
+extern "C" int rhosvd_graph_launch(void* graph, void* stream)
+{
+    if (!graph) return RHOSVD_ERR_INVALID_ARG;
+    GraphRec* r = (GraphRec*)graph;
+    if (cudaGraphLaunch(r->exec, (cudaStream_t)stream) != cudaSuccess) return RHOSVD_ERR_CUDA;
+    g_launches.fetch_add(r->launches);
+    return RHOSVD_OK;
+}
+
+extern "C" int rhosvd_graph_destroy(void* graph)
+{
+    if (!graph) return RHOSVD_OK;
+    GraphRec* r = (GraphRec*)graph;
+    cudaGraphExecDestroy(r->exec);
+    cudaGraphDestroy(r->graph);
+    delete r;
+    return RHOSVD_OK;
 }
 
 extern "C" int rhosvd_profile_filter(const char* stage)
