@@ -300,6 +300,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t aBase = smem_u32(oz_smem + buf * STAGE);
             const uint32_t bBase = aBase + SA * A_PLANE;
+            // descriptors of the stage's first A and B planes; a plane or K-half at byte offset o
+            // (a multiple of 16) is the base descriptor plus o / 16 in the 14-bit address field,
+            // which cannot carry: shared addresses stay below 2^18
+            const uint64_t dA0 = oz_desc(aBase), dB0 = oz_desc(bBase);
             bool started[NU];
 #pragma unroll
             for (int a = 0; a < NU; ++a) started[a] = false;
@@ -316,8 +320,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
                     const uint32_t tacc = tmem + (uint32_t)(a * NT);
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
-                        const uint64_t da = oz_desc(aBase + (s - 1) * A_PLANE + kk * 256);
-                        const uint64_t db = oz_desc(bBase + (t - 1) * B_PLANE + kk * 256);
+                        const uint64_t da = dA0 + (uint64_t)(((s - 1) * A_PLANE + kk * 256) >> 4);
+                        const uint64_t db = dB0 + (uint64_t)(((t - 1) * B_PLANE + kk * 256) >> 4);
                         oz_mma(tacc, da, db, IDESC, kk > 0 ? 1u : acc);
                     }
                 }
