@@ -451,6 +451,12 @@ int rhosvd_profile_enable(int on);
  * so one kernel can be timed inside a timed region without perturbing the rest. */
 int rhosvd_profile_filter(const char* stage);
 
+/* Keep (1) the recorded stage events across rhosvd_profile_read instead of clearing them, so that
+ * the events a graph capture recorded (see rhosvd_graph_begin: while capturing, a stage's events
+ * become record nodes that every replay executes) can be read after each replay; 0 clears the
+ * records.  Returns the previous setting. */
+int rhosvd_profile_keep(int on);
+
 /* Wait for the recorded events, then write one line "stage count total_ms" per stage into
  * buf (host memory, len bytes, NUL-terminated when it fits) and clear the records.
  * Returns the number of bytes written, or RHOSVD_ERR_CUDA. */

@@ -195,6 +195,8 @@ def load(build_if_missing: bool = False):
         L.rhosvd_graph_launch.argtypes = [_c.c_void_p, _c.c_void_p]
         L.rhosvd_graph_destroy.restype = _c.c_int
         L.rhosvd_graph_destroy.argtypes = [_c.c_void_p]
+        L.rhosvd_profile_keep.restype = _c.c_int
+        L.rhosvd_profile_keep.argtypes = [_c.c_int]
         L.rhosvd_profile_filter.restype = _c.c_int
         L.rhosvd_profile_filter.argtypes = [_c.c_char_p]
         L.rhosvd_profile_read.restype = _c.c_int
@@ -490,6 +492,11 @@ def rhosvd_capture(fn, stream):
     if rc != RHOSVD_OK:
         raise RhosvdError(rc, "rhosvd_graph_end")
     return Graph(g.value)
+
+
+def rhosvd_profile_keep(on=True) -> int:
+    """Keep the recorded stage events across reads (graph replays re-record them)."""
+    return int(load().rhosvd_profile_keep(1 if on else 0))
 
 
 def rhosvd_profile_filter(stage=None) -> int:

@@ -47,6 +47,18 @@ cudaEvent_t pool_event()
 }
 
 char g_prof_filter[64] = {0};
+int g_prof_keep = 0;
+
+// an event record that also works while the stream is being captured into a graph (there it
+// becomes a record node that every replay executes)
+void prof_record(cudaEvent_t e, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
 
 int prof_begin(const char* name, cudaStream_t st)
 {
@@ -57,13 +69,13 @@ int prof_begin(const char* name, cudaStream_t st)
     cudaEvent_t a = pool_event(), b = pool_event();
     if (!a || !b) return -1;
     g_prof[g_prof_n] = ProfRec{name, a, b};
-    cudaEventRecord(a, st);
+    prof_record(a, st);
     return g_prof_n++;
 }
 
 void prof_end(int id, cudaStream_t st)
 {
-    if (id >= 0) cudaEventRecord(g_prof[id].b, st);
+    if (id >= 0) prof_record(g_prof[id].b, st);
 }
 }  // namespace
 
@@ -149,6 +161,18 @@ extern "C" int rhosvd_graph_destroy(void* graph)
     return RHOSVD_OK;
 }
 
+extern "C" int rhosvd_profile_keep(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    const int prev = g_prof_keep;
+    g_prof_keep = on ? 1 : 0;
+    if (!on) {
+        g_prof_n = 0;
+        g_pool_used = 0;
+    }
+    return prev;
+}
+
 extern "C" int rhosvd_profile_filter(const char* stage)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -172,8 +196,10 @@ extern "C" int rhosvd_profile_read(char* buf, int len)
         if (j == g_acc_n && g_acc_n < 64) g_acc[g_acc_n++] = ProfAcc{g_prof[i].name, 0.0, 0};
         if (j < 64) { g_acc[j].ms += ms; g_acc[j].count += 1; }
     }
-    g_prof_n = 0;
-    g_pool_used = 0;
+    if (!g_prof_keep) {
+        g_prof_n = 0;
+        g_pool_used = 0;
+    }
     int w = 0;
     for (int j = 0; j < g_acc_n && buf && w < len; ++j)
         w += snprintf(buf + w, (size_t)(len - w), "%s %lld %.6f\n", g_acc[j].name, g_acc[j].count, g_acc[j].ms);
