@@ -652,6 +652,22 @@ def als_leg(P, steps, warmup, precision):
     return out
 
 
+def max_over_ranks(x, dev, world):
+    """The largest of every rank's value (the slowest replica sets the job's step time); the
+    value itself when there is one rank.  Works with any torch.distributed backend."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_rate(ms_step, world):
+    """Whole-job reductions per second: every replica reduces one tensor a step."""
+    return world * 1000.0 / ms_step
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -728,10 +744,8 @@ def run_ours(args):
         launches = P.rhosvd_launch_count() - l0
         P.rhosvd_profile_enable(False)
         prof = P.rhosvd_profile_read()
-        tot = torch.tensor([sum(s.elapsed_time(e) for s, e in zip(starts, ends))], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-        return tot.item() / steps, prof, launches, out.info()
+        tot = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), dev, world)
+        return tot / steps, prof, launches, out.info()
 
     main_prec = args.precision
     other = "plain" if main_prec == "mixed" else "mixed"
@@ -792,11 +806,8 @@ def run_ours(args):
     if info.status != 0:
         raise RuntimeError(P.rhosvd_strerror(info.status))
     prof_dom = {dom: (dom_cnt, dom_ms)} if dom_cnt else {}
-    tot = torch.tensor([sum(a.elapsed_time(b) for a, b in zip(e_s, e_e))], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    ms_per_step = tot.item() / args.steps
-    value = world * 1000.0 / ms_per_step
+    ms_per_step = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(e_s, e_e)), dev, world) / args.steps
+    value = job_rate(ms_per_step, world)
 
     # the other form, same run, same inputs (comparison; not the headline)
     step2, out2, ws2 = make_form(other)
@@ -852,10 +863,7 @@ def run_ours(args):
     gctx.__exit__(None, None, None)
     graph.close()
     e2e_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(e_s, e_e)) / args.steps
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * 1000.0 / te.item()
+    e2e_value = job_rate(max_over_ranks(e2e_ms, dev, world), world)
 
     # ---- roofline of the dominant stage (largest share in the traced pass), its launches timed
     #      by CUDA events on the launching stream inside the timed region
