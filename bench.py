@@ -186,11 +186,17 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def algorithmic_flops(stage, info, n, R):
-    """FP64-class flops of one launch of a stage (all three modes), from the ranks it saw."""
+def algorithmic_flops(stage, info, n, R, kin=None):
+    """FP64-class flops of one launch of a stage (all three modes), from the ranks it saw; kin is
+    the sketch width r_max + oversample (the bench workload's by default)."""
     r = [info.r[l] for l in range(3)]
     k = [info.k[l] for l in range(3)]
-    kin = WORKLOAD["r_max"] + WORKLOAD["oversample"]
+    if kin is None:
+        kin = WORKLOAD["r_max"] + WORKLOAD["oversample"]
+    kin = min(kin, n)
+    if stage == "als_contract":
+        # one mode a launch: C_l = B_l diag(xi) (V_m2 (.) V_m1)^T, k_l x r_m1 r_m2, R deep; mean
+        return sum(2.0 * k[l] * r[(l + 1) % 3] * r[(l + 2) % 3] * R for l in range(3)) / 3
     if stage == "core":
         return 2.0 * r[0] * r[1] * r[2] * R
     if stage == "sketch":
@@ -472,7 +478,8 @@ def poly_leg(P, steps, warmup, precision):
             return P.rhosvd_cp_horner(U, x, [0, 0, 0, 1], POLY["eps_tucker"], POLY["eps_t2c"], R_max=2000,
                                       r_max=64, precision=PRECISIONS[precision])
 
-        rec = {}
+        rec = {"roofline_direct": stage_roofline(P, direct, lambda r_: r_[1].info(), POLY["n"], cp.R ** 3, 96,
+                                                 precision)}
         for tag, fn in (("direct", direct), ("horner", horner)):
             for _ in range(max(warmup, 1)):
                 res = fn()
@@ -566,8 +573,9 @@ def rs_leg(P, steps, warmup, precision):
     U = [P.to_device_factor(u) for u in cp.U]
     x = torch.from_numpy(cp.xi).cuda()
     z = torch.from_numpy(M["z"]).cuda()
-    (can, tk), ms_c2c = timed(lambda: P.rhosvd_c2c(U, x, eps_t, eps_c, R_max=160 * 160, r_max=160,
-                                                   precision=PRECISIONS[precision]))
+    c2c_e = lambda: P.rhosvd_c2c(U, x, eps_t, eps_c, R_max=160 * 160, r_max=160, precision=PRECISIONS[precision])
+    roof_e = stage_roofline(P, c2c_e, lambda r_: r_[1].info(), C["n_cells"] + 1, cp.R, 192, precision)
+    (can, tk), ms_c2c = timed(c2c_e)
     R, st = can.rank()
     info = tk.info()
     Ur = [can.U[l][:, :R] for l in range(3)]
@@ -585,7 +593,7 @@ def rs_leg(P, steps, warmup, precision):
                      "E_reduced": Er, "E_unreduced": Ef, "E_coulomb_direct": Ec,
                      "rel_diff_reduced_vs_unreduced": abs(Er - Ef) / abs(Ef),
                      "rel_diff_unreduced_vs_coulomb": abs(Ef - Ec) / abs(Ec),
-                     "oracle_coulomb_s": t_c, "oracle_cores": 1}
+                     "oracle_coulomb_s": t_c, "oracle_cores": 1, "roofline_c2c": roof_e}
     return out
 
 
@@ -635,12 +643,18 @@ def als_leg(P, steps, warmup, precision):
                                                           precision=PRECISIONS[precision]), None))
     for name, U, x, kw, cp in cases:
         (res, hist), ms_als = timed(lambda: P.rhosvd_c2t_als(U, x, sweeps=1, **kw))
+        P.rhosvd_profile_filter("als_contract")
+        roof = stage_roofline(P, lambda: P.rhosvd_c2t_als(U, x, sweeps=1, energies=False, **kw)[0],
+                              lambda r_: r_.info(), U[0].shape[0], x.shape[0], kw["r_max"] + kw.get("oversample", 32),
+                              "plain")
+        P.rhosvd_profile_filter(None)
         rh, ms_rh = timed(lambda: P.rhosvd_c2t(U, x, **kw))
         e0, e1 = hist[0][0], hist[-1][1]
         info = res.info()
         rec = {"ms_rhosvd_plus_1_sweep": ms_als, "ms_rhosvd": ms_rh, "ms_sweep": ms_als - ms_rh,
                "ranks": [info.r[l] for l in range(3)], "status": info.status,
-               "energy_gain_rel": (e1 - e0) / e0, "energy_steps": [[b, a] for b, a in hist]}
+               "energy_gain_rel": (e1 - e0) / e0, "energy_steps": [[b, a] for b, a in hist],
+               "roofline_contract": roof}
         if cp is not None:
             rec["rel_err_rhosvd"] = full_err(U, x, rh)
             rec["rel_err_als"] = full_err(U, x, res)
@@ -649,6 +663,42 @@ def als_leg(P, steps, warmup, precision):
             rec["oracle_s"] = time.perf_counter() - t0
             rec["oracle_cores"] = 1
         out[name] = rec
+    return out
+
+
+def stage_roofline(P, fn, info_of, n, R, kin, precision):
+    """Run fn() once with the library's stage tracing and give the roofline of its dominant
+    stage (the one with the most time): algorithmic FP64-class flops of a launch (from the ranks
+    the call returned, info_of(result)) over the launch's average duration; tensor-core stages
+    against the measured BF16 rate over the digit pairs, FP64 stages against the nominal FP64
+    rate.  None when the stage has no flop model."""
+    import torch
+    torch.cuda.synchronize()
+    P.rhosvd_profile_read()
+    P.rhosvd_profile_enable(True)
+    res = fn()
+    torch.cuda.synchronize()
+    P.rhosvd_profile_enable(False)
+    prof = P.rhosvd_profile_read()
+    if not prof:
+        return None
+    name, (cnt, ms_tot) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg = ms_tot / cnt
+    fl = algorithmic_flops(name, info_of(res), n, R, kin)
+    out = {"kernel": name, "avg_launch_ms": avg, "launches": cnt, "stage_ms_total": ms_tot,
+           "call_ms_traced": sum(v[1] for v in prof.values())}
+    if fl is None:
+        out.update({"bound": None, "achieved": None, "note": "no flop model for this stage"})
+        return out
+    ach = fl / (avg * 1e-3) / 1e12
+    if precision == "mixed" and name in MIXED_PAIRS:
+        peak = peaks().get("bf16_tflops", 1912.0) / MIXED_PAIRS[name]
+        out.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "peak_source": f"MEASURED_PEAKS.json bf16_tflops (of measured) / {MIXED_PAIRS[name]} digit pairs"})
+    else:
+        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "GB300 nominal FP64 rate (of fallback)"})
+    out["algorithmic_flops_per_launch"] = fl
     return out
 
 

@@ -233,6 +233,7 @@ struct Plan {
     long long EX;         // per-mode stride of the per-row exponent arrays
     int oz_s_sketch, oz_s_gram, oz_s_bbt;   // split-K counts of the tensor-core products
     size_t o_ozpart;      // their partial sums
+    long long ozpart_n;   // its capacity in doubles
     long long sU1, sU2, sP1, sP2; // per-mode plane-set sizes (elements)
     long long rp_stride;   // residual partials per mode (tiles of the residual GEMM)
     // ALS refinement (als > 0 sweeps): C_l (KW x rmax^2), split-K partials of G_l, energies
@@ -375,6 +376,7 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
         if (3LL * p->oz_s_gram * KK > zp) zp = 3LL * p->oz_s_gram * KK;
         if (3LL * p->oz_s_bbt * KK > zp) zp = 3LL * p->oz_s_bbt * KK;
         p->o_ozpart = take(sizeof(double) * (size_t)zp);
+        p->ozpart_n = zp;
     }
     p->als = als;
     if (als > 0) {
@@ -1503,6 +1505,15 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             q.C = out->beta;
             q.crs = -1;
             q.ccs = 1;
+            // split-K by the ranks (on the device): few output tiles (small ranks) with a long
+            // R spread over more SMs, the partials in the tensor-core partial buffer
+            constexpr int CORE_SMAX = 8;
+            const long long sstride = p.ozpart_n / CORE_SMAX;
+            STAGE("core_prep", launch_core_split(S->r, R, CORE_SMAX, sstride, &S->core_split, st));
+            ob.nsplit = CORE_SMAX;
+            q.Cpart = ozpart;
+            q.split_stride = sstride;
+            q.dsplit = &S->core_split;
             STAGE("core", launch_ozgemm(ob, OZ_CORE, st));
         } else {
             STAGE("core", launch_gemm(gc, st));

@@ -29,6 +29,7 @@ struct DevState {
     double total[3];    // ||U^(l) normalised||_F^2
     double rho2[3];     // ||U - Z_hi V_hi||_F^2, energy outside the rhi leading directions
     double specmax[3];  // upper bound of the spectrum of L D L^T
+    int core_split;     // split-K count of the tensor-core Khatri-Rao core (from the ranks)
 };
 
 // Counter-based sign generator for the Rademacher sketch: bit (c & 63) of

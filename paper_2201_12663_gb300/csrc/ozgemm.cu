@@ -149,9 +149,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
     static_assert(GMAX >= 2 && GMAX <= SA + SB && NACC >= 1 && (NACC >= 2 || GMAX == 2), "groups");
     static_assert(oz_exact_ok(SA, SB, NE, W), "an exact group must fit one stage");
     static_assert(W == 7 || W == 8, "digit width");
-    const int nsplit = batch.nsplit > 1 ? batch.nsplit : 1;
-    const int split = blockIdx.z % nsplit;
-    const OzProblem& P = batch.p[blockIdx.z / nsplit];
+    const int nsplit_h = batch.nsplit > 1 ? batch.nsplit : 1;
+    const int split = blockIdx.z % nsplit_h;
+    const OzProblem& P = batch.p[blockIdx.z / nsplit_h];
+    const int nsplit = P.dsplit ? max(1, min(*P.dsplit, nsplit_h)) : nsplit_h;
+    if (split >= nsplit) return;
     int M = P.M_from_r2r3 ? (*P.dNa) * (*P.dNb) : oz_dim(P.dM, P.M);
     const int N = oz_dim(P.dN, P.N);
     const int Kall = oz_dim(P.dK, P.K);
@@ -528,6 +530,8 @@ __global__ void __launch_bounds__(256) k_oz_slice_tile(OzSliceArgs a)
 __global__ void k_oz_reduce(OzBatch batch)
 {
     const OzProblem& P = batch.p[blockIdx.y];
+    const int ns = P.dsplit ? max(1, min(*P.dsplit, batch.nsplit)) : batch.nsplit;
+    if (ns <= 1) return;                       // one split wrote C directly
     const int M = P.M_from_r2r3 ? (*P.dNa) * (*P.dNb) : oz_dim(P.dM, P.M);
     const int N = oz_dim(P.dN, P.N);
     const long long crs = P.crs < 0 ? (long long)N : P.crs;
@@ -538,9 +542,30 @@ __global__ void k_oz_reduce(OzBatch batch)
         const int i = (int)(e % M), j = (int)(e / M);
         const long long o = i * crs + j * ccs;
         double s = 0.0;
-        for (int sp = 0; sp < batch.nsplit; ++sp) s += P.Cpart[sp * P.split_stride + o];
+        for (int sp = 0; sp < ns; ++sp) s += P.Cpart[sp * P.split_stride + o];
         P.C[o] = s;
     }
+}
+
+// The core's split count from the ranks on the device: M = r2 r3 rows, N = r1 columns, K = R.
+// Doubles until the tiles times the splits fill the GPU once, each split keeps at least four
+// stages, every split's partial (M N values) fits split_stride, and smax is not passed.
+__global__ void k_core_split(const int* r, int K, int smax, long long split_stride, int* out)
+{
+    const long long M = (long long)r[1] * r[2], N = r[0];
+    const long long tiles = ((M + OZ_BM - 1) / OZ_BM) * ((N + 159) / 160);
+    const int stages = (K + OZ_BK - 1) / OZ_BK;
+    int s2 = 1;
+    if (M * N <= split_stride)
+        while (s2 * 2 <= smax && tiles * s2 < 152 && stages / (s2 * 2) >= 4) s2 *= 2;
+    *out = s2;
+}
+
+int launch_core_split(const int* r, int K, int smax, long long split_stride, int* out, cudaStream_t st)
+{
+    k_core_split<<<1, 1, 0, st>>>(r, K, smax, split_stride, out);
+    RH_CHECK_LAUNCH();
+    return 0;
 }
 
 int oz_choose_split(int M, int N, int K, int nt, int nbatch)

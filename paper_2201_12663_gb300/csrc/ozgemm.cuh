@@ -74,6 +74,9 @@ struct OzProblem {
     // the partials into C in a fixed order
     double* Cpart;
     long long split_stride;
+    // nullable: the split count decided on the device (sizes known only there), at most
+    // OzBatch::nsplit; CTAs of the splits beyond it exit, and 1 writes C directly
+    const int* dsplit;
 };
 
 struct OzBatch {
@@ -164,5 +167,7 @@ int launch_ozgemm(const OzBatch& b, OzKind kind, cudaStream_t st);
 
 // split count for an M x N x K product: enough CTAs for two per SM, at least 4 stages each
 int oz_choose_split(int M, int N, int K, int nt, int nbatch);
+// the Khatri-Rao core's split count from the device ranks r (see k_core_split)
+int launch_core_split(const int* r, int K, int smax, long long split_stride, int* out, cudaStream_t st);
 
 }  // namespace rh
