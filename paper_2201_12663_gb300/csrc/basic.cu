@@ -20,10 +20,10 @@ struct Col {
     {
         if (PROD) {
             const int i = nu % na.Ra, j = nu / na.Ra;
-            a = na.U[l] + (long long)i * na.ld[l];
-            b = na.B[l] + (long long)j * na.ldb[l];
+            a = sel3(na.U, l) + (long long)i * sel3(na.ld, l);
+            b = sel3(na.B, l) + (long long)j * sel3(na.ldb, l);
         } else {
-            a = na.U[l] + (long long)nu * na.ld[l];
+            a = sel3(na.U, l) + (long long)nu * sel3(na.ld, l);
             b = nullptr;
         }
     }
@@ -38,7 +38,7 @@ __global__ void k_colnorms(NormArgs a)
     const int lane = threadIdx.x & 31;
     if (warp >= a.R) return;
     const Col<PROD> u(a, l, warp);
-    const int n = a.n[l];
+    const int n = sel3(a.n, l);
     long long mb = 0;
     for (int i = lane; i < n; i += 32) {
         const long long b = __double_as_longlong(u[i]) & 0x7FFFFFFFFFFFFFFFll;
@@ -106,7 +106,7 @@ __global__ void k_colnorms_prod(NormArgs a)
     const int lane = threadIdx.x & 31;
     if (warp >= a.R) return;
     const Col<true> u(a, l, warp);
-    const int n = a.n[l];
+    const int n = sel3(a.n, l);
     double v[NR];
     long long mb = 0;
 #pragma unroll
@@ -189,7 +189,7 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= a.R) return;
-    const int n = a.n[l];
+    const int n = sel3(a.n, l);
     const Col<PROD> u(a, l, warp);
     double* dst = Un + l * ustride + (long long)warp * n;
     const bool keep = keepf[warp] != 0.0;
@@ -206,7 +206,9 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
             s2 = ldexp(1.0, e2);
         }
     }
-    uint16_t* P = ns.planes[l];
+    uint16_t* P = sel3(ns.planes, l);
+    const int pld = sel3(ns.ld, l);
+    const long long pst = sel3(ns.pstride, l);
     int E = -126;
     if (P) {
         const double mx = (a.colmax[(long long)l * a.R + warp] * s1) * s2;
@@ -214,25 +216,40 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
             frexp(mx, &E);
             E = E < -126 ? -126 : (E > 127 ? 127 : E);
         }
-        if (lane == 0) ns.exps[l][warp] = (signed char)E;
+        if (lane == 0) sel3(ns.exps, l)[warp] = (signed char)E;
     }
     double s = 0.0;
-    const int lim = P ? ns.ld[l] : n;
+    const int lim = P ? pld : n;
     // one multiply an element when s1 s2 is exact (s2 = 1 unless the exponent is extreme)
     const bool one = s2 == 1.0;
-    for (int i = lane; i < lim; i += 32) {
-        double v = 0.0;
-        if (i < n) {
-            v = keep ? (one ? u[i] * s1 : (u[i] * s1) * s2) : 0.0;
-            dst[i] = v;
-            s = fma(v, v, s);
-        }
-        if (P) {
-            uint16_t dg[OZ_S64];
-            oz_digits(v, E, OZ_S64, dg, OZ_W64);
-            uint16_t* q = P + (long long)warp * ns.ld[l] + i;
+    // NORM_UN loads of a lane issued before any is used: one load in flight per warp leaves the
+    // read stream latency-bound (a warp's 256 bytes against the ~40 KB an SM needs in flight)
+    constexpr int NORM_UN = 4;
+    for (int i0 = lane; i0 < lim; i0 += 32 * NORM_UN) {
+        double x[NORM_UN];
 #pragma unroll
-            for (int t = 0; t < OZ_S64; ++t) q[t * ns.pstride[l]] = dg[t];
+        for (int q = 0; q < NORM_UN; ++q) {
+            const int i = i0 + 32 * q;
+            x[q] = (keep && i < n) ? u[i] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < NORM_UN; ++q) {
+            const int i = i0 + 32 * q;
+            if (i < lim) {
+                double v = 0.0;
+                if (i < n) {
+                    v = keep ? (one ? x[q] * s1 : (x[q] * s1) * s2) : 0.0;
+                    dst[i] = v;
+                    s = fma(v, v, s);
+                }
+                if (P) {
+                    uint16_t dg[OZ_S64];
+                    oz_digits(v, E, OZ_S64, dg, OZ_W64);
+                    uint16_t* pq = P + (long long)warp * pld + i;
+#pragma unroll
+                    for (int t = 0; t < OZ_S64; ++t) pq[t * pst] = dg[t];
+                }
+            }
         }
     }
     s = warp_sum(s);
@@ -246,16 +263,18 @@ __global__ void k_slice_t(SliceTArgs a)
 {
     const int b = blockIdx.z;
     const int nu0 = blockIdx.x * 32, x0 = blockIdx.y * 32;
-    const int rows = a.rows[b], K = a.K[b], ld = a.ld[b];
+    const int rows = sel3(a.rows, b), K = sel3(a.K, b), ld = sel3(a.ld, b);
     if (x0 >= rows || nu0 >= ld) return;
     __shared__ double tile[32][33];
-    const double* X = a.X[b];
+    const double* X = sel3(a.X, b);
+    const int ldx = sel3(a.ldx, b);
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
         const int nu = nu0 + j, x = x0 + threadIdx.x;
-        tile[j][threadIdx.x] = (nu < K && x < rows) ? X[(long long)nu * a.ldx[b] + x] : 0.0;
+        tile[j][threadIdx.x] = (nu < K && x < rows) ? X[(long long)nu * ldx + x] : 0.0;
     }
     __syncthreads();
-    uint16_t* P = a.planes[b];
+    uint16_t* P = sel3(a.planes, b);
+    const long long pst = sel3(a.pstride, b);
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int x = x0 + i, nu = nu0 + threadIdx.x;
         if (x >= rows || nu >= ld) continue;
@@ -263,7 +282,7 @@ __global__ void k_slice_t(SliceTArgs a)
         oz_digits(tile[threadIdx.x][i], a.E0, OZ_S64, dg, OZ_W64);
         uint16_t* q = P + (long long)x * ld + nu;
 #pragma unroll
-        for (int t = 0; t < OZ_S64; ++t) q[t * a.pstride[b]] = dg[t];
+        for (int t = 0; t < OZ_S64; ++t) q[t * pst] = dg[t];
     }
 }
 
@@ -323,7 +342,7 @@ __global__ void k_hadamard(HadArgs a)
     const int l = blockIdx.y;
     const long long R = (long long)a.Ra * a.Rb;
     const int lane = threadIdx.x & 31;
-    const int n = a.n[l];
+    const int n = sel3(a.n, l);
     for (long long nu = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; nu < R;
          nu += ((long long)gridDim.x * blockDim.x) >> 5) {
         const int i = (int)(nu % a.Ra), j = (int)(nu / a.Ra);
@@ -341,7 +360,7 @@ __global__ void k_cpsum(SumArgs a)
     const int l = blockIdx.y;
     const int R = a.Ra + a.Rb;
     const int lane = threadIdx.x & 31;
-    const int n = a.n[l];
+    const int n = sel3(a.n, l);
     for (long long nu = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; nu < R;
          nu += ((long long)gridDim.x * blockDim.x) >> 5) {
         const bool fromA = nu < a.Ra;

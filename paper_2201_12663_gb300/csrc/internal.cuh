@@ -199,6 +199,15 @@ struct ModeMap {
 };
 
 // ---------------------------------------------------------------- kernel arguments
+// v[l] of a three-entry kernel-parameter array at a runtime index l.  Indexing the array itself
+// makes the compiler copy the whole parameter struct to local memory in every thread (a stack
+// frame of a few hundred bytes a thread); a select chain reads the parameter bank directly.
+template <typename T>
+__device__ __forceinline__ T sel3(const T (&v)[3], int l)
+{
+    return l == 0 ? v[0] : (l == 1 ? v[1] : v[2]);
+}
+
 struct NormArgs {
     const double* U[3];
     int ld[3];

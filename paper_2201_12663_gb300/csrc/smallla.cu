@@ -197,6 +197,13 @@ __device__ __forceinline__ int negcount(const double* D, const double* W, int k,
 // LDL^T = T + s I with s > 0 multiplied by 4 until every pivot is positive (one warp per
 // mode: the norms by all lanes, the recurrence by lane 0).  Writes D, Lo, the shift s and an
 // upper bound of the spectrum of L D L^T.
+// The pivots come from the leading principal minors of the matrix scaled by sig = 2^-ex
+// (||T|| < 2^ex): P_{-1} = 1, P_0 = c_0, P_{i+1} = c_{i+1} P_i - e_i^2 P_{i-1} with c_i = (d_i + s) sig
+// and e_i sig in place of e_i, D_i = 2^ex P_i / P_{i-1}.  The serial chain is then one FMA a step
+// (the product e_i^2 P_{i-1} is ready a step early) instead of a division; the pair (P_{i-1}, P_i)
+// is rescaled by one power of two when P_i leaves [2^-400, 2^400], and the quotients D_i and
+// l_i = e_i / D_i are taken afterwards by all lanes.  Rounding-wise a step perturbs c_i and e_i^2
+// by a few ulps, as the pivot recurrence D_{i+1} = c_{i+1} - e_i^2 / D_i does.
 __global__ void k_ldl(ModeMap mm, const double* d, const double* e, int vstride, const int* dk, double* D,
                       double* Lo, DevState* st)
 {
@@ -207,40 +214,69 @@ __global__ void k_ldl(ModeMap mm, const double* d, const double* e, int vstride,
     e += b * vstride;
     D += b * vstride;
     Lo += b * vstride;
-    // d and e in shared memory: the recurrence below is one serial chain, and a global load
-    // on it would cost an L2 round trip a step
-    __shared__ double ds[KMAX], es[KMAX];
+    // the scaled diagonal and squared off-diagonal in shared memory: the recurrence below is one
+    // serial chain, and a global load on it would cost an L2 round trip a step
+    __shared__ double ds[KMAX], e2[KMAX], pc[KMAX], pq[KMAX];
     double tnorm = 0.0;
     for (int i = lane; i < k; i += 32) {
-        ds[i] = d[i];
-        es[i] = i + 1 < k ? e[i] : 0.0;
         const double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < k ? fabs(e[i]) : 0.0);
         tnorm = fmax(tnorm, r);
     }
     tnorm = warp_max(tnorm);
+    int ex = 0;
+    if (tnorm > 0.0 && tnorm < INFINITY) frexp(tnorm, &ex);
+    ex = ex < -1000 ? -1000 : (ex > 1000 ? 1000 : ex);
+    const double sig = ldexp(1.0, -ex), isig = ldexp(1.0, ex);
+    for (int i = lane; i < k; i += 32) {
+        ds[i] = d[i] * sig;
+        const double es = i + 1 < k ? e[i] * sig : 0.0;
+        e2[i] = es * es;
+    }
     __syncwarp();
     __shared__ double s_shift;
+    __shared__ int s_valid;
     if (lane == 0) {
         double s = fmax(4.0 * k * DBL_EPSILON * tnorm, DBL_MIN);
         bool ok = false;
+        int valid = 0;
         for (int tries = 0; tries < 60 && !ok; ++tries) {
             ok = true;
-            double Dc = ds[0] + s;
+            const double ss = s * sig;
+            double q = 1.0, p = ds[0] + ss;               // P_{i-1}, P_i
+            valid = 0;
             for (int i = 0; i < k; ++i) {
-                if (!(Dc > 0.0)) { ok = false; break; }
-                D[i] = Dc;
+                const int ep = (__double2hiint(p) >> 20) & 0x7FF;
+                if (ep == 0x7FF) { ok = false; break; }
+                if (ep != 0 && (ep > 1023 + 400 || ep < 1023 - 400)) {
+                    const double sc = __hiloint2double((2046 - ep) << 20, 0);   // 2^(1023 - ep)
+                    p *= sc;
+                    q *= sc;
+                }
+                if (!(p > 0.0) || !(q < INFINITY)) { ok = false; break; }
+                pc[i] = p;
+                pq[i] = q;
+                valid = i + 1;
                 if (i + 1 < k) {
-                    const double l = es[i] / Dc;
-                    Lo[i] = l;
-                    Dc = ds[i + 1] + s - l * es[i];
-                } else {
-                    Lo[i] = 0.0;
+                    const double t = -e2[i] * q;
+                    const double pn = fma(ds[i + 1] + ss, p, t);
+                    q = p;
+                    p = pn;
                 }
             }
             if (!ok) s *= 4.0;
         }
         if (!ok) st->piv_fail[b] = 1;
         s_shift = s;
+        s_valid = valid;
+    }
+    __syncwarp();
+    {
+        const int valid = s_valid;
+        for (int i = lane; i < k; i += 32) {
+            const double Di = i < valid ? (pc[i] / pq[i]) * isig : 1.0;
+            D[i] = Di;
+            Lo[i] = (i + 1 < k && i < valid) ? e[i] / Di : 0.0;
+        }
     }
     __syncwarp();
     const double s = s_shift;
