@@ -497,7 +497,7 @@ __global__ void k_copy2d(CopyArgs a)
 // stationary qd  L D L^T - mu I = L+ D+ L+^T (top down, s_i), progressive qd
 // L D L^T - mu I = U- D- U-^T (bottom up, p_i), gamma_r = s_r + p_r + mu, twist at
 // argmin |gamma_r|; z_r = 1, z_i = -L+_i z_{i+1} above, z_{i+1} = -U-_i z_i below.
-// One thread per vector; grid (ceil(rmax / 16), nmodes), 16 threads a block.
+// One thread per vector; grid (ceil(rmax / 4), nmodes), 4 threads a block.
 __global__ void k_eigvecs(ModeMap mm, const double* D, const double* Lo, const double* mu, int vstride, const int* dk,
                           const DevState* st, double* W, long long wstride, int ldw)
 {
@@ -721,9 +721,10 @@ int launch_copy2d(const double* src, long long sstride, const int lds[3], double
 int launch_eigvecs(ModeMap mm, const double* D, const double* Lo, const double* mu, int vstride, const int* dk,
                    const DevState* s, double* W, long long wstride, int ldw, int rmax, int nb, cudaStream_t st)
 {
-    // 16 vectors a block: each vector is a serial chain, and a warp-wide FP64 instruction costs the
-    // SM's FP64 pipe 16 cycles, so the vectors are spread over many SMs rather than packed
-    constexpr int VPB = 16;
+    // 4 vectors a block: each vector is a serial chain, and a warp-wide FP64 instruction costs the
+    // SM's FP64 pipe 16 cycles, so the vectors are spread over many SMs rather than packed (three
+    // modes of ~150 vectors fill about 120 of the 152 SMs with one 4-lane warp each)
+    constexpr int VPB = 4;
     dim3 grid((rmax + VPB - 1) / VPB, nb);
     k_eigvecs<<<grid, VPB, 0, st>>>(mm, D, Lo, mu, vstride, dk, s, W, wstride, ldw);
     RH_CHECK_LAUNCH();
