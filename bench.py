@@ -34,9 +34,9 @@ if ROOT not in sys.path:
 WORKLOAD = dict(workload="hadamard_n1024_R64x64", n=1024, Ra=64, Rb=64, seeds=[0, 1], eps=1e-7,
                 r_max=160, oversample=32, grid="[-10,10]^3 cell centres")
 PRECISIONS = {"mixed": 1, "plain": 0}
-# tensor-core digit-plane products per FP64-class product in the mixed form: 6-digit operands
-# with every pair s + t <= 8 (26); the sketch against a +-1 operand (6); the core with 4-digit
-# operands, pairs s + t <= 5 (10)
+# tensor-core digit-plane products per FP64-class product in the mixed form: 7-digit operands
+# with every pair s + t <= 9 (34); the sketch, 7 digits against a +-1 operand (7); the core with
+# 4-digit operands, pairs s + t <= 5 (10)
 MIXED_PAIRS = {"sketch": 7, "project": 34, "v_hi": 34, "residual": 34, "z_hi": 34, "gram_bbt": 34,
                "cholqr_gram": 34, "cholqr_apply": 34, "core": 10}
 # DRAM bytes per launch of a stage's kernel from an ncu capture of the same code (None when the
