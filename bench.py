@@ -150,7 +150,48 @@ def oracle_sample(budget_s=25.0):
               f"(full, x3 modes), core over {Rs}/{R} terms (x{R / Rs:.0f}); measured "
               f"{t_prep + t_svd + t_proj + t_core * Rs / R:.1f} s, extrapolated {t_red:.1f} s/reduction")
     return {"value": 1.0 / t_red, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-            "seconds_per_reduction": t_red, "rank_mode1": r}
+            "seconds_per_reduction": t_red, "rank_mode1": r, "_parts": (Un, t_prep, t_core)}
+
+
+def _oracle_worker_ready(_):
+    import oracle
+    oracle.lib()
+    return os.getpid()
+
+
+def _oracle_mode_svd_project(job):
+    """One mode's side-matrix SVD, eps-rank and projection by the C oracle (a worker process)."""
+    import numpy as np
+    import oracle
+    Ul, eps = job
+    t0 = time.perf_counter()
+    sig, Z = oracle.side_svd(Ul)
+    r = oracle.eps_rank(sig, eps)
+    Z0 = np.asfortranarray(Z[:, :r])
+    V = np.zeros(r * Ul.shape[1])
+    oracle.lib().orc_project(Ul.shape[0], Ul.shape[1], r, oracle._dp(Z0), oracle._dp(Ul), oracle._dp(V))
+    return time.perf_counter() - t0, r
+
+
+def oracle_parallel_modes(parts):
+    """The same reduction with the three modes' SVD + projection in three worker processes at once
+    (the oracle's own code, one mode a process; spawned, and warmed up before the clock starts).
+    The Hadamard product, normalisation and core keep their single-core times."""
+    import multiprocessing as mp
+    import numpy as np
+    Un, t_prep, t_core = parts
+    jobs = [(np.asfortranarray(Un[l]), WORKLOAD["eps"]) for l in range(3)]
+    with mp.get_context("spawn").Pool(3) as pool:
+        pool.map(_oracle_worker_ready, range(3))
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_mode_svd_project, jobs)
+        wall = time.perf_counter() - t0
+    t_red = t_prep + wall + t_core
+    return {"value": 1.0 / t_red, "unit": UNIT, "cores": 3, "kind": "oracle",
+            "sample": (f"as the single-core sample, with the three modes' side-matrix SVD + projection "
+                       f"run at once in three processes (all three measured, {wall:.1f} s wall; modes "
+                       f"alone {', '.join(f'{t:.1f}' for t, _ in res)} s)"),
+            "seconds_per_reduction": t_red, "ranks": [r for _, r in res]}
 
 
 def nproc():
@@ -175,11 +216,16 @@ def run_reference(args):
     ms = 1000.0 * statistics.mean(t_steps)
     value = 1000.0 / ms
     cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]}
+    try:
+        par = oracle_parallel_modes(cb["_parts"])
+        par.pop("seconds_per_reduction", None)
+    except Exception as e:            # the single-core line stands without it
+        par = {"unavailable": f"{type(e).__name__}: {e}"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {**WORKLOAD, "precision": "oracle fp64", "l2": "n/a (CPU)"}, "cpu_baseline": cpu,
-            "samples_timed": len(t_steps),
+            "samples_timed": len(t_steps), "cpu_parallel_modes": par,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
