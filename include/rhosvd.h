@@ -158,8 +158,9 @@ int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rhosvd_tucker
  *              ||beta||^2 before and energy[2 s + 1] after the mode-l update (the call then
  *              synchronises `stream`; with NULL it stays asynchronous)
  *   workspace  rhosvd_c2t_als_workspace_size(cp, opts, sweeps) bytes (the RHOSVD's plus the
- *              r_max^2-column contraction C_l and its Gram partials)
- * Errors as rhosvd_c2t.
+ *              r_max^2-column contraction C_l and its Gram partials; 0 for invalid arguments,
+ *              sweeps outside 0 .. RHOSVD_ALS_MAX_SWEEPS included)
+ * Errors as rhosvd_c2t; RHOSVD_ERR_INVALID_ARG for sweeps outside 0 .. RHOSVD_ALS_MAX_SWEEPS.
  */
 #define RHOSVD_ALS_MAX_SWEEPS 8
 size_t rhosvd_c2t_als_workspace_size(const rhosvd_cp* cp, const rhosvd_opts* opts, int sweeps);

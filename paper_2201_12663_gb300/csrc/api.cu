@@ -1568,7 +1568,7 @@ extern "C" int rhosvd_c2t_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, const
 extern "C" size_t rhosvd_c2t_als_workspace_size(const rhosvd_cp* cp, const rhosvd_opts* opts, int sweeps)
 {
     Plan p;
-    if (sweeps < 0 || make_plan(cp, opts, &p, 0, sweeps) != RHOSVD_OK) return 0;
+    if (sweeps < 0 || sweeps > RHOSVD_ALS_MAX_SWEEPS || make_plan(cp, opts, &p, 0, sweeps) != RHOSVD_OK) return 0;
     return p.total;
 }
 
