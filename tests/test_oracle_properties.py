@@ -1,7 +1,9 @@
-"""Property tests of the numpy oracles on random small inputs (hypothesis): the T2C error bound and
+"""Property tests of the oracles on random small inputs (hypothesis): the T2C error bound and
 rank bound of Remark rem_can_red, the Horner evaluation with exact reductions against numpy's
-polyval, the ALS monotonicity, and the energy lemma against the direct pair sum.  Each property
-is a fact of the mathematics, independent of the oracle's code."""
+polyval, the ALS monotonicity, the energy lemma against the direct pair sum, the RHOSVD error
+bound of Thm. 2.3 with the projection identities, and the rank-growth operations (Hadamard
+product, linear combination, normalisation) against the full tensors.  Each property is a fact
+of the mathematics, independent of the oracle's code."""
 import numpy as np
 import pytest
 
@@ -62,3 +64,47 @@ def test_energy_lemma_is_the_pair_sum(L1, L2, L3, seed):
     E = oe.energy_lemma(cp.U, cp.xi, M["idx"], M["z"], M["p0"])
     Ep = oe.pair_sum(M["coords"], M["z"], oe.long_range_kernel(M["t"], M["p"])) if M["N"] > 1 else 0.0
     assert abs(E - Ep) <= 1e-12 * max(1.0, float(np.abs(M["z"]).sum()) ** 2)
+
+
+@SET
+@given(n=st.integers(3, 10), R=st.integers(1, 24), seed=st.integers(0, 10 ** 6), leps=st.floats(-9.0, -0.5),
+       signed=st.booleans())
+def test_c2t_bound_and_projection(n, R, seed, leps, signed):
+    """Thm. 2.3 on random CP tensors: ||A - A0||_F <= ||xi'|| sum_l tau_l, and A0 is the
+    orthogonal projection of A onto the Z bases (Pythagoras; the core is A x_l Z_l^T)."""
+    import oracle
+    from tests import tensor_utils as tu
+    cp = workloads.random_cp(n, R, seed % 100000, signed=signed)
+    out = oracle.c2t(cp.U, cp.xi, eps=10.0 ** leps)
+    A = tu.full_from_cp(cp.U, cp.xi)
+    nA = np.linalg.norm(A)
+    T = tu.tucker_full(out["beta"], out["Z"]) if min(out["ranks"]) > 0 else np.zeros_like(A)
+    err = np.linalg.norm(A - T)
+    assert err <= out["xi_norm"] * sum(out["tails"]) * (1 + 1e-10) + 1e-12 * max(nA, 1.0)
+    assert abs(nA ** 2 - np.linalg.norm(out["beta"]) ** 2 - err ** 2) <= 1e-10 * max(nA ** 2, 1.0)
+    for l in range(3):
+        Z = out["Z"][l]
+        assert np.allclose(Z.T @ Z, np.eye(Z.shape[1]), atol=1e-12)
+
+
+@SET
+@given(n=st.integers(2, 8), Ra=st.integers(1, 6), Rb=st.integers(1, 6), seed=st.integers(0, 10 ** 6),
+       alpha=st.floats(-3.0, 3.0), beta=st.floats(-3.0, 3.0))
+def test_rank_growth_ops_on_full_tensors(n, Ra, Rb, seed, alpha, beta):
+    """Hadamard product and linear combination of CP tensors equal the entrywise product and
+    the combination of the full tensors; normalisation leaves the full tensor unchanged."""
+    import oracle
+    from tests import tensor_utils as tu
+    a = workloads.random_cp(n, Ra, seed % 100000)
+    b = workloads.random_cp(n, Rb, (seed + 1) % 100000)
+    A, B = tu.full_from_cp(a.U, a.xi), tu.full_from_cp(b.U, b.xi)
+    Uh, xh = oracle.cp_hadamard(a.U, a.xi, b.U, b.xi)
+    assert np.allclose(tu.full_from_cp(Uh, xh), A * B, rtol=0, atol=1e-12 * max(np.abs(A * B).max(), 1.0))
+    Us, xs = oracle.cp_sum(alpha, a.U, a.xi, beta, b.U, b.xi)
+    C = alpha * A + beta * B
+    assert np.allclose(tu.full_from_cp(Us, xs), C, rtol=0, atol=1e-12 * max(np.abs(C).max(), 1.0))
+    Un, xin, norms, keep = oracle.normalize(a.U, a.xi)
+    assert np.allclose(tu.full_from_cp(Un, xin), A, rtol=0, atol=1e-12 * max(np.abs(A).max(), 1.0))
+    for l in range(3):
+        nz = np.linalg.norm(Un[l], axis=0)
+        assert np.allclose(nz[keep.astype(bool)], 1.0, atol=1e-14)
