@@ -44,7 +44,52 @@ MIXED_PAIRS = {"sketch": 7, "project": 34, "v_hi": 34, "residual": 34, "z_hi": 3
 NCU_TRAFFIC = {"cholqr_chol": 0.951e6}
 METRIC = "RHOSVD reductions/s at stated rel. err: mixed/learned vs FP64 plain, 1×GB300"
 UNIT = "reductions/s"
-FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (CUDA-core and tensor) rate
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 (CUDA-core and tensor) rate, used only until measured
+_FP64 = {}                  # the rate measured in this run by fp64_rate()
+
+
+def fp64_peak():
+    """(FP64 peak in TFLOP/s, where it comes from): the probe's rate measured in this run, else
+    the nominal figure."""
+    if _FP64.get("probe_tflops"):
+        return _FP64["probe_tflops"], "FP64 fma rate measured on this GPU in this run (rhosvd_probe_fp64, of measured)"
+    return FP64_NOMINAL_TFLOPS, "GB300 nominal FP64 rate (of fallback: not measured in this run)"
+
+
+def fp64_rate(P, dev, reps=5):
+    """FP64 fma rate of this GPU: the library's probe kernel (eight independent fma chains a
+    thread, 152 x 8 blocks of 256 threads), best of `reps` CUDA-event timings after warm-up; and
+    cuBLAS DGEMM 4096^3 (torch.matmul in float64) beside it as a comparator."""
+    import torch
+    blocks, iters = 152 * 8, 4096
+    buf = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        P.rhosvd_probe_fp64(blocks, iters, buf)
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        P.rhosvd_probe_fp64(blocks, iters, buf)
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    probe = blocks * 4096.0 * iters / (best * 1e-3) / 1e12
+    x = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    y = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        torch.matmul(x, y)
+    bestg = float("inf")
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        torch.matmul(x, y)
+        b.record()
+        torch.cuda.synchronize()
+        bestg = min(bestg, a.elapsed_time(b))
+    del x, y, buf
+    _FP64["probe_tflops"] = probe
+    return {"probe_tflops": probe, "probe_ms": best, "cublas_dgemm_4096_tflops": 2 * 4096.0 ** 3 / (bestg * 1e-3) / 1e12,
+            "note": "the probe's rate is the denominator of every FP64 roofline in this line; cuBLAS DGEMM is a comparator"}
 
 
 def peaks():
@@ -111,87 +156,100 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(budget_s=25.0):
-    """Time the plain C oracle on a bounded sample of the workload and extrapolate one
-    reduction: the full Hadamard product and normalisation, the side-matrix SVD of one mode
-    (Householder R + one-sided Jacobi, the dominant step), its projection, and the core
-    contraction over a slice of the terms; three modes and the full term count scale it."""
-    import numpy as np
-    import oracle
+# ------------------------------------------------------------------ CPU oracle
+def _oracle_input(wl):
     import workloads
-    A, B = workloads.hartree_like_factors(WORKLOAD["n"], WORKLOAD["Ra"], WORKLOAD["Rb"], WORKLOAD["seeds"])
-    t0 = time.perf_counter()
-    Uc, xc = oracle.cp_hadamard(A.U, A.xi, B.U, B.xi)
-    Un, xin, _, _ = oracle.normalize(Uc, xc)
-    t_prep = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    sig, Z = oracle.side_svd(Un[0])
-    t_svd = time.perf_counter() - t0
-    r = oracle.eps_rank(sig, WORKLOAD["eps"])
-    R = xc.shape[0]
-    t0 = time.perf_counter()
-    Z0 = np.asfortranarray(Z[:, :r])
-    V = np.zeros(r * R)
-    lib = oracle.lib()
-    lib.orc_project(Un[0].shape[0], R, r, oracle._dp(Z0), oracle._dp(np.asfortranarray(Un[0])), oracle._dp(V))
-    t_proj = time.perf_counter() - t0
-    # core over a slice of the terms (the loops are linear in R)
-    Rs = max(16, R // 64)
-    Vs = np.asfortranarray(V.reshape((r, R), order="F")[:, :Rs])
-    beta = np.zeros(r ** 3)
-    rr = np.array([r, r, r], dtype=np.int32)
-    t0 = time.perf_counter()
-    lib.orc_core(Rs, oracle._ip(rr), oracle._dp(Vs), oracle._dp(Vs), oracle._dp(Vs),
-                 oracle._dp(np.ascontiguousarray(xin[:Rs])), oracle._dp(beta))
-    t_core = (time.perf_counter() - t0) * (R / Rs)
-    t_red = t_prep + 3 * (t_svd + t_proj) + t_core
-    sample = (f"Hadamard product + normalisation (full), side-matrix SVD + projection of mode 1 "
-              f"(full, x3 modes), core over {Rs}/{R} terms (x{R / Rs:.0f}); measured "
-              f"{t_prep + t_svd + t_proj + t_core * Rs / R:.1f} s, extrapolated {t_red:.1f} s/reduction")
-    return {"value": 1.0 / t_red, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-            "seconds_per_reduction": t_red, "rank_mode1": r, "_parts": (Un, t_prep, t_core)}
+    A, B = workloads.hartree_like_factors(wl["n"], wl["Ra"], wl["Rb"], wl["seeds"])
+    return A, B
 
 
-def _oracle_worker_ready(_):
-    import oracle
-    oracle.lib()
-    return os.getpid()
-
-
-def _oracle_mode_svd_project(job):
-    """One mode's side-matrix SVD, eps-rank and projection by the C oracle (a worker process)."""
+def oracle_pieces(nsteps, wl=WORKLOAD):
+    """One whole oracle reduction of the bench workload cut into `nsteps` consecutive pieces of
+    work, in the order of orc_c2t: the Hadamard product and the normalisation; the full SVD of
+    each side matrix with its eps-rank (three pieces); the projections V = Z^T U~; the core over
+    consecutive slices of the terms (nsteps - 5 slices; the slices' cores are summed in order).
+    With fewer than six steps the same six kinds of work are spread over them.  Returns
+    (list of callables, state dict); running every callable in order leaves Z, beta, ranks in
+    the state."""
     import numpy as np
     import oracle
-    Ul, eps = job
-    t0 = time.perf_counter()
-    sig, Z = oracle.side_svd(Ul)
-    r = oracle.eps_rank(sig, eps)
-    Z0 = np.asfortranarray(Z[:, :r])
-    V = np.zeros(r * Ul.shape[1])
-    oracle.lib().orc_project(Ul.shape[0], Ul.shape[1], r, oracle._dp(Z0), oracle._dp(Ul), oracle._dp(V))
-    return time.perf_counter() - t0, r
+    A, B = _oracle_input(wl)
+    st = {}
+    eps = wl["eps"]
+
+    def prep():
+        Uc, xc = oracle.cp_hadamard(A.U, A.xi, B.U, B.xi)
+        st["Un"], st["xin"], _, _ = oracle.normalize(Uc, xc)
+        st["Z"], st["r"] = [None] * 3, [0] * 3
+
+    def svd(l):
+        def f():
+            sig, Z = oracle.side_svd(st["Un"][l])
+            r = oracle.eps_rank(sig, eps)
+            st["r"][l] = r
+            st["Z"][l] = np.asfortranarray(Z[:, :r])
+        return f
+
+    def proj():
+        st["V"] = [oracle.project(st["Z"][l], st["Un"][l]) for l in range(3)]
+        st["beta"] = np.zeros(tuple(st["r"]), order="F")
+
+    nc = max(1, nsteps - 5)
+    R = wl["Ra"] * wl["Rb"]
+    cuts = [R * i // nc for i in range(nc + 1)]
+
+    def core(i):
+        def f():
+            a, b = cuts[i], cuts[i + 1]
+            st["beta"] += oracle.core([np.asfortranarray(st["V"][l][:, a:b]) for l in range(3)], st["xin"][a:b])
+        return f
+
+    atoms = [prep, svd(0), svd(1), svd(2), proj] + [core(i) for i in range(nc)]
+    if nsteps >= len(atoms):
+        return atoms, st
+    groups = []
+    for i in range(nsteps):
+        part = atoms[i * len(atoms) // nsteps:(i + 1) * len(atoms) // nsteps]
+        groups.append(lambda part=part: [f() for f in part])
+    return groups, st
 
 
-def oracle_parallel_modes(parts):
-    """The same reduction with the three modes' SVD + projection in three worker processes at once
-    (the oracle's own code, one mode a process; spawned, and warmed up before the clock starts).
-    The Hadamard product, normalisation and core keep their single-core times."""
-    import multiprocessing as mp
+def oracle_full_threads(nthreads, wl=WORKLOAD):
+    """One whole oracle reduction of the bench workload on `nthreads` host threads: the three
+    side-matrix SVDs and the projections at once (one mode a thread), the core over nthreads
+    consecutive slices of the terms at once (summed in slice order).  The oracle's C routines are
+    called unchanged (ctypes releases the GIL).  Returns the Tucker tensor, the wall time and the
+    per-thread busy time of every piece."""
     import numpy as np
-    Un, t_prep, t_core = parts
-    jobs = [(np.asfortranarray(Un[l]), WORKLOAD["eps"]) for l in range(3)]
-    with mp.get_context("spawn").Pool(3) as pool:
-        pool.map(_oracle_worker_ready, range(3))
-        t0 = time.perf_counter()
-        res = pool.map(_oracle_mode_svd_project, jobs)
-        wall = time.perf_counter() - t0
-    t_red = t_prep + wall + t_core
-    return {"value": 1.0 / t_red, "unit": UNIT, "cores": 3, "kind": "oracle",
-            "sample": (f"as the single-core sample, with the three modes' side-matrix SVD + projection "
-                       f"run at once in three processes (all three measured, {wall:.1f} s wall; modes "
-                       f"alone {', '.join(f'{t:.1f}' for t, _ in res)} s)"),
-            "seconds_per_reduction": t_red, "ranks": [r for _, r in res]}
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    A, B = _oracle_input(wl)
+    eps = wl["eps"]
+    busy = []
+
+    def timed(f, *a):
+        t = time.perf_counter()
+        out = f(*a)
+        busy.append(time.perf_counter() - t)
+        return out
+    t0 = time.perf_counter()
+    Uc, xc = timed(oracle.cp_hadamard, A.U, A.xi, B.U, B.xi)
+    Un, xin, _, _ = timed(oracle.normalize, Uc, xc)
+    with ThreadPoolExecutor(max_workers=max(3, nthreads)) as ex:
+        svd = list(ex.map(lambda l: timed(oracle.side_svd, Un[l]), range(3)))
+        r = [oracle.eps_rank(svd[l][0], eps) for l in range(3)]
+        Z = [np.asfortranarray(svd[l][1][:, : r[l]]) for l in range(3)]
+        V = list(ex.map(lambda l: timed(oracle.project, Z[l], Un[l]), range(3)))
+        R = xin.shape[0]
+        cuts = [R * i // nthreads for i in range(nthreads + 1)]
+        parts = list(ex.map(lambda i: timed(oracle.core, [np.asfortranarray(V[l][:, cuts[i]:cuts[i + 1]])
+                                                          for l in range(3)], xin[cuts[i]:cuts[i + 1]]),
+                            range(nthreads)))
+    beta = np.zeros(tuple(r), order="F")
+    for p_ in parts:
+        beta += p_
+    wall = time.perf_counter() - t0
+    return dict(Z=Z, beta=beta, ranks=r, wall=wall, busy=sum(busy))
 
 
 def nproc():
@@ -203,29 +261,33 @@ def nproc():
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
+    """The oracle, as it stands, on one host core: the K timed steps together perform exactly
+    one whole reduction of the bench workload (oracle_pieces), so value = 1 / (sum of the step
+    times) reductions/s and ms_per_step is the mean step time.  Warm-up: W untimed repeats of the
+    first piece (Hadamard product and normalisation)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    # each timed sample is one full-size oracle measurement (~40 s of CPU work); at most three
-    # are timed so that the run ends within a few minutes (no warm-up is needed on the CPU)
+    steps, st = oracle_pieces(args.steps)
+    for _ in range(args.warmup):
+        steps[0]()
     t_steps = []
-    cb = None
-    for i in range(min(args.steps, 3)):
-        cb = oracle_sample()
-        t_steps.append(cb["seconds_per_reduction"])
-    ms = 1000.0 * statistics.mean(t_steps)
-    value = 1000.0 / ms
-    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]}
-    try:
-        par = oracle_parallel_modes(cb["_parts"])
-        par.pop("seconds_per_reduction", None)
-    except Exception as e:            # the single-core line stands without it
-        par = {"unavailable": f"{type(e).__name__}: {e}"}
+    for f in steps:
+        t0 = time.perf_counter()
+        f()
+        t_steps.append(time.perf_counter() - t0)
+    total = sum(t_steps)
+    value = 1.0 / total
+    ms = 1000.0 * total / len(t_steps)
+    sample = (f"one whole oracle reduction (Hadamard product, normalisation, three full side-matrix SVDs "
+              f"(Householder R + one-sided Jacobi), projections, core over all {WORKLOAD['Ra'] * WORKLOAD['Rb']} "
+              f"terms) cut into the {len(t_steps)} timed steps; {total:.1f} s on one core; ranks {st['r']}")
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {**WORKLOAD, "precision": "oracle fp64", "l2": "n/a (CPU)"}, "cpu_baseline": cpu,
-            "samples_timed": len(t_steps), "cpu_parallel_modes": par,
+            "step_seconds": [round(t, 3) for t in t_steps], "host_cores_available": nproc(),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -269,6 +331,109 @@ def algorithmic_flops(stage, info, n, R, kin=None):
     if stage == "tridiag":
         return sum(4.0 * k[l] ** 3 / 3.0 for l in range(3))
     return None
+
+
+def tucker_rel_diff_np(beta_a, Z_a, beta_b, Z_b):
+    """||T_a - T_b|| / ||T_b|| (numpy, FP64) for orthonormal Tucker factors, via an orthonormal
+    basis of span[Z_a Z_b] per mode, so the n^3 tensors are never formed."""
+    import numpy as np
+    ca, cb = np.asarray(beta_a, dtype=np.float64), np.asarray(beta_b, dtype=np.float64)
+    for l in range(3):
+        za, zb = np.asarray(Z_a[l], dtype=np.float64), np.asarray(Z_b[l], dtype=np.float64)
+        Pm, _ = np.linalg.qr(np.hstack([za, zb]))
+        ca = np.moveaxis(np.tensordot(Pm.T @ za, ca, axes=([1], [l])), 0, l)
+        cb = np.moveaxis(np.tensordot(Pm.T @ zb, cb, axes=([1], [l])), 0, l)
+    return float(np.linalg.norm(ca - cb) / np.linalg.norm(cb))
+
+
+RSC = dict(workload="newton_long_range_sum_n2048_N1000", n=2048, N=1000, R=20000, seed=0, eps=1e-6, r_max=64,
+           oversample=32, sketch_seed=2024, precision="mixed", out_fp32=True)
+
+
+def rs_collective_leg(P, dev, steps, warmup):
+    """The range-separated collective potential: long-range Newton Gaussians (20 a charge,
+    exponents e^{2kh}, h = 0.4, k = -19..0) of N = 1000 unit charges at centres U[-8, 8]^3, on
+    n = 2048 cell centres of [-10, 10]: R = 20000 terms, eps = 1e-6, the mixed form with FP32
+    outputs (Z and beta), and the plain form beside it.  Inputs (983 MB of factors) exceed L2,
+    so no flush is needed.  Roofline: the whole reduction against two reads of the factors
+    (1.97 GB) at the measured HBM rate; the dominant stage against its own peak."""
+    import numpy as np
+    import torch
+    import workloads
+    cp = workloads.newton_long_range_sum(n=RSC["n"], N=RSC["N"], seed=RSC["seed"])
+    Ud = [P.to_device_factor(u) for u in cp.U]
+    xd = torch.from_numpy(cp.xi).to(dev)
+    n, R = RSC["n"], cp.xi.shape[0]
+    rec = {**RSC, "l2": "inputs (983 MB) larger than L2: no flush"}
+    host = None
+    for prec, fp32 in (("mixed", True), ("plain", False)):
+        opts = dict(eps=RSC["eps"], r_max=RSC["r_max"], oversample=RSC["oversample"], seed=RSC["sketch_seed"],
+                    precision=PRECISIONS[prec], out_fp32=fp32)
+        ws = torch.empty(P.rhosvd_c2t_workspace_size(P.make_cp(Ud, xd), P.make_opts(**opts)), dtype=torch.uint8,
+                         device=dev)
+        out = P.alloc_tucker([n, n, n], R, RSC["r_max"], dev, fp32=fp32)
+        for _ in range(max(warmup, 3)):
+            P.rhosvd_c2t(Ud, xd, out=out, workspace=ws, **opts)
+        info = out.info()
+        if info.status != 0:
+            rec[prec] = {"status": info.status, "error": P.rhosvd_strerror(info.status)}
+            continue
+        nst = steps if prec == "mixed" else max(2, steps // 2)
+        a = [torch.cuda.Event(enable_timing=True) for _ in range(nst)]
+        b = [torch.cuda.Event(enable_timing=True) for _ in range(nst)]
+        torch.cuda.synchronize()
+        for i in range(nst):
+            a[i].record()
+            P.rhosvd_c2t(Ud, xd, out=out, workspace=ws, **opts)
+            b[i].record()
+        torch.cuda.synchronize()
+        ms = sum(x.elapsed_time(y) for x, y in zip(a, b)) / nst
+        r = [info.r[l] for l in range(3)]
+        alg = 2 * 3 * n * R * 8
+        hbm = peaks().get("hbm_gbs", 6800.0)
+        entry = {"ms": ms, "value": 1000.0 / ms, "unit": UNIT, "ranks": r, "k": [info.k[l] for l in range(3)],
+                 "tails": [info.tail[l] for l in range(3)], "status": 0,
+                 "roofline_whole": {"bound": "hbm", "algorithmic_bytes": alg, "achieved": alg / (ms * 1e-3) / 1e9,
+                                    "peak": hbm, "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / hbm,
+                                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
+        entry["roofline_dominant"] = stage_roofline(
+            P, lambda: P.rhosvd_c2t(Ud, xd, out=out, workspace=ws, **opts), lambda res: res.info(), n, R,
+            RSC["r_max"] + RSC["oversample"], prec)
+        rec[prec] = entry
+        if prec == "mixed":
+            cnt = r[0] * r[1] * r[2]
+            host = (out.beta[:cnt].double().cpu().numpy().reshape(r, order="F"),
+                    [out.Z[l][:, : r[l]].double().cpu().numpy() for l in range(3)], r)
+        del ws, out
+    if "ms" in rec.get("mixed", {}) and "ms" in rec.get("plain", {}):
+        rec["speedup_mixed_vs_plain"] = rec["plain"]["ms"] / rec["mixed"]["ms"]
+    rec["_host"] = (host, cp)
+    return rec
+
+
+def rs_collective_oracle_error(host_cp):
+    """The rs_collective leg's Tucker error against the oracle: the oracle's truncated bases of
+    this workload are stored (tests/golden/newton_n2048_N1000_eps1e-6_Z.npz, written by
+    tests/golden/make_full_size.py from oracle/ alone); V = Z^T U~ and the core are rebuilt here
+    at the GPU's ranks with the oracle's own routines."""
+    import numpy as np
+    import oracle
+    host, cp = host_cp
+    if host is None:
+        return {"tucker_rel_diff_vs_oracle": None, "note": "mixed run failed"}
+    beta, Z, r = host
+    path = os.path.join(ROOT, "tests", "golden", "newton_n2048_N1000_eps1e-6_Z.npz")
+    zs = np.load(path)
+    Zo = [np.asfortranarray(zs[f"Z{l}"][:, : r[l]]) for l in range(3)]
+    if any(Zo[l].shape[1] < r[l] for l in range(3)):
+        return {"tucker_rel_diff_vs_oracle": None, "note": f"ranks {r} beyond the stored oracle bases"}
+    t0 = time.perf_counter()
+    Un, xin, _, _ = oracle.normalize(cp.U, cp.xi)
+    Vo = [oracle.project(Zo[l], Un[l]) for l in range(3)]
+    bo = oracle.core(Vo, xin)
+    return {"vs": "oracle (FP64 CPU, exact SVDs; bases stored, V and core rebuilt by the oracle)",
+            "tucker_rel_diff_vs_oracle": tucker_rel_diff_np(beta, Z, bo, Zo), "outputs": "fp32 Z and beta",
+            "oracle_rebuild_s": time.perf_counter() - t0}
 
 
 def tucker_rel_diff_torch(beta_a, Z_a, beta_b, Z_b):
@@ -486,10 +651,10 @@ def t2c_leg(P, out, steps, warmup):
     return {**T2C, "core": r, "ms_per_t2c": ms, "canonical_rank": R, "status": st,
             "rank_bound": cap, "p_min_median_max": [int(p.min()), int(np.median(p)), int(p.max())],
             "oracle_rank": ref["R"], "oracle_s": t_or, "oracle_cores": 1,
-            "roofline": {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+            "roofline": {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": fp64_peak()[0],
+                         "unit": "TFLOP/s", "frac": fl / (ms * 1e-3) / 1e12 / fp64_peak()[0],
                          "work": "Golub-Kahan count per slice + factor GEMVs",
-                         "peak_source": "GB300 nominal FP64 rate (of fallback)"}}
+                         "peak_source": fp64_peak()[1]}}
 
 
 POLY = dict(workload="newton_cube_n257_eps1e-5", n=257, eps_tucker=1e-5, eps_t2c=1e-5,
@@ -716,8 +881,8 @@ def stage_roofline(P, fn, info_of, n, R, kin, precision):
     """Run fn() once with the library's stage tracing and give the roofline of its dominant
     stage (the one with the most time): algorithmic FP64-class flops of a launch (from the ranks
     the call returned, info_of(result)) over the launch's average duration; tensor-core stages
-    against the measured BF16 rate over the digit pairs, FP64 stages against the nominal FP64
-    rate.  None when the stage has no flop model."""
+    against the measured BF16 rate over the digit pairs, FP64 stages against the FP64 rate
+    measured in this run (fp64_peak).  None when the stage has no flop model."""
     import torch
     torch.cuda.synchronize()
     P.rhosvd_profile_read()
@@ -742,8 +907,8 @@ def stage_roofline(P, fn, info_of, n, R, kin, precision):
         out.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                     "peak_source": f"MEASURED_PEAKS.json bf16_tflops (of measured) / {MIXED_PAIRS[name]} digit pairs"})
     else:
-        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "GB300 nominal FP64 rate (of fallback)"})
+        out.update({"bound": "alu", "achieved": ach, "peak": fp64_peak()[0], "unit": "TFLOP/s",
+                    "frac": ach / fp64_peak()[0], "peak_source": fp64_peak()[1]})
     out["algorithmic_flops_per_launch"] = fl
     return out
 
@@ -922,6 +1087,9 @@ def run_ours(args):
     bm, Zm, rm = tucker_of(out)
     bp, Zp, rp = tucker_of(out2)
     agree = tucker_rel_diff_torch(bm, Zm, bp, Zp)     # common basis per mode: ranks may differ
+    host_main = (bm.cpu().numpy(), [z.cpu().numpy() for z in Zm], rm)
+    host_other = (bp.cpu().numpy(), [z.cpu().numpy() for z in Zp], rp)
+    fp64 = fp64_rate(P, dev)
 
     # ---- end to end through the C ABI: H2D inputs into the captured buffers, the graph replay,
     #      D2H result, per step, all on the graph's stream
@@ -985,16 +1153,26 @@ def run_ours(args):
                     "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": fl}
         elif fl is not None:
             ach = fl / (avg_ms * 1e-3) / 1e12
-            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(name),
-                    "peak_source": "GB300 nominal FP64 rate 1.25 TFLOP/s (of fallback: MEASURED_PEAKS.json has "
-                                   "no FP64 entry)",
+            pk64 = fp64["probe_tflops"]
+            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": pk64, "unit": "TFLOP/s",
+                    "frac": ach / pk64, "traffic": NCU_TRAFFIC.get(name),
+                    "peak_source": "FP64 fma rate measured on this GPU by the library's probe in this run "
+                                   "(of measured; MEASURED_PEAKS.json has no FP64 entry)",
                     "note": "sequential pivot steps on a 16-block cluster per mode: bound by the per-step exchange and cluster barrier, not by FP64 issue or memory",
                     "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": fl}
         else:
-            roof = {"bound": "alu", "kernel": name, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            roof = {"bound": "alu", "kernel": name, "achieved": None, "peak": fp64["probe_tflops"], "unit": "TFLOP/s",
                     "frac": None, "traffic": None, "note": "no flop model for this stage",
                     "avg_launch_ms": avg_ms}
+    if roof is not None:
+        # the whole step against the HBM roofline of the reduction: two reads of the three FP64
+        # side matrices (n R 8 bytes each) per reduction
+        hbm = peaks().get("hbm_gbs", 6800.0)
+        alg = 2 * 3 * n * R * 8
+        roof["whole_step"] = {"bound": "hbm", "algorithmic_bytes": alg, "ms_per_step": ms_per_step,
+                              "achieved": alg / (ms_per_step * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                              "frac": alg / (ms_per_step * 1e-3) / 1e9 / hbm,
+                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 (mixed: bf16 digit planes, fp32 accumulate)" if main_prec == "mixed"
@@ -1009,6 +1187,7 @@ def run_ours(args):
                        "tails": [info.tail[l] for l in range(3)]},
             "error": {"vs": f"{other} GPU form, same sketch", "tucker_rel_diff": agree,
                       "ranks_other": [info2.r[l] for l in range(3)]},
+            "fp64_peak": fp64,
             f"{other}_form": {"value": world * 1000.0 / ms2, "ms_per_step": ms2,
                               "stage_ms_per_step": {k: v[1] / max(3, args.steps // 2) for k, v in prof2.items()}},
             "speedup_vs_other_form": ms2 / ms_per_step,
@@ -1034,10 +1213,36 @@ def run_ours(args):
         line["rs"] = rs_leg(P, 3, 1, main_prec)
     if not args.no_als:
         line["als"] = als_leg(P, 3, 1, main_prec)
+    if not args.no_rs_collective:
+        rsc = rs_collective_leg(P, dev, max(3, args.steps // 2), args.warmup)
+        line["rs_collective"] = rsc
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_sample()
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
-        line["cpu_baseline"]["host_cores_available"] = nproc()
+        # the oracle's whole reduction of the same workload on all host cores (threads over the
+        # modes and over slices of the core's terms): the CPU baseline, and the reference the
+        # headline's error is stated against
+        nth = nproc() or 1
+        orc = oracle_full_threads(nth)
+        line["cpu_baseline"] = {
+            "value": 1.0 / orc["wall"], "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": (f"one whole reduction of the bench workload (no extrapolation): Hadamard product and "
+                       f"normalisation on one thread, the three side-matrix SVDs and projections one mode a "
+                       f"thread, the core over {nth} term slices one a thread; {orc['wall']:.1f} s wall, "
+                       f"{orc['busy']:.1f} s of busy thread time (1-core equivalent "
+                       f"{1.0 / orc['busy']:.4f} reductions/s)"),
+            "value_1core_equivalent": 1.0 / orc["busy"], "ranks": orc["ranks"]}
+        err = line["error"]
+        for key, (b_, Z_, r_) in (("tucker_rel_diff_vs_oracle", host_main), (f"{other}_tucker_rel_diff_vs_oracle", host_other)):
+            if r_ == orc["ranks"]:
+                err[key] = tucker_rel_diff_np(b_, Z_, orc["beta"], orc["Z"])
+            else:
+                err[key] = None
+                err[key + "_note"] = f"ranks {r_} differ from the oracle's {orc['ranks']}"
+        err["vs"] = "oracle (FP64 CPU, exact SVDs, same input)"
+        err["vs_other_form"] = f"{other} GPU form, same sketch"
+        if "rs_collective" in line:
+            line["rs_collective"]["error"] = rs_collective_oracle_error(line["rs_collective"].pop("_host"))
+    elif "rs_collective" in line:
+        line["rs_collective"].pop("_host", None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -1057,6 +1262,8 @@ def main():
     ap.add_argument("--no-poly", action="store_true", help="skip the Newton-cube / Horner leg")
     ap.add_argument("--no-rs", action="store_true", help="skip the range-separated Slater / energy leg")
     ap.add_argument("--no-als", action="store_true", help="skip the RHOSVD + ALS leg")
+    ap.add_argument("--no-rs-collective", action="store_true",
+                    help="skip the range-separated collective potential leg (n=2048, R=20000)")
     ap.add_argument("--fused", action="store_true",
                     help="headline step forms the Hadamard product inside the reduction (rhosvd_c2t_hadamard)")
     ap.add_argument("--precision", choices=["mixed", "plain"], default="mixed")

@@ -80,6 +80,13 @@ typedef struct rhosvd_opts {
                                of the largest, which a Gram-based orthonormalisation of a
                                single sketch cannot resolve (needed for eps near 1e-7)   */
     unsigned long long seed;/* seed of the counter-based sketch generator                 */
+    int out_fp32;           /* 0: Z^(l) and beta written as double; 1: written as float
+                               (FP32, each entry the FP64 result rounded once to nearest;
+                               the capacities below stay counted in entries).  sigma, V,
+                               xi_out and info keep their FP64 types.  Accepted by
+                               rhosvd_c2t, _noalloc, _batched, _hadamard, _start and _als;
+                               rhosvd_cp_horner, whose steps read their own Tucker
+                               tensors back, rejects it (INVALID_ARG)                     */
 } rhosvd_opts;
 
 /* Device-written result record (one per call).  Valid after the stream is synchronised. */
@@ -100,9 +107,10 @@ typedef struct rhosvd_info {
 
 /* Outputs of rhosvd_c2t (all device memory, caller-allocated). */
 typedef struct rhosvd_tucker {
-    double* Z[3];           /* Z^(l): n_l x r_max, ld n_l; columns >= r_l are zero         */
-    double* beta;           /* capacity r_max^3; the r1 x r2 x r3 core packed densely,
-                               beta[i + r1 (j + r2 m)]                                    */
+    void* Z[3];             /* Z^(l): n_l x r_max, ld n_l; columns >= r_l are zero; double
+                               entries, or float with opts->out_fp32                      */
+    void* beta;             /* capacity r_max^3 entries (double, or float with out_fp32);
+                               the r1 x r2 x r3 core packed densely, beta[i + r1 (j + r2 m)] */
     double* sigma[3];       /* capacity RHOSVD_K_MAX each: sigma_{l,1..k_l}, descending,
                                zero beyond k_l                                            */
     double* V[3];           /* optional (NULL = not returned): r_max x R, ld r_max; rows
@@ -210,7 +218,9 @@ int rhosvd_c2t_hadamard(const rhosvd_cp* a, const rhosvd_cp* b, const rhosvd_opt
  *   - Problems with rhosvd_c2t_workspace_size() > RHOSVD_NOALLOC_SCRATCH_BYTES are rejected
  *     with RHOSVD_ERR_SCRATCH_LIMIT; invalid arguments give RHOSVD_ERR_INVALID_ARG.
  *   - The first call on a device looks the array's address up (once per device); make that
- *     first call before any stream capture starts.
+ *     first call before any stream capture starts.  The address is kept per device ordinal,
+ *     so the entry point assumes each device's primary runtime context: after cudaDeviceReset
+ *     or under another context made current through the driver API it must not be called.
  *   - All calls on a device share the array and it keeps the previous call's contents (the
  *     reduction clears what it needs itself).  Calls that overlap on the GPU race on it:
  *     serialise them.
@@ -286,6 +296,21 @@ long long rhosvd_mlp_num_params(void);
  * get = 1 reads (which = 0: the weights, 1: the gradients of the last rhosvd_mlp_gradients),
  * get = 0 writes the weights.  Synchronises the device. */
 int rhosvd_mlp_params(void* handle, float* host, int get, int which);
+/* Checkpoint / resume of the network's training state.  rhosvd_mlp_save writes, to the file
+ * `path` (host path, created or truncated), a flat little-endian binary record: the 8-byte tag
+ * "RHMLPv01", the layer count and the five layer widths (int32), the Adam step count (int64),
+ * then per layer l the FP32 arrays W_l (out x in, row-major), b_l, the Adam moments m(W_l),
+ * v(W_l), m(b_l), v(b_l).  rhosvd_mlp_load reads such a file into an existing handle (any
+ * batch_max), restoring weights, moments and step, so that training resumes exactly where it
+ * stopped; a file with another tag, other widths or a short body is rejected with
+ * RHOSVD_ERR_INVALID_ARG and leaves the handle unchanged.  Both synchronise the device; file
+ * errors return RHOSVD_ERR_INVALID_ARG. */
+int rhosvd_mlp_save(void* handle, const char* path);
+int rhosvd_mlp_load(void* handle, const char* path);
+/* Status of the network's tensor-core products launched since the last call: synchronises
+ * `stream`, returns RHOSVD_ERR_TIMEOUT if a bounded wait inside one of them expired (its
+ * output is then not valid), else RHOSVD_OK; clears the record. */
+int rhosvd_mlp_status(void* handle, void* stream);
 /* Features of one Gaussian sum sum_k c_k exp(-a_k |x - x_k|^2) (device, FP64): per mode l,
  * out[128 l + 0..63] = c-weighted histogram (unit sum, 64 bins) of the centre coordinate x_{k,l}
  * over [-cbox, cbox], out[128 l + 64..127] = of log a_k over [la, lb] (values outside the range
@@ -418,6 +443,14 @@ int rhosvd_rs_energy(const rhosvd_cp* P_long, int N, const int* idx, const doubl
  * rcp[i] ~ 1/x[i], rsq[i] ~ 1/sqrt(x[i]) (device arrays of n doubles, caller-owned).  Returns
  * RHOSVD_ERR_INVALID_ARG for n < 0 or null pointers with n > 0; asynchronous on `stream`. */
 int rhosvd_selftest_fastmath(const double* x, double* rcp, double* rsq, int n, void* stream);
+
+/* FP64 rate probe (no paper counterpart: measurement support; the denominators of the FP64
+ * rooflines are measured with it).  Launches `blocks` blocks of 256 threads, each thread
+ * running eight independent FP64 fma chains of `iters` steps: 4096 * iters FLOP a block.
+ * out: device array of blocks * 256 doubles (caller-owned) receiving each thread's chain sum.
+ * Time it with events on `stream`.  RHOSVD_ERR_INVALID_ARG for blocks outside [1, 2^20],
+ * iters < 1 or a null `out`. */
+int rhosvd_probe_fp64(int blocks, int iters, double* out, void* stream);
 
 /* ---------------------------------------------------------------- tracing (no paper
  * counterpart: observability of the library itself) */

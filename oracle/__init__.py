@@ -143,6 +143,29 @@ def normalize(U, xi):
     return Un, xin, norms.reshape(3, R), keep
 
 
+def project(Z, Un):
+    """V = Z^T Un (r x R) by the oracle's explicit loops (Prop. 2.2: D_{l,0} V_0^T = Z_0^T U)."""
+    Z = _f64(Z)
+    Un = _f64(Un)
+    n, r = Z.shape
+    R = Un.shape[1]
+    V = np.zeros((r, R), order="F")
+    lib().orc_project(n, R, r, _dp(Z), _dp(Un), _dp(V))
+    return V
+
+
+def core(V, xin):
+    """beta(i, j, m) = sum_nu xin_nu V1(i, nu) V2(j, nu) V3(m, nu) by the oracle's explicit
+    loops (Prop. 2.2); returns an (r1, r2, r3) array."""
+    V = [_f64(v) for v in V]
+    xin = np.ascontiguousarray(xin, dtype=np.float64)
+    r = np.array([v.shape[0] for v in V], dtype=np.int32)
+    R = xin.shape[0]
+    beta = np.zeros(max(int(np.prod(r)), 1))
+    lib().orc_core(R, _ip(r), _dp(V[0]), _dp(V[1]), _dp(V[2]), _dp(xin), _dp(beta))
+    return beta[: int(np.prod(r))].reshape(tuple(int(x) for x in r), order="F")
+
+
 def c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=None, max_sweeps=100):
     """The whole RHOSVD.  Returns a dict with Z (list of n_l x r_l), beta (r1,r2,r3 array,
     index [i,j,m]), sigma (list), V (list of r_l x R), xin, ranks, kept, xi_norm, tails."""
@@ -175,6 +198,36 @@ def c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=None, max_sweeps=100):
     out["V"] = [V[l][: r[l] * R].reshape((r[l], R), order="F") for l in range(3)]
     out["beta"] = beta[: r[0] * r[1] * r[2]].reshape((r[0], r[1], r[2]), order="F")
     out["tails"] = [float(np.sqrt(np.sum(out["sigma"][l][r[l]:] ** 2))) for l in range(3)]
+    return out
+
+
+def c2t_threads(U, xi, eps=1e-6, ranks=(0, 0, 0), max_sweeps=100):
+    """The same RHOSVD as ``c2t`` (the steps of orc_c2t in its order: normalisation, per mode
+    the full side-matrix SVD and its eps-rank, V = Z^T U~, the core), with the three modes'
+    SVDs run at once in three host threads (ctypes releases the GIL during each C call; the
+    C routines keep no global state).  Returns the same dict, plus the wall time of each step."""
+    import time
+    from concurrent.futures import ThreadPoolExecutor
+    t0 = time.perf_counter()
+    Un, xin, _, keep = normalize(U, xi)
+    t1 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=3) as ex:
+        svd = list(ex.map(lambda l: side_svd(Un[l], max_sweeps), range(3)))
+    t2 = time.perf_counter()
+    r = []
+    for l in range(3):
+        sig = svd[l][0]
+        q = sig.shape[0]
+        r.append(min(ranks[l], q) if ranks[l] > 0 else eps_rank(sig, eps))
+    Z = [np.asfortranarray(svd[l][1][:, : r[l]]) for l in range(3)]
+    V = [project(Z[l], Un[l]) for l in range(3)]
+    t3 = time.perf_counter()
+    beta = core(V, xin)
+    t4 = time.perf_counter()
+    out = dict(ranks=r, kept=int(keep.sum()), xi_norm=float(np.sqrt(np.sum(xin * xin))), xin=xin,
+               Z=Z, Z_full=[svd[l][1] for l in range(3)], sigma=[svd[l][0] for l in range(3)], V=V, beta=beta)
+    out["tails"] = [float(np.sqrt(np.sum(out["sigma"][l][r[l]:] ** 2))) for l in range(3)]
+    out["seconds"] = dict(normalize=t1 - t0, svd=t2 - t1, project=t3 - t2, core=t4 - t3)
     return out
 
 

@@ -46,7 +46,7 @@ class rhosvd_cp(_c.Structure):
 
 class rhosvd_opts(_c.Structure):
     _fields_ = [("eps", _c.c_double), ("ranks", _c.c_int * 3), ("r_max", _c.c_int), ("oversample", _c.c_int),
-                ("precision", _c.c_int), ("deflate", _c.c_int), ("seed", _c.c_ulonglong)]
+                ("precision", _c.c_int), ("deflate", _c.c_int), ("seed", _c.c_ulonglong), ("out_fp32", _c.c_int)]
 
 
 class rhosvd_info(_c.Structure):
@@ -141,6 +141,14 @@ def load(build_if_missing: bool = False):
         L.rhosvd_mlp_num_params.restype = _c.c_longlong
         L.rhosvd_mlp_params.restype = _c.c_int
         L.rhosvd_mlp_params.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int]
+        L.rhosvd_probe_fp64.restype = _c.c_int
+        L.rhosvd_probe_fp64.argtypes = [_c.c_int, _c.c_int, _c.c_void_p, _c.c_void_p]
+        L.rhosvd_mlp_save.restype = _c.c_int
+        L.rhosvd_mlp_save.argtypes = [_c.c_void_p, _c.c_char_p]
+        L.rhosvd_mlp_load.restype = _c.c_int
+        L.rhosvd_mlp_load.argtypes = [_c.c_void_p, _c.c_char_p]
+        L.rhosvd_mlp_status.restype = _c.c_int
+        L.rhosvd_mlp_status.argtypes = [_c.c_void_p, _c.c_void_p]
         L.rhosvd_features.restype = _c.c_int
         L.rhosvd_features.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_double, _c.c_double,
                                       _c.c_double, _c.c_void_p, _c.c_void_p]
@@ -243,8 +251,9 @@ def make_cp(U, xi) -> rhosvd_cp:
 
 
 def make_opts(eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0,
-              precision=RHOSVD_PLAIN_FP64, deflate=0) -> rhosvd_opts:
+              precision=RHOSVD_PLAIN_FP64, deflate=0, out_fp32=False) -> rhosvd_opts:
     o = rhosvd_opts()
+    o.out_fp32 = 1 if out_fp32 else 0
     o.eps = float(eps)
     for l in range(3):
         o.ranks[l] = int(ranks[l])
@@ -553,10 +562,12 @@ class TuckerResult:
         return r, beta, Z
 
 
-def alloc_tucker(n, R, r_max, device="cuda", with_V=False, with_xi=False) -> TuckerResult:
+def alloc_tucker(n, R, r_max, device="cuda", with_V=False, with_xi=False, fp32=False) -> TuckerResult:
+    """Output buffers of one reduction; fp32=True gives float32 Z and beta (opts.out_fp32)."""
     torch = _torch()
-    Z = [torch.empty(r_max, n[l], dtype=torch.float64, device=device).t() for l in range(3)]
-    beta = torch.empty(r_max ** 3, dtype=torch.float64, device=device)
+    zt = torch.float32 if fp32 else torch.float64
+    Z = [torch.empty(r_max, n[l], dtype=zt, device=device).t() for l in range(3)]
+    beta = torch.empty(r_max ** 3, dtype=zt, device=device)
     sigma = torch.empty(3, RHOSVD_K_MAX, dtype=torch.float64, device=device)
     V = [torch.empty(max(R, 1), r_max, dtype=torch.float64, device=device).t() for _ in range(3)] if with_V else None
     xi_out = torch.empty(max(R, 1), dtype=torch.float64, device=device) if with_xi else None
@@ -576,21 +587,30 @@ def tucker_struct(res: TuckerResult) -> rhosvd_tucker:
     return t
 
 
+def _check_out_dtype(out, out_fp32):
+    torch = _torch()
+    want = torch.float32 if out_fp32 else torch.float64
+    if out.beta.dtype != want or any(z.dtype != want for z in out.Z):
+        raise ValueError(f"Z and beta buffers must be {want} (out_fp32={bool(out_fp32)})")
+
+
 def rhosvd_c2t(U, xi, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0, out=None,
                workspace=None, stream=None, with_V=False, with_xi=False,
-               precision=RHOSVD_PLAIN_FP64, deflate=0) -> TuckerResult:
-    """RHOSVD canonical-to-Tucker transform of the CP tensor (U[0], U[1], U[2], xi)."""
+               precision=RHOSVD_PLAIN_FP64, deflate=0, out_fp32=False) -> TuckerResult:
+    """RHOSVD canonical-to-Tucker transform of the CP tensor (U[0], U[1], U[2], xi).
+    out_fp32=True writes Z and beta as float32 (sigma, V, xi' stay float64)."""
     torch = _torch()
     L = load()
     cp = make_cp(U, xi)
-    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate)
+    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate, out_fp32)
     need = int(L.rhosvd_c2t_workspace_size(_c.byref(cp), _c.byref(opts)))
     if need == 0:
         raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_c2t_workspace_size")
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=U[0].device)
     if out is None:
-        out = alloc_tucker([cp.n[l] for l in range(3)], cp.R, r_max, U[0].device, with_V, with_xi)
+        out = alloc_tucker([cp.n[l] for l in range(3)], cp.R, r_max, U[0].device, with_V, with_xi, out_fp32)
+    _check_out_dtype(out, out_fp32)
     t = tucker_struct(out)
     rc = L.rhosvd_c2t(_c.byref(cp), _c.byref(opts), _c.byref(t), _c.c_void_p(workspace.data_ptr()),
                       _c.c_size_t(workspace.numel()), _stream_handle(stream))
@@ -628,20 +648,21 @@ def rhosvd_c2t_als(U, xi, sweeps=1, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversam
 
 def rhosvd_c2t_hadamard(Ua, xa, Ub, xb, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0, out=None,
                         workspace=None, stream=None, with_V=False, with_xi=False, precision=RHOSVD_PLAIN_FP64,
-                        deflate=0) -> TuckerResult:
+                        deflate=0, out_fp32=False) -> TuckerResult:
     """RHOSVD of the Hadamard product of the CP tensors (Ua, xa) and (Ub, xb), the product's
     columns formed as they are read (bit-identical to rhosvd_cp_hadamard + rhosvd_c2t)."""
     torch = _torch()
     L = load()
     a, b = make_cp(Ua, xa), make_cp(Ub, xb)
-    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate)
+    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate, out_fp32)
     need = int(L.rhosvd_c2t_hadamard_workspace_size(_c.byref(a), _c.byref(b), _c.byref(opts)))
     if need == 0:
         raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_c2t_hadamard_workspace_size")
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=Ua[0].device)
     if out is None:
-        out = alloc_tucker([a.n[l] for l in range(3)], a.R * b.R, r_max, Ua[0].device, with_V, with_xi)
+        out = alloc_tucker([a.n[l] for l in range(3)], a.R * b.R, r_max, Ua[0].device, with_V, with_xi, out_fp32)
+    _check_out_dtype(out, out_fp32)
     t = tucker_struct(out)
     rc = L.rhosvd_c2t_hadamard(_c.byref(a), _c.byref(b), _c.byref(opts), _c.byref(t),
                                _c.c_void_p(workspace.data_ptr()), _c.c_size_t(workspace.numel()),
@@ -652,13 +673,14 @@ def rhosvd_c2t_hadamard(Ua, xa, Ub, xb, eps=1e-6, ranks=(0, 0, 0), r_max=64, ove
 
 
 def rhosvd_c2t_noalloc(U, xi, out, eps=1e-6, ranks=(0, 0, 0), r_max=64, oversample=32, seed=0,
-                       stream=None, precision=RHOSVD_PLAIN_FP64, deflate=0) -> TuckerResult:
+                       stream=None, precision=RHOSVD_PLAIN_FP64, deflate=0, out_fp32=False) -> TuckerResult:
     """rhosvd_c2t without a workspace argument, for callers that cannot allocate device memory:
     the library uses its own static scratch array (RHOSVD_NOALLOC_SCRATCH_BYTES).  `out` must
     be provided (see alloc_tucker); this function allocates nothing."""
     L = load()
     cp = make_cp(U, xi)
-    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate)
+    opts = make_opts(eps, ranks, r_max, oversample, seed, precision, deflate, out_fp32)
+    _check_out_dtype(out, out_fp32)
     t = tucker_struct(out)
     rc = L.rhosvd_c2t_noalloc(_c.byref(cp), _c.byref(opts), _c.byref(t), _stream_handle(stream))
     if rc != RHOSVD_OK:
@@ -872,6 +894,34 @@ class Mlp:
         rc = load().rhosvd_mlp_params(self.h, _c.c_void_p(buf.ctypes.data), 0, 0)
         if rc != RHOSVD_OK:
             raise RhosvdError(rc, "rhosvd_mlp_params")
+
+    def save(self, path):
+        """Checkpoint: weights, Adam moments and step count into one binary file."""
+        rc = load().rhosvd_mlp_save(self.h, os.fsencode(path))
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_mlp_save")
+
+    def load_state(self, path):
+        """Resume from a checkpoint written by save() (the handle is unchanged on error)."""
+        rc = load().rhosvd_mlp_load(self.h, os.fsencode(path))
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_mlp_load")
+
+    def status(self, stream=None):
+        """Raise if a tensor-core product of the network hit its bounded wait since the last check."""
+        rc = load().rhosvd_mlp_status(self.h, _stream_handle(stream))
+        if rc != RHOSVD_OK:
+            raise RhosvdError(rc, "rhosvd_mlp_status")
+
+
+def rhosvd_probe_fp64(blocks, iters, out, stream=None):
+    """Launch the FP64 fma-rate probe (4096 * iters FLOP a block) writing into `out`
+    (float64 CUDA tensor of blocks * 256 entries)."""
+    if out.dtype != _torch().float64 or out.numel() < blocks * 256 or not out.is_cuda:
+        raise ValueError("out must be a float64 CUDA tensor of blocks * 256 entries")
+    rc = load().rhosvd_probe_fp64(int(blocks), int(iters), _c.c_void_p(out.data_ptr()), _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_probe_fp64")
 
 
 def rhosvd_features(centres, loga, c, cbox, la, lb, stream=None):

@@ -239,6 +239,9 @@ struct Plan {
     // ALS refinement (als > 0 sweeps): C_l (KW x rmax^2), split-K partials of G_l, energies
     int als, ks_als;
     size_t o_als_C, o_als_part, o_als_e, o_als_q, o_als_k;
+    // FP32 outputs: Z and beta are formed in FP64 here, then rounded into the caller's buffers
+    int out_fp32;
+    size_t o_zf, o_bf;
     size_t total;
 };
 
@@ -262,6 +265,7 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
     if (k0 < 0 || k0 > KMAX - 64) return RHOSVD_ERR_INVALID_ARG;
     if (o->precision != RHOSVD_PLAIN_FP64 && o->precision != RHOSVD_MIXED) return RHOSVD_ERR_INVALID_ARG;
     if (!(o->eps >= 0.0)) return RHOSVD_ERR_INVALID_ARG;
+    if (o->out_fp32 != 0 && o->out_fp32 != 1) return RHOSVD_ERR_INVALID_ARG;
     memset(p, 0, sizeof(*p));
     p->R = cp->R;
     p->rmax = o->r_max;
@@ -387,6 +391,11 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
         p->o_als_e = take(sizeof(double) * 6 * (size_t)als);
         p->o_als_q = take(sizeof(double) * rh::KMAX);
         p->o_als_k = take(sizeof(int) * 3);
+    }
+    p->out_fp32 = o->out_fp32;
+    if (p->out_fp32) {
+        p->o_zf = take(sizeof(double) * 3 * (size_t)p->NQ * p->rmax);
+        p->o_bf = take(sizeof(double) * (size_t)p->rmax * p->rmax * p->rmax);
     }
     p->total = off;
     return RHOSVD_OK;
@@ -514,8 +523,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
     // ---- reset outputs and state
     if (cudaMemsetAsync(out->info, 0, sizeof(rhosvd_info), st) != cudaSuccess) return RHOSVD_ERR_CUDA;
     if (cudaMemsetAsync(S, 0, sizeof(DevState), st) != cudaSuccess) return RHOSVD_ERR_CUDA;
+    // Z and beta as formed here: the caller's buffers, or FP64 staging for FP32 outputs
+    double* Zout[3];
+    double* beta_out = p.out_fp32 ? (double*)(ws + p.o_bf) : (double*)out->beta;
     for (int l = 0; l < 3; ++l) {
-        if (cudaMemsetAsync(out->Z[l], 0, sizeof(double) * (size_t)p.n[l] * rmax, st) != cudaSuccess)
+        Zout[l] = p.out_fp32 ? (double*)(ws + p.o_zf) + (size_t)l * p.NQ * rmax : (double*)out->Z[l];
+        if (cudaMemsetAsync(Zout[l], 0, sizeof(double) * (size_t)p.n[l] * rmax, st) != cudaSuccess)
             return RHOSVD_ERR_CUDA;
         if (cudaMemsetAsync(out->sigma[l], 0, sizeof(double) * KMAX, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
     }
@@ -1430,7 +1443,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
 
     if (R > 0) {
         // ---- outputs: Z = Z_hi(:, :r), optional V = V_hi(:r, :)
-        double* zd[3] = {out->Z[0], out->Z[1], out->Z[2]};
+        double* zd[3] = {Zout[0], Zout[1], Zout[2]};
         int zld[3] = {p.n[0], p.n[1], p.n[2]};
         STAGE("copy_out", launch_copy2d(Zw, NK, zld, zd, zld, nullptr, p.n, S->r, nullptr, st));
         if (out->V[0] && out->V[1] && out->V[2]) {
@@ -1449,7 +1462,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         gc.bkind = B_KR;
         GemmProblem g = blank_problem();
         g.A = Mat{Vw, 1, KW};
-        g.C = out->beta;
+        g.C = beta_out;
         g.crs = 1;
         g.ccs = -1;           // = r1, decided on the device
         g.M = rmax;
@@ -1502,7 +1515,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             q.N = rcap;
             q.dN = &S->r[0];
             q.K = R;
-            q.C = out->beta;
+            q.C = beta_out;
             q.crs = -1;
             q.ccs = 1;
             // split-K by the ranks (on the device): few output tiles (small ranks) with a long
@@ -1518,6 +1531,14 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         } else {
             STAGE("core", launch_gemm(gc, st));
         }
+    }
+    if (p.out_fp32) {
+        // round Z (every column, zeros included) and the packed core once into the FP32 outputs
+        const double* src[4] = {Zout[0], Zout[1], Zout[2], beta_out};
+        float* dst[4] = {(float*)out->Z[0], (float*)out->Z[1], (float*)out->Z[2], (float*)out->beta};
+        long long cnt[4] = {(long long)p.n[0] * rmax, (long long)p.n[1] * rmax, (long long)p.n[2] * rmax,
+                            R > 0 ? -1 : 0};
+        STAGE("copy_out", launch_to_f32(src, dst, cnt, S->r, 4, st));
     }
     return RHOSVD_OK;
 }

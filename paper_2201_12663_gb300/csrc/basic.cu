@@ -529,3 +529,67 @@ extern "C" int rhosvd_selftest_fastmath(const double* x, double* rcp, double* rs
     rh::count_launch();
     return cudaGetLastError() == cudaSuccess ? RHOSVD_OK : RHOSVD_ERR_CUDA;
 }
+
+namespace rh {
+
+struct ToF32Args {
+    const double* src[4];
+    float* dst[4];
+    long long cnt[4];
+    const int* dr;
+};
+
+// grid (blocks, nb), block 256: grid-stride over the entries of array blockIdx.y
+__global__ void k_to_f32(ToF32Args a)
+{
+    const int b = blockIdx.y;
+    const long long cnt = a.cnt[b] >= 0 ? a.cnt[b] : (long long)a.dr[0] * a.dr[1] * a.dr[2];
+    const double* s = a.src[b];
+    float* d = a.dst[b];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.x * blockDim.x)
+        d[e] = __double2float_rn(s[e]);
+}
+
+int launch_to_f32(const double* const src[4], float* const dst[4], const long long cnt[4], const int* dr, int nb,
+                  cudaStream_t st)
+{
+    if (nb < 1 || nb > 4) return RHOSVD_ERR_INVALID_ARG;
+    ToF32Args a;
+    for (int b = 0; b < 4; ++b) {
+        a.src[b] = b < nb ? src[b] : nullptr;
+        a.dst[b] = b < nb ? dst[b] : nullptr;
+        a.cnt[b] = b < nb ? cnt[b] : 0;
+    }
+    a.dr = dr;
+    k_to_f32<<<dim3(2 * 152, nb), 256, 0, st>>>(a);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
+
+}  // namespace rh
+
+// FP64 FMA rate probe: eight independent fma chains per thread (a <- a b + c), `iters` steps
+// each; the chains' sum is stored so that nothing is dead code.  2 * 8 * iters FLOP a thread.
+__global__ void __launch_bounds__(256) k_fp64_rate(int iters, double b, double c, double* out)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = 1.0 + 1e-3 * (double)(j + (int)(t & 255));
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fma(a[j], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += a[j];
+    out[t] = s;
+}
+
+extern "C" int rhosvd_probe_fp64(int blocks, int iters, double* out, void* stream)
+{
+    if (blocks < 1 || blocks > (1 << 20) || iters < 1 || !out) return RHOSVD_ERR_INVALID_ARG;
+    k_fp64_rate<<<blocks, 256, 0, (cudaStream_t)stream>>>(iters, 0.999999999, 1e-12, out);
+    RH_CHECK_LAUNCH();
+    return RHOSVD_OK;
+}

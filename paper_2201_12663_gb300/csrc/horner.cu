@@ -56,6 +56,7 @@ int horner_plan(const rhosvd_cp* A, int ncoeffs, const double* coeffs, const rho
 {
     if (!A || !o || ncoeffs < 1 || R_max < 1 || A->R < 0) return RHOSVD_ERR_INVALID_ARG;
     if (o->r_max < 1 || o->r_max > KMAX) return RHOSVD_ERR_INVALID_ARG;
+    if (o->out_fp32 != 0) return RHOSVD_ERR_INVALID_ARG;     // each step reads its Tucker tensor back in FP64
     if ((long long)o->r_max * o->r_max > RHOSVD_T2C_SLICE_MAX) return RHOSVD_ERR_INVALID_ARG;
     pl->deg = coeffs ? horner_degree(coeffs, ncoeffs) : ncoeffs - 1;
     pl->rin_max = (long long)A->R * R_max + 1;
@@ -193,10 +194,10 @@ extern "C" int rhosvd_cp_horner(const rhosvd_cp* A, const double* coeffs, int nc
         for (int l = 0; l < 3; ++l) {
             tin.n[l] = A->n[l];
             tin.r[l] = info.r[l];
-            tin.Z[l] = tk.Z[l];
+            tin.Z[l] = (const double*)tk.Z[l];
             tin.ldz[l] = A->n[l];
         }
-        tin.beta = tk.beta;
+        tin.beta = (const double*)tk.beta;
         rc = rhosvd_t2c(&tin, eps_t2c, R_max, U_out, ldu, xi_out, ints_d, nullptr, ints_d + 1, ws + pl.o_t2c,
                         pl.t2c_bytes, stream);
         if (rc) return rc;

@@ -366,6 +366,10 @@ int launch_rank(const RankArgs& a, cudaStream_t st);
 int launch_rank_final(const FinalArgs& a, cudaStream_t st);
 int launch_copy2d(const double* src, long long sstride, const int lds[3], double* const dst[3], const int ldd[3],
                   const int* drows, const int hrows[3], const int* dcols, const int hcols[3], cudaStream_t st);
+// FP32 outputs: dst[b][e] = (float)src[b][e] (round to nearest) for e < cnt[b], or, where cnt[b]
+// < 0, for e < dr[0] dr[1] dr[2] (the packed core of device ranks dr).  nb <= 4.
+int launch_to_f32(const double* const src[4], float* const dst[4], const long long cnt[4], const int* dr, int nb,
+                  cudaStream_t st);
 int launch_eigvecs(ModeMap mm, const double* D, const double* Lo, const double* mu, int vstride, const int* dk,
                    const DevState* s, double* W, long long wstride, int ldw, int rmax, int nb, cudaStream_t st);
 int launch_backtransform(ModeMap mm, const double* A, long long astride, int lda, const double* tau, int vstride,

@@ -14,6 +14,7 @@
 #include "ozgemm.cuh"
 
 #include <cuda_bf16.h>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -518,6 +519,116 @@ extern "C" int rhosvd_mlp_params(void* handle, float* host, int get, int which)
         if (refresh_bf16(m, 0) || cudaDeviceSynchronize() != cudaSuccess) return RHOSVD_ERR_CUDA;
     }
     return 0;
+}
+
+namespace {
+const char MLP_TAG[8] = {'R', 'H', 'M', 'L', 'P', 'v', '0', '1'};
+
+// lengths of the six FP32 state arrays of layer i in file order: W, b, m(W), v(W), m(b), v(b)
+void layer_lengths(int i, size_t len[6])
+{
+    const size_t wsz = (size_t)DIMS[i] * DIMS[i + 1], bsz = (size_t)DIMS[i + 1];
+    const size_t l[6] = {wsz, bsz, wsz, wsz, bsz, bsz};
+    for (int k = 0; k < 6; ++k) len[k] = l[k];
+}
+
+// the handle's device arrays of layer i in the same order
+void layer_arrays(Mlp* m, int i, float* arr[6])
+{
+    float* a[6] = {m->W[i], m->b[i], m->mW[i], m->vW[i], m->mb[i], m->vb[i]};
+    for (int k = 0; k < 6; ++k) arr[k] = a[k];
+}
+}  // namespace
+
+extern "C" int rhosvd_mlp_save(void* handle, const char* path)
+{
+    Mlp* m = (Mlp*)handle;
+    if (!m || !path) return RHOSVD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mlp_mu);
+    if (cudaDeviceSynchronize() != cudaSuccess) return RHOSVD_ERR_CUDA;
+    std::vector<float> host;
+    FILE* f = fopen(path, "wb");
+    if (!f) return RHOSVD_ERR_INVALID_ARG;
+    int32_t hdr[NL + 2];
+    hdr[0] = NL;
+    for (int i = 0; i <= NL; ++i) hdr[1 + i] = DIMS[i];
+    const int64_t step = m->step;
+    bool ok = fwrite(MLP_TAG, 1, 8, f) == 8 && fwrite(hdr, sizeof(int32_t), NL + 2, f) == (size_t)(NL + 2) &&
+              fwrite(&step, sizeof(step), 1, f) == 1;
+    int rc = RHOSVD_OK;
+    for (int i = 0; ok && i < NL; ++i) {
+        float* arr[6];
+        size_t len[6];
+        layer_lengths(i, len);
+        layer_arrays(m, i, arr);
+        for (int k = 0; ok && k < 6; ++k) {
+            host.resize(len[k]);
+            if (cudaMemcpy(host.data(), arr[k], sizeof(float) * len[k], cudaMemcpyDeviceToHost) != cudaSuccess) {
+                rc = RHOSVD_ERR_CUDA;
+                ok = false;
+                break;
+            }
+            ok = fwrite(host.data(), sizeof(float), len[k], f) == len[k];
+        }
+    }
+    ok = (fclose(f) == 0) && ok;
+    if (rc) return rc;
+    return ok ? RHOSVD_OK : RHOSVD_ERR_INVALID_ARG;
+}
+
+extern "C" int rhosvd_mlp_load(void* handle, const char* path)
+{
+    Mlp* m = (Mlp*)handle;
+    if (!m || !path) return RHOSVD_ERR_INVALID_ARG;
+    FILE* f = fopen(path, "rb");
+    if (!f) return RHOSVD_ERR_INVALID_ARG;
+    // read and check the whole file before touching the handle
+    char tag[8];
+    int32_t hdr[NL + 2];
+    int64_t step = 0;
+    bool ok = fread(tag, 1, 8, f) == 8 && memcmp(tag, MLP_TAG, 8) == 0 &&
+              fread(hdr, sizeof(int32_t), NL + 2, f) == (size_t)(NL + 2) && hdr[0] == NL &&
+              fread(&step, sizeof(step), 1, f) == 1 && step >= 0 && step < (1LL << 40);
+    for (int i = 0; ok && i <= NL; ++i) ok = hdr[1 + i] == DIMS[i];
+    std::vector<std::vector<float>> body;
+    for (int i = 0; ok && i < NL; ++i) {
+        size_t len[6];
+        layer_lengths(i, len);
+        for (int k = 0; ok && k < 6; ++k) {
+            body.emplace_back(len[k]);
+            ok = fread(body.back().data(), sizeof(float), len[k], f) == len[k];
+        }
+    }
+    if (ok) {                                 // nothing may follow the record
+        char extra;
+        ok = fread(&extra, 1, 1, f) == 0;
+    }
+    fclose(f);
+    if (!ok) return RHOSVD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mlp_mu);
+    if (cudaDeviceSynchronize() != cudaSuccess) return RHOSVD_ERR_CUDA;
+    size_t q = 0;
+    for (int i = 0; i < NL; ++i) {
+        float* arr[6];
+        size_t len[6];
+        layer_lengths(i, len);
+        layer_arrays(m, i, arr);
+        for (int k = 0; k < 6; ++k, ++q)
+            if (cudaMemcpy(arr[k], body[q].data(), sizeof(float) * len[k], cudaMemcpyHostToDevice) != cudaSuccess)
+                return RHOSVD_ERR_CUDA;
+    }
+    m->step = (int)step;
+    if (refresh_bf16(m, 0) || cudaDeviceSynchronize() != cudaSuccess) return RHOSVD_ERR_CUDA;
+    return RHOSVD_OK;
+}
+
+extern "C" int rhosvd_mlp_status(void* handle, void* stream)
+{
+    if (!handle) return RHOSVD_ERR_INVALID_ARG;
+    int v = 0;
+    const int rc = oz_take_status((cudaStream_t)stream, &v);
+    if (rc) return rc;
+    return v ? RHOSVD_ERR_TIMEOUT : RHOSVD_OK;
 }
 
 extern "C" int rhosvd_features(const double* centres, const double* loga, const double* c, int R, double cbox,

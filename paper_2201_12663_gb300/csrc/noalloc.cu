@@ -15,6 +15,10 @@
 //   * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
 //     once per device, with that device current).  Make that first call before any stream
 //     capture begins.
+//   * The address is cached per device ordinal for the life of the process, so the entry point
+//     assumes the runtime's primary context of each device: after cudaDeviceReset, or with
+//     another context made current through the driver API, the cached address is stale and the
+//     entry point must not be used.
 //   * Every call on a device uses the same array, and the array keeps whatever the previous
 //     call left in it.  The reduction clears what it needs cleared itself.  Calls whose work
 //     overlaps on the GPU (other streams, other host threads) race on the array: serialise them.

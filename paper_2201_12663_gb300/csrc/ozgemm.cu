@@ -19,6 +19,25 @@
 
 namespace rh {
 
+// status word of the tensor-core products launched without a caller status (the network
+// kernels): RHOSVD_ERR_TIMEOUT once a bounded wait expired; read and cleared by oz_take_status
+__device__ int g_oz_status = 0;
+
+int oz_take_status(cudaStream_t st, int* out)
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbolAsync(&v, g_oz_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RHOSVD_ERR_CUDA;
+    if (v != 0) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbolAsync(g_oz_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return RHOSVD_ERR_CUDA;
+    }
+    *out = v;
+    return RHOSVD_OK;
+}
+
 namespace {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -290,7 +309,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
         }
     };
 
+    // A bounded wait that expires sets s_fail; from then on no thread produces a stage, reads
+    // TMEM back or issues an MMA (every thread sees the flag after the next barrier), and the
+    // epilogue stores nothing.
     bool ok = true;
+    int last_commit = -1;                     // stage whose MMAs were committed last
     if (nkt > 0) produce(0, 0);
     constexpr uint32_t IDESC = oz_idesc(NT);
     for (int kt = 0; kt < nkt; ++kt) {
@@ -298,6 +321,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
+        if (*(volatile int*)&s_fail) break;
+        last_commit = kt;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t aBase = smem_u32(oz_smem + buf * STAGE);
@@ -332,21 +357,39 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
         }
         // produce the next stage into the other buffer once the MMAs that read it are done
         if (kt + 1 < nkt) {
-            if (kt >= 1) ok = oz_wait(&mbar[buf ^ 1], (uint32_t)(((kt - 1) >> 1) & 1)) && ok;
-            produce(kt + 1, buf ^ 1);
+            if (kt >= 1 && !oz_wait(&mbar[buf ^ 1], (uint32_t)(((kt - 1) >> 1) & 1))) {
+                ok = false;
+                s_fail = 1;
+            }
+            if (ok) produce(kt + 1, buf ^ 1);
         }
         const bool last = (kt + 1 == nkt);
-        if (last || (kt % MINCAD) == MINCAD - 1) {      // every cadence is a multiple of MINCAD
-            ok = oz_wait(&mbar[buf], (uint32_t)((kt >> 1) & 1)) && ok;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok && (last || (kt % MINCAD) == MINCAD - 1)) {      // every cadence is a multiple of MINCAD
+            if (!oz_wait(&mbar[buf], (uint32_t)((kt >> 1) & 1))) {
+                ok = false;
+                s_fail = 1;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int a = NU - 1; a >= 0; --a) {
-                const int cad = oz_acc_cad(SA, SB, NE, a, W);
-                if (last || (kt % cad) == cad - 1) readback(tmem + (uint32_t)(a * NT));
+                for (int a = NU - 1; a >= 0; --a) {
+                    const int cad = oz_acc_cad(SA, SB, NE, a, W);
+                    if (last || (kt % cad) == cad - 1) readback(tmem + (uint32_t)(a * NT));
+                }
             }
         }
     }
-    if (!ok) s_fail = 1;
+    __syncthreads();
+    const bool failed = *(volatile int*)&s_fail != 0;
+    if (failed) {
+        // wait (bounded again) for the last committed MMAs before TMEM is freed
+        if (last_commit >= 0) oz_wait(&mbar[last_commit & 1], (uint32_t)((last_commit >> 1) & 1));
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) atomicCAS(batch.err ? batch.err : &g_oz_status, 0, RHOSVD_ERR_TIMEOUT);
+        if (EPI == OZ_EPI_RESID && tid == 0) P.rpart[blockIdx.x + gridDim.x * blockIdx.y] = 0.0;
+        if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+        return;
+    }
     const int row = i0 + q4 * 32 + lane;
     int ea = (ASRC == OZ_A_PLANES && P.A.exps && row < M) ? (int)P.A.exps[row] : (ASRC == OZ_A_PLANES ? P.A.exp0 : 0);
     if (ASRC == OZ_A_KR && P.kr.e2 && row < M) ea = (int)P.kr.e2[row % r2] + (int)P.kr.e3[row / r2];
@@ -376,7 +419,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozgemm(OzBatch batch)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid == 0 && s_fail && batch.err) atomicCAS(batch.err, 0, RHOSVD_ERR_TIMEOUT);
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 

@@ -165,6 +165,10 @@ enum OzKind { OZ_F64_STORE = 0, OZ_F64_RESID = 1, OZ_SKETCH = 2, OZ_CORE = 3, OZ
 // used by the learned-proposal network.
 int launch_ozgemm(const OzBatch& b, OzKind kind, cudaStream_t st);
 
+// status of the products launched with OzBatch::err == nullptr: copies the library's status word
+// to *out (RHOSVD_ERR_TIMEOUT after an expired wait, else 0) and clears it; synchronises `st`
+int oz_take_status(cudaStream_t st, int* out);
+
 // split count for an M x N x K product: enough CTAs for two per SM, at least 4 stages each
 int oz_choose_split(int M, int N, int K, int nt, int nbatch);
 // the Khatri-Rao core's split count from the device ranks r (see k_core_split)

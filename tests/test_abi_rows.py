@@ -159,3 +159,32 @@ def test_graph_null_handles(lib):
     assert L.rhosvd_graph_end(None, ctypes.byref(h)) == P.RHOSVD_ERR_INVALID_ARG
     assert L.rhosvd_graph_launch(None, None) == P.RHOSVD_ERR_INVALID_ARG
     assert L.rhosvd_graph_destroy(None) == P.RHOSVD_OK
+
+
+def test_mlp_checkpoint_file_checks(lib, tmp_path):
+    """rhosvd_mlp_load validates the whole file before it touches the handle: a missing file, a
+    wrong tag, other layer widths, a short body and trailing bytes are all INVALID_ARG (the
+    placeholder handle is never dereferenced on these paths)."""
+    import numpy as np
+    P, L = lib
+    bad = P.RHOSVD_ERR_INVALID_ARG
+    h = ctypes.c_void_p(FAKE)
+    assert L.rhosvd_mlp_load(h, os.fsencode(str(tmp_path / "none.bin"))) == bad
+    assert L.rhosvd_mlp_load(None, os.fsencode(str(tmp_path / "none.bin"))) == bad
+    dims = [128, 512, 512, 512, 2048]
+    nbody = sum(3 * dims[i] * dims[i + 1] + 3 * dims[i + 1] for i in range(4))   # W, b and their moments
+
+    def write(name, tag=b"RHMLPv01", d=dims, step=7, n=nbody, extra=b""):
+        p = tmp_path / name
+        with open(p, "wb") as f:
+            f.write(tag)
+            f.write(np.array([4] + list(d), dtype="<i4").tobytes())
+            f.write(np.array([step], dtype="<i8").tobytes())
+            f.write(np.zeros(n, dtype="<f4").tobytes())
+            f.write(extra)
+        return os.fsencode(str(p))
+    assert L.rhosvd_mlp_load(h, write("tag.bin", tag=b"RHMLPv99")) == bad
+    assert L.rhosvd_mlp_load(h, write("dims.bin", d=[128, 256, 512, 512, 2048])) == bad
+    assert L.rhosvd_mlp_load(h, write("short.bin", n=nbody - 1)) == bad
+    assert L.rhosvd_mlp_load(h, write("extra.bin", extra=b"\0")) == bad
+    assert L.rhosvd_mlp_load(h, write("step.bin", step=-1)) == bad

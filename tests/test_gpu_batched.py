@@ -73,3 +73,41 @@ def test_batched_latency_record(rhosvd_cuda):
     torch.cuda.synchronize()
     assert all(np.isfinite(x) and x > 0 for x in lat)
     assert all(o.info().status == 0 for o in outs)
+
+
+_oracle_cache = {}
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_members_match_the_oracle(rhosvd_cuda, precision):
+    """Two members of a batch, one of the batched workload's largest kind (n = 1024, R = 4200),
+    against the oracle's exact RHOSVD: ranks (+-1 only at a threshold tie), tails, sigma and the
+    Tucker tensor to 1e-6, as for single calls (tests/test_gpu_parity.py)."""
+    import oracle
+    from tests.test_gpu_parity import assert_rank_parity, assert_sigma_parity, assert_tail_parity, oracle_at_ranks
+    from tests import tensor_utils as tu
+    P = rhosvd_cuda
+    import torch
+    shapes = [(1024, 4200, 21), (256, 300, 2), (128, 200, 1), (512, 1500, 9)]
+    opt = dict(eps=1e-6, r_max=160, oversample=32, seed=13)
+    cps = [workloads.gaussian_sum(n, R, s) for n, R, s in shapes]
+    ts = [([P.to_device_factor(u) for u in cp.U], torch.from_numpy(cp.xi).cuda()) for cp in cps]
+    outs, _ = P.rhosvd_c2t_batched(ts, lanes=0, precision=precision, with_V=False, **opt)
+    torch.cuda.synchronize()
+    for i in (0, 1):
+        if i not in _oracle_cache:
+            _oracle_cache[i] = oracle.c2t_threads(cps[i].U, cps[i].xi, eps=opt["eps"])
+        o = _oracle_cache[i]
+        info = outs[i].info()
+        assert info.status == 0, P.rhosvd_strerror(info.status)
+        r = [info.r[l] for l in range(3)]
+        g = dict(info=info, ranks=r, sigma=outs[i].sigma.cpu().numpy(),
+                 beta=outs[i].beta[: r[0] * r[1] * r[2]].cpu().numpy().reshape(r, order="F"),
+                 Z=[outs[i].Z[l][:, : r[l]].cpu().numpy() for l in range(3)])
+        assert_rank_parity(g, o, opt["eps"])
+        assert_sigma_parity(g, o, [shapes[i][0]] * 3)
+        oc = o if r == o["ranks"] else oracle_at_ranks(cps[i].U, cps[i].xi, o, r)
+        assert_tail_parity(g, oc, opt["eps"], True)
+        d = tu.tucker_rel_diff(g["beta"], g["Z"], oc["beta"], oc["Z"])
+        print(f"batch member {shapes[i]} precision={precision}: Tucker vs oracle {d:.3e}")
+        assert d <= 1e-6, (i, d)

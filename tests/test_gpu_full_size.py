@@ -1,18 +1,24 @@
 """Full-size parity on the Hadamard workload that bench.py times (two rank-64 Gaussian sums,
-n = 1024, product rank R = 4096, eps = 1e-7), in the bench's launch configuration, for both forms.
+n = 1024, product rank R = 4096, eps = 1e-7) and on the range-separated collective potential
+(n = 2048, R = 20000, eps = 1e-6), in the bench's launch configuration, for both forms.
 
-The oracle's exact RHOSVD at this size takes minutes, so its per-mode singular values, eps-ranks,
-tails, kept-term count and ||xi'|| are stored in tests/golden/ by tests/golden/make_full_size.py
-(which calls only oracle/).  Z and beta are checked through properties that hold at any size,
-on sampled entries computed one by one on the CPU:
+The oracle's exact RHOSVD at these sizes takes from a minute to tens of minutes, so its per-mode
+singular values, eps-ranks, tails, kept-term count and ||xi'|| (``<case>.json``) and its leading
+left singular vectors Z^(l) (``<case>_Z.npz``, r_l + 4 columns) are stored in tests/golden/ by
+tests/golden/make_full_size.py, which calls only oracle/.  From the stored Z the test rebuilds the
+oracle's V^(l) = Z^(l)T U~^(l) and core beta with the oracle's own loops (Prop. 2.2) and compares
+the Tucker tensors element by element in a common basis (tests/tensor_utils.tucker_rel_diff):
+<= 1e-6 relative for both forms (the plain-form bar; the mixed form's products carry FP64-class
+digits, its core about 2^-29 of the operands' row scales).  Where a GPU rank is one off at a
+threshold tie, the oracle is truncated at the GPU's rank (the stored extra columns).  On top:
   * Z^(l) orthonormal;
   * V^(l)(:, nu) = Z^(l)^T u~_nu for sampled terms nu, with u~_nu the normalised Hadamard column
     formed on the CPU from the two input factors (Prop. 2.2: V = D V_0^T = Z_0^T U);
-  * beta(i, j, m) = sum_nu xi'_nu V1(i, nu) V2(j, nu) V3(m, nu) for sampled (i, j, m), from the
-    library's own V and xi' (Prop. 2.2), so the Khatri-Rao contraction is checked at full size;
+  * beta(i, j, m) against the sum of xi'_nu V1(i, nu) V2(j, nu) V3(m, nu) over the library's own V
+    and xi', for sampled (i, j, m): the Khatri-Rao contraction's arithmetic on its own inputs,
+    with the bound derived from its digit scheme (see core_entry_bound);
   * the two forms agree on the Tucker tensor.
-Tolerances as in test_gpu_parity.py; the mixed core's bound is derived from its digit
-rounding relative to the operands' row maxima (see the core check)."""
+Tolerances for ranks, sigma and tails as in test_gpu_parity.py."""
 import json
 import math
 import os
@@ -20,14 +26,49 @@ import os
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 from tests import tensor_utils as tu
 
 pytestmark = pytest.mark.gpu
 
-GOLD_PATH = os.path.join(os.path.dirname(__file__), "golden", "hadamard_n1024_R64x64_eps1e-7.json")
+GOLD_DIR = os.path.join(os.path.dirname(__file__), "golden")
+GOLD_PATH = os.path.join(GOLD_DIR, "hadamard_n1024_R64x64_eps1e-7.json")
 OPTS = dict(eps=1e-7, r_max=160, oversample=32, seed=12345)     # bench.py's options
 U64 = np.finfo(np.float64).eps
+TUCKER_TOL = 1e-6
+
+
+def load_gold_Z(name):
+    z = np.load(os.path.join(GOLD_DIR, f"{name}_Z.npz"))
+    return [np.asfortranarray(z[f"Z{l}"]) for l in range(3)]
+
+
+class OracleTucker:
+    """The oracle's Tucker tensor of a full-size case at given ranks, from its stored singular
+    vectors: V = Z^T U~ (orc_project) and beta (orc_core) over the oracle's normalisation."""
+
+    def __init__(self, U, xi, Zs):
+        self.Un, self.xin, _, _ = oracle.normalize(U, xi)
+        self.Zs = Zs
+        self._cache = {}
+
+    def at(self, ranks):
+        key = tuple(ranks)
+        if key not in self._cache:
+            assert all(ranks[l] <= self.Zs[l].shape[1] for l in range(3)), (ranks, [z.shape for z in self.Zs])
+            Z = [np.asfortranarray(self.Zs[l][:, : ranks[l]]) for l in range(3)]
+            V = [oracle.project(Z[l], self.Un[l]) for l in range(3)]
+            self._cache[key] = (oracle.core(V, self.xin), Z)
+        return self._cache[key]
+
+
+def assert_ranks_at_tie(rg, ro, so, thr):
+    """Equal, or one apart where the oracle's tail is within 1e-3 of the threshold."""
+    if rg != ro:
+        lo = min(rg, ro)
+        t1, t0 = np.sum(so[lo + 1:] ** 2), np.sum(so[lo:] ** 2)
+        assert abs(rg - ro) == 1 and (abs(t1 - thr) <= 1e-3 * thr or abs(t0 - thr) <= 1e-3 * thr), (rg, ro)
 
 
 @pytest.fixture(scope="module")
@@ -39,6 +80,13 @@ def gold():
 @pytest.fixture(scope="module")
 def factors():
     return workloads.hartree_like_factors(1024, 64, 64, (0, 1))
+
+
+@pytest.fixture(scope="module")
+def oracle_had(factors):
+    A, B = factors
+    U, xi = oracle.cp_hadamard(A.U, A.xi, B.U, B.xi)
+    return OracleTucker(U, xi, load_gold_Z("hadamard_n1024_R64x64_eps1e-7"))
 
 
 _cache = {}
@@ -73,6 +121,45 @@ def normalised_column(A, B, l, nu):
     return u / np.linalg.norm(u)
 
 
+def frexp_scale(x, lo=-126, hi=127, widen=0.0):
+    """2^E, an upper bound on the per-row digit scale of the mixed form: E the frexp exponent of
+    max|x| (1 + widen) (|x| < 2^E), clamped to [lo, hi] as the slicers clamp it."""
+    m = float(np.max(np.abs(x)))
+    e = math.frexp(m * (1.0 + widen))[1] if m > 0.0 else lo
+    return 2.0 ** min(hi, max(lo, e))
+
+
+# Bound on one core entry of the mixed form, per term nu and in units of 2^(Ea + Eb) (the two
+# operand rows' digit scales): S = 4 base-256 digits per operand, the first <= 2^8, the others
+# < 2^8, the last rounded; every pair s + t <= GMAX = 5 is multiplied.
+#   * dropped pairs s + t = 6, 7, 8 (3, 2 and 1 pairs), each below 2^16 2^(-8 (s + t)):
+C_DROP = 3 * 2.0 ** -32 + 2 * 2.0 ** -40 + 2.0 ** -48
+#   * rounding of the last digit of each operand (|x - x^| <= 2^(E - 33)): 2 2^-33 + 2^-66
+C_ROUND = 2 * 2.0 ** -33 + 2.0 ** -66
+#   * groups 2 and 3 are accumulated exactly (read back before their FP32 sums can round); groups
+#     4 and 5 share one FP32 accumulator read back every 128 K (4 stages of 32).  In that
+#     accumulator's units (2^(Ea + Eb - 16)) a term adds at most 3 + 4 2^-8 (three pairs below 1,
+#     four below 2^-8), so a 128-term block stays below 128 (3 + 2^-6); it receives 7 pairs x 2
+#     K-halves x 4 stages = 56 MMAs, each rounding (the tensor cores truncate) by at most
+#     2 2^-23 of (|accumulator| + the sum of its 16 products):
+C_ACC = 56 * 2 * 2.0 ** -23 * (128 * (3 + 2.0 ** -6) + 16) * 2.0 ** -16 / 128
+C_CORE = C_DROP + C_ROUND + C_ACC          # about 2^-29.3 per term
+
+
+def core_entry_bound(precision, a, V2j, V3m, bb):
+    """|beta_gpu(i, j, m) - sum_nu a_nu bb_nu| for a = xi' V1(i, .), bb = V2(j, .) V3(m, .)."""
+    terms = np.abs(a * bb).sum()
+    if precision == 0:
+        return 1e-12 * terms                 # FP64 sum of R products: R u sum|terms| < 1e-12 sum|terms|
+    R = a.shape[0]
+    # the generated Khatri-Rao row is cut with E = e2[j] + e3[m], each taken from the FP32 heads
+    # of its factor's row (max |h| (1 + 2^-20), clamped to [-45, 1]); the other operand row with
+    # the frexp exponent of its own largest entry
+    ev = dict(lo=-45, hi=1, widen=2.0 ** -20 + 2.0 ** -23)
+    scale = frexp_scale(a) * frexp_scale(V2j, **ev) * frexp_scale(V3m, **ev)
+    return R * C_CORE * scale + 1e-12 * terms
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_full_size_ranks_sigma_tails(rhosvd_cuda, factors, gold, precision):
     g = run_full(rhosvd_cuda, factors, precision)
@@ -86,18 +173,24 @@ def test_full_size_ranks_sigma_tails(rhosvd_cuda, factors, gold, precision):
         total = gold["total"][l]
         thr = eps * eps * total
         rg, ro = g["ranks"][l], gold["ranks"][l]
-        if rg != ro:
-            # a difference of one only at a threshold tie (the oracle's tail within 1e-3 of eps^2 total)
-            lo = min(rg, ro)
-            t1, t0 = np.sum(so[lo + 1:] ** 2), np.sum(so[lo:] ** 2)
-            assert abs(rg - ro) == 1 and (abs(t1 - thr) <= 1e-3 * thr or abs(t0 - thr) <= 1e-3 * thr), (l, rg, ro)
+        assert_ranks_at_tie(rg, ro, so, thr)
         k = info.k[l]
         q = min(len(so), k, rg + 2)
         tol = 6 * U64 * (1024 * k + k * (k + 1)) * so[0] ** 2
         assert np.all(np.abs(g["sigma"][l][:q] ** 2 - so[:q] ** 2) <= tol + 1e-14 * so[:q] ** 2), l
-        if rg == ro:
-            assert info.tail[l] >= gold["tails"][l] * (1 - 1e-9) - 1e-13 * math.sqrt(total)
+        # the exact truncation at the GPU's rank is optimal
+        assert info.tail[l] >= np.sqrt(np.sum(so[rg:] ** 2)) * (1 - 1e-9) - 1e-13 * math.sqrt(total)
         assert info.tail[l] ** 2 <= thr * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_tucker_vs_oracle(rhosvd_cuda, factors, oracle_had, precision):
+    """||T_gpu - T_oracle||_F / ||T_oracle||_F at the benchmarked size, in a common basis."""
+    g = run_full(rhosvd_cuda, factors, precision)
+    beta_o, Z_o = oracle_had.at(g["ranks"])
+    d = tu.tucker_rel_diff(g["beta"], g["Z"], beta_o, Z_o)
+    print(f"hadamard n=1024 R=4096 precision={precision}: ||T_gpu - T_oracle|| / ||T_oracle|| = {d:.3e}")
+    assert d <= TUCKER_TOL, d
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -111,12 +204,6 @@ def test_full_size_factors_and_core(rhosvd_cuda, factors, precision):
         for nu in rng.choice(4096, size=48, replace=False):
             ref = Z.T @ normalised_column(A, B, l, int(nu))
             assert np.abs(g["V"][l][:, nu] - ref).max() <= 1e-12, (l, nu)
-    # core entries from the library's own V and xi'.  Plain: FP64 rounding of the sum.  Mixed:
-    # the core's operands a = xi' V1(i, .) and b = V2(j, .) V3(m, .) are cut into 4 base-256
-    # digits relative to their row maxima (a row of b uses max|V2(j, .)| max|V3(m, .)|), so each
-    # term is off by at most 2^-33 (max|a| |b_nu| + |a_nu| max|b|) from the digit rounding.  The
-    # groups s + t = 4, 5 are summed in FP32 over runs of 128 K between readbacks (inexact, the
-    # tensor cores truncate); 2^-28 leaves a factor 32 for them and the pair products.
     V1, V2, V3 = g["V"]
     xin = g["xin"]
     r = g["ranks"]
@@ -124,14 +211,8 @@ def test_full_size_factors_and_core(rhosvd_cuda, factors, precision):
         i, j, m = (int(rng.integers(r[0])), int(rng.integers(r[1])), int(rng.integers(r[2])))
         a = xin * V1[i]
         bb = V2[j] * V3[m]
-        terms = a * bb
-        if precision == 0:
-            tol = 1e-12 * np.abs(terms).sum()
-        else:
-            amax = np.abs(a).max()
-            bmax = np.abs(V2[j]).max() * np.abs(V3[m]).max()
-            tol = 2.0 ** -28 * (amax * np.abs(bb).sum() + bmax * np.abs(a).sum())
-        assert abs(g["beta"][i, j, m] - terms.sum()) <= tol, (i, j, m)
+        tol = core_entry_bound(precision, a, V2[j], V3[m], bb)
+        assert abs(g["beta"][i, j, m] - (a * bb).sum()) <= tol, (i, j, m)
 
 
 def test_full_size_forms_agree(rhosvd_cuda, factors):
@@ -144,7 +225,8 @@ def test_full_size_forms_agree(rhosvd_cuda, factors):
 # ---------------------------------------------------------------- range-separated collective potential
 # Long-range Newton Gaussians of N = 1000 unit charges (20 a charge): n = 2048, R = 20000, eps = 1e-6.
 
-NEWTON_GOLD = os.path.join(os.path.dirname(__file__), "golden", "newton_n2048_N1000_eps1e-6.json")
+NEWTON = "newton_n2048_N1000_eps1e-6"
+NEWTON_GOLD = os.path.join(GOLD_DIR, f"{NEWTON}.json")
 NEWTON_OPTS = dict(eps=1e-6, r_max=64, oversample=32, seed=2024)
 
 
@@ -152,17 +234,20 @@ NEWTON_OPTS = dict(eps=1e-6, r_max=64, oversample=32, seed=2024)
 def newton():
     cp = workloads.newton_long_range_sum(n=2048, N=1000, seed=0)
     with open(NEWTON_GOLD) as f:
-        return cp, json.load(f)
+        return cp, json.load(f), OracleTucker(cp.U, cp.xi, load_gold_Z(NEWTON))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_full_size_newton(rhosvd_cuda, newton, precision):
+@pytest.mark.parametrize("precision,out_fp32", [(0, False), (1, False), (1, True)])
+def test_full_size_newton(rhosvd_cuda, newton, precision, out_fp32):
+    """Ranks, sigma, tails, factors and the Tucker tensor against the oracle.  With FP32 outputs
+    (Z and beta rounded once to FP32, 2^-24 relative per entry) the Tucker bar is the same."""
     P = rhosvd_cuda
     import torch
-    cp, gold = newton
+    cp, gold, orc = newton
     Ud = [P.to_device_factor(u) for u in cp.U]
     xd = torch.from_numpy(cp.xi).cuda()
-    res = P.rhosvd_c2t(Ud, xd, with_V=True, with_xi=True, precision=precision, **NEWTON_OPTS)
+    res = P.rhosvd_c2t(Ud, xd, with_V=True, with_xi=True, precision=precision, out_fp32=out_fp32,
+                       **NEWTON_OPTS)
     info = res.info()
     assert info.status == 0, P.rhosvd_strerror(info.status)
     assert info.kept == gold["kept"]
@@ -170,25 +255,28 @@ def test_full_size_newton(rhosvd_cuda, newton, precision):
     r = [info.r[l] for l in range(3)]
     eps = NEWTON_OPTS["eps"]
     sig = res.sigma.cpu().numpy()
+    zt = 1e-6 if out_fp32 else 1e-12
+    Zs = []
     for l in range(3):
         so = np.array(gold["sigma"][l])
         total = gold["total"][l]
         thr = eps * eps * total
-        if r[l] != gold["ranks"][l]:
-            lo = min(r[l], gold["ranks"][l])
-            t1, t0 = np.sum(so[lo + 1:] ** 2), np.sum(so[lo:] ** 2)
-            assert abs(r[l] - gold["ranks"][l]) == 1 and (abs(t1 - thr) <= 1e-3 * thr or abs(t0 - thr) <= 1e-3 * thr)
-        else:
-            assert info.tail[l] >= gold["tails"][l] * (1 - 1e-9) - 1e-13 * math.sqrt(total)
+        assert_ranks_at_tie(r[l], gold["ranks"][l], so, thr)
+        assert info.tail[l] >= np.sqrt(np.sum(so[r[l]:] ** 2)) * (1 - 1e-9) - 1e-13 * math.sqrt(total)
         k = info.k[l]
         q = min(len(so), k, r[l] + 2)
         tol = 6 * U64 * (2048 * k + k * (k + 1)) * so[0] ** 2
         assert np.all(np.abs(sig[l][:q] ** 2 - so[:q] ** 2) <= tol + 1e-14 * so[:q] ** 2), l
         assert info.tail[l] ** 2 <= thr * (1 + 1e-9)
-        Z = res.Z[l][:, : r[l]].cpu().numpy()
-        assert np.abs(Z.T @ Z - np.eye(r[l])).max() <= 1e-12
+        Z = res.Z[l][:, : r[l]].cpu().double().numpy()
+        Zs.append(Z)
+        assert np.abs(Z.T @ Z - np.eye(r[l])).max() <= zt
         V = res.V[l][: r[l], :].cpu().numpy()
         for nu in np.random.default_rng(3 + l).choice(cp.U[l].shape[1], size=32, replace=False):
             u = cp.U[l][:, nu] / np.linalg.norm(cp.U[l][:, nu])
-            assert np.abs(V[:, nu] - Z.T @ u).max() <= 1e-12, (l, nu)
-
+            assert np.abs(V[:, nu] - Z.T @ u).max() <= zt, (l, nu)
+    beta = res.beta[: r[0] * r[1] * r[2]].cpu().double().numpy().reshape(r, order="F")
+    beta_o, Z_o = orc.at(r)
+    d = tu.tucker_rel_diff(beta, Zs, beta_o, Z_o)
+    print(f"newton n=2048 R=20000 precision={precision} fp32={out_fp32}: ||T_gpu - T_oracle|| / ||T_oracle|| = {d:.3e}")
+    assert d <= TUCKER_TOL, d

@@ -159,3 +159,51 @@ def test_training_lowers_the_loss_and_gains_over_random_and_untrained(rhosvd_cud
     assert missed[("learned", 0)] < missed[("untrained", 0)], missed
     prop.mlp.close()
     fresh.mlp.close()
+
+
+def test_checkpoint_resumes_training_exactly(rhosvd_cuda, tmp_path):
+    """rhosvd_mlp_save / rhosvd_mlp_load: train a few Adam steps, save, train on; a second handle
+    loaded from the file and trained on the same batches gives the same losses and weights bit
+    for bit (weights, both Adam moments and the step count are restored: without the moments or
+    the bias-correction step the first resumed update would differ).  The file follows the
+    documented layout (tag, widths, step, per layer W, b, m(W), v(W), m(b), v(b))."""
+    P = rhosvd_cuda
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(5)
+    batches = [(torch.rand(16, 128, generator=g, device="cuda"), torch.rand(16, 4096, generator=g, device="cuda"))
+               for _ in range(6)]
+    a = P.Mlp(batch_max=16, seed=9)
+    for X, G in batches[:3]:
+        a.train_step(X, G, 1e-3)
+    path = str(tmp_path / "mlp.bin")
+    a.save(path)
+    w_saved = a.params()
+    la = [float(a.train_step(X, G, 1e-3).item()) for X, G in batches[3:]]
+    a.status()
+    b = P.Mlp(batch_max=16, seed=123)            # other initial weights, overwritten by the load
+    b.load_state(path)
+    assert np.array_equal(b.params(), w_saved)
+    lb = [float(b.train_step(X, G, 1e-3).item()) for X, G in batches[3:]]
+    b.status()
+    assert la == lb, (la, lb)
+    assert np.array_equal(a.params(), b.params())
+    # the documented layout, read back with numpy
+    raw = open(path, "rb").read()
+    assert raw[:8] == b"RHMLPv01"
+    hdr = np.frombuffer(raw[8:32], dtype="<i4")
+    assert hdr.tolist() == [4, 128, 512, 512, 512, 2048]
+    assert int(np.frombuffer(raw[32:40], dtype="<i8")[0]) == 3
+    body = np.frombuffer(raw[40:], dtype="<f4")
+    dims = hdr[1:]
+    o, got = 0, []
+    for i in range(4):
+        wsz, bsz = int(dims[i] * dims[i + 1]), int(dims[i + 1])
+        got.append(body[o:o + wsz]); o += wsz
+        got.append(body[o:o + bsz]); o += bsz
+        o += 2 * wsz + 2 * bsz                     # the Adam moments
+    assert o == body.size
+    assert np.array_equal(np.concatenate(got), w_saved)
+    with pytest.raises(P.RhosvdError):
+        b.load_state(str(tmp_path / "missing.bin"))
+    a.close()
+    b.close()

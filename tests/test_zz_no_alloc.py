@@ -2,7 +2,9 @@
 host application owns every device allocation, or they must not risk the synchronisation
 cudaMalloc/cudaFree may cause).  It takes its scratch space from a static device array
 instead of a caller workspace.  Checked through the C ABI against rhosvd_c2t on the same
-input, on two calls in a row (the second runs on whatever the first left in the array).
+input, on two calls in a row; between them a different problem (other sizes, the mixed form)
+runs through the same array, so the second checked call starts from another call's leftovers
+in a different layout, not from a zero-initialised array or the same values.
 
 This file is collected last so that a run stopping at the first failure has already run
 every other test; it also passes on its own in a fresh process."""
@@ -47,8 +49,22 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(rhosvd_cuda):
     info_r, r_ref, beta_r, Z_r, sig_r = _read(ref)
     assert info_r.status == 0
 
+    # the problem run between the two checked calls: other n and R, the mixed form
+    Cg = workloads.gaussian_sum(192, 333, 4)
+    Ug = [P.to_device_factor(u) for u in Cg.U]
+    xg = torch.from_numpy(Cg.xi).cuda()
+    opts_g = dict(eps=1e-6, r_max=96, oversample=24, seed=5, precision=1)
+    ref_g = P.rhosvd_c2t(Ug, xg, **opts_g)
+    _, r_g, beta_g, Z_g, _ = _read(ref_g)
+    out_g = P.alloc_tucker([192, 192, 192], 333, opts_g["r_max"])
+
     out = P.alloc_tucker([256, 256, 256], Uc[0].shape[1], OPTS["r_max"])
     for call in range(2):
+        if call == 1:
+            P.rhosvd_c2t_noalloc(Ug, xg, out_g, **opts_g)
+            info_g, rr, bb, ZZ, _ = _read(out_g)
+            assert info_g.status == 0 and rr == r_g
+            assert tu.tucker_rel_diff(bb, ZZ, beta_g, Z_g) <= 1e-6
         out.beta.fill_(np.nan)
         for z in out.Z:
             z.fill_(np.nan)
