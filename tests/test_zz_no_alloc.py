@@ -53,9 +53,11 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(rhosvd_cuda):
     Cg = workloads.gaussian_sum(192, 333, 4)
     Ug = [P.to_device_factor(u) for u in Cg.U]
     xg = torch.from_numpy(Cg.xi).cuda()
-    opts_g = dict(eps=1e-6, r_max=96, oversample=24, seed=5, precision=1)
+    opts_g = dict(eps=1e-6, r_max=128, oversample=24, seed=5, precision=1)
     ref_g = P.rhosvd_c2t(Ug, xg, **opts_g)
-    _, r_g, beta_g, Z_g, _ = _read(ref_g)
+    info_rg, r_g, beta_g, Z_g, _ = _read(ref_g)
+    assert info_rg.status == 0, P.rhosvd_strerror(info_rg.status)
+    assert info_rg.direct[0] == 0                    # a sketched mode (n = 192 > k = 152)
     out_g = P.alloc_tucker([192, 192, 192], 333, opts_g["r_max"])
 
     out = P.alloc_tucker([256, 256, 256], Uc[0].shape[1], OPTS["r_max"])
