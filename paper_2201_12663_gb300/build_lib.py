@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librhosvd.so")
-SOURCES = ["api.cu", "basic.cu", "gemm_f64.cu", "smallla.cu", "noalloc.cu", "ozgemm.cu", "batched.cu", "mlp.cu", "cluster.cu", "t2c.cu", "horner.cu", "energy.cu", "als.cu"]
+SOURCES = ["api.cu", "basic.cu", "gemm_f64.cu", "smallla.cu", "noalloc.cu", "ozgemm.cu", "ozgemm_tma.cu", "batched.cu", "mlp.cu", "cluster.cu", "t2c.cu", "horner.cu", "energy.cu", "als.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-cudart", "shared",
          "--expt-relaxed-constexpr"]

@@ -229,6 +229,9 @@ struct Plan {
     // mixed-precision form: digit planes and helpers
     int mixed;
     int ldR, ldn, ldk;            // plane row lengths (multiples of 8) for K = R, n, k
+    int tkR;                      // k tiles of the tile-major U~ planes with K = R
+    long long sSg;                // per-mode size of the sketch's sign plane (elements)
+    size_t o_sgn;
     size_t o_pU1, o_pU2, o_pP1, o_pP2, o_eU2, o_eP1, o_eP2, o_Vt;
     long long EX;         // per-mode stride of the per-row exponent arrays
     int oz_s_sketch, oz_s_gram, oz_s_bbt;   // split-K counts of the tensor-core products
@@ -336,6 +339,10 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
     p->o_V = take(sizeof(double) * 3 * (size_t)p->KW * R);
     p->o_Z = take(sizeof(double) * 3 * NK);
     p->rp_stride = (long long)((p->NQ + 63) / 64) * ((R + 63) / 64);
+    if (o->precision == RHOSVD_MIXED) {
+        const long long t = rh::ozgemm_tma_tiles(rh::OZ_F64_RESID, p->NQ, R);
+        if (t > p->rp_stride) p->rp_stride = t;
+    }
     p->o_rp = take(sizeof(double) * 3 * (size_t)p->rp_stride);
     p->o_cpart = take(sizeof(double) * 3 * (size_t)rh::RITZ_CHUNKS * rh::KMAX);
     if (p->kdef > 0) {
@@ -349,16 +356,19 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
         p->ldR = up8(R);
         p->ldn = up8(p->NQ);
         p->ldk = up8(p->KW);
-        p->sU1 = (long long)OZ_S64 * p->NQ * p->ldR;
-        p->sU2 = (long long)OZ_S64 * R * p->ldn;
-        long long a1 = (long long)R * p->ldk, a2 = (long long)p->KW * p->ldR, a3 = (long long)p->KW * p->ldk;
-        a1 = a1 > a2 ? a1 : a2;
-        p->sP1 = (long long)OZ_S64 * (a1 > a3 ? a1 : a3);
-        long long b1 = (long long)p->KW * p->ldn, b2 = (long long)p->KW * p->ldk, b3 = (long long)p->NQ * p->ldk;
-        long long bm = b1 > b2 ? b1 : b2;
-        bm = bm > b3 ? bm : b3;
-        bm = bm > a2 ? bm : a2;
-        p->sP2 = (long long)OZ_S64 * bm;
+        // the two digit-plane sets of U~ are tile-major (whole 128 x 16 tiles, see ozgemm.cuh):
+        // U1 rows x, k = nu; U2 rows nu, k = x
+        p->tkR = (R + 15) / 16;
+        p->sU1 = (long long)OZ_S64 * ((p->NQ + 127) / 128 * 128) * (p->tkR * 16LL);
+        p->sU2 = (long long)OZ_S64 * ((R + 127) / 128 * 128) * ((p->NQ + 15) / 16 * 16LL);
+        // the small operands' plane sets (tile-major: rows padded to 128, k to 16; enough for
+        // the row-major layout too)
+        auto tsz = [](long long rows, long long K) { return (rows + 127) / 128 * 128 * ((K + 15) / 16 * 16); };
+        long long pm = tsz(R, p->KW);
+        const long long cand[4] = {tsz(p->KW, R), tsz(p->KW, p->KW), tsz(p->KW, p->NQ), tsz(p->NQ, p->KW)};
+        for (long long c : cand) pm = c > pm ? c : pm;
+        p->sP1 = (long long)OZ_S64 * pm;
+        p->sP2 = (long long)OZ_S64 * pm;
         p->o_pU1 = take(sizeof(uint16_t) * 3 * (size_t)p->sU1);
         p->o_pU2 = take(sizeof(uint16_t) * 3 * (size_t)p->sU2);
         p->o_pP1 = take(sizeof(uint16_t) * 3 * (size_t)p->sP1);
@@ -369,6 +379,9 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
         p->o_eP1 = take(3 * (size_t)p->EX);
         p->o_eP2 = take(3 * (size_t)p->EX);
         p->o_Vt = take(sizeof(double) * 3 * (size_t)R * p->KW);
+        // the sketch's signs as tile-major BF16 planes (rows = sketch columns)
+        p->sSg = (long long)((p->KW + 127) / 128 * 128) * (p->tkR * 16LL);
+        p->o_sgn = take(sizeof(uint16_t) * 3 * (size_t)p->sSg);
         int nsk = 0;
         for (int l = 0; l < 3; ++l) nsk += p->direct[l] ? 0 : 1;
         p->oz_s_sketch = nsk > 0 ? rh::oz_choose_split((int)p->NQ, p->KW, R, 96, nsk) : 1;
@@ -406,6 +419,28 @@ GemmProblem blank_problem()
     GemmProblem g;
     memset(&g, 0, sizeof(g));
     return g;
+}
+
+// Tile-major digit planes for the TMA-fed products: problem b of a slice call writes tiles of H
+// rows (LANE: the operand on the TMEM lanes; COL: the one stacked along N), and the operand handed
+// to the product describes the same layout.
+constexpr int LANE = rh::OZ_BM, COL = 32;
+
+void tiled_out(OzSliceArgs& s, int b, int H)
+{
+    s.tiles_k[b] = (s.K[b] + 15) / 16;
+    s.tile_h[b] = H;
+}
+
+OzPlanes planes_of(const OzSliceArgs& s, int b)
+{
+    return OzPlanes{s.planes[b], s.pstride[b], s.ld[b], s.exps[b], s.exp0, s.tiles_k[b], s.tile_h[b]};
+}
+
+// the second copy of a dual-layout slice
+OzPlanes planes2_of(const OzSliceArgs& s, int b)
+{
+    return OzPlanes{s.planes2[b], s.pstride[b], s.ld[b], s.exps[b], s.exp0, s.tiles_k[b], s.tile_h2[b]};
 }
 
 }  // namespace
@@ -517,6 +552,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
     signed char* eP2 = mixed ? (signed char*)(ws + p.o_eP2) : nullptr;
     const long long EX = mixed ? p.EX : 0;
     double* Vt = mixed ? (double*)(ws + p.o_Vt) : nullptr;
+    uint16_t* sgn = mixed ? (uint16_t*)(ws + p.o_sgn) : nullptr;
     double* ozpart = mixed ? (double*)(ws + p.o_ozpart) : nullptr;
     int* ozerr = &out->info->status;
 
@@ -559,6 +595,8 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             ns.pstride[l] = (long long)R * p.ldn;
             ns.ld[l] = p.ldn;
             ns.exps[l] = eU2 + l * EX;
+            ns.tiles_k[l] = (p.n[l] + 15) / 16;
+            ns.tile_h[l] = LANE;                   // on the TMEM lanes of the projection
         }
     }
     STAGE("normalize", launch_terms(na, cp->xi, keepf, xin, out->xi_out, out->info, Un, US, nn2, S->total, ns, st));
@@ -595,10 +633,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             sb.K[b] = R;
             sb.planes[b] = pU1 + l * p.sU1;
             sb.pstride[b] = (long long)p.n[l] * p.ldR;
-            sb.ld[b] = p.ldR;
+            sb.ld[b] = p.tkR * 16;                 // every k of the last tile written (zeros past R)
+            sb.tiles_k[b] = p.tkR;
+            sb.tile_h[b] = COL;                    // stacked along N in the sketches
             nmax = p.n[l] > nmax ? p.n[l] : nmax;
         }
-        STAGE("slice_u", launch_slice_t(sb, nsk, p.ldR, nmax, st));
+        STAGE("slice_u", launch_slice_t(sb, nsk, p.tkR * 16, nmax, st));
     }
 
     if (nsk > 0 && R > 0) {
@@ -655,9 +695,10 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                     sq.pstride[b] = (long long)p.kin[l] * p.ldn;
                     sq.ld[b] = p.ldn;
                     sq.exps[b] = eP2 + l * EX;
+                    tiled_out(sq, b, COL);
                     OzProblem& q = o1.p[b];
-                    q.A = OzPlanes{pU2 + l * p.sU2, (long long)R * p.ldn, p.ldn, eU2 + l * EX, 0};
-                    q.B = OzPlanes{sq.planes[b], sq.pstride[b], p.ldn, sq.exps[b], 0};
+                    q.A = OzPlanes{pU2 + l * p.sU2, (long long)R * p.ldn, p.ldn, eU2 + l * EX, 0, (p.n[l] + 15) / 16, LANE};
+                    q.B = planes_of(sq, b);
                     q.M = R;
                     q.N = p.kin[l];
                     q.K = p.n[l];
@@ -673,15 +714,18 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                     sp.pstride[b] = (long long)p.kin[l] * p.ldR;
                     sp.ld[b] = p.ldR;
                     sp.exps[b] = eP1 + l * EX;
+                    // Y^T = P^T U~^T: the rows j of P on the TMEM lanes, the tile-major planes
+                    // of U~ (rows x) stacked, Y(x, j) stored at x + n j
+                    tiled_out(sp, b, LANE);
                     OzProblem& q2 = o2.p[b];
-                    q2.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1};
-                    q2.B = OzPlanes{sp.planes[b], sp.pstride[b], p.ldR, sp.exps[b], 0};
-                    q2.M = p.n[l];
-                    q2.N = p.kin[l];
+                    q2.A = planes_of(sp, b);
+                    q2.B = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1, p.tkR, COL};
+                    q2.M = p.kin[l];
+                    q2.N = p.n[l];
                     q2.K = R;
                     q2.C = bufA + l * NK;
-                    q2.crs = 1;
-                    q2.ccs = p.n[l];
+                    q2.crs = p.n[l];
+                    q2.ccs = 1;
                 }
                 STAGE("sketch", launch_oz_slice(sq, nsk, st));
                 STAGE("sketch", launch_ozgemm(o1, OZ_F64_STORE, st));
@@ -727,10 +771,25 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             ob.nbatch = nsk;
             ob.nsplit = p.oz_s_sketch;
             ob.err = ozerr;
+            SignPlaneArgs sg;
+            memset(&sg, 0, sizeof(sg));
+            sg.tiles_k = p.tkR;
+            sg.seed = opts->seed;
+            int kmx = 0;
+            for (int b = 0; b < nsk; ++b) {
+                const int l = sk.m[b];
+                sg.planes[b] = sgn + l * p.sSg;
+                sg.rows[b] = p.kin[l];
+                sg.K[b] = R;
+                sg.mode[b] = l;
+                kmx = p.kin[l] > kmx ? p.kin[l] : kmx;
+            }
+            STAGE("sketch", launch_sign_planes(sg, nsk, kmx, st));
             for (int b = 0; b < nsk; ++b) {
                 const int l = sk.m[b];
                 OzProblem& q = ob.p[b];
-                q.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1};
+                q.B = OzPlanes{sgn + l * p.sSg, 0, 0, nullptr, 0, p.tkR, LANE};
+                q.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1, p.tkR, COL};
                 q.M = p.n[l];
                 q.N = p.kin[l];
                 q.K = R;
@@ -801,9 +860,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                     sg.pstride[b] = (long long)kh[l] * p.ldn;
                     sg.ld[b] = p.ldn;
                     sg.exps[b] = eP2 + l * EX;
+                    tiled_out(sg, b, LANE);
+                    sg.planes2[b] = pP1 + l * p.sP1;     // the same planes stacked along N
+                    sg.tile_h2[b] = COL;
                     OzProblem& q = ob.p[b];
-                    q.A = OzPlanes{sg.planes[b], sg.pstride[b], p.ldn, sg.exps[b], 0};
-                    q.B = q.A;
+                    q.A = planes_of(sg, b);
+                    q.B = planes2_of(sg, b);
                     q.M = q.N = kh[l];
                     if (pass > 0) q.dM = q.dN = &dm[l];
                     q.K = p.n[l];
@@ -858,9 +920,11 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                     sw.pstride[b] = (long long)kh[l] * p.ldk;
                     sw.ld[b] = p.ldk;
                     sw.exps[b] = eP1 + l * EX;
+                    tiled_out(sx, b, LANE);
+                    tiled_out(sw, b, COL);
                     OzProblem& q = ob.p[b];
-                    q.A = OzPlanes{sx.planes[b], sx.pstride[b], p.ldk, sx.exps[b], 0};
-                    q.B = OzPlanes{sw.planes[b], sw.pstride[b], p.ldk, sw.exps[b], 0};
+                    q.A = planes_of(sx, b);
+                    q.B = planes_of(sw, b);
                     q.M = p.n[l];
                     q.N = kh[l];
                     q.dN = &dm[l];
@@ -920,10 +984,23 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 ob.nbatch = nsk;
                 ob.nsplit = p.oz_s_defl;
                 ob.err = ozerr;
+                SignPlaneArgs sg;
+                memset(&sg, 0, sizeof(sg));
+                sg.tiles_k = p.tkR;
+                sg.seed = seed2;
+                for (int b = 0; b < nsk; ++b) {
+                    const int l = sk.m[b];
+                    sg.planes[b] = sgn + l * p.sSg;
+                    sg.rows[b] = p.kdef;
+                    sg.K[b] = R;
+                    sg.mode[b] = l;
+                }
+                STAGE("deflate_sketch", launch_sign_planes(sg, nsk, p.kdef, st));
                 for (int b = 0; b < nsk; ++b) {
                     const int l = sk.m[b];
                     OzProblem& q = ob.p[b];
-                    q.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1};
+                    q.B = OzPlanes{sgn + l * p.sSg, 0, 0, nullptr, 0, p.tkR, LANE};
+                    q.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1, p.tkR, COL};
                     q.M = p.n[l];
                     q.N = p.kdef;
                     q.K = R;
@@ -1011,8 +1088,9 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 sq.ld[l] = p.ldn;
                 sq.exps[l] = eP2 + l * EX;
                 OzProblem& q = ob.p[l];
-                q.A = OzPlanes{pU2 + l * p.sU2, (long long)R * p.ldn, p.ldn, eU2 + l * EX, 0};
-                q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.kb[l] * p.ldn, p.ldn, eP2 + l * EX, 0};
+                tiled_out(sq, l, COL);
+                q.A = OzPlanes{pU2 + l * p.sU2, (long long)R * p.ldn, p.ldn, eU2 + l * EX, 0, (p.n[l] + 15) / 16, LANE};
+                q.B = planes_of(sq, l);
                 q.M = R;
                 q.N = p.kb[l];
                 q.dN = &S->m[l];
@@ -1069,9 +1147,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 sg.pstride[l] = (long long)p.kb[l] * p.ldR;
                 sg.ld[l] = p.ldR;
                 sg.exps[l] = eP1 + l * EX;
+                tiled_out(sg, l, LANE);
+                sg.planes2[l] = pP2 + l * p.sP2;       // the same planes stacked along N
+                sg.tile_h2[l] = COL;
                 OzProblem& q = ob.p[l];
-                q.A = OzPlanes{sg.planes[l], sg.pstride[l], p.ldR, sg.exps[l], 0};
-                q.B = q.A;
+                q.A = planes_of(sg, l);
+                q.B = planes2_of(sg, l);
                 q.M = q.N = p.kb[l];
                 q.dM = q.dN = &S->m[l];
                 q.K = R;
@@ -1195,9 +1276,11 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 sw.pstride[l] = (long long)p.kb[l] * p.ldk;
                 sw.ld[l] = p.ldk;
                 sw.exps[l] = eP1 + l * EX;
+                tiled_out(sq, l, LANE);
+                tiled_out(sw, l, COL);
                 OzProblem& q = oz.p[l];
-                q.A = OzPlanes{sq.planes[l], sq.pstride[l], p.ldk, sq.exps[l], 0};
-                q.B = OzPlanes{sw.planes[l], sw.pstride[l], p.ldk, sw.exps[l], 0};
+                q.A = planes_of(sq, l);
+                q.B = planes_of(sw, l);
                 q.M = p.n[l];
                 q.N = p.kb[l];
                 q.dN = &S->rhi[l];
@@ -1245,9 +1328,11 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 s2.ld[l] = p.ldk;
                 s1.exps[l] = eP1 + l * EX;
                 s2.exps[l] = eP2 + l * EX;
+                tiled_out(s1, l, LANE);
+                tiled_out(s2, l, COL);
                 OzProblem& q = ob.p[l];
-                q.A = OzPlanes{pP1 + l * p.sP1, (long long)R * p.ldk, p.ldk, eP1 + l * EX, 0};
-                q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.kb[l] * p.ldk, p.ldk, eP2 + l * EX, 0};
+                q.A = planes_of(s1, l);
+                q.B = planes_of(s2, l);
                 q.M = R;
                 q.N = p.kb[l];
                 q.dN = &S->rhi[l];
@@ -1287,20 +1372,26 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
                 s2.ld[l] = p.ldk;
                 s1.exps[l] = eP1 + l * EX;
                 s2.exps[l] = eP2 + l * EX;
+                // (U~ - Z V)^T: operand rows x (Z) on the TMEM lanes, columns nu (V), so that the
+                // epilogue's reads of U~(x, nu) are consecutive across a warp
+                tiled_out(s2, l, LANE);
+                tiled_out(s1, l, COL);
                 OzProblem& q = orb.p[l];
-                q.A = OzPlanes{pP1 + l * p.sP1, (long long)R * p.ldk, p.ldk, eP1 + l * EX, 0};
-                q.B = OzPlanes{pP2 + l * p.sP2, (long long)p.n[l] * p.ldk, p.ldk, eP2 + l * EX, 0};
-                q.M = R;
-                q.N = p.n[l];
+                q.A = planes_of(s2, l);
+                q.B = planes_of(s1, l);
+                q.M = p.n[l];
+                q.N = R;
                 q.K = p.kb[l];
                 q.dK = &S->rhi[l];
                 q.ref = Un + l * US;
-                q.ref_rs = p.n[l];
-                q.ref_cs = 1;
+                q.ref_rs = 1;
+                q.ref_cs = p.n[l];
                 q.rpart = rpart + l * p.rp_stride;
             }
             STAGE("resid_slice", launch_oz_slice(s1, 3, st));
             STAGE("resid_slice", launch_oz_slice(s2, 3, st));
+            // every partial the final rank sums starts at zero, whatever grid the product runs on
+            if (cudaMemsetAsync(rpart, 0, sizeof(double) * 3 * p.rp_stride, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
             STAGE("residual", launch_ozgemm(orb, OZ_F64_RESID, st));
         } else {
             STAGE("v_hi", launch_gemm(gv, st));
@@ -1329,7 +1420,7 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
     for (int l = 0; l < 3; ++l) {
         fa.ranks[l] = opts->ranks[l];
         fa.n[l] = p.n[l];
-        fa.ntiles[l] = mixed ? ((R + OZ_BM - 1) / OZ_BM) * ((p.NQ + OZ_NT6 - 1) / OZ_NT6) : (int)p.rp_stride;
+        fa.ntiles[l] = (int)p.rp_stride;
     }
     STAGE("rank_final", launch_rank_final(fa, st));
 

@@ -209,6 +209,7 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
     uint16_t* P = sel3(ns.planes, l);
     const int pld = sel3(ns.ld, l);
     const long long pst = sel3(ns.pstride, l);
+    const int ptk = sel3(ns.tiles_k, l), pth = sel3(ns.tile_h, l);
     int E = -126;
     if (P) {
         const double mx = (a.colmax[(long long)l * a.R + warp] * s1) * s2;
@@ -219,7 +220,7 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
         if (lane == 0) sel3(ns.exps, l)[warp] = (signed char)E;
     }
     double s = 0.0;
-    const int lim = P ? pld : n;
+    const int lim = P ? (ptk > 0 ? ptk * 16 : pld) : n;
     // one multiply an element when s1 s2 is exact (s2 = 1 unless the exponent is extreme)
     const bool one = s2 == 1.0;
     // NORM_UN loads of a lane issued before any is used: one load in flight per warp leaves the
@@ -245,9 +246,14 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
                 if (P) {
                     uint16_t dg[OZ_S64];
                     oz_digits(v, E, OZ_S64, dg, OZ_W64);
-                    uint16_t* pq = P + (long long)warp * pld + i;
+                    if (ptk > 0) {
 #pragma unroll
-                    for (int t = 0; t < OZ_S64; ++t) pq[t * pst] = dg[t];
+                        for (int t = 0; t < OZ_S64; ++t) P[oz_tiled_index(OZ_S64, ptk, pth, t, warp, i)] = dg[t];
+                    } else {
+                        uint16_t* pq = P + (long long)warp * pld + i;
+#pragma unroll
+                        for (int t = 0; t < OZ_S64; ++t) pq[t * pst] = dg[t];
+                    }
                 }
             }
         }
@@ -275,15 +281,60 @@ __global__ void k_slice_t(SliceTArgs a)
     __syncthreads();
     uint16_t* P = sel3(a.planes, b);
     const long long pst = sel3(a.pstride, b);
+    const int tk = sel3(a.tiles_k, b), th = sel3(a.tile_h, b);
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int x = x0 + i, nu = nu0 + threadIdx.x;
         if (x >= rows || nu >= ld) continue;
         uint16_t dg[OZ_S64];
         oz_digits(tile[threadIdx.x][i], a.E0, OZ_S64, dg, OZ_W64);
-        uint16_t* q = P + (long long)x * ld + nu;
+        if (tk > 0) {
 #pragma unroll
-        for (int t = 0; t < OZ_S64; ++t) q[t * pst] = dg[t];
+            for (int t = 0; t < OZ_S64; ++t) P[oz_tiled_index(OZ_S64, tk, th, t, x, nu)] = dg[t];
+        } else {
+            uint16_t* q = P + (long long)x * ld + nu;
+#pragma unroll
+            for (int t = 0; t < OZ_S64; ++t) q[t * pst] = dg[t];
+        }
     }
+}
+
+// Rademacher signs of the range sketch as one tile-major BF16 plane of 128-row tiles (+-1.0, zero
+// outside; the operand on the TMEM lanes of the sketch product):
+// operand row j < k (sketch column), k-index nu < R; sign(nu, j) = rademacher(seed, mode, nu, j).
+// One thread per 8 consecutive nu of a row (a 16-byte chunk), grid (ceil(KT * 2 * rows / 256), nb).
+__global__ void k_sign_planes(SignPlaneArgs a)
+{
+    const int b = blockIdx.y;
+    const int rows = sel3(a.rows, b), K = sel3(a.K, b), mode = sel3(a.mode, b);
+    const int KT = a.tiles_k, rpad = (rows + 127) / 128 * 128;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;   // chunk index
+    const long long nchunk = (long long)rpad * KT * 2;
+    if (e >= nchunk) return;
+    const int j = (int)(e / (KT * 2)), c = (int)(e % (KT * 2));             // row, 8-wide chunk along nu
+    const int nu0 = c * 8;
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t lohi[2];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int nu = nu0 + 2 * q + hh;
+            lohi[hh] = (j < rows && nu < K) ? (rademacher_bit(a.seed, mode, nu, j) ? 0x3F80u : 0xBF80u) : 0u;
+        }
+        w[q] = lohi[0] | (lohi[1] << 16);
+    }
+    uint16_t* P = sel3(a.planes, b);
+    *reinterpret_cast<uint4*>(P + oz_tiled_index(1, KT, OZ_BM, 0, j, nu0)) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+int launch_sign_planes(const SignPlaneArgs& a, int nb, int rowsmax, cudaStream_t st)
+{
+    if (nb <= 0 || rowsmax <= 0 || a.tiles_k <= 0) return 0;
+    const long long nchunk = (long long)((rowsmax + 127) / 128 * 128) * a.tiles_k * 2;
+    dim3 grid((unsigned)((nchunk + 255) / 256), nb);
+    k_sign_planes<<<grid, 256, 0, st>>>(a);
+    RH_CHECK_LAUNCH();
+    return 0;
 }
 
 int launch_slice_t(const SliceTArgs& a, int nb, int ldmax, int rowsmax, cudaStream_t st)

@@ -231,6 +231,8 @@ struct NormSlice {
     long long pstride[3];
     int ld[3];
     signed char* exps[3];
+    int tiles_k[3];            // > 0: tile-major planes with this many k tiles (see ozgemm.cuh)
+    int tile_h[3];             // their rows per tile
 };
 
 struct HadArgs {
@@ -309,7 +311,20 @@ struct SliceTArgs {
     long long pstride[3];
     int ld[3];
     int E0;
+    int tiles_k[3];            // > 0: tile-major planes with this many k tiles (see ozgemm.cuh)
+    int tile_h[3];             // their rows per tile
 };
+
+// The range sketch's Rademacher signs as a tile-major BF16 plane (rows j = sketch column, k = nu).
+struct SignPlaneArgs {
+    uint16_t* planes[3];
+    int rows[3];               // sketch width k_l
+    int K[3];                  // R
+    int mode[3];
+    int tiles_k;               // k tiles (16 wide) of every plane
+    unsigned long long seed;
+};
+int launch_sign_planes(const SignPlaneArgs& a, int nb, int rowsmax, cudaStream_t st);
 
 struct DeflDims {
     int n[3];

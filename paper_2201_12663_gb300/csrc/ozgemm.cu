@@ -25,7 +25,7 @@ __device__ int g_oz_status = 0;
 
 int oz_take_status(cudaStream_t st, int* out)
 {
-    int v = 0;
+    int v = 0, w = 0;
     if (cudaMemcpyFromSymbolAsync(&v, g_oz_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return RHOSVD_ERR_CUDA;
@@ -34,7 +34,9 @@ int oz_take_status(cudaStream_t st, int* out)
         if (cudaMemcpyToSymbolAsync(g_oz_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return RHOSVD_ERR_CUDA;
     }
-    *out = v;
+    const int rc = oztma_take_status(st, &w);
+    if (rc) return rc;
+    *out = v ? v : w;
     return RHOSVD_OK;
 }
 
@@ -518,7 +520,8 @@ __global__ void __launch_bounds__(256) k_oz_slice_tile(OzSliceArgs a)
 {
     const int b = blockIdx.z;
     const int rows = a.rows[b];
-    const int ld = a.ld[b];
+    const int tk = a.tiles_k[b];
+    const int ld = tk > 0 ? tk * 16 : a.ld[b];          // tile-major: every k of the last tile
     const int i0 = blockIdx.y * OZ_ST_R, k0 = blockIdx.x * OZ_ST_K;
     if (i0 >= rows || k0 >= ld) return;
     const int live = a.drows[b] ? *a.drows[b] : rows;
@@ -562,9 +565,21 @@ __global__ void __launch_bounds__(256) k_oz_slice_tile(OzSliceArgs a)
         const int E = a.exps[b] ? (int)a.exps[b][i] : a.exp0;
         uint16_t d[S];
         oz_digits(T[r][kk], E, S, d, S == OZ_S64 ? OZ_W64 : 8);
-        uint16_t* q = P + (long long)i * ld + k;
+        if (tk > 0) {
+            const int th = a.tile_h[b];
 #pragma unroll
-        for (int s2 = 0; s2 < S; ++s2) q[s2 * ps] = d[s2];
+            for (int s2 = 0; s2 < S; ++s2) P[oz_tiled_index(S, tk, th, s2, i, k)] = d[s2];
+            uint16_t* P2 = a.planes2[b];
+            if (P2) {
+                const int th2 = a.tile_h2[b];
+#pragma unroll
+                for (int s2 = 0; s2 < S; ++s2) P2[oz_tiled_index(S, tk, th2, s2, i, k)] = d[s2];
+            }
+        } else {
+            uint16_t* q = P + (long long)i * ld + k;
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2) q[s2 * ps] = d[s2];
+        }
     }
 }
 
@@ -625,7 +640,7 @@ int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st)
     bool exps = false;
     for (int b = 0; b < nb; ++b) {
         rmax = max(rmax, a.rows[b]);
-        ldmax = max(ldmax, a.ld[b]);
+        ldmax = max(ldmax, a.tiles_k[b] > 0 ? a.tiles_k[b] * 16 : a.ld[b]);
         exps = exps || a.exps[b] != nullptr;
     }
     if (rmax <= 0 || ldmax <= 0) return 0;
@@ -681,6 +696,26 @@ static int run_oz(const OzBatch& b, cudaStream_t st)
 
 int launch_ozgemm(const OzBatch& b, OzKind kind, cudaStream_t st)
 {
+    if (ozgemm_tma_supports(b, kind)) {
+        // the warp-specialised TMA pipeline, then the split-K partials summed in a fixed order
+        int Mh = 0, Nh = 0;
+        for (int i = 0; i < b.nbatch; ++i) {
+            Mh = max(Mh, b.p[i].M);
+            Nh = max(Nh, b.p[i].N);
+        }
+        if (Mh <= 0 || Nh <= 0) return 0;
+        const int rc = launch_ozgemm_tma(b, kind, st);
+        if (rc) return rc;
+        if (b.nsplit > 1) {
+            const long long mn = (long long)Mh * Nh;
+            dim3 rg((unsigned)((mn + 255) / 256 < 4096 ? (mn + 255) / 256 : 4096), b.nbatch);
+            k_oz_reduce<<<rg, 256, 0, st>>>(b);
+            RH_CHECK_LAUNCH();
+        }
+        return 0;
+    }
+    for (int i = 0; i < b.nbatch; ++i)
+        if (b.p[i].A.tiles_k > 0 || b.p[i].B.tiles_k > 0) return RHOSVD_ERR_INVALID_ARG;   // TMA path only
     switch (kind) {
     case OZ_F64_STORE:
         return run_oz<OZ_S64, OZ_S64, 9, OZ_A_PLANES, OZ_B_PLANES, OZ_EPI_STORE, OZ_NT6, 8, OZ_W64>(b, st);

@@ -12,7 +12,9 @@
 // the dropped pairs s + t >= 9 (below 2^(Ea+Eb-54) per term), i.e. about 2^-48 of the
 // scaled sum 2^(Ea+Eb) K.  Each operand row gets its own exponent E (from its largest entry), so
 // the leading digit carries the row's leading bits.  The core contraction uses S = 4, GMAX = 5
-// with the groups s + t >= 4 in one inexact accumulator (about 2^-31).
+// with the groups s + t >= 4 in one inexact accumulator (about 2^-31).  In the TMA-fed form
+// (ozgemm_tma.cu) the FP64-class products keep groups 2..6 exact and accumulate the groups 7, 8, 9
+// (below 2^-35 of the leading group) together in FP32, read back every 128 K: about 2^-48.
 #pragma once
 #include "internal.cuh"
 #include <cuda_bf16.h>
@@ -24,15 +26,32 @@ constexpr int OZ_BK = 32;       // K per pipeline stage
 constexpr int OZ_THREADS = 512; // 16 warps
 constexpr int OZ_NT6 = 64;      // tile width of the FP64-class products (eight 64-column accumulators)
 
-// Operand given as digit planes in global memory: plane p, operand row i, k at
-// base[p * pstride + i * ld + k] (bf16 bit patterns), ld a multiple of 8.
+// Operand given as digit planes in global memory (bf16 bit patterns), in one of two layouts:
+//   row-major (tiles_k == 0): plane p, operand row i, k at base[p * pstride + i * ld + k], ld a
+//     multiple of 8;
+//   tile-major (tiles_k == KT > 0): rows in tiles of tile_h (128 for an operand on the TMEM lanes,
+//     32 for one stacked along N), k in tiles of 16; tile (rt, kt) holds the S planes of its
+//     tile_h x 16 block back to back, each in the 32-byte swizzled K-major order the MMA reads
+//     (oz_tiled_index), so one stage of an operand is one contiguous copy.
 struct OzPlanes {
     const uint16_t* base;
     long long pstride;
     int ld;
     const signed char* exps;   // per operand row exponent E_i (nullable = all `exp0`)
     int exp0;
+    int tiles_k;               // tile-major with this many k tiles per row tile (0: row-major)
+    int tile_h;                // rows per tile of the tile-major layout (128 or 32)
 };
+
+// element (row r, k, plane s) of a tile-major S-plane operand with KT k tiles and H rows per row
+// tile: inside an H x 16 plane tile, row r holds 32 bytes whose two 16-byte halves are swapped on
+// the rows with bit 2 set (the 32-byte swizzle, anchored to 256-byte boundaries)
+__host__ __device__ __forceinline__ long long oz_tiled_index(int S, int KT, int H, int s, int r, int k)
+{
+    const int rr = r % H, kk = k & 15;
+    return ((long long)((r / H) * KT + (k >> 4)) * S + s) * (H * 16) + rr * 16 + (((kk >> 3) ^ ((rr >> 2) & 1)) << 3) +
+           (kk & 7);
+}
 
 // Generated Khatri-Rao operand for the core: row (j + r2 m), k = nu: V2(j, nu) V3(m, nu)
 // (|.| <= 1), each factor given as an FP32 pair (h, l) at V2t[nu + ldt j], V3t[nu + ldt m].
@@ -154,6 +173,13 @@ struct OzSliceArgs {
     signed char* exps[3];
     int S;
     int exp0;
+    // tile-major output (tiles_k[b] > 0): tile_h[b] rows a tile, every k < 16 tiles_k written
+    // (zeros past K); optionally a second copy in another layout (planes2[b], tile_h2[b]: a
+    // product whose two operands are the same matrix needs it on the lanes and stacked)
+    int tiles_k[3];
+    int tile_h[3];
+    uint16_t* planes2[3];
+    int tile_h2[3];
 };
 int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st);
 
@@ -164,6 +190,16 @@ enum OzKind { OZ_F64_STORE = 0, OZ_F64_RESID = 1, OZ_SKETCH = 2, OZ_CORE = 3, OZ
 // (scale 2^0), FP32 accumulation read back every 256 K: a plain BF16 GEMM with FP64 output,
 // used by the learned-proposal network.
 int launch_ozgemm(const OzBatch& b, OzKind kind, cudaStream_t st);
+
+// The TMA-fed, warp-specialised form (ozgemm_tma.cu) of the plane-operand kinds OZ_F64_STORE,
+// OZ_F64_RESID, OZ_SKETCH and OZ_BF16: whether every operand of the batch can be described by a
+// tensor map (16-byte aligned planes, ld a multiple of 8, planes a whole number of rows apart),
+// the GEMM launch itself (launch_ozgemm adds the split-K reduction), and its status word.
+bool ozgemm_tma_supports(const OzBatch& b, OzKind kind);
+int launch_ozgemm_tma(const OzBatch& b, OzKind kind, cudaStream_t st);
+int oztma_take_status(cudaStream_t st, int* out);
+// tiles (residual partials) of one problem's grid in that form
+long long ozgemm_tma_tiles(OzKind kind, int M, int N);
 
 // status of the products launched with OzBatch::err == nullptr: copies the library's status word
 // to *out (RHOSVD_ERR_TIMEOUT after an expired wait, else 0) and clears it; synchronises `st`
