@@ -431,6 +431,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
             const long long ccs = P.ccs < 0 ? (long long)M : P.ccs;
             const long long crs = P.crs < 0 ? (long long)N : P.crs;
             double e2 = 0.0;
+            float e2f = 0.f;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const int ccol = j0 + hcol * NC + c;                  // col operand row
@@ -440,16 +441,20 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                 const int eb = SIGN ? W : (P.B.exps ? (int)P.B.exps[col] : P.B.exp0);
                 // x = 2^(E - W) sum_s plane_s: a product carries 2^(ea + eb - 2W), built from its bits
                 const double sc = __hiloint2double((ea + eb - 2 * W + 1023) << 20, 0);
-                const double v = ((double)hi[c] + (double)lo[c]) * sc;
                 if (EPI == OZ_EPI_STORE) {
-                    Cout[(long long)row * crs + (long long)col * ccs] = v;
+                    Cout[(long long)row * crs + (long long)col * ccs] = ((double)hi[c] + (double)lo[c]) * sc;
                 } else {
-                    const double d = P.ref[(long long)row * P.ref_rs + (long long)col * P.ref_cs] - v;
-                    e2 = fma(d, d, e2);
+                    // ref - (hi + lo) sc: the cancelling part ref - hi sc in one FP64 fma (exact
+                    // scaling, one rounding), the small remainder and its square in FP32 (the
+                    // residual's entries are far below ref's, so FP32 keeps them to 2^-24 of
+                    // themselves; a scale below FP32's range only drops a term below 2^-126)
+                    const double t = fma(-(double)hi[c], sc, P.ref[(long long)row * P.ref_rs + (long long)col * P.ref_cs]);
+                    const float d = __double2float_rn(t) - lo[c] * __double2float_rn(sc);
+                    e2f = fmaf(d, d, e2f);
                 }
             }
             if (EPI == OZ_EPI_RESID) {
-                e2 = warp_sum(e2);
+                e2 = warp_sum((double)e2f);
                 if (lane == 0) red[e] = e2;
                 asm volatile("bar.sync 1, %0;" ::"r"(T_NEPI * 32) : "memory");
                 if (e == 0 && lane == 0) {
