@@ -230,6 +230,7 @@ struct Plan {
     int mixed;
     int ldR, ldn, ldk;            // plane row lengths (multiples of 8) for K = R, n, k
     int tkR;                      // k tiles of the tile-major U~ planes with K = R
+    int tkC;                      // k tiles of the core's diag(xi') V1 planes
     long long sSg;                // per-mode size of the sketch's sign plane (elements)
     size_t o_sgn;
     size_t o_pU1, o_pU2, o_pP1, o_pP2, o_eU2, o_eP1, o_eP2, o_Vt;
@@ -369,6 +370,11 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
         for (long long c : cand) pm = c > pm ? c : pm;
         p->sP1 = (long long)OZ_S64 * pm;
         p->sP2 = (long long)OZ_S64 * pm;
+        // the core's diag(xi') V1 planes: 4 planes, 160-row tiles, k tiles of 16
+        p->tkC = (R + 15) / 16;
+        const long long rc = p->rmax < p->KW ? p->rmax : p->KW;
+        const long long score = 4LL * ((rc + OZ_CORE_NT - 1) / OZ_CORE_NT * OZ_CORE_NT) * (p->tkC * 16LL);
+        if (score > p->sP2) p->sP2 = score;
         p->o_pU1 = take(sizeof(uint16_t) * 3 * (size_t)p->sU1);
         p->o_pU2 = take(sizeof(uint16_t) * 3 * (size_t)p->sU2);
         p->o_pP1 = take(sizeof(uint16_t) * 3 * (size_t)p->sP1);
@@ -1569,13 +1575,13 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         g.ldv = KW;
         gc.p[0] = g;
         if (mixed) {
-            // V^(2), V^(3) with nu-contiguous rows for the generated Khatri-Rao operand, and the
-            // digit planes of diag(xi') V^(1) (rows i, k = nu, per-row exponents)
+            // V^(2), V^(3) as FP32 pairs (same layout as V) for the generated Khatri-Rao operand,
+            // and the digit planes of diag(xi') V^(1) (rows i, k = nu, per-row exponents)
             const long long VTS = (long long)R * KW;
-            STAGE("core_prep", launch_transpose_v(Vw, VS, KW, (float2*)Vt, VTS, R, R, S->r, 1, 2, st));
+            STAGE("core_prep", launch_split_v(Vw, VS, KW, (float2*)Vt, VTS, KW, R, S->r, 1, 2, st));
             // per-row exponents of V^(2), V^(3) (modes 1, 2 of eP1): the Khatri-Rao row (j, m)
             // is cut with e2[j] + e3[m]
-            STAGE("core_prep", launch_row_exps((const float2*)Vt, VTS, R, S->r, 1, 2, R, eP1, EX, st));
+            STAGE("core_prep", launch_row_exps((const float2*)Vt, VTS, KW, S->r, 1, 2, R, eP1, EX, st));
             const int rcap = rmax < KW ? rmax : KW;   // a rank never exceeds the basis width
             OzSliceArgs s1;
             memset(&s1, 0, sizeof(s1));
@@ -1588,21 +1594,21 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             s1.K[0] = R;
             s1.kscale[0] = xin;
             s1.planes[0] = pP2;
-            s1.pstride[0] = (long long)rcap * p.ldR;
-            s1.ld[0] = p.ldR;
             s1.exps[0] = eP2;
+            s1.tiles_k[0] = p.tkC;
+            s1.tile_h[0] = OZ_CORE_NT;
             STAGE("core_prep", launch_oz_slice(s1, 1, st));
             OzBatch ob;
             memset(&ob, 0, sizeof(ob));
             ob.nbatch = 1;
             ob.err = ozerr;
             OzProblem& q = ob.p[0];
-            q.kr = OzKR{(const float2*)(Vt + VTS), (const float2*)(Vt + 2 * VTS), R, eP1 + EX, eP1 + 2 * EX};
+            q.kr = OzKR{(const float2*)(Vt + VTS), (const float2*)(Vt + 2 * VTS), KW, eP1 + EX, eP1 + 2 * EX};
             q.M = rcap * rcap;
             q.M_from_r2r3 = 1;
             q.dNa = &S->r[1];
             q.dNb = &S->r[2];
-            q.B = OzPlanes{pP2, (long long)rcap * p.ldR, p.ldR, eP2, 0};
+            q.B = OzPlanes{pP2, 0, 0, eP2, 0, p.tkC, OZ_CORE_NT};
             q.N = rcap;
             q.dN = &S->r[0];
             q.K = R;

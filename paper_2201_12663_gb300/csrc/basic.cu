@@ -423,12 +423,12 @@ __global__ void k_cpsum(SumArgs a)
 }
 
 
-// dst_l(nu, j) = src_l(j, nu): V^(l) (rows j < r_l, ld lds) to nu-contiguous rows (ld ldd = R).
-// dst_l(j, nu) = src_l(nu, j) for j < r_l, nu < R, as a float pair (h, l) with h = fl32(v) and
-// l = fl32(v - h): the Khatri-Rao operand of the tensor-core core contraction forms its products
-// from these on the FP32 pipe (h h' exact by fma; about 2^-46 relative in all).
-__global__ void k_transpose_v(const double* src, long long sstride, int lds, float2* dst, long long dstride, int ldd,
-                              int R, const int* dr, int mode0)
+// V^(l)(j, nu) (j < r_l, nu < R, at src_l[nu lds + j]) split into a float pair (h, l) with
+// h = fl32(v) and l = fl32(v - h), at dst_l[nu ldd + j] (j contiguous, like the source): the
+// Khatri-Rao operand of the tensor-core core contraction forms its products from these on the
+// FP32 pipe (h h' exact by fma; about 2^-46 relative in all).
+__global__ void k_split_v(const double* src, long long sstride, int lds, float2* dst, long long dstride, int ldd,
+                          int R, const int* dr, int mode0)
 {
     const int l = mode0 + blockIdx.y;
     const int r = dr[l];
@@ -437,47 +437,66 @@ __global__ void k_transpose_v(const double* src, long long sstride, int lds, flo
     const long long total = (long long)R * r;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int nu = (int)(e % R), j = (int)(e / R);
+        const int j = (int)(e % r), nu = (int)(e / r);
         const double v = S[(long long)nu * lds + j];
         const float h = __double2float_rn(v);
-        D[(long long)j * ldd + nu] = make_float2(h, __double2float_rn(v - (double)h));
+        D[(long long)nu * ldd + j] = make_float2(h, __double2float_rn(v - (double)h));
     }
 }
 
-int launch_transpose_v(const double* src, long long sstride, int lds, float2* dst, long long dstride, int ldd, int R,
-                       const int* dr, int mode0, int nmodes, cudaStream_t st)
+int launch_split_v(const double* src, long long sstride, int lds, float2* dst, long long dstride, int ldd, int R,
+                   const int* dr, int mode0, int nmodes, cudaStream_t st)
 {
     dim3 grid(512, nmodes);
-    k_transpose_v<<<grid, 256, 0, st>>>(src, sstride, lds, dst, dstride, ldd, R, dr, mode0);
+    k_split_v<<<grid, 256, 0, st>>>(src, sstride, lds, dst, dstride, ldd, R, dr, mode0);
     RH_CHECK_LAUNCH();
     return 0;
 }
 
 // Per-row exponents of the split factors: out_l[j] = E with max_nu |V_l(j, nu)| < 2^E for the
-// pair (h, l) at Vt_l[j ldt + nu] (|v| <= |h| (1 + 2^-23), so E comes from max |h| (1 + 2^-20)),
-// clamped to [-45, 1].  Warp per row j < r_l.  grid (ceil(KMAX / 8), nmodes), block 256.
-__global__ void k_row_exps(const float2* Vt, long long vstride, int ldt, const int* dr, int mode0, int R,
-                           signed char* out, long long ostride)
+// pair (h, l) at Vp_l[nu ldp + j] (|v| <= |h| (1 + 2^-23), so E comes from max |h| (1 + 2^-20)),
+// clamped to [-45, 1].  A block covers 32 rows j (the lanes, reading consecutive pairs) with its
+// 32 warps striding over nu, eight loads in flight a thread.  grid (ceil(KMAX / 32), nmodes),
+// block 1024.
+__global__ void __launch_bounds__(1024) k_row_exps(const float2* Vp, long long vstride, int ldp, const int* dr,
+                                                   int mode0, int R, signed char* out, long long ostride)
 {
     const int l = mode0 + blockIdx.y;
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (j >= dr[l]) return;
-    const float2* v = Vt + l * vstride + (long long)j * ldt;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;
+    const int r = dr[l];
+    __shared__ float part[32][33];
+    if (blockIdx.x * 32 >= r) return;
+    const float2* v = Vp + l * vstride + j;
     float mx = 0.f;
-    for (int nu = lane; nu < R; nu += 32) mx = fmaxf(mx, fabsf(v[nu].x));
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int E = -45;
-    if (mx > 0.f) {
-        frexpf(mx * (1.0f + 0x1p-20f), &E);
-        E = E < -45 ? -45 : (E > 1 ? 1 : E);
+    if (j < r) {
+        int nu = w;
+        for (; nu + 7 * 32 < R; nu += 8 * 32) {
+            float h[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) h[q] = v[(long long)(nu + q * 32) * ldp].x;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) mx = fmaxf(mx, fabsf(h[q]));
+        }
+        for (; nu < R; nu += 32) mx = fmaxf(mx, fabsf(v[(long long)nu * ldp].x));
     }
-    if (lane == 0) out[l * ostride + j] = (signed char)E;
+    part[w][lane] = mx;
+    __syncthreads();
+    if (w == 0 && j < r) {
+        for (int q = 1; q < 32; ++q) mx = fmaxf(mx, part[q][lane]);
+        int E = -45;
+        if (mx > 0.f) {
+            frexpf(mx * (1.0f + 0x1p-20f), &E);
+            E = E < -45 ? -45 : (E > 1 ? 1 : E);
+        }
+        out[l * ostride + j] = (signed char)E;
+    }
 }
 
-int launch_row_exps(const float2* Vt, long long vstride, int ldt, const int* dr, int mode0, int nmodes, int R,
+int launch_row_exps(const float2* Vp, long long vstride, int ldp, const int* dr, int mode0, int nmodes, int R,
                     signed char* out, long long ostride, cudaStream_t st)
 {
-    k_row_exps<<<dim3((KMAX + 7) / 8, nmodes), 256, 0, st>>>(Vt, vstride, ldt, dr, mode0, R, out, ostride);
+    k_row_exps<<<dim3((KMAX + 31) / 32, nmodes), 1024, 0, st>>>(Vp, vstride, ldp, dr, mode0, R, out, ostride);
     RH_CHECK_LAUNCH();
     return 0;
 }

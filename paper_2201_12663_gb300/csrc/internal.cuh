@@ -340,10 +340,10 @@ int launch_terms(const NormArgs& na, const double* xi, double* keepf, double* xi
                  cudaStream_t st);
 int launch_identity(double* Q, int n, int ld, cudaStream_t st);
 int launch_slice_t(const SliceTArgs& a, int nb, int ldmax, int rowsmax, cudaStream_t st);
-int launch_row_exps(const float2* Vt, long long vstride, int ldt, const int* dr, int mode0, int nmodes, int R,
+int launch_row_exps(const float2* Vp, long long vstride, int ldp, const int* dr, int mode0, int nmodes, int R,
                     signed char* out, long long ostride, cudaStream_t st);
-int launch_transpose_v(const double* src, long long sstride, int lds, float2* dst, long long dstride, int ldd, int R,
-                       const int* dr, int mode0, int nmodes, cudaStream_t st);
+int launch_split_v(const double* src, long long sstride, int lds, float2* dst, long long dstride, int ldd, int R,
+                   const int* dr, int mode0, int nmodes, cudaStream_t st);
 int launch_init_state(DevState* s, int k0, int k1, int k2, int m0, int m1, int m2, int kdef, cudaStream_t st);
 int launch_hadamard(const HadArgs& a, cudaStream_t st);
 int launch_cpsum(const SumArgs& a, cudaStream_t st);

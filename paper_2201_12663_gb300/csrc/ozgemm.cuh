@@ -1,20 +1,19 @@
-// ozgemm.cuh -- FP64-class GEMM on the tcgen05 tensor cores by exact 8-bit slicing (used by
-// the mixed-precision form of the RHOSVD path).
+// ozgemm.cuh -- FP64-class GEMM on the tcgen05 tensor cores by exact digit slicing (used by the
+// mixed-precision form of the RHOSVD path).
 //
-// A real value x with |x| < 2^E is written as x = 2^E * sum_{s=1..S} d_s 2^(-8s), the d_s in
-// [0, 256] the base-256 digits of |x| 2^(8S-E) (the last one rounded) carrying the sign of x.
-// Every digit is exact in BF16, every product of two digits exact in FP32 (below 2^16), and a
-// sum of such products stays exact while it fits 24 bits.  The product of two operands is
-// x y = 2^(Ea+Eb) sum_{s,t} d_s d'_t 2^(-8(s+t)); the kernel forms the groups g = s + t up to
-// GMAX, each in its own TMEM accumulator, and reads every group back into double-float
-// registers before its FP32 sum could round.  For FP64 operands S = 6 and GMAX = 8: all seven
-// groups are exact, the error is the rounding of the last digits (|x - x^| <= 2^(E-49)) and
-// the dropped pairs s + t >= 9 (below 2^(Ea+Eb-54) per term), i.e. about 2^-48 of the
-// scaled sum 2^(Ea+Eb) K.  Each operand row gets its own exponent E (from its largest entry), so
-// the leading digit carries the row's leading bits.  The core contraction uses S = 4, GMAX = 5
-// with the groups s + t >= 4 in one inexact accumulator (about 2^-31).  In the TMA-fed form
-// (ozgemm_tma.cu) the FP64-class products keep groups 2..6 exact and accumulate the groups 7, 8, 9
-// (below 2^-35 of the leading group) together in FP32, read back every 128 K: about 2^-48.
+// A real value x with |x| < 2^E is written as x = 2^(E - W) sum_{s=1..S} d_s 2^(-W(s-1)), the d_s
+// base-2^W digits of |x| 2^(WS - E) (the last one rounded) carrying the sign of x.  Every digit is
+// exact in BF16, every product of two digits exact in FP32 (below 2^(2W)), and a sum of such
+// products stays exact while it fits 24 bits.  The product of two operands is
+// x y = 2^(Ea + Eb - 2W) sum_{s,t} d_s d'_t 2^(-W(s + t - 2)); the kernels form the groups
+// g = s + t up to GMAX in TMEM accumulators and read them back into double-float registers before
+// an exact group's FP32 sum could round.  Each operand row gets its own exponent E (from its
+// largest entry), so the leading digit carries the row's leading bits.
+//   FP64-class products: S = 7 digits of W = 7 bits, GMAX = 9, every group in its own accumulator,
+//     exact over its block of 128 K.  The error is the digits' rounding (|x - x^| <= 2^(E - 50))
+//     and the dropped pairs s + t >= 10: about 2^-48 of the scaled sum 2^(Ea + Eb) K.
+//   Khatri-Rao core: S = 4 digits of W = 8 bits, GMAX = 5, the groups 2 and 3 exact, the groups
+//     4 and 5 together in one FP32 accumulator: about 2^-31.
 #pragma once
 #include "internal.cuh"
 #include <cuda_bf16.h>
@@ -22,9 +21,8 @@
 namespace rh {
 
 constexpr int OZ_BM = 128;      // rows of a CTA tile (TMEM lanes)
-constexpr int OZ_BK = 32;       // K per pipeline stage
-constexpr int OZ_THREADS = 512; // 16 warps
-constexpr int OZ_NT6 = 64;      // tile width of the FP64-class products (eight 64-column accumulators)
+constexpr int OZ_BK = 32;       // K granule of a split-K range
+constexpr int OZ_NT6 = 64;      // column width that the split-count heuristics count tiles in
 
 // Operand given as digit planes in global memory (bf16 bit patterns), in one of two layouts:
 //   row-major (tiles_k == 0): plane p, operand row i, k at base[p * pstride + i * ld + k], ld a
@@ -54,11 +52,12 @@ __host__ __device__ __forceinline__ long long oz_tiled_index(int S, int KT, int 
 }
 
 // Generated Khatri-Rao operand for the core: row (j + r2 m), k = nu: V2(j, nu) V3(m, nu)
-// (|.| <= 1), each factor given as an FP32 pair (h, l) at V2t[nu + ldt j], V3t[nu + ldt m].
+// (|.| <= 1), each factor given as an FP32 pair (h, l) at V2p[nu ldp + j], V3p[nu ldp + m]
+// (consecutive rows j adjacent, so the lanes of a warp, on consecutive rows, read together).
 struct OzKR {
-    const float2* V2t;
-    const float2* V3t;
-    int ldt;
+    const float2* V2p;
+    const float2* V3p;
+    int ldp;
     // per-row exponents (|V2(j, .)| < 2^e2[j], |V3(m, .)| < 2^e3[m]): row (j, m) of the operand
     // is cut with E = e2[j] + e3[m], so small rows keep their own 32 bits (null: E = 0)
     const signed char* e2;
@@ -105,14 +104,11 @@ struct OzBatch {
     int* err;                    // status word: RHOSVD_ERR_TIMEOUT if a bounded wait gave up
 };
 
-enum OzASrc { OZ_A_PLANES = 0, OZ_A_KR = 1 };
-enum OzBSrc { OZ_B_PLANES = 0, OZ_B_SIGN = 1 };
 enum OzEpi { OZ_EPI_STORE = 0, OZ_EPI_RESID = 1 };
 
 // FP64-class operands are cut into OZ_S64 digits of OZ_W64 bits (49 bits in all); the
-// Khatri-Rao core and the plain BF16 product keep 8-bit digits.  A product of two W-bit digits
-// is below 2^(2W): with W = 7 a group of up to 7 digit pairs stays exact in FP32 for 4 stages of
-// 32 (np 2^14 128 < 2^24), so the accumulators are read back every 4 stages instead of every one.
+// Khatri-Rao core keeps 8-bit digits.  A product of two W-bit digits is below 2^(2W): with W = 7 a
+// group of up to 7 digit pairs stays exact in FP32 over 128 K (np 2^14 128 < 2^24).
 constexpr int OZ_S64 = 7, OZ_W64 = 7;
 
 // S digit planes (bf16 bit patterns) of the signed integer F = +-round(|x| 2^(W S - E)).
@@ -153,6 +149,34 @@ __device__ __forceinline__ void oz_digits(double x, int E, int S, uint16_t* out,
     }
     const long long Fs = (long long)F;
     oz_digits_int((bits >> 63) ? -Fs : Fs, S, out, W);
+}
+
+// The Khatri-Rao core's digits of one FP64 value for exponent E (|x| < 2^E): the signed integer
+// F = +-round(|x| 2^(32 - E)) cut into 4 balanced base-256 digits (each the rounded quotient of the
+// remainder, so |d1| <= 256 and |d2|, |d3|, |d4| <= 128), plane s holding d_s 2^(-8(s-1)).  The
+// smaller digits keep the core's exact groups exact over 256 K instead of 128 K.
+__device__ __forceinline__ void oz_digits_bal(double x, int E, uint16_t* out)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+    int e;
+    if (ef == 0) { e = -1022; } else { m |= 0x10000000000000ull; e = ef - 1023; }
+    const int sh = 52 - (e + 32 - E);
+    unsigned long long F;
+    if (m == 0 || sh >= 64) F = 0;
+    else if (sh <= 0) F = 1ull << 32;          // |x| >= 2^E does not occur for a valid exponent
+    else F = (m + (1ull << (sh - 1))) >> sh;
+    long long t = (bits >> 63) ? -(long long)F : (long long)F;
+#pragma unroll
+    for (int s = 1; s <= 4; ++s) {
+        const int b = 8 * (4 - s);
+        // round half up: floor((t + 2^(b-1)) / 2^b) (an arithmetic shift), the last digit the rest
+        const long long d = s < 4 ? (t + (1LL << (b - 1))) >> b : t;
+        t -= d << b;
+        const float v = (float)d * __int_as_float((127 - 8 * (s - 1)) << 23);
+        out[s - 1] = (uint16_t)(__float_as_uint(v) >> 16);
+    }
 }
 
 // Digit planes of an operand: operand row i < rows, k < K reads X[i * rs + k * cs] (times
@@ -200,6 +224,11 @@ int launch_ozgemm_tma(const OzBatch& b, OzKind kind, cudaStream_t st);
 int oztma_take_status(cudaStream_t st, int* out);
 // tiles (residual partials) of one problem's grid in that form
 long long ozgemm_tma_tiles(OzKind kind, int M, int N);
+// The Khatri-Rao core (OZ_CORE) in the same form: B (diag(xi') V1 digit planes, S = 4) tile-major
+// with 160-row tiles, A generated from OzProblem::kr in the kernel.
+constexpr int OZ_CORE_NT = 160;
+bool ozcore_tma_supports(const OzBatch& b);
+int launch_ozcore_tma(const OzBatch& b, cudaStream_t st);
 
 // status of the products launched with OzBatch::err == nullptr: copies the library's status word
 // to *out (RHOSVD_ERR_TIMEOUT after an expired wait, else 0) and clears it; synchronises `st`

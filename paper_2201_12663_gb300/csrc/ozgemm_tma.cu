@@ -15,19 +15,21 @@
 // Tiles are K-major with the 32-byte swizzle (8-row x 32-byte atoms, 256 B between 8-row groups),
 // the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_32B and the MMA descriptors read.
 //
-// Accumulators (Plan<KIND>): each digit group g = s + t, or a few of them together, has an FP32
-// accumulator in TMEM that is read back into double-float registers every cad stages, before its
-// sum could round (or, for the merged small F64 groups, while its rounding stays near 2^-48 of
-// the product's scale).  The readbacks of different accumulators fall on different stages, and
-// TMEM holds spare slots: an accumulator that is being read back moves to a free slot for the next
-// stage, so the MMA issuer never waits for the epilogue unless both are behind by a whole FIFO of
-// spare slots.  Both sides run the same deterministic slot allocator (SlotSim).
+// Accumulators (Plan<KIND>): the MMAs of one lane plane s against the stacked col planes t write
+// the groups g = s + t into consecutive column blocks, so a stage costs one MMA per lane plane.
+// Two buffers of every group's columns alternate by blocks of RBK stages: while the MMAs fill one,
+// the epilogue reads the other back into double-float registers.  Every group stays exact in FP32
+// over its block (Plan<KIND>::ok checks np 2^(2W) 16 RBK <= 2^24).
+//
+// The Khatri-Rao core (k_ozcore, below) has its own warp roles: its A operand is formed in shared
+// memory by the worker warps instead of being copied.
 //
 // Every mbarrier wait is bounded.  On expiry the CTA stops producing, issuing and reading back,
 // waits (bounded again) for its own copies and MMAs in flight, records RHOSVD_ERR_TIMEOUT in the
 // batch's status word (or the library's, see oz_take_status), frees TMEM and returns.
 #include "ozgemm.cuh"
 #include <cuda.h>
+#include <climits>
 #include <mutex>
 
 namespace rh {
@@ -223,8 +225,47 @@ __device__ __forceinline__ int dimv(const int* d, int h) { return d ? *d : h; }
 
 }  // namespace
 
+// One work item of a persistent CTA: problem pb, K split, lane tile tx, col tile ty; decoded the
+// same way by every warp.  An item with no work (a split beyond the device's split count, or a
+// tile outside the problem's device-side extent) is skipped by all of them.
+struct TmaItem {
+    int pb, split, tx, ty;
+    int M, N, kbase, nkt;
+    bool live;
+};
+
+template <int NT, int BK>
+__device__ __forceinline__ TmaItem tma_item(const OzBatch& batch, int w, int ntx, int nty, int nsplit_h, bool sign)
+{
+    TmaItem it;
+    it.tx = w % ntx;
+    w /= ntx;
+    it.ty = w % nty;
+    w /= nty;
+    it.split = w % nsplit_h;
+    it.pb = w / nsplit_h;
+    const OzProblem& P = batch.p[it.pb];
+    const int nsplit = P.dsplit ? max(1, min(*P.dsplit, nsplit_h)) : nsplit_h;
+    it.M = dimv(P.dM, P.M);
+    it.N = dimv(P.dN, P.N);
+    const int Kall = dimv(P.dK, P.K);
+    // this item's K range: whole 32-wide blocks, the last split takes the rest
+    const int kspan = ((Kall + nsplit - 1) / nsplit + BK - 1) / BK * BK;
+    it.kbase = min(Kall, it.split * kspan);
+    const int K = min(Kall, it.kbase + kspan) - it.kbase;
+    it.nkt = (K + TK - 1) / TK;
+    const int laneExt = sign ? it.N : it.M, colExt = sign ? it.M : it.N;
+    it.live = it.split < nsplit && it.tx * OZ_BM < laneExt && it.ty * NT < colExt;
+    return it;
+}
+
+// A persistent CTA: grid.x CTAs walk the items w = blockIdx.x, blockIdx.x + gridDim.x, ... (ntx lane
+// tiles x nty col tiles x splits x problems).  The stage ring, the block counter and the
+// accumulator buffers run on across items, so one item's readback and store overlap the next
+// item's copies and MMAs.
 template <int KIND, int EPI, int STAGES>
-__global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __grid_constant__ OzMaps maps)
+__global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __grid_constant__ OzMaps maps, int ntx,
+                                                        int nty)
 {
     using PL = Plan<KIND>;
     constexpr int SL = PL::SL, SC = PL::SC, NT = PL::NT, W = PL::W, NG = PL::NG, NCOL = PL::NCOL, RBK = PL::RBK;
@@ -241,40 +282,14 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
     static_assert(STAGES * STAGE + 2048 <= T_SMEM_MAX, "shared memory");
 
     const int nsplit_h = batch.nsplit > 1 ? batch.nsplit : 1;
-    const int split = blockIdx.z % nsplit_h;
-    const int pb = blockIdx.z / nsplit_h;
-    const OzProblem& P = batch.p[pb];
-    const int nsplit = P.dsplit ? max(1, min(*P.dsplit, nsplit_h)) : nsplit_h;
-    if (split >= nsplit) return;
-    const int M = dimv(P.dM, P.M);
-    const int N = dimv(P.dN, P.N);
-    const int Kall = dimv(P.dK, P.K);
-    // this CTA's K range [kbase, kbase + K): whole 32-wide blocks, the last split takes the rest
-    const int kspan = ((Kall + nsplit - 1) / nsplit + OZ_BK - 1) / OZ_BK * OZ_BK;
-    const int kbase = min(Kall, split * kspan);
-    const int K = min(Kall, kbase + kspan) - kbase;
-    double* const Cout = nsplit > 1 ? P.Cpart + split * P.split_stride : P.C;
-    // lane tile (128 rows) and col tile (NT rows); the sketch puts its sign operand (problem
-    // columns) on the lanes and the planes of U~ (problem rows) on the stacked side
-    const int i0 = blockIdx.x * OZ_BM, j0 = blockIdx.y * NT;
-    const int laneExt = SIGN ? N : M, colExt = SIGN ? M : N;
+    const int nitems = ntx * nty * nsplit_h * batch.nbatch;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (i0 >= laneExt || j0 >= colExt) {
-        if (EPI == OZ_EPI_RESID && tid == 0) P.rpart[blockIdx.x + gridDim.x * blockIdx.y] = 0.0;
-        return;
-    }
-    const int nkt = (K + TK - 1) / TK;
-    const int nblk = (nkt + RBK - 1) / RBK;
-    const OzPlanes& LP = SIGN ? P.B : P.A;               // lane operand planes (the signs for SIGN)
-    const OzPlanes& CP = SIGN ? P.A : P.B;               // col operand planes
-    const int rowsL = LP.pstride > 0 ? (int)(LP.pstride / LP.ld) : 0;
-    const int rowsC = CP.pstride > 0 ? (int)(CP.pstride / CP.ld) : 0;
 
     extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char* stages = (unsigned char*)(((uintptr_t)tsm + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], buf_full[2], buf_free[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_efail;
     __shared__ double red[T_NEPI];
 
     // the zero planes of every stage (never written by the copies)
@@ -300,6 +315,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
+        s_efail = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -310,79 +326,98 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
     if (warp == 0) {
         // ---------------------------------------------------------------- producer
         // lane 0 waits and decides; the decision is broadcast so that the warp stays converged
-        int issued = 0;                     // stages whose loads were issued
-        for (int kt = 0; kt < nkt; ++kt) {
-            const int s = kt % STAGES;
-            int go = 0;
-            if (lane == 0) {
-                go = *fail ? 0 : 1;
-                if (go && kt >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((kt / STAGES) - 1) & 1))) {
-                    *fail = 1;
-                    go = 0;
+        int gs = 0;                         // stages issued so far (all items)
+        for (int w = blockIdx.x; w < nitems && !*fail; w += gridDim.x) {
+            const TmaItem it = tma_item<NT, OZ_BK>(batch, w, ntx, nty, nsplit_h, SIGN);
+            if (!it.live) continue;
+            const OzProblem& P = batch.p[it.pb];
+            const OzPlanes& LP = SIGN ? P.B : P.A;
+            const OzPlanes& CP = SIGN ? P.A : P.B;
+            const int rowsL = LP.pstride > 0 ? (int)(LP.pstride / LP.ld) : 0;
+            const int rowsC = CP.pstride > 0 ? (int)(CP.pstride / CP.ld) : 0;
+            const int i0 = it.tx * OZ_BM, j0 = it.ty * NT;
+            bool stop = false;
+            for (int kt = 0; kt < it.nkt; ++kt, ++gs) {
+                const int s = gs % STAGES;
+                int go = 0;
+                if (lane == 0) {
+                    go = *fail ? 0 : 1;
+                    if (go && gs >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((gs / STAGES) - 1) & 1))) {
+                        *fail = 1;
+                        go = 0;
+                    }
                 }
-            }
-            if (!__shfl_sync(0xffffffffu, go, 0)) break;
-            unsigned char* sL = stages + s * STAGE;
-            unsigned char* sC = sL + L_BYTES;
-            const int k0 = kbase + kt * TK;
-            if (lane == 0) {
-                mbar_expect_tx(&full[s], TX_BYTES);
-                if (LP.tiles_k > 0) {
-                    // tile-major lane operand: the stage's SL plane tiles are one contiguous block
-                    const uint16_t* src = LP.base + ((long long)(i0 >> 7) * LP.tiles_k + (k0 >> 4)) * SL * 2048;
-                    bulk_g2s(sL, src, L_BYTES, &full[s]);
-                } else {
+                if (!__shfl_sync(0xffffffffu, go, 0)) {
+                    stop = true;
+                    break;
+                }
+                unsigned char* sL = stages + s * STAGE;
+                unsigned char* sC = sL + L_BYTES;
+                const int k0 = it.kbase + kt * TK;
+                if (lane == 0) {
+                    mbar_expect_tx(&full[s], TX_BYTES);
+                    if (LP.tiles_k > 0) {
+                        // tile-major lane operand: the stage's SL plane tiles are one contiguous block
+                        const uint16_t* src = LP.base + ((long long)it.tx * LP.tiles_k + (k0 >> 4)) * SL * 2048;
+                        bulk_g2s(sL, src, L_BYTES, &full[s]);
+                    } else {
 #pragma unroll
-                    for (int p = 0; p < SL; ++p) tma_2d(sL + p * L_PLANE, &maps.a[pb], k0, p * rowsL + i0, &full[s]);
-                }
-                if (CP.tiles_k > 0) {
-                    // tile-major col operand (NT-row tiles): the stage's SC plane tiles, one block
-                    const uint16_t* src = CP.base + ((long long)(j0 / NT) * CP.tiles_k + (k0 >> 4)) * SC * (NT * 16);
-                    bulk_g2s(sC, src, SC * C_PLANE, &full[s]);
-                } else {
+                        for (int p = 0; p < SL; ++p) tma_2d(sL + p * L_PLANE, &maps.a[it.pb], k0, p * rowsL + i0, &full[s]);
+                    }
+                    if (CP.tiles_k > 0) {
+                        // tile-major col operand (NT-row tiles): the stage's SC plane tiles, one block
+                        const uint16_t* src = CP.base + ((long long)it.ty * CP.tiles_k + (k0 >> 4)) * SC * (NT * 16);
+                        bulk_g2s(sC, src, SC * C_PLANE, &full[s]);
+                    } else {
 #pragma unroll
-                    for (int p = 0; p < SC; ++p) tma_2d(sC + p * C_PLANE, &maps.b[pb], k0, p * rowsC + j0, &full[s]);
+                        for (int p = 0; p < SC; ++p) tma_2d(sC + p * C_PLANE, &maps.b[it.pb], k0, p * rowsC + j0, &full[s]);
+                    }
                 }
+                __syncwarp();
             }
-            __syncwarp();
-            issued = kt + 1;
+            if (stop) break;
         }
         if (*fail && lane == 0) {
             // copies in flight land before the CTA's shared memory goes away
-            for (int kt = max(0, issued - STAGES); kt < issued; ++kt)
-                mbar_wait(&full[kt % STAGES], (uint32_t)((kt / STAGES) & 1));
+            for (int g = max(0, gs - STAGES); g < gs; ++g) mbar_wait(&full[g % STAGES], (uint32_t)((g / STAGES) & 1));
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            int last = -1;
-            for (int kt = 0; kt < nkt; ++kt) {
-                if (*fail) break;
-                const int s = kt % STAGES;
-                const int blk = kt / RBK;
-                const bool first = kt % RBK == 0;
-                const uint32_t buf = tmem + (uint32_t)((blk & 1) * NCOL);
-                // the block's buffer was read back by the epilogue two blocks ago
-                if (first && blk >= 2 && !mbar_wait(&buf_free[blk & 1], (uint32_t)(((blk >> 1) - 1) & 1))) {
-                    *fail = 1;
-                    break;
-                }
-                if (!mbar_wait(&full[s], (uint32_t)((kt / STAGES) & 1))) {
-                    *fail = 1;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t lBase = su32(stages + s * STAGE);
-                const uint64_t dL0 = desc_sw32(lBase), dC0 = desc_sw32(lBase + L_BYTES);
+            int gs = 0, gb = 0, last = -1;     // stages and blocks issued so far (all items)
+            for (int w = blockIdx.x; w < nitems && !*fail; w += gridDim.x) {
+                const TmaItem it = tma_item<NT, OZ_BK>(batch, w, ntx, nty, nsplit_h, SIGN);
+                if (!it.live) continue;
+                for (int kt = 0; kt < it.nkt; ++kt, ++gs) {
+                    if (*fail) break;
+                    const int s = gs % STAGES;
+                    const bool first = kt % RBK == 0;
+                    const uint32_t buf = tmem + (uint32_t)((gb & 1) * NCOL);
+                    // the block's buffer was read back by the epilogue two blocks ago
+                    if (first && gb >= 2 && !mbar_wait(&buf_free[gb & 1], (uint32_t)(((gb >> 1) - 1) & 1))) {
+                        *fail = 1;
+                        break;
+                    }
+                    if (!mbar_wait(&full[s], (uint32_t)((gs / STAGES) & 1))) {
+                        *fail = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t lBase = su32(stages + s * STAGE);
+                    const uint64_t dL0 = desc_sw32(lBase), dC0 = desc_sw32(lBase + L_BYTES);
 #pragma unroll
-                for (int sp = 1; sp <= SL; ++sp) {
-                    const uint32_t idesc = idesc_bf16(NT * PL::T(sp));
-                    mma_f16(buf + (uint32_t)(NT * (sp - 1)), dL0 + (uint64_t)(((sp - 1) * L_PLANE) >> 4), dC0, idesc,
-                            (first && sp == 1) ? 0u : 1u);
+                    for (int sp = 1; sp <= SL; ++sp) {
+                        const uint32_t idesc = idesc_bf16(NT * PL::T(sp));
+                        mma_f16(buf + (uint32_t)(NT * (sp - 1)), dL0 + (uint64_t)(((sp - 1) * L_PLANE) >> 4), dC0, idesc,
+                                (first && sp == 1) ? 0u : 1u);
+                    }
+                    mma_commit(&empty[s]);      // also tracks this stage's MMAs for the failure path
+                    last = gs;
+                    if (kt % RBK == RBK - 1 || kt + 1 == it.nkt) {
+                        mma_commit(&buf_full[gb & 1]);
+                        ++gb;
+                    }
                 }
-                mma_commit(&empty[s]);          // also tracks this stage's MMAs for the failure path
-                last = kt;
-                if (kt % RBK == RBK - 1 || kt + 1 == nkt) mma_commit(&buf_full[blk & 1]);
             }
             if (*fail && last >= 0) mbar_wait(&empty[last % STAGES], (uint32_t)((last / STAGES) & 1));
         }
@@ -393,44 +428,61 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
         const int q = warp & 3;                  // TMEM lane quarter of this warp
         const int hcol = e >> 2;                 // which half of the NT columns
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        float hi[NC], lo[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
-        for (int blk = 0; blk < nblk; ++blk) {
-            // lane 0 waits and decides for the warp (tcgen05.ld needs the whole warp converged)
-            int go = 0;
-            if (lane == 0) {
-                go = *fail ? 0 : 1;
-                if (go && !mbar_wait_sleep(&buf_full[blk & 1], (uint32_t)((blk >> 1) & 1))) {
-                    *fail = 1;
-                    go = 0;
-                }
+        int gb = 0;                              // blocks read back so far (all items)
+        for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+            const TmaItem it = tma_item<NT, OZ_BK>(batch, w, ntx, nty, nsplit_h, SIGN);
+            const OzProblem& P = batch.p[it.pb];
+            if (!it.live) {
+                if (EPI == OZ_EPI_RESID && e == 0 && lane == 0 && it.split == 0) P.rpart[it.tx + ntx * it.ty] = 0.0;
+                continue;
             }
-            if (!__shfl_sync(0xffffffffu, go, 0)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t buf = tmem + lane_base + (uint32_t)((blk & 1) * NCOL + hcol * NC);
+            const int nblk = (it.nkt + RBK - 1) / RBK;
+            float hi[NC], lo[NC];
 #pragma unroll
-            for (int g = 0; g < NG; ++g) {
-#pragma unroll
-                for (int c = 0; c < NC; c += 16) {
-                    float v[16];
-                    tmem_ld16(buf + (uint32_t)(g * NT + c), v);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) two_sum(hi[c + j], lo[c + j], v[j]);
+            for (int c = 0; c < NC; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
+            for (int blk = 0; blk < nblk; ++blk, ++gb) {
+                // lane 0 waits and decides for the warp (tcgen05.ld needs the whole warp converged)
+                int go = 0;
+                if (lane == 0) {
+                    go = *fail ? 0 : 1;
+                    if (go && !mbar_wait_sleep(&buf_full[gb & 1], (uint32_t)((gb >> 1) & 1))) {
+                        *fail = 1;
+                        go = 0;
+                    }
                 }
+                if (!__shfl_sync(0xffffffffu, go, 0)) {
+                    if (lane == 0) *(volatile int*)&s_efail = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t buf = tmem + lane_base + (uint32_t)((gb & 1) * NCOL + hcol * NC);
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+#pragma unroll
+                    for (int c = 0; c < NC; c += 16) {
+                        float v[16];
+                        tmem_ld16(buf + (uint32_t)(g * NT + c), v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) two_sum(hi[c + j], lo[c + j], v[j]);
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                // the MMA issuer waits for this before the buffer's next block (extra arrivals
+                // after the last block are never waited for)
+                if (lane == 0) mbar_arrive(&buf_free[gb & 1]);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0 && blk + 2 < nblk) mbar_arrive(&buf_free[blk & 1]);
-        }
-        // the epilogue warps decide together: a failure anywhere has been recorded before the
-        // last readback could complete, so after this barrier the flag no longer changes
-        asm volatile("bar.sync 1, %0;" ::"r"(T_NEPI * 32) : "memory");
-        if (!*fail) {
+            // the epilogue warps decide together: a warp whose readback failed has set s_efail
+            // before this barrier, and nothing else writes it
+            asm volatile("bar.sync 1, %0;" ::"r"(T_NEPI * 32) : "memory");
+            if (*(volatile int*)&s_efail) break;
+            const int M = it.M, N = it.N;
+            const int i0 = it.tx * OZ_BM, j0 = it.ty * NT;
+            const int nsplit = P.dsplit ? max(1, min(*P.dsplit, nsplit_h)) : nsplit_h;
+            double* const Cout = nsplit > 1 ? P.Cpart + it.split * P.split_stride : P.C;
             const int lrow = i0 + q * 32 + lane;                      // lane operand row
             const long long ccs = P.ccs < 0 ? (long long)M : P.ccs;
             const long long crs = P.crs < 0 ? (long long)N : P.crs;
-            double e2 = 0.0;
             float e2f = 0.f;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -454,24 +506,347 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                 }
             }
             if (EPI == OZ_EPI_RESID) {
-                e2 = warp_sum((double)e2f);
+                const double e2 = warp_sum((double)e2f);
                 if (lane == 0) red[e] = e2;
                 asm volatile("bar.sync 1, %0;" ::"r"(T_NEPI * 32) : "memory");
                 if (e == 0 && lane == 0) {
                     double t = 0.0;
 #pragma unroll
-                    for (int w = 0; w < T_NEPI; ++w) t += red[w];
-                    P.rpart[blockIdx.x + gridDim.x * blockIdx.y] = t;
+                    for (int w2 = 0; w2 < T_NEPI; ++w2) t += red[w2];
+                    P.rpart[it.tx + ntx * it.ty] = t;
                 }
+                // red[] is rewritten only after every warp has read this item's sum
+                asm volatile("bar.sync 1, %0;" ::"r"(T_NEPI * 32) : "memory");
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (*fail) {
-        if (tid == 0) atomicCAS(batch.err ? batch.err : &g_oztma_status, 0, RHOSVD_ERR_TIMEOUT);
-        if (EPI == OZ_EPI_RESID && tid == 0) P.rpart[blockIdx.x + gridDim.x * blockIdx.y] = 0.0;
+    if (*fail && tid == 0) atomicCAS(batch.err ? batch.err : &g_oztma_status, 0, RHOSVD_ERR_TIMEOUT);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------- the Khatri-Rao core
+// beta(i1, (j, m)) = sum_nu V1'(i1, nu) V2(j, nu) V3(m, nu) with V1' = V1 diag(xi'): C = A B^T
+// with A the generated Khatri-Rao operand (row j + r2 m, k = nu) and B the digit planes of V1'.
+// A CTA owns 128 rows of A (the TMEM lanes) and 160 rows of B (every r1 <= 160 at once); K runs
+// in stages of 16 through a ring of four shared-memory stages.  Warp roles:
+//   warp 0       MMA issuer: lane 0 issues, per stage, one tcgen05.mma of N = 160 per digit pair
+//                (s, t) with s + t <= 5 into the accumulator of its group;
+//   warps 1-16   workers: each thread forms 4 entries of A a stage (one row, 4 consecutive nu)
+//                from the FP32 pairs of V2 and V3 and writes their 4 digit planes into the stage;
+//                worker 0 also issues the stage's one bulk copy of B (tile-major, 160-row tiles);
+//                every 256 K they read the accumulators back into double-float sums (40 columns of
+//                one TMEM lane quarter a warp: the high words in registers, the low words in
+//                shared memory) and at the end store beta.
+// Both operands have balanced digits (|d1| <= 256, the others <= 128).  Three accumulators of 160
+// columns: the group g = 2 (products below 2^16: exact for 256 K), the group 3 (two pairs below
+// 2^15 each: exact for 256 K) and the groups 4 and 5 together in FP32 (their sum is below 2^-16
+// of the leading group's scale).  480 of the 512 TMEM columns, so there is no second buffer: the
+// MMAs of a block wait until the workers have read the previous one back, while the next stages
+// are already formed.
+namespace {
+
+constexpr int C_NT = OZ_CORE_NT;               // B rows (r1) a CTA
+constexpr int C_SK = 16;                       // K a stage (one MMA K step)
+constexpr int C_STAGES = 4;
+constexpr int C_WORK = 16;                     // worker warps
+constexpr int C_THREADS = 32 * (1 + C_WORK);
+constexpr int C_RBK = 16;                      // stages a readback block (256 K)
+constexpr int C_A_PLANE = OZ_BM * C_SK * 2;    // one digit plane of A: 4096 B
+constexpr int C_B_PLANE = C_NT * C_SK * 2;     // 5120 B
+constexpr int C_A_BYTES = 4 * C_A_PLANE;
+constexpr int C_B_BYTES = 4 * C_B_PLANE;
+constexpr int C_STAGE = C_A_BYTES + C_B_BYTES;
+constexpr int C_LO_BYTES = C_NT * OZ_BM * 4;   // low words of the double-float sums
+constexpr int C_SMEM = C_STAGES * C_STAGE + C_LO_BYTES + 1024;
+constexpr int C_COLS = C_NT / 4;               // output columns of a worker warp
+static_assert(C_STAGE % 1024 == 0 && C_SMEM + 1024 <= T_SMEM_MAX, "core shared memory (and the static part)");
+static_assert(3 * C_NT <= 512 && C_COLS % 8 == 0, "three accumulators in TMEM, 8-column loads");
+// exactness over a block: group 2 (one pair below 2^16), group 3 (two pairs below 2^15)
+static_assert(1LL * (1 << 16) * C_RBK * C_SK <= (1 << 24) && 2LL * (1 << 15) * C_RBK * C_SK <= (1 << 24),
+              "core readback cadence");
+
+// The four digit planes of one entry x = V2(j, nu) V3(m, nu) of the Khatri-Rao operand, row
+// exponent E (|x| < 2^E), scale T = 2^(32 - E): F = round(x_hi T) + round(x_lo T) with x_hi the
+// FP32 product of the heads and x_lo its error plus the cross terms (the tails' product, below
+// 2^-46 of x, is dropped).  F is cut into balanced base-256 digits by rounding to multiples of
+// 2^24, 2^16 and 2^8 (adding and subtracting 1.5 2^(23 + b) rounds an integer below 2^(22 + b)
+// to a multiple of 2^b); every step is exact on integers below 2^24.  |d1| <= 256, |d2|, |d3|,
+// |d4| <= 128; plane s holds d_s 2^(-8(s-1)), exact in BF16.
+__device__ __forceinline__ void kr_digits(float2 a, float2 b, float T, float* v)
+{
+    const float ph = __fmul_rn(a.x, b.x);
+    float pe = fmaf(a.x, b.x, -ph);
+    pe = fmaf(a.x, b.y, fmaf(a.y, b.x, pe));
+    const float yh = rintf(__fmul_rn(ph, T));
+    const float yl = rintf(__fmul_rn(pe, T));
+    const float t1 = __fsub_rn(__fadd_rn(yh, 0x1.8p47f), 0x1.8p47f);
+    float r = __fadd_rn(__fsub_rn(yh, t1), yl);
+    const float t2 = __fsub_rn(__fadd_rn(r, 0x1.8p39f), 0x1.8p39f);
+    r = __fsub_rn(r, t2);
+    const float t3 = __fsub_rn(__fadd_rn(r, 0x1.8p31f), 0x1.8p31f);
+    r = __fsub_rn(r, t3);
+    v[0] = __fmul_rn(t1, 0x1p-24f);
+    v[1] = __fmul_rn(t2, 0x1p-24f);
+    v[2] = __fmul_rn(t3, 0x1p-24f);
+    v[3] = __fmul_rn(r, 0x1p-24f);
+}
+
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t addr, uint32_t* r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+}
+
+// row exponent of Khatri-Rao row i (j = i mod r2, m = i / r2)
+__device__ __forceinline__ int kr_exp(const OzKR& kr, int i, int r2)
+{
+    return kr.e2 ? (int)kr.e2[i % r2] + (int)kr.e3[i / r2] : 0;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(C_THREADS, 1) k_ozcore(OzBatch batch)
+{
+    constexpr uint32_t IDESC = idesc_bf16(C_NT);
+    const int nsplit_h = batch.nsplit > 1 ? batch.nsplit : 1;
+    const int split = blockIdx.z % nsplit_h;
+    const OzProblem& P = batch.p[blockIdx.z / nsplit_h];
+    const int nsplit = P.dsplit ? max(1, min(*P.dsplit, nsplit_h)) : nsplit_h;
+    if (split >= nsplit) return;
+    const int r2 = *P.dNa;
+    const int M = r2 * (*P.dNb);
+    const int N = dimv(P.dN, P.N);
+    const int Kall = dimv(P.dK, P.K);
+    // this CTA's K range [kbase, kend): whole 32-wide pieces, the last split takes the rest
+    const int kspan = ((Kall + nsplit - 1) / nsplit + OZ_BK - 1) / OZ_BK * OZ_BK;
+    const int kbase = min(Kall, split * kspan);
+    const int kend = min(Kall, kbase + kspan);
+    double* const Cout = nsplit > 1 ? P.Cpart + split * P.split_stride : P.C;
+    const int i0 = blockIdx.x * OZ_BM, j0 = blockIdx.y * C_NT;
+    if (i0 >= M || j0 >= N) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nkt = (kend - kbase + C_SK - 1) / C_SK;
+    const int nblk = (nkt + C_RBK - 1) / C_RBK;
+
+    extern __shared__ __align__(1024) unsigned char csm[];
+    unsigned char* stages = (unsigned char*)(((uintptr_t)csm + 1023) & ~(uintptr_t)1023);
+    float* const lo_s = reinterpret_cast<float*>(stages + C_STAGES * C_STAGE);   // [column][row]
+    __shared__ __align__(8) uint64_t afull[C_STAGES], bfull[C_STAGES], empty[C_STAGES], acc_full, acc_free;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::);
     }
+    if (tid == 32) {
+        for (int s = 0; s < C_STAGES; ++s) {
+            mbar_init(&afull[s], C_WORK);
+            mbar_init(&bfull[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&acc_full, 1);
+        mbar_init(&acc_free, C_WORK);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    volatile int* fail = &s_fail;
+    int last = -1;          // MMA issuer: the stage committed last
+    int issued_b = 0;       // worker 0: stages whose B copy was issued
+    float hi[C_COLS];
+    const int q = warp & 3;                 // TMEM lane quarter of a worker warp
+    const int cg = (warp - 1) >> 2;         // its 40 output columns
+    const int orow = q * 32 + lane;         // its output row in the tile
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            for (int kt = 0; kt < nkt; ++kt) {
+                if (*fail) break;
+                const int s = kt % C_STAGES;
+                const int blk = kt / C_RBK;
+                const bool first = kt % C_RBK == 0;
+                // the accumulators were read back after the previous block
+                if (first && blk >= 1 && !mbar_wait(&acc_free, (uint32_t)((blk - 1) & 1))) {
+                    *fail = 1;
+                    break;
+                }
+                const uint32_t par = (uint32_t)((kt / C_STAGES) & 1);
+                if (!mbar_wait(&bfull[s], par) || !mbar_wait(&afull[s], par)) {
+                    *fail = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base = su32(stages + s * C_STAGE);
+                const uint64_t dA0 = desc_sw32(base), dB0 = desc_sw32(base + C_A_BYTES);
+#pragma unroll
+                for (int sa = 1; sa <= 4; ++sa) {
+#pragma unroll
+                    for (int tb = 1; tb <= 4; ++tb) {
+                        if (sa + tb > 5) continue;
+                        const int a = sa + tb - 2 < 2 ? sa + tb - 2 : 2;
+                        // (1, 1), (1, 2), (1, 3) open the accumulators of groups 2, 3, 4-5
+                        const bool reset = first && sa == 1 && tb <= 3;
+                        mma_f16(tmem + (uint32_t)(a * C_NT), dA0 + (uint64_t)(((sa - 1) * C_A_PLANE) >> 4),
+                                dB0 + (uint64_t)(((tb - 1) * C_B_PLANE) >> 4), IDESC, reset ? 0u : 1u);
+                    }
+                }
+                mma_commit(&empty[s]);
+                last = kt;
+                if (kt % C_RBK == C_RBK - 1 || kt + 1 == nkt) mma_commit(&acc_full);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------------- workers
+        const int w = warp - 1;
+#pragma unroll
+        for (int c = 0; c < C_COLS; ++c) {
+            hi[c] = 0.f;
+            lo_s[(cg * C_COLS + c) * OZ_BM + orow] = 0.f;
+        }
+        // generation unit: row gr of the tile, k = 4 c4 .. 4 c4 + 3 of each stage; a warp covers 8
+        // whole rows, so its digit stores fill 256 contiguous bytes of a plane
+        const int gr = w * 8 + (lane >> 2), c4 = lane & 3;
+        const int gi = i0 + gr;
+        const bool live = gi < M;
+        // the lanes' rows are consecutive: their V2 pairs are adjacent, their V3 pairs mostly one
+        const float2* V2 = P.kr.V2p + (live ? gi % r2 : 0);
+        const float2* V3 = P.kr.V3p + (live ? gi / r2 : 0);
+        const long long ldp = P.kr.ldp;
+        const float T = __int_as_float((127 + 32 - (live ? kr_exp(P.kr, gi, r2) : 0)) << 23);
+        // 8 bytes (4 k) of row gr in the 32-byte swizzled plane tile
+        const uint32_t a_off = (uint32_t)(gr * 32 + (((c4 >> 1) ^ ((gr >> 2) & 1)) << 4) + ((c4 & 1) << 3));
+
+        // read block b back (whole warp; false once a wait has failed)
+        auto readback = [&](int b) -> bool {
+            int go = 0;
+            if (lane == 0) {
+                go = *fail ? 0 : 1;
+                if (go && !mbar_wait_sleep(&acc_full, (uint32_t)(b & 1))) {
+                    *fail = 1;
+                    go = 0;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, go, 0)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cg * C_COLS);
+#pragma unroll
+            for (int c = 0; c < C_COLS; c += 8) {
+                uint32_t v[3][8];
+                tmem_ld8_nowait(acc + (uint32_t)(2 * C_NT + c), v[2]);
+                tmem_ld8_nowait(acc + (uint32_t)(C_NT + c), v[1]);
+                tmem_ld8_nowait(acc + (uint32_t)c, v[0]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float* lp = lo_s + (cg * C_COLS + c + j) * OZ_BM + orow;
+                    float l = *lp;
+                    two_sum(hi[c + j], l, __uint_as_float(v[2][j]));
+                    two_sum(hi[c + j], l, __uint_as_float(v[1][j]));
+                    two_sum(hi[c + j], l, __uint_as_float(v[0][j]));
+                    *lp = l;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0 && b + 1 < nblk) mbar_arrive(&acc_free);
+            return true;
+        };
+
+        int rb = 0;                 // next block to read back
+        for (int kt = 0; kt < nkt; ++kt) {
+            // the MMAs of stage kt - C_STAGES (which frees this stage) follow block rb's readback
+            if (rb < nblk && kt >= (rb + 1) * C_RBK + C_STAGES) {
+                if (!readback(rb)) break;
+                ++rb;
+            }
+            const int s = kt % C_STAGES;
+            int go = 0;
+            if (lane == 0) {
+                go = *fail ? 0 : 1;
+                if (go && kt >= C_STAGES && !mbar_wait(&empty[s], (uint32_t)(((kt / C_STAGES) - 1) & 1))) {
+                    *fail = 1;
+                    go = 0;
+                }
+            }
+            if (!__shfl_sync(0xffffffffu, go, 0)) break;
+            unsigned char* sA = stages + s * C_STAGE;
+            const int k0 = kbase + kt * C_SK;
+            if (w == 0 && lane == 0) {
+                // the stage's B: one 16-wide k tile of the 160-row tile, contiguous
+                const uint16_t* src = P.B.base + ((long long)(j0 / C_NT) * P.B.tiles_k + (k0 >> 4)) * 4 * (C_NT * C_SK);
+                mbar_expect_tx(&bfull[s], (uint32_t)C_B_BYTES);
+                bulk_g2s(sA + C_A_BYTES, src, (uint32_t)C_B_BYTES, &bfull[s]);
+                issued_b = kt + 1;
+            }
+            const int kg = k0 + c4 * 4;
+            uint32_t pk[4][2];
+#pragma unroll
+            for (int e2 = 0; e2 < 2; ++e2) {
+                float v[2][4];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int k = kg + 2 * e2 + e;
+                    float2 a = make_float2(0.f, 0.f), bb = a;
+                    if (live && k < kend) {
+                        a = __ldg(V2 + k * ldp);
+                        bb = __ldg(V3 + k * ldp);
+                    }
+                    kr_digits(a, bb, T, v[e]);
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+                    pk[p][e2] = __byte_perm(__float_as_uint(v[0][p]), __float_as_uint(v[1][p]), 0x7632);
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p) *reinterpret_cast<uint2*>(sA + a_off + p * C_A_PLANE) = make_uint2(pk[p][0], pk[p][1]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&afull[s]);
+        }
+        while (rb < nblk && !*fail) {
+            if (!readback(rb)) break;
+            ++rb;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool failed = *fail != 0;
+    if (failed) {
+        // what is still in flight lands before TMEM and shared memory go away
+        if (tid == 0 && last >= 0) mbar_wait(&empty[last % C_STAGES], (uint32_t)((last / C_STAGES) & 1));
+        if (tid == 32)
+            for (int kt = max(0, issued_b - C_STAGES); kt < issued_b; ++kt)
+                mbar_wait(&bfull[kt % C_STAGES], (uint32_t)((kt / C_STAGES) & 1));
+        if (tid == 0) atomicCAS(batch.err ? batch.err : &g_oztma_status, 0, RHOSVD_ERR_TIMEOUT);
+    } else if (warp > 0) {
+        const int row = i0 + orow;
+        if (row < M) {
+            const int ea = kr_exp(P.kr, row, r2);
+            const long long crs = P.crs < 0 ? (long long)N : P.crs;
+            const long long ccs = P.ccs < 0 ? (long long)M : P.ccs;
+#pragma unroll
+            for (int c = 0; c < C_COLS; ++c) {
+                const int col = j0 + cg * C_COLS + c;
+                if (col >= N) continue;
+                const int eb = P.B.exps ? (int)P.B.exps[col] : P.B.exp0;
+                // planes carry x 2^(8 - E): the product's scale is 2^(ea + eb - 16)
+                const double sc = __hiloint2double((ea + eb - 16 + 1023) << 20, 0);
+                const double lo = (double)lo_s[(cg * C_COLS + c) * OZ_BM + orow];
+                Cout[(long long)row * crs + (long long)col * ccs] = ((double)hi[c] + lo) * sc;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
@@ -493,6 +868,20 @@ EncodeTiledFn encoder()
             fn = (EncodeTiledFn)p;
     });
     return fn;
+}
+
+// streaming multiprocessors of the current device (the persistent kernels' CTA count)
+int sm_count()
+{
+    static int cnt[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!cnt[dev]) {
+        int c = 0;
+        if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) c = 1;
+        cnt[dev] = c;
+    }
+    return cnt[dev];
 }
 
 // 2D map over S planes of `rows` rows each (ld elements a row, bf16 patterns): dims {ld, S rows},
@@ -553,13 +942,48 @@ int run_tma(const OzBatch& b, cudaStream_t st)
     const int nsplit = b.nsplit > 1 ? b.nsplit : 1;
     if (nsplit > 1 && EPI != OZ_EPI_STORE) return RHOSVD_ERR_INVALID_ARG;
     const int laneExt = SIGN ? Nh : Mh, colExt = SIGN ? Mh : Nh;
-    dim3 grid((laneExt + OZ_BM - 1) / OZ_BM, (colExt + PL::NT - 1) / PL::NT, b.nbatch * nsplit);
-    kern<<<grid, T_THREADS, SMEM, st>>>(b, maps);
+    const int ntx = (laneExt + OZ_BM - 1) / OZ_BM, nty = (colExt + PL::NT - 1) / PL::NT;
+    const long long nitems = (long long)ntx * nty * b.nbatch * nsplit;
+    if (nitems > INT_MAX) return RHOSVD_ERR_INVALID_ARG;
+    const int ncta = (int)(nitems < sm_count() ? nitems : sm_count());
+    kern<<<ncta, T_THREADS, SMEM, st>>>(b, maps, ntx, nty);
     RH_CHECK_LAUNCH();
     return 0;
 }
 
 }  // namespace
+
+bool ozcore_tma_supports(const OzBatch& b)
+{
+    for (int i = 0; i < b.nbatch; ++i) {
+        const OzProblem& q = b.p[i];
+        if (!q.kr.V2p || !q.kr.V3p || !q.dNa || !q.dNb || !q.B.base || ((uintptr_t)q.B.base) % 16 != 0) return false;
+        if (q.B.tiles_k <= 0 || q.B.tile_h != C_NT) return false;
+    }
+    return true;
+}
+
+int launch_ozcore_tma(const OzBatch& b, cudaStream_t st)
+{
+    int Mh = 0, Nh = 0;
+    for (int i = 0; i < b.nbatch; ++i) {
+        Mh = max(Mh, b.p[i].M);
+        Nh = max(Nh, b.p[i].N);
+    }
+    if (Mh <= 0 || Nh <= 0) return 0;
+    if (!ozcore_tma_supports(b)) return RHOSVD_ERR_INVALID_ARG;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_ozcore, cudaFuncAttributeMaxDynamicSharedMemorySize, C_SMEM) != cudaSuccess)
+            return RHOSVD_ERR_CUDA;
+        attr = true;
+    }
+    const int nsplit = b.nsplit > 1 ? b.nsplit : 1;
+    dim3 grid((Mh + OZ_BM - 1) / OZ_BM, (Nh + C_NT - 1) / C_NT, b.nbatch * nsplit);
+    k_ozcore<<<grid, C_THREADS, C_SMEM, st>>>(b);
+    RH_CHECK_LAUNCH();
+    return 0;
+}
 
 bool ozgemm_tma_supports(const OzBatch& b, OzKind kind)
 {

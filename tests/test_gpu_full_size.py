@@ -130,20 +130,24 @@ def frexp_scale(x, lo=-126, hi=127, widen=0.0):
 
 
 # Bound on one core entry of the mixed form, per term nu and in units of 2^(Ea + Eb) (the two
-# operand rows' digit scales): S = 4 base-256 digits per operand, the first <= 2^8, the others
-# < 2^8, the last rounded; every pair s + t <= GMAX = 5 is multiplied.
-#   * dropped pairs s + t = 6, 7, 8 (3, 2 and 1 pairs), each below 2^16 2^(-8 (s + t)):
-C_DROP = 3 * 2.0 ** -32 + 2 * 2.0 ** -40 + 2.0 ** -48
-#   * rounding of the last digit of each operand (|x - x^| <= 2^(E - 33)): 2 2^-33 + 2^-66
-C_ROUND = 2 * 2.0 ** -33 + 2.0 ** -66
-#   * groups 2 and 3 are accumulated exactly (read back before their FP32 sums can round); groups
-#     4 and 5 share one FP32 accumulator read back every 128 K (4 stages of 32).  In that
-#     accumulator's units (2^(Ea + Eb - 16)) a term adds at most 3 + 4 2^-8 (three pairs below 1,
-#     four below 2^-8), so a 128-term block stays below 128 (3 + 2^-6); it receives 7 pairs x 2
-#     K-halves x 4 stages = 56 MMAs, each rounding (the tensor cores truncate) by at most
+# operand rows' digit scales): S = 4 balanced base-256 digits per operand, |d1| <= 2^8 and
+# |d2|, |d3|, |d4| <= 2^7, the last rounded; every pair s + t <= GMAX = 5 is multiplied, the term
+# of pair (s, t) being d_s d'_t 2^(-8 (s + t)).
+#   * dropped pairs s + t = 6, 7, 8 (3, 2 and 1 pairs, none with a leading digit): each below
+#     2^14 2^(-8 (s + t)):
+C_DROP = 3 * 2.0 ** -34 + 2 * 2.0 ** -42 + 2.0 ** -50
+#   * rounding: the Khatri-Rao operand's integer is the sum of its FP32 head product and of that
+#     product's error, each rounded to the last digit's unit (|x - x^| <= 2^(E - 32)); the other
+#     operand is rounded once (2^(E - 33)): 2^-32 + 2^-33 + 2^-65
+C_ROUND = 2.0 ** -32 + 2.0 ** -33 + 2.0 ** -65
+#   * groups 2 and 3 are accumulated exactly (read back every 256 K, before their FP32 sums can
+#     round); groups 4 and 5 share one FP32 accumulator read back at the same cadence.  In that
+#     accumulator's units (2^(Ea + Eb - 16)) a term adds at most 1.25 (group 4: 1/2 + 1/4 + 1/2)
+#     plus 1.5 2^-8 (group 5), so a 256-term block stays below 256 (1.25 + 1.5 2^-8); it receives
+#     7 pairs x 16 K steps of 16 = 112 MMAs, each rounding (the tensor cores truncate) by at most
 #     2 2^-23 of (|accumulator| + the sum of its 16 products):
-C_ACC = 56 * 2 * 2.0 ** -23 * (128 * (3 + 2.0 ** -6) + 16) * 2.0 ** -16 / 128
-C_CORE = C_DROP + C_ROUND + C_ACC          # about 2^-29.3 per term
+C_ACC = 112 * 2 * 2.0 ** -23 * ((256 + 16) * (1.25 + 1.5 * 2.0 ** -8)) * 2.0 ** -16 / 256
+C_CORE = C_DROP + C_ROUND + C_ACC          # about 2^-29.8 per term
 
 
 def core_entry_bound(precision, a, V2j, V3m, bb):
