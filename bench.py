@@ -897,7 +897,8 @@ def stage_roofline(P, fn, info_of, n, R, kin, precision):
     avg = ms_tot / cnt
     fl = algorithmic_flops(name, info_of(res), n, R, kin)
     out = {"kernel": name, "avg_launch_ms": avg, "launches": cnt, "stage_ms_total": ms_tot,
-           "call_ms_traced": sum(v[1] for v in prof.values())}
+           "call_ms_traced": sum(v[1] for v in prof.values()),
+           "stage_ms": {k: round(v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
     if fl is None:
         out.update({"bound": None, "achieved": None, "note": "no flop model for this stage"})
         return out

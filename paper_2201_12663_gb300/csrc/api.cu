@@ -4,6 +4,7 @@
 #include "internal.cuh"
 #include "ozgemm.cuh"
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <new>
 #include <stdio.h>
@@ -80,6 +81,40 @@ void prof_end(int id, cudaStream_t st)
 }  // namespace
 
 void rh::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// An auxiliary stream of a caller's stream, with the two events of a fork and a join: work that
+// does not depend on the chain in progress runs on it beside that chain.  Created once per
+// (device, caller stream), never while the caller's stream is being captured (then the work stays
+// on the caller's stream); at most 64 of them.
+struct AuxStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_aux_mu;
+std::map<std::pair<int, cudaStream_t>, AuxStream> g_aux;
+
+bool aux_stream(cudaStream_t st, AuxStream* out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(g_aux_mu);
+    auto it = g_aux.find({dev, st});
+    if (it != g_aux.end()) {
+        *out = it->second;
+        return true;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone || g_aux.size() >= 64)
+        return false;
+    AuxStream a;
+    if (cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess)
+        return false;
+    g_aux[{dev, st}] = a;
+    *out = a;
+    return true;
+}
 
 #define STAGE(name, call)                     \
     do {                                      \
@@ -222,8 +257,7 @@ struct Plan {
     int start;            // a caller's start basis replaces the random sketch
     int NQ;               // max n_l over modes
     int ks_sketch, ks_gram, ks_bbt;
-    size_t o_cpart, o_colmax, o_defl, o_defT;
-    int oz_s_defl;
+    size_t o_cpart, o_colmax, o_defl, o_defT, o_ydf2;
     size_t o_state, o_norms, o_keep, o_nn2, o_Un, o_xin, o_bufA, o_bufB, o_G, o_L, o_perm, o_B, o_vec, o_W, o_V, o_Z, o_rp,
         o_part;
     // mixed-precision form: digit planes and helpers
@@ -349,6 +383,8 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
     if (p->kdef > 0) {
         p->o_defl = take(sizeof(double) * 3 * (size_t)NK);
         p->o_defT = take(sizeof(double) * 3 * (size_t)rh::KMAX * p->kdef);
+        // the deflation sketch's own output, so that it can run beside the first CholeskyQR
+        if (o->precision == RHOSVD_MIXED) p->o_ydf2 = take(sizeof(double) * 3 * (size_t)NK);
     }
     p->o_part = take(sizeof(double) * (size_t)part);
     p->mixed = (o->precision == RHOSVD_MIXED);
@@ -393,9 +429,7 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
         p->oz_s_sketch = nsk > 0 ? rh::oz_choose_split((int)p->NQ, p->KW, R, 96, nsk) : 1;
         p->oz_s_gram = nsk > 0 ? rh::oz_choose_split(p->KW, p->KW, (int)p->NQ, rh::OZ_NT6, nsk) : 1;
         p->oz_s_bbt = rh::oz_choose_split(p->KW, p->KW, R, rh::OZ_NT6, 3);
-        p->oz_s_defl = (nsk > 0 && p->kdef > 0) ? rh::oz_choose_split((int)p->NQ, p->kdef, R, 96, nsk) : 1;
         long long zp = 3LL * p->oz_s_sketch * NK;
-        if (3LL * p->oz_s_defl * NK > zp) zp = 3LL * p->oz_s_defl * NK;
         if (3LL * p->oz_s_gram * KK > zp) zp = 3LL * p->oz_s_gram * KK;
         if (3LL * p->oz_s_bbt * KK > zp) zp = 3LL * p->oz_s_bbt * KK;
         p->o_ozpart = take(sizeof(double) * (size_t)zp);
@@ -500,74 +534,131 @@ struct HadSrc {
     const double* xa;
 };
 
-static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBasis* sb0, const rhosvd_tucker* out,
-                    void* workspace, size_t workspace_bytes, void* stream, const HadSrc* had = nullptr,
-                    int als_sweeps = 0)
-{
-    Plan p;
-    int rc = make_plan(cp, opts, &p, sb0 ? sb0->k0 : 0, als_sweeps);
-    if (rc) return rc;
-    if (!out || !out->info || !out->beta) return RHOSVD_ERR_INVALID_ARG;
-    for (int l = 0; l < 3; ++l) {
-        if (!out->Z[l] || !out->sigma[l]) return RHOSVD_ERR_INVALID_ARG;
-        if (cp->R > 0 && !cp->U[l]) return RHOSVD_ERR_INVALID_ARG;
-    }
-    if (cp->R > 0 && !cp->xi) return RHOSVD_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < p.total || ((uintptr_t)workspace % ALIGN) != 0)
-        return RHOSVD_ERR_WORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
-    char* ws = (char*)workspace;
-    DevState* S = (DevState*)(ws + p.o_state);
-    double* norms = (double*)(ws + p.o_norms);
-    double* colmax = (double*)(ws + p.o_colmax);
-    double* keepf = (double*)(ws + p.o_keep);
-    double* nn2 = (double*)(ws + p.o_nn2);
-    double* Un = (double*)(ws + p.o_Un);
-    double* xin = (double*)(ws + p.o_xin);
-    double* bufA = (double*)(ws + p.o_bufA);
-    double* bufB = (double*)(ws + p.o_bufB);
-    double* G = (double*)(ws + p.o_G);
-    double* L = (double*)(ws + p.o_L);
-    int* perm = (int*)(ws + p.o_perm);
-    double* Bm = (double*)(ws + p.o_B);
-    double* vec = (double*)(ws + p.o_vec);
-    double* W = (double*)(ws + p.o_W);
-    double* Vw = (double*)(ws + p.o_V);
-    double* Zw = (double*)(ws + p.o_Z);
-    double* rpart = (double*)(ws + p.o_rp);
-    double* part = (double*)(ws + p.o_part);
-    const int R = cp->R, KW = p.KW, rmax = p.rmax;
-    const long long NK = (long long)p.NQ * KW, KK = (long long)KW * KW;
-    const int vs = KW;
-    double* vd = vec;
-    double* ve = vec + 3 * vs;
-    double* vtau = vec + 6 * vs;
-    double* vD = vec + 9 * vs;
-    double* vL = vec + 12 * vs;
-    double* vmu = vec + 15 * vs;
-    const long long VS = (long long)KW * (R > 0 ? R : 1);
-    const long long US = (long long)p.NQ * (R > 0 ? R : 1);   // normalised side matrix per mode
-    const bool mixed = p.mixed != 0;
-    uint16_t* pU1 = mixed ? (uint16_t*)(ws + p.o_pU1) : nullptr;     // U planes, rows x, k = nu
-    uint16_t* pU2 = mixed ? (uint16_t*)(ws + p.o_pU2) : nullptr;     // U planes, rows nu, k = x
-    uint16_t* pP1 = mixed ? (uint16_t*)(ws + p.o_pP1) : nullptr;
-    uint16_t* pP2 = mixed ? (uint16_t*)(ws + p.o_pP2) : nullptr;
-    // per-row exponents of the digit planes (one array per plane buffer, stride EX per mode)
-    signed char* eU2 = mixed ? (signed char*)(ws + p.o_eU2) : nullptr;
-    signed char* eP1 = mixed ? (signed char*)(ws + p.o_eP1) : nullptr;
-    signed char* eP2 = mixed ? (signed char*)(ws + p.o_eP2) : nullptr;
-    const long long EX = mixed ? p.EX : 0;
-    double* Vt = mixed ? (double*)(ws + p.o_Vt) : nullptr;
-    uint16_t* sgn = mixed ? (uint16_t*)(ws + p.o_sgn) : nullptr;
-    double* ozpart = mixed ? (double*)(ws + p.o_ozpart) : nullptr;
-    int* ozerr = &out->info->status;
+namespace {
 
+// One reduction in flight: the call's arguments, its plan, the workspace's named regions and the
+// stream.  Each stage of the path is one member function; run() calls them in the path's order,
+// and the first error ends the call.
+struct Reduction {
+    const rhosvd_cp* cp = nullptr;
+    const rhosvd_opts* opts = nullptr;
+    const StartBasis* sb0 = nullptr;
+    const rhosvd_tucker* out = nullptr;
+    const HadSrc* had = nullptr;
+    Plan p;
+    cudaStream_t st = nullptr;
+    char* ws = nullptr;
+    int rc = 0;
+    // workspace regions and sizes (bind)
+    DevState* S = nullptr;
+    double *norms, *colmax, *keepf, *nn2, *Un, *xin, *bufA, *bufB, *G, *L;
+    int* perm;
+    double *Bm, *vec, *W, *Vw, *Zw, *rpart, *part;
+    int R = 0, KW = 0, rmax = 0;
+    long long NK = 0, KK = 0;
+    int vs = 0;
+    double *vd, *ve, *vtau, *vD, *vL, *vmu;
+    long long VS = 0, US = 0;
+    bool mixed = false;
+    uint16_t *pU1, *pU2, *pP1, *pP2;
+    signed char *eU2, *eP1, *eP2;
+    long long EX = 0;
+    double* Vt;
+    uint16_t* sgn;
+    double* ozpart;
+    int* ozerr;
+    // Z and beta as formed here: the caller's buffers, or FP64 staging for FP32 outputs (reset)
+    double* Zout[3];
+    double* beta_out = nullptr;
+    // the modes (all three, the sketched ones) and the basis each mode ends with (direct_bases)
+    ModeMap all, sk;
+    int nsk = 0;
+    double* Qfin[3];
+    int ldq[3];
+
+    void bind(void* workspace, void* stream);
+    int reset();
+    int normalise();
+    int direct_bases();
+    int slice_sketch_operand();
+    int sketch();
+    int cholqr3(double* bIn, double* bTmp, const int* kh, const int* dk0, int* dm, int* dkx, double* d0out,
+                const double* d0ref, double floor_rel, int* dnear, const AuxStream* fork_to = nullptr,
+                double* fork_ydf = nullptr);
+    int deflation_sketch(cudaStream_t st, double* Ydf);
+    int range_basis();
+    int project();
+    int eigen();
+    int bases_residual();
+    int rank_final();
+    int als();
+    int outputs_core();
+    int to_fp32();
+    int run();
+};
+
+// the workspace's named regions and the sizes every stage uses
+void Reduction::bind(void* workspace, void* stream)
+{
+    st = (cudaStream_t)stream;
+    ws = (char*)workspace;
+    S = (DevState*)(ws + p.o_state);
+    norms = (double*)(ws + p.o_norms);
+    colmax = (double*)(ws + p.o_colmax);
+    keepf = (double*)(ws + p.o_keep);
+    nn2 = (double*)(ws + p.o_nn2);
+    Un = (double*)(ws + p.o_Un);
+    xin = (double*)(ws + p.o_xin);
+    bufA = (double*)(ws + p.o_bufA);
+    bufB = (double*)(ws + p.o_bufB);
+    G = (double*)(ws + p.o_G);
+    L = (double*)(ws + p.o_L);
+    perm = (int*)(ws + p.o_perm);
+    Bm = (double*)(ws + p.o_B);
+    vec = (double*)(ws + p.o_vec);
+    W = (double*)(ws + p.o_W);
+    Vw = (double*)(ws + p.o_V);
+    Zw = (double*)(ws + p.o_Z);
+    rpart = (double*)(ws + p.o_rp);
+    part = (double*)(ws + p.o_part);
+    R = cp->R;
+    KW = p.KW;
+    rmax = p.rmax;
+    NK = (long long)p.NQ * KW;
+    KK = (long long)KW * KW;
+    vs = KW;
+    vd = vec;
+    ve = vec + 3 * vs;
+    vtau = vec + 6 * vs;
+    vD = vec + 9 * vs;
+    vL = vec + 12 * vs;
+    vmu = vec + 15 * vs;
+    VS = (long long)KW * (R > 0 ? R : 1);
+    US = (long long)p.NQ * (R > 0 ? R : 1);   // normalised side matrix per mode
+    mixed = p.mixed != 0;
+    pU1 = mixed ? (uint16_t*)(ws + p.o_pU1) : nullptr;     // U planes, rows x, k = nu
+    pU2 = mixed ? (uint16_t*)(ws + p.o_pU2) : nullptr;     // U planes, rows nu, k = x
+    pP1 = mixed ? (uint16_t*)(ws + p.o_pP1) : nullptr;
+    pP2 = mixed ? (uint16_t*)(ws + p.o_pP2) : nullptr;
+    // per-row exponents of the digit planes (one array per plane buffer, stride EX per mode)
+    eU2 = mixed ? (signed char*)(ws + p.o_eU2) : nullptr;
+    eP1 = mixed ? (signed char*)(ws + p.o_eP1) : nullptr;
+    eP2 = mixed ? (signed char*)(ws + p.o_eP2) : nullptr;
+    EX = mixed ? p.EX : 0;
+    Vt = mixed ? (double*)(ws + p.o_Vt) : nullptr;
+    sgn = mixed ? (uint16_t*)(ws + p.o_sgn) : nullptr;
+    ozpart = mixed ? (double*)(ws + p.o_ozpart) : nullptr;
+    ozerr = &out->info->status;
+}
+
+// outputs and device state cleared; the state counters set
+int Reduction::reset()
+{
     // ---- reset outputs and state
     if (cudaMemsetAsync(out->info, 0, sizeof(rhosvd_info), st) != cudaSuccess) return RHOSVD_ERR_CUDA;
     if (cudaMemsetAsync(S, 0, sizeof(DevState), st) != cudaSuccess) return RHOSVD_ERR_CUDA;
     // Z and beta as formed here: the caller's buffers, or FP64 staging for FP32 outputs
-    double* Zout[3];
-    double* beta_out = p.out_fp32 ? (double*)(ws + p.o_bf) : (double*)out->beta;
+    beta_out = p.out_fp32 ? (double*)(ws + p.o_bf) : (double*)out->beta;
     for (int l = 0; l < 3; ++l) {
         Zout[l] = p.out_fp32 ? (double*)(ws + p.o_zf) + (size_t)l * p.NQ * rmax : (double*)out->Z[l];
         if (cudaMemsetAsync(Zout[l], 0, sizeof(double) * (size_t)p.n[l] * rmax, st) != cudaSuccess)
@@ -576,7 +667,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
     }
     STAGE("init_state", launch_init_state(S, p.kin[0], p.kin[1], p.kin[2], p.direct[0] ? p.n[0] : 0,
                                 p.direct[1] ? p.n[1] : 0, p.direct[2] ? p.n[2] : 0, p.kdef, st));
+    return RHOSVD_OK;
+}
 
+// a1: column norms, dropped terms, normalised weights and side matrices
+int Reduction::normalise()
+{
     // ---- a1: column norms, normalised weights (Sec. 2.1)
     NormArgs na;
     memset(&na, 0, sizeof(na));
@@ -606,14 +702,16 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         }
     }
     STAGE("normalize", launch_terms(na, cp->xi, keepf, xin, out->xi_out, out->info, Un, US, nn2, S->total, ns, st));
+    return RHOSVD_OK;
+}
 
-    ModeMap all = {{0, 1, 2}};
-    ModeMap sk;
-    int nsk = 0;
+// the modes that are sketched, and the identity basis of the direct ones
+int Reduction::direct_bases()
+{
+    all = ModeMap{{0, 1, 2}};
+    nsk = 0;
     for (int l = 0; l < 3; ++l)
         if (!p.direct[l]) sk.m[nsk++] = l;
-    double* Qfin[3];
-    int ldq[3];
     for (int l = 0; l < 3; ++l) {
         ldq[l] = p.n[l];
         if (p.direct[l]) {
@@ -623,7 +721,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             Qfin[l] = bufB + l * NK;
         }
     }
+    return RHOSVD_OK;
+}
 
+// the range sketch's operand as digit planes (mixed form)
+int Reduction::slice_sketch_operand()
+{
     if (mixed && R > 0 && nsk > 0) {
         // digit planes of the range-sketch operand (rows x, k = nu): one fixed exponent (the
         // normalised entries are below 2^1), which is all a random range sketch needs
@@ -646,7 +749,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         }
         STAGE("slice_u", launch_slice_t(sb, nsk, p.tkR * 16, nmax, st));
     }
+    return RHOSVD_OK;
+}
 
+// a2: range sketch Y = U~ Omega (Rademacher) into bufA, or the caller's start basis
+int Reduction::sketch()
+{
     if (nsk > 0 && R > 0) {
         // ---- a2: range sketch Y = U diag(1/||u||) Omega (Rademacher), Y in bufA
         GemmBatch gb;
@@ -811,166 +919,254 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         } else {
             STAGE("sketch", launch_gemm_splitk(gb, part, st));
         }
+    }
+    return RHOSVD_OK;
+}
 
-        // ---- a3: CholeskyQR with pivoting, three passes: bIn -> bTmp -> bIn -> bTmp.  kh: host
-        // column bounds; dk0: device columns of the input; dm, dkx: device basis width and input
-        // columns (outputs); d0out: the first pass's largest Gram diagonal (optional); d0ref,
-        // floor_rel: absolute pivot floor floor_rel * d0ref (optional)
-        auto cholqr3 = [&](double* bIn, double* bTmp, const int* kh, const int* dk0, int* dm, int* dkx,
-                           double* d0out, const double* d0ref, double floor_rel, int* dnear) -> int {
-        const double tols[3] = {1e-15, 1e-11, 0.0};
-        const int pivots[3] = {1, 1, 0};
-        for (int pass = 0; pass < 3; ++pass) {
-            double* X = (pass == 1) ? bTmp : bIn;
-            double* Y = (pass == 1) ? bIn : bTmp;
-            GemmBatch g2;
-            memset(&g2, 0, sizeof(g2));
-            g2.nbatch = nsk;
-            g2.ksplit = p.ks_gram;
-            g2.bkind = B_PLAIN;
+// a3: CholeskyQR with pivoting, three passes: bIn -> bTmp -> bIn -> bTmp.  kh: host
+// column bounds; dk0: device columns of the input; dm, dkx: device basis width and input
+// columns (outputs); d0out: the first pass's largest Gram diagonal (optional); d0ref,
+// floor_rel: absolute pivot floor floor_rel * d0ref (optional); fork_to: the deflation sketch into
+// fork_ydf is launched on that auxiliary stream right after the first pass's Cholesky, once the
+// Cholesky's clusters hold their SMs (optional)
+int Reduction::cholqr3(double* bIn, double* bTmp, const int* kh, const int* dk0, int* dm, int* dkx, double* d0out,
+                       const double* d0ref, double floor_rel, int* dnear, const AuxStream* fork_to, double* fork_ydf)
+{
+    const double tols[3] = {1e-15, 1e-11, 0.0};
+    const int pivots[3] = {1, 1, 0};
+    for (int pass = 0; pass < 3; ++pass) {
+        double* X = (pass == 1) ? bTmp : bIn;
+        double* Y = (pass == 1) ? bIn : bTmp;
+        GemmBatch g2;
+        memset(&g2, 0, sizeof(g2));
+        g2.nbatch = nsk;
+        g2.ksplit = p.ks_gram;
+        g2.bkind = B_PLAIN;
+        for (int b = 0; b < nsk; ++b) {
+            const int l = sk.m[b];
+            GemmProblem g = blank_problem();
+            double* Xl = X + l * NK;
+            g.A = Mat{Xl, (long long)p.n[l], 1};      // A(i,x) = X(x,i)
+            g.B = Mat{Xl, 1, (long long)p.n[l]};      // B(x,j) = X(x,j)
+            g.C = G + l * KK;
+            g.crs = 1;
+            g.ccs = KW;
+            g.M = kh[l];
+            g.N = kh[l];
+            g.K = p.n[l];
+            if (pass > 0) { g.dM = &dm[l]; g.dN = &dm[l]; }
+            g2.p[b] = g;
+        }
+        if (mixed) {
+            // G = X^T X on the tensor cores: rows c of the operand = columns of X (k = x);
+            // every digit group is exact, so the Gram keeps FP64-class accuracy
+            OzSliceArgs sg;
+            memset(&sg, 0, sizeof(sg));
+            sg.S = OZ_S64;
+            OzBatch ob;
+            memset(&ob, 0, sizeof(ob));
+            ob.nbatch = nsk;
+            ob.nsplit = p.oz_s_gram;
+            ob.err = ozerr;
+            for (int b = 0; b < nsk; ++b) {
+                const int l = sk.m[b];
+                sg.X[b] = X + l * NK;
+                sg.rs[b] = p.n[l];
+                sg.cs[b] = 1;
+                sg.rows[b] = kh[l];
+                sg.drows[b] = pass > 0 ? &dm[l] : nullptr;
+                sg.K[b] = p.n[l];
+                sg.planes[b] = pP2 + l * p.sP2;
+                sg.pstride[b] = (long long)kh[l] * p.ldn;
+                sg.ld[b] = p.ldn;
+                sg.exps[b] = eP2 + l * EX;
+                tiled_out(sg, b, LANE);
+                sg.planes2[b] = pP1 + l * p.sP1;     // the same planes stacked along N
+                sg.tile_h2[b] = COL;
+                OzProblem& q = ob.p[b];
+                q.A = planes_of(sg, b);
+                q.B = planes2_of(sg, b);
+                q.M = q.N = kh[l];
+                if (pass > 0) q.dM = q.dN = &dm[l];
+                q.K = p.n[l];
+                q.C = G + l * KK;
+                q.crs = 1;
+                q.ccs = KW;
+                q.Cpart = ozpart + (size_t)l * p.oz_s_gram * KK;
+                q.split_stride = KK;
+            }
+            STAGE("cholqr_gram", launch_oz_slice(sg, nsk, st));
+            STAGE("cholqr_gram", launch_ozgemm(ob, OZ_F64_STORE, st));
+        } else {
+            STAGE("cholqr_gram", launch_gemm_splitk(g2, part, st));
+        }
+        const int* dk = (pass == 0) ? dk0 : dm;
+        // Y = X P Lt^{-T}: the triangular inverse scattered into W (the Gram's buffer), then
+        // one GEMM over the kx columns of X (a near-identity Gram has W written by the Cholesky)
+        double* Wq = G;
+        STAGE("cholqr_chol", launch_chol(sk, G, KK, KW, dk, dkx, L, KK, KW, perm, KW, dm, S->piv_fail,
+                                         pivots[pass], tols[pass], nsk, KW, pass == 0 ? d0out : nullptr,
+                                         d0ref, floor_rel, Wq, KK, KW, dnear, st));
+        if (pass == 0 && fork_to) {
+            if (cudaEventRecord(fork_to->fork, st) != cudaSuccess ||
+                cudaStreamWaitEvent(fork_to->s, fork_to->fork, 0) != cudaSuccess)
+                return RHOSVD_ERR_CUDA;
+            rc = deflation_sketch(fork_to->s, fork_ydf);
+            if (rc) return rc;
+            if (cudaEventRecord(fork_to->join, fork_to->s) != cudaSuccess) return RHOSVD_ERR_CUDA;
+        }
+        STAGE("cholqr_trinv", launch_trinv(sk, L, KK, KW, perm, KW, dkx, dm, Wq, KK, KW, dnear, nsk, st));
+        if (mixed) {
+            OzSliceArgs sx, sw;
+            memset(&sx, 0, sizeof(sx));
+            memset(&sw, 0, sizeof(sw));
+            sx.S = sw.S = OZ_S64;
+            OzBatch ob;
+            memset(&ob, 0, sizeof(ob));
+            ob.nbatch = nsk;
+            ob.err = ozerr;
+            for (int b = 0; b < nsk; ++b) {
+                const int l = sk.m[b];
+                sx.X[b] = X + l * NK;                 // rows x, k = column c of X
+                sx.rs[b] = 1;
+                sx.cs[b] = p.n[l];
+                sx.rows[b] = p.n[l];
+                sx.K[b] = kh[l];
+                sx.dK[b] = &dkx[l];
+                sx.planes[b] = pP2 + l * p.sP2;
+                sx.pstride[b] = (long long)p.n[l] * p.ldk;
+                sx.ld[b] = p.ldk;
+                sx.exps[b] = eP2 + l * EX;
+                sw.X[b] = Wq + l * KK;                // rows t (columns of W), k = c
+                sw.rs[b] = KW;
+                sw.cs[b] = 1;
+                sw.rows[b] = kh[l];
+                sw.drows[b] = &dm[l];
+                sw.K[b] = kh[l];
+                sw.dK[b] = &dkx[l];
+                sw.planes[b] = pP1 + l * p.sP1;
+                sw.pstride[b] = (long long)kh[l] * p.ldk;
+                sw.ld[b] = p.ldk;
+                sw.exps[b] = eP1 + l * EX;
+                tiled_out(sx, b, LANE);
+                tiled_out(sw, b, COL);
+                OzProblem& q = ob.p[b];
+                q.A = planes_of(sx, b);
+                q.B = planes_of(sw, b);
+                q.M = p.n[l];
+                q.N = kh[l];
+                q.dN = &dm[l];
+                q.K = kh[l];
+                q.dK = &dkx[l];
+                q.C = Y + l * NK;
+                q.crs = 1;
+                q.ccs = p.n[l];
+            }
+            STAGE("cholqr_apply", launch_oz_slice(sx, nsk, st));
+            STAGE("cholqr_apply", launch_oz_slice(sw, nsk, st));
+            STAGE("cholqr_apply", launch_ozgemm(ob, OZ_F64_STORE, st));
+        } else {
+            GemmBatch gq;
+            memset(&gq, 0, sizeof(gq));
+            gq.nbatch = nsk;
+            gq.ksplit = 1;
+            gq.bkind = B_PLAIN;
             for (int b = 0; b < nsk; ++b) {
                 const int l = sk.m[b];
                 GemmProblem g = blank_problem();
-                double* Xl = X + l * NK;
-                g.A = Mat{Xl, (long long)p.n[l], 1};      // A(i,x) = X(x,i)
-                g.B = Mat{Xl, 1, (long long)p.n[l]};      // B(x,j) = X(x,j)
-                g.C = G + l * KK;
+                g.A = Mat{X + l * NK, 1, (long long)p.n[l]};      // A(x, c) = X(x, c)
+                g.B = Mat{Wq + l * KK, 1, (long long)KW};         // B(c, t) = W(c, t)
+                g.C = Y + l * NK;
                 g.crs = 1;
-                g.ccs = KW;
-                g.M = kh[l];
+                g.ccs = p.n[l];
+                g.M = p.n[l];
                 g.N = kh[l];
-                g.K = p.n[l];
-                if (pass > 0) { g.dM = &dm[l]; g.dN = &dm[l]; }
-                g2.p[b] = g;
+                g.dN = &dm[l];
+                g.K = kh[l];
+                g.dK = &dkx[l];
+                gq.p[b] = g;
             }
-            if (mixed) {
-                // G = X^T X on the tensor cores: rows c of the operand = columns of X (k = x);
-                // every digit group is exact, so the Gram keeps FP64-class accuracy
-                OzSliceArgs sg;
-                memset(&sg, 0, sizeof(sg));
-                sg.S = OZ_S64;
-                OzBatch ob;
-                memset(&ob, 0, sizeof(ob));
-                ob.nbatch = nsk;
-                ob.nsplit = p.oz_s_gram;
-                ob.err = ozerr;
-                for (int b = 0; b < nsk; ++b) {
-                    const int l = sk.m[b];
-                    sg.X[b] = X + l * NK;
-                    sg.rs[b] = p.n[l];
-                    sg.cs[b] = 1;
-                    sg.rows[b] = kh[l];
-                    sg.drows[b] = pass > 0 ? &dm[l] : nullptr;
-                    sg.K[b] = p.n[l];
-                    sg.planes[b] = pP2 + l * p.sP2;
-                    sg.pstride[b] = (long long)kh[l] * p.ldn;
-                    sg.ld[b] = p.ldn;
-                    sg.exps[b] = eP2 + l * EX;
-                    tiled_out(sg, b, LANE);
-                    sg.planes2[b] = pP1 + l * p.sP1;     // the same planes stacked along N
-                    sg.tile_h2[b] = COL;
-                    OzProblem& q = ob.p[b];
-                    q.A = planes_of(sg, b);
-                    q.B = planes2_of(sg, b);
-                    q.M = q.N = kh[l];
-                    if (pass > 0) q.dM = q.dN = &dm[l];
-                    q.K = p.n[l];
-                    q.C = G + l * KK;
-                    q.crs = 1;
-                    q.ccs = KW;
-                    q.Cpart = ozpart + (size_t)l * p.oz_s_gram * KK;
-                    q.split_stride = KK;
-                }
-                STAGE("cholqr_gram", launch_oz_slice(sg, nsk, st));
-                STAGE("cholqr_gram", launch_ozgemm(ob, OZ_F64_STORE, st));
-            } else {
-                STAGE("cholqr_gram", launch_gemm_splitk(g2, part, st));
-            }
-            const int* dk = (pass == 0) ? dk0 : dm;
-            // Y = X P Lt^{-T}: the triangular inverse scattered into W (the Gram's buffer), then
-            // one GEMM over the kx columns of X (a near-identity Gram has W written by the Cholesky)
-            double* Wq = G;
-            STAGE("cholqr_chol", launch_chol(sk, G, KK, KW, dk, dkx, L, KK, KW, perm, KW, dm, S->piv_fail,
-                                             pivots[pass], tols[pass], nsk, KW, pass == 0 ? d0out : nullptr,
-                                             d0ref, floor_rel, Wq, KK, KW, dnear, st));
-            STAGE("cholqr_trinv", launch_trinv(sk, L, KK, KW, perm, KW, dkx, dm, Wq, KK, KW, dnear, nsk, st));
-            if (mixed) {
-                OzSliceArgs sx, sw;
-                memset(&sx, 0, sizeof(sx));
-                memset(&sw, 0, sizeof(sw));
-                sx.S = sw.S = OZ_S64;
-                OzBatch ob;
-                memset(&ob, 0, sizeof(ob));
-                ob.nbatch = nsk;
-                ob.err = ozerr;
-                for (int b = 0; b < nsk; ++b) {
-                    const int l = sk.m[b];
-                    sx.X[b] = X + l * NK;                 // rows x, k = column c of X
-                    sx.rs[b] = 1;
-                    sx.cs[b] = p.n[l];
-                    sx.rows[b] = p.n[l];
-                    sx.K[b] = kh[l];
-                    sx.dK[b] = &dkx[l];
-                    sx.planes[b] = pP2 + l * p.sP2;
-                    sx.pstride[b] = (long long)p.n[l] * p.ldk;
-                    sx.ld[b] = p.ldk;
-                    sx.exps[b] = eP2 + l * EX;
-                    sw.X[b] = Wq + l * KK;                // rows t (columns of W), k = c
-                    sw.rs[b] = KW;
-                    sw.cs[b] = 1;
-                    sw.rows[b] = kh[l];
-                    sw.drows[b] = &dm[l];
-                    sw.K[b] = kh[l];
-                    sw.dK[b] = &dkx[l];
-                    sw.planes[b] = pP1 + l * p.sP1;
-                    sw.pstride[b] = (long long)kh[l] * p.ldk;
-                    sw.ld[b] = p.ldk;
-                    sw.exps[b] = eP1 + l * EX;
-                    tiled_out(sx, b, LANE);
-                    tiled_out(sw, b, COL);
-                    OzProblem& q = ob.p[b];
-                    q.A = planes_of(sx, b);
-                    q.B = planes_of(sw, b);
-                    q.M = p.n[l];
-                    q.N = kh[l];
-                    q.dN = &dm[l];
-                    q.K = kh[l];
-                    q.dK = &dkx[l];
-                    q.C = Y + l * NK;
-                    q.crs = 1;
-                    q.ccs = p.n[l];
-                }
-                STAGE("cholqr_apply", launch_oz_slice(sx, nsk, st));
-                STAGE("cholqr_apply", launch_oz_slice(sw, nsk, st));
-                STAGE("cholqr_apply", launch_ozgemm(ob, OZ_F64_STORE, st));
-            } else {
-                GemmBatch gq;
-                memset(&gq, 0, sizeof(gq));
-                gq.nbatch = nsk;
-                gq.ksplit = 1;
-                gq.bkind = B_PLAIN;
-                for (int b = 0; b < nsk; ++b) {
-                    const int l = sk.m[b];
-                    GemmProblem g = blank_problem();
-                    g.A = Mat{X + l * NK, 1, (long long)p.n[l]};      // A(x, c) = X(x, c)
-                    g.B = Mat{Wq + l * KK, 1, (long long)KW};         // B(c, t) = W(c, t)
-                    g.C = Y + l * NK;
-                    g.crs = 1;
-                    g.ccs = p.n[l];
-                    g.M = p.n[l];
-                    g.N = kh[l];
-                    g.dN = &dm[l];
-                    g.K = kh[l];
-                    g.dK = &dkx[l];
-                    gq.p[b] = g;
-                }
-                STAGE("cholqr_apply", launch_gemm(gq, st));
-            }
+            STAGE("cholqr_apply", launch_gemm(gq, st));
         }
-        return 0;
-        };
+    }
+    return 0;
+}
+
+// the deflation sketch Y2 = U~ Omega2 into Ydf (projected afterwards), on stream st.  It does not
+// depend on the first basis, so the mixed form runs it on an auxiliary stream beside the first
+// CholeskyQR; it never splits its K there (the split partials are the chain's), and so that both
+// schedules give the same bits, not in the other schedule either
+int Reduction::deflation_sketch(cudaStream_t st, double* Ydf)
+{
+    const unsigned long long seed2 = opts->seed ^ 0x9E3779B97F4A7C15ull;
+    if (mixed) {
+        OzBatch ob;
+        memset(&ob, 0, sizeof(ob));
+        ob.nbatch = nsk;
+        ob.nsplit = 1;
+        ob.err = ozerr;
+        SignPlaneArgs sg;
+        memset(&sg, 0, sizeof(sg));
+        sg.tiles_k = p.tkR;
+        sg.seed = seed2;
+        for (int b = 0; b < nsk; ++b) {
+            const int l = sk.m[b];
+            sg.planes[b] = sgn + l * p.sSg;
+            sg.rows[b] = p.kdef;
+            sg.K[b] = R;
+            sg.mode[b] = l;
+        }
+        STAGE("deflate_sketch", launch_sign_planes(sg, nsk, p.kdef, st));
+        for (int b = 0; b < nsk; ++b) {
+            const int l = sk.m[b];
+            OzProblem& q = ob.p[b];
+            q.B = OzPlanes{sgn + l * p.sSg, 0, 0, nullptr, 0, p.tkR, LANE};
+            q.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1, p.tkR, COL};
+            q.M = p.n[l];
+            q.N = p.kdef;
+            q.K = R;
+            q.C = Ydf + l * NK;
+            q.crs = 1;
+            q.ccs = p.n[l];
+            q.seed = seed2;
+            q.mode = l;
+        }
+        STAGE("deflate_sketch", launch_ozgemm(ob, OZ_SKETCH, st));
+    } else {
+        GemmBatch gd;
+        memset(&gd, 0, sizeof(gd));
+        gd.nbatch = nsk;
+        gd.ksplit = p.ks_sketch;
+        gd.bkind = B_SKETCH;
+        for (int b = 0; b < nsk; ++b) {
+            const int l = sk.m[b];
+            GemmProblem g = blank_problem();
+            g.A = Mat{Un + l * US, 1, (long long)p.n[l]};
+            g.C = Ydf + l * NK;
+            g.crs = 1;
+            g.ccs = p.n[l];
+            g.M = p.n[l];
+            g.N = p.kdef;
+            g.K = R;
+            g.seed = seed2;
+            g.mode = l;
+            gd.p[b] = g;
+        }
+        STAGE("deflate_sketch", launch_gemm_splitk(gd, part, st));
+    }
+    return RHOSVD_OK;
+}
+
+// a3: the first basis by pivoted CholeskyQR (the deflation sketch beside it), then the deflation
+int Reduction::range_basis()
+{
+    if (nsk > 0 && R > 0) {
+        AuxStream aux;
+        const bool fork = mixed && p.kdef > 0 && p.o_ydf2 != 0 && aux_stream(st, &aux);
+        double* const Ydf = fork ? (double*)(ws + p.o_ydf2) : bufA;   // bufA: free after the first CholeskyQR
         {
-            const int rc = cholqr3(bufA, bufB, p.kin, S->kin, S->m, S->kx, S->gmax, nullptr, 0.0, S->near);
+            const int rc = cholqr3(bufA, bufB, p.kin, S->kin, S->m, S->kx, S->gmax, nullptr, 0.0, S->near,
+                                   fork ? &aux : nullptr, Ydf);
             if (rc) return rc;
         }
         if (p.kdef > 0) {
@@ -979,67 +1175,14 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             // appended to Q.  A Gram of one sketch resolves directions only down to ~sqrt(u) of
             // the largest; near eps = 1e-7 the tail energy sits there.  A pivot must also exceed
             // 1e-26 of the first sketch's largest Gram diagonal: below that, Y2 is rounding noise.
-            double* Ydf = bufA;                              // free after the first CholeskyQR
             double* Qdf = (double*)(ws + p.o_defl);
             double* Tdf = (double*)(ws + p.o_defT);
-            const unsigned long long seed2 = opts->seed ^ 0x9E3779B97F4A7C15ull;
             int kdh[3] = {p.kdef, p.kdef, p.kdef};
-            if (mixed) {
-                OzBatch ob;
-                memset(&ob, 0, sizeof(ob));
-                ob.nbatch = nsk;
-                ob.nsplit = p.oz_s_defl;
-                ob.err = ozerr;
-                SignPlaneArgs sg;
-                memset(&sg, 0, sizeof(sg));
-                sg.tiles_k = p.tkR;
-                sg.seed = seed2;
-                for (int b = 0; b < nsk; ++b) {
-                    const int l = sk.m[b];
-                    sg.planes[b] = sgn + l * p.sSg;
-                    sg.rows[b] = p.kdef;
-                    sg.K[b] = R;
-                    sg.mode[b] = l;
-                }
-                STAGE("deflate_sketch", launch_sign_planes(sg, nsk, p.kdef, st));
-                for (int b = 0; b < nsk; ++b) {
-                    const int l = sk.m[b];
-                    OzProblem& q = ob.p[b];
-                    q.B = OzPlanes{sgn + l * p.sSg, 0, 0, nullptr, 0, p.tkR, LANE};
-                    q.A = OzPlanes{pU1 + l * p.sU1, (long long)p.n[l] * p.ldR, p.ldR, nullptr, 1, p.tkR, COL};
-                    q.M = p.n[l];
-                    q.N = p.kdef;
-                    q.K = R;
-                    q.C = Ydf + l * NK;
-                    q.crs = 1;
-                    q.ccs = p.n[l];
-                    q.seed = seed2;
-                    q.mode = l;
-                    q.Cpart = ozpart + (size_t)l * p.oz_s_defl * NK;
-                    q.split_stride = NK;
-                }
-                STAGE("deflate_sketch", launch_ozgemm(ob, OZ_SKETCH, st));
+            if (fork) {
+                if (cudaStreamWaitEvent(st, aux.join, 0) != cudaSuccess) return RHOSVD_ERR_CUDA;
             } else {
-                GemmBatch gd;
-                memset(&gd, 0, sizeof(gd));
-                gd.nbatch = nsk;
-                gd.ksplit = p.ks_sketch;
-                gd.bkind = B_SKETCH;
-                for (int b = 0; b < nsk; ++b) {
-                    const int l = sk.m[b];
-                    GemmProblem g = blank_problem();
-                    g.A = Mat{Un + l * US, 1, (long long)p.n[l]};
-                    g.C = Ydf + l * NK;
-                    g.crs = 1;
-                    g.ccs = p.n[l];
-                    g.M = p.n[l];
-                    g.N = p.kdef;
-                    g.K = R;
-                    g.seed = seed2;
-                    g.mode = l;
-                    gd.p[b] = g;
-                }
-                STAGE("deflate_sketch", launch_gemm_splitk(gd, part, st));
+                rc = deflation_sketch(st, Ydf);
+                if (rc) return rc;
             }
             for (int it = 0; it < 2; ++it)
                 STAGE("deflate_project", launch_deflate(sk, bufB, Ydf, NK, p.n, S->m, p.kdef, Tdf,
@@ -1051,9 +1194,13 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             }
             STAGE("deflate_append", launch_append(sk, bufB, Qdf, NK, p.n, S->m, S->mdef, nsk, p.NQ, p.kdef, st));
         }
-
     }
+    return RHOSVD_OK;
+}
 
+// a4, a5: projection B = Q^T U~ and its Gram M = B B^T
+int Reduction::project()
+{
     if (R > 0) {
         // ---- a4: projection B = Q^T U diag(1/||u||)  (m_l x R, ld KW)
         GemmBatch gb;
@@ -1174,6 +1321,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             STAGE("gram_bbt", launch_gemm_splitk(gm, part, st));
         }
     }
+    return RHOSVD_OK;
+}
+
+// a5, a6: tridiagonal eigen-solver, provisional rank, eigenvectors
+int Reduction::eigen()
+{
     if (R == 0 && cudaMemsetAsync(G, 0, sizeof(double) * 3 * KK, st) != cudaSuccess) return RHOSVD_ERR_CUDA;
     STAGE("trace", launch_trace(all, G, KK, KW, S->m, S->trace, 3, st));
     STAGE("tridiag", launch_tridiag(all, G, KK, KW, S->m, vd, ve, vtau, vs, 3, KW, st));
@@ -1202,7 +1355,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
     STAGE("rank_provisional", launch_rank(ra, st));
     STAGE("eigvecs", launch_eigvecs(all, vD, vL, vmu, vs, S->m, S, W, KK, KW, KW, 3, st));
     STAGE("backtransform", launch_backtransform(all, G, KK, KW, vtau, vs, S->m, S, W, KK, KW, KW, 3, st));
+    return RHOSVD_OK;
+}
 
+// Z_hi = Q W, V_hi = W^T B and the residual energy of every rank candidate
+int Reduction::bases_residual()
+{
     if (R > 0) {
         // ---- Z_hi = Q W (n_l x rhi, ld n_l) and V_hi = W^T B (rhi x R, ld KW)
         GemmBatch gz;
@@ -1406,7 +1564,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
     } else if (cudaMemsetAsync(rpart, 0, sizeof(double) * 3 * p.rp_stride, st) != cudaSuccess) {
         return RHOSVD_ERR_CUDA;
     }
+    return RHOSVD_OK;
+}
 
+// a6: the final eps-rank from the residual and the Ritz energies
+int Reduction::rank_final()
+{
     // ---- final eps-rank (Thm. 2.3) from the residual and the Ritz energies
     FinalArgs fa;
     memset(&fa, 0, sizeof(fa));
@@ -1429,7 +1592,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         fa.ntiles[l] = (int)p.rp_stride;
     }
     STAGE("rank_final", launch_rank_final(fa, st));
+    return RHOSVD_OK;
+}
 
+// optional ALS sweeps inside the bases Q_l
+int Reduction::als()
+{
     if (R > 0 && p.als > 0) {
         // ---- ALS refinement (eq. can_A_Tuck_als), modes 0, 1, 2 in turn, inside the basis Q_l:
         //      C_l = B_l diag(xi') (V_m2 (.) V_m1)^T, G_l = C_l C_l^T, W_l = its r_l leading
@@ -1537,7 +1705,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         }
         STAGE("als_z", launch_gemm(gzb, st));
     }
+    return RHOSVD_OK;
+}
 
+// outputs Z (and V), a7: the Khatri-Rao core
+int Reduction::outputs_core()
+{
     if (R > 0) {
         // ---- outputs: Z = Z_hi(:, :r), optional V = V_hi(:r, :)
         double* zd[3] = {Zout[0], Zout[1], Zout[2]};
@@ -1629,6 +1802,12 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
             STAGE("core", launch_gemm(gc, st));
         }
     }
+    return RHOSVD_OK;
+}
+
+// FP32 outputs, when asked for
+int Reduction::to_fp32()
+{
     if (p.out_fp32) {
         // round Z (every column, zeros included) and the packed core once into the FP32 outputs
         const double* src[4] = {Zout[0], Zout[1], Zout[2], beta_out};
@@ -1638,6 +1817,48 @@ static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBas
         STAGE("copy_out", launch_to_f32(src, dst, cnt, S->r, 4, st));
     }
     return RHOSVD_OK;
+}
+
+int Reduction::run()
+{
+    // the path's stages in order
+    int (Reduction::*const stages[])() = {
+        &Reduction::reset,          &Reduction::normalise,  &Reduction::direct_bases, &Reduction::slice_sketch_operand,
+        &Reduction::sketch,         &Reduction::range_basis, &Reduction::project,     &Reduction::eigen,
+        &Reduction::bases_residual, &Reduction::rank_final, &Reduction::als,          &Reduction::outputs_core,
+        &Reduction::to_fp32};
+    for (auto f : stages) {
+        const int e = (this->*f)();
+        if (e) return e;
+    }
+    return RHOSVD_OK;
+}
+
+}  // namespace
+
+static int c2t_impl(const rhosvd_cp* cp, const rhosvd_opts* opts, const StartBasis* sb0, const rhosvd_tucker* out,
+                    void* workspace, size_t workspace_bytes, void* stream, const HadSrc* had = nullptr,
+                    int als_sweeps = 0)
+{
+    Reduction c;
+    Plan& p = c.p;
+    int rc = make_plan(cp, opts, &p, sb0 ? sb0->k0 : 0, als_sweeps);
+    if (rc) return rc;
+    if (!out || !out->info || !out->beta) return RHOSVD_ERR_INVALID_ARG;
+    for (int l = 0; l < 3; ++l) {
+        if (!out->Z[l] || !out->sigma[l]) return RHOSVD_ERR_INVALID_ARG;
+        if (cp->R > 0 && !cp->U[l]) return RHOSVD_ERR_INVALID_ARG;
+    }
+    if (cp->R > 0 && !cp->xi) return RHOSVD_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < p.total || ((uintptr_t)workspace % ALIGN) != 0)
+        return RHOSVD_ERR_WORKSPACE;
+    c.cp = cp;
+    c.opts = opts;
+    c.sb0 = sb0;
+    c.out = out;
+    c.had = had;
+    c.bind(workspace, stream);
+    return c.run();
 }
 
 extern "C" int rhosvd_c2t(const rhosvd_cp* cp, const rhosvd_opts* opts, const rhosvd_tucker* out,

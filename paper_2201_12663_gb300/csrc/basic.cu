@@ -220,41 +220,41 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
         if (lane == 0) sel3(ns.exps, l)[warp] = (signed char)E;
     }
     double s = 0.0;
-    const int lim = P ? (ptk > 0 ? ptk * 16 : pld) : n;
+    const int lim = P ? (ptk > 0 ? ptk * 16 : pld) : n;     // a multiple of 8 when planes are cut
     // one multiply an element when s1 s2 is exact (s2 = 1 unless the exponent is extreme)
     const bool one = s2 == 1.0;
-    // NORM_UN loads of a lane issued before any is used: one load in flight per warp leaves the
-    // read stream latency-bound (a warp's 256 bytes against the ~40 KB an SM needs in flight)
-    constexpr int NORM_UN = 4;
-    for (int i0 = lane; i0 < lim; i0 += 32 * NORM_UN) {
-        double x[NORM_UN];
+    // a lane takes 8 consecutive x a round: its 8 loads are in flight together, and each digit
+    // plane gets one 16-byte store (8 consecutive k of the plane row nu)
+    for (int i0 = lane * 8; i0 < lim; i0 += 32 * 8) {
+        double v[8];
 #pragma unroll
-        for (int q = 0; q < NORM_UN; ++q) {
-            const int i = i0 + 32 * q;
-            x[q] = (keep && i < n) ? u[i] : 0.0;
+        for (int q = 0; q < 8; ++q) {
+            const int i = i0 + q;
+            const double x = (keep && i < n) ? u[i] : 0.0;
+            v[q] = one ? x * s1 : (x * s1) * s2;
         }
 #pragma unroll
-        for (int q = 0; q < NORM_UN; ++q) {
-            const int i = i0 + 32 * q;
-            if (i < lim) {
-                double v = 0.0;
-                if (i < n) {
-                    v = keep ? (one ? x[q] * s1 : (x[q] * s1) * s2) : 0.0;
-                    dst[i] = v;
-                    s = fma(v, v, s);
-                }
-                if (P) {
-                    uint16_t dg[OZ_S64];
-                    oz_digits(v, E, OZ_S64, dg, OZ_W64);
-                    if (ptk > 0) {
+        for (int q = 0; q < 8; ++q) {
+            if (i0 + q < n) {
+                dst[i0 + q] = v[q];
+                s = fma(v[q], v[q], s);
+            }
+        }
+        if (P) {
+            uint32_t w[OZ_S64][4];
 #pragma unroll
-                        for (int t = 0; t < OZ_S64; ++t) P[oz_tiled_index(OZ_S64, ptk, pth, t, warp, i)] = dg[t];
-                    } else {
-                        uint16_t* pq = P + (long long)warp * pld + i;
+            for (int q = 0; q < 8; q += 2) {
+                uint16_t d0[OZ_S64], d1[OZ_S64];
+                oz_digits(v[q], E, OZ_S64, d0, OZ_W64);
+                oz_digits(v[q + 1], E, OZ_S64, d1, OZ_W64);
 #pragma unroll
-                        for (int t = 0; t < OZ_S64; ++t) pq[t * pst] = dg[t];
-                    }
-                }
+                for (int t = 0; t < OZ_S64; ++t) w[t][q >> 1] = (uint32_t)d0[t] | ((uint32_t)d1[t] << 16);
+            }
+#pragma unroll
+            for (int t = 0; t < OZ_S64; ++t) {
+                uint16_t* dq = ptk > 0 ? P + oz_tiled_index(OZ_S64, ptk, pth, t, warp, i0)
+                                       : P + (long long)t * pst + (long long)warp * pld + i0;
+                *reinterpret_cast<uint4*>(dq) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
             }
         }
     }
@@ -263,38 +263,45 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
 }
 
 // Transposed digit planes with one fixed exponent E0 (|x| < 2^E0): planes[s][x ld + nu] from
-// X(x, nu) = X[x + ldx nu], zero for nu in [K, ld).  A 32 x 32 tile goes through shared memory so
-// that reads run along x and writes along nu.  grid (ceil(ld/32), ceil(rows/32), nmodes), block 32 x 8.
-__global__ void k_slice_t(SliceTArgs a)
+// X(x, nu) = X[x + ldx nu], zero for nu in [K, ld).  A 64 x 32 (x by nu) tile goes through shared
+// memory so that reads run along x; a thread then cuts 8 consecutive nu of one x and writes one
+// 16-byte chunk to every plane.  grid (ceil(ld/32), ceil(rows/64), nmodes), block 256.
+__global__ void __launch_bounds__(256) k_slice_t(SliceTArgs a)
 {
     const int b = blockIdx.z;
-    const int nu0 = blockIdx.x * 32, x0 = blockIdx.y * 32;
+    const int nu0 = blockIdx.x * 32, x0 = blockIdx.y * 64;
     const int rows = sel3(a.rows, b), K = sel3(a.K, b), ld = sel3(a.ld, b);
     if (x0 >= rows || nu0 >= ld) return;
-    __shared__ double tile[32][33];
+    __shared__ double tile[32][64];
     const double* X = sel3(a.X, b);
     const int ldx = sel3(a.ldx, b);
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int nu = nu0 + j, x = x0 + threadIdx.x;
-        tile[j][threadIdx.x] = (nu < K && x < rows) ? X[(long long)nu * ldx + x] : 0.0;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 32 * 64; e += 256) {
+        const int j = e >> 6, xx = e & 63;
+        const int nu = nu0 + j, x = x0 + xx;
+        tile[j][xx] = (nu < K && x < rows) ? X[(long long)nu * ldx + x] : 0.0;
     }
     __syncthreads();
+    // a warp: 32 consecutive x (conflict-free column reads), one 8-wide chunk of nu
+    const int xx = tid & 63, c = tid >> 6;
+    const int x = x0 + xx, nuc = nu0 + c * 8;
+    if (x >= rows || nuc >= ld) return;
     uint16_t* P = sel3(a.planes, b);
     const long long pst = sel3(a.pstride, b);
     const int tk = sel3(a.tiles_k, b), th = sel3(a.tile_h, b);
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int x = x0 + i, nu = nu0 + threadIdx.x;
-        if (x >= rows || nu >= ld) continue;
-        uint16_t dg[OZ_S64];
-        oz_digits(tile[threadIdx.x][i], a.E0, OZ_S64, dg, OZ_W64);
-        if (tk > 0) {
+    uint32_t w[OZ_S64][4];
 #pragma unroll
-            for (int t = 0; t < OZ_S64; ++t) P[oz_tiled_index(OZ_S64, tk, th, t, x, nu)] = dg[t];
-        } else {
-            uint16_t* q = P + (long long)x * ld + nu;
+    for (int q = 0; q < 8; q += 2) {
+        uint16_t d0[OZ_S64], d1[OZ_S64];
+        oz_digits(tile[c * 8 + q][xx], a.E0, OZ_S64, d0, OZ_W64);
+        oz_digits(tile[c * 8 + q + 1][xx], a.E0, OZ_S64, d1, OZ_W64);
 #pragma unroll
-            for (int t = 0; t < OZ_S64; ++t) q[t * pst] = dg[t];
-        }
+        for (int t = 0; t < OZ_S64; ++t) w[t][q >> 1] = (uint32_t)d0[t] | ((uint32_t)d1[t] << 16);
+    }
+#pragma unroll
+    for (int t = 0; t < OZ_S64; ++t) {
+        uint16_t* dq = tk > 0 ? P + oz_tiled_index(OZ_S64, tk, th, t, x, nuc) : P + (long long)t * pst + (long long)x * ld + nuc;
+        *reinterpret_cast<uint4*>(dq) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
     }
 }
 
@@ -340,8 +347,8 @@ int launch_sign_planes(const SignPlaneArgs& a, int nb, int rowsmax, cudaStream_t
 int launch_slice_t(const SliceTArgs& a, int nb, int ldmax, int rowsmax, cudaStream_t st)
 {
     if (nb <= 0 || ldmax <= 0 || rowsmax <= 0) return 0;
-    dim3 grid((ldmax + 31) / 32, (rowsmax + 31) / 32, nb);
-    k_slice_t<<<grid, dim3(32, 8), 0, st>>>(a);
+    dim3 grid((ldmax + 31) / 32, (rowsmax + 63) / 64, nb);
+    k_slice_t<<<grid, 256, 0, st>>>(a);
     RH_CHECK_LAUNCH();
     return 0;
 }

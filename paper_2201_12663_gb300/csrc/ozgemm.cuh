@@ -123,7 +123,9 @@ __device__ __forceinline__ void oz_digits_int(long long F, int S, uint16_t* out,
     for (int s = 1; s <= S; ++s) {
         const unsigned long long mask = s == 1 ? ((2ull << W) - 1) : ((1ull << W) - 1);
         const int d = (int)((A >> (W * (S - s))) & mask);
-        const float v = (float)d * __int_as_float((127 - W * (s - 1)) << 23);
+        // d < 2^23 as a float without a conversion instruction: the float 2^23 + d, less 2^23
+        const float fd = __fsub_rn(__int_as_float(0x4B000000 | d), 8388608.0f);
+        const float v = fd * __int_as_float((127 - W * (s - 1)) << 23);
         out[s - 1] = d ? (uint16_t)((__float_as_uint(v) >> 16) | sgn) : (uint16_t)0;
     }
 }
@@ -174,8 +176,9 @@ __device__ __forceinline__ void oz_digits_bal(double x, int E, uint16_t* out)
         // round half up: floor((t + 2^(b-1)) / 2^b) (an arithmetic shift), the last digit the rest
         const long long d = s < 4 ? (t + (1LL << (b - 1))) >> b : t;
         t -= d << b;
-        const float v = (float)d * __int_as_float((127 - 8 * (s - 1)) << 23);
-        out[s - 1] = (uint16_t)(__float_as_uint(v) >> 16);
+        const int di = (int)d, ad = di < 0 ? -di : di;      // |d| <= 256
+        const float v = __fsub_rn(__int_as_float(0x4B000000 | ad), 8388608.0f) * __int_as_float((127 - 8 * (s - 1)) << 23);
+        out[s - 1] = (uint16_t)((__float_as_uint(v) >> 16) | (di < 0 ? 0x8000u : 0u));
     }
 }
 

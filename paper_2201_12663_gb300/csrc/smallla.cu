@@ -563,7 +563,8 @@ __global__ void k_eigvecs(ModeMap mm, const double* D, const double* Lo, const d
 // y <- H_0 H_1 ... H_{k-3} y for each of the r columns (one warp per column, 4 a block); H_j
 // uses the reflector stored in A(j+1:k, j) and tau[j].  The column lives in registers (lane l
 // holds entries l, l + 32, ...), and the reflectors are staged in shared memory 16 at a time by
-// the whole block, so a reflector costs one warp reduction instead of an L2 round trip.
+// the whole block, so a reflector costs one warp reduction instead of an L2 round trip.  Reflector
+// j is zero in rows 0..j: the 32-row groups entirely above it are skipped (less FP64 work).
 // grid: (ceil(KMAX / 4), nmodes), block 128.
 constexpr int BT_CH = 16;
 
@@ -604,14 +605,15 @@ __global__ void k_backtransform(ModeMap mm, const double* A, long long astride, 
         for (int c = 0; c < nc; ++c) {
             const double t = ts[c];
             if (t == 0.0) continue;
+            const int q0 = (jhi - c + 1) >> 5;                 // first group holding row j + 1
             double dot = 0.0;
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
-                if (32 * q < kp) dot = fma(Vs[c][lane + 32 * q], yr[q], dot);
+                if (q >= q0 && 32 * q < kp) dot = fma(Vs[c][lane + 32 * q], yr[q], dot);
             dot = warp_sum(dot) * t;
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
-                if (32 * q < kp) yr[q] = fma(-dot, Vs[c][lane + 32 * q], yr[q]);
+                if (q >= q0 && 32 * q < kp) yr[q] = fma(-dot, Vs[c][lane + 32 * q], yr[q]);
         }
     }
     if (live) {
