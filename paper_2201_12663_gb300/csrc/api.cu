@@ -257,19 +257,19 @@ struct Plan {
     int start;            // a caller's start basis replaces the random sketch
     int NQ;               // max n_l over modes
     int ks_sketch, ks_gram, ks_bbt;
-    size_t o_cpart, o_colmax, o_defl, o_defT, o_ydf2;
+    size_t o_cpart, o_colmax, o_defl, o_defT, o_ydf2, o_dpart;
     size_t o_state, o_norms, o_keep, o_nn2, o_Un, o_xin, o_bufA, o_bufB, o_G, o_L, o_perm, o_B, o_vec, o_W, o_V, o_Z, o_rp,
         o_part;
     // mixed-precision form: digit planes and helpers
     int mixed;
     int ldR, ldn, ldk;            // plane row lengths (multiples of 8) for K = R, n, k
-    int tkR;                      // k tiles of the tile-major U~ planes with K = R
+    int tkR;                      // k tiles of the tile-major U~ planes with K = R (even)
     int tkC;                      // k tiles of the core's diag(xi') V1 planes
     long long sSg;                // per-mode size of the sketch's sign plane (elements)
     size_t o_sgn;
     size_t o_pU1, o_pU2, o_pP1, o_pP2, o_eU2, o_eP1, o_eP2, o_Vt;
     long long EX;         // per-mode stride of the per-row exponent arrays
-    int oz_s_sketch, oz_s_gram, oz_s_bbt;   // split-K counts of the tensor-core products
+    int oz_s_sketch, oz_s_gram, oz_s_bbt, oz_s_defl;   // split-K counts of the tensor-core products
     size_t o_ozpart;      // their partial sums
     long long ozpart_n;   // its capacity in doubles
     long long sU1, sU2, sP1, sP2; // per-mode plane-set sizes (elements)
@@ -395,7 +395,7 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
         p->ldk = up8(p->KW);
         // the two digit-plane sets of U~ are tile-major (whole 128 x 16 tiles, see ozgemm.cuh):
         // U1 rows x, k = nu; U2 rows nu, k = x
-        p->tkR = (R + 15) / 16;
+        p->tkR = (R + 31) / 32 * 2;     // an even count: the sketch streams k tiles in pairs
         p->sU1 = (long long)OZ_S64 * ((p->NQ + 127) / 128 * 128) * (p->tkR * 16LL);
         p->sU2 = (long long)OZ_S64 * ((R + 127) / 128 * 128) * ((p->NQ + 15) / 16 * 16LL);
         // the small operands' plane sets (tile-major: rows padded to 128, k to 16; enough for
@@ -428,6 +428,11 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
         for (int l = 0; l < 3; ++l) nsk += p->direct[l] ? 0 : 1;
         p->oz_s_sketch = nsk > 0 ? rh::oz_choose_split((int)p->NQ, p->KW, R, 96, nsk) : 1;
         p->oz_s_gram = nsk > 0 ? rh::oz_choose_split(p->KW, p->KW, (int)p->NQ, rh::OZ_NT6, nsk) : 1;
+        // the deflation sketch's split partials have a buffer of their own (it may run beside the
+        // chain, whose products use the common one): n x kdef a mode and split
+        p->oz_s_defl = (nsk > 0 && p->kdef > 0) ? rh::oz_choose_split((int)p->NQ, p->kdef, R, 96, nsk) : 1;
+        if (p->kdef > 0 && p->oz_s_defl > 1)
+            p->o_dpart = take(sizeof(double) * 3 * (size_t)p->oz_s_defl * (size_t)p->NQ * p->kdef);
         p->oz_s_bbt = rh::oz_choose_split(p->KW, p->KW, R, rh::OZ_NT6, 3);
         long long zp = 3LL * p->oz_s_sketch * NK;
         if (3LL * p->oz_s_gram * KK > zp) zp = 3LL * p->oz_s_gram * KK;
@@ -1094,8 +1099,8 @@ int Reduction::cholqr3(double* bIn, double* bTmp, const int* kh, const int* dk0,
 
 // the deflation sketch Y2 = U~ Omega2 into Ydf (projected afterwards), on stream st.  It does not
 // depend on the first basis, so the mixed form runs it on an auxiliary stream beside the first
-// CholeskyQR; it never splits its K there (the split partials are the chain's), and so that both
-// schedules give the same bits, not in the other schedule either
+// CholeskyQR; its split partials have a buffer of their own, and its split count is the same
+// whether it runs there or not, so that both schedules give the same bits
 int Reduction::deflation_sketch(cudaStream_t st, double* Ydf)
 {
     const unsigned long long seed2 = opts->seed ^ 0x9E3779B97F4A7C15ull;
@@ -1103,7 +1108,7 @@ int Reduction::deflation_sketch(cudaStream_t st, double* Ydf)
         OzBatch ob;
         memset(&ob, 0, sizeof(ob));
         ob.nbatch = nsk;
-        ob.nsplit = 1;
+        ob.nsplit = p.oz_s_defl;
         ob.err = ozerr;
         SignPlaneArgs sg;
         memset(&sg, 0, sizeof(sg));
@@ -1130,6 +1135,8 @@ int Reduction::deflation_sketch(cudaStream_t st, double* Ydf)
             q.ccs = p.n[l];
             q.seed = seed2;
             q.mode = l;
+            q.Cpart = p.oz_s_defl > 1 ? (double*)(ws + p.o_dpart) + (size_t)l * p.oz_s_defl * p.NQ * p.kdef : nullptr;
+            q.split_stride = (long long)p.NQ * p.kdef;
         }
         STAGE("deflate_sketch", launch_ozgemm(ob, OZ_SKETCH, st));
     } else {

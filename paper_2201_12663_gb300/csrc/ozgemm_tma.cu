@@ -210,11 +210,15 @@ struct Plan {
     static constexpr int NG = GMAX - 1;
     static constexpr int ZP = NG > SC ? NG - SC : 0;     // zero planes after the stacked ones
     static constexpr int NCOL = NG * NT;
-    static constexpr int RBK = KIND == TK_F64 ? 8 : 16;
+    static constexpr int RBK = KIND == TK_F64 ? 8 : 16;   // K steps of 16 a readback block
+    // K steps a pipeline stage: the sketch streams its operands with two a stage (half the copies
+    // and barrier round trips per byte); its stacked planes need no zero plane between the steps
+    static constexpr int KSUB = KIND == TK_SIGN ? 2 : 1;
+    static constexpr int RBS = RBK / KSUB;              // stages a readback block
     static constexpr int T(int s) { return s == 1 ? NG : (SC < GMAX - s ? SC : GMAX - s); }
     static constexpr bool ok()
     {
-        bool good = 2 * NCOL <= 512 && NT * T(1) <= 256;
+        bool good = 2 * NCOL <= 512 && NT * T(1) <= 256 && RBK % KSUB == 0 && (KSUB == 1 || ZP == 0);
         for (int g = 2; g <= GMAX && KIND != TK_BF16; ++g)
             good = good && (long long)npairs(SL, SC, g) * (1 << (2 * W)) * 16 * RBK <= (1 << 24);
         return good;
@@ -268,15 +272,16 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                                                         int nty)
 {
     using PL = Plan<KIND>;
-    constexpr int SL = PL::SL, SC = PL::SC, NT = PL::NT, W = PL::W, NG = PL::NG, NCOL = PL::NCOL, RBK = PL::RBK;
+    constexpr int SL = PL::SL, SC = PL::SC, NT = PL::NT, W = PL::W, NG = PL::NG, NCOL = PL::NCOL;
+    constexpr int KSUB = PL::KSUB, RBS = PL::RBS;
     constexpr bool SIGN = KIND == TK_SIGN;
     constexpr int L_PLANE = OZ_BM * TK * 2;              // 4096 B: 128 rows x 32 B
     constexpr int C_PLANE = NT * TK * 2;
-    constexpr int L_BYTES = SL * L_PLANE;
-    constexpr int C_BYTES = (SC + PL::ZP) * C_PLANE;
-    constexpr int STAGE = (L_BYTES + C_BYTES + 1023) / 1024 * 1024;
+    constexpr int L_BYTES = SL * L_PLANE;                  // one K step of the lane operand
+    constexpr int C_BYTES = (SC + PL::ZP) * C_PLANE;      // one K step of the stacked operand
+    constexpr int STAGE = (KSUB * (L_BYTES + C_BYTES) + 1023) / 1024 * 1024;
     constexpr int NC = NT / 2;                            // columns per epilogue warp
-    constexpr uint32_t TX_BYTES = L_BYTES + SC * C_PLANE;
+    constexpr uint32_t TX_BYTES = KSUB * (L_BYTES + SC * C_PLANE);
     static_assert(PL::ok(), "plan: TMEM, MMA width or exactness");
     static_assert(NC % 16 == 0, "16-column TMEM loads");
     static_assert(STAGES * STAGE + 2048 <= T_SMEM_MAX, "shared memory");
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
     // the zero planes of every stage (never written by the copies)
     if (PL::ZP > 0) {
         for (int s = 0; s < STAGES; ++s) {
-            uint32_t* z = (uint32_t*)(stages + s * STAGE + L_BYTES + SC * C_PLANE);
+            uint32_t* z = (uint32_t*)(stages + s * STAGE + KSUB * L_BYTES + SC * C_PLANE);
             for (int e = tid; e < PL::ZP * C_PLANE / 4; e += T_THREADS) z[e] = 0u;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -336,8 +341,9 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
             const int rowsL = LP.pstride > 0 ? (int)(LP.pstride / LP.ld) : 0;
             const int rowsC = CP.pstride > 0 ? (int)(CP.pstride / CP.ld) : 0;
             const int i0 = it.tx * OZ_BM, j0 = it.ty * NT;
+            const int nst = (it.nkt + KSUB - 1) / KSUB;    // stages of the item (KSUB K steps each)
             bool stop = false;
-            for (int kt = 0; kt < it.nkt; ++kt, ++gs) {
+            for (int kt = 0; kt < nst; ++kt, ++gs) {
                 const int s = gs % STAGES;
                 int go = 0;
                 if (lane == 0) {
@@ -352,22 +358,24 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                     break;
                 }
                 unsigned char* sL = stages + s * STAGE;
-                unsigned char* sC = sL + L_BYTES;
-                const int k0 = it.kbase + kt * TK;
+                unsigned char* sC = sL + KSUB * L_BYTES;
+                const int k0 = it.kbase + kt * TK * KSUB;
                 if (lane == 0) {
                     mbar_expect_tx(&full[s], TX_BYTES);
                     if (LP.tiles_k > 0) {
-                        // tile-major lane operand: the stage's SL plane tiles are one contiguous block
+                        // tile-major lane operand: the stage's KSUB x SL plane tiles are one contiguous
+                        // block (k tiles in pairs when KSUB = 2: the tile count is even, zeros past K)
                         const uint16_t* src = LP.base + ((long long)it.tx * LP.tiles_k + (k0 >> 4)) * SL * 2048;
-                        bulk_g2s(sL, src, L_BYTES, &full[s]);
+                        bulk_g2s(sL, src, KSUB * L_BYTES, &full[s]);
                     } else {
+                        // (row-major operands only in kinds of one K step a stage: ozgemm_tma_supports)
 #pragma unroll
                         for (int p = 0; p < SL; ++p) tma_2d(sL + p * L_PLANE, &maps.a[it.pb], k0, p * rowsL + i0, &full[s]);
                     }
                     if (CP.tiles_k > 0) {
                         // tile-major col operand (NT-row tiles): the stage's SC plane tiles, one block
                         const uint16_t* src = CP.base + ((long long)it.ty * CP.tiles_k + (k0 >> 4)) * SC * (NT * 16);
-                        bulk_g2s(sC, src, SC * C_PLANE, &full[s]);
+                        bulk_g2s(sC, src, KSUB * SC * C_PLANE, &full[s]);
                     } else {
 #pragma unroll
                         for (int p = 0; p < SC; ++p) tma_2d(sC + p * C_PLANE, &maps.b[it.pb], k0, p * rowsC + j0, &full[s]);
@@ -388,10 +396,11 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
             for (int w = blockIdx.x; w < nitems && !*fail; w += gridDim.x) {
                 const TmaItem it = tma_item<NT, OZ_BK>(batch, w, ntx, nty, nsplit_h, SIGN);
                 if (!it.live) continue;
-                for (int kt = 0; kt < it.nkt; ++kt, ++gs) {
+                const int nst = (it.nkt + KSUB - 1) / KSUB;
+                for (int kt = 0; kt < nst; ++kt, ++gs) {
                     if (*fail) break;
                     const int s = gs % STAGES;
-                    const bool first = kt % RBK == 0;
+                    const bool first = kt % RBS == 0;
                     const uint32_t buf = tmem + (uint32_t)((gb & 1) * NCOL);
                     // the block's buffer was read back by the epilogue two blocks ago
                     if (first && gb >= 2 && !mbar_wait(&buf_free[gb & 1], (uint32_t)(((gb >> 1) - 1) & 1))) {
@@ -404,16 +413,20 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t lBase = su32(stages + s * STAGE);
-                    const uint64_t dL0 = desc_sw32(lBase), dC0 = desc_sw32(lBase + L_BYTES);
 #pragma unroll
-                    for (int sp = 1; sp <= SL; ++sp) {
-                        const uint32_t idesc = idesc_bf16(NT * PL::T(sp));
-                        mma_f16(buf + (uint32_t)(NT * (sp - 1)), dL0 + (uint64_t)(((sp - 1) * L_PLANE) >> 4), dC0, idesc,
-                                (first && sp == 1) ? 0u : 1u);
+                    for (int h = 0; h < KSUB; ++h) {
+                        const uint64_t dL0 = desc_sw32(lBase + (uint32_t)(h * L_BYTES));
+                        const uint64_t dC0 = desc_sw32(lBase + (uint32_t)(KSUB * L_BYTES + h * SC * C_PLANE));
+#pragma unroll
+                        for (int sp = 1; sp <= SL; ++sp) {
+                            const uint32_t idesc = idesc_bf16(NT * PL::T(sp));
+                            mma_f16(buf + (uint32_t)(NT * (sp - 1)), dL0 + (uint64_t)(((sp - 1) * L_PLANE) >> 4), dC0,
+                                    idesc, (first && h == 0 && sp == 1) ? 0u : 1u);
+                        }
                     }
                     mma_commit(&empty[s]);      // also tracks this stage's MMAs for the failure path
                     last = gs;
-                    if (kt % RBK == RBK - 1 || kt + 1 == it.nkt) {
+                    if (kt % RBS == RBS - 1 || kt + 1 == nst) {
                         mma_commit(&buf_full[gb & 1]);
                         ++gb;
                     }
@@ -436,10 +449,24 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                 if (EPI == OZ_EPI_RESID && e == 0 && lane == 0 && it.split == 0) P.rpart[it.tx + ntx * it.ty] = 0.0;
                 continue;
             }
-            const int nblk = (it.nkt + RBK - 1) / RBK;
+            const int nblk = ((it.nkt + KSUB - 1) / KSUB + RBS - 1) / RBS;
             float hi[NC], lo[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
+            // the residual's reference entries are loaded before the item's readbacks, so that
+            // their DRAM latency passes while the item's MMAs run
+            double rv[EPI == OZ_EPI_RESID ? NC : 1];
+            if (EPI == OZ_EPI_RESID) {
+                const int lrow = it.tx * OZ_BM + q * 32 + lane;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int ccol = it.ty * NT + hcol * NC + c;
+                    const int row = SIGN ? ccol : lrow, col = SIGN ? lrow : ccol;
+                    rv[c] = (row < it.M && col < it.N)
+                                ? __ldg(P.ref + (long long)row * P.ref_rs + (long long)col * P.ref_cs)
+                                : 0.0;
+                }
+            }
             for (int blk = 0; blk < nblk; ++blk, ++gb) {
                 // lane 0 waits and decides for the warp (tcgen05.ld needs the whole warp converged)
                 int go = 0;
@@ -500,7 +527,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                     // scaling, one rounding), the small remainder and its square in FP32 (the
                     // residual's entries are far below ref's, so FP32 keeps them to 2^-24 of
                     // themselves; a scale below FP32's range only drops a term below 2^-126)
-                    const double t = fma(-(double)hi[c], sc, P.ref[(long long)row * P.ref_rs + (long long)col * P.ref_cs]);
+                    const double t = fma(-(double)hi[c], sc, rv[EPI == OZ_EPI_RESID ? c : 0]);
                     const float d = __double2float_rn(t) - lo[c] * __double2float_rn(sc);
                     e2f = fmaf(d, d, e2f);
                 }
@@ -907,7 +934,7 @@ int run_tma(const OzBatch& b, cudaStream_t st)
     using PL = Plan<KIND>;
     constexpr bool SIGN = KIND == TK_SIGN;
     constexpr int L_BYTES = PL::SL * OZ_BM * TK * 2, C_PLANE = PL::NT * TK * 2;
-    constexpr int STAGE = (L_BYTES + (PL::SC + PL::ZP) * C_PLANE + 1023) / 1024 * 1024;
+    constexpr int STAGE = (PL::KSUB * (L_BYTES + (PL::SC + PL::ZP) * C_PLANE) + 1023) / 1024 * 1024;
     constexpr int ST_FIT = (T_SMEM_MAX - 4096) / STAGE;
     constexpr int STAGES = ST_FIT > 8 ? 8 : ST_FIT;
     static_assert(STAGES >= 2, "two stages at least");
@@ -1000,6 +1027,8 @@ bool ozgemm_tma_supports(const OzBatch& b, OzKind kind)
             if (!pl.base || ((uintptr_t)pl.base) % 16 != 0) return false;
             if (pl.tiles_k > 0) {
                 if (pl.tile_h != (o == 0 ? OZ_BM : nt)) return false;
+                // the sketch streams two k tiles a stage: an even tile count (zeros past K)
+                if (kind == OZ_SKETCH && pl.tiles_k % Plan<TK_SIGN>::KSUB != 0) return false;
                 continue;
             }
             if (kind == OZ_SKETCH) return false;       // the sketch reads tile-major planes of U~ and signs
