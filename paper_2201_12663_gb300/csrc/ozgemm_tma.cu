@@ -213,12 +213,12 @@ struct Plan {
     static constexpr int RBK = KIND == TK_F64 ? 8 : 16;   // K steps of 16 a readback block
     // K steps a pipeline stage: the sketch streams its operands with two a stage (half the copies
     // and barrier round trips per byte); its stacked planes need no zero plane between the steps
-    static constexpr int KSUB = KIND == TK_SIGN ? 2 : 1;
+    static constexpr int KSUB = KIND == TK_BF16 ? 1 : 2;
     static constexpr int RBS = RBK / KSUB;              // stages a readback block
     static constexpr int T(int s) { return s == 1 ? NG : (SC < GMAX - s ? SC : GMAX - s); }
     static constexpr bool ok()
     {
-        bool good = 2 * NCOL <= 512 && NT * T(1) <= 256 && RBK % KSUB == 0 && (KSUB == 1 || ZP == 0);
+        bool good = 2 * NCOL <= 512 && NT * T(1) <= 256 && RBK % KSUB == 0;
         for (int g = 2; g <= GMAX && KIND != TK_BF16; ++g)
             good = good && (long long)npairs(SL, SC, g) * (1 << (2 * W)) * 16 * RBK <= (1 << 24);
         return good;
@@ -281,7 +281,6 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
     constexpr int C_BYTES = (SC + PL::ZP) * C_PLANE;      // one K step of the stacked operand
     constexpr int STAGE = (KSUB * (L_BYTES + C_BYTES) + 1023) / 1024 * 1024;
     constexpr int NC = NT / 2;                            // columns per epilogue warp
-    constexpr uint32_t TX_BYTES = KSUB * (L_BYTES + SC * C_PLANE);
     static_assert(PL::ok(), "plan: TMEM, MMA width or exactness");
     static_assert(NC % 16 == 0, "16-column TMEM loads");
     static_assert(STAGES * STAGE + 2048 <= T_SMEM_MAX, "shared memory");
@@ -299,10 +298,11 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
 
     // the zero planes of every stage (never written by the copies)
     if (PL::ZP > 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            uint32_t* z = (uint32_t*)(stages + s * STAGE + KSUB * L_BYTES + SC * C_PLANE);
-            for (int e = tid; e < PL::ZP * C_PLANE / 4; e += T_THREADS) z[e] = 0u;
-        }
+        for (int s = 0; s < STAGES; ++s)
+            for (int h = 0; h < KSUB; ++h) {
+                uint32_t* z = (uint32_t*)(stages + s * STAGE + KSUB * L_BYTES + h * C_BYTES + SC * C_PLANE);
+                for (int e = tid; e < PL::ZP * C_PLANE / 4; e += T_THREADS) z[e] = 0u;
+            }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
@@ -360,13 +360,14 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                 unsigned char* sL = stages + s * STAGE;
                 unsigned char* sC = sL + KSUB * L_BYTES;
                 const int k0 = it.kbase + kt * TK * KSUB;
+                const int kk = min(KSUB, it.nkt - kt * KSUB);   // K steps in this stage
                 if (lane == 0) {
-                    mbar_expect_tx(&full[s], TX_BYTES);
+                    mbar_expect_tx(&full[s], (uint32_t)kk * (L_BYTES + SC * C_PLANE));
                     if (LP.tiles_k > 0) {
-                        // tile-major lane operand: the stage's KSUB x SL plane tiles are one contiguous
-                        // block (k tiles in pairs when KSUB = 2: the tile count is even, zeros past K)
+                        // tile-major lane operand: the stage's kk x SL plane tiles are one contiguous
+                        // block (consecutive k tiles of a row tile are adjacent)
                         const uint16_t* src = LP.base + ((long long)it.tx * LP.tiles_k + (k0 >> 4)) * SL * 2048;
-                        bulk_g2s(sL, src, KSUB * L_BYTES, &full[s]);
+                        bulk_g2s(sL, src, kk * L_BYTES, &full[s]);
                     } else {
                         // (row-major operands only in kinds of one K step a stage: ozgemm_tma_supports)
 #pragma unroll
@@ -375,7 +376,13 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                     if (CP.tiles_k > 0) {
                         // tile-major col operand (NT-row tiles): the stage's SC plane tiles, one block
                         const uint16_t* src = CP.base + ((long long)it.ty * CP.tiles_k + (k0 >> 4)) * SC * (NT * 16);
-                        bulk_g2s(sC, src, KSUB * SC * C_PLANE, &full[s]);
+                        if (PL::ZP == 0) {
+                            bulk_g2s(sC, src, kk * SC * C_PLANE, &full[s]);
+                        } else {
+                            // a zero plane follows each K step's stacked planes: one copy a step
+                            for (int h = 0; h < kk; ++h)
+                                bulk_g2s(sC + h * C_BYTES, src + (long long)h * SC * (NT * 16), SC * C_PLANE, &full[s]);
+                        }
                     } else {
 #pragma unroll
                         for (int p = 0; p < SC; ++p) tma_2d(sC + p * C_PLANE, &maps.b[it.pb], k0, p * rowsC + j0, &full[s]);
@@ -413,10 +420,12 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t lBase = su32(stages + s * STAGE);
+                    const int kk = min(KSUB, it.nkt - kt * KSUB);
 #pragma unroll
                     for (int h = 0; h < KSUB; ++h) {
+                        if (h >= kk) break;
                         const uint64_t dL0 = desc_sw32(lBase + (uint32_t)(h * L_BYTES));
-                        const uint64_t dC0 = desc_sw32(lBase + (uint32_t)(KSUB * L_BYTES + h * SC * C_PLANE));
+                        const uint64_t dC0 = desc_sw32(lBase + (uint32_t)(KSUB * L_BYTES + h * C_BYTES));
 #pragma unroll
                         for (int sp = 1; sp <= SL; ++sp) {
                             const uint32_t idesc = idesc_bf16(NT * PL::T(sp));
@@ -1027,11 +1036,11 @@ bool ozgemm_tma_supports(const OzBatch& b, OzKind kind)
             if (!pl.base || ((uintptr_t)pl.base) % 16 != 0) return false;
             if (pl.tiles_k > 0) {
                 if (pl.tile_h != (o == 0 ? OZ_BM : nt)) return false;
-                // the sketch streams two k tiles a stage: an even tile count (zeros past K)
-                if (kind == OZ_SKETCH && pl.tiles_k % Plan<TK_SIGN>::KSUB != 0) return false;
                 continue;
             }
-            if (kind == OZ_SKETCH) return false;       // the sketch reads tile-major planes of U~ and signs
+            // the kinds of two K steps a stage read tile-major planes only (their row-major
+            // tensor-map path would fetch one K step)
+            if (kind != OZ_BF16) return false;
             if (pl.ld <= 0 || pl.ld % 8 != 0) return false;
             if (S > 1 && (pl.pstride <= 0 || pl.pstride % pl.ld != 0)) return false;
         }
