@@ -152,16 +152,54 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t addr, float* v)
+// One 32-lane x 16-column TMEM load; several are issued before one tcgen05.wait::ld
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t addr, uint32_t* r)
 {
-    uint32_t r[16];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                    "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                  : "r"(addr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// The epilogues' conversions, from the bits (GB300 issues FP64 instructions, the conversions
+// between FP32 and FP64 among them, at about two lanes a cycle per SM, so that four of them per
+// output element would bound a small-K product; integer operations run at the full rate).
+//
+// x 2^e as a double, exactly, for a finite FP32 x: the exponent is rebiased, the 23 fraction bits
+// move to the top of FP64's 52.  Zero gives +0; an FP32 subnormal (or a result below FP64's normal
+// range) takes the conversion instruction, with the same result as (double)x 2^e.
+__device__ __forceinline__ double f2d_scaled(float x, int e)
+{
+    const uint32_t b = __float_as_uint(x);
+    if ((b << 1) == 0u) return 0.0;
+    const int fe = (int)((b >> 23) & 0xffu), be = fe + (1023 - 127) + e;
+    if (fe == 0 || be <= 0) return (double)x * __hiloint2double((1023 + e) << 20, 0);
+    return __hiloint2double((int)((b & 0x80000000u) | ((uint32_t)be << 20) | ((b >> 3) & 0xfffffu)), (int)(b << 29));
+}
+
+// 2^e as a float (subnormal from 2^-149, zero below it, infinity above 2^127)
+__device__ __forceinline__ float pow2f(int e)
+{
+    return e >= -126 ? __int_as_float(min(e + 127, 255) << 23) : (e >= -149 ? __int_as_float(1 << (e + 149)) : 0.f);
+}
+
+// t rounded to the nearest float (ties to even) from its bits: the 52-bit fraction keeps its top
+// 23 bits, the 29 below decide the rounding (a carry runs into the exponent, up to infinity).
+// A result below FP32's normal range (|t| < 2^-126) gives a signed zero, where the conversion
+// instruction would give a subnormal.
+__device__ __forceinline__ float d2f_rn(double t)
+{
+    const uint32_t h = (uint32_t)__double2hiint(t), l = (uint32_t)__double2loint(t);
+    const uint32_t sgn = h & 0x80000000u;
+    const int fe = (int)((h >> 20) & 0x7ffu) - (1023 - 127);
+    if (fe <= 0) return __uint_as_float(sgn);
+    if (fe >= 255) return __uint_as_float(sgn | 0x7f800000u);
+    uint32_t f = ((uint32_t)fe << 23) | ((h & 0xfffffu) << 3) | (l >> 29);
+    const uint32_t rest = l & 0x1fffffffu;
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(sgn | f);
 }
 
 __device__ __forceinline__ void two_sum(float& hi, float& lo, float x)
@@ -281,6 +319,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
     constexpr int C_BYTES = (SC + PL::ZP) * C_PLANE;      // one K step of the stacked operand
     constexpr int STAGE = (KSUB * (L_BYTES + C_BYTES) + 1023) / 1024 * 1024;
     constexpr int NC = NT / 2;                            // columns per epilogue warp
+    constexpr int GB = NG < 4 ? NG : (EPI == OZ_EPI_RESID ? 2 : 4);   // groups a readback wait
     static_assert(PL::ok(), "plan: TMEM, MMA width or exactness");
     static_assert(NC % 16 == 0, "16-column TMEM loads");
     static_assert(STAGES * STAGE + 2048 <= T_SMEM_MAX, "shared memory");
@@ -492,14 +531,26 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t buf = tmem + lane_base + (uint32_t)((gb & 1) * NCOL + hcol * NC);
+                // up to four groups' loads in flight before one wait
 #pragma unroll
-                for (int g = 0; g < NG; ++g) {
+                for (int g0 = 0; g0 < NG; g0 += GB) {
+                    uint32_t v[GB][NC];
 #pragma unroll
-                    for (int c = 0; c < NC; c += 16) {
-                        float v[16];
-                        tmem_ld16(buf + (uint32_t)(g * NT + c), v);
+                    for (int g = 0; g < GB; ++g)
+                        if (g0 + g < NG)
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) two_sum(hi[c + j], lo[c + j], v[j]);
+                            for (int c = 0; c < NC; c += 16) tmem_ld16_issue(buf + (uint32_t)((g0 + g) * NT + c), &v[g][c]);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int g = 0; g < GB; ++g) {
+                        if (g0 + g >= NG) continue;
+#pragma unroll
+                        for (int j = 0; j < NC; ++j) {
+                            const float x = __uint_as_float(v[g][j]);
+                            // the item's first value starts the sum (two_sum from zero gives the same)
+                            if (g0 + g == 0 && blk == 0) { hi[j] = x; lo[j] = 0.f; }
+                            else two_sum(hi[j], lo[j], x);
+                        }
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -527,23 +578,27 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                 if (row >= M || col >= N) continue;
                 const int ea = P.A.exps ? (int)P.A.exps[row] : P.A.exp0;
                 const int eb = SIGN ? W : (P.B.exps ? (int)P.B.exps[col] : P.B.exp0);
-                // x = 2^(E - W) sum_s plane_s: a product carries 2^(ea + eb - 2W), built from its bits
-                const double sc = __hiloint2double((ea + eb - 2 * W + 1023) << 20, 0);
+                // x = 2^(E - W) sum_s plane_s: a product carries 2^(ea + eb - 2W)
+                const int se = ea + eb - 2 * W;
                 if (EPI == OZ_EPI_STORE) {
-                    Cout[(long long)row * crs + (long long)col * ccs] = ((double)hi[c] + (double)lo[c]) * sc;
+                    // (hi + lo) 2^se: both parts scaled exactly, one FP64 add
+                    Cout[(long long)row * crs + (long long)col * ccs] = f2d_scaled(hi[c], se) + f2d_scaled(lo[c], se);
                 } else {
-                    // ref - (hi + lo) sc: the cancelling part ref - hi sc in one FP64 fma (exact
-                    // scaling, one rounding), the small remainder and its square in FP32 (the
-                    // residual's entries are far below ref's, so FP32 keeps them to 2^-24 of
-                    // themselves; a scale below FP32's range only drops a term below 2^-126)
-                    const double t = fma(-(double)hi[c], sc, rv[EPI == OZ_EPI_RESID ? c : 0]);
-                    const float d = __double2float_rn(t) - lo[c] * __double2float_rn(sc);
+                    // ref - (hi + lo) 2^se: the cancelling part ref - hi 2^se in one FP64 add
+                    // (exact scaling, one rounding), the small remainder and its square in FP32
+                    // (the residual's entries are far below ref's, so FP32 keeps them to 2^-24 of
+                    // themselves; a scale or a remainder below FP32's normal range only drops a
+                    // term below 2^-126)
+                    const double t = rv[EPI == OZ_EPI_RESID ? c : 0] - f2d_scaled(hi[c], se);
+                    const float d = d2f_rn(t) - lo[c] * pow2f(se);
                     e2f = fmaf(d, d, e2f);
                 }
             }
             if (EPI == OZ_EPI_RESID) {
-                const double e2 = warp_sum((double)e2f);
-                if (lane == 0) red[e] = e2;
+                // the warp's sum in FP32 (32 partial sums of 16 squares), one conversion
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) e2f += __shfl_xor_sync(0xffffffffu, e2f, o);
+                if (lane == 0) red[e] = (double)e2f;
                 asm volatile("bar.sync 1, %0;" ::"r"(T_NEPI * 32) : "memory");
                 if (e == 0 && lane == 0) {
                     double t = 0.0;
@@ -875,9 +930,9 @@ __global__ void __launch_bounds__(C_THREADS, 1) k_ozcore(OzBatch batch)
                 if (col >= N) continue;
                 const int eb = P.B.exps ? (int)P.B.exps[col] : P.B.exp0;
                 // planes carry x 2^(8 - E): the product's scale is 2^(ea + eb - 16)
-                const double sc = __hiloint2double((ea + eb - 16 + 1023) << 20, 0);
-                const double lo = (double)lo_s[(cg * C_COLS + c) * OZ_BM + orow];
-                Cout[(long long)row * crs + (long long)col * ccs] = ((double)hi[c] + lo) * sc;
+                const int se = ea + eb - 16;
+                const float lo = lo_s[(cg * C_COLS + c) * OZ_BM + orow];
+                Cout[(long long)row * crs + (long long)col * ccs] = f2d_scaled(hi[c], se) + f2d_scaled(lo, se);
             }
         }
     }
