@@ -24,18 +24,24 @@ constexpr int TC_THREADS = 256;
 // alpha = -sign(x_0) ||x||, v = x - alpha e_1, tau = 2 / v^T v; the trailing block gets
 // A <- H A H via p = tau A v, w = p - (tau/2)(p^T v) v, A <- A - v w^T - w v^T.  Output: d
 // (diagonal), e (sub-diagonal), tau, and v stored in A(j+1:k, j) for the back-transformation.
-// Block `rank` holds rows i = rank + li C (full rows, ld k).  Per step:
-//   A  the owners send column j of their rows (x) and their part of ||x(2:)||^2 to every block;
-//      cluster barrier;
-//   B  every block forms alpha, tau and v; p_i = tau A(i, :) v for its rows, sent to every block
-//      with its part of p^T v; cluster barrier;
-//   C  every block forms w and updates its rows.
-// The gather buffers need no double buffering: a block writes step j+1's x only after passing
-// step j's second barrier (all blocks have finished reading step j's x), and step j+1's p only
-// after step j+1's first barrier (all blocks have finished step j's update, the last read of p).
+// Block `rank` holds rows i = rank + li C (full rows, ld k).  Every block also holds the step's
+// pivot row x = A(j, j:k) (= column j by symmetry), the same in every block.  Per step, one
+// cluster barrier:
+//   B  every block forms alpha, tau and v from x (the same sums in the same order everywhere);
+//      p_i = tau A(i, :) v for its rows and its part of p^T v, both kept locally; the owner of
+//      row j+1 keeps a copy of that row as it stands before the update; cluster barrier;
+//   C  every block reads p and the p^T v parts from their owners and the copy of row j+1, forms
+//      w, updates its rows and applies the same update to the copy, which gives step j+1's pivot
+//      row without a second exchange.
+// Nothing is written into another block's memory: on GB300 a cluster barrier alone costs ~540
+// cycles, ~1400 more with remote stores pending at it, and a round of remote loads after it
+// ~1100; the step's loads go out together, in the one round its pivot row copy needs anyway.
 // The update applies to element (i, c) and to its mirror (c, i) the same operations on the
 // same operands, fma(-v_lo, w_hi, fma(-w_lo, v_hi, a)) with lo = min(i, c), hi = max(i, c), so
-// the full-row storage stays exactly symmetric.
+// the full-row storage stays exactly symmetric, and the pivot row every block rebuilds is the
+// owner's row bit for bit.  The buffers read across blocks (p, the p^T v part, the row copy)
+// alternate by step parity: a block writes step j+2's only after the barrier of step j+1, which
+// no block passes before it has read step j's.
 template <int C>
 __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, double* A, long long astride, int lda,
                                                                 const int* dk, double* d, double* e, double* tau,
@@ -54,9 +60,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
     e += b * vstride;
     tau += b * vstride;
     extern __shared__ double Srow[];
-    __shared__ double xg[KMAX], pg[KMAX], vl[KMAX], wl[KMAX], ploc[32], qloc[32];
+    __shared__ double xg[KMAX], xn[KMAX], pg[KMAX], vl[KMAX], wl[KMAX], qloc[32];
+    __shared__ double pown[2][32], nrow[2][KMAX], pvl[2];
     __shared__ double dsh[KMAX], esh[KMAX], tsh[KMAX];
-    __shared__ double nrm[C], pvp[C];
     __shared__ double sc[4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nloc = rank < k ? (k - rank + C - 1) / C : 0;
@@ -66,43 +72,28 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
         const int i = rank + li * C;
         Srow[idx] = c <= i ? A[(long long)c * lda + i] : A[(long long)i * lda + c];
     }
-    cl.sync();                     // every block resident and loaded before the first remote store
+    // the first pivot row, A(0, c) = A[c]
+    for (int c = tid; c < k; c += TC_THREADS) xg[c] = A[c];
+    cl.sync();                     // every block resident and loaded before the first remote access
     for (int j = 0; j + 2 < k; ++j) {
-        const int c0 = j + 1;
+        const int c0 = j + 1, par = j & 1;
         const int li0 = c0 <= rank ? 0 : (c0 - rank + C - 1) / C;  // first owned row >= c0
         const int nr = nloc > li0 ? nloc - li0 : 0;
-        // ---- A: x = column j of the owned rows, and the owned part of the tail norm
-        if (tid < nr * C) {
-            const int r = tid / C, dst = tid - r * C;
-            const int li = li0 + r;
-            cl.map_shared_rank(xg, dst)[rank + li * C] = Srow[li * k + j];
-        }
-        if (warp == TC_THREADS / 32 - 1) {
-            double s = 0.0;
-            if (lane < nr) {
-                const int li = li0 + lane;
-                if (rank + li * C > c0) {
-                    const double x = Srow[li * k + j];
-                    s = x * x;
-                }
-            }
-            s = warp_sum(s);
-            if (lane < C) cl.map_shared_rank(nrm, lane)[rank] = s;
-        }
-        cl.sync();
         // ---- B: the Householder scalars in the last warp while warps 0..6 form
         // q_i = sum_{c > c0} A(i, c) x_c for the owned rows: v differs from x only in entry c0,
         // so A v = q + A(:, c0) v0 needs no scalar until the end, and the scalar chain (a square
         // root and a reciprocal, long dependent FP64 sequences) runs beside the product
         if (warp == TC_THREADS / 32 - 1) {
-            const double t2 = warp_sum(lane < C ? nrm[lane] : 0.0);   // same tree in every block
+            double s = 0.0;
+            for (int c = c0 + 1 + lane; c < k; c += 32) s = fma(xg[c], xg[c], s);
+            const double t2 = warp_sum(s);                        // same order in every block
             if (lane == 0) {
                 const double x0 = xg[c0];
                 double tj = 0.0, al = x0, v0 = 0.0;
                 if (t2 != 0.0) {
                     const double s2 = fma(x0, x0, t2);
-                    const double xn = s2 * fast_rsqrt(s2);
-                    al = (x0 >= 0.0) ? -xn : xn;
+                    const double xn0 = s2 * fast_rsqrt(s2);
+                    al = (x0 >= 0.0) ? -xn0 : xn0;
                     v0 = x0 - al;
                     tj = 2.0 * fast_rcp(fma(v0, v0, t2));
                 }
@@ -111,7 +102,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
                 sc[2] = v0;
                 tsh[j] = tj;                           // outputs stay in shared memory until the end:
                 esh[j] = al;                           // a global store pending at a cluster barrier
-                if (j % C == rank) dsh[j] = Srow[(j / C) * k + j];   // costs ~1200 cycles there
+                dsh[j] = xg[j];                        // costs ~1200 cycles there
             }
         } else {
             constexpr int MV_ROWS = (TC_THREADS - 32) / NCH;
@@ -136,33 +127,37 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
         const double t_j = sc[0], v0 = sc[2];
         for (int c = c0 + tid; c < k; c += TC_THREADS)
             vl[c] = (t_j == 0.0) ? 0.0 : (c == c0 ? v0 : xg[c]);
-        if (tid < nr) {
-            const int li = li0 + tid, i = rank + li * C;
-            const double vi = (t_j == 0.0) ? 0.0 : (i == c0 ? v0 : xg[i]);
-            ploc[tid] = t_j * fma(Srow[li * k + c0], v0, qloc[tid]);
-            Srow[li * k + j] = vi;                     // the reflector: column j of the row is dead now
+        if (c0 % C == rank)                            // the owner's copy of row c0 before the update
+            for (int c = c0 + tid; c < k; c += TC_THREADS) nrow[par][c] = Srow[(c0 / C) * k + c];
+        if (warp == 0) {                               // nr <= 32: the owned rows are warp 0's lanes
+            double s3 = 0.0;
+            if (lane < nr) {
+                const int li = li0 + lane, i = rank + li * C;
+                const double vi = (t_j == 0.0) ? 0.0 : (i == c0 ? v0 : xg[i]);
+                const double pi = t_j * fma(Srow[li * k + c0], v0, qloc[lane]);
+                pown[par][li] = pi;
+                s3 = pi * vi;
+                Srow[li * k + j] = vi;                 // the reflector: column j of the row is dead now
+            }
+            s3 = warp_sum(s3);
+            if (lane == 0) pvl[par] = s3;
+        }
+        cl.sync();
+        // ---- C: p and the pivot row copy from their owners, w = p - (tau/2)(p^T v) v, then the
+        // rank-2 update of the owned rows and of the copy (step j+1's pivot row)
+        {
+            const double* nsrc = cl.map_shared_rank(&nrow[par][0], c0 % C);
+            for (int c = c0 + tid; c < k; c += TC_THREADS) {
+                xn[c] = nsrc[c];
+                if (t_j != 0.0) pg[c] = cl.map_shared_rank(&pown[par][0], c % C)[c / C];
+            }
+        }
+        if (t_j != 0.0 && warp == 0) {
+            const double t2 = warp_sum(lane < C ? *cl.map_shared_rank(&pvl[par], lane) : 0.0);
+            if (lane == 0) sc[3] = 0.5 * t_j * t2;
         }
         __syncthreads();
         if (t_j != 0.0) {
-            if (tid < nr * C) {
-                const int r2 = tid / C, dst = tid - r2 * C;
-                cl.map_shared_rank(pg, dst)[rank + (li0 + r2) * C] = ploc[r2];
-            }
-            if (warp == TC_THREADS / 32 - 1) {
-                double s3 = 0.0;
-                if (lane < nr) s3 = ploc[lane] * vl[rank + (li0 + lane) * C];
-                s3 = warp_sum(s3);
-                if (lane < C) cl.map_shared_rank(pvp, lane)[rank] = s3;
-            }
-        }
-        cl.sync();
-        // ---- C: w = p - (tau/2)(p^T v) v, then the rank-2 update of the owned rows
-        if (t_j != 0.0) {
-            if (warp == 0) {
-                const double t2 = warp_sum(lane < C ? pvp[lane] : 0.0);
-                if (lane == 0) sc[3] = 0.5 * t_j * t2;
-            }
-            __syncthreads();
             const double Kc = sc[3];
             for (int c = c0 + tid; c < k; c += TC_THREADS) wl[c] = pg[c] - Kc * vl[c];
             __syncthreads();
@@ -180,6 +175,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_tridiag_cluster(ModeMap mm, doub
                     row[c] = fma(-x1, y1, fma(-x2, y2, row[c]));
                 }
             }
+            // the next pivot row: row c0 updated exactly as its owner updates it (c >= c0 = i)
+            const double vi = vl[c0], wi = wl[c0];
+            for (int c = c0 + tid; c < k; c += TC_THREADS) xg[c] = fma(-vi, wl[c], fma(-wi, vl[c], xn[c]));
+        } else {
+            for (int c = c0 + tid; c < k; c += TC_THREADS) xg[c] = xn[c];
         }
         __syncthreads();
     }

@@ -132,6 +132,12 @@ __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x,
                  : "memory");
 }
 
+// a contiguous range pulled into L2 (16-byte aligned, a multiple of 16 bytes; a hint, no completion)
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // one contiguous global -> shared copy onto an mbarrier (16-byte aligned, a multiple of 16 bytes)
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
 {
@@ -163,20 +169,25 @@ __device__ __forceinline__ void tmem_ld16_issue(uint32_t addr, uint32_t* r)
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// The epilogues' conversions, from the bits (GB300 issues FP64 instructions, the conversions
-// between FP32 and FP64 among them, at about two lanes a cycle per SM, so that four of them per
-// output element would bound a small-K product; integer operations run at the full rate).
+// The epilogues' conversions, from the bits, without branches.  GB300 issues FP64 instructions
+// (the conversions between FP32 and FP64 among them) at about two lanes a cycle per SM, and a
+// dependent FP64 operation waits ~64 cycles (several hundred behind a busy FP64 pipe): the
+// store epilogue keeps one FP64 add per output element, all of an item's adds independent of one
+// another and free of branches, so that they issue back to back; the residual none (FP32
+// double-float arithmetic); the rest is integer work.
 //
-// x 2^e as a double, exactly, for a finite FP32 x: the exponent is rebiased, the 23 fraction bits
-// move to the top of FP64's 52.  Zero gives +0; an FP32 subnormal (or a result below FP64's normal
-// range) takes the conversion instruction, with the same result as (double)x 2^e.
+// x 2^e as a double, exactly, for a finite FP32 x: the exponent is rebiased and the 23 fraction
+// bits move to the top of FP64's 52; an FP32 subnormal m 2^-149 is normalised first (its leading
+// bit p: 1.f 2^(p - 149)).  Zero, and a result below FP64's normal range, give +0.
 __device__ __forceinline__ double f2d_scaled(float x, int e)
 {
     const uint32_t b = __float_as_uint(x);
-    if ((b << 1) == 0u) return 0.0;
-    const int fe = (int)((b >> 23) & 0xffu), be = fe + (1023 - 127) + e;
-    if (fe == 0 || be <= 0) return (double)x * __hiloint2double((1023 + e) << 20, 0);
-    return __hiloint2double((int)((b & 0x80000000u) | ((uint32_t)be << 20) | ((b >> 3) & 0xfffffu)), (int)(b << 29));
+    const uint32_t fe = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    const int p = 31 - __clz((int)(m | 1u));
+    const uint32_t f = fe ? m : ((m << (23 - p)) & 0x7fffffu);
+    const int be = (fe ? (int)fe - 127 : p - 149) + e + 1023;
+    const uint32_t h = (b & 0x80000000u) | ((uint32_t)be << 20) | (f >> 3);
+    return ((b << 1) == 0u || be <= 0) ? 0.0 : __hiloint2double((int)h, (int)(f << 29));
 }
 
 // 2^e as a float (subnormal from 2^-149, zero below it, infinity above 2^127)
@@ -185,21 +196,35 @@ __device__ __forceinline__ float pow2f(int e)
     return e >= -126 ? __int_as_float(min(e + 127, 255) << 23) : (e >= -149 ? __int_as_float(1 << (e + 149)) : 0.f);
 }
 
-// t rounded to the nearest float (ties to even) from its bits: the 52-bit fraction keeps its top
-// 23 bits, the 29 below decide the rounding (a carry runs into the exponent, up to infinity).
-// A result below FP32's normal range (|t| < 2^-126) gives a signed zero, where the conversion
-// instruction would give a subnormal.
-__device__ __forceinline__ float d2f_rn(double t)
+// ref = rh + rl as two floats without FP64 work: rh is ref truncated to 24 significant bits, rl the
+// rest (up to 29 bits) rounded to a float (|rl - (ref - rh)| <= 2^-47 |ref|).  An entry outside
+// FP32's normal range (|ref| < 2^-126; |ref| >= 2^128 does not occur, the operands are
+// normalised) gives 0 + 0.
+__device__ __forceinline__ void split_ref(double ref, float& rh, float& rl)
 {
-    const uint32_t h = (uint32_t)__double2hiint(t), l = (uint32_t)__double2loint(t);
+    const uint32_t h = (uint32_t)__double2hiint(ref), l = (uint32_t)__double2loint(ref);
     const uint32_t sgn = h & 0x80000000u;
-    const int fe = (int)((h >> 20) & 0x7ffu) - (1023 - 127);
-    if (fe <= 0) return __uint_as_float(sgn);
-    if (fe >= 255) return __uint_as_float(sgn | 0x7f800000u);
-    uint32_t f = ((uint32_t)fe << 23) | ((h & 0xfffffu) << 3) | (l >> 29);
-    const uint32_t rest = l & 0x1fffffffu;
-    f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;
-    return __uint_as_float(sgn | f);
+    const int E = (int)((h >> 20) & 0x7ffu) - 1023;
+    const bool ok = E >= -126 && E <= 127;
+    const uint32_t fh = sgn | ((uint32_t)(E + 127) << 23) | ((h & 0xfffffu) << 3) | (l >> 29);
+    const uint32_t r29 = l & 0x1fffffffu;
+    // the 29-bit rest as a float: its two parts are exact (2^23 + d less 2^23), one rounding in the fma
+    const float ra = __fsub_rn(__uint_as_float(0x4B000000u | (r29 >> 6)), 8388608.0f);
+    const float rb = __fsub_rn(__uint_as_float(0x4B000000u | (r29 & 63u)), 8388608.0f);
+    const float rm = __fmul_rn(__fmaf_rn(ra, 64.0f, rb), pow2f(E - 52));
+    rh = ok ? __uint_as_float(fh) : 0.f;
+    rl = ok ? __uint_as_float(__float_as_uint(rm) | sgn) : 0.f;
+}
+
+// hi + lo += x, with the error of the high sum kept exactly (Knuth's two-sum) but the pair not
+// renormalised: seven operations instead of nine, for the residual's short sums (an item of at
+// most a few readback blocks: the low word's own rounding stays below 2^-40 of the sum)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
+{
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
 }
 
 __device__ __forceinline__ void two_sum(float& hi, float& lo, float x)
@@ -334,6 +359,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail, s_efail;
     __shared__ double red[T_NEPI];
+    __shared__ int s_ec[T_NEPI][NC];     // the epilogue warps' column exponents of the current item
 
     // the zero planes of every stage (never written by the copies)
     if (PL::ZP > 0) {
@@ -381,6 +407,14 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
             const int rowsC = CP.pstride > 0 ? (int)(CP.pstride / CP.ld) : 0;
             const int i0 = it.tx * OZ_BM, j0 = it.ty * NT;
             const int nst = (it.nkt + KSUB - 1) / KSUB;    // stages of the item (KSUB K steps each)
+            if (EPI == OZ_EPI_RESID && !SIGN && P.ref_rs == 1) {
+                // the item's reference columns (128 consecutive rows each) go to L2 while its
+                // operands stream in, so that the epilogue's reads of them do not wait on DRAM
+                const int col = j0 + lane;
+                const uint32_t bytes = (uint32_t)(min(OZ_BM, it.M - i0) * 8) & ~15u;
+                const double* src = P.ref + (long long)col * P.ref_cs + i0;
+                if (lane < NT && col < it.N && bytes > 0 && ((uintptr_t)src & 15) == 0) prefetch_l2(src, bytes);
+            }
             bool stop = false;
             for (int kt = 0; kt < nst; ++kt, ++gs) {
                 const int s = gs % STAGES;
@@ -501,11 +535,21 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
             float hi[NC], lo[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
-            // the residual's reference entries are loaded before the item's readbacks, so that
-            // their DRAM latency passes while the item's MMAs run
+            // the entries' scale exponents (and the residual's reference entries) are loaded before
+            // the item's readbacks, all at once, so that their latency passes while the item's
+            // MMAs run instead of one load after another in the stores.  x = 2^(E - W) sum_s
+            // plane_s: a product carries 2^(ea + eb - 2W), ea + eb = eL (this lane's operand row)
+            // + the column's exponent, the same for the whole warp (kept in shared memory)
+            const int lrow = it.tx * OZ_BM + q * 32 + lane;
+            const int eL = SIGN ? W : ((lrow < it.M && P.A.exps) ? (int)P.A.exps[lrow] : P.A.exp0);
+            {
+                const OzPlanes& CPl = SIGN ? P.A : P.B;
+                const int ccol = it.ty * NT + hcol * NC + lane;
+                if (lane < NC) s_ec[e][lane] = (ccol < (SIGN ? it.M : it.N) && CPl.exps) ? (int)CPl.exps[ccol] : CPl.exp0;
+                __syncwarp();
+            }
             double rv[EPI == OZ_EPI_RESID ? NC : 1];
             if (EPI == OZ_EPI_RESID) {
-                const int lrow = it.tx * OZ_BM + q * 32 + lane;
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     const int ccol = it.ty * NT + hcol * NC + c;
@@ -549,6 +593,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                             const float x = __uint_as_float(v[g][j]);
                             // the item's first value starts the sum (two_sum from zero gives the same)
                             if (g0 + g == 0 && blk == 0) { hi[j] = x; lo[j] = 0.f; }
+                            else if (EPI == OZ_EPI_RESID) two_sum_acc(hi[j], lo[j], x);
                             else two_sum(hi[j], lo[j], x);
                         }
                     }
@@ -564,34 +609,47 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
             asm volatile("bar.sync 1, %0;" ::"r"(T_NEPI * 32) : "memory");
             if (*(volatile int*)&s_efail) break;
             const int M = it.M, N = it.N;
-            const int i0 = it.tx * OZ_BM, j0 = it.ty * NT;
+            const int j0 = it.ty * NT;
             const int nsplit = P.dsplit ? max(1, min(*P.dsplit, nsplit_h)) : nsplit_h;
             double* const Cout = nsplit > 1 ? P.Cpart + it.split * P.split_stride : P.C;
-            const int lrow = i0 + q * 32 + lane;                      // lane operand row
             const long long ccs = P.ccs < 0 ? (long long)M : P.ccs;
             const long long crs = P.crs < 0 ? (long long)N : P.crs;
             float e2f = 0.f;
+            if (EPI == OZ_EPI_STORE) {
+                // (hi + lo) 2^se: both parts scaled exactly, one FP64 add; the adds of all NC
+                // entries first, then the stores, the bounds as predicates
+                double tv[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int ccol = j0 + hcol * NC + c;                  // col operand row
-                const int row = SIGN ? ccol : lrow, col = SIGN ? lrow : ccol;
-                if (row >= M || col >= N) continue;
-                const int ea = P.A.exps ? (int)P.A.exps[row] : P.A.exp0;
-                const int eb = SIGN ? W : (P.B.exps ? (int)P.B.exps[col] : P.B.exp0);
-                // x = 2^(E - W) sum_s plane_s: a product carries 2^(ea + eb - 2W)
-                const int se = ea + eb - 2 * W;
-                if (EPI == OZ_EPI_STORE) {
-                    // (hi + lo) 2^se: both parts scaled exactly, one FP64 add
-                    Cout[(long long)row * crs + (long long)col * ccs] = f2d_scaled(hi[c], se) + f2d_scaled(lo[c], se);
-                } else {
-                    // ref - (hi + lo) 2^se: the cancelling part ref - hi 2^se in one FP64 add
-                    // (exact scaling, one rounding), the small remainder and its square in FP32
-                    // (the residual's entries are far below ref's, so FP32 keeps them to 2^-24 of
-                    // themselves; a scale or a remainder below FP32's normal range only drops a
-                    // term below 2^-126)
-                    const double t = rv[EPI == OZ_EPI_RESID ? c : 0] - f2d_scaled(hi[c], se);
-                    const float d = d2f_rn(t) - lo[c] * pow2f(se);
-                    e2f = fmaf(d, d, e2f);
+                for (int c = 0; c < NC; ++c) {
+                    const int se = eL + s_ec[e][c] - 2 * W;
+                    tv[c] = f2d_scaled(hi[c], se) + f2d_scaled(lo[c], se);
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int ccol = j0 + hcol * NC + c;              // col operand row
+                    const int row = SIGN ? ccol : lrow, col = SIGN ? lrow : ccol;
+                    if (row < M && col < N) Cout[(long long)row * crs + (long long)col * ccs] = tv[c];
+                }
+            } else {
+                // d = ref - (hi + lo) 2^se in FP32 arithmetic: ref = rh + rl, the cancelling part
+                // rh - hi 2^se exactly by two-sum (the scaling is exact), the small parts added to
+                // its error.  |d - exact| <= 2^-24 |d| + ~2^-46 |ref|: the residual energy keeps
+                // 2^-22 of itself wherever it matters (entries of eps |ref| and more), and the
+                // entries' absolute errors add at most 2^-92 ||ref||^2 to it.  A scale or a part
+                // below FP32's normal range only drops a term below 2^-126.
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int ccol = j0 + hcol * NC + c;              // col operand row
+                    const int row = SIGN ? ccol : lrow, col = SIGN ? lrow : ccol;
+                    const float sf = pow2f(eL + s_ec[e][c] - 2 * W);
+                    const float h = __fmul_rn(hi[c], sf), l = __fmul_rn(lo[c], sf);
+                    float rh, rl;
+                    split_ref(rv[EPI == OZ_EPI_RESID ? c : 0], rh, rl);
+                    const float s1 = __fsub_rn(rh, h);
+                    const float bp = __fsub_rn(s1, rh);
+                    const float e1 = __fadd_rn(__fsub_rn(rh, __fsub_rn(s1, bp)), __fsub_rn(-h, bp));
+                    const float d = __fadd_rn(s1, __fadd_rn(e1, __fsub_rn(rl, l)));
+                    e2f = (row < M && col < N) ? fmaf(d, d, e2f) : e2f;
                 }
             }
             if (EPI == OZ_EPI_RESID) {
