@@ -132,12 +132,6 @@ __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x,
                  : "memory");
 }
 
-// a contiguous range pulled into L2 (16-byte aligned, a multiple of 16 bytes; a hint, no completion)
-__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 // one contiguous global -> shared copy onto an mbarrier (16-byte aligned, a multiple of 16 bytes)
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
 {
@@ -407,14 +401,6 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
             const int rowsC = CP.pstride > 0 ? (int)(CP.pstride / CP.ld) : 0;
             const int i0 = it.tx * OZ_BM, j0 = it.ty * NT;
             const int nst = (it.nkt + KSUB - 1) / KSUB;    // stages of the item (KSUB K steps each)
-            if (EPI == OZ_EPI_RESID && !SIGN && P.ref_rs == 1) {
-                // the item's reference columns (128 consecutive rows each) go to L2 while its
-                // operands stream in, so that the epilogue's reads of them do not wait on DRAM
-                const int col = j0 + lane;
-                const uint32_t bytes = (uint32_t)(min(OZ_BM, it.M - i0) * 8) & ~15u;
-                const double* src = P.ref + (long long)col * P.ref_cs + i0;
-                if (lane < NT && col < it.N && bytes > 0 && ((uintptr_t)src & 15) == 0) prefetch_l2(src, bytes);
-            }
             bool stop = false;
             for (int kt = 0; kt < nst; ++kt, ++gs) {
                 const int s = gs % STAGES;
