@@ -176,7 +176,8 @@ __global__ void k_terms(NormArgs a, const double* xi, double* keepf, double* xin
 }
 
 // Normalised copy of the side matrices (Sec. 2.1): Un(:, nu) = u_nu / ||u_nu|| for kept
-// terms (to about one ulp), zero columns for dropped terms; nn2 = ||Un(:, nu)||^2 as stored.
+// terms (to about one ulp), zero columns for dropped terms; nn2 = ||Un(:, nu)||^2 as stored, to
+// about 2^-44 of itself (it only enters the total energy behind the eps^2 thresholds).
 // u / d is u * (2^-e / f) with d = f 2^e, f in [0.5, 1) (one FP64 multiply an entry; two exact
 // power-of-two steps when 2^-e would leave the range).  With digit planes requested, column nu
 // is also cut into OZ_S64 planes as operand row nu (k = x) with exponent E_nu from
@@ -219,7 +220,9 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
         }
         if (lane == 0) sel3(ns.exps, l)[warp] = (signed char)E;
     }
-    double s = 0.0;
+    // nn2 in FP32 double-float arithmetic (the square's exact high product by fma, the cross term,
+    // a two-sum of the high parts): the multiply above is the entry's one FP64 instruction
+    float sh = 0.f, sl = 0.f;
     const int lim = P ? (ptk > 0 ? ptk * 16 : pld) : n;     // a multiple of 8 when planes are cut
     // one multiply an element when s1 s2 is exact (s2 = 1 unless the exponent is extreme)
     const bool one = s2 == 1.0;
@@ -237,7 +240,13 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
         for (int q = 0; q < 8; ++q) {
             if (i0 + q < n) {
                 dst[i0 + q] = v[q];
-                s = fma(v[q], v[q], s);
+                float vh, vl;
+                split_f64(v[q], vh, vl);
+                const float p = __fmul_rn(vh, vh);
+                const float pe = __fadd_rn(__fmaf_rn(vh, vh, -p), __fmul_rn(2.0f * vh, vl));   // vl^2 dropped
+                const float t = __fadd_rn(sh, p), bp = __fsub_rn(t, sh);
+                sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp)), pe));
+                sh = t;
             }
         }
         if (P) {
@@ -258,7 +267,7 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
             }
         }
     }
-    s = warp_sum(s);
+    const double s = warp_sum((double)sh + (double)sl);
     if (lane == 0) nn2[(long long)l * a.R + warp] = s;
 }
 

@@ -103,10 +103,56 @@ __global__ void k_oz_rowexp(OzSliceArgs a)
     }
 }
 
-constexpr int OZ_ST_R = 32, OZ_ST_K = 64;
+// The same exponents for k-contiguous operands of few rows and long K (the Gram B Bᵀ's B: k rows,
+// K = R; the core's V¹: r1 rows, K = R): one row per block, all 256 threads along k, so that the
+// launch has rows x problems blocks instead of rows / 8 (a block of 8 rows took 157 us for
+// K = 20000, this form about a tenth of it).  grid (rows, nb).
+__global__ void __launch_bounds__(256) k_oz_rowexp_long(OzSliceArgs a)
+{
+    const int b = blockIdx.y, i = blockIdx.x;
+    const int rows = a.rows[b];
+    if (i >= rows) return;
+    const int live = a.drows[b] ? *a.drows[b] : rows;
+    const int K = a.dK[b] ? *a.dK[b] : a.K[b];
+    const double* X = a.X[b];
+    const double* ks = a.kscale[b];
+    const long long rs = a.rs[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ int wmax[8];
+    int e = -4096;
+    if (i < live) {
+        const double* row = X + (long long)i * rs;
+        int k = tid;
+        // four independent loads in flight per thread
+        for (; k + 3 * 256 < K; k += 4 * 256) {
+            double x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = row[k + q * 256];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) e = max(e, oz_frexp_exp(ks ? x[q] * ks[k + q * 256] : x[q]));
+        }
+        for (; k < K; k += 256) e = max(e, oz_frexp_exp(ks ? row[k] * ks[k] : row[k]));
+    }
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (lane == 0) wmax[warp] = e;
+    __syncthreads();
+    if (tid == 0) {
+        int E = wmax[0];
+        for (int w = 1; w < 8; ++w) E = max(E, wmax[w]);
+        if (E == -4096) E = -126;
+        a.exps[b][i] = (signed char)min(127, max(-126, E));
+    }
+}
 
-// S as a template argument: the digit loops unroll and the digits stay in registers.
-template <int S>
+constexpr int OZ_ST_R = 32, OZ_ST_K = 64;
+constexpr int OZ_FUSE_KMAX = 256;   // K up to which a slicer block finds its rows' exponents itself
+
+// S as a template argument: the digit loops unroll and the digits stay in registers.  With FUSE
+// (every problem of the call has K <= OZ_FUSE_KMAX) a block first finds the exponents of its 32
+// rows itself, reading the rows' whole K (the other k tiles' blocks read the same rows, from L2),
+// and the blocks of the first k tile store them for the product: one launch instead of two, the
+// same exponents as k_oz_rowexp's.
+template <int S, bool FUSE>
 __global__ void __launch_bounds__(256) k_oz_slice_tile(OzSliceArgs a)
 {
     const int b = blockIdx.z;
@@ -121,7 +167,47 @@ __global__ void __launch_bounds__(256) k_oz_slice_tile(OzSliceArgs a)
     const double* ks = a.kscale[b];
     const long long rs = a.rs[b], cs = a.cs[b];
     __shared__ double T[OZ_ST_R][OZ_ST_K + 1];
+    __shared__ int s_e[OZ_ST_R];
     const int tid = threadIdx.x;
+    if (FUSE) {
+        if (tid < OZ_ST_R) s_e[tid] = -4096;
+        __syncthreads();
+        if (rs == 1) {
+            // rows contiguous: a warp reads 32 consecutive rows at one k
+            const int r = tid & 31, i = i0 + r;
+            int e = -4096;
+            if (i < live)
+                for (int k = tid >> 5; k < K; k += 8) {
+                    double x = X[(long long)i + (long long)k * cs];
+                    if (ks) x *= ks[k];
+                    e = max(e, oz_frexp_exp(x));
+                }
+            atomicMax(&s_e[r], e);
+        } else {
+            // k contiguous (or strided both ways): a warp per row, lanes along k
+            const int lane = tid & 31, w = tid >> 5;
+            for (int r = w; r < OZ_ST_R; r += 8) {
+                const int i = i0 + r;
+                int e = -4096;
+                if (i < live)
+                    for (int k = lane; k < K; k += 32) {
+                        double x = X[(long long)i * rs + (long long)k * cs];
+                        if (ks) x *= ks[k];
+                        e = max(e, oz_frexp_exp(x));
+                    }
+                for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+                if (lane == 0) s_e[r] = e;
+            }
+        }
+        __syncthreads();
+        if (tid < OZ_ST_R) {
+            int E = s_e[tid];
+            if (E == -4096) E = -126;
+            E = min(127, max(-126, E));
+            s_e[tid] = E;
+            if (blockIdx.x == 0 && i0 + tid < rows) a.exps[b][i0 + tid] = (signed char)E;
+        }
+    }
     if (rs == 1) {
         const int r = tid & 31;
         for (int kk = tid >> 5; kk < OZ_ST_K; kk += 8) {
@@ -153,7 +239,7 @@ __global__ void __launch_bounds__(256) k_oz_slice_tile(OzSliceArgs a)
     for (int r = tid / OZ_ST_K; r < OZ_ST_R; r += 256 / OZ_ST_K) {
         const int i = i0 + r;
         if (i >= rows) break;
-        const int E = a.exps[b] ? (int)a.exps[b][i] : a.exp0;
+        const int E = FUSE ? s_e[r] : (a.exps[b] ? (int)a.exps[b][i] : a.exp0);
         uint16_t d[S];
         if (S == 4)
             oz_digits_bal(T[r][kk], E, d);       // the Khatri-Rao core's operand (balanced digits)
@@ -238,18 +324,33 @@ int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st)
         exps = exps || a.exps[b] != nullptr;
     }
     if (rmax <= 0 || ldmax <= 0) return 0;
+    bool fuse = false;
     if (exps) {
         // every problem of one call either has exponents or not (the slicers are per operand)
-        for (int b = 0; b < nb; ++b)
+        int kmax = 0;
+        for (int b = 0; b < nb; ++b) {
             if (!a.exps[b]) return RHOSVD_ERR_INVALID_ARG;
-        k_oz_rowexp<<<dim3((rmax + OZ_RE_ROWS - 1) / OZ_RE_ROWS, nb), 256, 0, st>>>(a);
-        RH_CHECK_LAUNCH();
+            kmax = max(kmax, a.K[b]);
+        }
+        fuse = a.S == OZ_S64 && kmax <= OZ_FUSE_KMAX;
+        bool kcontig = true;
+        for (int b = 0; b < nb; ++b) kcontig = kcontig && a.cs[b] == 1;
+        if (!fuse && kcontig && kmax >= 1024) {
+            k_oz_rowexp_long<<<dim3(rmax, nb), 256, 0, st>>>(a);
+            RH_CHECK_LAUNCH();
+        } else if (!fuse) {
+            k_oz_rowexp<<<dim3((rmax + OZ_RE_ROWS - 1) / OZ_RE_ROWS, nb), 256, 0, st>>>(a);
+            RH_CHECK_LAUNCH();
+        }
     }
     dim3 grid((ldmax + OZ_ST_K - 1) / OZ_ST_K, (rmax + OZ_ST_R - 1) / OZ_ST_R, nb);
     switch (a.S) {
-    case OZ_S64: k_oz_slice_tile<OZ_S64><<<grid, 256, 0, st>>>(a); break;
-    case 4: k_oz_slice_tile<4><<<grid, 256, 0, st>>>(a); break;
-    case 1: k_oz_slice_tile<1><<<grid, 256, 0, st>>>(a); break;
+    case OZ_S64:
+        if (fuse) k_oz_slice_tile<OZ_S64, true><<<grid, 256, 0, st>>>(a);
+        else k_oz_slice_tile<OZ_S64, false><<<grid, 256, 0, st>>>(a);
+        break;
+    case 4: k_oz_slice_tile<4, false><<<grid, 256, 0, st>>>(a); break;
+    case 1: k_oz_slice_tile<1, false><<<grid, 256, 0, st>>>(a); break;
     default: return RHOSVD_ERR_INVALID_ARG;
     }
     RH_CHECK_LAUNCH();

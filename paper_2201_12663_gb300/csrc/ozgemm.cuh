@@ -111,6 +111,34 @@ enum OzEpi { OZ_EPI_STORE = 0, OZ_EPI_RESID = 1 };
 // group of up to 7 digit pairs stays exact in FP32 over 128 K (np 2^14 128 < 2^24).
 constexpr int OZ_S64 = 7, OZ_W64 = 7;
 
+// FP32 helpers built from the bits (integer work, no FP64 instruction: GB300 issues those at about
+// two lanes a cycle per SM).
+// 2^e as a float (subnormal from 2^-149, zero below it, infinity above 2^127)
+__device__ __forceinline__ float pow2f(int e)
+{
+    return e >= -126 ? __int_as_float(min(e + 127, 255) << 23) : (e >= -149 ? __int_as_float(1 << (e + 149)) : 0.f);
+}
+
+// x = rh + rl as two floats without FP64 work: rh is x truncated to 24 significant bits, rl the
+// rest (up to 29 bits) rounded to a float (|rl - (x - rh)| <= 2^-48 |x|).  A value outside FP32's
+// normal range (|x| < 2^-126; |x| >= 2^128 does not occur, the operands are normalised) gives
+// 0 + 0.
+__device__ __forceinline__ void split_f64(double x, float& rh, float& rl)
+{
+    const uint32_t h = (uint32_t)__double2hiint(x), l = (uint32_t)__double2loint(x);
+    const uint32_t sgn = h & 0x80000000u;
+    const int E = (int)((h >> 20) & 0x7ffu) - 1023;
+    const bool ok = E >= -126 && E <= 127;
+    const uint32_t fh = sgn | ((uint32_t)(E + 127) << 23) | ((h & 0xfffffu) << 3) | (l >> 29);
+    const uint32_t r29 = l & 0x1fffffffu;
+    // the 29-bit rest as a float: its two parts are exact (2^23 + d less 2^23), one rounding in the fma
+    const float ra = __fsub_rn(__uint_as_float(0x4B000000u | (r29 >> 6)), 8388608.0f);
+    const float rb = __fsub_rn(__uint_as_float(0x4B000000u | (r29 & 63u)), 8388608.0f);
+    const float rm = __fmul_rn(__fmaf_rn(ra, 64.0f, rb), pow2f(E - 52));
+    rh = ok ? __uint_as_float(fh) : 0.f;
+    rl = ok ? __uint_as_float(__float_as_uint(rm) | sgn) : 0.f;
+}
+
 // S digit planes (bf16 bit patterns) of the signed integer F = +-round(|x| 2^(W S - E)).
 // Digit s (s = 1..S) is d 2^(-W(s-1)) with d < 2^W (s > 1) or d <= 2^W (s = 1): at most eight
 // significant bits and a power-of-two scale, so the float d * 2^(-W(s-1)) is exact and its bf16
@@ -210,7 +238,7 @@ struct OzSliceArgs {
 };
 int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st);
 
-// the four instantiations: FP64-class product (S = 6, all groups exact) storing C or reducing
+// the instantiations: FP64-class product (S = 7 digits of 7 bits, all groups exact) storing C or reducing
 // the residual energy; range sketch against Rademacher signs; Khatri-Rao core (S = 4)
 enum OzKind { OZ_F64_STORE = 0, OZ_F64_RESID = 1, OZ_SKETCH = 2, OZ_CORE = 3, OZ_BF16 = 4 };
 // OZ_BF16: one plane per operand holding arbitrary BF16 values (not digits), exponents 8 and 8

@@ -184,32 +184,6 @@ __device__ __forceinline__ double f2d_scaled(float x, int e)
     return ((b << 1) == 0u || be <= 0) ? 0.0 : __hiloint2double((int)h, (int)(f << 29));
 }
 
-// 2^e as a float (subnormal from 2^-149, zero below it, infinity above 2^127)
-__device__ __forceinline__ float pow2f(int e)
-{
-    return e >= -126 ? __int_as_float(min(e + 127, 255) << 23) : (e >= -149 ? __int_as_float(1 << (e + 149)) : 0.f);
-}
-
-// ref = rh + rl as two floats without FP64 work: rh is ref truncated to 24 significant bits, rl the
-// rest (up to 29 bits) rounded to a float (|rl - (ref - rh)| <= 2^-47 |ref|).  An entry outside
-// FP32's normal range (|ref| < 2^-126; |ref| >= 2^128 does not occur, the operands are
-// normalised) gives 0 + 0.
-__device__ __forceinline__ void split_ref(double ref, float& rh, float& rl)
-{
-    const uint32_t h = (uint32_t)__double2hiint(ref), l = (uint32_t)__double2loint(ref);
-    const uint32_t sgn = h & 0x80000000u;
-    const int E = (int)((h >> 20) & 0x7ffu) - 1023;
-    const bool ok = E >= -126 && E <= 127;
-    const uint32_t fh = sgn | ((uint32_t)(E + 127) << 23) | ((h & 0xfffffu) << 3) | (l >> 29);
-    const uint32_t r29 = l & 0x1fffffffu;
-    // the 29-bit rest as a float: its two parts are exact (2^23 + d less 2^23), one rounding in the fma
-    const float ra = __fsub_rn(__uint_as_float(0x4B000000u | (r29 >> 6)), 8388608.0f);
-    const float rb = __fsub_rn(__uint_as_float(0x4B000000u | (r29 & 63u)), 8388608.0f);
-    const float rm = __fmul_rn(__fmaf_rn(ra, 64.0f, rb), pow2f(E - 52));
-    rh = ok ? __uint_as_float(fh) : 0.f;
-    rl = ok ? __uint_as_float(__float_as_uint(rm) | sgn) : 0.f;
-}
-
 // hi + lo += x, with the error of the high sum kept exactly (Knuth's two-sum) but the pair not
 // renormalised: seven operations instead of nine, for the residual's short sums (an item of at
 // most a few readback blocks: the low word's own rounding stays below 2^-40 of the sum)
@@ -630,7 +604,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
                     const float sf = pow2f(eL + s_ec[e][c] - 2 * W);
                     const float h = __fmul_rn(hi[c], sf), l = __fmul_rn(lo[c], sf);
                     float rh, rl;
-                    split_ref(rv[EPI == OZ_EPI_RESID ? c : 0], rh, rl);
+                    split_f64(rv[EPI == OZ_EPI_RESID ? c : 0], rh, rl);
                     const float s1 = __fsub_rn(rh, h);
                     const float bp = __fsub_rn(s1, rh);
                     const float e1 = __fadd_rn(__fsub_rn(rh, __fsub_rn(s1, bp)), __fsub_rn(-h, bp));
