@@ -47,9 +47,11 @@ extern "C" {
                                            projection, Ritz vectors, residual, core) on the
                                            tcgen05 tensor cores with exact digit planes held as
                                            BF16 (seven 7-bit digits for the FP64-class products,
-                                           four 8-bit digits for the core) and FP32 accumulation
-                                           read back into FP64 (about 2^-40 of sum|a||b| for the
-                                           core); the small factorisations stay FP64           */
+                                           five for the range sketch when every rank is chosen
+                                           by eps and eps >= 1.5e-9 sqrt(max n), four 8-bit
+                                           digits for the core) and FP32 accumulation read back
+                                           into FP64 (about 2^-40 of sum|a||b| for the core);
+                                           the small factorisations stay FP64                  */
 
 #define RHOSVD_K_MAX 256                /* largest subspace width k handled on the device    */
 

@@ -264,6 +264,7 @@ struct Plan {
     int mixed;
     int ldR, ldn, ldk;            // plane row lengths (multiples of 8) for K = R, n, k
     int tkR;                      // k tiles of the tile-major U~ planes with K = R (even)
+    int sk5;                      // the range sketches take five digits of U~ (OZ_SKETCH5)
     int tkC;                      // k tiles of the core's diag(xi') V1 planes
     long long sSg;                // per-mode size of the sketch's sign plane (elements)
     size_t o_sgn;
@@ -396,6 +397,16 @@ int make_plan(const rhosvd_cp* cp, const rhosvd_opts* o, Plan* p, int k0 = 0, in
         // the two digit-plane sets of U~ are tile-major (whole 128 x 16 tiles, see ozgemm.cuh):
         // U1 rows x, k = nu; U2 rows nu, k = x
         p->tkR = (R + 31) / 32 * 2;     // an even count: the sketch streams k tiles in pairs
+        // Five digits of U~ for the range sketch where their error cannot matter at the
+        // requested eps: the sketch of U~ + E with |E_ij| <= 2^-35 (fixed exponent 1, 35 bits)
+        // finds a basis whose projection error exceeds U~'s own by at most ||E||_F <= 2^-35
+        // sqrt(n) ||U~||_F (unit columns), and the residual energy that decides the ranks is
+        // measured on U~ itself afterwards.  With eps >= 1.5e-9 sqrt(n) that is at most 2% of
+        // eps ||U~||_F, 4e-4 of the threshold energy: a rank moves only at a tie that close.
+        // Every rank chosen by eps; otherwise, and below that eps, seven digits.
+        bool by_eps = true;
+        for (int l = 0; l < 3; ++l) by_eps = by_eps && o->ranks[l] == 0;
+        p->sk5 = by_eps && o->eps >= 1.5e-9 * sqrt((double)p->NQ);
         p->sU1 = (long long)OZ_S64 * ((p->NQ + 127) / 128 * 128) * (p->tkR * 16LL);
         p->sU2 = (long long)OZ_S64 * ((R + 127) / 128 * 128) * ((p->NQ + 15) / 16 * 16LL);
         // the small operands' plane sets (tile-major: rows padded to 128, k to 16; enough for
@@ -738,6 +749,7 @@ int Reduction::slice_sketch_operand()
         SliceTArgs sb;
         memset(&sb, 0, sizeof(sb));
         sb.E0 = 1;
+        sb.S = p.sk5 ? OZ_S_SKETCH5 : OZ_S64;
         int nmax = 0;
         for (int b = 0; b < nsk; ++b) {
             const int l = sk.m[b];
@@ -920,7 +932,7 @@ int Reduction::sketch()
                 q.Cpart = ozpart + (size_t)l * p.oz_s_sketch * NK;
                 q.split_stride = NK;
             }
-            STAGE("sketch", launch_ozgemm(ob, OZ_SKETCH, st));
+            STAGE("sketch", launch_ozgemm(ob, p.sk5 ? OZ_SKETCH5 : OZ_SKETCH, st));
         } else {
             STAGE("sketch", launch_gemm_splitk(gb, part, st));
         }
@@ -1138,7 +1150,7 @@ int Reduction::deflation_sketch(cudaStream_t st, double* Ydf)
             q.Cpart = p.oz_s_defl > 1 ? (double*)(ws + p.o_dpart) + (size_t)l * p.oz_s_defl * p.NQ * p.kdef : nullptr;
             q.split_stride = (long long)p.NQ * p.kdef;
         }
-        STAGE("deflate_sketch", launch_ozgemm(ob, OZ_SKETCH, st));
+        STAGE("deflate_sketch", launch_ozgemm(ob, p.sk5 ? OZ_SKETCH5 : OZ_SKETCH, st));
     } else {
         GemmBatch gd;
         memset(&gd, 0, sizeof(gd));

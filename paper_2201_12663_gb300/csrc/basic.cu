@@ -271,10 +271,12 @@ __global__ void k_normalize(NormArgs a, const double* keepf, double* Un, long lo
     if (lane == 0) nn2[(long long)l * a.R + warp] = s;
 }
 
-// Transposed digit planes with one fixed exponent E0 (|x| < 2^E0): planes[s][x ld + nu] from
-// X(x, nu) = X[x + ldx nu], zero for nu in [K, ld).  A 64 x 32 (x by nu) tile goes through shared
-// memory so that reads run along x; a thread then cuts 8 consecutive nu of one x and writes one
-// 16-byte chunk to every plane.  grid (ceil(ld/32), ceil(rows/64), nmodes), block 256.
+// Transposed digit planes (S digits of 7 bits) with one fixed exponent E0 (|x| < 2^E0):
+// planes[s][x ld + nu] from X(x, nu) = X[x + ldx nu], zero for nu in [K, ld).  A 64 x 32 (x by
+// nu) tile goes through shared memory so that reads run along x; a thread then cuts 8 consecutive
+// nu of one x and writes one 16-byte chunk to every plane.  grid (ceil(ld/32), ceil(rows/64),
+// nmodes), block 256.
+template <int S>
 __global__ void __launch_bounds__(256) k_slice_t(SliceTArgs a)
 {
     const int b = blockIdx.z;
@@ -298,18 +300,18 @@ __global__ void __launch_bounds__(256) k_slice_t(SliceTArgs a)
     uint16_t* P = sel3(a.planes, b);
     const long long pst = sel3(a.pstride, b);
     const int tk = sel3(a.tiles_k, b), th = sel3(a.tile_h, b);
-    uint32_t w[OZ_S64][4];
+    uint32_t w[S][4];
 #pragma unroll
     for (int q = 0; q < 8; q += 2) {
-        uint16_t d0[OZ_S64], d1[OZ_S64];
-        oz_digits(tile[c * 8 + q][xx], a.E0, OZ_S64, d0, OZ_W64);
-        oz_digits(tile[c * 8 + q + 1][xx], a.E0, OZ_S64, d1, OZ_W64);
+        uint16_t d0[S], d1[S];
+        oz_digits(tile[c * 8 + q][xx], a.E0, S, d0, OZ_W64);
+        oz_digits(tile[c * 8 + q + 1][xx], a.E0, S, d1, OZ_W64);
 #pragma unroll
-        for (int t = 0; t < OZ_S64; ++t) w[t][q >> 1] = (uint32_t)d0[t] | ((uint32_t)d1[t] << 16);
+        for (int t = 0; t < S; ++t) w[t][q >> 1] = (uint32_t)d0[t] | ((uint32_t)d1[t] << 16);
     }
 #pragma unroll
-    for (int t = 0; t < OZ_S64; ++t) {
-        uint16_t* dq = tk > 0 ? P + oz_tiled_index(OZ_S64, tk, th, t, x, nuc) : P + (long long)t * pst + (long long)x * ld + nuc;
+    for (int t = 0; t < S; ++t) {
+        uint16_t* dq = tk > 0 ? P + oz_tiled_index(S, tk, th, t, x, nuc) : P + (long long)t * pst + (long long)x * ld + nuc;
         *reinterpret_cast<uint4*>(dq) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
     }
 }
@@ -357,7 +359,9 @@ int launch_slice_t(const SliceTArgs& a, int nb, int ldmax, int rowsmax, cudaStre
 {
     if (nb <= 0 || ldmax <= 0 || rowsmax <= 0) return 0;
     dim3 grid((ldmax + 31) / 32, (rowsmax + 63) / 64, nb);
-    k_slice_t<<<grid, 256, 0, st>>>(a);
+    if (a.S == OZ_S_SKETCH5) k_slice_t<OZ_S_SKETCH5><<<grid, 256, 0, st>>>(a);
+    else if (a.S == 0 || a.S == OZ_S64) k_slice_t<OZ_S64><<<grid, 256, 0, st>>>(a);
+    else return RHOSVD_ERR_INVALID_ARG;
     RH_CHECK_LAUNCH();
     return 0;
 }

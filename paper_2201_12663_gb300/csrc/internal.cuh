@@ -313,6 +313,7 @@ struct SliceTArgs {
     int E0;
     int tiles_k[3];            // > 0: tile-major planes with this many k tiles (see ozgemm.cuh)
     int tile_h[3];             // their rows per tile
+    int S;                     // digits: 0 or 7 (the FP64-class seven), or 5 (OZ_SKETCH5)
 };
 
 // The range sketch's Rademacher signs as a tile-major BF16 plane (rows j = sketch column, k = nu).

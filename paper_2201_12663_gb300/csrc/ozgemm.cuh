@@ -240,7 +240,10 @@ int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st);
 
 // the instantiations: FP64-class product (S = 7 digits of 7 bits, all groups exact) storing C or reducing
 // the residual energy; range sketch against Rademacher signs; Khatri-Rao core (S = 4)
-enum OzKind { OZ_F64_STORE = 0, OZ_F64_RESID = 1, OZ_SKETCH = 2, OZ_CORE = 3, OZ_BF16 = 4 };
+enum OzKind { OZ_F64_STORE = 0, OZ_F64_RESID = 1, OZ_SKETCH = 2, OZ_CORE = 3, OZ_BF16 = 4, OZ_SKETCH5 = 5 };
+// OZ_SKETCH5: the range sketch with OZ_S_SKETCH5 digits of U~ (35 bits) instead of seven, for the
+// tolerances at which its digit error stays far below eps (the choice and its bound: api.cu).
+constexpr int OZ_S_SKETCH5 = 5;
 // OZ_BF16: one plane per operand holding arbitrary BF16 values (not digits), exponents 8 and 8
 // (scale 2^0), FP32 accumulation read back every 256 K: a plain BF16 GEMM with FP64 output,
 // used by the learned-proposal network.

@@ -228,15 +228,17 @@ __host__ __device__ constexpr int npairs(int SA, int SB, int g)
 //           B, tile-major, 128 sketch columns, written once per sketch by k_sign_planes), col =
 //           the U~ planes (the problem's A, tile-major, 32 rows of x), one MMA of N = 224 a
 //           stage, 7 exact groups of one pair each.
+//   TK_SIGN5 (the range sketch with five digits of U~): as TK_SIGN, one MMA of N = 160 a K step,
+//           5 exact groups.
 //   TK_BF16 (one plane of arbitrary BF16 values): lane = A, col = B, NT = 64, one group.
-enum TmaKind { TK_F64 = 0, TK_SIGN = 1, TK_BF16 = 2 };
+enum TmaKind { TK_F64 = 0, TK_SIGN = 1, TK_BF16 = 2, TK_SIGN5 = 3 };
 
 template <int KIND>
 struct Plan {
     static constexpr int SL = KIND == TK_F64 ? OZ_S64 : 1;
-    static constexpr int SC = KIND == TK_BF16 ? 1 : OZ_S64;
+    static constexpr int SC = KIND == TK_BF16 ? 1 : (KIND == TK_SIGN5 ? OZ_S_SKETCH5 : OZ_S64);
     static constexpr int NT = KIND == TK_BF16 ? 64 : 32;
-    static constexpr int GMAX = KIND == TK_F64 ? 9 : (KIND == TK_SIGN ? 8 : 2);
+    static constexpr int GMAX = KIND == TK_F64 ? 9 : (KIND == TK_SIGN ? 8 : (KIND == TK_SIGN5 ? OZ_S_SKETCH5 + 1 : 2));
     static constexpr int W = KIND == TK_BF16 ? 8 : OZ_W64;
     static constexpr int NG = GMAX - 1;
     static constexpr int ZP = NG > SC ? NG - SC : 0;     // zero planes after the stacked ones
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_oztma(OzBatch batch, const __g
     using PL = Plan<KIND>;
     constexpr int SL = PL::SL, SC = PL::SC, NT = PL::NT, W = PL::W, NG = PL::NG, NCOL = PL::NCOL;
     constexpr int KSUB = PL::KSUB, RBS = PL::RBS;
-    constexpr bool SIGN = KIND == TK_SIGN;
+    constexpr bool SIGN = KIND == TK_SIGN || KIND == TK_SIGN5;
     constexpr int L_PLANE = OZ_BM * TK * 2;              // 4096 B: 128 rows x 32 B
     constexpr int C_PLANE = NT * TK * 2;
     constexpr int L_BYTES = SL * L_PLANE;                  // one K step of the lane operand
@@ -1014,7 +1016,7 @@ template <int KIND, int EPI>
 int run_tma(const OzBatch& b, cudaStream_t st)
 {
     using PL = Plan<KIND>;
-    constexpr bool SIGN = KIND == TK_SIGN;
+    constexpr bool SIGN = KIND == TK_SIGN || KIND == TK_SIGN5;
     constexpr int L_BYTES = PL::SL * OZ_BM * TK * 2, C_PLANE = PL::NT * TK * 2;
     constexpr int STAGE = (PL::KSUB * (L_BYTES + (PL::SC + PL::ZP) * C_PLANE) + 1023) / 1024 * 1024;
     constexpr int ST_FIT = (T_SMEM_MAX - 4096) / STAGE;
@@ -1096,14 +1098,16 @@ int launch_ozcore_tma(const OzBatch& b, cudaStream_t st)
 
 bool ozgemm_tma_supports(const OzBatch& b, OzKind kind)
 {
-    if (kind != OZ_F64_STORE && kind != OZ_F64_RESID && kind != OZ_SKETCH && kind != OZ_BF16) return false;
+    if (kind != OZ_F64_STORE && kind != OZ_F64_RESID && kind != OZ_SKETCH && kind != OZ_SKETCH5 && kind != OZ_BF16)
+        return false;
+    const bool sketch = kind == OZ_SKETCH || kind == OZ_SKETCH5;
     if (!encoder()) return false;
     const int S = kind == OZ_BF16 ? 1 : OZ_S64;
     const int nt = kind == OZ_BF16 ? Plan<TK_BF16>::NT : Plan<TK_F64>::NT;
     for (int i = 0; i < b.nbatch; ++i) {
         const OzProblem& q = b.p[i];
         // the operand on the TMEM lanes and the one stacked along N (the sketch swaps them)
-        const OzPlanes* ops[2] = {kind == OZ_SKETCH ? &q.B : &q.A, kind == OZ_SKETCH ? &q.A : &q.B};
+        const OzPlanes* ops[2] = {sketch ? &q.B : &q.A, sketch ? &q.A : &q.B};
         for (int o = 0; o < 2; ++o) {
             const OzPlanes& pl = *ops[o];
             if (!pl.base || ((uintptr_t)pl.base) % 16 != 0) return false;
@@ -1125,7 +1129,8 @@ bool ozgemm_tma_supports(const OzBatch& b, OzKind kind)
 long long ozgemm_tma_tiles(OzKind kind, int M, int N)
 {
     const int nt = kind == OZ_BF16 ? Plan<TK_BF16>::NT : Plan<TK_F64>::NT;
-    if (kind == OZ_SKETCH) return (long long)((N + OZ_BM - 1) / OZ_BM) * ((M + Plan<TK_SIGN>::NT - 1) / Plan<TK_SIGN>::NT);
+    if (kind == OZ_SKETCH || kind == OZ_SKETCH5)
+        return (long long)((N + OZ_BM - 1) / OZ_BM) * ((M + Plan<TK_SIGN>::NT - 1) / Plan<TK_SIGN>::NT);
     return (long long)((M + OZ_BM - 1) / OZ_BM) * ((N + nt - 1) / nt);
 }
 
@@ -1135,6 +1140,7 @@ int launch_ozgemm_tma(const OzBatch& b, OzKind kind, cudaStream_t st)
     case OZ_F64_STORE: return run_tma<TK_F64, OZ_EPI_STORE>(b, st);
     case OZ_F64_RESID: return run_tma<TK_F64, OZ_EPI_RESID>(b, st);
     case OZ_SKETCH: return run_tma<TK_SIGN, OZ_EPI_STORE>(b, st);
+    case OZ_SKETCH5: return run_tma<TK_SIGN5, OZ_EPI_STORE>(b, st);
     case OZ_BF16: return run_tma<TK_BF16, OZ_EPI_STORE>(b, st);
     default: return RHOSVD_ERR_INVALID_ARG;
     }
