@@ -172,31 +172,49 @@ __global__ void __launch_bounds__(256) k_oz_slice_tile(OzSliceArgs a)
     if (FUSE) {
         if (tid < OZ_ST_R) s_e[tid] = -4096;
         __syncthreads();
+        // (loads issued four at a time: these reads are latency-bound L2 hits)
         if (rs == 1) {
             // rows contiguous: a warp reads 32 consecutive rows at one k
             const int r = tid & 31, i = i0 + r;
             int e = -4096;
-            if (i < live)
-                for (int k = tid >> 5; k < K; k += 8) {
+            if (i < live) {
+                int k = tid >> 5;
+                for (; k + 24 < K; k += 32) {
+                    double x[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) x[q] = X[(long long)i + (long long)(k + 8 * q) * cs];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) e = max(e, oz_frexp_exp(ks ? x[q] * ks[k + 8 * q] : x[q]));
+                }
+                for (; k < K; k += 8) {
                     double x = X[(long long)i + (long long)k * cs];
                     if (ks) x *= ks[k];
                     e = max(e, oz_frexp_exp(x));
                 }
+            }
             atomicMax(&s_e[r], e);
         } else {
-            // k contiguous (or strided both ways): a warp per row, lanes along k
+            // k contiguous (or strided both ways): lanes along k, a warp's four rows read together
             const int lane = tid & 31, w = tid >> 5;
-            for (int r = w; r < OZ_ST_R; r += 8) {
-                const int i = i0 + r;
-                int e = -4096;
-                if (i < live)
-                    for (int k = lane; k < K; k += 32) {
-                        double x = X[(long long)i * rs + (long long)k * cs];
-                        if (ks) x *= ks[k];
-                        e = max(e, oz_frexp_exp(x));
-                    }
-                for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-                if (lane == 0) s_e[r] = e;
+            int e[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) e[q] = -4096;
+            for (int k = lane; k < K; k += 32) {
+                double x[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = i0 + w + 8 * q;
+                    x[q] = i < live ? X[(long long)i * rs + (long long)k * cs] : 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (i0 + w + 8 * q < live) e[q] = max(e[q], oz_frexp_exp(ks ? x[q] * ks[k] : x[q]));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int eq = e[q];
+                for (int o = 16; o > 0; o >>= 1) eq = max(eq, __shfl_xor_sync(0xffffffffu, eq, o));
+                if (lane == 0) s_e[w + 8 * q] = eq;
             }
         }
         __syncthreads();

@@ -244,9 +244,10 @@ struct Plan {
     static constexpr int ZP = NG > SC ? NG - SC : 0;     // zero planes after the stacked ones
     static constexpr int NCOL = NG * NT;
     static constexpr int RBK = KIND == TK_F64 ? 8 : 16;   // K steps of 16 a readback block
-    // K steps a pipeline stage: the sketch streams its operands with two a stage (half the copies
-    // and barrier round trips per byte); its stacked planes need no zero plane between the steps
-    static constexpr int KSUB = KIND == TK_BF16 ? 1 : 2;
+    // K steps a pipeline stage: one producer thread completes about one stage per 0.7 us whatever
+    // its size, so the sketch kinds (no zero plane between the steps' stacked planes) take four
+    // (36 or 44 KB stages) and the FP64-class kinds two (their per-step col copies, 72 KB stages)
+    static constexpr int KSUB = KIND == TK_BF16 ? 1 : (KIND == TK_F64 ? 2 : 4);
     static constexpr int RBS = RBK / KSUB;              // stages a readback block
     static constexpr int T(int s) { return s == 1 ? NG : (SC < GMAX - s ? SC : GMAX - s); }
     static constexpr bool ok()
