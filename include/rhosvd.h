@@ -446,6 +446,17 @@ int rhosvd_rs_energy(const rhosvd_cp* P_long, int N, const int* idx, const doubl
  * RHOSVD_ERR_INVALID_ARG for n < 0 or null pointers with n > 0; asynchronous on `stream`. */
 int rhosvd_selftest_fastmath(const double* x, double* rcp, double* rsq, int n, void* stream);
 
+/* rhosvd_selftest_bits evaluates, for n elements, the conversions the tensor-core products'
+ * epilogues and the normalisation build from the bits instead of FP64 instructions:
+ * rh[i] + rl[i] ~ x[i] (rh = x truncated to 24 significant bits, rl the rest rounded to a float:
+ * within 2^-48 |x| for |x| >= 2^-97, 2^-120 below; both 0 for |x| < 2^-126), fd[i] = f[i] 2^e[i] exactly as a double (0 below FP64's normal
+ * range), p2[i] = 2^e[i] as a float (subnormal from 2^-149, 0 below, infinity above 2^127).
+ * Inputs x (doubles), f (floats), e (ints) and outputs rh, rl, p2 (floats), fd (doubles) are
+ * device arrays of n elements, caller-owned.  Returns RHOSVD_ERR_INVALID_ARG for n < 0 or null
+ * pointers with n > 0; asynchronous on `stream`. */
+int rhosvd_selftest_bits(const double* x, const float* f, const int* e, float* rh, float* rl, double* fd,
+                         float* p2, int n, void* stream);
+
 /* FP64 rate probe (no paper counterpart: measurement support; the denominators of the FP64
  * rooflines are measured with it).  Launches `blocks` blocks of 256 threads, each thread
  * running eight independent FP64 fma chains of `iters` steps: 4096 * iters FLOP a block.

@@ -192,6 +192,8 @@ def load(build_if_missing: bool = False):
                                        _c.POINTER(rhosvd_horner_step), _c.c_void_p, _c.c_size_t, _c.c_void_p]
         L.rhosvd_selftest_fastmath.restype = _c.c_int
         L.rhosvd_selftest_fastmath.argtypes = [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p]
+        L.rhosvd_selftest_bits.restype = _c.c_int
+        L.rhosvd_selftest_bits.argtypes = [_c.c_void_p] * 7 + [_c.c_int, _c.c_void_p]
         L.rhosvd_launch_count.restype = _c.c_longlong
         L.rhosvd_profile_enable.restype = _c.c_int
         L.rhosvd_profile_enable.argtypes = [_c.c_int]
@@ -452,6 +454,25 @@ def rhosvd_selftest_fastmath(x, stream=None):
     if rc != RHOSVD_OK:
         raise RhosvdError(rc, "rhosvd_selftest_fastmath")
     return rcp, rsq
+
+
+def rhosvd_selftest_bits(x, f, e, stream=None):
+    """(rh, rl, fd, p2) by the library's bit-level conversions: x float64, f float32, e int32 CUDA
+    tensors of one length; rh + rl ~ x, fd = f 2^e (float64), p2 = 2^e (float32)."""
+    torch = _torch()
+    x, f, e = x.contiguous(), f.contiguous(), e.contiguous()
+    n = int(x.numel())
+    if f.numel() != n or e.numel() != n:
+        raise RhosvdError(RHOSVD_ERR_INVALID_ARG, "rhosvd_selftest_bits: lengths differ")
+    rh = torch.empty(n, dtype=torch.float32, device=x.device)
+    rl, p2 = torch.empty_like(rh), torch.empty_like(rh)
+    fd = torch.empty(n, dtype=torch.float64, device=x.device)
+    ptr = lambda t: _c.c_void_p(t.data_ptr())
+    rc = load().rhosvd_selftest_bits(ptr(x), ptr(f), ptr(e), ptr(rh), ptr(rl), ptr(fd), ptr(p2), n,
+                                     _stream_handle(stream))
+    if rc != RHOSVD_OK:
+        raise RhosvdError(rc, "rhosvd_selftest_bits")
+    return rh, rl, fd, p2
 
 
 def rhosvd_launch_count() -> int:

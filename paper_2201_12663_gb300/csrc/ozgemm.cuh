@@ -120,7 +120,8 @@ __device__ __forceinline__ float pow2f(int e)
 }
 
 // x = rh + rl as two floats without FP64 work: rh is x truncated to 24 significant bits, rl the
-// rest (up to 29 bits) rounded to a float (|rl - (x - rh)| <= 2^-48 |x|).  A value outside FP32's
+// rest (up to 29 bits) rounded to a float: |rh + rl - x| <= 2^-48 |x| for |x| >= 2^-97, below
+// that the rest leaves FP32's range (an absolute error under 2^-120).  A value outside FP32's
 // normal range (|x| < 2^-126; |x| >= 2^128 does not occur, the operands are normalised) gives
 // 0 + 0.
 __device__ __forceinline__ void split_f64(double x, float& rh, float& rl)

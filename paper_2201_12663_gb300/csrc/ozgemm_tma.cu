@@ -1065,6 +1065,20 @@ int run_tma(const OzBatch& b, cudaStream_t st)
 
 }  // namespace
 
+namespace {
+
+__global__ void k_selftest_bits(const double* x, const float* f, const int* e, float* rh, float* rl, double* fd,
+                                float* p2, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        split_f64(x[i], rh[i], rl[i]);
+        fd[i] = f2d_scaled(f[i], e[i]);
+        p2[i] = pow2f(e[i]);
+    }
+}
+
+}  // namespace
+
 bool ozcore_tma_supports(const OzBatch& b)
 {
     for (int i = 0; i < b.nbatch; ++i) {
@@ -1148,3 +1162,13 @@ int launch_ozgemm_tma(const OzBatch& b, OzKind kind, cudaStream_t st)
 }
 
 }  // namespace rh
+
+extern "C" int rhosvd_selftest_bits(const double* x, const float* f, const int* e, float* rh, float* rl, double* fd,
+                                    float* p2, int n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !f || !e || !rh || !rl || !fd || !p2))) return RHOSVD_ERR_INVALID_ARG;
+    if (n == 0) return RHOSVD_OK;
+    const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    rh::k_selftest_bits<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, f, e, rh, rl, fd, p2, n);
+    return cudaGetLastError() == cudaSuccess ? RHOSVD_OK : RHOSVD_ERR_CUDA;
+}
