@@ -144,6 +144,53 @@ __global__ void __launch_bounds__(256) k_oz_rowexp_long(OzSliceArgs a)
     }
 }
 
+// The same for rows-contiguous operands of long K (rs = 1: B of B Bᵀ stored with its k rows
+// adjacent, the core's V¹): two rows a block, 128 threads along k each, so that a launch has
+// rows / 2 x problems blocks instead of rows / 8 (eight rows a block took ~37 us at K = 4096).
+// A warp's load covers 16 k of two adjacent rows (16-byte pieces of L2-resident data).
+// grid (ceil(rows / 2), nb).
+__global__ void __launch_bounds__(256) k_oz_rowexp_cols(OzSliceArgs a)
+{
+    const int b = blockIdx.y;
+    const int rows = a.rows[b];
+    const int r0 = blockIdx.x * 2;
+    if (r0 >= rows) return;
+    const int live = a.drows[b] ? *a.drows[b] : rows;
+    const int K = a.dK[b] ? *a.dK[b] : a.K[b];
+    const double* X = a.X[b];
+    const double* ks = a.kscale[b];
+    const long long cs = a.cs[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r = tid & 1, i = r0 + r;
+    __shared__ int wmax[8][2];
+    int e = -4096;
+    if (i < live) {
+        int k = tid >> 1;
+        // eight independent loads in flight per thread
+        for (; k + 7 * 128 < K; k += 8 * 128) {
+            double x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x[q] = X[(long long)i + (long long)(k + q * 128) * cs];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) e = max(e, oz_frexp_exp(ks ? x[q] * ks[k + q * 128] : x[q]));
+        }
+        for (; k < K; k += 128) {
+            double x = X[(long long)i + (long long)k * cs];
+            if (ks) x *= ks[k];
+            e = max(e, oz_frexp_exp(x));
+        }
+    }
+    for (int o = 16; o > 1; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));   // lanes of one row
+    if (lane < 2) wmax[warp][lane] = e;
+    __syncthreads();
+    if (tid < 2 && r0 + tid < rows) {
+        int E = wmax[0][tid];
+        for (int w = 1; w < 8; ++w) E = max(E, wmax[w][tid]);
+        if (E == -4096) E = -126;
+        a.exps[b][r0 + tid] = (signed char)min(127, max(-126, E));
+    }
+}
+
 constexpr int OZ_ST_R = 32, OZ_ST_K = 64;
 constexpr int OZ_FUSE_KMAX = 256;   // K up to which a slicer block finds its rows' exponents itself
 
@@ -351,10 +398,16 @@ int launch_oz_slice(const OzSliceArgs& a, int nb, cudaStream_t st)
             kmax = max(kmax, a.K[b]);
         }
         fuse = a.S == OZ_S64 && kmax <= OZ_FUSE_KMAX;
-        bool kcontig = true;
-        for (int b = 0; b < nb; ++b) kcontig = kcontig && a.cs[b] == 1;
+        bool kcontig = true, rcontig = true;
+        for (int b = 0; b < nb; ++b) {
+            kcontig = kcontig && a.cs[b] == 1;
+            rcontig = rcontig && a.rs[b] == 1;
+        }
         if (!fuse && kcontig && kmax >= 1024) {
             k_oz_rowexp_long<<<dim3(rmax, nb), 256, 0, st>>>(a);
+            RH_CHECK_LAUNCH();
+        } else if (!fuse && rcontig && kmax >= 1024) {
+            k_oz_rowexp_cols<<<dim3((rmax + 1) / 2, nb), 256, 0, st>>>(a);
             RH_CHECK_LAUNCH();
         } else if (!fuse) {
             k_oz_rowexp<<<dim3((rmax + OZ_RE_ROWS - 1) / OZ_RE_ROWS, nb), 256, 0, st>>>(a);
