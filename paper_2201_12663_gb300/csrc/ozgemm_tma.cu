@@ -185,8 +185,9 @@ __device__ __forceinline__ double f2d_scaled(float x, int e)
 }
 
 // hi + lo += x, with the error of the high sum kept exactly (Knuth's two-sum) but the pair not
-// renormalised: seven operations instead of nine, for the residual's short sums (an item of at
-// most a few readback blocks: the low word's own rounding stays below 2^-40 of the sum)
+// renormalised: seven operations instead of nine, for the residual's short sums (K = r <= 256:
+// at most two readback blocks of eight groups, 16 additions, so the low word's own rounding
+// stays below 2^-40 of the largest partial sum)
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
 {
     const float s = hi + x;
