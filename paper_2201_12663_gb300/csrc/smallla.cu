@@ -72,7 +72,7 @@ __global__ void k_deflate_proj(ModeMap mm, const double* Q, const double* Y, lon
 {
     const int b = mm.m[blockIdx.z];
     const int c = blockIdx.x;
-    const int n = d.n[b], m = d.dm[b];
+    const int n = sel3(d.n, b), m = d.dm[b];
     const double* y = Y + b * nk + (long long)c * n;
     const double* q = Q + b * nk;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -94,7 +94,7 @@ __global__ void k_deflate_sub(ModeMap mm, const double* Q, double* Y, long long 
     const int b = mm.m[blockIdx.z];
     const int c = blockIdx.y;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = d.n[b], m = d.dm[b];
+    const int n = sel3(d.n, b), m = d.dm[b];
     if (x >= n) return;
     const double* q = Q + b * nk + x;
     const double* t = T + b * tstride + (long long)c * KMAX;
@@ -128,7 +128,7 @@ __global__ void k_append(ModeMap mm, double* Q, const double* Q2, long long nk, 
     const int b = mm.m[blockIdx.z];
     const int j = blockIdx.y;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = d.n[b], m = d.dm[b];
+    const int n = sel3(d.n, b), m = d.dm[b];
     if (j >= dm2[b] || x >= n) return;
     Q[b * nk + (long long)(m + j) * n + x] = Q2[b * nk + (long long)j * n + x];
 }
